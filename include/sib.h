@@ -1,0 +1,171 @@
+/*
+ * sib.h -- C ABI of the GB300 Stokes-IB multigrid solver (libsib.so).
+ *
+ * Solves one semi-implicit immersed-boundary step as the linear system of the paper's
+ * Eq. (matrix-impib) (Bhalla, Knepley, Adams, Guy, Griffith, "Scalable smoothing strategies for
+ * a geometric multigrid method for the immersed boundary equations", Sec. 2.2):
+ *
+ *     [ A - dt S K J   G ] [u]   [ g + S K X^n ]
+ *     [ -D             0 ] [p] = [ 0           ]
+ *
+ * on a periodic N x N staggered (MAC) grid of the unit square, h = 1/N, A = (rho/dt) I - mu Lap,
+ * with Peskin four-point spreading S and interpolation J (S = J^T / h^2, Appendix), and the
+ * stiffness K of zero-rest-length springs between Lagrangian markers (Sec. 5, Eq. F-lin-functional).
+ * The solver is flexible GMRES (FP64) preconditioned by one geometric-multigrid V-cycle (Alg. 1)
+ * whose smoother is additive Vanka (Alg. 2, per-cell patches) or the Schur-complement smoother
+ * (Eq. approx-fact-Stokes-IB), with RT0 prolongation, restriction = its adjoint, and the Galerkin
+ * coarse IB operator (Sec. 3.1-3.2).  The V-cycle may run in FP32.
+ *
+ * Conventions for every call
+ *   - Return value: SIB_OK (0) or a negative SIB_ERR_* code; sib_last_error() gives the text.
+ *     No C++ exception crosses this boundary.
+ *   - Array arguments are DEVICE pointers owned by the caller unless the name ends in _host.
+ *     Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL = legacy default
+ *     stream); results are valid once that stream has been synchronised.
+ *   - Eulerian vectors hold 3*N*N values laid out [u | v | p], each block row-major [j][i]:
+ *     u[j][i] at the x-face (i*h, (j+1/2)*h), v[j][i] at the y-face ((i+1/2)*h, j*h), p[j][i] at
+ *     the cell centre.  Level-l vectors (N_l = n_min * 2^l) use the same layout with N_l.
+ *   - Marker positions X are float64 (M, 2) interleaved x,y; edges int32 (E, 2); kappa float64 (E).
+ *   - The library owns all workspace.  It allocates device memory in sib_create/sib_setup
+ *     (and when sizes grow); sib_solve and the level calls do not allocate.
+ *   - A context is not thread-safe; different contexts are independent.
+ *   - N must be n_min * 2^k with n_min a power of two in [4, 64]; N <= 8192.
+ */
+#ifndef SIB_H
+#define SIB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SIB_OK                  0
+#define SIB_ERR_ARG            -1  /* invalid argument (size, null pointer, option out of range)    */
+#define SIB_ERR_CUDA           -2  /* a CUDA runtime call failed                                      */
+#define SIB_ERR_NONFINITE      -3  /* a non-finite value in inputs or in the Krylov recurrence        */
+#define SIB_ERR_NOT_CONVERGED  -4  /* max_it reached; outputs and stats are still written             */
+#define SIB_ERR_BREAKDOWN      -5  /* reserved: Arnoldi breakdown that is not a converged solve      */
+#define SIB_ERR_UNIMPLEMENTED  -6  /* option combination not implemented                             */
+#define SIB_ERR_STATE          -7  /* call out of order (e.g. solve before setup)                    */
+#define SIB_ERR_ALLOC          -8  /* device or host allocation failed                               */
+
+#define SIB_SMOOTHER_VANKA 0       /* additive per-cell Vanka (Alg. 2 with one-cell subdomains)     */
+#define SIB_SMOOTHER_SC    1       /* Schur-complement smoother (Eq. approx-fact-Stokes-IB)         */
+
+#define SIB_PREC_FP64 0
+#define SIB_PREC_FP32 1
+
+#define SIB_MAX_LEVELS 12
+
+typedef struct sib_ctx sib_ctx;    /* opaque, library-owned */
+
+typedef struct {
+    int    smoother;      /* SIB_SMOOTHER_VANKA (default) or SIB_SMOOTHER_SC                       */
+    int    nu1, nu2;      /* pre- and post-smoothing sweeps (2, 2)                                   */
+    double omega;         /* damping of one sweep: Vanka 0.8, SC 1.0 (a negative value = default)    */
+    int    cheb_iters;    /* SC: Chebyshev iterations for the A_IB and Schur-complement solves (2)   */
+    double cheb_lo;       /* SC: Chebyshev interval [cheb_lo, cheb_hi] * lambda_max (0.1, 1.1)       */
+    double cheb_hi;
+    int    power_iters;   /* SC: power iterations for lambda_max estimates at setup (10)             */
+    int    vcycle_fp32;   /* 1: V-cycle in FP32 (coarsest solve FP64), 0: all FP64 (default 1)       */
+    double rtol;          /* stop when ||b - L x||_2 <= rtol ||b||_2 (1e-8)                          */
+    int    max_it;        /* iteration cap (100, the paper's cap)                                    */
+    int    restart;       /* FGMRES restart length (100)                                             */
+    int    add_SKXn;      /* 1: right-hand side g + S K X^n (paper form), 0: g only (1)              */
+    int    use_graphs;    /* 1: replay the V-cycle as a CUDA graph (1)                               */
+} sib_opts;
+
+typedef struct {
+    int    iterations;          /* FGMRES iterations performed                                       */
+    int    converged;           /* 1 if the estimate reached rtol                                    */
+    double rel_residual;        /* true ||b - L x|| / ||b|| computed at exit (FP64)                  */
+    double rel_residual_est;    /* Givens estimate at exit                                           */
+    double bnorm;               /* ||b||_2 of the (projected) right-hand side                        */
+    double setup_ms;            /* device time of the last sib_setup                                 */
+    double solve_ms;            /* device time of the last solve                                     */
+    double history[101];        /* residual estimates, history[0] = ||b||; only the first
+                                   min(iterations + 1, 101) entries are written                      */
+} sib_stats;
+
+/* ---- lifecycle ----------------------------------------------------------------------------- */
+void        sib_default_opts(sib_opts* opts);
+/* Creates a context for an N x N periodic grid with coarsest grid n_min x n_min (8 in the paper,
+ * Sec. 5).  Allocates the grid-sized workspace.  *out is NULL on failure. */
+int         sib_create(sib_ctx** out, int N, int n_min);
+void        sib_destroy(sib_ctx* ctx);
+const char* sib_last_error(const sib_ctx* ctx);   /* never NULL; "" when no error */
+
+/* ---- problem definition (Sec. 2.2: rho, mu, dt; Appendix: markers and springs) ---------------- */
+int sib_set_fluid(sib_ctx* ctx, double rho, double mu, double dt);
+/* Copies X (M x 2), edges (E x 2, int32, 0 <= index < M) and kappa (E) from device memory into
+ * library-owned buffers; marks the structure dirty.  M = 0 or E = 0 are allowed. */
+int sib_set_structure(sib_ctx* ctx, int M, const double* X, int E, const int32_t* edges,
+                      const double* kappa, void* stream);
+/* Replaces kappa only (same edge list); marks the stiffness-dependent setup dirty. */
+int sib_set_stiffness(sib_ctx* ctx, const double* kappa, void* stream);
+int sib_set_options(sib_ctx* ctx, const sib_opts* opts);
+/* SC smoother: override the per-level lambda_max estimates (arrays of sib_num_levels() values;
+ * entry 0, the coarsest level, is ignored).  Pass NULL to return to the power-iteration estimates. */
+int sib_set_eigen_estimates(sib_ctx* ctx, const double* lamA, const double* lamM);
+int sib_get_eigen_estimates(const sib_ctx* ctx, double* lamA, double* lamM);
+
+/* Builds everything that depends on X and kappa: marker binning (stable Morton-ordered sort of
+ * the markers' interpolation stencils), per-level composite stencils J_l = J P (Galerkin coarse IB
+ * operator, Sec. 3.1), the IB entries of every Vanka patch and of diag(A_IB), the dense coarsest
+ * operator and its pseudo-inverse, and (SC) the lambda_max estimates.  Synchronises `stream`. */
+int sib_setup(sib_ctx* ctx, void* stream);
+
+/* ---- the solve (Eq. matrix-impib) -------------------------------------------------------------- */
+/* g: 3N^2 right-hand side [g_u | g_v | g_p] (g_p is used as the divergence right-hand side and is
+ * 0 in the paper's form).  w: 3N^2 output [u | v | p], gauge-fixed (zero-mean p; zero-mean u and
+ * v when rho = 0).  When rho = 0 the velocity means of the right-hand side are removed first.
+ * stats may be NULL.  Returns SIB_ERR_NOT_CONVERGED (outputs written) if max_it is reached. */
+int sib_solve(sib_ctx* ctx, const double* g, double* w, sib_stats* stats, void* stream);
+/* Same with HOST buffers (pageable or pinned): copies g in and w out inside the call. */
+int sib_solve_host(sib_ctx* ctx, const double* g_host, double* w_host, sib_stats* stats, void* stream);
+/* Solve L w = rhs for an arbitrary right-hand side rhs (3N^2), without adding S K X^n.  L is
+ * symmetric, so this is also the transposed (adjoint) solve. */
+int sib_solve_rhs(sib_ctx* ctx, const double* rhs, double* w, sib_stats* stats, void* stream);
+
+/* Gradients of a loss l(w) through the solve (discrete adjoint of Eq. matrix-impib): given the
+ * forward solution w and the adjoint solution lam (both 3N^2), writes
+ *   dkappa[e] = -(Lam_a - Lam_b) . (Y_a - Y_b),   Lam = J lam_u / h^2,  Y = a X^n + dt J u,
+ *   dX[l][d]  = sum_c (d_{X_l^d} Lam_l^c) (K Y)_l^c + a (K Lam)_l^d + dt sum_c (K Lam)_l^c d_{X_l^d} U_l^c
+ * with a = add_SKXn.  dkappa: E doubles, dX: 2M doubles (M x 2).  Spread weights are recomputed
+ * from X (nothing is stored between the solve and this call). */
+int sib_grad(sib_ctx* ctx, const double* w, const double* lam, double* dkappa, double* dX, void* stream);
+
+/* ---- level-wise operations (building blocks of the V-cycle, for parity checks) --------------- */
+int sib_num_levels(const sib_ctx* ctx);                  /* lmax + 1; level 0 is the coarsest   */
+int sib_level_size(const sib_ctx* ctx, int level);       /* N_l                                 */
+/* y = L^l x (prec: SIB_PREC_FP64 -> double*, SIB_PREC_FP32 -> float*). */
+int sib_apply_operator(sib_ctx* ctx, int level, int prec, const void* x, void* y, void* stream);
+/* f = [S K J]^l u on the velocity faces: u and f hold 2 N_l^2 values [u | v]. */
+int sib_apply_ib(sib_ctx* ctx, int level, int prec, const void* u, void* f, void* stream);
+/* x <- `sweeps` smoothing sweeps for L^l x = b (in place), level >= 1. */
+int sib_smooth(sib_ctx* ctx, int level, int prec, void* x, const void* b, int sweeps, void* stream);
+/* rc = R (b - L^l x): residual on level `level` restricted to level-1 (3 N_{l-1}^2 values). */
+int sib_residual_restrict(sib_ctx* ctx, int level, int prec, const void* x, const void* b, void* rc,
+                          void* stream);
+/* xf += P ec, ec on level-1, xf on level `level`. */
+int sib_prolong_add(sib_ctx* ctx, int level, int prec, const void* ec, void* xf, void* stream);
+/* x = (L^0)^+ b on the coarsest level (computed in FP64 for both precisions). */
+int sib_coarse_solve(sib_ctx* ctx, int prec, const void* b, void* x, void* stream);
+/* z = one V-cycle (Alg. 1) applied to b on the finest level, from a zero initial guess. */
+int sib_vcycle(sib_ctx* ctx, int prec, const void* b, void* z, void* stream);
+/* Fine-level interpolation U = J u (u: 2N^2, U: 2M doubles, M x 2) and spreading f = S F
+ * (F: 2M doubles, f: 2N^2), FP64. */
+int sib_interp(sib_ctx* ctx, const double* u, double* U, void* stream);
+int sib_spread(sib_ctx* ctx, const double* F, double* f, void* stream);
+
+/* ---- accounting ---------------------------------------------------------------------------- */
+/* Number of kernels this context has launched (graph replays count every kernel node). */
+int64_t sib_launch_count(const sib_ctx* ctx);
+/* Bytes of device memory this context holds. */
+int64_t sib_device_bytes(const sib_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIB_H */

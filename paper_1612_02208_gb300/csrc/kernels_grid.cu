@@ -1,0 +1,371 @@
+// MAC-grid stencil kernels of one multigrid level: Stokes-IB residual, additive Vanka sweep,
+// RT0 restriction / prolongation, precision casts, Schur-complement smoother pieces.
+//
+// Layout: a level vector is [u | v | p], each N*N row-major [j][i]; u[j][i] on the x-face
+// (i-1/2, j), v[j][i] on the y-face (i, j-1/2), p[j][i] at the cell centre (Appendix,
+// "Eulerian discretization").  N is a power of two, so periodic wrap is a mask.
+#include "sib_internal.h"
+
+namespace sib {
+
+// ------------------------------------------------------------------------------------------
+// Residual r = b - L x, or y = L x when b == nullptr, with
+//   (L x)_u = A u - dt [SKJ] u + G p,   (L x)_p = -D u     (Eq. matrix-impib / matrix-h-impib)
+//   A u = a0 u - c (u_E + u_W + u_N + u_S),  (G p)_{i-1/2,j} = (p_ij - p_{i-1,j}) / h,
+//   (D u)_ij = (u_{i+1/2,j} - u_{i-1/2,j} + v_{i,j+1/2} - v_{i,j-1/2}) / h.
+// The IB term dt [SKJ]^l u enters through g.fib, computed beforehand for the same x.
+template <typename T, bool HAS_B>
+__global__ void __launch_bounds__(256) k_residual(GridK<T> g, const T* __restrict__ x, const T* __restrict__ b,
+                                                  T* __restrict__ r) {
+    const int N = g.N, n = N * N, m = N - 1;
+    const int i = blockIdx.x * g.tx + threadIdx.x;
+    const int j = blockIdx.y * g.ty + threadIdx.y;
+    const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m;
+    const T* u = x;
+    const T* v = x + n;
+    const T* p = x + 2 * n;
+    const int c = j * N + i;
+    const T uc = u[c], vc = v[c], pc = p[c];
+    const T uE = u[j * N + ip], uW = u[j * N + im], uN = u[jp * N + i], uS = u[jm * N + i];
+    const T vE = v[j * N + ip], vW = v[j * N + im], vN = v[jp * N + i], vS = v[jm * N + i];
+    const T pW = p[j * N + im], pS = p[jm * N + i];
+    T Au = g.a0 * uc - g.c * ((uE + uW) + (uN + uS)) + (pc - pW) * g.inv_h;
+    T Av = g.a0 * vc - g.c * ((vE + vW) + (vN + vS)) + (pc - pS) * g.inv_h;
+    const T Dp = -((uE - uc) + (vN - vc)) * g.inv_h;
+    if (g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x]) {
+        Au -= g.dt * g.fib[c];
+        Av -= g.dt * g.fib[n + c];
+    }
+    if (HAS_B) {
+        r[c] = b[c] - Au;
+        r[n + c] = b[n + c] - Av;
+        r[2 * n + c] = b[2 * n + c] - Dp;
+    } else {
+        r[c] = Au;
+        r[n + c] = Av;
+        r[2 * n + c] = Dp;
+    }
+}
+
+template <typename T>
+void launch_residual(const GridK<T>& g, const T* x, const T* b, T* r, cudaStream_t s) {
+    dim3 blk(g.tx, g.ty), grd(g.N / g.tx, g.N / g.ty);
+    if (b)
+        k_residual<T, true><<<grd, blk, 0, s>>>(g, x, b, r);
+    else
+        k_residual<T, false><<<grd, blk, 0, s>>>(g, x, nullptr, r);
+}
+
+// ------------------------------------------------------------------------------------------
+// One additive Vanka sweep (Alg. 2 with one-cell subdomains, corrections weighted and summed):
+//   xo = x + omega * sum_c W_c R_c^T L_c^{-1} R_c (b - L x),  W = diag(1/2, 1/2, 1/2, 1/2, 1).
+// Patch of cell (i,j): (u_{i-1/2,j}, u_{i+1/2,j}, v_{i,j-1/2}, v_{i,j+1/2}, p_ij) with
+//   L_c = [[A_u, 0, g], [0, A_v, g], [g^T, g^T, 0]],  g = (1/h, -1/h),
+//   A_u = [[a0 - dt B(uL,uL), -c - dt B(uL,uR)], [., a0 - dt B(uR,uR)]] (same for v),
+// solved by block elimination on the pressure.  Phase 1 forms the residual on the tile plus a
+// one-cell halo, phase 2 solves the patches of the tile plus its left/bottom halo cells,
+// phase 3 adds to every face the average of the corrections of its two cells.
+template <typename T>
+__global__ void __launch_bounds__(256) k_vanka(GridK<T> g, const T* __restrict__ x, const T* __restrict__ b,
+                                               T* __restrict__ xo) {
+    __shared__ T sru[(TY + 2) * (TX + 2)];
+    __shared__ T srv[(TY + 2) * (TX + 2)];
+    __shared__ T srp[(TY + 2) * (TX + 2)];
+    __shared__ T sd[5][(TY + 1) * (TX + 1)];
+    const int N = g.N, n = N * N, m = N - 1;
+    const int tx = g.tx, ty = g.ty;
+    const int i0 = blockIdx.x * tx, j0 = blockIdx.y * ty;
+    const int tid = threadIdx.y * tx + threadIdx.x, nth = tx * ty;
+    const bool act = g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x];
+    const T* u = x;
+    const T* v = x + n;
+    const T* p = x + 2 * n;
+    const int RW = tx + 2, RH = ty + 2;
+    for (int q = tid; q < RW * RH; q += nth) {
+        const int i = (i0 - 1 + q % RW) & m, j = (j0 - 1 + q / RW) & m;
+        const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m;
+        const int c = j * N + i;
+        const T uc = u[c], vc = v[c], pc = p[c];
+        const T uE = u[j * N + ip], uW = u[j * N + im], uN = u[jp * N + i], uS = u[jm * N + i];
+        const T vE = v[j * N + ip], vW = v[j * N + im], vN = v[jp * N + i], vS = v[jm * N + i];
+        T Au = g.a0 * uc - g.c * ((uE + uW) + (uN + uS)) + (pc - p[j * N + im]) * g.inv_h;
+        T Av = g.a0 * vc - g.c * ((vE + vW) + (vN + vS)) + (pc - p[jm * N + i]) * g.inv_h;
+        if (act) {
+            Au -= g.dt * g.fib[c];
+            Av -= g.dt * g.fib[n + c];
+        }
+        sru[q] = b[c] - Au;
+        srv[q] = b[n + c] - Av;
+        srp[q] = b[2 * n + c] + ((uE - uc) + (vN - vc)) * g.inv_h;
+    }
+    __syncthreads();
+    const int PW = tx + 1, PH = ty + 1;
+    const T ih = g.inv_h;
+    for (int q = tid; q < PW * PH; q += nth) {
+        const int pi = q % PW, pj = q / PW;
+        const int i = (i0 - 1 + pi) & m, j = (j0 - 1 + pj) & m;
+        const T r0 = sru[pj * RW + pi], r1 = sru[pj * RW + pi + 1];
+        const T r2 = srv[pj * RW + pi], r3 = srv[(pj + 1) * RW + pi];
+        const T r4 = srp[pj * RW + pi];
+        T au00 = g.a0, au11 = g.a0, au01 = -g.c, av00 = g.a0, av11 = g.a0, av01 = -g.c;
+        if (act) {
+            const int cc = j * N + i, ce = j * N + ((i + 1) & m), cn = ((j + 1) & m) * N + i;
+            au00 -= g.dt * g.ibd[cc];
+            au11 -= g.dt * g.ibd[ce];
+            au01 -= g.dt * g.ibd[n + cc];
+            av00 -= g.dt * g.ibd[2 * n + cc];
+            av11 -= g.dt * g.ibd[2 * n + cn];
+            av01 -= g.dt * g.ibd[3 * n + cc];
+        }
+        const T idu = T(1) / (au00 * au11 - au01 * au01);
+        const T idv = T(1) / (av00 * av11 - av01 * av01);
+        // s = A^{-1} (ih, -ih), t = A^{-1} r
+        const T su0 = (au11 + au01) * ih * idu, su1 = -(au01 + au00) * ih * idu;
+        const T sv0 = (av11 + av01) * ih * idv, sv1 = -(av01 + av00) * ih * idv;
+        const T tu0 = (au11 * r0 - au01 * r1) * idu, tu1 = (au00 * r1 - au01 * r0) * idu;
+        const T tv0 = (av11 * r2 - av01 * r3) * idv, tv1 = (av00 * r3 - av01 * r2) * idv;
+        const T S = ih * ((su0 - su1) + (sv0 - sv1));
+        const T dp = (ih * ((tu0 - tu1) + (tv0 - tv1)) - r4) / S;
+        sd[0][q] = tu0 - su0 * dp;
+        sd[1][q] = tu1 - su1 * dp;
+        sd[2][q] = tv0 - sv0 * dp;
+        sd[3][q] = tv1 - sv1 * dp;
+        sd[4][q] = dp;
+    }
+    __syncthreads();
+    const int ci = threadIdx.x, cj = threadIdx.y;
+    const int c = (j0 + cj) * N + (i0 + ci);
+    const int pc = (cj + 1) * PW + ci + 1, pl = (cj + 1) * PW + ci, pb = cj * PW + ci + 1;
+    const T hw = T(0.5) * g.omega;
+    xo[c] = u[c] + hw * (sd[0][pc] + sd[1][pl]);
+    xo[n + c] = v[c] + hw * (sd[2][pc] + sd[3][pb]);
+    xo[2 * n + c] = p[c] + g.omega * sd[4][pc];
+}
+
+template <typename T>
+void launch_vanka(const GridK<T>& g, const T* x, const T* b, T* xo, cudaStream_t s) {
+    dim3 blk(g.tx, g.ty), grd(g.N / g.tx, g.N / g.ty);
+    k_vanka<T><<<grd, blk, 0, s>>>(g, x, b, xo);
+}
+
+// ------------------------------------------------------------------------------------------
+// Restriction of a fine residual to the coarse right-hand side (Sec. 3.2):
+//   velocity R_u = P_u^T / 4 (the h^2-weighted adjoint of RT0 prolongation): a coarse x-face
+//   takes 1/4 of the two coincident fine faces plus 1/8 of the four fine faces half a coarse
+//   cell away in x; pressure: average of the four fine cells.
+template <typename T>
+__global__ void k_restrict(int Nc, const T* __restrict__ rf, T* __restrict__ bc) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    if (I >= Nc || J >= Nc) return;
+    const int Nf = 2 * Nc, nf = Nf * Nf, nc = Nc * Nc, mf = Nf - 1;
+    const T* ru = rf;
+    const T* rv = rf + nf;
+    const T* rp = rf + 2 * nf;
+    const int i = 2 * I, j = 2 * J, ip = i + 1, jp = j + 1, im = (i - 1) & mf, jm = (j - 1) & mf;
+    const T su = (ru[j * Nf + i] + ru[jp * Nf + i]) +
+                 T(0.5) * ((ru[j * Nf + ip] + ru[jp * Nf + ip]) + (ru[j * Nf + im] + ru[jp * Nf + im]));
+    const T sv = (rv[j * Nf + i] + rv[j * Nf + ip]) +
+                 T(0.5) * ((rv[jp * Nf + i] + rv[jp * Nf + ip]) + (rv[jm * Nf + i] + rv[jm * Nf + ip]));
+    const T sp = (rp[j * Nf + i] + rp[j * Nf + ip]) + (rp[jp * Nf + i] + rp[jp * Nf + ip]);
+    const int c = J * Nc + I;
+    bc[c] = T(0.25) * su;
+    bc[nc + c] = T(0.25) * sv;
+    bc[2 * nc + c] = T(0.25) * sp;
+}
+
+template <typename T>
+void launch_restrict(int Nc, const T* rf, T* bc, cudaStream_t s) {
+    dim3 blk(Nc < 32 ? Nc : 32, Nc < 8 ? Nc : 8);
+    dim3 grd((Nc + blk.x - 1) / blk.x, (Nc + blk.y - 1) / blk.y);
+    k_restrict<T><<<grd, blk, 0, s>>>(Nc, rf, bc);
+}
+
+// Prolongation and correction xf += P ec (Sec. 3.2): RT0 for velocity (fine faces that coincide
+// with coarse faces copy, faces half-way between two coarse faces average them, constant in the
+// tangential direction), bilinear cell-centred interpolation for pressure (9/16, 3/16, 3/16, 1/16).
+template <typename T>
+__global__ void k_prolong_add(int Nc, const T* __restrict__ ec, T* __restrict__ xf) {
+    const int Nf = 2 * Nc;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= Nf || j >= Nf) return;
+    const int nf = Nf * Nf, nc = Nc * Nc, mc = Nc - 1;
+    const T* eu = ec;
+    const T* ev = ec + nc;
+    const T* ep = ec + 2 * nc;
+    const int I = i >> 1, J = j >> 1;
+    const T pu = (i & 1) ? T(0.5) * (eu[J * Nc + I] + eu[J * Nc + ((I + 1) & mc)]) : eu[J * Nc + I];
+    const T pv = (j & 1) ? T(0.5) * (ev[J * Nc + I] + ev[((J + 1) & mc) * Nc + I]) : ev[J * Nc + I];
+    const int I2 = (I + ((i & 1) ? 1 : -1)) & mc, J2 = (J + ((j & 1) ? 1 : -1)) & mc;
+    const T pp = T(9.0 / 16.0) * ep[J * Nc + I] + T(3.0 / 16.0) * (ep[J * Nc + I2] + ep[J2 * Nc + I]) +
+                 T(1.0 / 16.0) * ep[J2 * Nc + I2];
+    const int c = j * Nf + i;
+    xf[c] += pu;
+    xf[nf + c] += pv;
+    xf[2 * nf + c] += pp;
+}
+
+template <typename T>
+void launch_prolong_add(int Nc, const T* ec, T* xf, cudaStream_t s) {
+    const int Nf = 2 * Nc;
+    dim3 blk(Nf < 32 ? Nf : 32, Nf < 8 ? Nf : 8);
+    dim3 grd((Nf + blk.x - 1) / blk.x, (Nf + blk.y - 1) / blk.y);
+    k_prolong_add<T><<<grd, blk, 0, s>>>(Nc, ec, xf);
+}
+
+// ------------------------------------------------------------------------------------------
+template <typename Ti, typename To>
+__global__ void k_convert(const Ti* __restrict__ in, To* __restrict__ out, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = static_cast<To>(in[k]);
+}
+
+int num_blocks_for(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    const int64_t cap = 152 * 16;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+template <typename Ti, typename To>
+void launch_convert(const Ti* in, To* out, int64_t n, cudaStream_t s) {
+    k_convert<Ti, To><<<num_blocks_for(n), 256, 0, s>>>(in, out, n);
+}
+
+template <typename T>
+__global__ void k_axpby(T a, const T* __restrict__ x, T b, const T* __restrict__ y, T* __restrict__ z, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        z[k] = a * x[k] + (y ? b * y[k] : T(0));
+}
+
+template <typename T>
+void launch_axpby(T a, const T* x, T b, const T* y, T* z, int64_t n, cudaStream_t s) {
+    k_axpby<T><<<num_blocks_for(n), 256, 0, s>>>(a, x, b, y, z, n);
+}
+
+// ------------------------------------------------------------------------------------------
+// Schur-complement smoother pieces (Eq. approx-fact-Stokes-IB).
+// diag(A_IB) on a face: a0 - dt B(f,f) (B(f,f) read only in IB-active tiles).
+template <typename T>
+__device__ __forceinline__ T diagA(const GridK<T>& g, bool act, int comp, int c, int n) {
+    return act ? g.a0 - g.dt * g.ibd[2 * comp * n + c] : g.a0;
+}
+
+// z = scale * diag(A_IB)^{-1} r on both velocity components
+template <typename T>
+__global__ void k_jacobi_A(GridK<T> g, const T* __restrict__ r, T* __restrict__ z, T scale) {
+    const int N = g.N, n = N * N;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const bool act = g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x];
+    const int c = j * N + i;
+    z[c] = scale * r[c] / diagA(g, act, 0, c, n);
+    z[n + c] = scale * r[n + c] / diagA(g, act, 1, c, n);
+}
+template <typename T>
+void launch_sc_jacobi_A(const GridK<T>& g, const T* r, T* z, T scale, cudaStream_t s) {
+    k_jacobi_A<T><<<dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s>>>(g, r, z, scale);
+}
+
+// y = A_IB u = A u - dt [SKJ] u on the velocity faces (fib holds [SKJ] u)
+template <typename T>
+__global__ void k_apply_AIB(GridK<T> g, const T* __restrict__ x, T* __restrict__ y) {
+    const int N = g.N, n = N * N, m = N - 1;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m;
+    const bool act = g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x];
+    const int c = j * N + i;
+    for (int comp = 0; comp < 2; ++comp) {
+        const T* u = x + comp * n;
+        T a = g.a0 * u[c] - g.c * ((u[j * N + ip] + u[j * N + im]) + (u[jp * N + i] + u[jm * N + i]));
+        if (act) a -= g.dt * g.fib[comp * n + c];
+        y[comp * n + c] = a;
+    }
+}
+template <typename T>
+void launch_apply_AIB(const GridK<T>& g, const T* u, T* y, cudaStream_t s) {
+    k_apply_AIB<T><<<dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s>>>(g, u, y);
+}
+
+// gu = G p on the velocity faces
+template <typename T>
+__global__ void k_gradient(GridK<T> g, const T* __restrict__ p, T* __restrict__ gu) {
+    const int N = g.N, n = N * N, m = N - 1;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const int c = j * N + i;
+    const T pc = p[c];
+    gu[c] = (pc - p[j * N + ((i - 1) & m)]) * g.inv_h;
+    gu[n + c] = (pc - p[((j - 1) & m) * N + i]) * g.inv_h;
+}
+template <typename T>
+void launch_gradient(const GridK<T>& g, const T* p, T* gu, cudaStream_t s) {
+    k_gradient<T><<<dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s>>>(g, p, gu);
+}
+
+// d = D u on the cells
+template <typename T>
+__global__ void k_divergence(GridK<T> g, const T* __restrict__ u, T* __restrict__ d) {
+    const int N = g.N, n = N * N, m = N - 1;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const int c = j * N + i;
+    d[c] = ((u[j * N + ((i + 1) & m)] - u[c]) + (u[n + ((j + 1) & m) * N + i] - u[n + c])) * g.inv_h;
+}
+template <typename T>
+void launch_divergence(const GridK<T>& g, const T* u, T* d, cudaStream_t s) {
+    k_divergence<T><<<dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s>>>(g, u, d);
+}
+
+// z = scale * diag(Mh)^{-1} r with Mh = D diag(A_IB)^{-1} G:
+//   diag(Mh)_ij = -(1/h^2) (1/dA(u_ij) + 1/dA(u_i+1,j) + 1/dA(v_ij) + 1/dA(v_i,j+1))
+// (the four neighbouring faces may belong to a neighbouring tile; the tile flags are dilated by
+// one tile, so the flag of the cell's own tile covers them).
+template <typename T>
+__global__ void k_jacobi_M(GridK<T> g, const T* __restrict__ r, T* __restrict__ z, T scale) {
+    const int N = g.N, n = N * N, m = N - 1;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const bool act = g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x];
+    const int c = j * N + i, ce = j * N + ((i + 1) & m), cn = ((j + 1) & m) * N + i;
+    const T s = T(1) / diagA(g, act, 0, c, n) + T(1) / diagA(g, act, 0, ce, n) + T(1) / diagA(g, act, 1, c, n) +
+                T(1) / diagA(g, act, 1, cn, n);
+    const T dM = -s * g.inv_h * g.inv_h;
+    z[c] = scale * r[c] / dM;
+}
+template <typename T>
+void launch_jacobi_M(const GridK<T>& g, const T* r, T* z, T scale, cudaStream_t s) {
+    k_jacobi_M<T><<<dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s>>>(g, r, z, scale);
+}
+
+// Chebyshev direction update d = ra * d + rb * dinvr, then x += d
+template <typename T>
+__global__ void k_cheb_update(const T* __restrict__ dinvr, T* __restrict__ d, T* __restrict__ x, T ra, T rb,
+                              int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const T dn = ra * d[k] + rb * dinvr[k];
+        d[k] = dn;
+        x[k] += dn;
+    }
+}
+template <typename T>
+void launch_cheb_update(const T* dinvr, T* d, T* x, T ra, T rb, int64_t n, cudaStream_t s) {
+    k_cheb_update<T><<<num_blocks_for(n), 256, 0, s>>>(dinvr, d, x, ra, rb, n);
+}
+
+// ------------------------------------------------------------------------------------------
+#define SIB_INST(T)                                                                                        \
+    template void launch_residual<T>(const GridK<T>&, const T*, const T*, T*, cudaStream_t);              \
+    template void launch_vanka<T>(const GridK<T>&, const T*, const T*, T*, cudaStream_t);                 \
+    template void launch_restrict<T>(int, const T*, T*, cudaStream_t);                                    \
+    template void launch_prolong_add<T>(int, const T*, T*, cudaStream_t);                                 \
+    template void launch_axpby<T>(T, const T*, T, const T*, T*, int64_t, cudaStream_t);                   \
+    template void launch_sc_jacobi_A<T>(const GridK<T>&, const T*, T*, T, cudaStream_t);                  \
+    template void launch_apply_AIB<T>(const GridK<T>&, const T*, T*, cudaStream_t);                       \
+    template void launch_gradient<T>(const GridK<T>&, const T*, T*, cudaStream_t);                        \
+    template void launch_divergence<T>(const GridK<T>&, const T*, T*, cudaStream_t);                      \
+    template void launch_jacobi_M<T>(const GridK<T>&, const T*, T*, T, cudaStream_t);                     \
+    template void launch_cheb_update<T>(const T*, T*, T*, T, T, int64_t, cudaStream_t);
+SIB_INST(float)
+SIB_INST(double)
+template void launch_convert<double, float>(const double*, float*, int64_t, cudaStream_t);
+template void launch_convert<float, double>(const float*, double*, int64_t, cudaStream_t);
+template void launch_convert<double, double>(const double*, double*, int64_t, cudaStream_t);
+
+}  // namespace sib

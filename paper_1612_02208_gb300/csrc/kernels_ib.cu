@@ -1,0 +1,706 @@
+// Lagrangian-Eulerian kernels: Peskin four-point stencils and their Galerkin coarsening, marker
+// binning (Morton-ordered stable sort), interpolation J, spring forces K, spreading S as a
+// cell-binned gather, and the set-up assembly of IB operator entries.
+//
+// Interpolation / spreading (Appendix, "Lagrangian-Eulerian interaction"):
+//   U_l = sum_f u_f phi((x_f - X_l)/h) phi((y_f - Y_l)/h),   f_f = (1/h^2) sum_l F_l phi(.) phi(.)
+// i.e. S = J^T / h^2 for a spring force F given in force units.  On coarse levels the composite
+// stencil J_l = J P_u^(lmax<-l) is used, so that (1/h_l^2) J_l^T K J_l equals the Galerkin
+// operator R_u [S K J]^(l+1) P_u of Sec. 3.1 (R_u = P_u^T / 4).
+#include <cmath>
+
+#include "sib_internal.h"
+
+namespace sib {
+
+// Peskin's four-point kernel phi(r) (Appendix): piecewise in |r| with square roots, support |r| < 2.
+__device__ __forceinline__ double phi4(double r) {
+    const double a = fabs(r);
+    if (a < 1.0) return 0.125 * (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a));
+    if (a < 2.0) return 0.125 * (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a));
+    return 0.0;
+}
+// d phi / d r
+__device__ __forceinline__ double dphi4(double r) {
+    const double a = fabs(r);
+    const double sg = r < 0.0 ? -1.0 : 1.0;
+    if (a < 1.0) return sg * 0.125 * (-2.0 + (2.0 - 4.0 * a) / sqrt(1.0 + 4.0 * a - 4.0 * a * a));
+    if (a < 2.0) return sg * 0.125 * (-2.0 - (6.0 - 4.0 * a) / sqrt(-7.0 + 12.0 * a - 4.0 * a * a));
+    return 0.0;
+}
+
+struct StencilOut {
+    int* base[SIB_MAX_LEVELS][2];
+    double* w64[SIB_MAX_LEVELS][2];
+    float* w32[SIB_MAX_LEVELS][2];
+};
+
+// 1-D restriction of a row of interpolation weights by one level, w <- w P (P = RT0 prolongation):
+// linear in the face-normal direction (fine face 2I -> I; 2I+1 -> I and I+1 with 1/2) ...
+__device__ __forceinline__ void coarsen_linear(int& b0, double w[4]) {
+    const int nb = b0 >> 1;   // floor(b0 / 2) for negative b0 as well
+    double c[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int a = 0; a < 4; ++a) {
+        const int idx = b0 + a;
+        const int k = (idx >> 1) - nb;
+        if ((idx & 1) == 0) {
+            c[k] += w[a];
+        } else {
+            c[k] += 0.5 * w[a];
+            c[k + 1] += 0.5 * w[a];
+        }
+    }
+    b0 = nb;
+    for (int a = 0; a < 4; ++a) w[a] = c[a];
+}
+// ... and constant in the tangential direction (fine index j -> floor(j/2)).
+__device__ __forceinline__ void coarsen_const(int& b0, double w[4]) {
+    const int nb = b0 >> 1;
+    double c[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int a = 0; a < 4; ++a) c[((b0 + a) >> 1) - nb] += w[a];
+    b0 = nb;
+    for (int a = 0; a < 4; ++a) w[a] = c[a];
+}
+
+__global__ void k_stencils(const double* __restrict__ X, int M, int Nf, int lmax, StencilOut out) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int comp = blockIdx.y;
+    if (m >= M) return;
+    const double ox = comp == 0 ? 0.0 : 0.5, oy = comp == 0 ? 0.5 : 0.0;
+    const double sx = X[2 * m] * Nf - ox, sy = X[2 * m + 1] * Nf - oy;
+    int bi = (int)floor(sx) - 1, bj = (int)floor(sy) - 1;
+    double wx[4], wy[4];
+    for (int a = 0; a < 4; ++a) {
+        wx[a] = phi4((double)(bi + a) - sx);
+        wy[a] = phi4((double)(bj + a) - sy);
+    }
+    int N = Nf;
+    for (int l = lmax; l >= 0; --l) {
+        if (l < lmax) {
+            if (comp == 0) {
+                coarsen_linear(bi, wx);
+                coarsen_const(bj, wy);
+            } else {
+                coarsen_const(bi, wx);
+                coarsen_linear(bj, wy);
+            }
+            N >>= 1;
+        }
+        out.base[l][comp][m] = ((bj & (N - 1)) << 16) | (bi & (N - 1));
+        for (int a = 0; a < 4; ++a) {
+            out.w64[l][comp][8 * m + a] = wx[a];
+            out.w64[l][comp][8 * m + 4 + a] = wy[a];
+            out.w32[l][comp][8 * m + a] = (float)wx[a];
+            out.w32[l][comp][8 * m + 4 + a] = (float)wy[a];
+        }
+    }
+}
+
+void launch_stencils(const double* X, int M, int Nf, int lmax, int** base, double** w64, float** w32,
+                     cudaStream_t s) {
+    if (M == 0) return;
+    StencilOut o;
+    for (int l = 0; l <= lmax; ++l)
+        for (int c = 0; c < 2; ++c) {
+            o.base[l][c] = base[2 * l + c];
+            o.w64[l][c] = w64[2 * l + c];
+            o.w32[l][c] = w32[2 * l + c];
+        }
+    k_stencils<<<dim3((M + 127) / 128, 2), 128, 0, s>>>(X, M, Nf, lmax, o);
+}
+
+// ------------------------------------------------------------------------------------------
+// Stable ordering of markers by the Morton code of their fine stencil origin: keys
+// (morton << 32 | id) sorted by a bitonic network (ties cannot occur, ids are distinct).
+__global__ void k_sort_keys(const int* __restrict__ base, int M, int Mpad, uint64_t* __restrict__ keys) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Mpad) return;
+    if (m < M) {
+        const int b = base[m];
+        keys[m] = ((uint64_t)morton(b & 0xffff, (b >> 16) & 0xffff) << 32) | (uint32_t)m;
+    } else {
+        keys[m] = ~0ull;
+    }
+}
+void launch_sort_keys(const int* baseFine, int M, int Mpad, uint64_t* keys, cudaStream_t s) {
+    k_sort_keys<<<(Mpad + 255) / 256, 256, 0, s>>>(baseFine, M, Mpad, keys);
+}
+
+__global__ void k_bitonic_step(uint64_t* __restrict__ a, int Mpad, int j, int k) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Mpad) return;
+    const int l = i ^ j;
+    if (l > i) {
+        const uint64_t x = a[i], y = a[l];
+        const bool up = (i & k) == 0;
+        if ((up && x > y) || (!up && x < y)) {
+            a[i] = y;
+            a[l] = x;
+        }
+    }
+}
+// all steps with j < 1024 of stage k run in shared memory
+__global__ void k_bitonic_smem(uint64_t* __restrict__ a, int Mpad, int k, int jstart) {
+    __shared__ uint64_t sh[2048];
+    const int base = blockIdx.x * 2048;
+    for (int t = threadIdx.x; t < 2048; t += blockDim.x) sh[t] = a[base + t];
+    __syncthreads();
+    for (int j = jstart; j > 0; j >>= 1) {
+        for (int t = threadIdx.x; t < 2048; t += blockDim.x) {
+            const int i = base + t, l = i ^ j;
+            if (l > i) {
+                const uint64_t x = sh[t], y = sh[l - base];
+                const bool up = (i & k) == 0;
+                if ((up && x > y) || (!up && x < y)) {
+                    sh[t] = y;
+                    sh[l - base] = x;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < 2048; t += blockDim.x) a[base + t] = sh[t];
+}
+void launch_bitonic(uint64_t* keys, int Mpad, cudaStream_t s) {
+    for (int k = 2; k <= Mpad; k <<= 1) {
+        int j = k >> 1;
+        if (Mpad >= 2048) {
+            for (; j >= 1024; j >>= 1) k_bitonic_step<<<(Mpad + 255) / 256, 256, 0, s>>>(keys, Mpad, j, k);
+            k_bitonic_smem<<<Mpad / 2048, 1024, 0, s>>>(keys, Mpad, k, j);
+        } else {
+            for (; j >= 1; j >>= 1) k_bitonic_step<<<(Mpad + 255) / 256, 256, 0, s>>>(keys, Mpad, j, k);
+        }
+    }
+}
+
+__global__ void k_unpack_sorted(const uint64_t* __restrict__ keys, int M, int* __restrict__ sorted,
+                                uint32_t* __restrict__ mkey) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    sorted[m] = (int)(keys[m] & 0xffffffffu);
+    mkey[m] = (uint32_t)(keys[m] >> 32);
+}
+void launch_unpack_sorted(const uint64_t* keys, int M, int* sorted, uint32_t* mkey, cudaStream_t s) {
+    if (M == 0) return;
+    k_unpack_sorted<<<(M + 255) / 256, 256, 0, s>>>(keys, M, sorted, mkey);
+}
+
+// binStart[b] = first position p with (mkey[p] >> shift) >= b, for b = 0..nbins
+__global__ void k_bins(const uint32_t* __restrict__ mkey, int M, int nbins, int shift, int* __restrict__ binStart) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nbins) return;
+    int lo = 0, hi = M;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int)(mkey[mid] >> shift) < b)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    binStart[b] = lo;
+}
+void launch_bins(const uint32_t* mkey, int M, int nbins, int shift, int* binStart, cudaStream_t s) {
+    k_bins<<<(nbins + 1 + 255) / 256, 256, 0, s>>>(mkey, M, nbins, shift, binStart);
+}
+
+// ------------------------------------------------------------------------------------------
+// IB-active tiles: every tile containing a face of some marker's stencil (either component),
+// then dilated by one tile (so that a tile's one-cell halo is covered by its own flag) and
+// compacted into an ordered list.
+__global__ void k_tile_mark(const int* __restrict__ base, int M, int W, int N, int tx, int ty, int ntx,
+                            unsigned char* __restrict__ flag) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const int b = base[m], bi = b & 0xffff, bj = (b >> 16) & 0xffff, mk = N - 1;
+    for (int q = 0; q < W; ++q)
+        for (int p = 0; p < W; ++p) {
+            const int i = (bi + p) & mk, j = (bj + q) & mk;
+            flag[(j / ty) * ntx + i / tx] = 1;
+        }
+}
+void launch_tile_flags(const int* base, int M, int W, int N, int tx, int ty, int ntx, unsigned char* flag,
+                       cudaStream_t s) {
+    if (M == 0) return;
+    k_tile_mark<<<(M + 127) / 128, 128, 0, s>>>(base, M, W, N, tx, ty, ntx, flag);
+}
+
+// single block: raw flags in flag[0..nt), dilated flags written to flag[nt..2nt), list of
+// active tiles (ascending) to tiles[], count to *nTiles
+__global__ void k_tile_finish(unsigned char* __restrict__ flag, int ntx, int nty, int* __restrict__ tiles,
+                              int* __restrict__ nTiles) {
+    __shared__ int warpSums[32];
+    __shared__ int carry;
+    const int nt = ntx * nty;
+    unsigned char* dil = flag + nt;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        const int ti = t % ntx, tj = t / ntx;
+        unsigned char f = 0;
+        for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di) {
+                const int a = (ti + di + ntx) % ntx, bq = (tj + dj + nty) % nty;
+                f |= flag[bq * ntx + a];
+            }
+        dil[t] = f;
+    }
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int t0 = 0; t0 < nt; t0 += blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        const int f = (t < nt && dil[t]) ? 1 : 0;
+        // block-wide inclusive scan of f
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        int v = f;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane == 31) warpSums[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            int w = (lane < (int)(blockDim.x >> 5)) ? warpSums[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warpSums[lane] = w;
+        }
+        __syncthreads();
+        const int incl = v + (wid > 0 ? warpSums[wid - 1] : 0);
+        if (f) tiles[carry + incl - 1] = t;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *nTiles = carry;
+}
+void launch_tile_finish(unsigned char* flag, int ntx, int nty, int* tiles, int* nTiles, cudaStream_t s) {
+    k_tile_finish<<<1, 1024, 0, s>>>(flag, ntx, nty, tiles, nTiles);
+}
+
+// ------------------------------------------------------------------------------------------
+// Spring adjacency (CSR, deterministic): each marker's incident springs ordered by edge id.
+__global__ void k_degree(const int* __restrict__ edges, int E, int* __restrict__ deg) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    atomicAdd(&deg[edges[2 * e]], 1);
+    atomicAdd(&deg[edges[2 * e + 1]], 1);
+}
+// single block exclusive scan of deg[0..M) into start[0..M]
+__global__ void k_scan_single(const int* __restrict__ deg, int M, int* __restrict__ start) {
+    __shared__ int partial[1024];
+    const int T = blockDim.x;
+    const int chunk = (M + T - 1) / T;
+    const int lo = threadIdx.x * chunk, hi = min(M, lo + chunk);
+    int s = 0;
+    for (int k = lo; k < hi; ++k) s += deg[k];
+    partial[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int t = 0; t < T; ++t) {
+            const int v = partial[t];
+            partial[t] = acc;
+            acc += v;
+        }
+        start[M] = acc;
+    }
+    __syncthreads();
+    int acc = partial[threadIdx.x];
+    for (int k = lo; k < hi; ++k) {
+        start[k] = acc;
+        acc += deg[k];
+    }
+}
+__global__ void k_adj_fill(const int* __restrict__ edges, int E, const int* __restrict__ start, int* __restrict__ cursor,
+                           int* __restrict__ nbr, int* __restrict__ eid) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const int a = edges[2 * e], b = edges[2 * e + 1];
+    int pa = start[a] + atomicAdd(&cursor[a], 1);
+    nbr[pa] = b;
+    eid[pa] = e;
+    int pb = start[b] + atomicAdd(&cursor[b], 1);
+    nbr[pb] = a;
+    eid[pb] = e;
+}
+__global__ void k_adj_sort(int M, const int* __restrict__ start, int* __restrict__ nbr, int* __restrict__ eid) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const int s = start[m], e = start[m + 1];
+    for (int p = s + 1; p < e; ++p) {
+        const int ke = eid[p], kn = nbr[p];
+        int q = p - 1;
+        while (q >= s && (eid[q] > ke || (eid[q] == ke && nbr[q] > kn))) {
+            eid[q + 1] = eid[q];
+            nbr[q + 1] = nbr[q];
+            --q;
+        }
+        eid[q + 1] = ke;
+        nbr[q + 1] = kn;
+    }
+}
+void launch_adjacency(const int* edges, int E, int M, int* deg, int* start, int* nbr, int* eid, cudaStream_t s) {
+    cudaMemsetAsync(deg, 0, sizeof(int) * (size_t)(M > 0 ? M : 1), s);
+    if (E > 0) k_degree<<<(E + 255) / 256, 256, 0, s>>>(edges, E, deg);
+    k_scan_single<<<1, 1024, 0, s>>>(deg, M, start);
+    cudaMemsetAsync(deg, 0, sizeof(int) * (size_t)(M > 0 ? M : 1), s);   // reused as cursor
+    if (E > 0) k_adj_fill<<<(E + 255) / 256, 256, 0, s>>>(edges, E, start, deg, nbr, eid);
+    if (M > 0) k_adj_sort<<<(M + 255) / 256, 256, 0, s>>>(M, start, nbr, eid);
+}
+
+template <typename T>
+__global__ void k_adj_kappa(const int* __restrict__ eid, const double* __restrict__ kappa, int n2E, T* __restrict__ kap) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n2E) return;
+    kap[p] = (T)kappa[eid[p]];
+}
+template <typename T>
+void launch_adj_kappa(const int* eid, const double* kappa, int n2E, T* kap, cudaStream_t s) {
+    if (n2E == 0) return;
+    k_adj_kappa<T><<<(n2E + 255) / 256, 256, 0, s>>>(eid, kappa, n2E, kap);
+}
+
+// ------------------------------------------------------------------------------------------
+// Interpolation U^c_m = sum_{a,b < W} wx[a] wy[b] u^c[(bj+b) mod N][(bi+a) mod N]  (one thread per
+// marker and component; U, F are stored component-major: U[c*M + m]).
+template <typename T>
+__global__ void k_interp(IBK<T> k, const T* __restrict__ u, T* __restrict__ U) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (m >= k.M) return;
+    const int N = k.N, mk = N - 1;
+    const int b = k.base[c][m], bi = b & 0xffff, bj = (b >> 16) & 0xffff;
+    const T* w = k.wgt[c] + 8 * m;
+    const T* uc = u + (size_t)c * N * N;
+    T acc = T(0);
+    for (int q = 0; q < k.W; ++q) {
+        const int row = ((bj + q) & mk) * N;
+        T s = T(0);
+        for (int p = 0; p < k.W; ++p) s += w[p] * uc[row + ((bi + p) & mk)];
+        acc += w[4 + q] * s;
+    }
+    U[c * k.M + m] = acc;
+}
+template <typename T>
+void launch_interp(const IBK<T>& k, const T* u, T* U, cudaStream_t s) {
+    if (k.M == 0) return;
+    k_interp<T><<<dim3((k.M + 127) / 128, 2), 128, 0, s>>>(k, u, U);
+}
+
+// Spring forces F_a = sum_{springs (a,b)} kappa_ab (U_b - U_a), per component (Appendix,
+// "Lagrangian discretization", zero rest length).
+template <typename T>
+__global__ void k_spring(const int* __restrict__ start, const int* __restrict__ nbr, const T* __restrict__ kap, int M,
+                         const T* __restrict__ U, T* __restrict__ F) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (m >= M) return;
+    const T* Uc = U + c * M;
+    const T um = Uc[m];
+    T acc = T(0);
+    for (int p = start[m]; p < start[m + 1]; ++p) acc += kap[p] * (Uc[nbr[p]] - um);
+    F[c * M + m] = acc;
+}
+template <typename T>
+void launch_spring(const int* start, const int* nbr, const T* kap, int M, const T* U, T* F, cudaStream_t s) {
+    if (M == 0) return;
+    k_spring<T><<<dim3((M + 127) / 128, 2), 128, 0, s>>>(start, nbr, kap, M, U, F);
+}
+
+// Spreading as a cell-binned gather: face (i, j) of component c collects every marker whose
+// level-l stencil origin is (i - a, j - b), a, b < W, from the Morton-ordered bin of that origin:
+//   f^c_ij = (1/h^2) sum_{a,b} sum_{m in bin(i-a, j-b)} wx_m[a] wy_m[b] F^c_m.
+// No atomics; the summation order is fixed.  Only IB-active tiles are written.
+template <typename T>
+__device__ __forceinline__ T gather_face(const IBK<T>& k, const T* __restrict__ F, int c, int i, int j, int lane,
+                                         int stride) {
+    const int mk = k.N - 1;
+    const int* bs = k.binStart[c];
+    const int* srt = k.sorted[c];
+    const T* wg = k.wgt[c];
+    const T* Fc = F + c * k.M;
+    T acc = T(0);
+    for (int b = 0; b < k.W; ++b)
+        for (int a = 0; a < k.W; ++a) {
+            const uint32_t bin = morton((i - a) & mk, (j - b) & mk);
+            const int s = bs[bin], e = bs[bin + 1];
+            for (int q = s + lane; q < e; q += stride) {
+                const int m = srt[q];
+                acc += wg[8 * m + a] * wg[8 * m + 4 + b] * Fc[m];
+            }
+        }
+    return acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_spread_thread(IBK<T> k, const T* __restrict__ F, T* __restrict__ f,
+                                                       const int* __restrict__ tiles, const int* __restrict__ nTiles,
+                                                       int tx, int ty, int ntx) {
+    if ((int)blockIdx.x >= *nTiles) return;
+    const int t = tiles[blockIdx.x];
+    const int i = (t % ntx) * tx + threadIdx.x, j = (t / ntx) * ty + threadIdx.y;
+    const int n = k.N * k.N;
+    for (int c = 0; c < 2; ++c) f[c * n + j * k.N + i] = k.inv_h2 * gather_face(k, F, c, i, j, 0, 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_spread_warp(IBK<T> k, const T* __restrict__ F, T* __restrict__ f,
+                                                     const int* __restrict__ tiles, const int* __restrict__ nTiles,
+                                                     int tx, int ty, int ntx) {
+    if ((int)blockIdx.x >= *nTiles) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int face = blockIdx.y * 8 + warp;
+    const int per = tx * ty;
+    if (face >= 2 * per) return;
+    const int c = face / per, q = face % per;
+    const int t = tiles[blockIdx.x];
+    const int i = (t % ntx) * tx + q % tx, j = (t / ntx) * ty + q / tx;
+    T acc = gather_face(k, F, c, i, j, lane, 32);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) f[c * k.N * k.N + j * k.N + i] = k.inv_h2 * acc;
+}
+
+template <typename T>
+void launch_spread(const IBK<T>& k, const T* F, T* f, const int* tiles, const int* nTiles, int maxTiles, int tx,
+                   int ty, int ntx, int warpPerFace, cudaStream_t s) {
+    if (maxTiles == 0) return;
+    if (warpPerFace) {
+        const int groups = (2 * tx * ty + 7) / 8;
+        k_spread_warp<T><<<dim3(maxTiles, groups), 256, 0, s>>>(k, F, f, tiles, nTiles, tx, ty, ntx);
+    } else {
+        k_spread_thread<T><<<maxTiles, dim3(tx, ty), 0, s>>>(k, F, f, tiles, nTiles, tx, ty, ntx);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Set-up assembly of IB operator entries, B = [S K J]^l = -(1/h^2) sum_e kappa_e d_e d_e^T with
+// d_e = J_l[a] - J_l[b] (the level-l stencil rows of the spring's two markers).  One thread per
+// (spring, component) scatters with FP64 atomics (set-up only; the solve never uses atomics).
+struct EdgeStencil {
+    int face[32];
+    double coef[32];
+    int n;
+};
+__device__ __forceinline__ void edge_stencil(EdgeStencil& es, int a, int b, const int* base, const double* w,
+                                             int N, int W) {
+    const int mk = N - 1;
+    es.n = 0;
+    for (int side = 0; side < 2; ++side) {
+        const int m = side == 0 ? a : b;
+        const double sg = side == 0 ? 1.0 : -1.0;
+        const int bb = base[m], bi = bb & 0xffff, bj = (bb >> 16) & 0xffff;
+        for (int q = 0; q < W; ++q)
+            for (int p = 0; p < W; ++p) {
+                es.face[es.n] = ((bj + q) & mk) * N + ((bi + p) & mk);
+                es.coef[es.n] = sg * w[8 * m + p] * w[8 * m + 4 + q];
+                ++es.n;
+            }
+    }
+}
+
+// Diagonal B(f,f) and the patch off-diagonal B(f, f+e) (e = +x for u faces, +y for v faces).
+__global__ void k_patch_entries(const int* __restrict__ edges, const double* __restrict__ kappa, int E,
+                                const int* __restrict__ base0, const int* __restrict__ base1,
+                                const double* __restrict__ w0, const double* __restrict__ w1, int N, int W,
+                                double inv_h2, double* __restrict__ ibd) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (e >= E) return;
+    const int a = edges[2 * e], b = edges[2 * e + 1];
+    if (a == b) return;
+    const double kap = kappa[e];
+    EdgeStencil es;
+    edge_stencil(es, a, b, c == 0 ? base0 : base1, c == 0 ? w0 : w1, N, W);
+    const int n = N * N, mk = N - 1;
+    double* diag = ibd + 2 * c * n;
+    double* off = ibd + (2 * c + 1) * n;
+    for (int p = 0; p < es.n; ++p) {
+        const int f = es.face[p];
+        bool owner = true;
+        for (int q = 0; q < p; ++q)
+            if (es.face[q] == f) owner = false;
+        if (!owner) continue;
+        const int fi = f % N, fj = f / N;
+        const int fn = c == 0 ? fj * N + ((fi + 1) & mk) : ((fj + 1) & mk) * N + fi;
+        double d = 0.0, dn = 0.0;
+        for (int q = 0; q < es.n; ++q) {
+            if (es.face[q] == f) d += es.coef[q];
+            if (es.face[q] == fn) dn += es.coef[q];
+        }
+        if (d != 0.0) {
+            atomicAdd(&diag[f], -kap * d * d * inv_h2);
+            if (dn != 0.0) atomicAdd(&off[f], -kap * d * dn * inv_h2);
+        }
+    }
+}
+void launch_patch_entries(const int* edges, const double* kappa, int E, const int* base0, const int* base1,
+                          const double* w0, const double* w1, int M, int N, int W, double inv_h2, double* ibd,
+                          cudaStream_t s) {
+    (void)M;
+    if (E == 0) return;
+    k_patch_entries<<<dim3((E + 127) / 128, 2), 128, 0, s>>>(edges, kappa, E, base0, base1, w0, w1, N, W, inv_h2,
+                                                             ibd);
+}
+
+// Dense coarsest-level IB block B (2 x n0 x n0, per component) accumulated per block in shared
+// memory when it fits, then added to global memory.
+__global__ void k_dense_ib(const int* __restrict__ edges, const double* __restrict__ kappa, int E,
+                           const int* __restrict__ base0, const int* __restrict__ base1,
+                           const double* __restrict__ w0, const double* __restrict__ w1, int N, int W,
+                           double inv_h2, double* __restrict__ B, int useSmem) {
+    extern __shared__ double sB[];
+    const int n0 = N * N;
+    const int tot = 2 * n0 * n0;
+    if (useSmem) {
+        for (int t = threadIdx.x; t < tot; t += blockDim.x) sB[t] = 0.0;
+        __syncthreads();
+    }
+    double* acc = useSmem ? sB : B;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+        const int a = edges[2 * e], b = edges[2 * e + 1];
+        if (a == b) continue;
+        const double kap = kappa[e];
+        for (int c = 0; c < 2; ++c) {
+            EdgeStencil es;
+            edge_stencil(es, a, b, c == 0 ? base0 : base1, c == 0 ? w0 : w1, N, W);
+            double* Bc = acc + (size_t)c * n0 * n0;
+            for (int p = 0; p < es.n; ++p) {
+                const double cp = -kap * es.coef[p] * inv_h2;
+                if (cp == 0.0) continue;
+                for (int q = 0; q < es.n; ++q)
+                    if (es.coef[q] != 0.0) atomicAdd(&Bc[(size_t)es.face[p] * n0 + es.face[q]], cp * es.coef[q]);
+            }
+        }
+    }
+    if (useSmem) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < tot; t += blockDim.x)
+            if (sB[t] != 0.0) atomicAdd(&B[t], sB[t]);
+    }
+}
+void launch_dense_ib(const int* edges, const double* kappa, int E, const int* base0, const int* base1,
+                     const double* w0, const double* w1, int N, int W, double inv_h2, double* B, cudaStream_t s) {
+    if (E == 0) return;
+    const int n0 = N * N;
+    const size_t bytes = sizeof(double) * 2 * (size_t)n0 * n0;
+    const int useSmem = bytes <= 96 * 1024 ? 1 : 0;
+    int blocks = (E + 255) / 256;
+    if (blocks > 304) blocks = 304;
+    if (useSmem) cudaFuncSetAttribute(k_dense_ib, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    k_dense_ib<<<blocks, 256, useSmem ? bytes : 0, s>>>(edges, kappa, E, base0, base1, w0, w1, N, W, inv_h2, B,
+                                                         useSmem);
+}
+
+// ------------------------------------------------------------------------------------------
+// (M x 2) interleaved <-> component-major [x (M) | y (M)]
+__global__ void k_deinterleave(const double* __restrict__ in, int M, double* __restrict__ out) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    out[m] = in[2 * m];
+    out[M + m] = in[2 * m + 1];
+}
+__global__ void k_interleave(const double* __restrict__ in, int M, double* __restrict__ out) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    out[2 * m] = in[m];
+    out[2 * m + 1] = in[M + m];
+}
+void launch_deinterleave(const double* in, int M, double* out, cudaStream_t s) {
+    if (M == 0) return;
+    k_deinterleave<<<(M + 255) / 256, 256, 0, s>>>(in, M, out);
+}
+void launch_interleave(const double* in, int M, double* out, cudaStream_t s) {
+    if (M == 0) return;
+    k_interleave<<<(M + 255) / 256, 256, 0, s>>>(in, M, out);
+}
+
+// Deterministic start vector of the power iterations: Knuth's multiplicative hash of k+1,
+// (k+1) * 2654435761 mod 2^32, mapped to [-1/2, 1/2).
+__global__ void k_hash_vector(double* __restrict__ x, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = (uint32_t)(k + 1) * 2654435761u;
+        x[k] = (double)v / 4294967296.0 - 0.5;
+    }
+}
+void launch_hash_vector(double* x, int64_t n, cudaStream_t s) {
+    k_hash_vector<<<num_blocks_for(n), 256, 0, s>>>(x, n);
+}
+
+// ------------------------------------------------------------------------------------------
+// Gradients of the discrete adjoint (see sib_grad): per spring
+//   dkappa_e = -(Lam_a - Lam_b) . (Y_a - Y_b)
+// and per marker, with the interpolation weights and their derivatives recomputed from X:
+//   dX_l^d = sum_c (d_d Lam_l^c) (K Y)_l^c + a (K Lam)_l^d + dt sum_c (K Lam)_l^c d_d U_l^c,
+//   d_d J^c_{l,f} = -(1/h) phi'(r_x) phi(r_y)  (d = x),  -(1/h) phi(r_x) phi'(r_y)  (d = y).
+// Lam, Y, KY, KL are component-major (M | M).
+__global__ void k_grad_kappa(const int* __restrict__ edges, int E, int M, const double* __restrict__ Lam,
+                             const double* __restrict__ Y, double* __restrict__ dkappa) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const int a = edges[2 * e], b = edges[2 * e + 1];
+    double s = 0.0;
+    for (int c = 0; c < 2; ++c) s += (Lam[c * M + a] - Lam[c * M + b]) * (Y[c * M + a] - Y[c * M + b]);
+    dkappa[e] = -s;
+}
+__global__ void k_grad_X(const double* __restrict__ X, int M, int N, const double* __restrict__ w,
+                         const double* __restrict__ lam, const double* __restrict__ KY, const double* __restrict__ KL,
+                         double dt, double acoef, double* __restrict__ dX) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const int n = N * N, mk = N - 1;
+    const double h = 1.0 / N, ih = (double)N, ih2 = ih * ih;
+    double gd[2] = {acoef * KL[m], acoef * KL[M + m]};
+    for (int c = 0; c < 2; ++c) {
+        const double ox = c == 0 ? 0.0 : 0.5, oy = c == 0 ? 0.5 : 0.0;
+        const double sx = X[2 * m] * N - ox, sy = X[2 * m + 1] * N - oy;
+        const int bi = (int)floor(sx) - 1, bj = (int)floor(sy) - 1;
+        double wx[4], wy[4], dx[4], dy[4];
+        for (int a = 0; a < 4; ++a) {
+            wx[a] = phi4((double)(bi + a) - sx);
+            wy[a] = phi4((double)(bj + a) - sy);
+            dx[a] = dphi4((double)(bi + a) - sx);
+            dy[a] = dphi4((double)(bj + a) - sy);
+        }
+        const double* uc = w + c * n;
+        const double* lc = lam + c * n;
+        double gU[2] = {0.0, 0.0}, gL[2] = {0.0, 0.0};
+        for (int q = 0; q < 4; ++q) {
+            const int row = ((bj + q) & mk) * N;
+            for (int p = 0; p < 4; ++p) {
+                const int f = row + ((bi + p) & mk);
+                const double jx = -dx[p] * wy[q] * ih;   // d J / d X^x
+                const double jy = -wx[p] * dy[q] * ih;   // d J / d X^y
+                gU[0] += jx * uc[f];
+                gU[1] += jy * uc[f];
+                gL[0] += jx * lc[f];
+                gL[1] += jy * lc[f];
+            }
+        }
+        (void)h;
+        for (int d = 0; d < 2; ++d) gd[d] += gL[d] * ih2 * KY[c * M + m] + dt * KL[c * M + m] * gU[d];
+    }
+    dX[2 * m] = gd[0];
+    dX[2 * m + 1] = gd[1];
+}
+void launch_grad_kappa(const int* edges, int E, int M, const double* Lam, const double* Y, double* dkappa,
+                       cudaStream_t s) {
+    if (E == 0) return;
+    k_grad_kappa<<<(E + 255) / 256, 256, 0, s>>>(edges, E, M, Lam, Y, dkappa);
+}
+void launch_grad_X(const double* X, int M, int N, const double* w, const double* lam, const double* KY,
+                   const double* KL, double dt, double acoef, double* dX, cudaStream_t s) {
+    if (M == 0) return;
+    k_grad_X<<<(M + 127) / 128, 128, 0, s>>>(X, M, N, w, lam, KY, KL, dt, acoef, dX);
+}
+
+// ------------------------------------------------------------------------------------------
+#define SIB_IB_INST(T)                                                                                           \
+    template void launch_adj_kappa<T>(const int*, const double*, int, T*, cudaStream_t);                        \
+    template void launch_interp<T>(const IBK<T>&, const T*, T*, cudaStream_t);                                  \
+    template void launch_spring<T>(const int*, const int*, const T*, int, const T*, T*, cudaStream_t);           \
+    template void launch_spread<T>(const IBK<T>&, const T*, T*, const int*, const int*, int, int, int, int, int, \
+                                   cudaStream_t);
+SIB_IB_INST(float)
+SIB_IB_INST(double)
+
+}  // namespace sib

@@ -1,0 +1,288 @@
+// FP64 kernels of the outer flexible GMRES (dot products, classical Gram-Schmidt, gauge
+// projection) and of the coarsest-grid exact solve (dense operator, Gauss-Jordan inverse,
+// pseudo-inverse apply).  All reductions use a fixed block count and a fixed reduction tree,
+// so results are bitwise reproducible run to run.
+#include <cmath>
+
+#include "sib_internal.h"
+
+namespace sib {
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double ws[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) ws[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? ws[threadIdx.x] : 0.0;
+    if (wid == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;   // valid in thread 0
+}
+
+__global__ void k_dot_partials(const double* __restrict__ x, const double* __restrict__ y, int64_t n,
+                               double* __restrict__ partials) {
+    double s = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        s += x[k] * y[k];
+    s = block_sum(s);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+void launch_dot_partials(const double* x, const double* y, int64_t n, double* partials, int nblk, cudaStream_t s) {
+    k_dot_partials<<<nblk, 256, 0, s>>>(x, y, n, partials);
+}
+
+// partials[i * nblk + b] = sum over block b's slice of V_i . w, for i < k
+__global__ void k_multidot(const double* __restrict__ V, int64_t ld, const double* __restrict__ w, int64_t n,
+                           double* __restrict__ partials) {
+    const int i = blockIdx.y;
+    const double* v = V + (int64_t)i * ld;
+    double s = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        s += v[k] * w[k];
+    s = block_sum(s);
+    if (threadIdx.x == 0) partials[(int64_t)i * gridDim.x + blockIdx.x] = s;
+}
+void launch_multidot(const double* V, int64_t ld, int k, const double* w, int64_t n, double* partials, int nblk,
+                     cudaStream_t s) {
+    k_multidot<<<dim3(nblk, k), 256, 0, s>>>(V, ld, w, n, partials);
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ partials, int nblk, double* __restrict__ out) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partials[(int64_t)blockIdx.x * nblk + b];
+    s = block_sum(s);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+void launch_reduce_partials(const double* partials, int k, int nblk, double* out, cudaStream_t s) {
+    k_reduce_partials<<<k, 256, 0, s>>>(partials, nblk, out);
+}
+
+// y += sign * sum_{i<k} coef[i] V_i
+__global__ void k_multi_axpy(const double* __restrict__ V, int64_t ld, int k, const double* __restrict__ coef,
+                             double sign, double* __restrict__ y, int64_t n) {
+    __shared__ double c[128];
+    for (int t = threadIdx.x; t < k; t += blockDim.x) c[t] = sign * coef[t];
+    __syncthreads();
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = y[e];
+        for (int i = 0; i < k; ++i) acc += c[i] * V[(int64_t)i * ld + e];
+        y[e] = acc;
+    }
+}
+void launch_multi_axpy(const double* V, int64_t ld, int k, const double* coef, double sign, double* y, int64_t n,
+                       cudaStream_t s) {
+    k_multi_axpy<<<num_blocks_for(n), 256, 0, s>>>(V, ld, k, coef, sign, y, n);
+}
+
+// x *= 1 / sqrt(vals[idx])   (normalisation of the next Arnoldi vector)
+__global__ void k_scale_rsqrt(double* __restrict__ x, const double* __restrict__ vals, int idx, int64_t n) {
+    const double nrm = sqrt(vals[idx]);
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        x[k] *= inv;
+}
+void launch_scale(double* x, const double* vals, int idx, int64_t n, cudaStream_t s) {
+    k_scale_rsqrt<<<num_blocks_for(n), 256, 0, s>>>(x, vals, idx, n);
+}
+
+// gauge projection: means of the u, v, p blocks and their removal (mask bit b = block b)
+__global__ void k_block_means(const double* __restrict__ x, int64_t n, double* __restrict__ partials) {
+    const double* xb = x + blockIdx.y * n;
+    double s = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        s += xb[k];
+    s = block_sum(s);
+    if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+void launch_block_means(const double* x, int N, int nblocks_vec, double* partials, int nblk, cudaStream_t s) {
+    k_block_means<<<dim3(nblk, nblocks_vec), 256, 0, s>>>(x, (int64_t)N * N, partials);
+}
+__global__ void k_subtract_means(double* __restrict__ x, int64_t n, const double* __restrict__ partials, int nblk,
+                                 int mask) {
+    __shared__ double mean[3];
+    if (threadIdx.x < 32) {
+        for (int b = 0; b < 3; ++b) {
+            double s = 0.0;
+            for (int q = threadIdx.x; q < nblk; q += 32) s += partials[b * nblk + q];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (threadIdx.x == 0) mean[b] = ((mask >> b) & 1) ? s / (double)n : 0.0;
+        }
+    }
+    __syncthreads();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 3 * n; k += (int64_t)gridDim.x * blockDim.x)
+        x[k] -= mean[k / n];
+}
+void launch_subtract_means(double* x, int N, const double* partials, int nblk, int mask, cudaStream_t s) {
+    const int64_t n = (int64_t)N * N;
+    k_subtract_means<<<num_blocks_for(3 * n), 256, 0, s>>>(x, n, partials, nblk, mask);
+}
+
+// ------------------------------------------------------------------------------------------
+// Coarsest level: dense L^0 + Z Z^T (Z = orthonormal kernel basis: the constant pressure, and
+// the constant velocity components when rho = 0), augmented with the identity: Aug = [L0+ZZ^T | I].
+__global__ void k_assemble_L0(int N, double rho, double mu, double dt, const double* __restrict__ B,
+                              double* __restrict__ Aug) {
+    const int n0 = N * N, n = 3 * n0, mk = N - 1;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double* row = Aug + (int64_t)r * 2 * n;
+    for (int c = 0; c < 2 * n; ++c) row[c] = 0.0;
+    row[n + r] = 1.0;
+    const double h = 1.0 / N, ih = (double)N;
+    const double a0 = rho / dt + 4.0 * mu / (h * h), cc = mu / (h * h);
+    const int blk = r / n0, f = r % n0, i = f % N, j = f / N;
+    if (blk < 2) {
+        const int off = blk * n0;
+        row[off + f] += a0;
+        row[off + j * N + ((i + 1) & mk)] -= cc;
+        row[off + j * N + ((i - 1) & mk)] -= cc;
+        row[off + ((j + 1) & mk) * N + i] -= cc;
+        row[off + ((j - 1) & mk) * N + i] -= cc;
+        // G p: (p_ij - p_{i-1,j})/h on u faces, (p_ij - p_{i,j-1})/h on v faces
+        row[2 * n0 + f] += ih;
+        if (blk == 0)
+            row[2 * n0 + j * N + ((i - 1) & mk)] -= ih;
+        else
+            row[2 * n0 + ((j - 1) & mk) * N + i] -= ih;
+        // - dt [SKJ]^0
+        const double* Bc = B + (int64_t)blk * n0 * n0 + (int64_t)f * n0;
+        for (int g = 0; g < n0; ++g) row[off + g] -= dt * Bc[g];
+    } else {
+        // - D u
+        row[f] += ih;
+        row[j * N + ((i + 1) & mk)] -= ih;
+        row[n0 + f] += ih;
+        row[n0 + ((j + 1) & mk) * N + i] -= ih;
+    }
+    if (rho == 0.0 || blk == 2) {
+        const double z = 1.0 / (double)n0;
+        for (int g = 0; g < n0; ++g) row[blk * n0 + g] += z;
+    }
+}
+void launch_assemble_L0(int N0, double rho, double mu, double dt, const double* B, double* Aug, cudaStream_t s) {
+    const int n = 3 * N0 * N0;
+    k_assemble_L0<<<(n + 127) / 128, 128, 0, s>>>(N0, rho, mu, dt, B, Aug);
+}
+
+// In-place Gauss-Jordan elimination with partial pivoting on Aug (n x 2n, row-major) by one
+// block; on exit the right half holds the inverse.  info = 0, or k+1 if pivot k is zero.
+__global__ void __launch_bounds__(1024) k_gauss_jordan(double* __restrict__ A, int n, int* __restrict__ info) {
+    extern __shared__ double fac[];   // n factors
+    __shared__ int piv;
+    __shared__ double wv[32];
+    __shared__ int wi[32];
+    const int ld = 2 * n;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) *info = 0;
+    for (int k = 0; k < n; ++k) {
+        // pivot search over rows k..n-1 of column k
+        double best = -1.0;
+        int bi = k;
+        for (int r = k + threadIdx.x; r < n; r += blockDim.x) {
+            const double a = fabs(A[(int64_t)r * ld + k]);
+            if (a > best) {
+                best = a;
+                bi = r;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            wv[wid] = best;
+            wi[wid] = bi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = wv[0];
+            int p = wi[0];
+            for (int w = 1; w < nw; ++w)
+                if (wv[w] > b || (wv[w] == b && wi[w] < p)) {
+                    b = wv[w];
+                    p = wi[w];
+                }
+            piv = p;
+            if (!(b > 0.0) && *info == 0) *info = k + 1;
+        }
+        __syncthreads();
+        const int p = piv;
+        if (p != k)
+            for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+                const double t = A[(int64_t)k * ld + c];
+                A[(int64_t)k * ld + c] = A[(int64_t)p * ld + c];
+                A[(int64_t)p * ld + c] = t;
+            }
+        __syncthreads();
+        const double pv = A[(int64_t)k * ld + k];
+        const double ipv = pv != 0.0 ? 1.0 / pv : 0.0;
+        __syncthreads();
+        for (int c = threadIdx.x; c < ld; c += blockDim.x) A[(int64_t)k * ld + c] *= ipv;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) fac[r] = (r == k) ? 0.0 : A[(int64_t)r * ld + k];
+        __syncthreads();
+        // eliminate column k from every other row (columns k.. of the left half, all of the right)
+        const int w = ld - k;
+        for (int64_t q = threadIdx.x; q < (int64_t)n * w; q += blockDim.x) {
+            const int r = (int)(q / w), c = k + (int)(q % w);
+            const double f = fac[r];
+            if (f != 0.0) A[(int64_t)r * ld + c] -= f * A[(int64_t)k * ld + c];
+        }
+        __syncthreads();
+    }
+}
+void launch_gauss_jordan(double* Aug, int n, int* info, cudaStream_t s) {
+    k_gauss_jordan<<<1, 1024, sizeof(double) * n, s>>>(Aug, n, info);
+}
+
+// Pinv = (L0 + Z Z^T)^{-1} - Z Z^T, the pseudo-inverse of the symmetric L0 whose kernel is span Z.
+__global__ void k_extract_pinv(const double* __restrict__ Aug, int n, int N0, double rho, double* __restrict__ P) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n * n) return;
+    const int r = (int)(q / n), c = (int)(q % n);
+    const int n0 = N0 * N0;
+    double v = Aug[(int64_t)r * 2 * n + n + c];
+    const int br = r / n0, bc = c / n0;
+    if (br == bc && (rho == 0.0 || br == 2)) v -= 1.0 / (double)n0;
+    P[q] = v;
+}
+void launch_extract_pinv(const double* Aug, int n, int N0, double rho, double* Pinv, cudaStream_t s) {
+    const int64_t tot = (int64_t)n * n;
+    k_extract_pinv<<<(int)((tot + 255) / 256), 256, 0, s>>>(Aug, n, N0, rho, Pinv);
+}
+
+// x = Pinv b, one warp per row, FP64 accumulation for both precisions
+template <typename T>
+__global__ void k_coarse_apply(const double* __restrict__ P, int n, const T* __restrict__ b, T* __restrict__ x) {
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= n) return;
+    const double* row = P + (int64_t)r * n;
+    double s = 0.0;
+    for (int c = lane; c < n; c += 32) s += row[c] * (double)b[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[r] = (T)s;
+}
+template <typename T>
+void launch_coarse_apply(const double* Pinv, int n, const T* b, T* x, cudaStream_t s) {
+    k_coarse_apply<T><<<(n + 7) / 8, 256, 0, s>>>(Pinv, n, b, x);
+}
+template void launch_coarse_apply<float>(const double*, int, const float*, float*, cudaStream_t);
+template void launch_coarse_apply<double>(const double*, int, const double*, double*, cudaStream_t);
+
+__global__ void k_check_finite(const double* __restrict__ x, int64_t n, int* __restrict__ flag) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(x[k])) *flag = 1;
+}
+void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t s) {
+    if (n == 0) return;
+    k_check_finite<<<num_blocks_for(n), 256, 0, s>>>(x, n, flag);
+}
+
+}  // namespace sib

@@ -1,0 +1,125 @@
+// Internal declarations of libsib: kernel argument blocks, launchers and the solver context.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sib.h"
+
+namespace sib {
+
+// Grid kernels work on tiles of TX x TY cells (one thread per cell); smaller levels use
+// min(N, TX) x min(N, TY).  The IB "active tile" flags use the same tiles.
+constexpr int TX = 32;
+constexpr int TY = 8;
+constexpr int MAX_N = 8192;
+
+// ------------------------------------------------------------------------------------------
+// Morton order of a cell (i, j): bits of i on even positions, bits of j on odd positions.
+// The bins of level l are the Morton codes of the fine-level bins shifted right by 2(lmax-l).
+__host__ __device__ inline uint32_t part1by1(uint32_t x) {
+    x &= 0x0000ffffu;
+    x = (x | (x << 8)) & 0x00ff00ffu;
+    x = (x | (x << 4)) & 0x0f0f0f0fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+__host__ __device__ inline uint32_t morton(uint32_t i, uint32_t j) { return part1by1(i) | (part1by1(j) << 1); }
+
+// ------------------------------------------------------------------------------------------
+// Arguments of the MAC-grid stencil kernels on one level.
+template <typename T>
+struct GridK {
+    int N, tx, ty, ntx;
+    T inv_h;       // 1/h
+    T a0;          // rho/dt + 4 mu / h^2   (diagonal of A)
+    T c;           // mu / h^2              (off-diagonal magnitude of A)
+    T dt;
+    T omega;
+    const T* fib;                    // [S K J]^l u on the faces (2 n), valid where the tile is active
+    const T* ibd;                    // 4 n: B(f,f) on u faces, B(u_ij,u_i+1j), B(f,f) on v, B(v_ij,v_ij+1)
+    const unsigned char* tile;       // per-tile IB flag (dilated by one tile), may be null
+};
+
+// Arguments of the marker kernels on one level (per velocity component c = 0, 1).
+template <typename T>
+struct IBK {
+    int N, W, M;
+    int shift;                       // Morton shift from fine bins to this level's bins
+    const int* base[2];              // packed stencil origin (bj << 16) | bi, per marker
+    const T* wgt[2];                 // per marker 8 weights: wx[0..3], wy[0..3]
+    const int* binStart[2];          // N*N + 1, Morton-indexed ranges into sorted[]
+    const int* sorted[2];            // marker ids in Morton order of their fine stencil origin
+    T inv_h2;
+};
+
+// ------------------------------------------------------------------------------------------
+// launchers (kernels_grid.cu)
+template <typename T> void launch_residual(const GridK<T>& g, const T* x, const T* b, T* r, cudaStream_t s);
+template <typename T> void launch_vanka(const GridK<T>& g, const T* x, const T* b, T* xo, cudaStream_t s);
+template <typename T> void launch_restrict(int Nc, const T* rf, T* bc, cudaStream_t s);
+template <typename T> void launch_prolong_add(int Nc, const T* ec, T* xf, cudaStream_t s);
+template <typename Ti, typename To> void launch_convert(const Ti* in, To* out, int64_t n, cudaStream_t s);
+template <typename T> void launch_axpby(T a, const T* x, T b, const T* y, T* z, int64_t n, cudaStream_t s);
+// Schur-complement smoother pieces
+template <typename T> void launch_sc_jacobi_A(const GridK<T>& g, const T* r, T* z, T scale, cudaStream_t s);
+template <typename T> void launch_apply_AIB(const GridK<T>& g, const T* u, T* y, cudaStream_t s);
+template <typename T> void launch_gradient(const GridK<T>& g, const T* p, T* gu, cudaStream_t s);
+template <typename T> void launch_divergence(const GridK<T>& g, const T* u, T* d, cudaStream_t s);
+template <typename T> void launch_jacobi_M(const GridK<T>& g, const T* r, T* z, T scale, cudaStream_t s);
+template <typename T> void launch_cheb_update(const T* dinvr, T* d, T* x, T ra, T rb, int64_t n, cudaStream_t s);
+
+// launchers (kernels_ib.cu)
+void launch_stencils(const double* X, int M, int Nf, int lmax, int** base, double** w64, float** w32,
+                     cudaStream_t s);
+void launch_sort_keys(const int* baseFine, int M, int Mpad, uint64_t* keys, cudaStream_t s);
+void launch_bitonic(uint64_t* keys, int Mpad, cudaStream_t s);
+void launch_unpack_sorted(const uint64_t* keys, int M, int* sorted, uint32_t* mkey, cudaStream_t s);
+void launch_bins(const uint32_t* mkey, int M, int nbins, int shift, int* binStart, cudaStream_t s);
+void launch_tile_flags(const int* base, int M, int W, int N, int tx, int ty, int ntx, unsigned char* flag,
+                       cudaStream_t s);
+void launch_tile_finish(unsigned char* flag, int ntx, int nty, int* tiles, int* nTiles, cudaStream_t s);
+void launch_adjacency(const int* edges, int E, int M, int* deg, int* start, int* nbr, int* eid,
+                      cudaStream_t s);
+template <typename T> void launch_adj_kappa(const int* eid, const double* kappa, int n2E, T* kap, cudaStream_t s);
+template <typename T> void launch_interp(const IBK<T>& k, const T* u, T* U, cudaStream_t s);
+template <typename T> void launch_spring(const int* start, const int* nbr, const T* kap, int M, const T* U, T* F,
+                                         cudaStream_t s);
+template <typename T> void launch_spread(const IBK<T>& k, const T* F, T* f, const int* tiles, const int* nTiles,
+                                         int maxTiles, int tx, int ty, int ntx, int warpPerFace, cudaStream_t s);
+void launch_patch_entries(const int* edges, const double* kappa, int E, const int* base0, const int* base1,
+                          const double* w0, const double* w1, int M, int N, int W, double inv_h2,
+                          double* ibd, cudaStream_t s);
+void launch_dense_ib(const int* edges, const double* kappa, int E, const int* base0, const int* base1,
+                     const double* w0, const double* w1, int N, int W, double inv_h2, double* B,
+                     cudaStream_t s);
+void launch_deinterleave(const double* in, int M, double* out, cudaStream_t s);
+void launch_interleave(const double* in, int M, double* out, cudaStream_t s);
+void launch_hash_vector(double* x, int64_t n, cudaStream_t s);
+void launch_grad_kappa(const int* edges, int E, int M, const double* Lam, const double* Y, double* dkappa,
+                       cudaStream_t s);
+void launch_grad_X(const double* X, int M, int N, const double* w, const double* lam, const double* KY,
+                   const double* KL, double dt, double acoef, double* dX, cudaStream_t s);
+
+// launchers (kernels_krylov.cu)
+void launch_dot_partials(const double* x, const double* y, int64_t n, double* partials, int nblk, cudaStream_t s);
+void launch_multidot(const double* V, int64_t ld, int k, const double* w, int64_t n, double* partials, int nblk,
+                     cudaStream_t s);
+void launch_reduce_partials(const double* partials, int k, int nblk, double* out, cudaStream_t s);
+void launch_multi_axpy(const double* V, int64_t ld, int k, const double* coef, double sign, double* y,
+                       int64_t n, cudaStream_t s);
+void launch_scale(double* x, const double* num_den, int idx, int64_t n, cudaStream_t s);
+void launch_block_means(const double* x, int N, int nblocks_vec, double* partials, int nblk, cudaStream_t s);
+void launch_subtract_means(double* x, int N, const double* partials, int nblk, int mask, cudaStream_t s);
+void launch_assemble_L0(int N0, double rho, double mu, double dt, const double* B, double* Aug, cudaStream_t s);
+void launch_gauss_jordan(double* Aug, int n, int* info, cudaStream_t s);
+void launch_extract_pinv(const double* Aug, int n, int N0, double rho, double* Pinv, cudaStream_t s);
+template <typename T> void launch_coarse_apply(const double* Pinv, int n, const T* b, T* x, cudaStream_t s);
+void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t s);
+
+int num_blocks_for(int64_t n);
+
+}  // namespace sib

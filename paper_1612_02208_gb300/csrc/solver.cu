@@ -1,0 +1,1338 @@
+// libsib: solver context, set-up, V-cycle (Alg. 1), flexible GMRES and the C ABI of sib.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "sib_internal.h"
+
+using namespace sib;
+
+namespace {
+
+struct SibError : std::runtime_error {
+    int code;
+    SibError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define CK(call)                                                                                        \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            throw SibError(SIB_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));            \
+    } while (0)
+
+constexpr int NBLK = 296;   // fixed block count of the FP64 reductions (2 x 148 ... any fixed value)
+
+template <typename T> struct Prec;
+template <> struct Prec<double> { static constexpr int id = 0; };
+template <> struct Prec<float> { static constexpr int id = 1; };
+
+}  // namespace
+
+struct LevelBuf {
+    void* x = nullptr;
+    void* xt = nullptr;
+    void* b = nullptr;
+    void* r = nullptr;
+    void* fib = nullptr;
+    void* ibd = nullptr;
+    void* w[2] = {nullptr, nullptr};
+    // Schur-complement smoother temporaries: 8 velocity-sized, 6 pressure-sized
+    void* tv[8] = {};
+    void* tp[6] = {};
+};
+
+struct Level {
+    int N = 0, tx = 0, ty = 0, ntx = 0, nty = 0, ntiles = 0, W = 4;
+    double h = 0;
+    int* base[2] = {nullptr, nullptr};
+    int* binStart[2] = {nullptr, nullptr};
+    unsigned char* tileFlag = nullptr;   // 2 * ntiles: raw, dilated
+    int* tiles = nullptr;
+    int* nTiles = nullptr;
+    int hnTiles = 0;
+    int spreadWarp = 0;
+    LevelBuf p[2];                       // [0] FP64, [1] FP32
+    double lamA = 0, lamM = 0;
+};
+
+struct sib_ctx {
+    int N = 0, n_min = 8, lmax = 0;
+    double rho = 0.0, mu = 1.0, dt = 1e-2;
+    sib_opts opts{};
+    std::string err;
+    int64_t launches = 0;
+    int64_t bytes = 0;
+    double setup_ms = 0.0;
+    std::vector<void*> allocs;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // structure
+    int M = 0, E = 0;
+    int Mcap = 0, Ecap = 0;
+    double* X = nullptr;         // M x 2 interleaved
+    double* Xc = nullptr;        // component-major
+    int* edges = nullptr;
+    double* kappa = nullptr;
+    bool structDirty = true, kappaDirty = true, fluidDirty = true, setupDone = false;
+    bool haveIB = false;
+    // topology
+    uint64_t* keys = nullptr;
+    int Mpad = 0;
+    int* sorted[2] = {nullptr, nullptr};
+    uint32_t* mkey[2] = {nullptr, nullptr};
+    int* adjStart = nullptr;
+    int* adjNbr = nullptr;
+    int* adjEid = nullptr;
+    int* deg = nullptr;
+    double* kap64 = nullptr;
+    float* kap32 = nullptr;
+    void* U[2] = {nullptr, nullptr};
+    void* F[2] = {nullptr, nullptr};
+    double* gradTmp = nullptr;   // 8 M: Lam, Y, KY, KL (component-major)
+    std::vector<Level> L;
+    // coarsest
+    double* B0 = nullptr;
+    double* Aug = nullptr;
+    double* Pinv = nullptr;
+    int* info = nullptr;
+    int n0 = 0;
+    // FGMRES
+    int mcap = 0;
+    double* V = nullptr;
+    double* Z = nullptr;
+    double* rhs = nullptr;
+    double* sol = nullptr;
+    double* res = nullptr;
+    double* part = nullptr;      // NBLK * 128
+    double* scal = nullptr;      // 3 * 128 scalars: h, h2, misc
+    double* hbuf = nullptr;      // pinned host mirror
+    int* flag = nullptr;
+    // eigen estimate override
+    bool lamOverride = false;
+    std::vector<double> lamA_ov, lamM_ov;
+    // graphs
+    cudaGraphExec_t vg[2] = {nullptr, nullptr};
+    void* vgOut[2] = {nullptr, nullptr};
+    int64_t vgNodes[2] = {0, 0};
+};
+
+namespace {
+
+void* dalloc(sib_ctx* c, size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw SibError(SIB_ERR_ALLOC, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    c->allocs.push_back(p);
+    c->bytes += (int64_t)bytes;
+    return p;
+}
+void dfree(sib_ctx* c, void* p) {
+    if (!p) return;
+    for (size_t k = 0; k < c->allocs.size(); ++k)
+        if (c->allocs[k] == p) {
+            c->allocs.erase(c->allocs.begin() + k);
+            break;
+        }
+    cudaFree(p);
+}
+
+inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+void kcheck(sib_ctx* c) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw SibError(SIB_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    (void)c;
+}
+
+// count one kernel launch (every launcher used on the solve path starts exactly one kernel)
+#define KL(c, call)         \
+    do {                    \
+        call;               \
+        ++(c)->launches;    \
+    } while (0)
+
+void invalidate_graphs(sib_ctx* c) {
+    for (int p = 0; p < 2; ++p) {
+        if (c->vg[p]) cudaGraphExecDestroy(c->vg[p]);
+        c->vg[p] = nullptr;
+        c->vgOut[p] = nullptr;
+    }
+}
+
+template <typename T>
+GridK<T> gridk(sib_ctx* c, int l) {
+    Level& lv = c->L[l];
+    GridK<T> g;
+    g.N = lv.N;
+    g.tx = lv.tx;
+    g.ty = lv.ty;
+    g.ntx = lv.ntx;
+    const double h = lv.h;
+    g.inv_h = (T)(1.0 / h);
+    g.a0 = (T)(c->rho / c->dt + 4.0 * c->mu / (h * h));
+    g.c = (T)(c->mu / (h * h));
+    g.dt = (T)c->dt;
+    g.omega = (T)c->opts.omega;
+    const int pi = Prec<T>::id;
+    g.fib = (const T*)lv.p[pi].fib;
+    g.ibd = (const T*)lv.p[pi].ibd;
+    g.tile = c->haveIB ? lv.tileFlag + lv.ntiles : nullptr;
+    return g;
+}
+
+template <typename T>
+IBK<T> ibk(sib_ctx* c, int l) {
+    Level& lv = c->L[l];
+    IBK<T> k;
+    k.N = lv.N;
+    k.W = lv.W;
+    k.M = c->M;
+    k.shift = 2 * (c->lmax - l);
+    const int pi = Prec<T>::id;
+    for (int q = 0; q < 2; ++q) {
+        k.base[q] = lv.base[q];
+        k.wgt[q] = (const T*)lv.p[pi].w[q];
+        k.binStart[q] = lv.binStart[q];
+        k.sorted[q] = c->sorted[q];
+    }
+    k.inv_h2 = (T)(1.0 / (lv.h * lv.h));
+    return k;
+}
+
+template <typename T>
+const T* kapp(sib_ctx* c) {
+    if constexpr (Prec<T>::id == 0)
+        return c->kap64;
+    else
+        return c->kap32;
+}
+
+// f = [S K J]^l u (velocity part of x), written into the level's fib (only IB-active tiles)
+template <typename T>
+void ib_apply(sib_ctx* c, int l, const T* u, cudaStream_t s) {
+    if (!c->haveIB) return;
+    Level& lv = c->L[l];
+    const int pi = Prec<T>::id;
+    IBK<T> k = ibk<T>(c, l);
+    T* U = (T*)c->U[pi];
+    T* F = (T*)c->F[pi];
+    KL(c, launch_interp<T>(k, u, U, s));
+    KL(c, launch_spring<T>(c->adjStart, c->adjNbr, kapp<T>(c), c->M, U, F, s));
+    KL(c, launch_spread<T>(k, F, (T*)lv.p[pi].fib, lv.tiles, lv.nTiles, lv.hnTiles, lv.tx, lv.ty, lv.ntx,
+                           lv.spreadWarp, s));
+}
+
+template <typename T>
+void apply_operator(sib_ctx* c, int l, const T* x, const T* b, T* r, cudaStream_t s) {
+    ib_apply<T>(c, l, x, s);
+    KL(c, launch_residual<T>(gridk<T>(c, l), x, b, r, s));
+}
+
+// ---- Schur-complement smoother (Eq. approx-fact-Stokes-IB) -----------------------------------
+struct ChebCoef {
+    double theta, delta, sigma;
+};
+ChebCoef cheb_coef(double lam, double lo, double hi) {
+    const double a = lo * lam, b = hi * lam;
+    ChebCoef k;
+    k.theta = 0.5 * (a + b);
+    k.delta = 0.5 * (b - a);
+    k.sigma = k.theta / k.delta;
+    return k;
+}
+
+// out = At^{-1} q: cheb_iters Chebyshev iterations on A_IB, Jacobi-preconditioned, from 0.
+// Uses tv[0..3] of the level.
+template <typename T>
+void cheb_A(sib_ctx* c, int l, const T* q, T* out, cudaStream_t s) {
+    Level& lv = c->L[l];
+    const int pi = Prec<T>::id;
+    const int64_t nv = 2LL * lv.N * lv.N;
+    T* rr = (T*)lv.p[pi].tv[0];
+    T* t = (T*)lv.p[pi].tv[1];
+    T* z = (T*)lv.p[pi].tv[2];
+    T* d = (T*)lv.p[pi].tv[3];
+    GridK<T> g = gridk<T>(c, l);
+    const ChebCoef k = cheb_coef(lv.lamA, c->opts.cheb_lo, c->opts.cheb_hi);
+    KL(c, launch_sc_jacobi_A<T>(g, q, d, (T)(1.0 / k.theta), s));
+    KL(c, launch_axpby<T>((T)1, d, (T)0, nullptr, out, nv, s));
+    double rho = 1.0 / k.sigma;
+    const int iters = c->opts.cheb_iters;
+    if (iters > 1) KL(c, launch_axpby<T>((T)1, q, (T)0, nullptr, rr, nv, s));
+    for (int it = 1; it < iters; ++it) {
+        ib_apply<T>(c, l, d, s);
+        KL(c, launch_apply_AIB<T>(g, d, t, s));
+        KL(c, launch_axpby<T>((T)1, rr, (T)-1, t, rr, nv, s));
+        KL(c, launch_sc_jacobi_A<T>(g, rr, z, (T)1, s));
+        const double rn = 1.0 / (2.0 * k.sigma - rho);
+        KL(c, launch_cheb_update<T>(z, d, out, (T)(rn * rho), (T)(2.0 * rn / k.delta), nv, s));
+        rho = rn;
+    }
+}
+
+// out = Mt^{-1} q: Chebyshev iterations on D At^{-1} G preconditioned by diag(D diag(A_IB)^{-1} G).
+// Uses tv[4..5] and tp[2..5].
+template <typename T>
+void cheb_M(sib_ctx* c, int l, const T* q, T* out, cudaStream_t s) {
+    Level& lv = c->L[l];
+    const int pi = Prec<T>::id;
+    const int64_t np = (int64_t)lv.N * lv.N;
+    T* gq = (T*)lv.p[pi].tv[4];
+    T* ya = (T*)lv.p[pi].tv[5];
+    T* rr = (T*)lv.p[pi].tp[2];
+    T* z = (T*)lv.p[pi].tp[3];
+    T* d = (T*)lv.p[pi].tp[4];
+    T* md = (T*)lv.p[pi].tp[5];
+    GridK<T> g = gridk<T>(c, l);
+    const ChebCoef k = cheb_coef(lv.lamM, c->opts.cheb_lo, c->opts.cheb_hi);
+    KL(c, launch_jacobi_M<T>(g, q, d, (T)(1.0 / k.theta), s));
+    KL(c, launch_axpby<T>((T)1, d, (T)0, nullptr, out, np, s));
+    double rho = 1.0 / k.sigma;
+    const int iters = c->opts.cheb_iters;
+    if (iters > 1) KL(c, launch_axpby<T>((T)1, q, (T)0, nullptr, rr, np, s));
+    for (int it = 1; it < iters; ++it) {
+        KL(c, launch_gradient<T>(g, d, gq, s));
+        cheb_A<T>(c, l, gq, ya, s);
+        KL(c, launch_divergence<T>(g, ya, md, s));
+        KL(c, launch_axpby<T>((T)1, rr, (T)-1, md, rr, np, s));
+        KL(c, launch_jacobi_M<T>(g, rr, z, (T)1, s));
+        const double rn = 1.0 / (2.0 * k.sigma - rho);
+        KL(c, launch_cheb_update<T>(z, d, out, (T)(rn * rho), (T)(2.0 * rn / k.delta), np, s));
+        rho = rn;
+    }
+}
+
+// xo = x + omega * Lt^{-1} (b - L x)
+template <typename T>
+void sc_sweep(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream_t s) {
+    Level& lv = c->L[l];
+    const int pi = Prec<T>::id;
+    const int64_t np = (int64_t)lv.N * lv.N, nv = 2 * np;
+    T* r = (T*)lv.p[pi].r;
+    T* y = (T*)lv.p[pi].tv[6];
+    T* yy = (T*)lv.p[pi].tv[7];
+    T* sv = (T*)lv.p[pi].tp[0];
+    T* dp = (T*)lv.p[pi].tp[1];
+    GridK<T> g = gridk<T>(c, l);
+    apply_operator<T>(c, l, x, b, r, s);
+    cheb_A<T>(c, l, r, y, s);                                        // y = At^{-1} r_u
+    KL(c, launch_divergence<T>(g, y, sv, s));                        // s = r_p + D y
+    KL(c, launch_axpby<T>((T)1, r + nv, (T)1, sv, sv, np, s));
+    cheb_M<T>(c, l, sv, dp, s);                                      // dp = Mt^{-1} s
+    T* gq = (T*)lv.p[pi].tv[4];
+    KL(c, launch_gradient<T>(g, dp, gq, s));                         // yy = At^{-1} G dp
+    cheb_A<T>(c, l, gq, yy, s);
+    const T om = (T)c->opts.omega;
+    KL(c, launch_axpby<T>((T)1, y, (T)-1, yy, y, nv, s));            // du = y - yy
+    KL(c, launch_axpby<T>((T)1, x, om, y, xo, nv, s));               // xo_u = x_u + omega du
+    KL(c, launch_axpby<T>((T)1, x + nv, om, dp, xo + nv, np, s));    // xo_p = x_p + omega dp
+}
+
+// one smoothing sweep xo <- smooth(x, b)
+template <typename T>
+void sweep(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream_t s) {
+    if (c->opts.smoother == SIB_SMOOTHER_SC) {
+        sc_sweep<T>(c, l, x, b, xo, s);
+    } else {
+        ib_apply<T>(c, l, x, s);
+        KL(c, launch_vanka<T>(gridk<T>(c, l), x, b, xo, s));
+    }
+}
+
+// Alg. 1 on level l with right-hand side in the level's b; returns the buffer holding w.
+template <typename T>
+T* vcycle_level(sib_ctx* c, int l, cudaStream_t s) {
+    Level& lv = c->L[l];
+    const int pi = Prec<T>::id;
+    if (l == 0) {
+        KL(c, launch_coarse_apply<T>(c->Pinv, c->n0, (const T*)lv.p[pi].b, (T*)lv.p[pi].x, s));
+        return (T*)lv.p[pi].x;
+    }
+    const int64_t n3 = 3LL * lv.N * lv.N;
+    T* x = (T*)lv.p[pi].x;
+    T* xt = (T*)lv.p[pi].xt;
+    const T* b = (const T*)lv.p[pi].b;
+    CK(cudaMemsetAsync(x, 0, sizeof(T) * n3, s));
+    for (int k = 0; k < c->opts.nu1; ++k) {
+        sweep<T>(c, l, x, b, xt, s);
+        std::swap(x, xt);
+    }
+    apply_operator<T>(c, l, x, b, (T*)lv.p[pi].r, s);
+    KL(c, launch_restrict<T>(c->L[l - 1].N, (const T*)lv.p[pi].r, (T*)c->L[l - 1].p[pi].b, s));
+    T* ec = vcycle_level<T>(c, l - 1, s);
+    KL(c, launch_prolong_add<T>(c->L[l - 1].N, ec, x, s));
+    for (int k = 0; k < c->opts.nu2; ++k) {
+        sweep<T>(c, l, x, b, xt, s);
+        std::swap(x, xt);
+    }
+    return x;
+}
+
+// Run one V-cycle on the finest level's b; returns the output buffer.
+template <typename T>
+T* vcycle(sib_ctx* c, cudaStream_t s) {
+    const int pi = Prec<T>::id;
+    if (!c->opts.use_graphs) return vcycle_level<T>(c, c->lmax, s);
+    if (!c->vg[pi]) {
+        const int64_t before = c->launches;
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        T* out = nullptr;
+        try {
+            out = vcycle_level<T>(c, c->lmax, c->cap);
+        } catch (...) {
+            cudaStreamEndCapture(c->cap, &graph);
+            throw;
+        }
+        CK(cudaStreamEndCapture(c->cap, &graph));
+        CK(cudaGraphInstantiate(&c->vg[pi], graph, 0));
+        cudaGraphDestroy(graph);
+        c->vgOut[pi] = out;
+        c->vgNodes[pi] = c->launches - before;
+        c->launches = before;
+    }
+    CK(cudaGraphLaunch(c->vg[pi], s));
+    c->launches += c->vgNodes[pi];
+    return (T*)c->vgOut[pi];
+}
+
+int64_t n3f(sib_ctx* c) { return 3LL * c->N * c->N; }
+
+// ---- set-up -----------------------------------------------------------------------------------
+void alloc_level_bufs(sib_ctx* c) {
+    for (int l = 0; l <= c->lmax; ++l) {
+        Level& lv = c->L[l];
+        const size_t n = (size_t)lv.N * lv.N;
+        for (int pi = 0; pi < 2; ++pi) {
+            const size_t e = pi == 0 ? 8 : 4;
+            LevelBuf& b = lv.p[pi];
+            b.x = dalloc(c, e * 3 * n);
+            b.xt = dalloc(c, e * 3 * n);
+            b.b = dalloc(c, e * 3 * n);
+            b.r = dalloc(c, e * 3 * n);
+            b.fib = dalloc(c, e * 2 * n);
+            b.ibd = dalloc(c, e * 4 * n);
+        }
+        lv.tileFlag = (unsigned char*)dalloc(c, 2 * (size_t)lv.ntiles);
+        lv.tiles = (int*)dalloc(c, sizeof(int) * (size_t)lv.ntiles);
+        lv.nTiles = (int*)dalloc(c, sizeof(int));
+        lv.binStart[0] = (int*)dalloc(c, sizeof(int) * (n + 1));
+        lv.binStart[1] = (int*)dalloc(c, sizeof(int) * (n + 1));
+    }
+}
+
+void alloc_sc_bufs(sib_ctx* c) {
+    for (int l = 1; l <= c->lmax; ++l) {
+        Level& lv = c->L[l];
+        const size_t n = (size_t)lv.N * lv.N;
+        for (int pi = 0; pi < 2; ++pi) {
+            const size_t e = pi == 0 ? 8 : 4;
+            LevelBuf& b = lv.p[pi];
+            if (b.tv[0]) continue;
+            for (int k = 0; k < 8; ++k) b.tv[k] = dalloc(c, e * 2 * n);
+            for (int k = 0; k < 6; ++k) b.tp[k] = dalloc(c, e * n);
+        }
+    }
+}
+
+void alloc_markers(sib_ctx* c) {
+    if (c->M <= c->Mcap && c->E <= c->Ecap && c->X) return;
+    for (int l = 0; l <= c->lmax; ++l) {
+        Level& lv = c->L[l];
+        for (int q = 0; q < 2; ++q) {
+            dfree(c, lv.base[q]);
+            dfree(c, lv.p[0].w[q]);
+            dfree(c, lv.p[1].w[q]);
+        }
+    }
+    for (void* p : {(void*)c->X, (void*)c->Xc, (void*)c->edges, (void*)c->kappa, (void*)c->keys, (void*)c->sorted[0],
+                    (void*)c->sorted[1], (void*)c->mkey[0], (void*)c->mkey[1], (void*)c->adjStart, (void*)c->adjNbr,
+                    (void*)c->adjEid, (void*)c->deg, (void*)c->kap64, (void*)c->kap32, c->U[0], c->U[1], c->F[0],
+                    c->F[1], (void*)c->gradTmp})
+        dfree(c, p);
+    const int Mc = c->M > c->Mcap ? c->M : (c->Mcap > 0 ? c->Mcap : 1);
+    const int Ec = c->E > c->Ecap ? c->E : (c->Ecap > 0 ? c->Ecap : 1);
+    c->Mcap = Mc;
+    c->Ecap = Ec;
+    int Mpad = 1;
+    while (Mpad < Mc) Mpad <<= 1;
+    c->X = (double*)dalloc(c, sizeof(double) * 2 * Mc);
+    c->Xc = (double*)dalloc(c, sizeof(double) * 2 * Mc);
+    c->edges = (int*)dalloc(c, sizeof(int) * 2 * Ec);
+    c->kappa = (double*)dalloc(c, sizeof(double) * Ec);
+    c->keys = (uint64_t*)dalloc(c, sizeof(uint64_t) * Mpad);
+    for (int q = 0; q < 2; ++q) {
+        c->sorted[q] = (int*)dalloc(c, sizeof(int) * Mc);
+        c->mkey[q] = (uint32_t*)dalloc(c, sizeof(uint32_t) * Mc);
+    }
+    c->adjStart = (int*)dalloc(c, sizeof(int) * (Mc + 1));
+    c->adjNbr = (int*)dalloc(c, sizeof(int) * 2 * Ec);
+    c->adjEid = (int*)dalloc(c, sizeof(int) * 2 * Ec);
+    c->deg = (int*)dalloc(c, sizeof(int) * Mc);
+    c->kap64 = (double*)dalloc(c, sizeof(double) * 2 * Ec);
+    c->kap32 = (float*)dalloc(c, sizeof(float) * 2 * Ec);
+    c->U[0] = dalloc(c, sizeof(double) * 2 * Mc);
+    c->F[0] = dalloc(c, sizeof(double) * 2 * Mc);
+    c->U[1] = dalloc(c, sizeof(float) * 2 * Mc);
+    c->F[1] = dalloc(c, sizeof(float) * 2 * Mc);
+    c->gradTmp = (double*)dalloc(c, sizeof(double) * 8 * Mc);
+    for (int l = 0; l <= c->lmax; ++l) {
+        Level& lv = c->L[l];
+        for (int q = 0; q < 2; ++q) {
+            lv.base[q] = (int*)dalloc(c, sizeof(int) * Mc);
+            lv.p[0].w[q] = dalloc(c, sizeof(double) * 8 * Mc);
+            lv.p[1].w[q] = dalloc(c, sizeof(float) * 8 * Mc);
+        }
+    }
+}
+
+void alloc_krylov(sib_ctx* c) {
+    const int m = c->opts.restart < c->opts.max_it ? c->opts.restart : c->opts.max_it;
+    if (m <= c->mcap && c->V) return;
+    dfree(c, c->V);
+    dfree(c, c->Z);
+    const size_t n = (size_t)n3f(c);
+    c->V = (double*)dalloc(c, sizeof(double) * n * (m + 1));
+    c->Z = (double*)dalloc(c, sizeof(double) * n * m);
+    c->mcap = m;
+}
+
+// power iterations for lambda_max of diag^{-1} Op (FP64), start vector = hash vector
+double power_A(sib_ctx* c, int l, cudaStream_t s) {
+    Level& lv = c->L[l];
+    const int64_t nv = 2LL * lv.N * lv.N;
+    double* v = (double*)lv.p[0].tv[6];
+    double* w = (double*)lv.p[0].tv[7];
+    double* t = (double*)lv.p[0].tv[1];
+    GridK<double> g = gridk<double>(c, l);
+    KL(c, launch_hash_vector(v, nv, s));
+    KL(c, launch_dot_partials(v, v, nv, c->part, NBLK, s));
+    KL(c, launch_reduce_partials(c->part, 1, NBLK, c->scal + 300, s));
+    KL(c, launch_scale(v, c->scal, 300, nv, s));
+    for (int it = 0; it < c->opts.power_iters; ++it) {
+        ib_apply<double>(c, l, v, s);
+        KL(c, launch_apply_AIB<double>(g, v, t, s));
+        KL(c, launch_sc_jacobi_A<double>(g, t, w, 1.0, s));
+        KL(c, launch_dot_partials(w, w, nv, c->part, NBLK, s));
+        KL(c, launch_reduce_partials(c->part, 1, NBLK, c->scal + 300, s));
+        KL(c, launch_scale(w, c->scal, 300, nv, s));
+        std::swap(v, w);
+    }
+    double val = 0;
+    CK(cudaMemcpyAsync(&val, c->scal + 300, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return std::sqrt(val);
+}
+double power_M(sib_ctx* c, int l, cudaStream_t s) {
+    Level& lv = c->L[l];
+    const int64_t np = (int64_t)lv.N * lv.N;
+    double* v = (double*)lv.p[0].tp[0];
+    double* w = (double*)lv.p[0].tp[1];
+    double* md = (double*)lv.p[0].tp[5];
+    double* gq = (double*)lv.p[0].tv[4];
+    double* ya = (double*)lv.p[0].tv[5];
+    GridK<double> g = gridk<double>(c, l);
+    KL(c, launch_hash_vector(v, np, s));
+    KL(c, launch_dot_partials(v, v, np, c->part, NBLK, s));
+    KL(c, launch_reduce_partials(c->part, 1, NBLK, c->scal + 300, s));
+    KL(c, launch_scale(v, c->scal, 300, np, s));
+    for (int it = 0; it < c->opts.power_iters; ++it) {
+        KL(c, launch_gradient<double>(g, v, gq, s));
+        cheb_A<double>(c, l, gq, ya, s);
+        KL(c, launch_divergence<double>(g, ya, md, s));
+        KL(c, launch_jacobi_M<double>(g, md, w, 1.0, s));
+        KL(c, launch_dot_partials(w, w, np, c->part, NBLK, s));
+        KL(c, launch_reduce_partials(c->part, 1, NBLK, c->scal + 300, s));
+        KL(c, launch_scale(w, c->scal, 300, np, s));
+        std::swap(v, w);
+    }
+    double val = 0;
+    CK(cudaMemcpyAsync(&val, c->scal + 300, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return std::sqrt(val);
+}
+
+void setup(sib_ctx* c, cudaStream_t s) {
+    CK(cudaEventRecord(c->ev0, s));
+    invalidate_graphs(c);
+    c->haveIB = c->M > 0 && c->E > 0;
+    if (c->structDirty) {
+        if (c->M > 0) {
+            std::vector<int*> base(2 * (c->lmax + 1));
+            std::vector<double*> w64(2 * (c->lmax + 1));
+            std::vector<float*> w32(2 * (c->lmax + 1));
+            for (int l = 0; l <= c->lmax; ++l)
+                for (int q = 0; q < 2; ++q) {
+                    base[2 * l + q] = c->L[l].base[q];
+                    w64[2 * l + q] = (double*)c->L[l].p[0].w[q];
+                    w32[2 * l + q] = (float*)c->L[l].p[1].w[q];
+                }
+            KL(c, launch_stencils(c->X, c->M, c->N, c->lmax, base.data(), w64.data(), w32.data(), s));
+            KL(c, launch_deinterleave(c->X, c->M, c->Xc, s));
+            int Mpad = 1;
+            while (Mpad < c->M) Mpad <<= 1;
+            c->Mpad = Mpad;
+            for (int q = 0; q < 2; ++q) {
+                KL(c, launch_sort_keys(c->L[c->lmax].base[q], c->M, Mpad, c->keys, s));
+                launch_bitonic(c->keys, Mpad, s);
+                KL(c, launch_unpack_sorted(c->keys, c->M, c->sorted[q], c->mkey[q], s));
+                for (int l = 0; l <= c->lmax; ++l)
+                    KL(c, launch_bins(c->mkey[q], c->M, c->L[l].N * c->L[l].N, 2 * (c->lmax - l),
+                                      c->L[l].binStart[q], s));
+            }
+        }
+        for (int l = 0; l <= c->lmax; ++l) {
+            Level& lv = c->L[l];
+            CK(cudaMemsetAsync(lv.tileFlag, 0, 2 * (size_t)lv.ntiles, s));
+            if (c->M > 0)
+                for (int q = 0; q < 2; ++q)
+                    KL(c, launch_tile_flags(lv.base[q], c->M, lv.W, lv.N, lv.tx, lv.ty, lv.ntx, lv.tileFlag, s));
+            KL(c, launch_tile_finish(lv.tileFlag, lv.ntx, lv.nty, lv.tiles, lv.nTiles, s));
+        }
+        launch_adjacency(c->edges, c->E, c->M, c->deg, c->adjStart, c->adjNbr, c->adjEid, s);
+        std::vector<int> cnt(c->lmax + 1);
+        for (int l = 0; l <= c->lmax; ++l)
+            CK(cudaMemcpyAsync(&cnt[l], c->L[l].nTiles, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int l = 0; l <= c->lmax; ++l) {
+            Level& lv = c->L[l];
+            lv.hnTiles = cnt[l];
+            // warp per face when a face gathers from many markers on average
+            const double faces = (double)lv.hnTiles * lv.tx * lv.ty;
+            lv.spreadWarp = faces > 0 && (double)c->M * lv.W * lv.W > 16.0 * faces ? 1 : 0;
+        }
+        kcheck(c);
+        c->structDirty = false;
+        c->kappaDirty = true;
+    }
+    if (c->kappaDirty) {
+        KL(c, launch_adj_kappa<double>(c->adjEid, c->kappa, 2 * c->E, c->kap64, s));
+        KL(c, launch_adj_kappa<float>(c->adjEid, c->kappa, 2 * c->E, c->kap32, s));
+        for (int l = 0; l <= c->lmax; ++l) {
+            Level& lv = c->L[l];
+            const size_t n = (size_t)lv.N * lv.N;
+            for (int pi = 0; pi < 2; ++pi) {
+                const size_t e = pi == 0 ? 8 : 4;
+                CK(cudaMemsetAsync(lv.p[pi].fib, 0, e * 2 * n, s));
+            }
+            CK(cudaMemsetAsync(lv.p[0].ibd, 0, 8 * 4 * n, s));
+            if (c->haveIB && l > 0) {
+                KL(c, launch_patch_entries(c->edges, c->kappa, c->E, lv.base[0], lv.base[1],
+                                           (const double*)lv.p[0].w[0], (const double*)lv.p[0].w[1], c->M, lv.N,
+                                           lv.W, 1.0 / (lv.h * lv.h), (double*)lv.p[0].ibd, s));
+            }
+            KL(c, (launch_convert<double, float>((const double*)lv.p[0].ibd, (float*)lv.p[1].ibd, 4 * (int64_t)n,
+                                                 s)));
+        }
+        Level& l0 = c->L[0];
+        CK(cudaMemsetAsync(c->B0, 0, sizeof(double) * 2 * (size_t)c->n0 / 3 * c->n0 / 3, s));
+        if (c->haveIB)
+            KL(c, launch_dense_ib(c->edges, c->kappa, c->E, l0.base[0], l0.base[1], (const double*)l0.p[0].w[0],
+                                  (const double*)l0.p[0].w[1], l0.N, l0.W, 1.0 / (l0.h * l0.h), c->B0, s));
+        c->kappaDirty = false;
+        c->fluidDirty = true;
+    }
+    // coarsest pseudo-inverse (depends on rho, mu, dt and kappa)
+    {
+        const int n = c->n0;
+        KL(c, launch_assemble_L0(c->L[0].N, c->rho, c->mu, c->dt, c->B0, c->Aug, s));
+        KL(c, launch_gauss_jordan(c->Aug, n, c->info, s));
+        KL(c, launch_extract_pinv(c->Aug, n, c->L[0].N, c->rho, c->Pinv, s));
+        int info = 0;
+        CK(cudaMemcpyAsync(&info, c->info, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (info != 0) throw SibError(SIB_ERR_ARG, "coarsest operator is singular beyond its gauge kernel");
+        c->fluidDirty = false;
+    }
+    if (c->opts.smoother == SIB_SMOOTHER_SC) {
+        alloc_sc_bufs(c);
+        for (int l = 1; l <= c->lmax; ++l) {
+            Level& lv = c->L[l];
+            if (c->lamOverride) {
+                lv.lamA = c->lamA_ov[l];
+                lv.lamM = c->lamM_ov[l];
+            } else {
+                lv.lamA = power_A(c, l, s);
+                lv.lamM = power_M(c, l, s);
+            }
+        }
+    }
+    alloc_krylov(c);
+    CK(cudaEventRecord(c->ev1, s));
+    CK(cudaStreamSynchronize(s));
+    kcheck(c);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    c->setup_ms = ms;
+    c->setupDone = true;
+}
+
+void require_setup(sib_ctx* c) {
+    if (!c->setupDone || c->structDirty || c->kappaDirty || c->fluidDirty)
+        throw SibError(SIB_ERR_STATE, "sib_setup must be called after the last change of fluid, structure or kappa");
+}
+
+// ---- flexible GMRES (right-preconditioned, CGS2, Givens) ---------------------------------------
+void dot(sib_ctx* c, const double* x, const double* y, int64_t n, double* dst, cudaStream_t s) {
+    KL(c, launch_dot_partials(x, y, n, c->part, NBLK, s));
+    KL(c, launch_reduce_partials(c->part, 1, NBLK, dst, s));
+}
+
+void project(sib_ctx* c, double* x, cudaStream_t s) {
+    const int mask = c->rho == 0.0 ? 7 : 4;
+    KL(c, launch_block_means(x, c->N, 3, c->part, NBLK, s));
+    KL(c, launch_subtract_means(x, c->N, c->part, NBLK, mask, s));
+}
+
+// z = M^{-1} v (V-cycle in the configured precision, casts fused into the copies)
+void precondition(sib_ctx* c, const double* v, double* z, cudaStream_t s) {
+    const int64_t n = n3f(c);
+    Level& lv = c->L[c->lmax];
+    if (c->opts.vcycle_fp32) {
+        KL(c, (launch_convert<double, float>(v, (float*)lv.p[1].b, n, s)));
+        float* out = vcycle<float>(c, s);
+        KL(c, (launch_convert<float, double>(out, z, n, s)));
+    } else {
+        KL(c, (launch_convert<double, double>(v, (double*)lv.p[0].b, n, s)));
+        double* out = vcycle<double>(c, s);
+        KL(c, (launch_convert<double, double>(out, z, n, s)));
+    }
+}
+
+void matvec(sib_ctx* c, const double* x, double* y, cudaStream_t s) { apply_operator<double>(c, c->lmax, x, nullptr, y, s); }
+
+int fgmres(sib_ctx* c, const double* b, double* x, sib_stats* st, cudaStream_t s) {
+    const int64_t n = n3f(c);
+    const int max_it = c->opts.max_it;
+    const int mres = c->mcap;
+    double* hb = c->hbuf;
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    dot(c, b, b, n, c->scal + 256, s);
+    CK(cudaMemcpyAsync(hb, c->scal + 256, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double bnorm = std::sqrt(hb[0]);
+    if (!std::isfinite(bnorm)) throw SibError(SIB_ERR_NONFINITE, "right-hand side is not finite");
+    std::vector<double> hist;
+    hist.push_back(bnorm);
+    int its = 0;
+    bool converged = bnorm == 0.0;
+    double est = bnorm;
+    std::vector<double> H((size_t)(mres + 1) * mres), cs(mres), sn(mres), g(mres + 1), y(mres);
+    while (!converged && its < max_it) {
+        double* r = c->V;   // V_0
+        double beta;
+        if (its == 0) {
+            KL(c, (launch_convert<double, double>(b, r, n, s)));
+            beta = bnorm;
+        } else {
+            matvec(c, x, c->res, s);
+            KL(c, launch_axpby<double>(1.0, b, -1.0, c->res, r, n, s));
+            dot(c, r, r, n, c->scal + 256, s);
+            CK(cudaMemcpyAsync(hb, c->scal + 256, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            beta = std::sqrt(hb[0]);
+        }
+        if (beta == 0.0) {
+            converged = true;
+            break;
+        }
+        // scale V0 by 1/beta (scal[258] = beta^2, staged through pinned memory)
+        hb[450] = beta * beta;
+        CK(cudaMemcpyAsync(c->scal + 258, hb + 450, sizeof(double), cudaMemcpyHostToDevice, s));
+        KL(c, launch_scale(r, c->scal, 258, n, s));
+        const int m = std::min(mres, max_it - its);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int k = 0;
+        for (int j = 0; j < m; ++j) {
+            double* vj = c->V + (int64_t)j * n;
+            double* zj = c->Z + (int64_t)j * n;
+            double* w = c->V + (int64_t)(j + 1) * n;
+            precondition(c, vj, zj, s);
+            matvec(c, zj, w, s);
+            KL(c, launch_multidot(c->V, n, j + 1, w, n, c->part, NBLK, s));
+            KL(c, launch_reduce_partials(c->part, j + 1, NBLK, c->scal, s));
+            KL(c, launch_multi_axpy(c->V, n, j + 1, c->scal, -1.0, w, n, s));
+            KL(c, launch_multidot(c->V, n, j + 1, w, n, c->part, NBLK, s));
+            KL(c, launch_reduce_partials(c->part, j + 1, NBLK, c->scal + 128, s));
+            KL(c, launch_multi_axpy(c->V, n, j + 1, c->scal + 128, -1.0, w, n, s));
+            dot(c, w, w, n, c->scal + 256, s);
+            KL(c, launch_scale(w, c->scal, 256, n, s));
+            CK(cudaMemcpyAsync(hb, c->scal, sizeof(double) * 257, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            double* Hj = &H[(size_t)j * (mres + 1)];   // column j
+            for (int i = 0; i <= j; ++i) Hj[i] = hb[i] + hb[128 + i];
+            const double hn = std::sqrt(hb[256]);
+            Hj[j + 1] = hn;
+            for (int i = 0; i < j; ++i) {
+                const double a = Hj[i], bq = Hj[i + 1];
+                Hj[i] = cs[i] * a + sn[i] * bq;
+                Hj[i + 1] = -sn[i] * a + cs[i] * bq;
+            }
+            const double d = std::hypot(Hj[j], Hj[j + 1]);
+            cs[j] = Hj[j] / d;
+            sn[j] = Hj[j + 1] / d;
+            Hj[j] = d;
+            Hj[j + 1] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            ++its;
+            k = j + 1;
+            est = std::fabs(g[j + 1]);
+            hist.push_back(est);
+            if (!std::isfinite(est) || !std::isfinite(d)) throw SibError(SIB_ERR_NONFINITE, "non-finite value in FGMRES");
+            if (est <= c->opts.rtol * bnorm || hn == 0.0) {
+                converged = true;
+                break;
+            }
+            if (its >= max_it) break;
+        }
+        for (int i = k - 1; i >= 0; --i) {
+            double acc = g[i];
+            for (int q = i + 1; q < k; ++q) acc -= H[(size_t)q * (mres + 1) + i] * y[q];
+            y[i] = acc / H[(size_t)i * (mres + 1) + i];
+        }
+        for (int i = 0; i < k; ++i) hb[300 + i] = y[i];
+        CK(cudaMemcpyAsync(c->scal + 384, hb + 300, sizeof(double) * k, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));   // hb is reused by the next cycle's reads
+        KL(c, launch_multi_axpy(c->Z, n, k, c->scal + 384, 1.0, x, n, s));
+    }
+    project(c, x, s);
+    // true residual of the gauge-fixed solution
+    matvec(c, x, c->res, s);
+    KL(c, launch_axpby<double>(1.0, b, -1.0, c->res, c->res, n, s));
+    dot(c, c->res, c->res, n, c->scal + 256, s);
+    CK(cudaMemcpyAsync(hb, c->scal + 256, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double rt = std::sqrt(hb[0]);
+    if (st) {
+        st->iterations = its;
+        st->converged = converged ? 1 : 0;
+        st->bnorm = bnorm;
+        st->rel_residual = bnorm > 0 ? rt / bnorm : 0.0;
+        st->rel_residual_est = bnorm > 0 ? est / bnorm : 0.0;
+        const size_t nh = std::min<size_t>(hist.size(), 101);
+        for (size_t i = 0; i < nh; ++i) st->history[i] = hist[i];
+    }
+    return converged ? SIB_OK : SIB_ERR_NOT_CONVERGED;
+}
+
+// b = g (+ S K X^n), projected
+void build_rhs(sib_ctx* c, const double* g, bool addSKX, cudaStream_t s) {
+    const int64_t n = n3f(c);
+    const int64_t nv = 2LL * c->N * c->N;
+    KL(c, (launch_convert<double, double>(g, c->rhs, n, s)));
+    if (addSKX && c->haveIB) {
+        Level& lv = c->L[c->lmax];
+        IBK<double> k = ibk<double>(c, c->lmax);
+        double* F = (double*)c->F[0];
+        KL(c, launch_spring<double>(c->adjStart, c->adjNbr, c->kap64, c->M, c->Xc, F, s));
+        KL(c, launch_spread<double>(k, F, (double*)lv.p[0].fib, lv.tiles, lv.nTiles, lv.hnTiles, lv.tx, lv.ty, lv.ntx,
+                                    lv.spreadWarp, s));
+        KL(c, launch_axpby<double>(1.0, c->rhs, 1.0, (const double*)lv.p[0].fib, c->rhs, nv, s));
+    }
+    project(c, c->rhs, s);
+}
+
+int solve_impl(sib_ctx* c, const double* g, double* w, sib_stats* st, cudaStream_t s, bool addSKX) {
+    require_setup(c);
+    CK(cudaMemsetAsync(c->flag, 0, sizeof(int), s));
+    KL(c, launch_check_finite(g, n3f(c), c->flag, s));
+    int fl = 0;
+    CK(cudaMemcpyAsync(&fl, c->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (fl) throw SibError(SIB_ERR_NONFINITE, "right-hand side contains a non-finite value");
+    CK(cudaEventRecord(c->ev0, s));
+    build_rhs(c, g, addSKX, s);
+    const int rc = fgmres(c, c->rhs, w, st, s);
+    CK(cudaEventRecord(c->ev1, s));
+    CK(cudaEventSynchronize(c->ev1));
+    kcheck(c);
+    if (st) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        st->solve_ms = ms;
+        st->setup_ms = c->setup_ms;
+    }
+    return rc;
+}
+
+bool valid_prec(int p) { return p == SIB_PREC_FP64 || p == SIB_PREC_FP32; }
+void check_level(sib_ctx* c, int l, int lo) {
+    if (l < lo || l > c->lmax) throw SibError(SIB_ERR_ARG, "level out of range");
+}
+
+template <typename T>
+void smooth_impl(sib_ctx* c, int l, T* x, const T* b, int sweeps, cudaStream_t s) {
+    Level& lv = c->L[l];
+    const int pi = Prec<T>::id;
+    const int64_t n3 = 3LL * lv.N * lv.N;
+    T* xa = (T*)lv.p[pi].x;
+    T* xb = (T*)lv.p[pi].xt;
+    CK(cudaMemcpyAsync(xa, x, sizeof(T) * n3, cudaMemcpyDeviceToDevice, s));
+    for (int k = 0; k < sweeps; ++k) {
+        sweep<T>(c, l, xa, b, xb, s);
+        std::swap(xa, xb);
+    }
+    CK(cudaMemcpyAsync(x, xa, sizeof(T) * n3, cudaMemcpyDeviceToDevice, s));
+}
+
+#define API_BEGIN(c)                       \
+    if (!(c)) return SIB_ERR_ARG;          \
+    try {                                  \
+        (c)->err.clear();
+
+#define API_END(c)                                  \
+    }                                               \
+    catch (const SibError& e) {                     \
+        (c)->err = e.what();                        \
+        return e.code;                              \
+    }                                               \
+    catch (const std::exception& e) {               \
+        (c)->err = e.what();                        \
+        return SIB_ERR_CUDA;                        \
+    }
+
+}  // namespace
+
+// ============================================================================================
+extern "C" {
+
+void sib_default_opts(sib_opts* o) {
+    if (!o) return;
+    o->smoother = SIB_SMOOTHER_VANKA;
+    o->nu1 = 2;
+    o->nu2 = 2;
+    o->omega = -1.0;
+    o->cheb_iters = 2;
+    o->cheb_lo = 0.1;
+    o->cheb_hi = 1.1;
+    o->power_iters = 10;
+    o->vcycle_fp32 = 1;
+    o->rtol = 1e-8;
+    o->max_it = 100;
+    o->restart = 100;
+    o->add_SKXn = 1;
+    o->use_graphs = 1;
+}
+
+static void resolve_opts(sib_opts* o) {
+    if (o->omega < 0) o->omega = o->smoother == SIB_SMOOTHER_SC ? 1.0 : 0.8;
+}
+
+int sib_create(sib_ctx** out, int N, int n_min) {
+    if (!out) return SIB_ERR_ARG;
+    *out = nullptr;
+    if (n_min < 4 || n_min > 16 || (n_min & (n_min - 1)) || N < n_min || N > MAX_N || (N & (N - 1)))
+        return SIB_ERR_ARG;
+    sib_ctx* c = new (std::nothrow) sib_ctx();
+    if (!c) return SIB_ERR_ALLOC;
+    try {
+        c->N = N;
+        c->n_min = n_min;
+        int lmax = 0;
+        while ((n_min << lmax) < N) ++lmax;
+        c->lmax = lmax;
+        sib_default_opts(&c->opts);
+        resolve_opts(&c->opts);
+        c->L.resize(lmax + 1);
+        for (int l = 0; l <= lmax; ++l) {
+            Level& lv = c->L[l];
+            lv.N = n_min << l;
+            lv.h = 1.0 / lv.N;
+            lv.tx = lv.N < TX ? lv.N : TX;
+            lv.ty = lv.N < TY ? lv.N : TY;
+            lv.ntx = lv.N / lv.tx;
+            lv.nty = lv.N / lv.ty;
+            lv.ntiles = lv.ntx * lv.nty;
+            lv.W = l == lmax ? 4 : 3;
+        }
+        CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+        CK(cudaEventCreate(&c->ev0));
+        CK(cudaEventCreate(&c->ev1));
+        alloc_level_bufs(c);
+        const int N0 = n_min;
+        c->n0 = 3 * N0 * N0;
+        c->B0 = (double*)dalloc(c, sizeof(double) * 2 * (size_t)N0 * N0 * N0 * N0);
+        c->Aug = (double*)dalloc(c, sizeof(double) * 2 * (size_t)c->n0 * c->n0);
+        c->Pinv = (double*)dalloc(c, sizeof(double) * (size_t)c->n0 * c->n0);
+        c->info = (int*)dalloc(c, sizeof(int));
+        c->flag = (int*)dalloc(c, sizeof(int));
+        const size_t n3 = 3 * (size_t)N * N;
+        c->rhs = (double*)dalloc(c, sizeof(double) * n3);
+        c->sol = (double*)dalloc(c, sizeof(double) * n3);
+        c->res = (double*)dalloc(c, sizeof(double) * n3);
+        c->part = (double*)dalloc(c, sizeof(double) * NBLK * 128);
+        c->scal = (double*)dalloc(c, sizeof(double) * 512);
+        CK(cudaMallocHost(&c->hbuf, sizeof(double) * 512));
+        alloc_markers(c);
+    } catch (const SibError& e) {
+        std::fprintf(stderr, "sib_create: %s\n", e.what());
+        sib_destroy(c);
+        return e.code;
+    }
+    *out = c;
+    return SIB_OK;
+}
+
+void sib_destroy(sib_ctx* c) {
+    if (!c) return;
+    invalidate_graphs(c);
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    if (c->hbuf) cudaFreeHost(c->hbuf);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+}
+
+const char* sib_last_error(const sib_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int sib_set_fluid(sib_ctx* c, double rho, double mu, double dt) {
+    API_BEGIN(c)
+    if (!(rho >= 0.0) || !(mu > 0.0) || !(dt > 0.0) || !std::isfinite(rho) || !std::isfinite(mu) || !std::isfinite(dt))
+        throw SibError(SIB_ERR_ARG, "need rho >= 0, mu > 0, dt > 0 (finite)");
+    c->rho = rho;
+    c->mu = mu;
+    c->dt = dt;
+    c->fluidDirty = true;
+    c->kappaDirty = true;   // SC eigen estimates and coarsest operator depend on the fluid too
+    invalidate_graphs(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_set_structure(sib_ctx* c, int M, const double* X, int E, const int32_t* edges, const double* kappa,
+                      void* stream) {
+    API_BEGIN(c)
+    if (M < 0 || E < 0 || (M > 0 && !X) || (E > 0 && (!edges || !kappa)) || (E > 0 && M == 0))
+        throw SibError(SIB_ERR_ARG, "invalid structure sizes or null pointers");
+    cudaStream_t s = S(stream);
+    // validate on the host (set-up time): indices in range, finite positions, kappa >= 0
+    std::vector<double> hX(2 * (size_t)M);
+    std::vector<int> hE(2 * (size_t)E);
+    std::vector<double> hK(E);
+    if (M) CK(cudaMemcpyAsync(hX.data(), X, sizeof(double) * 2 * M, cudaMemcpyDeviceToHost, s));
+    if (E) {
+        CK(cudaMemcpyAsync(hE.data(), edges, sizeof(int) * 2 * E, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hK.data(), kappa, sizeof(double) * E, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    for (double v : hX) {
+        if (!std::isfinite(v)) throw SibError(SIB_ERR_NONFINITE, "marker positions must be finite");
+        if (std::fabs(v) > 1e3) throw SibError(SIB_ERR_ARG, "marker positions must lie within 1000 periods");
+    }
+    for (int v : hE)
+        if (v < 0 || v >= M) throw SibError(SIB_ERR_ARG, "edge index out of range");
+    for (double v : hK)
+        if (!std::isfinite(v) || v < 0.0) throw SibError(SIB_ERR_ARG, "kappa must be finite and >= 0");
+    c->M = M;
+    c->E = E;
+    alloc_markers(c);
+    if (M) CK(cudaMemcpyAsync(c->X, X, sizeof(double) * 2 * M, cudaMemcpyDeviceToDevice, s));
+    if (E) {
+        CK(cudaMemcpyAsync(c->edges, edges, sizeof(int) * 2 * E, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(c->kappa, kappa, sizeof(double) * E, cudaMemcpyDeviceToDevice, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    c->structDirty = true;
+    c->kappaDirty = true;
+    c->setupDone = false;
+    invalidate_graphs(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_set_stiffness(sib_ctx* c, const double* kappa, void* stream) {
+    API_BEGIN(c)
+    if (c->E > 0 && !kappa) throw SibError(SIB_ERR_ARG, "null kappa");
+    cudaStream_t s = S(stream);
+    std::vector<double> hK(c->E);
+    if (c->E) {
+        CK(cudaMemcpyAsync(hK.data(), kappa, sizeof(double) * c->E, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    for (double v : hK)
+        if (!std::isfinite(v) || v < 0.0) throw SibError(SIB_ERR_ARG, "kappa must be finite and >= 0");
+    if (c->E) CK(cudaMemcpyAsync(c->kappa, kappa, sizeof(double) * c->E, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    c->kappaDirty = true;
+    invalidate_graphs(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_set_options(sib_ctx* c, const sib_opts* o) {
+    API_BEGIN(c)
+    if (!o) throw SibError(SIB_ERR_ARG, "null options");
+    sib_opts n = *o;
+    if ((n.smoother != SIB_SMOOTHER_VANKA && n.smoother != SIB_SMOOTHER_SC) || n.nu1 < 0 || n.nu2 < 0 ||
+        n.nu1 + n.nu2 > 64 || n.cheb_iters < 1 || n.cheb_iters > 16 || !(n.cheb_lo > 0) || !(n.cheb_hi > n.cheb_lo) ||
+        n.power_iters < 1 || n.power_iters > 1000 || !(n.rtol >= 0) || n.max_it < 1 || n.max_it > 100000 ||
+        n.restart < 1 || n.restart > 100)
+        throw SibError(SIB_ERR_ARG, "option out of range");
+    resolve_opts(&n);
+    const bool smootherChanged = n.smoother != c->opts.smoother;
+    c->opts = n;
+    if (smootherChanged && n.smoother == SIB_SMOOTHER_SC) c->fluidDirty = true;   // needs eigen estimates
+    invalidate_graphs(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_set_eigen_estimates(sib_ctx* c, const double* lamA, const double* lamM) {
+    API_BEGIN(c)
+    if (!lamA || !lamM) {
+        c->lamOverride = false;
+    } else {
+        c->lamOverride = true;
+        c->lamA_ov.assign(lamA, lamA + c->lmax + 1);
+        c->lamM_ov.assign(lamM, lamM + c->lmax + 1);
+        for (int l = 1; l <= c->lmax; ++l)
+            if (!(c->lamA_ov[l] > 0) || !(c->lamM_ov[l] > 0)) throw SibError(SIB_ERR_ARG, "estimates must be > 0");
+    }
+    c->fluidDirty = true;
+    invalidate_graphs(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_get_eigen_estimates(const sib_ctx* c, double* lamA, double* lamM) {
+    if (!c || !lamA || !lamM) return SIB_ERR_ARG;
+    for (int l = 0; l <= c->lmax; ++l) {
+        lamA[l] = c->L[l].lamA;
+        lamM[l] = c->L[l].lamM;
+    }
+    return SIB_OK;
+}
+
+int sib_setup(sib_ctx* c, void* stream) {
+    API_BEGIN(c)
+    setup(c, S(stream));
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_solve(sib_ctx* c, const double* g, double* w, sib_stats* st, void* stream) {
+    API_BEGIN(c)
+    if (!g || !w) throw SibError(SIB_ERR_ARG, "null pointer");
+    return solve_impl(c, g, w, st, S(stream), c->opts.add_SKXn != 0);
+    API_END(c)
+}
+
+int sib_solve_rhs(sib_ctx* c, const double* rhs, double* w, sib_stats* st, void* stream) {
+    API_BEGIN(c)
+    if (!rhs || !w) throw SibError(SIB_ERR_ARG, "null pointer");
+    return solve_impl(c, rhs, w, st, S(stream), false);
+    API_END(c)
+}
+
+int sib_solve_host(sib_ctx* c, const double* g_host, double* w_host, sib_stats* st, void* stream) {
+    API_BEGIN(c)
+    if (!g_host || !w_host) throw SibError(SIB_ERR_ARG, "null pointer");
+    cudaStream_t s = S(stream);
+    const size_t bytes = sizeof(double) * n3f(c);
+    CK(cudaMemcpyAsync(c->sol, g_host, bytes, cudaMemcpyHostToDevice, s));
+    // solve_impl copies g into its right-hand side before it writes w, so sol can serve as both
+    const int rc = solve_impl(c, c->sol, c->sol, st, s, c->opts.add_SKXn != 0);
+    CK(cudaMemcpyAsync(w_host, c->sol, bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return rc;
+    API_END(c)
+}
+
+int sib_grad(sib_ctx* c, const double* w, const double* lam, double* dkappa, double* dX, void* stream) {
+    API_BEGIN(c)
+    require_setup(c);
+    if (!w || !lam || (c->E && !dkappa) || (c->M && !dX)) throw SibError(SIB_ERR_ARG, "null pointer");
+    cudaStream_t s = S(stream);
+    if (!c->haveIB) {
+        if (c->E) CK(cudaMemsetAsync(dkappa, 0, sizeof(double) * c->E, s));
+        if (c->M) CK(cudaMemsetAsync(dX, 0, sizeof(double) * 2 * c->M, s));
+        return SIB_OK;
+    }
+    const int M = c->M;
+    double* Lam = c->gradTmp;
+    double* Y = c->gradTmp + 2 * M;
+    double* KY = c->gradTmp + 4 * M;
+    double* KLm = c->gradTmp + 6 * M;
+    IBK<double> k = ibk<double>(c, c->lmax);
+    const double a = c->opts.add_SKXn ? 1.0 : 0.0;
+    KL(c, launch_interp<double>(k, w, Y, s));                     // U = J u
+    KL(c, launch_axpby<double>(a, c->Xc, c->dt, Y, Y, 2LL * M, s));   // Y = a X + dt U
+    KL(c, launch_interp<double>(k, lam, Lam, s));                 // J lam_u
+    const double ih2 = (double)c->N * c->N;
+    KL(c, launch_axpby<double>(ih2, Lam, 0.0, nullptr, Lam, 2LL * M, s));
+    KL(c, launch_spring<double>(c->adjStart, c->adjNbr, c->kap64, M, Y, KY, s));
+    KL(c, launch_spring<double>(c->adjStart, c->adjNbr, c->kap64, M, Lam, KLm, s));
+    KL(c, launch_grad_kappa(c->edges, c->E, M, Lam, Y, dkappa, s));
+    KL(c, launch_grad_X(c->X, M, c->N, w, lam, KY, KLm, c->dt, a, dX, s));
+    kcheck(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_num_levels(const sib_ctx* c) { return c ? c->lmax + 1 : SIB_ERR_ARG; }
+int sib_level_size(const sib_ctx* c, int l) { return (c && l >= 0 && l <= c->lmax) ? c->L[l].N : SIB_ERR_ARG; }
+
+int sib_apply_operator(sib_ctx* c, int l, int prec, const void* x, void* y, void* stream) {
+    API_BEGIN(c)
+    require_setup(c);
+    check_level(c, l, 0);
+    if (!valid_prec(prec) || !x || !y) throw SibError(SIB_ERR_ARG, "bad precision or null pointer");
+    if (prec == SIB_PREC_FP64)
+        apply_operator<double>(c, l, (const double*)x, nullptr, (double*)y, S(stream));
+    else
+        apply_operator<float>(c, l, (const float*)x, nullptr, (float*)y, S(stream));
+    kcheck(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_apply_ib(sib_ctx* c, int l, int prec, const void* u, void* f, void* stream) {
+    API_BEGIN(c)
+    require_setup(c);
+    check_level(c, l, 0);
+    if (!valid_prec(prec) || !u || !f) throw SibError(SIB_ERR_ARG, "bad precision or null pointer");
+    cudaStream_t s = S(stream);
+    const int64_t nv = 2LL * c->L[l].N * c->L[l].N;
+    if (prec == SIB_PREC_FP64) {
+        ib_apply<double>(c, l, (const double*)u, s);
+        CK(cudaMemcpyAsync(f, c->L[l].p[0].fib, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+    } else {
+        ib_apply<float>(c, l, (const float*)u, s);
+        CK(cudaMemcpyAsync(f, c->L[l].p[1].fib, sizeof(float) * nv, cudaMemcpyDeviceToDevice, s));
+    }
+    kcheck(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_smooth(sib_ctx* c, int l, int prec, void* x, const void* b, int sweeps, void* stream) {
+    API_BEGIN(c)
+    require_setup(c);
+    check_level(c, l, 1);
+    if (!valid_prec(prec) || !x || !b || sweeps < 0) throw SibError(SIB_ERR_ARG, "bad argument");
+    if (prec == SIB_PREC_FP64)
+        smooth_impl<double>(c, l, (double*)x, (const double*)b, sweeps, S(stream));
+    else
+        smooth_impl<float>(c, l, (float*)x, (const float*)b, sweeps, S(stream));
+    kcheck(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_residual_restrict(sib_ctx* c, int l, int prec, const void* x, const void* b, void* rc, void* stream) {
+    API_BEGIN(c)
+    require_setup(c);
+    check_level(c, l, 1);
+    if (!valid_prec(prec) || !x || !b || !rc) throw SibError(SIB_ERR_ARG, "bad argument");
+    cudaStream_t s = S(stream);
+    if (prec == SIB_PREC_FP64) {
+        apply_operator<double>(c, l, (const double*)x, (const double*)b, (double*)c->L[l].p[0].r, s);
+        KL(c, launch_restrict<double>(c->L[l - 1].N, (const double*)c->L[l].p[0].r, (double*)rc, s));
+    } else {
+        apply_operator<float>(c, l, (const float*)x, (const float*)b, (float*)c->L[l].p[1].r, s);
+        KL(c, launch_restrict<float>(c->L[l - 1].N, (const float*)c->L[l].p[1].r, (float*)rc, s));
+    }
+    kcheck(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_prolong_add(sib_ctx* c, int l, int prec, const void* ec, void* xf, void* stream) {
+    API_BEGIN(c)
+    check_level(c, l, 1);
+    if (!valid_prec(prec) || !ec || !xf) throw SibError(SIB_ERR_ARG, "bad argument");
+    if (prec == SIB_PREC_FP64)
+        KL(c, launch_prolong_add<double>(c->L[l - 1].N, (const double*)ec, (double*)xf, S(stream)));
+    else
+        KL(c, launch_prolong_add<float>(c->L[l - 1].N, (const float*)ec, (float*)xf, S(stream)));
+    kcheck(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_coarse_solve(sib_ctx* c, int prec, const void* b, void* x, void* stream) {
+    API_BEGIN(c)
+    require_setup(c);
+    if (!valid_prec(prec) || !b || !x) throw SibError(SIB_ERR_ARG, "bad argument");
+    if (prec == SIB_PREC_FP64)
+        KL(c, launch_coarse_apply<double>(c->Pinv, c->n0, (const double*)b, (double*)x, S(stream)));
+    else
+        KL(c, launch_coarse_apply<float>(c->Pinv, c->n0, (const float*)b, (float*)x, S(stream)));
+    kcheck(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_vcycle(sib_ctx* c, int prec, const void* b, void* z, void* stream) {
+    API_BEGIN(c)
+    require_setup(c);
+    if (!valid_prec(prec) || !b || !z) throw SibError(SIB_ERR_ARG, "bad argument");
+    cudaStream_t s = S(stream);
+    const int64_t n = n3f(c);
+    Level& lv = c->L[c->lmax];
+    if (prec == SIB_PREC_FP64) {
+        CK(cudaMemcpyAsync(lv.p[0].b, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        double* out = vcycle<double>(c, s);
+        CK(cudaMemcpyAsync(z, out, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    } else {
+        CK(cudaMemcpyAsync(lv.p[1].b, b, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+        float* out = vcycle<float>(c, s);
+        CK(cudaMemcpyAsync(z, out, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    kcheck(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_interp(sib_ctx* c, const double* u, double* U, void* stream) {
+    API_BEGIN(c)
+    require_setup(c);
+    if (!u || (c->M && !U)) throw SibError(SIB_ERR_ARG, "null pointer");
+    if (c->M == 0) return SIB_OK;
+    cudaStream_t s = S(stream);
+    IBK<double> k = ibk<double>(c, c->lmax);
+    KL(c, launch_interp<double>(k, u, (double*)c->U[0], s));
+    KL(c, launch_interleave((const double*)c->U[0], c->M, U, s));
+    kcheck(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_spread(sib_ctx* c, const double* F, double* f, void* stream) {
+    API_BEGIN(c)
+    require_setup(c);
+    if ((c->M && !F) || !f) throw SibError(SIB_ERR_ARG, "null pointer");
+    cudaStream_t s = S(stream);
+    const int64_t nv = 2LL * c->N * c->N;
+    Level& lv = c->L[c->lmax];
+    if (c->M == 0) {
+        CK(cudaMemsetAsync(f, 0, sizeof(double) * nv, s));
+        return SIB_OK;
+    }
+    IBK<double> k = ibk<double>(c, c->lmax);
+    KL(c, launch_deinterleave(F, c->M, (double*)c->F[0], s));
+    CK(cudaMemsetAsync(lv.p[0].fib, 0, sizeof(double) * nv, s));
+    KL(c, launch_spread<double>(k, (const double*)c->F[0], (double*)lv.p[0].fib, lv.tiles, lv.nTiles, lv.hnTiles,
+                                lv.tx, lv.ty, lv.ntx, lv.spreadWarp, s));
+    CK(cudaMemcpyAsync(f, lv.p[0].fib, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+    kcheck(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int64_t sib_launch_count(const sib_ctx* c) { return c ? c->launches : 0; }
+int64_t sib_device_bytes(const sib_ctx* c) { return c ? c->bytes : 0; }
+
+}  // extern "C"
