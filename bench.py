@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""Benchmark of the Stokes-IB solve: FP64 flexible GMRES preconditioned by an FP32 multigrid
+V-cycle, to a 1e-8 relative residual, on the thick-disk workload.
+
+Workload (one step): periodic 128 x 128 MAC grid, Stokes flow (rho = 0, mu = 1, dt = 1e-2), an
+elastic disk of radius 0.25 made of concentric marker rings at half-cell spacing (13,070 markers,
+26,138 zero-rest-length springs), seeded N(0,1) forcing; the stiffness is swept over
+kappa in {1e0, 1e2, 1e4, 1e6} for both the additive-Vanka and the Schur-complement smoother.
+A step is those 8 solves, each with its set-up (stiffness, Galerkin coarse operators, coarsest
+pseudo-inverse, eigenvalue estimates) and its FGMRES solve (cap 100 iterations).
+
+Output: one JSON line (rank 0).  `value` is device time per solve in milliseconds over the
+whole job (all ranks; replicas), `e2e` the same through the host-buffer C call.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Stokes-IB solve time to 1e-8 rel resid; V-cycle Mdof/s & %HBM; FP32 vs FP64 MG"
+KAPPAS = [1e0, 1e2, 1e4, 1e6]
+SMOOTHERS = ["vanka", "sc"]
+N_GRID = 128
+WORKLOAD = "disk_stokes_N128_kappa_sweep"
+LARGE_N = 2048
+L2_BYTES = 129 * 2 ** 20
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1612_02208_gb300", "csrc", "kernels_grid.cu")
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["native", "reference"], default="native")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-large", action="store_true", help="skip the large-grid V-cycle roofline")
+    p.add_argument("--kappas", default=",".join(str(k) for k in KAPPAS),
+                   help="comma-separated stiffness values of the sweep (default: the full workload)")
+    p.add_argument("--smoothers", default=",".join(SMOOTHERS), help="comma-separated subset of vanka,sc")
+    a = p.parse_args(argv)
+    KAPPAS[:] = [float(x) for x in a.kappas.split(",")]
+    SMOOTHERS[:] = [x for x in a.smoothers.split(",")]
+    return a
+
+
+# ------------------------------------------------------------------------------------ ranks
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    rank, world, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend, rank=rank, world_size=world)
+    return rank, world
+
+
+def dist_barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def dist_max(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_sum(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_ms_per_solve(max_time_ms: float, solves_per_rank: int, world: int) -> float:
+    """Whole-job time per solve: the slowest rank's time over the solves all ranks completed."""
+    return max_time_ms / float(solves_per_rank * world)
+
+
+# ------------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.index = index
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            self.path = tempfile.mktemp(suffix=".csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for k, name in enumerate(names):
+                if len(r) > 3 + k and r[3 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------ peaks / traffic
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_hash():
+    return hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()[:12]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    h = source_hash()
+    for line in open(TRAFFIC_FILE):
+        f = line.split()
+        if len(f) >= 4 and not line.startswith("#") and f[0] == kernel and f[1] == workload and f[3] == h:
+            return float(f[2])
+    return None
+
+
+# ------------------------------------------------------------------------------------ native arm
+def make_problem():
+    from paper_1612_02208_gb300 import inputs
+    return inputs.disk_stokes(N_GRID, kappa=1.0, seed=1)
+
+
+def native_step(S, g, w, kap_dev, sib, records=None, vcycle_fp32=1):
+    for sm in SMOOTHERS:
+        S.set_options(smoother=sib.SMOOTHER_SC if sm == "sc" else sib.SMOOTHER_VANKA, vcycle_fp32=vcycle_fp32,
+                      omega=-1.0)
+        for kap in KAPPAS:
+            S.set_stiffness(kap_dev[kap])
+            S.setup()
+            S.solve(g, w, allow_unconverged=True)
+            if records is not None:
+                d = S.stats.as_dict()
+                records.append(dict(smoother=sm, kappa=kap, iterations=d["iterations"], converged=d["converged"],
+                                    rel_residual=d["rel_residual"], setup_ms=round(d["setup_ms"], 4),
+                                    solve_ms=round(d["solve_ms"], 4)))
+
+
+def e2e_step(S, g_host, w_host, kap_host, kap_dev, sib, torch):
+    """Through the host-buffer call: stiffness uploaded from pinned memory, g in, w out."""
+    for sm in SMOOTHERS:
+        S.set_options(smoother=sib.SMOOTHER_SC if sm == "sc" else sib.SMOOTHER_VANKA, vcycle_fp32=1, omega=-1.0)
+        for kap in KAPPAS:
+            kap_dev[kap].copy_(kap_host[kap], non_blocking=True)
+            S.set_stiffness(kap_dev[kap])
+            S.setup()
+            S.solve_host(g_host, w_host, allow_unconverged=True)
+
+
+def large_vcycle(sib, torch, reps=20):
+    """V-cycle throughput and the Vanka kernel's roofline on a grid whose working set exceeds L2:
+    2048^2, rho = 1, mu = 1e-2, dt = 1e-3, thin ellipse, kappa = 1e4, FP32 V-cycle."""
+    from paper_1612_02208_gb300 import inputs
+    prob = inputs.thin_ellipse_re(LARGE_N, kappa=1e4, seed=2)
+    S = sib.Solver(LARGE_N)
+    S.set_fluid(prob.rho, prob.mu, prob.dt)
+    st = prob.structure
+    dev = torch.device("cuda")
+    S.set_structure(torch.as_tensor(st.X, device=dev), torch.as_tensor(st.edges, device=dev),
+                    torch.as_tensor(st.kappa, device=dev))
+    S.set_options(restart=1, max_it=1)
+    S.setup()
+    n3 = 3 * LARGE_N * LARGE_N
+    b = torch.randn(n3, device=dev, dtype=torch.float32)
+    z = torch.empty_like(b)
+    for _ in range(3):
+        S.vcycle(b, z)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        S.vcycle(b, z)
+    e1.record()
+    torch.cuda.synchronize()
+    t_v = e0.elapsed_time(e1) / reps
+    lmax = S.num_levels - 1
+    out = {"workload": f"thin_ellipse_re_N{LARGE_N}_kappa1e4", "N": LARGE_N, "vcycle_ms": round(t_v, 4),
+           "vcycle_mdofs": round(n3 / (t_v * 1e-3) / 1e6, 1), "kernels": {}}
+    for name in ("vanka", "residual", "restrict", "prolong"):
+        ms, by = S.time_kernel(name, lmax, True, reps=20)
+        out["kernels"][name] = {"ms": round(ms, 5), "bytes": by, "gbs": round(by / (ms * 1e-3) / 1e9, 1)}
+    S.close()
+    return out
+
+
+def run_native(args):
+    import torch
+    from paper_1612_02208_gb300 import sib
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    rank, world = dist_init("nccl")
+    dev = torch.device("cuda", local)
+    prob = make_problem()
+    st = prob.structure
+    S = sib.Solver(prob.N)
+    S.set_fluid(prob.rho, prob.mu, prob.dt)
+    X = torch.as_tensor(st.X, device=dev)
+    Ed = torch.as_tensor(st.edges, device=dev)
+    S.set_structure(X, Ed, torch.as_tensor(st.kappa, device=dev))
+    kap_dev = {k: torch.full((st.E,), k, dtype=torch.float64, device=dev) for k in KAPPAS}
+    g = torch.as_tensor(prob.g, device=dev)
+    w = torch.empty_like(g)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(max(args.warmup, 0)):
+        native_step(S, g, w, kap_dev, sib)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    dist_barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = S.launch_count
+    records = []
+    step_ms = []
+    t_wall = time.perf_counter()
+    stream = torch.cuda.current_stream()
+    for k in range(args.steps):
+        flush.fill_(float(k))                     # L2 flush between timed steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        native_step(S, g, w, kap_dev, sib, records if k == 0 else None)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    dist_barrier()
+    wall = time.perf_counter() - t_wall
+    launches = S.launch_count - launches0
+    clk = clocks.stop()
+
+    total_ms = float(sum(step_ms))
+    solves = len(SMOOTHERS) * len(KAPPAS)
+    max_total = dist_max(total_ms, dev)
+    value = job_ms_per_solve(max_total, solves * args.steps, world)
+
+    # dominant kernel of the step, timed live on the benchmark's own context and stream
+    lmax = S.num_levels - 1
+    S.set_options(smoother=sib.SMOOTHER_VANKA, omega=-1.0)
+    S.set_stiffness(kap_dev[1e2])
+    S.setup()
+    dom_ms, dom_bytes = S.time_kernel("vanka", lmax, True, reps=50)
+    peak, peak_kind = measured_peaks()
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_vanka<float> (finest level)", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": recorded_traffic("k_vanka_f32", WORKLOAD), "bytes_per_launch": dom_bytes,
+                "launch_ms": round(dom_ms, 5), "peak_source": peak_kind,
+                "note": "working set fits in L2 at N=128; see vcycle_large for the HBM-bound size"}
+
+    # FP64 V-cycle for the same step (context: FP32 vs FP64 multigrid)
+    fp64_records = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    flush.fill_(0.5)
+    e0.record(stream)
+    native_step(S, g, w, kap_dev, sib, fp64_records, vcycle_fp32=0)
+    e1.record(stream)
+    e1.synchronize()
+    fp64_ms = e0.elapsed_time(e1) / solves
+
+    # end to end through the host-buffer C call, pinned host memory
+    g_host = torch.as_tensor(prob.g).pin_memory().numpy()
+    w_host = torch.empty(g.numel(), dtype=torch.float64).pin_memory().numpy()
+    kap_host = {k: torch.full((st.E,), k, dtype=torch.float64).pin_memory() for k in KAPPAS}
+    e2e_step(S, g_host, w_host, kap_host, kap_dev, sib, torch)
+    torch.cuda.synchronize()
+    dist_barrier()
+    t = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        e2e_step(S, g_host, w_host, kap_host, kap_dev, sib, torch)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t) * 1e3
+    e2e_value = job_ms_per_solve(dist_max(e2e_ms, dev), solves * e2e_steps, world)
+    n3 = 3 * prob.N * prob.N
+    e2e = {"value": round(e2e_value, 4), "unit": "ms/solve", "h2d_bytes_per_step": solves * (8 * n3 + 8 * st.E),
+           "d2h_bytes_per_step": solves * 8 * n3}
+
+    large = None
+    if not args.no_large:
+        large = large_vcycle(sib, torch)
+        large["roofline_vanka"] = {"achieved": large["kernels"]["vanka"]["gbs"], "peak": peak,
+                                   "frac": round(large["kernels"]["vanka"]["gbs"] / peak, 4),
+                                   "traffic": recorded_traffic("k_vanka_f32", large["workload"])}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ms, cases = oracle_sweep()
+        cpu = {"value": round(ms, 2), "unit": "ms/solve", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "one full step: the 8 solves of the kappa x smoother sweep, numpy/scipy FP64, "
+                         "set-up included", "iterations": [c["iterations"] for c in cases]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "ms/solve", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(max_total / args.steps, 4), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": prob.N, "markers": st.M, "springs": st.E,
+                       "kappa": KAPPAS, "smoothers": SMOOTHERS, "vcycle": "fp32, coarsest fp64",
+                       "krylov": "fp64 FGMRES(100), CGS2", "rtol": 1e-8, "max_it": 100,
+                       "parallelism": f"replicas x{world}", "l2": "flushed between timed steps",
+                       "timing": "CUDA events per step on the launching stream"},
+            "cases": records, "fp64_vcycle": {"ms_per_solve": round(fp64_ms, 4), "cases": fp64_records},
+            "roofline": roofline, "vcycle_large": large, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk, "wall_s": round(wall, 3),
+        }
+        print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------ reference arm
+def oracle_sweep():
+    """The oracle (FP64 numpy/scipy) on one full step of the workload; returns (ms/solve, cases)."""
+    from oracle import krylov, multigrid, system
+    prob = make_problem()
+    cases = []
+    t0 = time.perf_counter()
+    for sm in SMOOTHERS:
+        for kap in KAPPAS:
+            prob.structure.kappa[:] = kap
+            L = system.operator_of(prob)
+            b = system.rhs(prob)
+            H = multigrid.Hierarchy(prob, smoother=sm)
+            x, its, hist, conv = krylov.fgmres(lambda z: L @ z, H.vcycle, b, rtol=1e-8, max_it=100,
+                                               project=lambda z: system.project(z, prob.N, prob.rho))
+            cases.append(dict(smoother=sm, kappa=kap, iterations=its, converged=bool(conv)))
+    ms = (time.perf_counter() - t0) * 1e3 / len(cases)
+    return ms, cases
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(max(args.warmup, 0)):
+        oracle_sweep()
+    per = []
+    cases = None
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        ms, cases = oracle_sweep()
+        per.append(ms)
+    wall = time.perf_counter() - t
+    value = float(np.mean(per))
+    solves = len(SMOOTHERS) * len(KAPPAS)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": "ms/solve", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value * solves, 2),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N_GRID, "kappa": KAPPAS, "smoothers": SMOOTHERS, "rtol": 1e-8,
+                   "max_it": 100, "parallelism": "rank 0 only (CPU)"},
+        "cases": cases,
+        "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": round(value, 2), "unit": "ms/solve",
+                         "sample": f"{args.steps} full steps of the workload (8 solves each), set-up included"},
+        "e2e": {"value": round(value, 2), "unit": "ms/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": round(wall, 2),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

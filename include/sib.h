@@ -29,7 +29,7 @@
  *   - The library owns all workspace.  It allocates device memory in sib_create/sib_setup
  *     (and when sizes grow); sib_solve and the level calls do not allocate.
  *   - A context is not thread-safe; different contexts are independent.
- *   - N must be n_min * 2^k with n_min a power of two in [4, 64]; N <= 8192.
+ *   - N must be n_min * 2^k with n_min a power of two in [4, 16]; N <= 8192.
  */
 #ifndef SIB_H
 #define SIB_H
@@ -158,6 +158,21 @@ int sib_vcycle(sib_ctx* ctx, int prec, const void* b, void* z, void* stream);
  * (F: 2M doubles, f: 2N^2), FP64. */
 int sib_interp(sib_ctx* ctx, const double* u, double* U, void* stream);
 int sib_spread(sib_ctx* ctx, const double* F, double* f, void* stream);
+
+/* ---- measurement ----------------------------------------------------------------------------- */
+#define SIB_KERNEL_VANKA     0   /* one additive Vanka sweep kernel (residual + patch solves + update) */
+#define SIB_KERNEL_RESIDUAL  1   /* Stokes-IB residual r = b - L x                                   */
+#define SIB_KERNEL_SPREAD    2   /* spreading gather of the level                                    */
+#define SIB_KERNEL_INTERP    3   /* interpolation of the level                                       */
+#define SIB_KERNEL_RESTRICT  4   /* restriction of a residual from `level` to level-1                 */
+#define SIB_KERNEL_PROLONG   5   /* prolongation-correction from level-1 to `level`                   */
+/* Times `reps` back-to-back launches of one kernel of the V-cycle on `level` (operands: the
+ * level's own work buffers, zero-filled first) between two CUDA events recorded on `stream`,
+ * and returns the mean device time of one launch (*ms) and the algorithmic DRAM bytes one
+ * launch must move (*bytes: every operand word read once and every result word written once;
+ * IB data counted only in IB-active tiles).  Synchronises `stream`.  Requires sib_setup. */
+int sib_time_kernel(sib_ctx* ctx, int kernel, int level, int prec, int reps, void* stream, double* ms,
+                    double* bytes);
 
 /* ---- accounting ---------------------------------------------------------------------------- */
 /* Number of kernels this context has launched (graph replays count every kernel node). */

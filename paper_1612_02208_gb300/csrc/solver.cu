@@ -1,4 +1,5 @@
 // libsib: solver context, set-up, V-cycle (Alg. 1), flexible GMRES and the C ABI of sib.h.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -885,6 +886,81 @@ void smooth_impl(sib_ctx* c, int l, T* x, const T* b, int sweeps, cudaStream_t s
     CK(cudaMemcpyAsync(x, xa, sizeof(T) * n3, cudaMemcpyDeviceToDevice, s));
 }
 
+template <typename T>
+void time_kernel(sib_ctx* c, int kernel, int l, int reps, cudaStream_t s, double* ms, double* bytes) {
+    Level& lv = c->L[l];
+    const int pi = Prec<T>::id;
+    LevelBuf& b = lv.p[pi];
+    const double n = (double)lv.N * lv.N;
+    const double w = sizeof(T);
+    const double active = c->haveIB ? (double)lv.hnTiles * lv.tx * lv.ty : 0.0;   // cells in IB-active tiles
+    const int64_t n3 = 3LL * lv.N * lv.N;
+    CK(cudaMemsetAsync(b.x, 0, sizeof(T) * n3, s));
+    CK(cudaMemsetAsync(b.b, 0, sizeof(T) * n3, s));
+    CK(cudaMemsetAsync(b.r, 0, sizeof(T) * n3, s));
+    GridK<T> g = gridk<T>(c, l);
+    IBK<T> k = ibk<T>(c, l);
+    T* U = (T*)c->U[pi];
+    T* F = (T*)c->F[pi];
+    double by = 0;
+    auto launch = [&]() {
+        switch (kernel) {
+            case SIB_KERNEL_VANKA:
+                launch_vanka<T>(g, (const T*)b.x, (const T*)b.b, (T*)b.xt, s);
+                break;
+            case SIB_KERNEL_RESIDUAL:
+                launch_residual<T>(g, (const T*)b.x, (const T*)b.b, (T*)b.r, s);
+                break;
+            case SIB_KERNEL_SPREAD:
+                launch_spread<T>(k, F, (T*)b.fib, lv.tiles, lv.nTiles, lv.hnTiles, lv.tx, lv.ty, lv.ntx, lv.spreadWarp, s);
+                break;
+            case SIB_KERNEL_INTERP:
+                launch_interp<T>(k, (const T*)b.x, U, s);
+                break;
+            case SIB_KERNEL_RESTRICT:
+                launch_restrict<T>(c->L[l - 1].N, (const T*)b.r, (T*)c->L[l - 1].p[pi].b, s);
+                break;
+            case SIB_KERNEL_PROLONG:
+                launch_prolong_add<T>(c->L[l - 1].N, (const T*)c->L[l - 1].p[pi].x, (T*)b.x, s);
+                break;
+            default:
+                throw SibError(SIB_ERR_ARG, "unknown kernel id");
+        }
+    };
+    switch (kernel) {
+        case SIB_KERNEL_VANKA:   // x, b read; xo written; fib (2) + ibd (4) words in active tiles
+            by = 9.0 * n * w + 6.0 * active * w;
+            break;
+        case SIB_KERNEL_RESIDUAL:
+            by = 9.0 * n * w + 2.0 * active * w;
+            break;
+        case SIB_KERNEL_SPREAD:   // every active face written, every marker's weights and force read once
+            by = 2.0 * active * w + (double)c->M * 2.0 * (8.0 * w + 4.0 + w) + 2.0 * (n + 1) * 4.0;
+            break;
+        case SIB_KERNEL_INTERP:   // stencil origin, weights, W^2 velocities (distinct faces at most), U
+            by = (double)c->M * 2.0 * (4.0 + 8.0 * w + w) + std::min(2.0 * active, (double)c->M * 2.0 * lv.W * lv.W) * w;
+            break;
+        case SIB_KERNEL_RESTRICT:
+            by = 3.0 * n * w + 0.75 * n * w;
+            break;
+        case SIB_KERNEL_PROLONG:
+            by = 0.75 * n * w + 6.0 * n * w;
+            break;
+        default:
+            throw SibError(SIB_ERR_ARG, "unknown kernel id");
+    }
+    launch();   // warm-up
+    CK(cudaEventRecord(c->ev0, s));
+    for (int r = 0; r < reps; ++r) launch();
+    CK(cudaEventRecord(c->ev1, s));
+    CK(cudaEventSynchronize(c->ev1));
+    kcheck(c);
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, c->ev0, c->ev1));
+    *ms = t / reps;
+    *bytes = by;
+}
+
 #define API_BEGIN(c)                       \
     if (!(c)) return SIB_ERR_ARG;          \
     try {                                  \
@@ -1328,6 +1404,23 @@ int sib_spread(sib_ctx* c, const double* F, double* f, void* stream) {
                                 lv.tx, lv.ty, lv.ntx, lv.spreadWarp, s));
     CK(cudaMemcpyAsync(f, lv.p[0].fib, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
     kcheck(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_time_kernel(sib_ctx* c, int kernel, int l, int prec, int reps, void* stream, double* ms, double* bytes) {
+    API_BEGIN(c)
+    require_setup(c);
+    check_level(c, l, 0);
+    if (!valid_prec(prec) || reps < 1 || !ms || !bytes) throw SibError(SIB_ERR_ARG, "bad argument");
+    if ((kernel == SIB_KERNEL_RESTRICT || kernel == SIB_KERNEL_PROLONG || kernel == SIB_KERNEL_VANKA) && l < 1)
+        throw SibError(SIB_ERR_ARG, "kernel needs level >= 1");
+    if ((kernel == SIB_KERNEL_SPREAD || kernel == SIB_KERNEL_INTERP) && !c->haveIB)
+        throw SibError(SIB_ERR_ARG, "no immersed structure");
+    if (prec == SIB_PREC_FP64)
+        time_kernel<double>(c, kernel, l, reps, S(stream), ms, bytes);
+    else
+        time_kernel<float>(c, kernel, l, reps, S(stream), ms, bytes);
     return SIB_OK;
     API_END(c)
 }

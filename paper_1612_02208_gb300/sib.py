@@ -36,8 +36,10 @@ EXPORTS = [
     "sib_set_stiffness", "sib_set_options", "sib_set_eigen_estimates", "sib_get_eigen_estimates", "sib_setup",
     "sib_solve", "sib_solve_host", "sib_solve_rhs", "sib_grad", "sib_num_levels", "sib_level_size",
     "sib_apply_operator", "sib_apply_ib", "sib_smooth", "sib_residual_restrict", "sib_prolong_add",
-    "sib_coarse_solve", "sib_vcycle", "sib_interp", "sib_spread", "sib_launch_count", "sib_device_bytes",
+    "sib_coarse_solve", "sib_vcycle", "sib_interp", "sib_spread", "sib_time_kernel", "sib_launch_count",
+    "sib_device_bytes",
 ]
+KERNELS = {"vanka": 0, "residual": 1, "spread": 2, "interp": 3, "restrict": 4, "prolong": 5}
 
 
 class SibOpts(ctypes.Structure):
@@ -118,6 +120,7 @@ def load(build_if_missing: bool = True):
         "sib_vcycle": (I, [ctx, I, P, P, P]),
         "sib_interp": (I, [ctx, P, P, P]),
         "sib_spread": (I, [ctx, P, P, P]),
+        "sib_time_kernel": (I, [ctx, I, I, I, I, P, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "sib_launch_count": (ctypes.c_int64, [ctx]),
         "sib_device_bytes": (ctypes.c_int64, [ctx]),
     }
@@ -319,6 +322,14 @@ class Solver:
         f = torch.empty(2 * self.N * self.N, dtype=torch.float64, device=F.device)
         self._check(self.lib.sib_spread(self.ctx, _ptr(F) if self.M else None, _ptr(f), _stream()))
         return f
+
+    def time_kernel(self, kernel: str, level: int, fp32: bool, reps: int = 20):
+        """(mean ms per launch, algorithmic bytes per launch) of one V-cycle kernel, CUDA events."""
+        ms = ctypes.c_double()
+        by = ctypes.c_double()
+        self._check(self.lib.sib_time_kernel(self.ctx, KERNELS[kernel], int(level), PREC_FP32 if fp32 else PREC_FP64,
+                                             int(reps), _stream(), ctypes.byref(ms), ctypes.byref(by)))
+        return ms.value, by.value
 
     @property
     def launch_count(self):
