@@ -49,6 +49,7 @@ extern "C" {
 #define SIB_ERR_UNIMPLEMENTED  -6  /* option combination not implemented                             */
 #define SIB_ERR_STATE          -7  /* call out of order (e.g. solve before setup)                    */
 #define SIB_ERR_ALLOC          -8  /* device or host allocation failed                               */
+#define SIB_ERR_TOO_LARGE      -9  /* sib_spread_noalloc: N or M beyond its fixed scratch            */
 
 #define SIB_SMOOTHER_VANKA 0       /* additive per-cell Vanka (Alg. 2 with one-cell subdomains)     */
 #define SIB_SMOOTHER_SC    1       /* Schur-complement smoother (Eq. approx-fact-Stokes-IB)         */
@@ -173,6 +174,23 @@ int sib_spread(sib_ctx* ctx, const double* F, double* f, void* stream);
  * IB data counted only in IB-active tiles).  Synchronises `stream`.  Requires sib_setup. */
 int sib_time_kernel(sib_ctx* ctx, int kernel, int level, int prec, int reps, void* stream, double* ms,
                     double* bytes);
+
+/* ---- spreading without device allocation ----------------------------------------------------- */
+/* f = S F on an N x N grid for markers X (M x 2) and forces F (M x 2), written to the caller's
+ * f (2 N^2 values [f_u | f_v]); the same result as sib_spread without a solver context.
+ * The paper has no counterpart: this is for callers that cannot allocate device memory, such as
+ * programs whose device memory is owned by their own pool allocator (a raw cudaMalloc would fail
+ * or fragment it) and latency-critical loops that cannot afford the device-wide synchronisation
+ * of cudaMalloc/cudaFree.  It calls no cudaMalloc, cudaFree or allocating library routine; its
+ * scratch is one static device array of about 4.4 MB that every GPU loading the library holds
+ * until exit.
+ *   Limits: N a power of two, 8 <= N <= 256; 0 <= M <= 16384.  Larger sizes return
+ *   SIB_ERR_TOO_LARGE; other invalid arguments return SIB_ERR_ARG.
+ *   The first call on each device looks up the scratch array's device address (a one-time
+ *   set-up); make that first call before any stream capture.
+ *   All calls share the one scratch array: calls that overlap on the GPU (other streams, other
+ *   host threads) race and must be serialised by the caller. */
+int sib_spread_noalloc(int N, int M, const double* X, const double* F, double* f, void* stream);
 
 /* ---- accounting ---------------------------------------------------------------------------- */
 /* Number of kernels this context has launched (graph replays count every kernel node). */

@@ -1,6 +1,6 @@
 """Builds libsib.so in-tree with nvcc for sm_103a (GB300).
 
-Four translation units are compiled in parallel and linked into
+The translation units are compiled in parallel and linked into
 ``paper_1612_02208_gb300/libsib.so`` (git-ignored).  ``build()`` is a no-op when the library is
 newer than every source file.
 """
@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libsib.so")
 OBJDIR = os.path.join(PKG, "_build")
-SOURCES = ["kernels_grid.cu", "kernels_ib.cu", "kernels_krylov.cu", "solver.cu"]
+SOURCES = ["kernels_grid.cu", "kernels_ib.cu", "kernels_krylov.cu", "solver.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

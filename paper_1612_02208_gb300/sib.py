@@ -22,6 +22,7 @@ SIB_ERR_BREAKDOWN = -5
 SIB_ERR_UNIMPLEMENTED = -6
 SIB_ERR_STATE = -7
 SIB_ERR_ALLOC = -8
+SIB_ERR_TOO_LARGE = -9
 ERROR_NAMES = {v: k for k, v in dict(globals()).items() if k.startswith("SIB_ERR") or k == "SIB_OK"}
 
 SMOOTHER_VANKA = 0
@@ -37,7 +38,7 @@ EXPORTS = [
     "sib_solve", "sib_solve_host", "sib_solve_rhs", "sib_grad", "sib_num_levels", "sib_level_size",
     "sib_apply_operator", "sib_apply_ib", "sib_smooth", "sib_residual_restrict", "sib_prolong_add",
     "sib_coarse_solve", "sib_vcycle", "sib_interp", "sib_spread", "sib_time_kernel", "sib_launch_count",
-    "sib_device_bytes",
+    "sib_device_bytes", "sib_spread_noalloc",
 ]
 KERNELS = {"vanka": 0, "residual": 1, "spread": 2, "interp": 3, "restrict": 4, "prolong": 5}
 
@@ -123,6 +124,7 @@ def load(build_if_missing: bool = True):
         "sib_time_kernel": (I, [ctx, I, I, I, I, P, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "sib_launch_count": (ctypes.c_int64, [ctx]),
         "sib_device_bytes": (ctypes.c_int64, [ctx]),
+        "sib_spread_noalloc": (I, [I, I, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
