@@ -34,7 +34,7 @@ KAPPAS = [1e0, 1e2, 1e4, 1e6]
 SMOOTHERS = ["vanka", "sc"]
 N_GRID = 128
 WORKLOAD = "disk_stokes_N128_kappa_sweep"
-LARGE_N = 2048
+LARGE_N = 4096
 L2_BYTES = 129 * 2 ** 20
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
 KERNEL_SOURCE = os.path.join(ROOT, "paper_1612_02208_gb300", "csrc", "kernels_grid.cu")
@@ -51,6 +51,7 @@ def parse_args(argv=None):
     p.add_argument("--kappas", default=",".join(str(k) for k in KAPPAS),
                    help="comma-separated stiffness values of the sweep (default: the full workload)")
     p.add_argument("--smoothers", default=",".join(SMOOTHERS), help="comma-separated subset of vanka,sc")
+    p.add_argument("--large-n", type=int, default=LARGE_N, help="grid of the large-grid V-cycle roofline")
     a = p.parse_args(argv)
     KAPPAS[:] = [float(x) for x in a.kappas.split(",")]
     SMOOTHERS[:] = [x for x in a.smoothers.split(",")]
@@ -210,12 +211,14 @@ def e2e_step(S, g_host, w_host, kap_host, kap_dev, sib, torch):
             S.solve_host(g_host, w_host, allow_unconverged=True)
 
 
-def large_vcycle(sib, torch, reps=20):
-    """V-cycle throughput and the Vanka kernel's roofline on a grid whose working set exceeds L2:
-    2048^2, rho = 1, mu = 1e-2, dt = 1e-3, thin ellipse, kappa = 1e4, FP32 V-cycle."""
+def large_vcycle(sib, torch, reps=20, N=None):
+    """V-cycle throughput and the Vanka kernel's roofline on a grid whose working set exceeds L2
+    (4096^2: one FP32 sweep moves 600 MB), rho = 1, mu = 1e-2, dt = 1e-3, thin ellipse,
+    kappa = 1e4, FP32 V-cycle."""
     from paper_1612_02208_gb300 import inputs
-    prob = inputs.thin_ellipse_re(LARGE_N, kappa=1e4, seed=2)
-    S = sib.Solver(LARGE_N)
+    LARGE = N or LARGE_N
+    prob = inputs.thin_ellipse_re(LARGE, kappa=1e4, seed=2)
+    S = sib.Solver(LARGE)
     S.set_fluid(prob.rho, prob.mu, prob.dt)
     st = prob.structure
     dev = torch.device("cuda")
@@ -223,7 +226,7 @@ def large_vcycle(sib, torch, reps=20):
                     torch.as_tensor(st.kappa, device=dev))
     S.set_options(restart=1, max_it=1)
     S.setup()
-    n3 = 3 * LARGE_N * LARGE_N
+    n3 = 3 * LARGE * LARGE
     b = torch.randn(n3, device=dev, dtype=torch.float32)
     z = torch.empty_like(b)
     for _ in range(3):
@@ -237,7 +240,7 @@ def large_vcycle(sib, torch, reps=20):
     torch.cuda.synchronize()
     t_v = e0.elapsed_time(e1) / reps
     lmax = S.num_levels - 1
-    out = {"workload": f"thin_ellipse_re_N{LARGE_N}_kappa1e4", "N": LARGE_N, "vcycle_ms": round(t_v, 4),
+    out = {"workload": f"thin_ellipse_re_N{LARGE}_kappa1e4", "N": LARGE, "vcycle_ms": round(t_v, 4),
            "vcycle_mdofs": round(n3 / (t_v * 1e-3) / 1e6, 1), "kernels": {}}
     for name in ("vanka", "residual", "restrict", "prolong"):
         ms, by = S.time_kernel(name, lmax, True, reps=20)
@@ -274,6 +277,7 @@ def run_native(args):
     dist_barrier()
     torch.cuda.synchronize()
     clocks.start()
+    torch.cuda.nvtx.range_push("timed_steps")
     launches0 = S.launch_count
     records = []
     step_ms = []
@@ -289,6 +293,7 @@ def run_native(args):
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     dist_barrier()
     wall = time.perf_counter() - t_wall
     launches = S.launch_count - launches0
@@ -344,7 +349,9 @@ def run_native(args):
 
     large = None
     if not args.no_large:
-        large = large_vcycle(sib, torch)
+        torch.cuda.nvtx.range_push("vcycle_large")
+        large = large_vcycle(sib, torch, N=args.large_n)
+        torch.cuda.nvtx.range_pop()
         large["roofline_vanka"] = {"achieved": large["kernels"]["vanka"]["gbs"], "peak": peak,
                                    "frac": round(large["kernels"]["vanka"]["gbs"] / peak, 4),
                                    "traffic": recorded_traffic("k_vanka_f32", large["workload"])}

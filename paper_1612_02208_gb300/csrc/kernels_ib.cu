@@ -592,6 +592,197 @@ void launch_dense_ib(const int* edges, const double* kappa, int E, const int* ba
 }
 
 // ------------------------------------------------------------------------------------------
+// Assembled Galerkin IB operator.  On a level where every spring joins markers whose stencil
+// origins differ by at most WR - W + 1 cells, [S K J]^l couples a face only to faces within
+// +-WR in each direction, so it is stored per face as a (2 WR + 1)^2 window of coefficients
+//   B(f, f + o) = (1/h^2) sum_a J_l[a, f] sum_b K_ab J_l[b, f + o]
+// (the same sum as the marker path, regrouped by face).  Windows exist for the faces of the
+// IB-active tiles only, laid out [slot][comp][o][face in tile] (slot = index in the tile list).
+// Set-up: one warp per face gathers the markers of its bins (lanes strided, private partial
+// windows, fixed-order warp reduction); a spring reaching outside the window sets *overflow.
+__device__ __forceinline__ int wrapdiff(int d, int N) {
+    d &= N - 1;
+    return d >= N / 2 ? d - N : d;
+}
+
+__global__ void __launch_bounds__(256) k_window_assemble(IBK<double> k, const int* __restrict__ adjStart,
+                                                         const int* __restrict__ adjNbr,
+                                                         const double* __restrict__ adjKap,
+                                                         const int* __restrict__ tiles, int nTiles, int tx, int ty,
+                                                         int ntx, double* __restrict__ win, int* __restrict__ overflow) {
+    const int slot = blockIdx.x;
+    if (slot >= nTiles) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per = tx * ty;
+    const int face = blockIdx.y * 8 + warp;
+    if (face >= 2 * per) return;
+    const int c = face / per, q = face % per;
+    const int t = tiles[slot];
+    const int N = k.N, mk = N - 1;
+    const int i = (t % ntx) * tx + q % tx, j = (t / ntx) * ty + q / tx;
+    double acc[WIN_SIZE];
+    for (int o = 0; o < WIN_SIZE; ++o) acc[o] = 0.0;
+    int ovf = 0;
+    const int* bs = k.binStart[c];
+    const int* srt = k.sorted[c];
+    const double* wg = k.wgt[c];
+    const int* bse = k.base[c];
+    for (int bb = 0; bb < k.W; ++bb)
+        for (int aa = 0; aa < k.W; ++aa) {
+            const uint32_t bin = morton((i - aa) & mk, (j - bb) & mk);
+            const int s0 = bs[bin], e0 = bs[bin + 1];
+            for (int qq = s0 + lane; qq < e0; qq += 32) {
+                const int m = srt[qq];
+                const double jf = wg[8 * m + aa] * wg[8 * m + 4 + bb] * k.inv_h2;   // J[m, f] / h^2
+                if (jf == 0.0) continue;
+                double ksum = 0.0;
+                for (int p = adjStart[m]; p < adjStart[m + 1]; ++p) {
+                    const double kap = adjKap[p];
+                    ksum += kap;
+                    const int b = adjNbr[p];
+                    const int ob = bse[b];
+                    const int bi = ob & 0xffff, bj = (ob >> 16) & 0xffff;
+                    for (int y = 0; y < k.W; ++y) {
+                        const int oy = wrapdiff(bj + y - j, N);
+                        for (int x = 0; x < k.W; ++x) {
+                            const double wgt = wg[8 * b + x] * wg[8 * b + 4 + y];
+                            if (wgt == 0.0) continue;
+                            const int ox = wrapdiff(bi + x - i, N);
+                            if (ox < -WR || ox > WR || oy < -WR || oy > WR) {
+                                ovf = 1;
+                                continue;
+                            }
+                            acc[(oy + WR) * WD + ox + WR] += kap * jf * wgt;
+                        }
+                    }
+                }
+                // diagonal of K: -sum kappa
+                const int om = bse[m];
+                const int mi = om & 0xffff, mj = (om >> 16) & 0xffff;
+                for (int y = 0; y < k.W; ++y) {
+                    const int oy = wrapdiff(mj + y - j, N);
+                    for (int x = 0; x < k.W; ++x) {
+                        const double wgt = wg[8 * m + x] * wg[8 * m + 4 + y];
+                        if (wgt == 0.0) continue;
+                        const int ox = wrapdiff(mi + x - i, N);
+                        if (ox < -WR || ox > WR || oy < -WR || oy > WR) {
+                            ovf = 1;
+                            continue;
+                        }
+                        acc[(oy + WR) * WD + ox + WR] -= ksum * jf * wgt;
+                    }
+                }
+            }
+        }
+    double* wout = win + ((size_t)(slot * 2 + c) * WIN_SIZE) * per;
+    for (int o = 0; o < WIN_SIZE; ++o) {
+        double v = acc[o];
+        for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+        if (lane == (o & 31)) wout[(size_t)o * per + q] = v;
+    }
+    ovf = __any_sync(0xffffffffu, ovf);
+    if (ovf && lane == 0) atomicOr(overflow, 1);
+}
+void launch_window_assemble(const IBK<double>& k, const int* adjStart, const int* adjNbr, const double* adjKap,
+                            const int* tiles, int nTiles, int tx, int ty, int ntx, double* win, int* overflow,
+                            cudaStream_t s) {
+    if (nTiles == 0 || k.M == 0) return;
+    const int groups = (2 * tx * ty + 7) / 8;
+    k_window_assemble<<<dim3(nTiles, groups), 256, 0, s>>>(k, adjStart, adjNbr, adjKap, tiles, nTiles, tx, ty, ntx,
+                                                           win, overflow);
+}
+
+// Patch entries of the Vanka/SC smoothers from the windows: B(f,f) and B(f, f+e), e = +x for u
+// faces, +y for v faces; ibd is zero outside the active tiles.
+__global__ void k_window_patch(const double* __restrict__ win, const int* __restrict__ tiles, int nTiles, int N,
+                               int tx, int ty, int ntx, double* __restrict__ ibd) {
+    const int slot = blockIdx.x;
+    if (slot >= nTiles) return;
+    const int per = tx * ty;
+    const int q = threadIdx.y * tx + threadIdx.x;
+    const int t = tiles[slot];
+    const int i = (t % ntx) * tx + threadIdx.x, j = (t / ntx) * ty + threadIdx.y;
+    const int n = N * N, f = j * N + i;
+    const double* wu = win + ((size_t)(slot * 2 + 0) * WIN_SIZE) * per;
+    const double* wv = win + ((size_t)(slot * 2 + 1) * WIN_SIZE) * per;
+    const int ctr = WR * WD + WR;
+    ibd[f] = wu[(size_t)ctr * per + q];
+    ibd[n + f] = wu[(size_t)(ctr + 1) * per + q];
+    ibd[2 * n + f] = wv[(size_t)ctr * per + q];
+    ibd[3 * n + f] = wv[(size_t)(ctr + WD) * per + q];
+}
+void launch_window_patch(const double* win, const int* tiles, int nTiles, int N, int tx, int ty, int ntx, double* ibd,
+                         cudaStream_t s) {
+    if (nTiles == 0) return;
+    k_window_patch<<<nTiles, dim3(tx, ty), 0, s>>>(win, tiles, nTiles, N, tx, ty, ntx, ibd);
+}
+
+// Dense coarsest block B0 (per component, n0 x n0) from the level-0 windows (rows owned by one
+// thread; window offsets that alias on the small grid add into the same entry).
+__global__ void k_window_dense(const double* __restrict__ win, const int* __restrict__ tiles, int nTiles, int N,
+                               int tx, int ty, int ntx, double* __restrict__ B) {
+    const int n0 = N * N;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= 2 * n0) return;
+    const int c = r / n0, f = r % n0, i = f % N, j = f / N;
+    const int t = (j / ty) * ntx + i / tx;
+    int slot = -1;
+    for (int s2 = 0; s2 < nTiles; ++s2)
+        if (tiles[s2] == t) slot = s2;
+    if (slot < 0) return;
+    const int per = tx * ty, q = (j % ty) * tx + (i % tx), mk = N - 1;
+    const double* w = win + ((size_t)(slot * 2 + c) * WIN_SIZE) * per;
+    double* row = B + (size_t)c * n0 * n0 + (size_t)f * n0;
+    for (int oy = -WR; oy <= WR; ++oy)
+        for (int ox = -WR; ox <= WR; ++ox) {
+            const double v = w[(size_t)((oy + WR) * WD + ox + WR) * per + q];
+            if (v != 0.0) row[((j + oy) & mk) * N + ((i + ox) & mk)] += v;
+        }
+}
+void launch_window_dense(const double* win, const int* tiles, int nTiles, int N, int tx, int ty, int ntx, double* B,
+                         cudaStream_t s) {
+    if (nTiles == 0) return;
+    const int rows = 2 * N * N;
+    k_window_dense<<<(rows + 127) / 128, 128, 0, s>>>(win, tiles, nTiles, N, tx, ty, ntx, B);
+}
+
+// Apply: f^c(face) = sum_o B(face, face + o) u^c(face + o), one block per IB-active tile.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ib_window(const T* __restrict__ win, const int* __restrict__ tiles,
+                                                   const int* __restrict__ nTiles, int N, int tx, int ty, int ntx,
+                                                   const T* __restrict__ u, T* __restrict__ f) {
+    const int slot = blockIdx.x;
+    if (slot >= *nTiles) return;
+    const int per = tx * ty, q = threadIdx.y * tx + threadIdx.x;
+    const int t = tiles[slot];
+    const int i = (t % ntx) * tx + threadIdx.x, j = (t / ntx) * ty + threadIdx.y;
+    const int n = N * N, mk = N - 1;
+    for (int c = 0; c < 2; ++c) {
+        const T* w = win + ((size_t)(slot * 2 + c) * WIN_SIZE) * per + q;
+        const T* uc = u + (size_t)c * n;
+        T acc = T(0);
+#pragma unroll
+        for (int oy = -WR; oy <= WR; ++oy) {
+            const int row = ((j + oy) & mk) * N;
+#pragma unroll
+            for (int ox = -WR; ox <= WR; ++ox)
+                acc += w[(size_t)((oy + WR) * WD + ox + WR) * per] * uc[row + ((i + ox) & mk)];
+        }
+        f[(size_t)c * n + j * N + i] = acc;
+    }
+}
+template <typename T>
+void launch_ib_window(const T* win, const int* tiles, const int* nTiles, int maxTiles, int N, int tx, int ty, int ntx,
+                      const T* u, T* f, cudaStream_t s) {
+    if (maxTiles == 0) return;
+    k_ib_window<T><<<maxTiles, dim3(tx, ty), 0, s>>>(win, tiles, nTiles, N, tx, ty, ntx, u, f);
+}
+template void launch_ib_window<float>(const float*, const int*, const int*, int, int, int, int, int, const float*,
+                                      float*, cudaStream_t);
+template void launch_ib_window<double>(const double*, const int*, const int*, int, int, int, int, int, const double*,
+                                       double*, cudaStream_t);
+
+// ------------------------------------------------------------------------------------------
 // (M x 2) interleaved <-> component-major [x (M) | y (M)]
 __global__ void k_deinterleave(const double* __restrict__ in, int M, double* __restrict__ out) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;

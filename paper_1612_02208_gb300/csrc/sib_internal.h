@@ -15,6 +15,10 @@ namespace sib {
 constexpr int TX = 32;
 constexpr int TY = 8;
 constexpr int MAX_N = 8192;
+// Assembled IB operator windows: offsets -WR..WR in each direction, WD = 2 WR + 1 per side.
+constexpr int WR = 4;
+constexpr int WD = 2 * WR + 1;
+constexpr int WIN_SIZE = WD * WD;
 
 // ------------------------------------------------------------------------------------------
 // Morton order of a cell (i, j): bits of i on even positions, bits of j on odd positions.
@@ -96,6 +100,16 @@ void launch_patch_entries(const int* edges, const double* kappa, int E, const in
 void launch_dense_ib(const int* edges, const double* kappa, int E, const int* base0, const int* base1,
                      const double* w0, const double* w1, int N, int W, double inv_h2, double* B,
                      cudaStream_t s);
+void launch_window_assemble(const IBK<double>& k, const int* adjStart, const int* adjNbr, const double* adjKap,
+                            const int* tiles, int nTiles, int tx, int ty, int ntx, double* win, int* overflow,
+                            cudaStream_t s);
+void launch_window_patch(const double* win, const int* tiles, int nTiles, int N, int tx, int ty, int ntx, double* ibd,
+                         cudaStream_t s);
+void launch_window_dense(const double* win, const int* tiles, int nTiles, int N, int tx, int ty, int ntx, double* B,
+                         cudaStream_t s);
+template <typename T>
+void launch_ib_window(const T* win, const int* tiles, const int* nTiles, int maxTiles, int N, int tx, int ty, int ntx,
+                      const T* u, T* f, cudaStream_t s);
 void launch_deinterleave(const double* in, int M, double* out, cudaStream_t s);
 void launch_interleave(const double* in, int M, double* out, cudaStream_t s);
 void launch_hash_vector(double* x, int64_t n, cudaStream_t s);

@@ -58,6 +58,12 @@ struct Level {
     int spreadWarp = 0;
     LevelBuf p[2];                       // [0] FP64, [1] FP32
     double lamA = 0, lamM = 0;
+    // assembled IB operator windows (per active tile), FP64 and FP32
+    void* win[2] = {nullptr, nullptr};
+    int winSlots = 0;
+    int* winOverflow = nullptr;
+    int useWindow = 0;                   // windows valid on this level
+    int applyWindow = 0;                 // the solve applies the IB operator through the windows
 };
 
 struct sib_ctx {
@@ -222,6 +228,11 @@ void ib_apply(sib_ctx* c, int l, const T* u, cudaStream_t s) {
     if (!c->haveIB) return;
     Level& lv = c->L[l];
     const int pi = Prec<T>::id;
+    if (lv.applyWindow) {
+        KL(c, launch_ib_window<T>((const T*)lv.win[pi], lv.tiles, lv.nTiles, lv.hnTiles, lv.N, lv.tx, lv.ty, lv.ntx, u,
+                                  (T*)lv.p[pi].fib, s));
+        return;
+    }
     IBK<T> k = ibk<T>(c, l);
     T* U = (T*)c->U[pi];
     T* F = (T*)c->F[pi];
@@ -606,6 +617,15 @@ void setup(sib_ctx* c, cudaStream_t s) {
         for (int l = 0; l <= c->lmax; ++l) {
             Level& lv = c->L[l];
             lv.hnTiles = cnt[l];
+            if (lv.hnTiles > lv.winSlots || !lv.win[0]) {
+                dfree(c, lv.win[0]);
+                dfree(c, lv.win[1]);
+                const size_t ent = (size_t)(lv.hnTiles > 0 ? lv.hnTiles : 1) * 2 * WIN_SIZE * lv.tx * lv.ty;
+                lv.win[0] = dalloc(c, sizeof(double) * ent);
+                lv.win[1] = dalloc(c, sizeof(float) * ent);
+                lv.winSlots = lv.hnTiles > 0 ? lv.hnTiles : 1;
+            }
+            if (!lv.winOverflow) lv.winOverflow = (int*)dalloc(c, sizeof(int));
             // warp per face when a face gathers from many markers on average
             const double faces = (double)lv.hnTiles * lv.tx * lv.ty;
             lv.spreadWarp = faces > 0 && (double)c->M * lv.W * lv.W > 16.0 * faces ? 1 : 0;
@@ -617,6 +637,22 @@ void setup(sib_ctx* c, cudaStream_t s) {
     if (c->kappaDirty) {
         KL(c, launch_adj_kappa<double>(c->adjEid, c->kappa, 2 * c->E, c->kap64, s));
         KL(c, launch_adj_kappa<float>(c->adjEid, c->kappa, 2 * c->E, c->kap32, s));
+        // assembled windows of [S K J]^l on every level (FP64), overflow flags read back once
+        if (c->haveIB) {
+            for (int l = 0; l <= c->lmax; ++l) {
+                Level& lv = c->L[l];
+                CK(cudaMemsetAsync(lv.winOverflow, 0, sizeof(int), s));
+                KL(c, launch_window_assemble(ibk<double>(c, l), c->adjStart, c->adjNbr, c->kap64, lv.tiles, lv.hnTiles,
+                                             lv.tx, lv.ty, lv.ntx, (double*)lv.win[0], lv.winOverflow, s));
+            }
+            std::vector<int> ovf(c->lmax + 1, 0);
+            for (int l = 0; l <= c->lmax; ++l)
+                CK(cudaMemcpyAsync(&ovf[l], c->L[l].winOverflow, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int l = 0; l <= c->lmax; ++l) c->L[l].useWindow = ovf[l] == 0;
+        } else {
+            for (int l = 0; l <= c->lmax; ++l) c->L[l].useWindow = 0;
+        }
         for (int l = 0; l <= c->lmax; ++l) {
             Level& lv = c->L[l];
             const size_t n = (size_t)lv.N * lv.N;
@@ -626,18 +662,36 @@ void setup(sib_ctx* c, cudaStream_t s) {
             }
             CK(cudaMemsetAsync(lv.p[0].ibd, 0, 8 * 4 * n, s));
             if (c->haveIB && l > 0) {
-                KL(c, launch_patch_entries(c->edges, c->kappa, c->E, lv.base[0], lv.base[1],
-                                           (const double*)lv.p[0].w[0], (const double*)lv.p[0].w[1], c->M, lv.N,
-                                           lv.W, 1.0 / (lv.h * lv.h), (double*)lv.p[0].ibd, s));
+                if (lv.useWindow)
+                    KL(c, launch_window_patch((const double*)lv.win[0], lv.tiles, lv.hnTiles, lv.N, lv.tx, lv.ty, lv.ntx,
+                                              (double*)lv.p[0].ibd, s));
+                else
+                    KL(c, launch_patch_entries(c->edges, c->kappa, c->E, lv.base[0], lv.base[1],
+                                               (const double*)lv.p[0].w[0], (const double*)lv.p[0].w[1], c->M, lv.N,
+                                               lv.W, 1.0 / (lv.h * lv.h), (double*)lv.p[0].ibd, s));
             }
             KL(c, (launch_convert<double, float>((const double*)lv.p[0].ibd, (float*)lv.p[1].ibd, 4 * (int64_t)n,
                                                  s)));
+            if (lv.useWindow) {
+                const int64_t ent = (int64_t)lv.hnTiles * 2 * WIN_SIZE * lv.tx * lv.ty;
+                KL(c, (launch_convert<double, float>((const double*)lv.win[0], (float*)lv.win[1], ent, s)));
+            }
+            // the solve applies the windows on coarse levels, and on the finest level when the
+            // windows hold fewer than 8 coefficients per marker-face pair of the marker path
+            const double winEnt = (double)lv.hnTiles * lv.tx * lv.ty * 2.0 * WIN_SIZE;
+            const double pairs = (double)c->M * 2.0 * lv.W * lv.W;
+            lv.applyWindow = c->haveIB && lv.useWindow && (l < c->lmax || winEnt <= 8.0 * pairs);
         }
         Level& l0 = c->L[0];
         CK(cudaMemsetAsync(c->B0, 0, sizeof(double) * 2 * (size_t)c->n0 / 3 * c->n0 / 3, s));
-        if (c->haveIB)
-            KL(c, launch_dense_ib(c->edges, c->kappa, c->E, l0.base[0], l0.base[1], (const double*)l0.p[0].w[0],
-                                  (const double*)l0.p[0].w[1], l0.N, l0.W, 1.0 / (l0.h * l0.h), c->B0, s));
+        if (c->haveIB) {
+            if (l0.useWindow)
+                KL(c, launch_window_dense((const double*)l0.win[0], l0.tiles, l0.hnTiles, l0.N, l0.tx, l0.ty, l0.ntx,
+                                          c->B0, s));
+            else
+                KL(c, launch_dense_ib(c->edges, c->kappa, c->E, l0.base[0], l0.base[1], (const double*)l0.p[0].w[0],
+                                      (const double*)l0.p[0].w[1], l0.N, l0.W, 1.0 / (l0.h * l0.h), c->B0, s));
+        }
         c->kappaDirty = false;
         c->fluidDirty = true;
     }
