@@ -598,98 +598,189 @@ void launch_dense_ib(const int* edges, const double* kappa, int E, const int* ba
 //   B(f, f + o) = (1/h^2) sum_a J_l[a, f] sum_b K_ab J_l[b, f + o]
 // (the same sum as the marker path, regrouped by face).  Windows exist for the faces of the
 // IB-active tiles only, laid out [slot][comp][o][face in tile] (slot = index in the tile list).
-// Set-up: one warp per face gathers the markers of its bins (lanes strided, private partial
-// windows, fixed-order warp reduction); a spring reaching outside the window sets *overflow.
 __device__ __forceinline__ int wrapdiff(int d, int N) {
     d &= N - 1;
     return d >= N / 2 ? d - N : d;
 }
 
-__global__ void __launch_bounds__(256) k_window_assemble(IBK<double> k, const int* __restrict__ adjStart,
-                                                         const int* __restrict__ adjNbr,
-                                                         const double* __restrict__ adjKap,
-                                                         const int* __restrict__ tiles, int nTiles, int tx, int ty,
-                                                         int ntx, double* __restrict__ win, int* __restrict__ overflow) {
+// Faster set-up of the same windows.  Finest level: (1) per marker a the row (K J)_a =
+// sum_b K_ab J[b, .] on a 6 x 6 patch anchored at a's stencil origin minus one (springs whose
+// markers' origins differ by more than one cell set *overflow); (2) one thread per (face, window
+// row oy) accumulates B(f, f+o) = (1/h^2) sum_{a: f in stencil(a)} J[a, f] (K J)_a(f + o) over
+// the nine o of its row, in registers (the window index is static under full unrolling).
+__global__ void k_kj_patch(IBK<double> k, const int* __restrict__ adjStart, const int* __restrict__ adjNbr,
+                           const double* __restrict__ adjKap, double* __restrict__ KJ, int* __restrict__ overflow) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (m >= k.M) return;
+    const int N = k.N;
+    const double* wg = k.wgt[c];
+    const int* bse = k.base[c];
+    double acc[36];
+    for (int e = 0; e < 36; ++e) acc[e] = 0.0;
+    const int om = bse[m], mi = om & 0xffff, mj = (om >> 16) & 0xffff;
+    double ksum = 0.0;
+    int ovf = 0;
+    for (int p = adjStart[m]; p < adjStart[m + 1]; ++p) {
+        const double kap = adjKap[p];
+        ksum += kap;
+        const int b = adjNbr[p];
+        const int ob = bse[b];
+        const int dx = wrapdiff((ob & 0xffff) - mi, N), dy = wrapdiff(((ob >> 16) & 0xffff) - mj, N);
+        if (dx < -1 || dx > 1 || dy < -1 || dy > 1) {
+            ovf = 1;
+            continue;
+        }
+        for (int y = 0; y < 4; ++y)
+            for (int x = 0; x < 4; ++x) acc[(dy + 1 + y) * 6 + dx + 1 + x] += kap * wg[8 * b + x] * wg[8 * b + 4 + y];
+    }
+    for (int y = 0; y < 4; ++y)
+        for (int x = 0; x < 4; ++x) acc[(1 + y) * 6 + 1 + x] -= ksum * wg[8 * m + x] * wg[8 * m + 4 + y];
+    double* out = KJ + ((size_t)c * k.M + m) * 36;
+    for (int e = 0; e < 36; ++e) out[e] = acc[e];
+    if (ovf) atomicOr(overflow, 1);
+}
+void launch_kj_patch(const IBK<double>& k, const int* adjStart, const int* adjNbr, const double* adjKap, double* KJ,
+                     int* overflow, cudaStream_t s) {
+    if (k.M == 0) return;
+    k_kj_patch<<<dim3((k.M + 127) / 128, 2), 128, 0, s>>>(k, adjStart, adjNbr, adjKap, KJ, overflow);
+}
+
+__global__ void __launch_bounds__(256) k_window_fine(IBK<double> k, const double* __restrict__ KJ,
+                                                     const int* __restrict__ tiles, int nTiles, int tx, int ty, int ntx,
+                                                     double* __restrict__ win) {
     const int slot = blockIdx.x;
     if (slot >= nTiles) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int per = tx * ty;
-    const int face = blockIdx.y * 8 + warp;
-    if (face >= 2 * per) return;
-    const int c = face / per, q = face % per;
+    const int c = blockIdx.y / WD, oy = (int)(blockIdx.y % WD) - WR;
+    const int per = tx * ty, q = threadIdx.y * tx + threadIdx.x;
     const int t = tiles[slot];
     const int N = k.N, mk = N - 1;
-    const int i = (t % ntx) * tx + q % tx, j = (t / ntx) * ty + q / tx;
-    double acc[WIN_SIZE];
-    for (int o = 0; o < WIN_SIZE; ++o) acc[o] = 0.0;
-    int ovf = 0;
+    const int i = (t % ntx) * tx + threadIdx.x, j = (t / ntx) * ty + threadIdx.y;
     const int* bs = k.binStart[c];
     const int* srt = k.sorted[c];
     const double* wg = k.wgt[c];
-    const int* bse = k.base[c];
-    for (int bb = 0; bb < k.W; ++bb)
-        for (int aa = 0; aa < k.W; ++aa) {
-            const uint32_t bin = morton((i - aa) & mk, (j - bb) & mk);
+    const double* kj = KJ + (size_t)c * k.M * 36;
+    double acc[WD];
+#pragma unroll
+    for (int e = 0; e < WD; ++e) acc[e] = 0.0;
+    for (int bo = 0; bo < 4; ++bo) {
+        const int py = oy + 1 + bo;   // patch row holding f + o for markers with f in stencil row bo
+        if (py < 0 || py > 5) continue;
+#pragma unroll
+        for (int ao = 0; ao < 4; ++ao) {
+            const uint32_t bin = morton((i - ao) & mk, (j - bo) & mk);
             const int s0 = bs[bin], e0 = bs[bin + 1];
-            for (int qq = s0 + lane; qq < e0; qq += 32) {
+            for (int qq = s0; qq < e0; ++qq) {
                 const int m = srt[qq];
-                const double jf = wg[8 * m + aa] * wg[8 * m + 4 + bb] * k.inv_h2;   // J[m, f] / h^2
-                if (jf == 0.0) continue;
-                double ksum = 0.0;
-                for (int p = adjStart[m]; p < adjStart[m + 1]; ++p) {
-                    const double kap = adjKap[p];
-                    ksum += kap;
-                    const int b = adjNbr[p];
-                    const int ob = bse[b];
-                    const int bi = ob & 0xffff, bj = (ob >> 16) & 0xffff;
-                    for (int y = 0; y < k.W; ++y) {
-                        const int oy = wrapdiff(bj + y - j, N);
-                        for (int x = 0; x < k.W; ++x) {
-                            const double wgt = wg[8 * b + x] * wg[8 * b + 4 + y];
-                            if (wgt == 0.0) continue;
-                            const int ox = wrapdiff(bi + x - i, N);
-                            if (ox < -WR || ox > WR || oy < -WR || oy > WR) {
-                                ovf = 1;
-                                continue;
-                            }
-                            acc[(oy + WR) * WD + ox + WR] += kap * jf * wgt;
-                        }
-                    }
-                }
-                // diagonal of K: -sum kappa
-                const int om = bse[m];
-                const int mi = om & 0xffff, mj = (om >> 16) & 0xffff;
-                for (int y = 0; y < k.W; ++y) {
-                    const int oy = wrapdiff(mj + y - j, N);
-                    for (int x = 0; x < k.W; ++x) {
-                        const double wgt = wg[8 * m + x] * wg[8 * m + 4 + y];
-                        if (wgt == 0.0) continue;
-                        const int ox = wrapdiff(mi + x - i, N);
-                        if (ox < -WR || ox > WR || oy < -WR || oy > WR) {
-                            ovf = 1;
-                            continue;
-                        }
-                        acc[(oy + WR) * WD + ox + WR] -= ksum * jf * wgt;
-                    }
+                const double jf = wg[8 * m + ao] * wg[8 * m + 4 + bo] * k.inv_h2;
+                const double* row = kj + (size_t)m * 36 + py * 6;
+#pragma unroll
+                for (int px = 0; px < 6; ++px) {
+                    const int e = px - 1 - ao + WR;   // ox + WR, in [0, 8]
+                    if (e >= 0 && e < WD) acc[e] += jf * row[px];
                 }
             }
         }
-    double* wout = win + ((size_t)(slot * 2 + c) * WIN_SIZE) * per;
-    for (int o = 0; o < WIN_SIZE; ++o) {
-        double v = acc[o];
-        for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-        if (lane == (o & 31)) wout[(size_t)o * per + q] = v;
     }
-    ovf = __any_sync(0xffffffffu, ovf);
-    if (ovf && lane == 0) atomicOr(overflow, 1);
+    double* wout = win + ((size_t)(slot * 2 + c) * WIN_SIZE + (size_t)(oy + WR) * WD) * per + q;
+#pragma unroll
+    for (int e = 0; e < WD; ++e) wout[(size_t)e * per] = acc[e];
 }
-void launch_window_assemble(const IBK<double>& k, const int* adjStart, const int* adjNbr, const double* adjKap,
-                            const int* tiles, int nTiles, int tx, int ty, int ntx, double* win, int* overflow,
-                            cudaStream_t s) {
+void launch_window_fine(const IBK<double>& k, const double* KJ, const int* tiles, int nTiles, int tx, int ty, int ntx,
+                        double* win, cudaStream_t s) {
     if (nTiles == 0 || k.M == 0) return;
-    const int groups = (2 * tx * ty + 7) / 8;
-    k_window_assemble<<<dim3(nTiles, groups), 256, 0, s>>>(k, adjStart, adjNbr, adjKap, tiles, nTiles, tx, ty, ntx,
-                                                           win, overflow);
+    k_window_fine<<<dim3(nTiles, 2 * WD), dim3(tx, ty), 0, s>>>(k, KJ, tiles, nTiles, tx, ty, ntx, win);
+}
+
+// Coarse levels: the Galerkin product of Sec. 3.1 applied window to window,
+//   B_c(F, G) = sum_f R_u(F, f) sum_g B_f(f, g) P_u(g, G),  R_u = P_u^T / 4,
+// one thread per (coarse face, window row OY).  For x-faces R_u takes 1/4 of the two coincident
+// fine faces and 1/8 of the four faces half a coarse cell away in x, and P_u is linear in x and
+// constant in y; for y-faces the roles of x and y swap.
+__global__ void __launch_bounds__(256) k_window_rap(const double* __restrict__ winF, const int* __restrict__ slotF,
+                                                    int Nf, int txf, int tyf, int ntxf, const int* __restrict__ tilesC,
+                                                    int nTilesC, int Nc, int txc, int tyc, int ntxc,
+                                                    double* __restrict__ winC) {
+    const int slot = blockIdx.x;
+    if (slot >= nTilesC) return;
+    const int c = blockIdx.y / WD, OY = (int)(blockIdx.y % WD) - WR;
+    const int perc = txc * tyc, perf = txf * tyf, q = threadIdx.y * txc + threadIdx.x;
+    const int t = tilesC[slot];
+    const int I = (t % ntxc) * txc + threadIdx.x, J = (t / ntxc) * tyc + threadIdx.y;
+    const int mkf = Nf - 1;
+    double acc[WD];
+    for (int e = 0; e < WD; ++e) acc[e] = 0.0;
+    for (int r = 0; r < 6; ++r) {
+        int dx, dy;
+        double wr;
+        if (c == 0) {
+            dx = r < 2 ? 0 : (r < 4 ? 1 : -1);
+            dy = r & 1;
+            wr = r < 2 ? 0.25 : 0.125;
+        } else {
+            dy = r < 2 ? 0 : (r < 4 ? 1 : -1);
+            dx = r & 1;
+            wr = r < 2 ? 0.25 : 0.125;
+        }
+        const int fx = 2 * I + dx, fy = 2 * J + dy;                 // unwrapped fine face
+        const int wx = fx & mkf, wy = fy & mkf;
+        const int sf = slotF[(wy / tyf) * ntxf + wx / txf];
+        if (sf < 0) continue;
+        const int qf = (wy % tyf) * txf + (wx % txf);
+        const double* w = winF + ((size_t)(sf * 2 + c) * WIN_SIZE) * perf + qf;
+        for (int oy = -WR; oy <= WR; ++oy) {
+            const int gy = fy + oy;
+            // targets of gy in y: constant (c == 0) or linear (c == 1)
+            int Gy[2];
+            double wyv[2];
+            int ny;
+            if (c == 0 || (gy & 1) == 0) {
+                Gy[0] = gy >> 1;
+                wyv[0] = 1.0;
+                ny = 1;
+            } else {
+                Gy[0] = (gy - 1) >> 1;
+                Gy[1] = (gy + 1) >> 1;
+                wyv[0] = wyv[1] = 0.5;
+                ny = 2;
+            }
+            double wsum = 0.0;
+            for (int a = 0; a < ny; ++a)
+                if (wrapdiff(Gy[a] - J, Nc) == OY) wsum += wyv[a];
+            if (wsum == 0.0) continue;
+            for (int ox = -WR; ox <= WR; ++ox) {
+                const double b = w[(size_t)((oy + WR) * WD + ox + WR) * perf];
+                if (b == 0.0) continue;
+                const int gx = fx + ox;
+                const double v = wr * wsum * b;
+                if (c == 1 || (gx & 1) == 0) {
+                    const int OX = wrapdiff((gx >> 1) - I, Nc);
+                    acc[OX + WR] += v;
+                } else {
+                    acc[wrapdiff(((gx - 1) >> 1) - I, Nc) + WR] += 0.5 * v;
+                    acc[wrapdiff(((gx + 1) >> 1) - I, Nc) + WR] += 0.5 * v;
+                }
+            }
+        }
+    }
+    double* wout = winC + ((size_t)(slot * 2 + c) * WIN_SIZE + (size_t)(OY + WR) * WD) * perc + q;
+    for (int e = 0; e < WD; ++e) wout[(size_t)e * perc] = acc[e];
+}
+void launch_window_rap(const double* winF, const int* slotF, int Nf, int txf, int tyf, int ntxf, const int* tilesC,
+                       int nTilesC, int Nc, int txc, int tyc, int ntxc, double* winC, cudaStream_t s) {
+    if (nTilesC == 0) return;
+    k_window_rap<<<dim3(nTilesC, 2 * WD), dim3(txc, tyc), 0, s>>>(winF, slotF, Nf, txf, tyf, ntxf, tilesC, nTilesC, Nc,
+                                                                 txc, tyc, ntxc, winC);
+}
+
+// slot of every tile of a level (-1 when the tile is not IB-active)
+__global__ void k_slot_map(const int* __restrict__ tiles, const int* __restrict__ nTiles, int* __restrict__ slotOf) {
+    const int s2 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s2 < *nTiles) slotOf[tiles[s2]] = s2;
+}
+void launch_slot_map(const int* tiles, const int* nTiles, int ntiles, int* slotOf, cudaStream_t s) {
+    cudaMemsetAsync(slotOf, 0xff, sizeof(int) * (size_t)ntiles, s);
+    k_slot_map<<<(ntiles + 255) / 256, 256, 0, s>>>(tiles, nTiles, slotOf);
 }
 
 // Patch entries of the Vanka/SC smoothers from the windows: B(f,f) and B(f, f+e), e = +x for u

@@ -2,9 +2,13 @@
 // projection) and of the coarsest-grid exact solve (dense operator, Gauss-Jordan inverse,
 // pseudo-inverse apply).  All reductions use a fixed block count and a fixed reduction tree,
 // so results are bitwise reproducible run to run.
+#include <cooperative_groups.h>
+
 #include <cmath>
 
 #include "sib_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace sib {
 
@@ -169,9 +173,11 @@ void launch_assemble_L0(int N0, double rho, double mu, double dt, const double* 
 
 // In-place Gauss-Jordan elimination with partial pivoting on Aug (n x 2n, row-major) by one
 // block; on exit the right half holds the inverse.  info = 0, or k+1 if pivot k is zero.
-__global__ void __launch_bounds__(1024) k_gauss_jordan(double* __restrict__ A, int n, int* __restrict__ info) {
+// (Fallback for coarsest grids too large for the cluster version below.)
+__global__ void __launch_bounds__(1024) k_gauss_jordan(double* __restrict__ A, int n, int* __restrict__ info,
+                                                       int* __restrict__ piv) {
     extern __shared__ double fac[];   // n factors
-    __shared__ int piv;
+    __shared__ int pivs;
     __shared__ double wv[32];
     __shared__ int wi[32];
     const int ld = 2 * n;
@@ -209,11 +215,11 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(double* __restrict__ A, i
                     b = wv[w];
                     p = wi[w];
                 }
-            piv = p;
+            pivs = p;
             if (!(b > 0.0) && *info == 0) *info = k + 1;
         }
         __syncthreads();
-        const int p = piv;
+        const int p = pivs;
         if (p != k)
             for (int c = threadIdx.x; c < ld; c += blockDim.x) {
                 const double t = A[(int64_t)k * ld + c];
@@ -228,33 +234,164 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(double* __restrict__ A, i
         for (int r = threadIdx.x; r < n; r += blockDim.x) fac[r] = (r == k) ? 0.0 : A[(int64_t)r * ld + k];
         __syncthreads();
         // eliminate column k from every other row (columns k.. of the left half, all of the right)
-        const int w = ld - k;
-        for (int64_t q = threadIdx.x; q < (int64_t)n * w; q += blockDim.x) {
-            const int r = (int)(q / w), c = k + (int)(q % w);
+        for (int r = 0; r < n; ++r) {
             const double f = fac[r];
-            if (f != 0.0) A[(int64_t)r * ld + c] -= f * A[(int64_t)k * ld + c];
+            if (f == 0.0) continue;
+            for (int c = k + threadIdx.x; c < ld; c += blockDim.x) A[(int64_t)r * ld + c] -= f * A[(int64_t)k * ld + c];
         }
         __syncthreads();
     }
+    for (int r = threadIdx.x; r < n; r += blockDim.x) piv[r] = r;
 }
-void launch_gauss_jordan(double* Aug, int n, int* info, cudaStream_t s) {
-    k_gauss_jordan<<<1, 1024, sizeof(double) * n, s>>>(Aug, n, info);
+// Gauss-Jordan elimination with partial pivoting by one thread-block cluster: block r of the
+// cluster keeps rows [r*rpc, (r+1)*rpc) of Aug in shared memory.  Pivot k: every block proposes
+// its largest |A[row][k]| among rows not yet used as pivots (ties: lower row), the cluster picks
+// the largest; every block copies the pivot row out of the owner's shared memory, and after a
+// cluster barrier eliminates column k from its rows while the owner scales the pivot row.  Rows
+// are not swapped: piv[k] records the pivot row of column k, so inverse row k = Aug[piv[k]][n:].
+__global__ void __launch_bounds__(256) k_gauss_jordan_cluster(double* __restrict__ A, int n, int rpc,
+                                                              int* __restrict__ info, int* __restrict__ piv) {
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ double sm[];
+    const int ld = 2 * n;
+    double* rows = sm;                          // rpc x ld
+    double* prow = sm + (size_t)rpc * ld;       // ld
+    double* fac = prow + ld;                    // rpc
+    __shared__ double candVal;
+    __shared__ int candRow;
+    __shared__ double pivVal;
+    __shared__ int pivRow;
+    __shared__ int usedLocal[64];
+    const int rank = (int)cluster.block_rank();
+    const int csize = (int)cluster.num_blocks();
+    const int r0 = rank * rpc;
+    for (int q = threadIdx.x; q < rpc * ld; q += blockDim.x) rows[q] = A[(size_t)r0 * ld + q];
+    if (threadIdx.x < rpc) usedLocal[threadIdx.x] = 0;
+    if (rank == 0 && threadIdx.x == 0) *info = 0;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x < 32) {
+            double best = -1.0;
+            int bi = n;
+            for (int r = threadIdx.x; r < rpc; r += 32) {
+                if (usedLocal[r]) continue;
+                const double a = fabs(rows[(size_t)r * ld + k]);
+                if (a > best) {
+                    best = a;
+                    bi = r0 + r;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (threadIdx.x == 0) {
+                candVal = best;
+                candRow = bi;
+            }
+        }
+        cluster.sync();
+        // warp 0 gathers the cluster's candidates (lane b reads block b) and broadcasts the pivot
+        if (threadIdx.x < 32) {
+            double best = -1.0;
+            int bi = n;
+            if ((int)threadIdx.x < csize) {
+                best = *cluster.map_shared_rank(&candVal, (int)threadIdx.x);
+                bi = *cluster.map_shared_rank(&candRow, (int)threadIdx.x);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (threadIdx.x == 0) {
+                pivVal = best;
+                pivRow = bi;
+            }
+        }
+        __syncthreads();
+        const double best = pivVal;
+        const int p = pivRow;
+        const int owner = p / rpc, pl = p - owner * rpc;
+        const double* src = cluster.map_shared_rank(rows, owner) + (size_t)pl * ld;
+        for (int c = k + threadIdx.x; c < ld; c += blockDim.x) prow[c] = src[c];
+        for (int r = threadIdx.x; r < rpc; r += blockDim.x) fac[r] = (r0 + r == p) ? 0.0 : rows[(size_t)r * ld + k];
+        if (rank == 0 && threadIdx.x == 0) {
+            piv[k] = p;
+            if (!(best > 0.0) && *info == 0) *info = k + 1;
+        }
+        cluster.sync();
+        const double pv = prow[k];
+        const double ipv = pv != 0.0 ? 1.0 / pv : 0.0;
+        for (int r = 0; r < rpc; ++r) {
+            if (r0 + r == p) {
+                for (int c = k + threadIdx.x; c < ld; c += blockDim.x) rows[(size_t)r * ld + c] = prow[c] * ipv;
+                if (threadIdx.x == 0) usedLocal[r] = 1;
+                continue;
+            }
+            const double f = fac[r] * ipv;
+            if (f == 0.0) continue;
+            for (int c = k + threadIdx.x; c < ld; c += blockDim.x) rows[(size_t)r * ld + c] -= f * prow[c];
+        }
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < rpc * ld; q += blockDim.x) A[(size_t)r0 * ld + q] = rows[q];
 }
 
-// Pinv = (L0 + Z Z^T)^{-1} - Z Z^T, the pseudo-inverse of the symmetric L0 whose kernel is span Z.
-__global__ void k_extract_pinv(const double* __restrict__ Aug, int n, int N0, double rho, double* __restrict__ P) {
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= (int64_t)n * n) return;
-    const int r = (int)(q / n), c = (int)(q % n);
+void launch_gauss_jordan(double* Aug, int n, int* info, int* piv, cudaStream_t s) {
+    for (int cs : {16, 8}) {
+        if (n % cs != 0) continue;
+        const int rpc = n / cs;
+        if (rpc > 64) continue;
+        const size_t smem = sizeof(double) * ((size_t)rpc * 2 * n + 2 * n + rpc);
+        if (smem > 200 * 1024) continue;
+        cudaFuncSetAttribute(k_gauss_jordan_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cs > 8) cudaFuncSetAttribute(k_gauss_jordan_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, k_gauss_jordan_cluster, &cfg) != cudaSuccess || clusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        if (cudaLaunchKernelEx(&cfg, k_gauss_jordan_cluster, Aug, n, rpc, info, piv) == cudaSuccess) return;
+        cudaGetLastError();
+    }
+    k_gauss_jordan<<<1, 1024, sizeof(double) * n, s>>>(Aug, n, info, piv);
+}
+
+// Pinv = (L0 + Z Z^T)^{-1} - Z Z^T, the pseudo-inverse of the symmetric L0 whose kernel is span Z;
+// row r of the inverse is the right half of Aug's pivot row piv[r].
+__global__ void k_extract_pinv(const double* __restrict__ Aug, const int* __restrict__ piv, int n, int N0, double rho,
+                               double* __restrict__ P) {
+    const int r = blockIdx.y;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
     const int n0 = N0 * N0;
-    double v = Aug[(int64_t)r * 2 * n + n + c];
+    double v = Aug[(int64_t)piv[r] * 2 * n + n + c];
     const int br = r / n0, bc = c / n0;
     if (br == bc && (rho == 0.0 || br == 2)) v -= 1.0 / (double)n0;
-    P[q] = v;
+    P[(int64_t)r * n + c] = v;
 }
-void launch_extract_pinv(const double* Aug, int n, int N0, double rho, double* Pinv, cudaStream_t s) {
-    const int64_t tot = (int64_t)n * n;
-    k_extract_pinv<<<(int)((tot + 255) / 256), 256, 0, s>>>(Aug, n, N0, rho, Pinv);
+void launch_extract_pinv(const double* Aug, const int* piv, int n, int N0, double rho, double* Pinv, cudaStream_t s) {
+    k_extract_pinv<<<dim3((n + 127) / 128, n), 128, 0, s>>>(Aug, piv, n, N0, rho, Pinv);
 }
 
 // x = Pinv b, one warp per row, FP64 accumulation for both precisions

@@ -100,9 +100,13 @@ void launch_patch_entries(const int* edges, const double* kappa, int E, const in
 void launch_dense_ib(const int* edges, const double* kappa, int E, const int* base0, const int* base1,
                      const double* w0, const double* w1, int N, int W, double inv_h2, double* B,
                      cudaStream_t s);
-void launch_window_assemble(const IBK<double>& k, const int* adjStart, const int* adjNbr, const double* adjKap,
-                            const int* tiles, int nTiles, int tx, int ty, int ntx, double* win, int* overflow,
-                            cudaStream_t s);
+void launch_kj_patch(const IBK<double>& k, const int* adjStart, const int* adjNbr, const double* adjKap, double* KJ,
+                     int* overflow, cudaStream_t s);
+void launch_window_fine(const IBK<double>& k, const double* KJ, const int* tiles, int nTiles, int tx, int ty, int ntx,
+                        double* win, cudaStream_t s);
+void launch_window_rap(const double* winF, const int* slotF, int Nf, int txf, int tyf, int ntxf, const int* tilesC,
+                       int nTilesC, int Nc, int txc, int tyc, int ntxc, double* winC, cudaStream_t s);
+void launch_slot_map(const int* tiles, const int* nTiles, int ntiles, int* slotOf, cudaStream_t s);
 void launch_window_patch(const double* win, const int* tiles, int nTiles, int N, int tx, int ty, int ntx, double* ibd,
                          cudaStream_t s);
 void launch_window_dense(const double* win, const int* tiles, int nTiles, int N, int tx, int ty, int ntx, double* B,
@@ -129,8 +133,8 @@ void launch_scale(double* x, const double* num_den, int idx, int64_t n, cudaStre
 void launch_block_means(const double* x, int N, int nblocks_vec, double* partials, int nblk, cudaStream_t s);
 void launch_subtract_means(double* x, int N, const double* partials, int nblk, int mask, cudaStream_t s);
 void launch_assemble_L0(int N0, double rho, double mu, double dt, const double* B, double* Aug, cudaStream_t s);
-void launch_gauss_jordan(double* Aug, int n, int* info, cudaStream_t s);
-void launch_extract_pinv(const double* Aug, int n, int N0, double rho, double* Pinv, cudaStream_t s);
+void launch_gauss_jordan(double* Aug, int n, int* info, int* piv, cudaStream_t s);
+void launch_extract_pinv(const double* Aug, const int* piv, int n, int N0, double rho, double* Pinv, cudaStream_t s);
 template <typename T> void launch_coarse_apply(const double* Pinv, int n, const T* b, T* x, cudaStream_t s);
 void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t s);
 

@@ -62,6 +62,7 @@ struct Level {
     void* win[2] = {nullptr, nullptr};
     int winSlots = 0;
     int* winOverflow = nullptr;
+    int* slotOf = nullptr;               // tile -> slot in the active-tile list, -1 if inactive
     int useWindow = 0;                   // windows valid on this level
     int applyWindow = 0;                 // the solve applies the IB operator through the windows
 };
@@ -100,12 +101,14 @@ struct sib_ctx {
     void* U[2] = {nullptr, nullptr};
     void* F[2] = {nullptr, nullptr};
     double* gradTmp = nullptr;   // 8 M: Lam, Y, KY, KL (component-major)
+    double* KJ = nullptr;        // 2 x M x 36: per-marker (K J) rows on 6 x 6 patches
     std::vector<Level> L;
     // coarsest
     double* B0 = nullptr;
     double* Aug = nullptr;
     double* Pinv = nullptr;
     int* info = nullptr;
+    int* piv = nullptr;
     int n0 = 0;
     // FGMRES
     int mcap = 0;
@@ -435,6 +438,7 @@ void alloc_level_bufs(sib_ctx* c) {
         }
         lv.tileFlag = (unsigned char*)dalloc(c, 2 * (size_t)lv.ntiles);
         lv.tiles = (int*)dalloc(c, sizeof(int) * (size_t)lv.ntiles);
+        lv.slotOf = (int*)dalloc(c, sizeof(int) * (size_t)lv.ntiles);
         lv.nTiles = (int*)dalloc(c, sizeof(int));
         lv.binStart[0] = (int*)dalloc(c, sizeof(int) * (n + 1));
         lv.binStart[1] = (int*)dalloc(c, sizeof(int) * (n + 1));
@@ -468,7 +472,7 @@ void alloc_markers(sib_ctx* c) {
     for (void* p : {(void*)c->X, (void*)c->Xc, (void*)c->edges, (void*)c->kappa, (void*)c->keys, (void*)c->sorted[0],
                     (void*)c->sorted[1], (void*)c->mkey[0], (void*)c->mkey[1], (void*)c->adjStart, (void*)c->adjNbr,
                     (void*)c->adjEid, (void*)c->deg, (void*)c->kap64, (void*)c->kap32, c->U[0], c->U[1], c->F[0],
-                    c->F[1], (void*)c->gradTmp})
+                    c->F[1], (void*)c->gradTmp, (void*)c->KJ})
         dfree(c, p);
     const int Mc = c->M > c->Mcap ? c->M : (c->Mcap > 0 ? c->Mcap : 1);
     const int Ec = c->E > c->Ecap ? c->E : (c->Ecap > 0 ? c->Ecap : 1);
@@ -496,6 +500,7 @@ void alloc_markers(sib_ctx* c) {
     c->U[1] = dalloc(c, sizeof(float) * 2 * Mc);
     c->F[1] = dalloc(c, sizeof(float) * 2 * Mc);
     c->gradTmp = (double*)dalloc(c, sizeof(double) * 8 * Mc);
+    c->KJ = (double*)dalloc(c, sizeof(double) * 2 * 36 * (size_t)Mc);
     for (int l = 0; l <= c->lmax; ++l) {
         Level& lv = c->L[l];
         for (int q = 0; q < 2; ++q) {
@@ -608,6 +613,7 @@ void setup(sib_ctx* c, cudaStream_t s) {
                 for (int q = 0; q < 2; ++q)
                     KL(c, launch_tile_flags(lv.base[q], c->M, lv.W, lv.N, lv.tx, lv.ty, lv.ntx, lv.tileFlag, s));
             KL(c, launch_tile_finish(lv.tileFlag, lv.ntx, lv.nty, lv.tiles, lv.nTiles, s));
+            KL(c, launch_slot_map(lv.tiles, lv.nTiles, lv.ntiles, lv.slotOf, s));
         }
         launch_adjacency(c->edges, c->E, c->M, c->deg, c->adjStart, c->adjNbr, c->adjEid, s);
         std::vector<int> cnt(c->lmax + 1);
@@ -637,19 +643,24 @@ void setup(sib_ctx* c, cudaStream_t s) {
     if (c->kappaDirty) {
         KL(c, launch_adj_kappa<double>(c->adjEid, c->kappa, 2 * c->E, c->kap64, s));
         KL(c, launch_adj_kappa<float>(c->adjEid, c->kappa, 2 * c->E, c->kap32, s));
-        // assembled windows of [S K J]^l on every level (FP64), overflow flags read back once
+        // assembled windows of [S K J]^l: finest level from the markers, coarser levels by the
+        // Galerkin product R_u B P_u of the next finer window; one overflow flag read back
         if (c->haveIB) {
-            for (int l = 0; l <= c->lmax; ++l) {
-                Level& lv = c->L[l];
-                CK(cudaMemsetAsync(lv.winOverflow, 0, sizeof(int), s));
-                KL(c, launch_window_assemble(ibk<double>(c, l), c->adjStart, c->adjNbr, c->kap64, lv.tiles, lv.hnTiles,
-                                             lv.tx, lv.ty, lv.ntx, (double*)lv.win[0], lv.winOverflow, s));
+            Level& lf = c->L[c->lmax];
+            CK(cudaMemsetAsync(lf.winOverflow, 0, sizeof(int), s));
+            KL(c, launch_kj_patch(ibk<double>(c, c->lmax), c->adjStart, c->adjNbr, c->kap64, c->KJ, lf.winOverflow, s));
+            KL(c, launch_window_fine(ibk<double>(c, c->lmax), c->KJ, lf.tiles, lf.hnTiles, lf.tx, lf.ty, lf.ntx,
+                                     (double*)lf.win[0], s));
+            for (int l = c->lmax - 1; l >= 0; --l) {
+                Level& F = c->L[l + 1];
+                Level& C = c->L[l];
+                KL(c, launch_window_rap((const double*)F.win[0], F.slotOf, F.N, F.tx, F.ty, F.ntx, C.tiles, C.hnTiles, C.N,
+                                        C.tx, C.ty, C.ntx, (double*)C.win[0], s));
             }
-            std::vector<int> ovf(c->lmax + 1, 0);
-            for (int l = 0; l <= c->lmax; ++l)
-                CK(cudaMemcpyAsync(&ovf[l], c->L[l].winOverflow, sizeof(int), cudaMemcpyDeviceToHost, s));
+            int ovf = 0;
+            CK(cudaMemcpyAsync(&ovf, lf.winOverflow, sizeof(int), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            for (int l = 0; l <= c->lmax; ++l) c->L[l].useWindow = ovf[l] == 0;
+            for (int l = 0; l <= c->lmax; ++l) c->L[l].useWindow = ovf == 0;
         } else {
             for (int l = 0; l <= c->lmax; ++l) c->L[l].useWindow = 0;
         }
@@ -699,8 +710,8 @@ void setup(sib_ctx* c, cudaStream_t s) {
     {
         const int n = c->n0;
         KL(c, launch_assemble_L0(c->L[0].N, c->rho, c->mu, c->dt, c->B0, c->Aug, s));
-        KL(c, launch_gauss_jordan(c->Aug, n, c->info, s));
-        KL(c, launch_extract_pinv(c->Aug, n, c->L[0].N, c->rho, c->Pinv, s));
+        KL(c, launch_gauss_jordan(c->Aug, n, c->info, c->piv, s));
+        KL(c, launch_extract_pinv(c->Aug, c->piv, n, c->L[0].N, c->rho, c->Pinv, s));
         int info = 0;
         CK(cudaMemcpyAsync(&info, c->info, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1095,6 +1106,7 @@ int sib_create(sib_ctx** out, int N, int n_min) {
         c->Aug = (double*)dalloc(c, sizeof(double) * 2 * (size_t)c->n0 * c->n0);
         c->Pinv = (double*)dalloc(c, sizeof(double) * (size_t)c->n0 * c->n0);
         c->info = (int*)dalloc(c, sizeof(int));
+        c->piv = (int*)dalloc(c, sizeof(int) * c->n0);
         c->flag = (int*)dalloc(c, sizeof(int));
         const size_t n3 = 3 * (size_t)N * N;
         c->rhs = (double*)dalloc(c, sizeof(double) * n3);
