@@ -8,6 +8,26 @@
 
 namespace sib {
 
+// IB force ([S K J]^l fld) at face (i, j) of component comp, precomputed into g.fib by the IB
+// pass for the same field; zero outside IB-active tiles.
+template <typename T>
+__device__ __forceinline__ T ibf(const GridK<T>& g, const T* __restrict__ fld, int comp, int i, int j) {
+    (void)fld;
+    if (g.tile == nullptr) return T(0);
+    const int tile = (j >> g.lgty) * g.ntx + (i >> g.lgtx);
+    if (!g.tile[tile]) return T(0);
+    return g.fib[(size_t)comp * g.N * g.N + j * g.N + i];
+}
+
+// diagonal of A_IB on a face: a0 - dt B(f,f) (B(f,f) is zero outside IB-active tiles)
+template <typename T>
+__device__ __forceinline__ T diag_face(const GridK<T>& g, int comp, int i, int j) {
+    if (g.tile == nullptr) return g.a0;
+    const int tile = (j >> g.lgty) * g.ntx + (i >> g.lgtx);
+    if (!g.tile[tile]) return g.a0;
+    return g.a0 - g.dt * g.ibd[(size_t)2 * comp * g.N * g.N + j * g.N + i];
+}
+
 // ------------------------------------------------------------------------------------------
 // Residual r = b - L x, or y = L x when b == nullptr, with
 //   (L x)_u = A u - dt [SKJ] u + G p,   (L x)_p = -D u     (Eq. matrix-impib / matrix-h-impib)
@@ -32,10 +52,8 @@ __global__ void __launch_bounds__(256) k_residual(GridK<T> g, const T* __restric
     T Au = g.a0 * uc - g.c * ((uE + uW) + (uN + uS)) + (pc - pW) * g.inv_h;
     T Av = g.a0 * vc - g.c * ((vE + vW) + (vN + vS)) + (pc - pS) * g.inv_h;
     const T Dp = -((uE - uc) + (vN - vc)) * g.inv_h;
-    if (g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x]) {
-        Au -= g.dt * g.fib[c];
-        Av -= g.dt * g.fib[n + c];
-    }
+    Au -= g.dt * ibf(g, x, 0, i, j);
+    Av -= g.dt * ibf(g, x, 1, i, j);
     if (HAS_B) {
         r[c] = b[c] - Au;
         r[n + c] = b[n + c] - Av;
@@ -65,7 +83,7 @@ void launch_residual(const GridK<T>& g, const T* x, const T* b, T* r, cudaStream
 // solved by block elimination on the pressure.  Phase 1 forms the residual on the tile plus a
 // one-cell halo, phase 2 solves the patches of the tile plus its left/bottom halo cells,
 // phase 3 adds to every face the average of the corrections of its two cells.
-template <typename T>
+template <typename T, bool ZERO>
 __global__ void __launch_bounds__(256) k_vanka(GridK<T> g, const T* __restrict__ x, const T* __restrict__ b,
                                                T* __restrict__ xo) {
     __shared__ T sru[(TY + 2) * (TX + 2)];
@@ -83,14 +101,20 @@ __global__ void __launch_bounds__(256) k_vanka(GridK<T> g, const T* __restrict__
     const int RW = tx + 2, RH = ty + 2;
     for (int q = tid; q < RW * RH; q += nth) {
         const int i = (i0 - 1 + q % RW) & m, j = (j0 - 1 + q / RW) & m;
-        const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m;
         const int c = j * N + i;
+        if (ZERO) {   // x = 0: the residual is b
+            sru[q] = b[c];
+            srv[q] = b[n + c];
+            srp[q] = b[2 * n + c];
+            continue;
+        }
+        const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m;
         const T uc = u[c], vc = v[c], pc = p[c];
         const T uE = u[j * N + ip], uW = u[j * N + im], uN = u[jp * N + i], uS = u[jm * N + i];
         const T vE = v[j * N + ip], vW = v[j * N + im], vN = v[jp * N + i], vS = v[jm * N + i];
         T Au = g.a0 * uc - g.c * ((uE + uW) + (uN + uS)) + (pc - p[j * N + im]) * g.inv_h;
         T Av = g.a0 * vc - g.c * ((vE + vW) + (vN + vS)) + (pc - p[jm * N + i]) * g.inv_h;
-        if (act) {
+        if (act) {   // fib holds [S K J] x (zero in inactive tiles; the flags are dilated by one tile)
             Au -= g.dt * g.fib[c];
             Av -= g.dt * g.fib[n + c];
         }
@@ -137,15 +161,94 @@ __global__ void __launch_bounds__(256) k_vanka(GridK<T> g, const T* __restrict__
     const int c = (j0 + cj) * N + (i0 + ci);
     const int pc = (cj + 1) * PW + ci + 1, pl = (cj + 1) * PW + ci, pb = cj * PW + ci + 1;
     const T hw = T(0.5) * g.omega;
-    xo[c] = u[c] + hw * (sd[0][pc] + sd[1][pl]);
-    xo[n + c] = v[c] + hw * (sd[2][pc] + sd[3][pb]);
-    xo[2 * n + c] = p[c] + g.omega * sd[4][pc];
+    if (ZERO) {
+        xo[c] = hw * (sd[0][pc] + sd[1][pl]);
+        xo[n + c] = hw * (sd[2][pc] + sd[3][pb]);
+        xo[2 * n + c] = g.omega * sd[4][pc];
+    } else {
+        xo[c] = u[c] + hw * (sd[0][pc] + sd[1][pl]);
+        xo[n + c] = v[c] + hw * (sd[2][pc] + sd[3][pb]);
+        xo[2 * n + c] = p[c] + g.omega * sd[4][pc];
+    }
 }
 
 template <typename T>
 void launch_vanka(const GridK<T>& g, const T* x, const T* b, T* xo, cudaStream_t s) {
     dim3 blk(g.tx, g.ty), grd(g.N / g.tx, g.N / g.ty);
-    k_vanka<T><<<grd, blk, 0, s>>>(g, x, b, xo);
+    k_vanka<T, false><<<grd, blk, 0, s>>>(g, x, b, xo);
+}
+// the first sweep from a zero initial guess (Alg. 1 recursion): no reads of x, residual = b
+template <typename T>
+void launch_vanka_zero(const GridK<T>& g, const T* b, T* xo, cudaStream_t s) {
+    dim3 blk(g.tx, g.ty), grd(g.N / g.tx, g.N / g.ty);
+    k_vanka<T, true><<<grd, blk, 0, s>>>(g, b, b, xo);   // x is never read
+}
+
+// ------------------------------------------------------------------------------------------
+// Fine residual and its restriction in one pass (Sec. 3.2, Alg. 1): one thread per coarse cell
+// evaluates the sixteen fine residuals that R = diag(P_u^T / 4, P_v^T / 4, average) combines.
+template <typename T>
+__device__ __forceinline__ T res_u(const GridK<T>& g, const T* __restrict__ x, const T* __restrict__ b, int i, int j) {
+    const int N = g.N, m = N - 1;
+    const T* u = x;
+    const T* p = x + 2 * N * N;
+    i &= m;
+    j &= m;
+    const int c = j * N + i;
+    T Au = g.a0 * u[c] - g.c * ((u[j * N + ((i + 1) & m)] + u[j * N + ((i - 1) & m)]) +
+                                (u[((j + 1) & m) * N + i] + u[((j - 1) & m) * N + i])) +
+           (p[c] - p[j * N + ((i - 1) & m)]) * g.inv_h;
+    Au -= g.dt * ibf(g, x, 0, i, j);
+    return b[c] - Au;
+}
+template <typename T>
+__device__ __forceinline__ T res_v(const GridK<T>& g, const T* __restrict__ x, const T* __restrict__ b, int i, int j) {
+    const int N = g.N, n = N * N, m = N - 1;
+    const T* v = x + n;
+    const T* p = x + 2 * n;
+    i &= m;
+    j &= m;
+    const int c = j * N + i;
+    T Av = g.a0 * v[c] - g.c * ((v[j * N + ((i + 1) & m)] + v[j * N + ((i - 1) & m)]) +
+                                (v[((j + 1) & m) * N + i] + v[((j - 1) & m) * N + i])) +
+           (p[c] - p[((j - 1) & m) * N + i]) * g.inv_h;
+    Av -= g.dt * ibf(g, x, 1, i, j);
+    return b[n + c] - Av;
+}
+template <typename T>
+__device__ __forceinline__ T res_p(const GridK<T>& g, const T* __restrict__ x, const T* __restrict__ b, int i, int j) {
+    const int N = g.N, n = N * N, m = N - 1;
+    i &= m;
+    j &= m;
+    const int c = j * N + i;
+    return b[2 * n + c] + ((x[j * N + ((i + 1) & m)] - x[c]) + (x[n + ((j + 1) & m) * N + i] - x[n + c])) * g.inv_h;
+}
+
+template <typename T>
+__global__ void k_residual_restrict(GridK<T> g, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ bc) {
+    const int Nc = g.N / 2;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    if (I >= Nc || J >= Nc) return;
+    const int i = 2 * I, j = 2 * J;
+    const T su = (res_u(g, x, b, i, j) + res_u(g, x, b, i, j + 1)) +
+                 T(0.5) * ((res_u(g, x, b, i + 1, j) + res_u(g, x, b, i + 1, j + 1)) +
+                           (res_u(g, x, b, i - 1, j) + res_u(g, x, b, i - 1, j + 1)));
+    const T sv = (res_v(g, x, b, i, j) + res_v(g, x, b, i + 1, j)) +
+                 T(0.5) * ((res_v(g, x, b, i, j + 1) + res_v(g, x, b, i + 1, j + 1)) +
+                           (res_v(g, x, b, i, j - 1) + res_v(g, x, b, i + 1, j - 1)));
+    const T sp = (res_p(g, x, b, i, j) + res_p(g, x, b, i + 1, j)) + (res_p(g, x, b, i, j + 1) + res_p(g, x, b, i + 1, j + 1));
+    const int nc = Nc * Nc, c = J * Nc + I;
+    bc[c] = T(0.25) * su;
+    bc[nc + c] = T(0.25) * sv;
+    bc[2 * nc + c] = T(0.25) * sp;
+}
+template <typename T>
+void launch_residual_restrict(const GridK<T>& g, const T* x, const T* b, T* bc, cudaStream_t s) {
+    const int Nc = g.N / 2;
+    dim3 blk(Nc < 32 ? Nc : 32, Nc < 8 ? Nc : 8);
+    dim3 grd((Nc + blk.x - 1) / blk.x, (Nc + blk.y - 1) / blk.y);
+    k_residual_restrict<T><<<grd, blk, 0, s>>>(g, x, b, bc);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -272,12 +375,11 @@ __global__ void k_apply_AIB(GridK<T> g, const T* __restrict__ x, T* __restrict__
     const int N = g.N, n = N * N, m = N - 1;
     const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
     const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m;
-    const bool act = g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x];
     const int c = j * N + i;
     for (int comp = 0; comp < 2; ++comp) {
         const T* u = x + comp * n;
         T a = g.a0 * u[c] - g.c * ((u[j * N + ip] + u[j * N + im]) + (u[jp * N + i] + u[jm * N + i]));
-        if (act) a -= g.dt * g.fib[comp * n + c];
+        a -= g.dt * ibf(g, x, comp, i, j);
         y[comp * n + c] = a;
     }
 }
@@ -350,6 +452,208 @@ void launch_cheb_update(const T* dinvr, T* d, T* x, T ra, T rb, int64_t n, cudaS
 }
 
 // ------------------------------------------------------------------------------------------
+// Schur-complement sweep with two Chebyshev iterations in each inner solve, fused into six
+// kernels (Eq. approx-fact-Stokes-IB):
+//   r = b - L x;  y = At^{-1} r_u;  s = r_p + D y;  dp = Mt^{-1} s;  yy = At^{-1} G dp;
+//   xo = x + omega (y - yy, dp)
+// with At^{-1} q = (1 + c1) d0 + c2 DA^{-1}(q - A_IB d0), d0 = DA^{-1} q / theta_A, and
+// Mt^{-1} s = (1 + c1) e0 + c2 DM^{-1}(s - D At^{-1} G e0), e0 = DM^{-1} s / theta_M, where DA is
+// diag(A_IB) and DM = diag(D DA^{-1} G).  A kernel that needs G of a cell-centred quantity
+// recomputes that quantity on the two neighbouring cells instead of synchronising.
+template <typename T>
+__device__ __forceinline__ T Aib(const GridK<T>& g, const T* __restrict__ d, int comp, int i, int j) {
+    const int N = g.N, m = N - 1;
+    const T* dc = d + (size_t)comp * N * N;
+    const T a = g.a0 * dc[j * N + i] - g.c * ((dc[j * N + ((i + 1) & m)] + dc[j * N + ((i - 1) & m)]) +
+                                             (dc[((j + 1) & m) * N + i] + dc[((j - 1) & m) * N + i]));
+    return a - g.dt * ibf(g, d, comp, i, j);
+}
+template <typename T>
+__device__ __forceinline__ T divg(const GridK<T>& g, const T* __restrict__ w, int i, int j) {
+    const int N = g.N, m = N - 1;
+    i &= m;
+    j &= m;
+    return ((w[j * N + ((i + 1) & m)] - w[j * N + i]) + (w[N * N + ((j + 1) & m) * N + i] - w[N * N + j * N + i])) *
+           g.inv_h;
+}
+template <typename T>
+__device__ __forceinline__ T dM_inv(const GridK<T>& g, int i, int j) {
+    const int m = g.N - 1;
+    i &= m;
+    j &= m;
+    const T s = T(1) / diag_face(g, 0, i, j) + T(1) / diag_face(g, 0, (i + 1) & m, j) + T(1) / diag_face(g, 1, i, j) +
+                T(1) / diag_face(g, 1, i, (j + 1) & m);
+    return T(1) / (-s * g.inv_h * g.inv_h);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sc_start(GridK<T> g, Cheb2<T> ka, const T* __restrict__ x,
+                                                  const T* __restrict__ b, T* __restrict__ r, T* __restrict__ d) {
+    const int N = g.N, n = N * N;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const int c = j * N + i;
+    const T ru = res_u(g, x, b, i, j), rv = res_v(g, x, b, i, j);
+    r[c] = ru;
+    r[n + c] = rv;
+    r[2 * n + c] = res_p(g, x, b, i, j);
+    d[c] = ka.inv_theta * ru * g.dinv[c];
+    d[n + c] = ka.inv_theta * rv * g.dinv[n + c];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sc_chebA(GridK<T> g, Cheb2<T> ka, const T* __restrict__ q,
+                                                  const T* __restrict__ d, T* __restrict__ y) {
+    const int N = g.N, n = N * N;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const int c = j * N + i;
+    for (int comp = 0; comp < 2; ++comp) {
+        const int f = comp * n + c;
+        const T rr = q[f] - Aib(g, d, comp, i, j);
+        y[f] = ka.one_c1 * d[f] + ka.c2 * rr * g.dinv[f];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sc_mstart(GridK<T> g, Cheb2<T> ka, Cheb2<T> km, const T* __restrict__ rp,
+                                                   const T* __restrict__ y, T* __restrict__ sv, T* __restrict__ dMo,
+                                                   T* __restrict__ gq, T* __restrict__ dA) {
+    const int N = g.N, n = N * N, m = N - 1;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const int c = j * N + i;
+    auto e0 = [&](int ii, int jj, T* sOut) {
+        ii &= m;
+        jj &= m;
+        const T sval = rp[jj * N + ii] + divg(g, y, ii, jj);
+        if (sOut) *sOut = sval;
+        return km.inv_theta * sval * g.dinv[2 * n + jj * N + ii];
+    };
+    T sc;
+    const T ec = e0(i, j, &sc), ew = e0(i - 1, j, nullptr), es = e0(i, j - 1, nullptr);
+    sv[c] = sc;
+    dMo[c] = ec;
+    const T gu = (ec - ew) * g.inv_h, gv = (ec - es) * g.inv_h;
+    gq[c] = gu;
+    gq[n + c] = gv;
+    dA[c] = ka.inv_theta * gu * g.dinv[c];
+    dA[n + c] = ka.inv_theta * gv * g.dinv[n + c];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sc_mfinish(GridK<T> g, Cheb2<T> ka, Cheb2<T> km, const T* __restrict__ sv,
+                                                    const T* __restrict__ dM, const T* __restrict__ ya,
+                                                    T* __restrict__ dp, T* __restrict__ gq, T* __restrict__ dA) {
+    const int N = g.N, n = N * N, m = N - 1;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const int c = j * N + i;
+    auto pval = [&](int ii, int jj) {
+        ii &= m;
+        jj &= m;
+        const int cc = jj * N + ii;
+        return km.one_c1 * dM[cc] + km.c2 * (sv[cc] - divg(g, ya, ii, jj)) * g.dinv[2 * n + cc];
+    };
+    const T pc = pval(i, j), pw = pval(i - 1, j), ps = pval(i, j - 1);
+    dp[c] = pc;
+    const T gu = (pc - pw) * g.inv_h, gv = (pc - ps) * g.inv_h;
+    gq[c] = gu;
+    gq[n + c] = gv;
+    dA[c] = ka.inv_theta * gu * g.dinv[c];
+    dA[n + c] = ka.inv_theta * gv * g.dinv[n + c];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sc_finish(GridK<T> g, Cheb2<T> ka, const T* __restrict__ x,
+                                                   const T* __restrict__ y, const T* __restrict__ gq,
+                                                   const T* __restrict__ dA, const T* __restrict__ dp,
+                                                   T* __restrict__ xo) {
+    const int N = g.N, n = N * N;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const int c = j * N + i;
+    for (int comp = 0; comp < 2; ++comp) {
+        const int f = comp * n + c;
+        const T yy = ka.one_c1 * dA[f] + ka.c2 * (gq[f] - Aib(g, dA, comp, i, j)) * g.dinv[f];
+        xo[f] = x[f] + g.omega * (y[f] - yy);
+    }
+    xo[2 * n + c] = x[2 * n + c] + g.omega * dp[c];
+}
+
+// power iterations: w = DA^{-1} A_IB v; gq = G v, dA = DA^{-1} gq / theta_A; w = DM^{-1} D ya
+template <typename T>
+__global__ void k_power_A(GridK<T> g, const T* __restrict__ v, T* __restrict__ w) {
+    const int N = g.N, n = N * N;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const int c = j * N + i;
+    for (int comp = 0; comp < 2; ++comp) w[comp * n + c] = Aib(g, v, comp, i, j) * g.dinv[comp * n + c];
+}
+template <typename T>
+__global__ void k_power_Mstart(GridK<T> g, Cheb2<T> ka, const T* __restrict__ v, T* __restrict__ gq,
+                               T* __restrict__ dA) {
+    const int N = g.N, n = N * N, m = N - 1;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const int c = j * N + i;
+    const T gu = (v[c] - v[j * N + ((i - 1) & m)]) * g.inv_h, gv = (v[c] - v[((j - 1) & m) * N + i]) * g.inv_h;
+    gq[c] = gu;
+    gq[n + c] = gv;
+    dA[c] = ka.inv_theta * gu * g.dinv[c];
+    dA[n + c] = ka.inv_theta * gv * g.dinv[n + c];
+}
+template <typename T>
+__global__ void k_power_Mfinish(GridK<T> g, const T* __restrict__ ya, T* __restrict__ w) {
+    const int N = g.N;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    w[j * N + i] = divg(g, ya, i, j) * g.dinv[2 * N * N + j * N + i];
+}
+
+// set-up of the SC diagonals (FP64): 1/diag(A_IB) on both face sets and 1/diag(M^) on cells
+__global__ void k_sc_diag(GridK<double> g, double* __restrict__ dinv) {
+    const int N = g.N, n = N * N;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const int c = j * N + i;
+    dinv[c] = 1.0 / diag_face(g, 0, i, j);
+    dinv[n + c] = 1.0 / diag_face(g, 1, i, j);
+    dinv[2 * n + c] = dM_inv(g, i, j);
+}
+void launch_sc_diag(const GridK<double>& g, double* dinv, cudaStream_t s) {
+    k_sc_diag<<<dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s>>>(g, dinv);
+}
+
+#define SIB_GRID_LAUNCH(kern, ...) kern<T><<<dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s>>>(__VA_ARGS__)
+template <typename T>
+void launch_sc_start(const GridK<T>& g, Cheb2<T> ka, const T* x, const T* b, T* r, T* d, cudaStream_t s) {
+    SIB_GRID_LAUNCH(k_sc_start, g, ka, x, b, r, d);
+}
+template <typename T>
+void launch_sc_chebA(const GridK<T>& g, Cheb2<T> ka, const T* q, const T* d, T* y, cudaStream_t s) {
+    SIB_GRID_LAUNCH(k_sc_chebA, g, ka, q, d, y);
+}
+template <typename T>
+void launch_sc_mstart(const GridK<T>& g, Cheb2<T> ka, Cheb2<T> km, const T* rp, const T* y, T* sv, T* dM, T* gq, T* dA,
+                      cudaStream_t s) {
+    SIB_GRID_LAUNCH(k_sc_mstart, g, ka, km, rp, y, sv, dM, gq, dA);
+}
+template <typename T>
+void launch_sc_mfinish(const GridK<T>& g, Cheb2<T> ka, Cheb2<T> km, const T* sv, const T* dM, const T* ya, T* dp,
+                       T* gq, T* dA, cudaStream_t s) {
+    SIB_GRID_LAUNCH(k_sc_mfinish, g, ka, km, sv, dM, ya, dp, gq, dA);
+}
+template <typename T>
+void launch_sc_finish(const GridK<T>& g, Cheb2<T> ka, const T* x, const T* y, const T* gq, const T* dA, const T* dp,
+                      T* xo, cudaStream_t s) {
+    SIB_GRID_LAUNCH(k_sc_finish, g, ka, x, y, gq, dA, dp, xo);
+}
+template <typename T>
+void launch_power_A(const GridK<T>& g, const T* v, T* w, cudaStream_t s) {
+    SIB_GRID_LAUNCH(k_power_A, g, v, w);
+}
+template <typename T>
+void launch_power_Mstart(const GridK<T>& g, Cheb2<T> ka, const T* v, T* gq, T* dA, cudaStream_t s) {
+    SIB_GRID_LAUNCH(k_power_Mstart, g, ka, v, gq, dA);
+}
+template <typename T>
+void launch_power_Mfinish(const GridK<T>& g, const T* ya, T* w, cudaStream_t s) {
+    SIB_GRID_LAUNCH(k_power_Mfinish, g, ya, w);
+}
+
+// ------------------------------------------------------------------------------------------
 #define SIB_INST(T)                                                                                        \
     template void launch_residual<T>(const GridK<T>&, const T*, const T*, T*, cudaStream_t);              \
     template void launch_vanka<T>(const GridK<T>&, const T*, const T*, T*, cudaStream_t);                 \
@@ -361,7 +665,20 @@ void launch_cheb_update(const T* dinvr, T* d, T* x, T ra, T rb, int64_t n, cudaS
     template void launch_gradient<T>(const GridK<T>&, const T*, T*, cudaStream_t);                        \
     template void launch_divergence<T>(const GridK<T>&, const T*, T*, cudaStream_t);                      \
     template void launch_jacobi_M<T>(const GridK<T>&, const T*, T*, T, cudaStream_t);                     \
-    template void launch_cheb_update<T>(const T*, T*, T*, T, T, int64_t, cudaStream_t);
+    template void launch_cheb_update<T>(const T*, T*, T*, T, T, int64_t, cudaStream_t);                   \
+    template void launch_vanka_zero<T>(const GridK<T>&, const T*, T*, cudaStream_t);                       \
+    template void launch_residual_restrict<T>(const GridK<T>&, const T*, const T*, T*, cudaStream_t);       \
+    template void launch_sc_start<T>(const GridK<T>&, Cheb2<T>, const T*, const T*, T*, T*, cudaStream_t);   \
+    template void launch_sc_chebA<T>(const GridK<T>&, Cheb2<T>, const T*, const T*, T*, cudaStream_t);       \
+    template void launch_sc_mstart<T>(const GridK<T>&, Cheb2<T>, Cheb2<T>, const T*, const T*, T*, T*, T*, T*, \
+                                      cudaStream_t);                                                         \
+    template void launch_sc_mfinish<T>(const GridK<T>&, Cheb2<T>, Cheb2<T>, const T*, const T*, const T*, T*, \
+                                       T*, T*, cudaStream_t);                                                \
+    template void launch_sc_finish<T>(const GridK<T>&, Cheb2<T>, const T*, const T*, const T*, const T*,     \
+                                      const T*, T*, cudaStream_t);                                           \
+    template void launch_power_A<T>(const GridK<T>&, const T*, T*, cudaStream_t);                          \
+    template void launch_power_Mstart<T>(const GridK<T>&, Cheb2<T>, const T*, T*, T*, cudaStream_t);       \
+    template void launch_power_Mfinish<T>(const GridK<T>&, const T*, T*, cudaStream_t);
 SIB_INST(float)
 SIB_INST(double)
 template void launch_convert<double, float>(const double*, float*, int64_t, cudaStream_t);

@@ -837,36 +837,46 @@ void launch_window_dense(const double* win, const int* tiles, int nTiles, int N,
     k_window_dense<<<(rows + 127) / 128, 128, 0, s>>>(win, tiles, nTiles, N, tx, ty, ntx, B);
 }
 
-// Apply: f^c(face) = sum_o B(face, face + o) u^c(face + o), one block per IB-active tile.
+// Apply: f^c(face) = sum_o B(face, face + o) u^c(face + o) on the IB-active tiles.  A block
+// takes 32 consecutive faces of one tile and component; thread (x, oy) sums window row oy of face
+// x (nine terms), and the nine row sums are added in a fixed order.
 template <typename T>
-__global__ void __launch_bounds__(256) k_ib_window(const T* __restrict__ win, const int* __restrict__ tiles,
-                                                   const int* __restrict__ nTiles, int N, int tx, int ty, int ntx,
-                                                   const T* __restrict__ u, T* __restrict__ f) {
+__global__ void __launch_bounds__(32 * WD) k_ib_window(const T* __restrict__ win, const int* __restrict__ tiles,
+                                                       const int* __restrict__ nTiles, int N, int tx, int ty, int ntx,
+                                                       const T* __restrict__ u, T* __restrict__ f) {
+    __shared__ T part[WD][32];
     const int slot = blockIdx.x;
     if (slot >= *nTiles) return;
-    const int per = tx * ty, q = threadIdx.y * tx + threadIdx.x;
+    const int per = tx * ty;
+    const int q = blockIdx.y * 32 + threadIdx.x;
+    const int c = blockIdx.z;
+    const int oy = (int)threadIdx.y - WR;
+    const bool live = q < per;
     const int t = tiles[slot];
-    const int i = (t % ntx) * tx + threadIdx.x, j = (t / ntx) * ty + threadIdx.y;
+    const int i = (t % ntx) * tx + (live ? q % tx : 0), j = (t / ntx) * ty + (live ? q / tx : 0);
     const int n = N * N, mk = N - 1;
-    for (int c = 0; c < 2; ++c) {
-        const T* w = win + ((size_t)(slot * 2 + c) * WIN_SIZE) * per + q;
-        const T* uc = u + (size_t)c * n;
-        T acc = T(0);
+    T acc = T(0);
+    if (live) {
+        const T* w = win + ((size_t)(slot * 2 + c) * WIN_SIZE + (size_t)threadIdx.y * WD) * per + q;
+        const T* row = u + (size_t)c * n + (size_t)((j + oy) & mk) * N;
 #pragma unroll
-        for (int oy = -WR; oy <= WR; ++oy) {
-            const int row = ((j + oy) & mk) * N;
+        for (int ox = -WR; ox <= WR; ++ox) acc += w[(size_t)(ox + WR) * per] * row[(i + ox) & mk];
+    }
+    part[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && live) {
+        T sum = T(0);
 #pragma unroll
-            for (int ox = -WR; ox <= WR; ++ox)
-                acc += w[(size_t)((oy + WR) * WD + ox + WR) * per] * uc[row + ((i + ox) & mk)];
-        }
-        f[(size_t)c * n + j * N + i] = acc;
+        for (int r = 0; r < WD; ++r) sum += part[r][threadIdx.x];
+        f[(size_t)c * n + j * N + i] = sum;
     }
 }
 template <typename T>
 void launch_ib_window(const T* win, const int* tiles, const int* nTiles, int maxTiles, int N, int tx, int ty, int ntx,
                       const T* u, T* f, cudaStream_t s) {
     if (maxTiles == 0) return;
-    k_ib_window<T><<<maxTiles, dim3(tx, ty), 0, s>>>(win, tiles, nTiles, N, tx, ty, ntx, u, f);
+    const int groups = (tx * ty + 31) / 32;
+    k_ib_window<T><<<dim3(maxTiles, groups, 2), dim3(32, WD), 0, s>>>(win, tiles, nTiles, N, tx, ty, ntx, u, f);
 }
 template void launch_ib_window<float>(const float*, const int*, const int*, int, int, int, int, int, const float*,
                                       float*, cudaStream_t);

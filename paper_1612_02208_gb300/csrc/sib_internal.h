@@ -37,7 +37,7 @@ __host__ __device__ inline uint32_t morton(uint32_t i, uint32_t j) { return part
 // Arguments of the MAC-grid stencil kernels on one level.
 template <typename T>
 struct GridK {
-    int N, tx, ty, ntx;
+    int N, tx, ty, ntx, lgtx, lgty;
     T inv_h;       // 1/h
     T a0;          // rho/dt + 4 mu / h^2   (diagonal of A)
     T c;           // mu / h^2              (off-diagonal magnitude of A)
@@ -46,6 +46,14 @@ struct GridK {
     const T* fib;                    // [S K J]^l u on the faces (2 n), valid where the tile is active
     const T* ibd;                    // 4 n: B(f,f) on u faces, B(u_ij,u_i+1j), B(f,f) on v, B(v_ij,v_ij+1)
     const unsigned char* tile;       // per-tile IB flag (dilated by one tile), may be null
+    const T* dinv;                   // SC: 1/diag(A_IB) on u and v faces, 1/diag(D diag(A_IB)^-1 G) on cells
+};
+
+// Chebyshev coefficients of two iterations from x0 = 0 on [lo, hi] lambda_max:
+//   x2 = (1 + c1) d0 + c2 Dinv (q - Op d0),  d0 = Dinv q / theta
+template <typename T>
+struct Cheb2 {
+    T inv_theta, one_c1, c2;
 };
 
 // Arguments of the marker kernels on one level (per velocity component c = 0, 1).
@@ -75,6 +83,24 @@ template <typename T> void launch_gradient(const GridK<T>& g, const T* p, T* gu,
 template <typename T> void launch_divergence(const GridK<T>& g, const T* u, T* d, cudaStream_t s);
 template <typename T> void launch_jacobi_M(const GridK<T>& g, const T* r, T* z, T scale, cudaStream_t s);
 template <typename T> void launch_cheb_update(const T* dinvr, T* d, T* x, T ra, T rb, int64_t n, cudaStream_t s);
+// fused kernels
+template <typename T> void launch_vanka_zero(const GridK<T>& g, const T* b, T* xo, cudaStream_t s);
+template <typename T> void launch_residual_restrict(const GridK<T>& g, const T* x, const T* b, T* bc, cudaStream_t s);
+template <typename T> void launch_sc_start(const GridK<T>& g, Cheb2<T> ka, const T* x, const T* b, T* r, T* d,
+                                           cudaStream_t s);
+template <typename T> void launch_sc_chebA(const GridK<T>& g, Cheb2<T> ka, const T* q, const T* d, T* y,
+                                           cudaStream_t s);
+template <typename T> void launch_sc_mstart(const GridK<T>& g, Cheb2<T> ka, Cheb2<T> km, const T* rp, const T* y,
+                                            T* sv, T* dM, T* gq, T* dA, cudaStream_t s);
+template <typename T> void launch_sc_mfinish(const GridK<T>& g, Cheb2<T> ka, Cheb2<T> km, const T* sv, const T* dM,
+                                             const T* ya, T* dp, T* gq, T* dA, cudaStream_t s);
+template <typename T> void launch_sc_finish(const GridK<T>& g, Cheb2<T> ka, const T* x, const T* y, const T* gq,
+                                            const T* dA, const T* dp, T* xo, cudaStream_t s);
+void launch_sc_diag(const GridK<double>& g, double* dinv, cudaStream_t s);
+template <typename T> void launch_power_A(const GridK<T>& g, const T* v, T* w, cudaStream_t s);
+template <typename T> void launch_power_Mstart(const GridK<T>& g, Cheb2<T> ka, const T* v, T* gq, T* dA,
+                                               cudaStream_t s);
+template <typename T> void launch_power_Mfinish(const GridK<T>& g, const T* ya, T* w, cudaStream_t s);
 
 // launchers (kernels_ib.cu)
 void launch_stencils(const double* X, int M, int Nf, int lmax, int** base, double** w64, float** w32,

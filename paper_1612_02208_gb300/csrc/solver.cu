@@ -44,6 +44,7 @@ struct LevelBuf {
     // Schur-complement smoother temporaries: 8 velocity-sized, 6 pressure-sized
     void* tv[8] = {};
     void* tp[6] = {};
+    void* dinv = nullptr;   // 3 n: SC diagonals
 };
 
 struct Level {
@@ -195,6 +196,13 @@ GridK<T> gridk(sib_ctx* c, int l) {
     g.fib = (const T*)lv.p[pi].fib;
     g.ibd = (const T*)lv.p[pi].ibd;
     g.tile = c->haveIB ? lv.tileFlag + lv.ntiles : nullptr;
+    int lg = 0;
+    while ((1 << lg) < lv.tx) ++lg;
+    g.lgtx = lg;
+    lg = 0;
+    while ((1 << lg) < lv.ty) ++lg;
+    g.lgty = lg;
+    g.dinv = (const T*)lv.p[pi].dinv;
     return g;
 }
 
@@ -223,6 +231,11 @@ const T* kapp(sib_ctx* c) {
         return c->kap64;
     else
         return c->kap32;
+}
+
+void dot_into(sib_ctx* c, const double* x, const double* y, int64_t n, double* dst, cudaStream_t s) {
+    KL(c, launch_dot_partials(x, y, n, c->part, NBLK, s));
+    KL(c, launch_reduce_partials(c->part, 1, NBLK, dst, s));
 }
 
 // f = [S K J]^l u (velocity part of x), written into the level's fib (only IB-active tiles)
@@ -325,9 +338,57 @@ void cheb_M(sib_ctx* c, int l, const T* q, T* out, cudaStream_t s) {
     }
 }
 
+template <typename T>
+Cheb2<T> cheb2(double lam, double lo, double hi) {
+    const ChebCoef k = cheb_coef(lam, lo, hi);
+    const double rho0 = 1.0 / k.sigma, rho1 = 1.0 / (2.0 * k.sigma - rho0);
+    Cheb2<T> r;
+    r.inv_theta = (T)(1.0 / k.theta);
+    r.one_c1 = (T)(1.0 + rho1 * rho0);
+    r.c2 = (T)(2.0 * rho1 / k.delta);
+    return r;
+}
+
+// fused sweep for two Chebyshev iterations per inner solve (6 kernels, plus IB passes on levels
+// that use the marker path)
+template <typename T>
+void sc_sweep_fused(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream_t s) {
+    Level& lv = c->L[l];
+    const int pi = Prec<T>::id;
+    const int64_t nv = 2LL * lv.N * lv.N;
+    GridK<T> g = gridk<T>(c, l);
+    const Cheb2<T> ka = cheb2<T>(lv.lamA, c->opts.cheb_lo, c->opts.cheb_hi);
+    const Cheb2<T> km = cheb2<T>(lv.lamM, c->opts.cheb_lo, c->opts.cheb_hi);
+    T* r = (T*)lv.p[pi].r;
+    T* y = (T*)lv.p[pi].tv[6];
+    T* d = (T*)lv.p[pi].tv[3];
+    T* gq = (T*)lv.p[pi].tv[4];
+    T* ya = (T*)lv.p[pi].tv[5];
+    T* gq2 = (T*)lv.p[pi].tv[0];
+    T* dA2 = (T*)lv.p[pi].tv[1];
+    T* dA = (T*)lv.p[pi].tv[2];
+    T* sv = (T*)lv.p[pi].tp[0];
+    T* dp = (T*)lv.p[pi].tp[1];
+    T* dM = (T*)lv.p[pi].tp[2];
+    ib_apply<T>(c, l, x, s);
+    KL(c, launch_sc_start<T>(g, ka, x, b, r, d, s));
+    ib_apply<T>(c, l, d, s);
+    KL(c, launch_sc_chebA<T>(g, ka, r, d, y, s));
+    KL(c, launch_sc_mstart<T>(g, ka, km, r + nv, y, sv, dM, gq, dA, s));
+    ib_apply<T>(c, l, dA, s);
+    KL(c, launch_sc_chebA<T>(g, ka, gq, dA, ya, s));
+    KL(c, launch_sc_mfinish<T>(g, ka, km, sv, dM, ya, dp, gq2, dA2, s));
+    ib_apply<T>(c, l, dA2, s);
+    KL(c, launch_sc_finish<T>(g, ka, x, y, gq2, dA2, dp, xo, s));
+}
+
 // xo = x + omega * Lt^{-1} (b - L x)
 template <typename T>
 void sc_sweep(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream_t s) {
+    if (c->opts.cheb_iters == 2) {
+        sc_sweep_fused<T>(c, l, x, b, xo, s);
+        return;
+    }
     Level& lv = c->L[l];
     const int pi = Prec<T>::id;
     const int64_t np = (int64_t)lv.N * lv.N, nv = 2 * np;
@@ -375,13 +436,20 @@ T* vcycle_level(sib_ctx* c, int l, cudaStream_t s) {
     T* x = (T*)lv.p[pi].x;
     T* xt = (T*)lv.p[pi].xt;
     const T* b = (const T*)lv.p[pi].b;
-    CK(cudaMemsetAsync(x, 0, sizeof(T) * n3, s));
-    for (int k = 0; k < c->opts.nu1; ++k) {
+    int k0 = 0;
+    if (c->opts.smoother == SIB_SMOOTHER_VANKA && c->opts.nu1 > 0) {
+        KL(c, launch_vanka_zero<T>(gridk<T>(c, l), b, xt, s));   // first sweep from w = 0
+        std::swap(x, xt);
+        k0 = 1;
+    } else {
+        CK(cudaMemsetAsync(x, 0, sizeof(T) * n3, s));
+    }
+    for (int k = k0; k < c->opts.nu1; ++k) {
         sweep<T>(c, l, x, b, xt, s);
         std::swap(x, xt);
     }
-    apply_operator<T>(c, l, x, b, (T*)lv.p[pi].r, s);
-    KL(c, launch_restrict<T>(c->L[l - 1].N, (const T*)lv.p[pi].r, (T*)c->L[l - 1].p[pi].b, s));
+    ib_apply<T>(c, l, x, s);
+    KL(c, launch_residual_restrict<T>(gridk<T>(c, l), x, b, (T*)c->L[l - 1].p[pi].b, s));
     T* ec = vcycle_level<T>(c, l - 1, s);
     KL(c, launch_prolong_add<T>(c->L[l - 1].N, ec, x, s));
     for (int k = 0; k < c->opts.nu2; ++k) {
@@ -455,6 +523,7 @@ void alloc_sc_bufs(sib_ctx* c) {
             if (b.tv[0]) continue;
             for (int k = 0; k < 8; ++k) b.tv[k] = dalloc(c, e * 2 * n);
             for (int k = 0; k < 6; ++k) b.tp[k] = dalloc(c, e * n);
+            b.dinv = dalloc(c, e * 3 * n);
         }
     }
 }
@@ -522,33 +591,27 @@ void alloc_krylov(sib_ctx* c) {
     c->mcap = m;
 }
 
-// power iterations for lambda_max of diag^{-1} Op (FP64), start vector = hash vector
-double power_A(sib_ctx* c, int l, cudaStream_t s) {
+// Power iterations for lambda_max of DA^{-1} A_IB and of DM^{-1} D At^{-1} G on level l (FP64),
+// from the hash start vector; everything stays on the device, ||w||^2 of the last iterate lands in
+// scal[slot] (setup reads all levels back with one synchronisation per operator).
+void power_A_enqueue(sib_ctx* c, int l, int slot, cudaStream_t s) {
     Level& lv = c->L[l];
     const int64_t nv = 2LL * lv.N * lv.N;
     double* v = (double*)lv.p[0].tv[6];
     double* w = (double*)lv.p[0].tv[7];
-    double* t = (double*)lv.p[0].tv[1];
     GridK<double> g = gridk<double>(c, l);
     KL(c, launch_hash_vector(v, nv, s));
-    KL(c, launch_dot_partials(v, v, nv, c->part, NBLK, s));
-    KL(c, launch_reduce_partials(c->part, 1, NBLK, c->scal + 300, s));
-    KL(c, launch_scale(v, c->scal, 300, nv, s));
+    dot_into(c, v, v, nv, c->scal + slot, s);
+    KL(c, launch_scale(v, c->scal, slot, nv, s));
     for (int it = 0; it < c->opts.power_iters; ++it) {
         ib_apply<double>(c, l, v, s);
-        KL(c, launch_apply_AIB<double>(g, v, t, s));
-        KL(c, launch_sc_jacobi_A<double>(g, t, w, 1.0, s));
-        KL(c, launch_dot_partials(w, w, nv, c->part, NBLK, s));
-        KL(c, launch_reduce_partials(c->part, 1, NBLK, c->scal + 300, s));
-        KL(c, launch_scale(w, c->scal, 300, nv, s));
+        KL(c, launch_power_A<double>(g, v, w, s));
+        dot_into(c, w, w, nv, c->scal + slot, s);
+        KL(c, launch_scale(w, c->scal, slot, nv, s));
         std::swap(v, w);
     }
-    double val = 0;
-    CK(cudaMemcpyAsync(&val, c->scal + 300, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    return std::sqrt(val);
 }
-double power_M(sib_ctx* c, int l, cudaStream_t s) {
+void power_M_enqueue(sib_ctx* c, int l, int slot, cudaStream_t s) {
     Level& lv = c->L[l];
     const int64_t np = (int64_t)lv.N * lv.N;
     double* v = (double*)lv.p[0].tp[0];
@@ -556,25 +619,28 @@ double power_M(sib_ctx* c, int l, cudaStream_t s) {
     double* md = (double*)lv.p[0].tp[5];
     double* gq = (double*)lv.p[0].tv[4];
     double* ya = (double*)lv.p[0].tv[5];
+    double* dA = (double*)lv.p[0].tv[2];
     GridK<double> g = gridk<double>(c, l);
+    const Cheb2<double> ka = cheb2<double>(lv.lamA, c->opts.cheb_lo, c->opts.cheb_hi);
     KL(c, launch_hash_vector(v, np, s));
-    KL(c, launch_dot_partials(v, v, np, c->part, NBLK, s));
-    KL(c, launch_reduce_partials(c->part, 1, NBLK, c->scal + 300, s));
-    KL(c, launch_scale(v, c->scal, 300, np, s));
+    dot_into(c, v, v, np, c->scal + slot, s);
+    KL(c, launch_scale(v, c->scal, slot, np, s));
     for (int it = 0; it < c->opts.power_iters; ++it) {
-        KL(c, launch_gradient<double>(g, v, gq, s));
-        cheb_A<double>(c, l, gq, ya, s);
-        KL(c, launch_divergence<double>(g, ya, md, s));
-        KL(c, launch_jacobi_M<double>(g, md, w, 1.0, s));
-        KL(c, launch_dot_partials(w, w, np, c->part, NBLK, s));
-        KL(c, launch_reduce_partials(c->part, 1, NBLK, c->scal + 300, s));
-        KL(c, launch_scale(w, c->scal, 300, np, s));
+        if (c->opts.cheb_iters == 2) {
+            KL(c, launch_power_Mstart<double>(g, ka, v, gq, dA, s));
+            ib_apply<double>(c, l, dA, s);
+            KL(c, launch_sc_chebA<double>(g, ka, gq, dA, ya, s));
+            KL(c, launch_power_Mfinish<double>(g, ya, w, s));
+        } else {
+            KL(c, launch_gradient<double>(g, v, gq, s));
+            cheb_A<double>(c, l, gq, ya, s);
+            KL(c, launch_divergence<double>(g, ya, md, s));
+            KL(c, launch_jacobi_M<double>(g, md, w, 1.0, s));
+        }
+        dot_into(c, w, w, np, c->scal + slot, s);
+        KL(c, launch_scale(w, c->scal, slot, np, s));
         std::swap(v, w);
     }
-    double val = 0;
-    CK(cudaMemcpyAsync(&val, c->scal + 300, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    return std::sqrt(val);
 }
 
 void setup(sib_ctx* c, cudaStream_t s) {
@@ -725,10 +791,24 @@ void setup(sib_ctx* c, cudaStream_t s) {
             if (c->lamOverride) {
                 lv.lamA = c->lamA_ov[l];
                 lv.lamM = c->lamM_ov[l];
-            } else {
-                lv.lamA = power_A(c, l, s);
-                lv.lamM = power_M(c, l, s);
             }
+        }
+        for (int l = 1; l <= c->lmax; ++l) {
+            Level& lv = c->L[l];
+            const int64_t n3 = 3LL * lv.N * lv.N;
+            KL(c, launch_sc_diag(gridk<double>(c, l), (double*)lv.p[0].dinv, s));
+            KL(c, (launch_convert<double, float>((const double*)lv.p[0].dinv, (float*)lv.p[1].dinv, n3, s)));
+        }
+        if (!c->lamOverride && c->lmax > 0) {
+            const int L = c->lmax;
+            for (int l = 1; l <= L; ++l) power_A_enqueue(c, l, 300 + l, s);
+            CK(cudaMemcpyAsync(c->hbuf + 300, c->scal + 300, sizeof(double) * (L + 1), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int l = 1; l <= L; ++l) c->L[l].lamA = std::sqrt(c->hbuf[300 + l]);
+            for (int l = 1; l <= L; ++l) power_M_enqueue(c, l, 320 + l, s);
+            CK(cudaMemcpyAsync(c->hbuf + 320, c->scal + 320, sizeof(double) * (L + 1), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int l = 1; l <= L; ++l) c->L[l].lamM = std::sqrt(c->hbuf[320 + l]);
         }
     }
     alloc_krylov(c);
@@ -747,10 +827,7 @@ void require_setup(sib_ctx* c) {
 }
 
 // ---- flexible GMRES (right-preconditioned, CGS2, Givens) ---------------------------------------
-void dot(sib_ctx* c, const double* x, const double* y, int64_t n, double* dst, cudaStream_t s) {
-    KL(c, launch_dot_partials(x, y, n, c->part, NBLK, s));
-    KL(c, launch_reduce_partials(c->part, 1, NBLK, dst, s));
-}
+void dot(sib_ctx* c, const double* x, const double* y, int64_t n, double* dst, cudaStream_t s) { dot_into(c, x, y, n, dst, s); }
 
 void project(sib_ctx* c, double* x, cudaStream_t s) {
     const int mask = c->rho == 0.0 ? 7 : 4;
@@ -1347,13 +1424,15 @@ int sib_apply_ib(sib_ctx* c, int l, int prec, const void* u, void* f, void* stre
     if (!valid_prec(prec) || !u || !f) throw SibError(SIB_ERR_ARG, "bad precision or null pointer");
     cudaStream_t s = S(stream);
     const int64_t nv = 2LL * c->L[l].N * c->L[l].N;
-    if (prec == SIB_PREC_FP64) {
+    Level& lv = c->L[l];
+    const int pi = prec == SIB_PREC_FP64 ? 0 : 1;
+    const size_t es = prec == SIB_PREC_FP64 ? 8 : 4;
+    if (pi == 0) {
         ib_apply<double>(c, l, (const double*)u, s);
-        CK(cudaMemcpyAsync(f, c->L[l].p[0].fib, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
     } else {
         ib_apply<float>(c, l, (const float*)u, s);
-        CK(cudaMemcpyAsync(f, c->L[l].p[1].fib, sizeof(float) * nv, cudaMemcpyDeviceToDevice, s));
     }
+    CK(cudaMemcpyAsync(f, lv.p[pi].fib, es * nv, cudaMemcpyDeviceToDevice, s));
     kcheck(c);
     return SIB_OK;
     API_END(c)
