@@ -172,16 +172,146 @@ __global__ void __launch_bounds__(256) k_vanka(GridK<T> g, const T* __restrict__
     }
 }
 
+// Tiled form of the same sweep for levels with N >= 32 (tiles exactly TX x TY): x is staged in
+// shared memory with a two-cell halo by coalesced loads, index arithmetic uses compile-time tile
+// sizes, and cells of tiles without IB entries use the constant patch inverse (no divisions).
+template <typename T>
+VankaBulk<T> vanka_bulk(double a0, double c, double inv_h) {
+    const double det = a0 * a0 - c * c;
+    const double s0 = inv_h / (a0 + c);
+    VankaBulk<T> k;
+    k.ai0 = (T)(a0 / det);
+    k.ai1 = (T)(c / det);
+    k.s0 = (T)s0;
+    k.invS = (T)(1.0 / (4.0 * inv_h * s0));
+    return k;
+}
+
+template <typename T, bool ZERO>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_vanka_tiled(GridK<T> g, VankaBulk<T> kb, const T* __restrict__ x,
+                                                     const T* __restrict__ b, T* __restrict__ xo) {
+    constexpr int SX = TX + 4, SY = TY + 4;   // staged x: tile plus two cells each side
+    constexpr int RX = TX + 2, RY = TY + 2;   // residuals: tile plus one cell each side
+    constexpr int PX = TX + 1, PY = TY + 1;   // patches: tile plus its left and bottom neighbours
+    __shared__ T xs[3][SY][SX];
+    __shared__ T rs[3][RY][RX];
+    __shared__ T ds[5][PY][PX];
+    const int N = g.N, n = N * N, m = N - 1;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const bool act = g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x];
+    if (!ZERO) {
+        for (int q = tid; q < SY * SX; q += TX * TY) {
+            const int jj = q / SX, ii = q - jj * SX;
+            const int gc = ((j0 - 2 + jj) & m) * N + ((i0 - 2 + ii) & m);
+            xs[0][jj][ii] = x[gc];
+            xs[1][jj][ii] = x[n + gc];
+            xs[2][jj][ii] = x[2 * n + gc];
+        }
+        __syncthreads();
+    }
+    for (int q = tid; q < RY * RX; q += TX * TY) {
+        const int rj = q / RX, ri = q - rj * RX;
+        const int gc = ((j0 - 1 + rj) & m) * N + ((i0 - 1 + ri) & m);
+        if (ZERO) {
+            rs[0][rj][ri] = b[gc];
+            rs[1][rj][ri] = b[n + gc];
+            rs[2][rj][ri] = b[2 * n + gc];
+            continue;
+        }
+        const int sx = ri + 1, sy = rj + 1;
+        const T uc = xs[0][sy][sx], vc = xs[1][sy][sx], pc = xs[2][sy][sx];
+        const T uE = xs[0][sy][sx + 1], vN = xs[1][sy + 1][sx];
+        T Au = g.a0 * uc - g.c * ((uE + xs[0][sy][sx - 1]) + (xs[0][sy + 1][sx] + xs[0][sy - 1][sx])) +
+               (pc - xs[2][sy][sx - 1]) * g.inv_h;
+        T Av = g.a0 * vc - g.c * ((xs[1][sy][sx + 1] + xs[1][sy][sx - 1]) + (vN + xs[1][sy - 1][sx])) +
+               (pc - xs[2][sy - 1][sx]) * g.inv_h;
+        if (act) {
+            Au -= g.dt * g.fib[gc];
+            Av -= g.dt * g.fib[n + gc];
+        }
+        rs[0][rj][ri] = b[gc] - Au;
+        rs[1][rj][ri] = b[n + gc] - Av;
+        rs[2][rj][ri] = b[2 * n + gc] + ((uE - uc) + (vN - vc)) * g.inv_h;
+    }
+    __syncthreads();
+    const T ih = g.inv_h;
+    for (int q = tid; q < PY * PX; q += TX * TY) {
+        const int pj = q / PX, pi = q - pj * PX;
+        const T r0 = rs[0][pj][pi], r1 = rs[0][pj][pi + 1];
+        const T r2 = rs[1][pj][pi], r3 = rs[1][pj + 1][pi];
+        const T r4 = rs[2][pj][pi];
+        T d0, d1, d2, d3, dp;
+        if (!act) {
+            const T tu0 = kb.ai0 * r0 + kb.ai1 * r1, tu1 = kb.ai1 * r0 + kb.ai0 * r1;
+            const T tv0 = kb.ai0 * r2 + kb.ai1 * r3, tv1 = kb.ai1 * r2 + kb.ai0 * r3;
+            dp = (ih * ((tu0 - tu1) + (tv0 - tv1)) - r4) * kb.invS;
+            d0 = tu0 - kb.s0 * dp;
+            d1 = tu1 + kb.s0 * dp;
+            d2 = tv0 - kb.s0 * dp;
+            d3 = tv1 + kb.s0 * dp;
+        } else {
+            const int i = (i0 - 1 + pi) & m, j = (j0 - 1 + pj) & m;
+            const int cc = j * N + i, ce = j * N + ((i + 1) & m), cn = ((j + 1) & m) * N + i;
+            const T au00 = g.a0 - g.dt * g.ibd[cc], au11 = g.a0 - g.dt * g.ibd[ce], au01 = -g.c - g.dt * g.ibd[n + cc];
+            const T av00 = g.a0 - g.dt * g.ibd[2 * n + cc], av11 = g.a0 - g.dt * g.ibd[2 * n + cn],
+                    av01 = -g.c - g.dt * g.ibd[3 * n + cc];
+            const T idu = T(1) / (au00 * au11 - au01 * au01);
+            const T idv = T(1) / (av00 * av11 - av01 * av01);
+            const T su0 = (au11 + au01) * ih * idu, su1 = -(au01 + au00) * ih * idu;
+            const T sv0 = (av11 + av01) * ih * idv, sv1 = -(av01 + av00) * ih * idv;
+            const T tu0 = (au11 * r0 - au01 * r1) * idu, tu1 = (au00 * r1 - au01 * r0) * idu;
+            const T tv0 = (av11 * r2 - av01 * r3) * idv, tv1 = (av00 * r3 - av01 * r2) * idv;
+            const T S = ih * ((su0 - su1) + (sv0 - sv1));
+            dp = (ih * ((tu0 - tu1) + (tv0 - tv1)) - r4) / S;
+            d0 = tu0 - su0 * dp;
+            d1 = tu1 - su1 * dp;
+            d2 = tv0 - sv0 * dp;
+            d3 = tv1 - sv1 * dp;
+        }
+        ds[0][pj][pi] = d0;
+        ds[1][pj][pi] = d1;
+        ds[2][pj][pi] = d2;
+        ds[3][pj][pi] = d3;
+        ds[4][pj][pi] = dp;
+    }
+    __syncthreads();
+    const int ci = threadIdx.x, cj = threadIdx.y;
+    const int c = (j0 + cj) * N + (i0 + ci);
+    const T hw = T(0.5) * g.omega;
+    const T du = hw * (ds[0][cj + 1][ci + 1] + ds[1][cj + 1][ci]);
+    const T dv = hw * (ds[2][cj + 1][ci + 1] + ds[3][cj][ci + 1]);
+    const T dq = g.omega * ds[4][cj + 1][ci + 1];
+    if (ZERO) {
+        xo[c] = du;
+        xo[n + c] = dv;
+        xo[2 * n + c] = dq;
+    } else {
+        xo[c] = xs[0][cj + 2][ci + 2] + du;
+        xo[n + c] = xs[1][cj + 2][ci + 2] + dv;
+        xo[2 * n + c] = xs[2][cj + 2][ci + 2] + dq;
+    }
+}
+
+template <typename T, bool ZERO>
+void launch_vanka_any(const GridK<T>& g, const T* x, const T* b, T* xo, cudaStream_t s) {
+    dim3 blk(g.tx, g.ty), grd(g.N / g.tx, g.N / g.ty);
+    if (g.tx != TX || g.ty != TY) {
+        k_vanka<T, ZERO><<<grd, blk, 0, s>>>(g, x, b, xo);
+        return;
+    }
+    const VankaBulk<T> kb = vanka_bulk<T>(g.a0, g.c, g.inv_h);
+    k_vanka_tiled<T, ZERO><<<grd, blk, 0, s>>>(g, kb, x, b, xo);
+}
+
 template <typename T>
 void launch_vanka(const GridK<T>& g, const T* x, const T* b, T* xo, cudaStream_t s) {
-    dim3 blk(g.tx, g.ty), grd(g.N / g.tx, g.N / g.ty);
-    k_vanka<T, false><<<grd, blk, 0, s>>>(g, x, b, xo);
+    launch_vanka_any<T, false>(g, x, b, xo, s);
 }
 // the first sweep from a zero initial guess (Alg. 1 recursion): no reads of x, residual = b
 template <typename T>
 void launch_vanka_zero(const GridK<T>& g, const T* b, T* xo, cudaStream_t s) {
-    dim3 blk(g.tx, g.ty), grd(g.N / g.tx, g.N / g.ty);
-    k_vanka<T, true><<<grd, blk, 0, s>>>(g, b, b, xo);   // x is never read
+    launch_vanka_any<T, true>(g, b, b, xo, s);   // x is never read
 }
 
 // ------------------------------------------------------------------------------------------

@@ -49,6 +49,14 @@ struct GridK {
     const T* dinv;                   // SC: 1/diag(A_IB) on u and v faces, 1/diag(D diag(A_IB)^-1 G) on cells
 };
 
+// Constants of the Vanka patch solve for cells without IB entries (the patch matrix is the same
+// for all of them): A^{-1} = [[ai0, ai1], [ai1, ai0]], s = A^{-1}(1/h, -1/h) = (s0, -s0), and the
+// inverse of the pressure Schur complement 1 / (g^T s_u + g^T s_v).
+template <typename T>
+struct VankaBulk {
+    T ai0, ai1, s0, invS;
+};
+
 // Chebyshev coefficients of two iterations from x0 = 0 on [lo, hi] lambda_max:
 //   x2 = (1 + c1) d0 + c2 Dinv (q - Op d0),  d0 = Dinv q / theta
 template <typename T>
@@ -85,6 +93,7 @@ template <typename T> void launch_jacobi_M(const GridK<T>& g, const T* r, T* z, 
 template <typename T> void launch_cheb_update(const T* dinvr, T* d, T* x, T ra, T rb, int64_t n, cudaStream_t s);
 // fused kernels
 template <typename T> void launch_vanka_zero(const GridK<T>& g, const T* b, T* xo, cudaStream_t s);
+template <typename T> VankaBulk<T> vanka_bulk(double a0, double c, double inv_h);
 template <typename T> void launch_residual_restrict(const GridK<T>& g, const T* x, const T* b, T* bc, cudaStream_t s);
 template <typename T> void launch_sc_start(const GridK<T>& g, Cheb2<T> ka, const T* x, const T* b, T* r, T* d,
                                            cudaStream_t s);

@@ -366,3 +366,44 @@ def test_errors_are_reported_not_raised_from_cuda():
         S.set_options(restart=1000)
     with pytest.raises(sib.SibError):
         sib.Solver(48)
+
+
+def test_vanka_sweep_large_grid_against_oracle():
+    """One fine-level sweep at N = 512, where the FP32 path runs the persistent cp.async-pipelined
+    kernel and the FP64 path the tiled kernel; the oracle sweep is built for the finest level only."""
+    prob = I.thin_ellipse_re(512, kappa=1e4)
+    S = sib.solver_for(prob)
+    L = system.operator_of(prob)
+    dofs = smoothers.vanka_patch_dofs(512)
+    patches = smoothers.vanka_patches(L, dofs)
+    l = S.num_levels - 1
+    x = rand(3 * 512 * 512, 901)
+    b = rand(3 * 512 * 512, 902, 10.0)
+    ref = smoothers.vanka_sweep(L, dofs, patches, x, b, 0.8)
+    y = cu(x.copy())
+    S.smooth(l, y, cu(b), 1)
+    assert rel(host(y), ref) < TOL64, rel(host(y), ref)
+    x32 = x.astype(np.float32).astype(np.float64)
+    b32 = b.astype(np.float32).astype(np.float64)
+    ref32 = smoothers.vanka_sweep(L, dofs, patches, x32, b32, 0.8)
+    y32 = cu(x32, torch.float32)
+    S.smooth(l, y32, cu(b32, torch.float32), 1)
+    assert rel(host(y32), ref32) < TOL32, rel(host(y32), ref32)
+    # the first sweep from a zero guess (no reads of x) inside a V-cycle level: one sweep from 0
+    z32 = torch.zeros_like(y32)
+    S.smooth(l, z32, cu(b32, torch.float32), 1)
+    ref0 = smoothers.vanka_sweep(L, dofs, patches, np.zeros_like(b32), b32, 0.8)
+    assert rel(host(z32), ref0) < TOL32
+
+
+def test_vcycle_large_grid_against_oracle():
+    """One V-cycle at N = 512 (FP32 levels 512 and 256 use the pipelined and tiled sweep kernels,
+    the first sweep of each level the zero-guess form) against the oracle's V-cycle."""
+    prob = I.thin_ellipse_re(512, kappa=1e2)
+    H = multigrid.Hierarchy(prob)
+    S = sib.solver_for(prob)
+    b = system.rhs(prob)
+    ref = H.vcycle(b)
+    assert rel(host(S.vcycle(cu(b))), ref) < TOL64
+    b32 = b.astype(np.float32).astype(np.float64)
+    assert rel(host(S.vcycle(cu(b32, torch.float32))), H.vcycle(b32)) < 1e-4
