@@ -307,7 +307,7 @@ def run_native(args):
     # dominant kernel of the step, timed live on the benchmark's own context and stream
     lmax = S.num_levels - 1
     S.set_options(smoother=sib.SMOOTHER_VANKA, omega=-1.0)
-    S.set_stiffness(kap_dev[1e2])
+    S.set_stiffness(torch.full((st.E,), 1e2, dtype=torch.float64, device=dev))
     S.setup()
     dom_ms, dom_bytes = S.time_kernel("vanka", lmax, True, reps=50)
     peak, peak_kind = measured_peaks()

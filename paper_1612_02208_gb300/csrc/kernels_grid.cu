@@ -37,6 +37,7 @@ __device__ __forceinline__ T diag_face(const GridK<T>& g, int comp, int i, int j
 template <typename T, bool HAS_B>
 __global__ void __launch_bounds__(256) k_residual(GridK<T> g, const T* __restrict__ x, const T* __restrict__ b,
                                                   T* __restrict__ r) {
+    pdl_entry();
     const int N = g.N, n = N * N, m = N - 1;
     const int i = blockIdx.x * g.tx + threadIdx.x;
     const int j = blockIdx.y * g.ty + threadIdx.y;
@@ -69,9 +70,9 @@ template <typename T>
 void launch_residual(const GridK<T>& g, const T* x, const T* b, T* r, cudaStream_t s) {
     dim3 blk(g.tx, g.ty), grd(g.N / g.tx, g.N / g.ty);
     if (b)
-        k_residual<T, true><<<grd, blk, 0, s>>>(g, x, b, r);
+        launch_pdl(k_residual<T, true>, grd, blk, 0, s, g, x, b, r);
     else
-        k_residual<T, false><<<grd, blk, 0, s>>>(g, x, nullptr, r);
+        launch_pdl(k_residual<T, false>, grd, blk, 0, s, g, x, nullptr, r);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -86,6 +87,7 @@ void launch_residual(const GridK<T>& g, const T* x, const T* b, T* r, cudaStream
 template <typename T, bool ZERO>
 __global__ void __launch_bounds__(256) k_vanka(GridK<T> g, const T* __restrict__ x, const T* __restrict__ b,
                                                T* __restrict__ xo) {
+    pdl_entry();
     __shared__ T sru[(TY + 2) * (TX + 2)];
     __shared__ T srv[(TY + 2) * (TX + 2)];
     __shared__ T srp[(TY + 2) * (TX + 2)];
@@ -190,6 +192,7 @@ VankaBulk<T> vanka_bulk(double a0, double c, double inv_h) {
 template <typename T, bool ZERO>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_vanka_tiled(GridK<T> g, VankaBulk<T> kb, const T* __restrict__ x,
                                                      const T* __restrict__ b, T* __restrict__ xo) {
+    pdl_entry();
     constexpr int SX = TX + 4, SY = TY + 4;   // staged x: tile plus two cells each side
     constexpr int RX = TX + 2, RY = TY + 2;   // residuals: tile plus one cell each side
     constexpr int PX = TX + 1, PY = TY + 1;   // patches: tile plus its left and bottom neighbours
@@ -297,11 +300,11 @@ template <typename T, bool ZERO>
 void launch_vanka_any(const GridK<T>& g, const T* x, const T* b, T* xo, cudaStream_t s) {
     dim3 blk(g.tx, g.ty), grd(g.N / g.tx, g.N / g.ty);
     if (g.tx != TX || g.ty != TY) {
-        k_vanka<T, ZERO><<<grd, blk, 0, s>>>(g, x, b, xo);
+        launch_pdl(k_vanka<T, ZERO>, grd, blk, 0, s, g, x, b, xo);
         return;
     }
     const VankaBulk<T> kb = vanka_bulk<T>(g.a0, g.c, g.inv_h);
-    k_vanka_tiled<T, ZERO><<<grd, blk, 0, s>>>(g, kb, x, b, xo);
+    launch_pdl(k_vanka_tiled<T, ZERO>, grd, blk, 0, s, g, kb, x, b, xo);
 }
 
 template <typename T>
@@ -356,6 +359,7 @@ __device__ __forceinline__ T res_p(const GridK<T>& g, const T* __restrict__ x, c
 
 template <typename T>
 __global__ void k_residual_restrict(GridK<T> g, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ bc) {
+    pdl_entry();
     const int Nc = g.N / 2;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
@@ -378,7 +382,7 @@ void launch_residual_restrict(const GridK<T>& g, const T* x, const T* b, T* bc, 
     const int Nc = g.N / 2;
     dim3 blk(Nc < 32 ? Nc : 32, Nc < 8 ? Nc : 8);
     dim3 grd((Nc + blk.x - 1) / blk.x, (Nc + blk.y - 1) / blk.y);
-    k_residual_restrict<T><<<grd, blk, 0, s>>>(g, x, b, bc);
+    launch_pdl(k_residual_restrict<T>, grd, blk, 0, s, g, x, b, bc);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -388,6 +392,7 @@ void launch_residual_restrict(const GridK<T>& g, const T* x, const T* b, T* bc, 
 //   cell away in x; pressure: average of the four fine cells.
 template <typename T>
 __global__ void k_restrict(int Nc, const T* __restrict__ rf, T* __restrict__ bc) {
+    pdl_entry();
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
     if (I >= Nc || J >= Nc) return;
@@ -411,7 +416,7 @@ template <typename T>
 void launch_restrict(int Nc, const T* rf, T* bc, cudaStream_t s) {
     dim3 blk(Nc < 32 ? Nc : 32, Nc < 8 ? Nc : 8);
     dim3 grd((Nc + blk.x - 1) / blk.x, (Nc + blk.y - 1) / blk.y);
-    k_restrict<T><<<grd, blk, 0, s>>>(Nc, rf, bc);
+    launch_pdl(k_restrict<T>, grd, blk, 0, s, Nc, rf, bc);
 }
 
 // Prolongation and correction xf += P ec (Sec. 3.2): RT0 for velocity (fine faces that coincide
@@ -419,6 +424,7 @@ void launch_restrict(int Nc, const T* rf, T* bc, cudaStream_t s) {
 // tangential direction), bilinear cell-centred interpolation for pressure (9/16, 3/16, 3/16, 1/16).
 template <typename T>
 __global__ void k_prolong_add(int Nc, const T* __restrict__ ec, T* __restrict__ xf) {
+    pdl_entry();
     const int Nf = 2 * Nc;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -444,12 +450,13 @@ void launch_prolong_add(int Nc, const T* ec, T* xf, cudaStream_t s) {
     const int Nf = 2 * Nc;
     dim3 blk(Nf < 32 ? Nf : 32, Nf < 8 ? Nf : 8);
     dim3 grd((Nf + blk.x - 1) / blk.x, (Nf + blk.y - 1) / blk.y);
-    k_prolong_add<T><<<grd, blk, 0, s>>>(Nc, ec, xf);
+    launch_pdl(k_prolong_add<T>, grd, blk, 0, s, Nc, ec, xf);
 }
 
 // ------------------------------------------------------------------------------------------
 template <typename Ti, typename To>
 __global__ void k_convert(const Ti* __restrict__ in, To* __restrict__ out, int64_t n) {
+    pdl_entry();
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
         out[k] = static_cast<To>(in[k]);
 }
@@ -462,18 +469,19 @@ int num_blocks_for(int64_t n) {
 
 template <typename Ti, typename To>
 void launch_convert(const Ti* in, To* out, int64_t n, cudaStream_t s) {
-    k_convert<Ti, To><<<num_blocks_for(n), 256, 0, s>>>(in, out, n);
+    launch_pdl(k_convert<Ti, To>, num_blocks_for(n), 256, 0, s, in, out, n);
 }
 
 template <typename T>
 __global__ void k_axpby(T a, const T* __restrict__ x, T b, const T* __restrict__ y, T* __restrict__ z, int64_t n) {
+    pdl_entry();
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
         z[k] = a * x[k] + (y ? b * y[k] : T(0));
 }
 
 template <typename T>
 void launch_axpby(T a, const T* x, T b, const T* y, T* z, int64_t n, cudaStream_t s) {
-    k_axpby<T><<<num_blocks_for(n), 256, 0, s>>>(a, x, b, y, z, n);
+    launch_pdl(k_axpby<T>, num_blocks_for(n), 256, 0, s, a, x, b, y, z, n);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -487,6 +495,7 @@ __device__ __forceinline__ T diagA(const GridK<T>& g, bool act, int comp, int c,
 // z = scale * diag(A_IB)^{-1} r on both velocity components
 template <typename T>
 __global__ void k_jacobi_A(GridK<T> g, const T* __restrict__ r, T* __restrict__ z, T scale) {
+    pdl_entry();
     const int N = g.N, n = N * N;
     const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
     const bool act = g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x];
@@ -496,12 +505,13 @@ __global__ void k_jacobi_A(GridK<T> g, const T* __restrict__ r, T* __restrict__ 
 }
 template <typename T>
 void launch_sc_jacobi_A(const GridK<T>& g, const T* r, T* z, T scale, cudaStream_t s) {
-    k_jacobi_A<T><<<dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s>>>(g, r, z, scale);
+    launch_pdl(k_jacobi_A<T>, dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s, g, r, z, scale);
 }
 
 // y = A_IB u = A u - dt [SKJ] u on the velocity faces (fib holds [SKJ] u)
 template <typename T>
 __global__ void k_apply_AIB(GridK<T> g, const T* __restrict__ x, T* __restrict__ y) {
+    pdl_entry();
     const int N = g.N, n = N * N, m = N - 1;
     const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
     const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m;
@@ -515,12 +525,13 @@ __global__ void k_apply_AIB(GridK<T> g, const T* __restrict__ x, T* __restrict__
 }
 template <typename T>
 void launch_apply_AIB(const GridK<T>& g, const T* u, T* y, cudaStream_t s) {
-    k_apply_AIB<T><<<dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s>>>(g, u, y);
+    launch_pdl(k_apply_AIB<T>, dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s, g, u, y);
 }
 
 // gu = G p on the velocity faces
 template <typename T>
 __global__ void k_gradient(GridK<T> g, const T* __restrict__ p, T* __restrict__ gu) {
+    pdl_entry();
     const int N = g.N, n = N * N, m = N - 1;
     const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
     const int c = j * N + i;
@@ -530,12 +541,13 @@ __global__ void k_gradient(GridK<T> g, const T* __restrict__ p, T* __restrict__ 
 }
 template <typename T>
 void launch_gradient(const GridK<T>& g, const T* p, T* gu, cudaStream_t s) {
-    k_gradient<T><<<dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s>>>(g, p, gu);
+    launch_pdl(k_gradient<T>, dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s, g, p, gu);
 }
 
 // d = D u on the cells
 template <typename T>
 __global__ void k_divergence(GridK<T> g, const T* __restrict__ u, T* __restrict__ d) {
+    pdl_entry();
     const int N = g.N, n = N * N, m = N - 1;
     const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
     const int c = j * N + i;
@@ -543,7 +555,7 @@ __global__ void k_divergence(GridK<T> g, const T* __restrict__ u, T* __restrict_
 }
 template <typename T>
 void launch_divergence(const GridK<T>& g, const T* u, T* d, cudaStream_t s) {
-    k_divergence<T><<<dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s>>>(g, u, d);
+    launch_pdl(k_divergence<T>, dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s, g, u, d);
 }
 
 // z = scale * diag(Mh)^{-1} r with Mh = D diag(A_IB)^{-1} G:
@@ -552,6 +564,7 @@ void launch_divergence(const GridK<T>& g, const T* u, T* d, cudaStream_t s) {
 // one tile, so the flag of the cell's own tile covers them).
 template <typename T>
 __global__ void k_jacobi_M(GridK<T> g, const T* __restrict__ r, T* __restrict__ z, T scale) {
+    pdl_entry();
     const int N = g.N, n = N * N, m = N - 1;
     const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
     const bool act = g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x];
@@ -563,13 +576,14 @@ __global__ void k_jacobi_M(GridK<T> g, const T* __restrict__ r, T* __restrict__ 
 }
 template <typename T>
 void launch_jacobi_M(const GridK<T>& g, const T* r, T* z, T scale, cudaStream_t s) {
-    k_jacobi_M<T><<<dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s>>>(g, r, z, scale);
+    launch_pdl(k_jacobi_M<T>, dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s, g, r, z, scale);
 }
 
 // Chebyshev direction update d = ra * d + rb * dinvr, then x += d
 template <typename T>
 __global__ void k_cheb_update(const T* __restrict__ dinvr, T* __restrict__ d, T* __restrict__ x, T ra, T rb,
                               int64_t n) {
+    pdl_entry();
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const T dn = ra * d[k] + rb * dinvr[k];
         d[k] = dn;
@@ -578,7 +592,7 @@ __global__ void k_cheb_update(const T* __restrict__ dinvr, T* __restrict__ d, T*
 }
 template <typename T>
 void launch_cheb_update(const T* dinvr, T* d, T* x, T ra, T rb, int64_t n, cudaStream_t s) {
-    k_cheb_update<T><<<num_blocks_for(n), 256, 0, s>>>(dinvr, d, x, ra, rb, n);
+    launch_pdl(k_cheb_update<T>, num_blocks_for(n), 256, 0, s, dinvr, d, x, ra, rb, n);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -619,6 +633,7 @@ __device__ __forceinline__ T dM_inv(const GridK<T>& g, int i, int j) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_sc_start(GridK<T> g, Cheb2<T> ka, const T* __restrict__ x,
                                                   const T* __restrict__ b, T* __restrict__ r, T* __restrict__ d) {
+    pdl_entry();
     const int N = g.N, n = N * N;
     const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
     const int c = j * N + i;
@@ -633,6 +648,7 @@ __global__ void __launch_bounds__(256) k_sc_start(GridK<T> g, Cheb2<T> ka, const
 template <typename T>
 __global__ void __launch_bounds__(256) k_sc_chebA(GridK<T> g, Cheb2<T> ka, const T* __restrict__ q,
                                                   const T* __restrict__ d, T* __restrict__ y) {
+    pdl_entry();
     const int N = g.N, n = N * N;
     const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
     const int c = j * N + i;
@@ -647,6 +663,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_sc_mstart(GridK<T> g, Cheb2<T> ka, Cheb2<T> km, const T* __restrict__ rp,
                                                    const T* __restrict__ y, T* __restrict__ sv, T* __restrict__ dMo,
                                                    T* __restrict__ gq, T* __restrict__ dA) {
+    pdl_entry();
     const int N = g.N, n = N * N, m = N - 1;
     const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
     const int c = j * N + i;
@@ -672,6 +689,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_sc_mfinish(GridK<T> g, Cheb2<T> ka, Cheb2<T> km, const T* __restrict__ sv,
                                                     const T* __restrict__ dM, const T* __restrict__ ya,
                                                     T* __restrict__ dp, T* __restrict__ gq, T* __restrict__ dA) {
+    pdl_entry();
     const int N = g.N, n = N * N, m = N - 1;
     const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
     const int c = j * N + i;
@@ -695,6 +713,7 @@ __global__ void __launch_bounds__(256) k_sc_finish(GridK<T> g, Cheb2<T> ka, cons
                                                    const T* __restrict__ y, const T* __restrict__ gq,
                                                    const T* __restrict__ dA, const T* __restrict__ dp,
                                                    T* __restrict__ xo) {
+    pdl_entry();
     const int N = g.N, n = N * N;
     const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
     const int c = j * N + i;
@@ -709,6 +728,7 @@ __global__ void __launch_bounds__(256) k_sc_finish(GridK<T> g, Cheb2<T> ka, cons
 // power iterations: w = DA^{-1} A_IB v; gq = G v, dA = DA^{-1} gq / theta_A; w = DM^{-1} D ya
 template <typename T>
 __global__ void k_power_A(GridK<T> g, const T* __restrict__ v, T* __restrict__ w) {
+    pdl_entry();
     const int N = g.N, n = N * N;
     const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
     const int c = j * N + i;
@@ -717,6 +737,7 @@ __global__ void k_power_A(GridK<T> g, const T* __restrict__ v, T* __restrict__ w
 template <typename T>
 __global__ void k_power_Mstart(GridK<T> g, Cheb2<T> ka, const T* __restrict__ v, T* __restrict__ gq,
                                T* __restrict__ dA) {
+    pdl_entry();
     const int N = g.N, n = N * N, m = N - 1;
     const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
     const int c = j * N + i;
@@ -728,6 +749,7 @@ __global__ void k_power_Mstart(GridK<T> g, Cheb2<T> ka, const T* __restrict__ v,
 }
 template <typename T>
 __global__ void k_power_Mfinish(GridK<T> g, const T* __restrict__ ya, T* __restrict__ w) {
+    pdl_entry();
     const int N = g.N;
     const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
     w[j * N + i] = divg(g, ya, i, j) * g.dinv[2 * N * N + j * N + i];
@@ -735,6 +757,7 @@ __global__ void k_power_Mfinish(GridK<T> g, const T* __restrict__ ya, T* __restr
 
 // set-up of the SC diagonals (FP64): 1/diag(A_IB) on both face sets and 1/diag(M^) on cells
 __global__ void k_sc_diag(GridK<double> g, double* __restrict__ dinv) {
+    pdl_entry();
     const int N = g.N, n = N * N;
     const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
     const int c = j * N + i;
@@ -743,10 +766,10 @@ __global__ void k_sc_diag(GridK<double> g, double* __restrict__ dinv) {
     dinv[2 * n + c] = dM_inv(g, i, j);
 }
 void launch_sc_diag(const GridK<double>& g, double* dinv, cudaStream_t s) {
-    k_sc_diag<<<dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s>>>(g, dinv);
+    launch_pdl(k_sc_diag, dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s, g, dinv);
 }
 
-#define SIB_GRID_LAUNCH(kern, ...) kern<T><<<dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s>>>(__VA_ARGS__)
+#define SIB_GRID_LAUNCH(kern, ...) launch_pdl(kern<T>, dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s, __VA_ARGS__)
 template <typename T>
 void launch_sc_start(const GridK<T>& g, Cheb2<T> ka, const T* x, const T* b, T* r, T* d, cudaStream_t s) {
     SIB_GRID_LAUNCH(k_sc_start, g, ka, x, b, r, d);

@@ -63,6 +63,7 @@ __device__ __forceinline__ void coarsen_const(int& b0, double w[4]) {
 }
 
 __global__ void k_stencils(const double* __restrict__ X, int M, int Nf, int lmax, StencilOut out) {
+    pdl_entry();
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int comp = blockIdx.y;
     if (m >= M) return;
@@ -106,13 +107,14 @@ void launch_stencils(const double* X, int M, int Nf, int lmax, int** base, doubl
             o.w64[l][c] = w64[2 * l + c];
             o.w32[l][c] = w32[2 * l + c];
         }
-    k_stencils<<<dim3((M + 127) / 128, 2), 128, 0, s>>>(X, M, Nf, lmax, o);
+    launch_pdl(k_stencils, dim3((M + 127) / 128, 2), 128, 0, s, X, M, Nf, lmax, o);
 }
 
 // ------------------------------------------------------------------------------------------
 // Stable ordering of markers by the Morton code of their fine stencil origin: keys
 // (morton << 32 | id) sorted by a bitonic network (ties cannot occur, ids are distinct).
 __global__ void k_sort_keys(const int* __restrict__ base, int M, int Mpad, uint64_t* __restrict__ keys) {
+    pdl_entry();
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= Mpad) return;
     if (m < M) {
@@ -123,10 +125,11 @@ __global__ void k_sort_keys(const int* __restrict__ base, int M, int Mpad, uint6
     }
 }
 void launch_sort_keys(const int* baseFine, int M, int Mpad, uint64_t* keys, cudaStream_t s) {
-    k_sort_keys<<<(Mpad + 255) / 256, 256, 0, s>>>(baseFine, M, Mpad, keys);
+    launch_pdl(k_sort_keys, (Mpad + 255) / 256, 256, 0, s, baseFine, M, Mpad, keys);
 }
 
 __global__ void k_bitonic_step(uint64_t* __restrict__ a, int Mpad, int j, int k) {
+    pdl_entry();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Mpad) return;
     const int l = i ^ j;
@@ -141,6 +144,7 @@ __global__ void k_bitonic_step(uint64_t* __restrict__ a, int Mpad, int j, int k)
 }
 // all steps with j < 1024 of stage k run in shared memory
 __global__ void k_bitonic_smem(uint64_t* __restrict__ a, int Mpad, int k, int jstart) {
+    pdl_entry();
     __shared__ uint64_t sh[2048];
     const int base = blockIdx.x * 2048;
     for (int t = threadIdx.x; t < 2048; t += blockDim.x) sh[t] = a[base + t];
@@ -165,16 +169,17 @@ void launch_bitonic(uint64_t* keys, int Mpad, cudaStream_t s) {
     for (int k = 2; k <= Mpad; k <<= 1) {
         int j = k >> 1;
         if (Mpad >= 2048) {
-            for (; j >= 1024; j >>= 1) k_bitonic_step<<<(Mpad + 255) / 256, 256, 0, s>>>(keys, Mpad, j, k);
-            k_bitonic_smem<<<Mpad / 2048, 1024, 0, s>>>(keys, Mpad, k, j);
+            for (; j >= 1024; j >>= 1) launch_pdl(k_bitonic_step, (Mpad + 255) / 256, 256, 0, s, keys, Mpad, j, k);
+            launch_pdl(k_bitonic_smem, Mpad / 2048, 1024, 0, s, keys, Mpad, k, j);
         } else {
-            for (; j >= 1; j >>= 1) k_bitonic_step<<<(Mpad + 255) / 256, 256, 0, s>>>(keys, Mpad, j, k);
+            for (; j >= 1; j >>= 1) launch_pdl(k_bitonic_step, (Mpad + 255) / 256, 256, 0, s, keys, Mpad, j, k);
         }
     }
 }
 
 __global__ void k_unpack_sorted(const uint64_t* __restrict__ keys, int M, int* __restrict__ sorted,
                                 uint32_t* __restrict__ mkey) {
+    pdl_entry();
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     sorted[m] = (int)(keys[m] & 0xffffffffu);
@@ -182,11 +187,12 @@ __global__ void k_unpack_sorted(const uint64_t* __restrict__ keys, int M, int* _
 }
 void launch_unpack_sorted(const uint64_t* keys, int M, int* sorted, uint32_t* mkey, cudaStream_t s) {
     if (M == 0) return;
-    k_unpack_sorted<<<(M + 255) / 256, 256, 0, s>>>(keys, M, sorted, mkey);
+    launch_pdl(k_unpack_sorted, (M + 255) / 256, 256, 0, s, keys, M, sorted, mkey);
 }
 
 // binStart[b] = first position p with (mkey[p] >> shift) >= b, for b = 0..nbins
 __global__ void k_bins(const uint32_t* __restrict__ mkey, int M, int nbins, int shift, int* __restrict__ binStart) {
+    pdl_entry();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b > nbins) return;
     int lo = 0, hi = M;
@@ -200,7 +206,7 @@ __global__ void k_bins(const uint32_t* __restrict__ mkey, int M, int nbins, int 
     binStart[b] = lo;
 }
 void launch_bins(const uint32_t* mkey, int M, int nbins, int shift, int* binStart, cudaStream_t s) {
-    k_bins<<<(nbins + 1 + 255) / 256, 256, 0, s>>>(mkey, M, nbins, shift, binStart);
+    launch_pdl(k_bins, (nbins + 1 + 255) / 256, 256, 0, s, mkey, M, nbins, shift, binStart);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -209,6 +215,7 @@ void launch_bins(const uint32_t* mkey, int M, int nbins, int shift, int* binStar
 // compacted into an ordered list.
 __global__ void k_tile_mark(const int* __restrict__ base, int M, int W, int N, int tx, int ty, int ntx,
                             unsigned char* __restrict__ flag) {
+    pdl_entry();
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     const int b = base[m], bi = b & 0xffff, bj = (b >> 16) & 0xffff, mk = N - 1;
@@ -221,13 +228,14 @@ __global__ void k_tile_mark(const int* __restrict__ base, int M, int W, int N, i
 void launch_tile_flags(const int* base, int M, int W, int N, int tx, int ty, int ntx, unsigned char* flag,
                        cudaStream_t s) {
     if (M == 0) return;
-    k_tile_mark<<<(M + 127) / 128, 128, 0, s>>>(base, M, W, N, tx, ty, ntx, flag);
+    launch_pdl(k_tile_mark, (M + 127) / 128, 128, 0, s, base, M, W, N, tx, ty, ntx, flag);
 }
 
 // single block: raw flags in flag[0..nt), dilated flags written to flag[nt..2nt), list of
 // active tiles (ascending) to tiles[], count to *nTiles
 __global__ void k_tile_finish(unsigned char* __restrict__ flag, int ntx, int nty, int* __restrict__ tiles,
                               int* __restrict__ nTiles) {
+    pdl_entry();
     __shared__ int warpSums[32];
     __shared__ int carry;
     const int nt = ntx * nty;
@@ -274,12 +282,13 @@ __global__ void k_tile_finish(unsigned char* __restrict__ flag, int ntx, int nty
     if (threadIdx.x == 0) *nTiles = carry;
 }
 void launch_tile_finish(unsigned char* flag, int ntx, int nty, int* tiles, int* nTiles, cudaStream_t s) {
-    k_tile_finish<<<1, 1024, 0, s>>>(flag, ntx, nty, tiles, nTiles);
+    launch_pdl(k_tile_finish, 1, 1024, 0, s, flag, ntx, nty, tiles, nTiles);
 }
 
 // ------------------------------------------------------------------------------------------
 // Spring adjacency (CSR, deterministic): each marker's incident springs ordered by edge id.
 __global__ void k_degree(const int* __restrict__ edges, int E, int* __restrict__ deg) {
+    pdl_entry();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     atomicAdd(&deg[edges[2 * e]], 1);
@@ -287,6 +296,7 @@ __global__ void k_degree(const int* __restrict__ edges, int E, int* __restrict__
 }
 // single block exclusive scan of deg[0..M) into start[0..M]
 __global__ void k_scan_single(const int* __restrict__ deg, int M, int* __restrict__ start) {
+    pdl_entry();
     __shared__ int partial[1024];
     const int T = blockDim.x;
     const int chunk = (M + T - 1) / T;
@@ -313,6 +323,7 @@ __global__ void k_scan_single(const int* __restrict__ deg, int M, int* __restric
 }
 __global__ void k_adj_fill(const int* __restrict__ edges, int E, const int* __restrict__ start, int* __restrict__ cursor,
                            int* __restrict__ nbr, int* __restrict__ eid) {
+    pdl_entry();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     const int a = edges[2 * e], b = edges[2 * e + 1];
@@ -324,6 +335,7 @@ __global__ void k_adj_fill(const int* __restrict__ edges, int E, const int* __re
     eid[pb] = e;
 }
 __global__ void k_adj_sort(int M, const int* __restrict__ start, int* __restrict__ nbr, int* __restrict__ eid) {
+    pdl_entry();
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     const int s = start[m], e = start[m + 1];
@@ -341,15 +353,16 @@ __global__ void k_adj_sort(int M, const int* __restrict__ start, int* __restrict
 }
 void launch_adjacency(const int* edges, int E, int M, int* deg, int* start, int* nbr, int* eid, cudaStream_t s) {
     cudaMemsetAsync(deg, 0, sizeof(int) * (size_t)(M > 0 ? M : 1), s);
-    if (E > 0) k_degree<<<(E + 255) / 256, 256, 0, s>>>(edges, E, deg);
-    k_scan_single<<<1, 1024, 0, s>>>(deg, M, start);
+    if (E > 0) launch_pdl(k_degree, (E + 255) / 256, 256, 0, s, edges, E, deg);
+    launch_pdl(k_scan_single, 1, 1024, 0, s, deg, M, start);
     cudaMemsetAsync(deg, 0, sizeof(int) * (size_t)(M > 0 ? M : 1), s);   // reused as cursor
-    if (E > 0) k_adj_fill<<<(E + 255) / 256, 256, 0, s>>>(edges, E, start, deg, nbr, eid);
-    if (M > 0) k_adj_sort<<<(M + 255) / 256, 256, 0, s>>>(M, start, nbr, eid);
+    if (E > 0) launch_pdl(k_adj_fill, (E + 255) / 256, 256, 0, s, edges, E, start, deg, nbr, eid);
+    if (M > 0) launch_pdl(k_adj_sort, (M + 255) / 256, 256, 0, s, M, start, nbr, eid);
 }
 
 template <typename T>
 __global__ void k_adj_kappa(const int* __restrict__ eid, const double* __restrict__ kappa, int n2E, T* __restrict__ kap) {
+    pdl_entry();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n2E) return;
     kap[p] = (T)kappa[eid[p]];
@@ -357,7 +370,7 @@ __global__ void k_adj_kappa(const int* __restrict__ eid, const double* __restric
 template <typename T>
 void launch_adj_kappa(const int* eid, const double* kappa, int n2E, T* kap, cudaStream_t s) {
     if (n2E == 0) return;
-    k_adj_kappa<T><<<(n2E + 255) / 256, 256, 0, s>>>(eid, kappa, n2E, kap);
+    launch_pdl(k_adj_kappa<T>, (n2E + 255) / 256, 256, 0, s, eid, kappa, n2E, kap);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -365,6 +378,7 @@ void launch_adj_kappa(const int* eid, const double* kappa, int n2E, T* kap, cuda
 // marker and component; U, F are stored component-major: U[c*M + m]).
 template <typename T>
 __global__ void k_interp(IBK<T> k, const T* __restrict__ u, T* __restrict__ U) {
+    pdl_entry();
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
     if (m >= k.M) return;
@@ -384,7 +398,7 @@ __global__ void k_interp(IBK<T> k, const T* __restrict__ u, T* __restrict__ U) {
 template <typename T>
 void launch_interp(const IBK<T>& k, const T* u, T* U, cudaStream_t s) {
     if (k.M == 0) return;
-    k_interp<T><<<dim3((k.M + 127) / 128, 2), 128, 0, s>>>(k, u, U);
+    launch_pdl(k_interp<T>, dim3((k.M + 127) / 128, 2), 128, 0, s, k, u, U);
 }
 
 // Spring forces F_a = sum_{springs (a,b)} kappa_ab (U_b - U_a), per component (Appendix,
@@ -392,6 +406,7 @@ void launch_interp(const IBK<T>& k, const T* u, T* U, cudaStream_t s) {
 template <typename T>
 __global__ void k_spring(const int* __restrict__ start, const int* __restrict__ nbr, const T* __restrict__ kap, int M,
                          const T* __restrict__ U, T* __restrict__ F) {
+    pdl_entry();
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
     if (m >= M) return;
@@ -404,7 +419,7 @@ __global__ void k_spring(const int* __restrict__ start, const int* __restrict__ 
 template <typename T>
 void launch_spring(const int* start, const int* nbr, const T* kap, int M, const T* U, T* F, cudaStream_t s) {
     if (M == 0) return;
-    k_spring<T><<<dim3((M + 127) / 128, 2), 128, 0, s>>>(start, nbr, kap, M, U, F);
+    launch_pdl(k_spring<T>, dim3((M + 127) / 128, 2), 128, 0, s, start, nbr, kap, M, U, F);
 }
 
 // Spreading as a cell-binned gather: face (i, j) of component c collects every marker whose
@@ -436,6 +451,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_spread_thread(IBK<T> k, const T* __restrict__ F, T* __restrict__ f,
                                                        const int* __restrict__ tiles, const int* __restrict__ nTiles,
                                                        int tx, int ty, int ntx) {
+    pdl_entry();
     if ((int)blockIdx.x >= *nTiles) return;
     const int t = tiles[blockIdx.x];
     const int i = (t % ntx) * tx + threadIdx.x, j = (t / ntx) * ty + threadIdx.y;
@@ -447,6 +463,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_spread_warp(IBK<T> k, const T* __restrict__ F, T* __restrict__ f,
                                                      const int* __restrict__ tiles, const int* __restrict__ nTiles,
                                                      int tx, int ty, int ntx) {
+    pdl_entry();
     if ((int)blockIdx.x >= *nTiles) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int face = blockIdx.y * 8 + warp;
@@ -466,9 +483,9 @@ void launch_spread(const IBK<T>& k, const T* F, T* f, const int* tiles, const in
     if (maxTiles == 0) return;
     if (warpPerFace) {
         const int groups = (2 * tx * ty + 7) / 8;
-        k_spread_warp<T><<<dim3(maxTiles, groups), 256, 0, s>>>(k, F, f, tiles, nTiles, tx, ty, ntx);
+        launch_pdl(k_spread_warp<T>, dim3(maxTiles, groups), 256, 0, s, k, F, f, tiles, nTiles, tx, ty, ntx);
     } else {
-        k_spread_thread<T><<<maxTiles, dim3(tx, ty), 0, s>>>(k, F, f, tiles, nTiles, tx, ty, ntx);
+        launch_pdl(k_spread_thread<T>, maxTiles, dim3(tx, ty), 0, s, k, F, f, tiles, nTiles, tx, ty, ntx);
     }
 }
 
@@ -503,6 +520,7 @@ __global__ void k_patch_entries(const int* __restrict__ edges, const double* __r
                                 const int* __restrict__ base0, const int* __restrict__ base1,
                                 const double* __restrict__ w0, const double* __restrict__ w1, int N, int W,
                                 double inv_h2, double* __restrict__ ibd) {
+    pdl_entry();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
     if (e >= E) return;
@@ -538,7 +556,7 @@ void launch_patch_entries(const int* edges, const double* kappa, int E, const in
                           cudaStream_t s) {
     (void)M;
     if (E == 0) return;
-    k_patch_entries<<<dim3((E + 127) / 128, 2), 128, 0, s>>>(edges, kappa, E, base0, base1, w0, w1, N, W, inv_h2,
+    launch_pdl(k_patch_entries, dim3((E + 127) / 128, 2), 128, 0, s, edges, kappa, E, base0, base1, w0, w1, N, W, inv_h2,
                                                              ibd);
 }
 
@@ -548,6 +566,7 @@ __global__ void k_dense_ib(const int* __restrict__ edges, const double* __restri
                            const int* __restrict__ base0, const int* __restrict__ base1,
                            const double* __restrict__ w0, const double* __restrict__ w1, int N, int W,
                            double inv_h2, double* __restrict__ B, int useSmem) {
+    pdl_entry();
     extern __shared__ double sB[];
     const int n0 = N * N;
     const int tot = 2 * n0 * n0;
@@ -587,7 +606,7 @@ void launch_dense_ib(const int* edges, const double* kappa, int E, const int* ba
     int blocks = (E + 255) / 256;
     if (blocks > 304) blocks = 304;
     if (useSmem) cudaFuncSetAttribute(k_dense_ib, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    k_dense_ib<<<blocks, 256, useSmem ? bytes : 0, s>>>(edges, kappa, E, base0, base1, w0, w1, N, W, inv_h2, B,
+    launch_pdl(k_dense_ib, blocks, 256, useSmem ? bytes : 0, s, edges, kappa, E, base0, base1, w0, w1, N, W, inv_h2, B,
                                                          useSmem);
 }
 
@@ -610,6 +629,7 @@ __device__ __forceinline__ int wrapdiff(int d, int N) {
 // the nine o of its row, in registers (the window index is static under full unrolling).
 __global__ void k_kj_patch(IBK<double> k, const int* __restrict__ adjStart, const int* __restrict__ adjNbr,
                            const double* __restrict__ adjKap, double* __restrict__ KJ, int* __restrict__ overflow) {
+    pdl_entry();
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
     if (m >= k.M) return;
@@ -643,12 +663,13 @@ __global__ void k_kj_patch(IBK<double> k, const int* __restrict__ adjStart, cons
 void launch_kj_patch(const IBK<double>& k, const int* adjStart, const int* adjNbr, const double* adjKap, double* KJ,
                      int* overflow, cudaStream_t s) {
     if (k.M == 0) return;
-    k_kj_patch<<<dim3((k.M + 127) / 128, 2), 128, 0, s>>>(k, adjStart, adjNbr, adjKap, KJ, overflow);
+    launch_pdl(k_kj_patch, dim3((k.M + 127) / 128, 2), 128, 0, s, k, adjStart, adjNbr, adjKap, KJ, overflow);
 }
 
 __global__ void __launch_bounds__(256) k_window_fine(IBK<double> k, const double* __restrict__ KJ,
                                                      const int* __restrict__ tiles, int nTiles, int tx, int ty, int ntx,
                                                      double* __restrict__ win) {
+    pdl_entry();
     const int slot = blockIdx.x;
     if (slot >= nTiles) return;
     const int c = blockIdx.y / WD, oy = (int)(blockIdx.y % WD) - WR;
@@ -689,7 +710,7 @@ __global__ void __launch_bounds__(256) k_window_fine(IBK<double> k, const double
 void launch_window_fine(const IBK<double>& k, const double* KJ, const int* tiles, int nTiles, int tx, int ty, int ntx,
                         double* win, cudaStream_t s) {
     if (nTiles == 0 || k.M == 0) return;
-    k_window_fine<<<dim3(nTiles, 2 * WD), dim3(tx, ty), 0, s>>>(k, KJ, tiles, nTiles, tx, ty, ntx, win);
+    launch_pdl(k_window_fine, dim3(nTiles, 2 * WD), dim3(tx, ty), 0, s, k, KJ, tiles, nTiles, tx, ty, ntx, win);
 }
 
 // Coarse levels: the Galerkin product of Sec. 3.1 applied window to window,
@@ -701,6 +722,7 @@ __global__ void __launch_bounds__(256) k_window_rap(const double* __restrict__ w
                                                     int Nf, int txf, int tyf, int ntxf, const int* __restrict__ tilesC,
                                                     int nTilesC, int Nc, int txc, int tyc, int ntxc,
                                                     double* __restrict__ winC) {
+    pdl_entry();
     const int slot = blockIdx.x;
     if (slot >= nTilesC) return;
     const int c = blockIdx.y / WD, OY = (int)(blockIdx.y % WD) - WR;
@@ -769,24 +791,26 @@ __global__ void __launch_bounds__(256) k_window_rap(const double* __restrict__ w
 void launch_window_rap(const double* winF, const int* slotF, int Nf, int txf, int tyf, int ntxf, const int* tilesC,
                        int nTilesC, int Nc, int txc, int tyc, int ntxc, double* winC, cudaStream_t s) {
     if (nTilesC == 0) return;
-    k_window_rap<<<dim3(nTilesC, 2 * WD), dim3(txc, tyc), 0, s>>>(winF, slotF, Nf, txf, tyf, ntxf, tilesC, nTilesC, Nc,
+    launch_pdl(k_window_rap, dim3(nTilesC, 2 * WD), dim3(txc, tyc), 0, s, winF, slotF, Nf, txf, tyf, ntxf, tilesC, nTilesC, Nc,
                                                                  txc, tyc, ntxc, winC);
 }
 
 // slot of every tile of a level (-1 when the tile is not IB-active)
 __global__ void k_slot_map(const int* __restrict__ tiles, const int* __restrict__ nTiles, int* __restrict__ slotOf) {
+    pdl_entry();
     const int s2 = blockIdx.x * blockDim.x + threadIdx.x;
     if (s2 < *nTiles) slotOf[tiles[s2]] = s2;
 }
 void launch_slot_map(const int* tiles, const int* nTiles, int ntiles, int* slotOf, cudaStream_t s) {
     cudaMemsetAsync(slotOf, 0xff, sizeof(int) * (size_t)ntiles, s);
-    k_slot_map<<<(ntiles + 255) / 256, 256, 0, s>>>(tiles, nTiles, slotOf);
+    launch_pdl(k_slot_map, (ntiles + 255) / 256, 256, 0, s, tiles, nTiles, slotOf);
 }
 
 // Patch entries of the Vanka/SC smoothers from the windows: B(f,f) and B(f, f+e), e = +x for u
 // faces, +y for v faces; ibd is zero outside the active tiles.
 __global__ void k_window_patch(const double* __restrict__ win, const int* __restrict__ tiles, int nTiles, int N,
                                int tx, int ty, int ntx, double* __restrict__ ibd) {
+    pdl_entry();
     const int slot = blockIdx.x;
     if (slot >= nTiles) return;
     const int per = tx * ty;
@@ -805,13 +829,14 @@ __global__ void k_window_patch(const double* __restrict__ win, const int* __rest
 void launch_window_patch(const double* win, const int* tiles, int nTiles, int N, int tx, int ty, int ntx, double* ibd,
                          cudaStream_t s) {
     if (nTiles == 0) return;
-    k_window_patch<<<nTiles, dim3(tx, ty), 0, s>>>(win, tiles, nTiles, N, tx, ty, ntx, ibd);
+    launch_pdl(k_window_patch, nTiles, dim3(tx, ty), 0, s, win, tiles, nTiles, N, tx, ty, ntx, ibd);
 }
 
 // Dense coarsest block B0 (per component, n0 x n0) from the level-0 windows (rows owned by one
 // thread; window offsets that alias on the small grid add into the same entry).
 __global__ void k_window_dense(const double* __restrict__ win, const int* __restrict__ tiles, int nTiles, int N,
                                int tx, int ty, int ntx, double* __restrict__ B) {
+    pdl_entry();
     const int n0 = N * N;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= 2 * n0) return;
@@ -834,7 +859,7 @@ void launch_window_dense(const double* win, const int* tiles, int nTiles, int N,
                          cudaStream_t s) {
     if (nTiles == 0) return;
     const int rows = 2 * N * N;
-    k_window_dense<<<(rows + 127) / 128, 128, 0, s>>>(win, tiles, nTiles, N, tx, ty, ntx, B);
+    launch_pdl(k_window_dense, (rows + 127) / 128, 128, 0, s, win, tiles, nTiles, N, tx, ty, ntx, B);
 }
 
 // Apply: f^c(face) = sum_o B(face, face + o) u^c(face + o) on the IB-active tiles.  A block
@@ -844,6 +869,7 @@ template <typename T>
 __global__ void __launch_bounds__(32 * WD) k_ib_window(const T* __restrict__ win, const int* __restrict__ tiles,
                                                        const int* __restrict__ nTiles, int N, int tx, int ty, int ntx,
                                                        const T* __restrict__ u, T* __restrict__ f) {
+    pdl_entry();
     __shared__ T part[WD][32];
     const int slot = blockIdx.x;
     if (slot >= *nTiles) return;
@@ -876,7 +902,7 @@ void launch_ib_window(const T* win, const int* tiles, const int* nTiles, int max
                       const T* u, T* f, cudaStream_t s) {
     if (maxTiles == 0) return;
     const int groups = (tx * ty + 31) / 32;
-    k_ib_window<T><<<dim3(maxTiles, groups, 2), dim3(32, WD), 0, s>>>(win, tiles, nTiles, N, tx, ty, ntx, u, f);
+    launch_pdl(k_ib_window<T>, dim3(maxTiles, groups, 2), dim3(32, WD), 0, s, win, tiles, nTiles, N, tx, ty, ntx, u, f);
 }
 template void launch_ib_window<float>(const float*, const int*, const int*, int, int, int, int, int, const float*,
                                       float*, cudaStream_t);
@@ -886,12 +912,14 @@ template void launch_ib_window<double>(const double*, const int*, const int*, in
 // ------------------------------------------------------------------------------------------
 // (M x 2) interleaved <-> component-major [x (M) | y (M)]
 __global__ void k_deinterleave(const double* __restrict__ in, int M, double* __restrict__ out) {
+    pdl_entry();
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     out[m] = in[2 * m];
     out[M + m] = in[2 * m + 1];
 }
 __global__ void k_interleave(const double* __restrict__ in, int M, double* __restrict__ out) {
+    pdl_entry();
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     out[2 * m] = in[m];
@@ -899,23 +927,24 @@ __global__ void k_interleave(const double* __restrict__ in, int M, double* __res
 }
 void launch_deinterleave(const double* in, int M, double* out, cudaStream_t s) {
     if (M == 0) return;
-    k_deinterleave<<<(M + 255) / 256, 256, 0, s>>>(in, M, out);
+    launch_pdl(k_deinterleave, (M + 255) / 256, 256, 0, s, in, M, out);
 }
 void launch_interleave(const double* in, int M, double* out, cudaStream_t s) {
     if (M == 0) return;
-    k_interleave<<<(M + 255) / 256, 256, 0, s>>>(in, M, out);
+    launch_pdl(k_interleave, (M + 255) / 256, 256, 0, s, in, M, out);
 }
 
 // Deterministic start vector of the power iterations: Knuth's multiplicative hash of k+1,
 // (k+1) * 2654435761 mod 2^32, mapped to [-1/2, 1/2).
 __global__ void k_hash_vector(double* __restrict__ x, int64_t n) {
+    pdl_entry();
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t v = (uint32_t)(k + 1) * 2654435761u;
         x[k] = (double)v / 4294967296.0 - 0.5;
     }
 }
 void launch_hash_vector(double* x, int64_t n, cudaStream_t s) {
-    k_hash_vector<<<num_blocks_for(n), 256, 0, s>>>(x, n);
+    launch_pdl(k_hash_vector, num_blocks_for(n), 256, 0, s, x, n);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -927,6 +956,7 @@ void launch_hash_vector(double* x, int64_t n, cudaStream_t s) {
 // Lam, Y, KY, KL are component-major (M | M).
 __global__ void k_grad_kappa(const int* __restrict__ edges, int E, int M, const double* __restrict__ Lam,
                              const double* __restrict__ Y, double* __restrict__ dkappa) {
+    pdl_entry();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     const int a = edges[2 * e], b = edges[2 * e + 1];
@@ -937,6 +967,7 @@ __global__ void k_grad_kappa(const int* __restrict__ edges, int E, int M, const 
 __global__ void k_grad_X(const double* __restrict__ X, int M, int N, const double* __restrict__ w,
                          const double* __restrict__ lam, const double* __restrict__ KY, const double* __restrict__ KL,
                          double dt, double acoef, double* __restrict__ dX) {
+    pdl_entry();
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     const int n = N * N, mk = N - 1;
@@ -977,12 +1008,12 @@ __global__ void k_grad_X(const double* __restrict__ X, int M, int N, const doubl
 void launch_grad_kappa(const int* edges, int E, int M, const double* Lam, const double* Y, double* dkappa,
                        cudaStream_t s) {
     if (E == 0) return;
-    k_grad_kappa<<<(E + 255) / 256, 256, 0, s>>>(edges, E, M, Lam, Y, dkappa);
+    launch_pdl(k_grad_kappa, (E + 255) / 256, 256, 0, s, edges, E, M, Lam, Y, dkappa);
 }
 void launch_grad_X(const double* X, int M, int N, const double* w, const double* lam, const double* KY,
                    const double* KL, double dt, double acoef, double* dX, cudaStream_t s) {
     if (M == 0) return;
-    k_grad_X<<<(M + 127) / 128, 128, 0, s>>>(X, M, N, w, lam, KY, KL, dt, acoef, dX);
+    launch_pdl(k_grad_X, (M + 127) / 128, 128, 0, s, X, M, N, w, lam, KY, KL, dt, acoef, dX);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -28,6 +28,7 @@ __device__ __forceinline__ double block_sum(double v) {
 
 __global__ void k_dot_partials(const double* __restrict__ x, const double* __restrict__ y, int64_t n,
                                double* __restrict__ partials) {
+    pdl_entry();
     double s = 0.0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
         s += x[k] * y[k];
@@ -35,12 +36,13 @@ __global__ void k_dot_partials(const double* __restrict__ x, const double* __res
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 void launch_dot_partials(const double* x, const double* y, int64_t n, double* partials, int nblk, cudaStream_t s) {
-    k_dot_partials<<<nblk, 256, 0, s>>>(x, y, n, partials);
+    launch_pdl(k_dot_partials, nblk, 256, 0, s, x, y, n, partials);
 }
 
 // partials[i * nblk + b] = sum over block b's slice of V_i . w, for i < k
 __global__ void k_multidot(const double* __restrict__ V, int64_t ld, const double* __restrict__ w, int64_t n,
                            double* __restrict__ partials) {
+    pdl_entry();
     const int i = blockIdx.y;
     const double* v = V + (int64_t)i * ld;
     double s = 0.0;
@@ -51,22 +53,24 @@ __global__ void k_multidot(const double* __restrict__ V, int64_t ld, const doubl
 }
 void launch_multidot(const double* V, int64_t ld, int k, const double* w, int64_t n, double* partials, int nblk,
                      cudaStream_t s) {
-    k_multidot<<<dim3(nblk, k), 256, 0, s>>>(V, ld, w, n, partials);
+    launch_pdl(k_multidot, dim3(nblk, k), 256, 0, s, V, ld, w, n, partials);
 }
 
 __global__ void k_reduce_partials(const double* __restrict__ partials, int nblk, double* __restrict__ out) {
+    pdl_entry();
     double s = 0.0;
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partials[(int64_t)blockIdx.x * nblk + b];
     s = block_sum(s);
     if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 void launch_reduce_partials(const double* partials, int k, int nblk, double* out, cudaStream_t s) {
-    k_reduce_partials<<<k, 256, 0, s>>>(partials, nblk, out);
+    launch_pdl(k_reduce_partials, k, 256, 0, s, partials, nblk, out);
 }
 
 // y += sign * sum_{i<k} coef[i] V_i
 __global__ void k_multi_axpy(const double* __restrict__ V, int64_t ld, int k, const double* __restrict__ coef,
                              double sign, double* __restrict__ y, int64_t n) {
+    pdl_entry();
     __shared__ double c[128];
     for (int t = threadIdx.x; t < k; t += blockDim.x) c[t] = sign * coef[t];
     __syncthreads();
@@ -78,22 +82,24 @@ __global__ void k_multi_axpy(const double* __restrict__ V, int64_t ld, int k, co
 }
 void launch_multi_axpy(const double* V, int64_t ld, int k, const double* coef, double sign, double* y, int64_t n,
                        cudaStream_t s) {
-    k_multi_axpy<<<num_blocks_for(n), 256, 0, s>>>(V, ld, k, coef, sign, y, n);
+    launch_pdl(k_multi_axpy, num_blocks_for(n), 256, 0, s, V, ld, k, coef, sign, y, n);
 }
 
 // x *= 1 / sqrt(vals[idx])   (normalisation of the next Arnoldi vector)
 __global__ void k_scale_rsqrt(double* __restrict__ x, const double* __restrict__ vals, int idx, int64_t n) {
+    pdl_entry();
     const double nrm = sqrt(vals[idx]);
     const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
         x[k] *= inv;
 }
 void launch_scale(double* x, const double* vals, int idx, int64_t n, cudaStream_t s) {
-    k_scale_rsqrt<<<num_blocks_for(n), 256, 0, s>>>(x, vals, idx, n);
+    launch_pdl(k_scale_rsqrt, num_blocks_for(n), 256, 0, s, x, vals, idx, n);
 }
 
 // gauge projection: means of the u, v, p blocks and their removal (mask bit b = block b)
 __global__ void k_block_means(const double* __restrict__ x, int64_t n, double* __restrict__ partials) {
+    pdl_entry();
     const double* xb = x + blockIdx.y * n;
     double s = 0.0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
@@ -102,10 +108,11 @@ __global__ void k_block_means(const double* __restrict__ x, int64_t n, double* _
     if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 void launch_block_means(const double* x, int N, int nblocks_vec, double* partials, int nblk, cudaStream_t s) {
-    k_block_means<<<dim3(nblk, nblocks_vec), 256, 0, s>>>(x, (int64_t)N * N, partials);
+    launch_pdl(k_block_means, dim3(nblk, nblocks_vec), 256, 0, s, x, (int64_t)N * N, partials);
 }
 __global__ void k_subtract_means(double* __restrict__ x, int64_t n, const double* __restrict__ partials, int nblk,
                                  int mask) {
+    pdl_entry();
     __shared__ double mean[3];
     if (threadIdx.x < 32) {
         for (int b = 0; b < 3; ++b) {
@@ -121,7 +128,7 @@ __global__ void k_subtract_means(double* __restrict__ x, int64_t n, const double
 }
 void launch_subtract_means(double* x, int N, const double* partials, int nblk, int mask, cudaStream_t s) {
     const int64_t n = (int64_t)N * N;
-    k_subtract_means<<<num_blocks_for(3 * n), 256, 0, s>>>(x, n, partials, nblk, mask);
+    launch_pdl(k_subtract_means, num_blocks_for(3 * n), 256, 0, s, x, n, partials, nblk, mask);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -129,6 +136,7 @@ void launch_subtract_means(double* x, int N, const double* partials, int nblk, i
 // the constant velocity components when rho = 0), augmented with the identity: Aug = [L0+ZZ^T | I].
 __global__ void k_assemble_L0(int N, double rho, double mu, double dt, const double* __restrict__ B,
                               double* __restrict__ Aug) {
+    pdl_entry();
     const int n0 = N * N, n = 3 * n0, mk = N - 1;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -168,7 +176,7 @@ __global__ void k_assemble_L0(int N, double rho, double mu, double dt, const dou
 }
 void launch_assemble_L0(int N0, double rho, double mu, double dt, const double* B, double* Aug, cudaStream_t s) {
     const int n = 3 * N0 * N0;
-    k_assemble_L0<<<(n + 127) / 128, 128, 0, s>>>(N0, rho, mu, dt, B, Aug);
+    launch_pdl(k_assemble_L0, (n + 127) / 128, 128, 0, s, N0, rho, mu, dt, B, Aug);
 }
 
 // In-place Gauss-Jordan elimination with partial pivoting on Aug (n x 2n, row-major) by one
@@ -176,6 +184,7 @@ void launch_assemble_L0(int N0, double rho, double mu, double dt, const double* 
 // (Fallback for coarsest grids too large for the cluster version below.)
 __global__ void __launch_bounds__(1024) k_gauss_jordan(double* __restrict__ A, int n, int* __restrict__ info,
                                                        int* __restrict__ piv) {
+    pdl_entry();
     extern __shared__ double fac[];   // n factors
     __shared__ int pivs;
     __shared__ double wv[32];
@@ -251,6 +260,7 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(double* __restrict__ A, i
 // are not swapped: piv[k] records the pivot row of column k, so inverse row k = Aug[piv[k]][n:].
 __global__ void __launch_bounds__(256) k_gauss_jordan_cluster(double* __restrict__ A, int n, int rpc,
                                                               int* __restrict__ info, int* __restrict__ piv) {
+    pdl_entry();
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ double sm[];
     const int ld = 2 * n;
@@ -374,13 +384,14 @@ void launch_gauss_jordan(double* Aug, int n, int* info, int* piv, cudaStream_t s
         if (cudaLaunchKernelEx(&cfg, k_gauss_jordan_cluster, Aug, n, rpc, info, piv) == cudaSuccess) return;
         cudaGetLastError();
     }
-    k_gauss_jordan<<<1, 1024, sizeof(double) * n, s>>>(Aug, n, info, piv);
+    launch_pdl(k_gauss_jordan, 1, 1024, sizeof(double) * n, s, Aug, n, info, piv);
 }
 
 // Pinv = (L0 + Z Z^T)^{-1} - Z Z^T, the pseudo-inverse of the symmetric L0 whose kernel is span Z;
 // row r of the inverse is the right half of Aug's pivot row piv[r].
 __global__ void k_extract_pinv(const double* __restrict__ Aug, const int* __restrict__ piv, int n, int N0, double rho,
                                double* __restrict__ P) {
+    pdl_entry();
     const int r = blockIdx.y;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
@@ -391,12 +402,13 @@ __global__ void k_extract_pinv(const double* __restrict__ Aug, const int* __rest
     P[(int64_t)r * n + c] = v;
 }
 void launch_extract_pinv(const double* Aug, const int* piv, int n, int N0, double rho, double* Pinv, cudaStream_t s) {
-    k_extract_pinv<<<dim3((n + 127) / 128, n), 128, 0, s>>>(Aug, piv, n, N0, rho, Pinv);
+    launch_pdl(k_extract_pinv, dim3((n + 127) / 128, n), 128, 0, s, Aug, piv, n, N0, rho, Pinv);
 }
 
 // x = Pinv b, one warp per row, FP64 accumulation for both precisions
 template <typename T>
 __global__ void k_coarse_apply(const double* __restrict__ P, int n, const T* __restrict__ b, T* __restrict__ x) {
+    pdl_entry();
     const int lane = threadIdx.x & 31;
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= n) return;
@@ -408,18 +420,19 @@ __global__ void k_coarse_apply(const double* __restrict__ P, int n, const T* __r
 }
 template <typename T>
 void launch_coarse_apply(const double* Pinv, int n, const T* b, T* x, cudaStream_t s) {
-    k_coarse_apply<T><<<(n + 7) / 8, 256, 0, s>>>(Pinv, n, b, x);
+    launch_pdl(k_coarse_apply<T>, (n + 7) / 8, 256, 0, s, Pinv, n, b, x);
 }
 template void launch_coarse_apply<float>(const double*, int, const float*, float*, cudaStream_t);
 template void launch_coarse_apply<double>(const double*, int, const double*, double*, cudaStream_t);
 
 __global__ void k_check_finite(const double* __restrict__ x, int64_t n, int* __restrict__ flag) {
+    pdl_entry();
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
         if (!isfinite(x[k])) *flag = 1;
 }
 void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t s) {
     if (n == 0) return;
-    k_check_finite<<<num_blocks_for(n), 256, 0, s>>>(x, n, flag);
+    launch_pdl(k_check_finite, num_blocks_for(n), 256, 0, s, x, n, flag);
 }
 
 }  // namespace sib

@@ -21,6 +21,33 @@ constexpr int WD = 2 * WR + 1;
 constexpr int WIN_SIZE = WD * WD;
 
 // ------------------------------------------------------------------------------------------
+// Programmatic dependent launch: every kernel waits for the grids it depends on before touching
+// memory, then lets its dependents be scheduled (they start waiting while this grid finishes), so
+// consecutive kernels of a stream or graph overlap their launch latency.  Dependents become
+// eligible only after every block of this grid has started, so early triggering cannot starve it.
+__device__ __forceinline__ void pdl_entry() {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+#endif
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// ------------------------------------------------------------------------------------------
 // Morton order of a cell (i, j): bits of i on even positions, bits of j on odd positions.
 // The bins of level l are the Morton codes of the fine-level bins shifted right by 2(lmax-l).
 __host__ __device__ inline uint32_t part1by1(uint32_t x) {

@@ -407,3 +407,23 @@ def test_vcycle_large_grid_against_oracle():
     assert rel(host(S.vcycle(cu(b))), ref) < TOL64
     b32 = b.astype(np.float32).astype(np.float64)
     assert rel(host(S.vcycle(cu(b32, torch.float32))), H.vcycle(b32)) < 1e-4
+
+
+def test_iteration_counts_match_stored_oracle_histories():
+    """FGMRES iteration counts and residual histories against the stored oracle runs
+    (tests/golden/fgmres_histories.json): equal counts with the FP64 V-cycle, within one with FP32."""
+    import json
+    import os
+    from tests.golden import make_golden
+    stored = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                         "fgmres_histories.json")))
+    for key, rec in stored.items():
+        name, sm = key.split("/")
+        prob = make_golden.CASES[name]()
+        S = sib.solver_for(prob, smoother=sib.SMOOTHER_SC if sm == "sc" else sib.SMOOTHER_VANKA, vcycle_fp32=0)
+        S.solve(cu(prob.g), allow_unconverged=True)
+        assert S.stats.iterations == rec["iterations"], key
+        np.testing.assert_allclose(S.stats.as_dict()["history"], rec["history"], rtol=1e-7, err_msg=key)
+        S.set_options(vcycle_fp32=1)
+        S.solve(cu(prob.g), allow_unconverged=True)
+        assert abs(S.stats.iterations - rec["iterations"]) <= 1, key
