@@ -435,4 +435,205 @@ void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t s) 
     launch_pdl(k_check_finite, num_blocks_for(n), 256, 0, s, x, n, flag);
 }
 
+
+// ------------------------------------------------------------------------------------------
+// Flexible GMRES cycle on the device (the same recurrence as the host loop: CGS2 Arnoldi,
+// Givens rotations, stop at ||r|| <= tol, at the cycle length or at the iteration cap).
+__global__ void k_fg_init(FgDev* st, double beta, int m, int max_it, double tol) {
+    pdl_entry();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    st->j = 0;
+    st->jn = 0;
+    st->its = 0;
+    st->k = 0;
+    st->converged = 0;
+    st->m = m;
+    st->max_it = max_it;
+    st->tol = tol;
+    st->est = beta;
+    st->beta = beta;
+    st->inv_hn = 0.0;
+    for (int i = 0; i <= FG_MAXM; ++i) st->g[i] = 0.0;
+    st->g[0] = beta;
+    st->hist[0] = beta;
+}
+void launch_fg_init(FgDev* st, double beta, int m, int max_it, double tol, cudaStream_t s) {
+    launch_pdl(k_fg_init, 1, 1, 0, s, st, beta, m, max_it, tol);
+}
+
+template <typename T>
+__global__ void k_fg_prep(const double* __restrict__ V, int64_t n, FgDev* st, T* __restrict__ dst) {
+    pdl_entry();
+    const int j = st->jn;
+    const double* v = V + (int64_t)j * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = (T)v[e];
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->j = j;
+}
+template <typename T>
+void launch_fg_prep(const double* V, int64_t n, FgDev* st, T* dst, cudaStream_t s) {
+    launch_pdl(k_fg_prep<T>, num_blocks_for(n), 256, 0, s, V, n, st, dst);
+}
+
+template <typename T>
+__global__ void k_fg_zstore(const T* __restrict__ src, double* __restrict__ Z, int64_t n, const FgDev* st,
+                            double* __restrict__ zcur) {
+    pdl_entry();
+    double* z = Z + (int64_t)st->j * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)src[e];
+        z[e] = v;
+        zcur[e] = v;
+    }
+}
+template <typename T>
+void launch_fg_zstore(const T* src, double* Z, int64_t n, const FgDev* st, double* zcur, cudaStream_t s) {
+    launch_pdl(k_fg_zstore<T>, num_blocks_for(n), 256, 0, s, src, Z, n, st, zcur);
+}
+template void launch_fg_prep<float>(const double*, int64_t, FgDev*, float*, cudaStream_t);
+template void launch_fg_prep<double>(const double*, int64_t, FgDev*, double*, cudaStream_t);
+template void launch_fg_zstore<float>(const float*, double*, int64_t, const FgDev*, double*, cudaStream_t);
+template void launch_fg_zstore<double>(const double*, double*, int64_t, const FgDev*, double*, cudaStream_t);
+
+// partials[i * nblk + b] = slice b of V_i . w for all i <= j.  Block (b, c) takes vectors
+// 8c .. 8c+7 (blocks past j return at once) and slice b of the elements, accumulates the eight
+// products in registers, and reduces them through warp shuffles and one shared-memory pass.
+constexpr int MD_CHUNK = 8;
+__global__ void __launch_bounds__(256) k_multidot_dev(const double* __restrict__ V, int64_t ld,
+                                                      const double* __restrict__ w, int64_t n,
+                                                      double* __restrict__ partials, const FgDev* st) {
+    pdl_entry();
+    __shared__ double ws[8][MD_CHUNK];
+    const int j = st->j;
+    const int i0 = blockIdx.y * MD_CHUNK;
+    if (i0 > j) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double acc[MD_CHUNK];
+#pragma unroll
+    for (int q = 0; q < MD_CHUNK; ++q) acc[q] = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += stride) {
+        const double we = w[e];
+#pragma unroll
+        for (int q = 0; q < MD_CHUNK; ++q)
+            if (i0 + q <= j) acc[q] += V[(int64_t)(i0 + q) * ld + e] * we;
+    }
+#pragma unroll
+    for (int q = 0; q < MD_CHUNK; ++q) {
+        double v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) ws[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < MD_CHUNK && i0 + (int)threadIdx.x <= j) {
+        double v = 0.0;
+        for (int q = 0; q < 8; ++q) v += ws[q][threadIdx.x];
+        partials[(int64_t)(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = v;
+    }
+}
+void launch_multidot_dev(const double* V, int64_t ld, const double* w, int64_t n, double* partials, int nblk,
+                         const FgDev* st, cudaStream_t s) {
+    (void)nblk;
+    launch_pdl(k_multidot_dev, dim3(MD_SLICES, (FG_MAXM + 1 + MD_CHUNK - 1) / MD_CHUNK), 256, 0, s, V, ld, w, n,
+               partials, st);
+}
+__global__ void k_reduce_partials_dev(const double* __restrict__ partials, int nblk, double* __restrict__ out,
+                                      const FgDev* st) {
+    pdl_entry();
+    if ((int)blockIdx.x > st->j) return;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partials[(int64_t)blockIdx.x * nblk + b];
+    s = block_sum(s);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+void launch_reduce_partials_dev(const double* partials, int nblk, double* out, const FgDev* st, cudaStream_t s) {
+    (void)nblk;
+    launch_pdl(k_reduce_partials_dev, FG_MAXM + 1, 128, 0, s, partials, MD_SLICES, out, st);
+}
+// y += sign * sum_{i<k} coef[i] V_i with k = j + 1 (useK = 0) or k = st->k (useK = 1)
+__global__ void k_multi_axpy_dev(const double* __restrict__ V, int64_t ld, const double* __restrict__ coef,
+                                 double sign, double* __restrict__ y, int64_t n, const FgDev* st, int useK) {
+    pdl_entry();
+    __shared__ double c[FG_MAXM + 1];
+    const int k = useK ? st->k : st->j + 1;
+    for (int t = threadIdx.x; t < k; t += blockDim.x) c[t] = sign * coef[t];
+    __syncthreads();
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = y[e];
+        for (int i = 0; i < k; ++i) acc += c[i] * V[(int64_t)i * ld + e];
+        y[e] = acc;
+    }
+}
+void launch_multi_axpy_dev(const double* V, int64_t ld, const double* coef, double sign, double* y, int64_t n,
+                           const FgDev* st, int useK, cudaStream_t s) {
+    launch_pdl(k_multi_axpy_dev, num_blocks_for(n), 256, 0, s, V, ld, coef, sign, y, n, st, useK);
+}
+
+// One thread: Hessenberg column j from the two Gram-Schmidt passes, previous and new Givens
+// rotation, residual estimate, and the loop decision (always terminates: the iteration cap and
+// the cycle length bound it, and a non-finite estimate or a zero new norm stops it).
+__global__ void k_fg_arnoldi(FgDev* st, const double* __restrict__ h1, const double* __restrict__ h2,
+                             const double* __restrict__ nrm, cudaGraphConditionalHandle handle) {
+    pdl_entry();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int j = st->j;
+    double* Hj = st->H + (size_t)j * (FG_MAXM + 1);
+    for (int i = 0; i <= j; ++i) Hj[i] = h1[i] + h2[i];
+    const double hn = sqrt(nrm[0]);
+    Hj[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double a = Hj[i], b = Hj[i + 1];
+        Hj[i] = st->cs[i] * a + st->sn[i] * b;
+        Hj[i + 1] = -st->sn[i] * a + st->cs[i] * b;
+    }
+    const double d = hypot(Hj[j], Hj[j + 1]);
+    st->cs[j] = Hj[j] / d;
+    st->sn[j] = Hj[j + 1] / d;
+    Hj[j] = d;
+    Hj[j + 1] = 0.0;
+    st->g[j + 1] = -st->sn[j] * st->g[j];
+    st->g[j] = st->cs[j] * st->g[j];
+    const double est = fabs(st->g[j + 1]);
+    st->its += 1;
+    st->est = est;
+    st->hist[j + 1] = est;
+    const bool conv = est <= st->tol;
+    const bool stop = conv || !(hn > 0.0) || !isfinite(est) || !isfinite(d) || st->its >= st->max_it || j + 1 >= st->m;
+    st->inv_hn = hn > 0.0 ? 1.0 / hn : 0.0;
+    st->jn = j + 1;
+    if (stop) {
+        st->k = j + 1;
+        st->converged = (conv || hn == 0.0) ? 1 : 0;   // a zero new direction: the solution is exact
+    }
+    cudaGraphSetConditional(handle, stop ? 0u : 1u);
+}
+void launch_fg_arnoldi(FgDev* st, const double* h1, const double* h2, const double* nrm,
+                       cudaGraphConditionalHandle handle, cudaStream_t s) {
+    launch_pdl(k_fg_arnoldi, 1, 32, 0, s, st, h1, h2, nrm, handle);
+}
+
+__global__ void k_fg_store_v(const double* __restrict__ w, double* __restrict__ V, int64_t n, const FgDev* st) {
+    pdl_entry();
+    const double inv = st->inv_hn;
+    double* v = V + (int64_t)(st->j + 1) * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        v[e] = w[e] * inv;
+}
+void launch_fg_store_v(const double* w, double* V, int64_t n, const FgDev* st, cudaStream_t s) {
+    launch_pdl(k_fg_store_v, num_blocks_for(n), 256, 0, s, w, V, n, st);
+}
+
+// y = H^{-1} g on the k x k upper triangle (one thread)
+__global__ void k_fg_backsolve(FgDev* st) {
+    pdl_entry();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int k = st->k;
+    for (int i = k - 1; i >= 0; --i) {
+        double acc = st->g[i];
+        for (int q = i + 1; q < k; ++q) acc -= st->H[(size_t)q * (FG_MAXM + 1) + i] * st->y[q];
+        st->y[i] = acc / st->H[(size_t)i * (FG_MAXM + 1) + i];
+    }
+}
+void launch_fg_backsolve(FgDev* st, cudaStream_t s) { launch_pdl(k_fg_backsolve, 1, 32, 0, s, st); }
+
 }  // namespace sib

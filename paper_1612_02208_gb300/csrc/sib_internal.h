@@ -184,6 +184,17 @@ void launch_grad_kappa(const int* edges, int E, int M, const double* Lam, const 
 void launch_grad_X(const double* X, int M, int N, const double* w, const double* lam, const double* KY,
                    const double* KL, double dt, double acoef, double* dX, cudaStream_t s);
 
+// Device-side state of one flexible-GMRES cycle (the loop runs as a conditional graph node).
+constexpr int FG_MAXM = 100;                 // restart length cap
+constexpr int MD_SLICES = 128;               // element slices of the device multi-dot
+struct FgDev {
+    int j, jn, its, k, converged, m, max_it, pad;
+    double tol, est, inv_hn, beta;
+    double g[FG_MAXM + 1], cs[FG_MAXM], sn[FG_MAXM], y[FG_MAXM];
+    double hist[FG_MAXM + 1];                // residual estimates of this cycle, hist[0] = beta
+    double H[(FG_MAXM + 1) * FG_MAXM];       // column j at H[j * (FG_MAXM + 1)]
+};
+
 // launchers (kernels_krylov.cu)
 void launch_dot_partials(const double* x, const double* y, int64_t n, double* partials, int nblk, cudaStream_t s);
 void launch_multidot(const double* V, int64_t ld, int k, const double* w, int64_t n, double* partials, int nblk,
@@ -199,6 +210,20 @@ void launch_gauss_jordan(double* Aug, int n, int* info, int* piv, cudaStream_t s
 void launch_extract_pinv(const double* Aug, const int* piv, int n, int N0, double rho, double* Pinv, cudaStream_t s);
 template <typename T> void launch_coarse_apply(const double* Pinv, int n, const T* b, T* x, cudaStream_t s);
 void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t s);
+
+void launch_fg_init(FgDev* st, double beta, int m, int max_it, double tol, cudaStream_t s);
+template <typename T> void launch_fg_prep(const double* V, int64_t n, FgDev* st, T* dst, cudaStream_t s);
+template <typename T> void launch_fg_zstore(const T* src, double* Z, int64_t n, const FgDev* st, double* zcur,
+                                            cudaStream_t s);
+void launch_multidot_dev(const double* V, int64_t ld, const double* w, int64_t n, double* partials, int nblk,
+                         const FgDev* st, cudaStream_t s);
+void launch_reduce_partials_dev(const double* partials, int nblk, double* out, const FgDev* st, cudaStream_t s);
+void launch_multi_axpy_dev(const double* V, int64_t ld, const double* coef, double sign, double* y, int64_t n,
+                           const FgDev* st, int useK, cudaStream_t s);
+void launch_fg_arnoldi(FgDev* st, const double* h1, const double* h2, const double* nrm,
+                       cudaGraphConditionalHandle handle, cudaStream_t s);
+void launch_fg_store_v(const double* w, double* V, int64_t n, const FgDev* st, cudaStream_t s);
+void launch_fg_backsolve(FgDev* st, cudaStream_t s);
 
 int num_blocks_for(int64_t n);
 

@@ -1,6 +1,7 @@
 // libsib: solver context, set-up, V-cycle (Alg. 1), flexible GMRES and the C ABI of sib.h.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <stdexcept>
@@ -129,6 +130,12 @@ struct sib_ctx {
     cudaGraphExec_t vg[2] = {nullptr, nullptr};
     void* vgOut[2] = {nullptr, nullptr};
     int64_t vgNodes[2] = {0, 0};
+    // device-side FGMRES cycle (conditional graph)
+    FgDev* fg = nullptr;
+    double* zcur = nullptr;
+    cudaGraphExec_t fgExec[2] = {nullptr, nullptr};
+    int64_t fgBody[2] = {0, 0}, fgTail[2] = {0, 0};
+    bool fgUnavailable = false;
 };
 
 namespace {
@@ -175,6 +182,8 @@ void invalidate_graphs(sib_ctx* c) {
         if (c->vg[p]) cudaGraphExecDestroy(c->vg[p]);
         c->vg[p] = nullptr;
         c->vgOut[p] = nullptr;
+        if (c->fgExec[p]) cudaGraphExecDestroy(c->fgExec[p]);
+        c->fgExec[p] = nullptr;
     }
 }
 
@@ -968,6 +977,153 @@ int fgmres(sib_ctx* c, const double* b, double* x, sib_stats* st, cudaStream_t s
     return converged ? SIB_OK : SIB_ERR_NOT_CONVERGED;
 }
 
+// ---- device-side FGMRES cycle: a conditional WHILE graph node runs the iterations -------------
+template <typename T>
+void build_fg_graph(sib_ctx* c) {
+    const int pi = Prec<T>::id;
+    const int64_t n = n3f(c);
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    const int64_t before = c->launches;
+    try {
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = h;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        CK(cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &p));
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        cudaStream_t s = c->cap;
+        CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        try {
+            Level& lv = c->L[c->lmax];
+            KL(c, launch_fg_prep<T>(c->V, n, c->fg, (T*)lv.p[pi].b, s));
+            T* out = vcycle_level<T>(c, c->lmax, s);
+            KL(c, launch_fg_zstore<T>(out, c->Z, n, c->fg, c->zcur, s));
+            matvec(c, c->zcur, c->res, s);
+            KL(c, launch_multidot_dev(c->V, n, c->res, n, c->part, NBLK, c->fg, s));
+            KL(c, launch_reduce_partials_dev(c->part, NBLK, c->scal, c->fg, s));
+            KL(c, launch_multi_axpy_dev(c->V, n, c->scal, -1.0, c->res, n, c->fg, 0, s));
+            KL(c, launch_multidot_dev(c->V, n, c->res, n, c->part, NBLK, c->fg, s));
+            KL(c, launch_reduce_partials_dev(c->part, NBLK, c->scal + 128, c->fg, s));
+            KL(c, launch_multi_axpy_dev(c->V, n, c->scal + 128, -1.0, c->res, n, c->fg, 0, s));
+            dot_into(c, c->res, c->res, n, c->scal + 256, s);
+            KL(c, launch_fg_arnoldi(c->fg, c->scal, c->scal + 128, c->scal + 256, h, s));
+            KL(c, launch_fg_store_v(c->res, c->V, n, c->fg, s));
+        } catch (...) {
+            cudaGraph_t tmp;
+            cudaStreamEndCapture(s, &tmp);
+            throw;
+        }
+        cudaGraph_t tmp;
+        CK(cudaStreamEndCapture(s, &tmp));
+        const int64_t mid = c->launches;
+        CK(cudaStreamBeginCaptureToGraph(s, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+        const double* y = reinterpret_cast<const double*>(reinterpret_cast<const char*>(c->fg) + offsetof(FgDev, y));
+        KL(c, launch_fg_backsolve(c->fg, s));
+        KL(c, launch_multi_axpy_dev(c->Z, n, y, 1.0, c->sol, n, c->fg, 1, s));
+        CK(cudaStreamEndCapture(s, &tmp));
+        CK(cudaGraphInstantiate(&c->fgExec[pi], g, 0));
+        c->fgBody[pi] = mid - before;
+        c->fgTail[pi] = c->launches - mid;
+    } catch (...) {
+        c->launches = before;
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        throw;
+    }
+    c->launches = before;
+    cudaGraphDestroy(g);
+}
+
+// FGMRES with the cycles on the device; x is accumulated in c->sol.  Synchronises once per cycle.
+int fgmres_device(sib_ctx* c, const double* b, double* w, sib_stats* st, cudaStream_t s) {
+    const int64_t n = n3f(c);
+    const int max_it = c->opts.max_it;
+    const int pi = c->opts.vcycle_fp32 ? 1 : 0;
+    double* hb = c->hbuf;
+    double* x = c->sol;
+    if (!c->fgExec[pi]) {
+        if (pi == 1)
+            build_fg_graph<float>(c);
+        else
+            build_fg_graph<double>(c);
+    }
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    dot(c, b, b, n, c->scal + 256, s);
+    CK(cudaMemcpyAsync(hb, c->scal + 256, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double bnorm = std::sqrt(hb[0]);
+    if (!std::isfinite(bnorm)) throw SibError(SIB_ERR_NONFINITE, "right-hand side is not finite");
+    std::vector<double> hist{bnorm};
+    int its = 0;
+    bool converged = bnorm == 0.0;
+    double est = bnorm;
+    while (!converged && its < max_it) {
+        double* r = c->V;
+        double beta;
+        if (its == 0) {
+            KL(c, (launch_convert<double, double>(b, r, n, s)));
+            beta = bnorm;
+        } else {
+            matvec(c, x, c->res, s);
+            KL(c, launch_axpby<double>(1.0, b, -1.0, c->res, r, n, s));
+            dot(c, r, r, n, c->scal + 256, s);
+            CK(cudaMemcpyAsync(hb, c->scal + 256, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            beta = std::sqrt(hb[0]);
+        }
+        if (beta == 0.0) {
+            converged = true;
+            break;
+        }
+        hb[450] = beta * beta;
+        CK(cudaMemcpyAsync(c->scal + 258, hb + 450, sizeof(double), cudaMemcpyHostToDevice, s));
+        KL(c, launch_scale(r, c->scal, 258, n, s));
+        const int m = std::min(c->mcap, max_it - its);
+        KL(c, launch_fg_init(c->fg, beta, m, m, c->opts.rtol * bnorm, s));
+        CK(cudaGraphLaunch(c->fgExec[pi], s));
+        // cycle results: the int header (j, jn, its, k, converged, ...) and (tol, est, ...)
+        int hdr[8];
+        double dv[4];
+        CK(cudaMemcpyAsync(hdr, c->fg, sizeof(hdr), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(dv, reinterpret_cast<const char*>(c->fg) + offsetof(FgDev, tol), sizeof(dv),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hb + 300, reinterpret_cast<const char*>(c->fg) + offsetof(FgDev, hist),
+                           sizeof(double) * (FG_MAXM + 1), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const int cyc = hdr[2];
+        c->launches += (int64_t)cyc * c->fgBody[pi] + c->fgTail[pi];
+        for (int i = 1; i <= cyc; ++i) hist.push_back(hb[300 + i]);
+        its += cyc;
+        est = dv[1];
+        converged = hdr[4] != 0;
+        if (!std::isfinite(est)) throw SibError(SIB_ERR_NONFINITE, "non-finite value in FGMRES");
+        if (cyc == 0) break;
+    }
+    project(c, x, s);
+    matvec(c, x, c->res, s);
+    KL(c, launch_axpby<double>(1.0, b, -1.0, c->res, c->res, n, s));
+    dot(c, c->res, c->res, n, c->scal + 256, s);
+    CK(cudaMemcpyAsync(hb, c->scal + 256, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (w != x) CK(cudaMemcpyAsync(w, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    const double rt = std::sqrt(hb[0]);
+    if (st) {
+        st->iterations = its;
+        st->converged = converged ? 1 : 0;
+        st->bnorm = bnorm;
+        st->rel_residual = bnorm > 0 ? rt / bnorm : 0.0;
+        st->rel_residual_est = bnorm > 0 ? est / bnorm : 0.0;
+        const size_t nh = std::min<size_t>(hist.size(), 101);
+        for (size_t i = 0; i < nh; ++i) st->history[i] = hist[i];
+    }
+    return converged ? SIB_OK : SIB_ERR_NOT_CONVERGED;
+}
+
 // b = g (+ S K X^n), projected
 void build_rhs(sib_ctx* c, const double* g, bool addSKX, cudaStream_t s) {
     const int64_t n = n3f(c);
@@ -995,7 +1151,18 @@ int solve_impl(sib_ctx* c, const double* g, double* w, sib_stats* st, cudaStream
     if (fl) throw SibError(SIB_ERR_NONFINITE, "right-hand side contains a non-finite value");
     CK(cudaEventRecord(c->ev0, s));
     build_rhs(c, g, addSKX, s);
-    const int rc = fgmres(c, c->rhs, w, st, s);
+    int rc;
+    if (c->opts.use_graphs && !c->fgUnavailable && c->mcap <= FG_MAXM) {
+        try {
+            rc = fgmres_device(c, c->rhs, w, st, s);
+        } catch (const SibError& e) {
+            if (c->fgExec[0] || c->fgExec[1] || e.code != SIB_ERR_CUDA) throw;
+            c->fgUnavailable = true;   // conditional graphs not supported here: host loop
+            rc = fgmres(c, c->rhs, w, st, s);
+        }
+    } else {
+        rc = fgmres(c, c->rhs, w, st, s);
+    }
     CK(cudaEventRecord(c->ev1, s));
     CK(cudaEventSynchronize(c->ev1));
     kcheck(c);
@@ -1187,6 +1354,8 @@ int sib_create(sib_ctx** out, int N, int n_min) {
         c->flag = (int*)dalloc(c, sizeof(int));
         const size_t n3 = 3 * (size_t)N * N;
         c->rhs = (double*)dalloc(c, sizeof(double) * n3);
+        c->zcur = (double*)dalloc(c, sizeof(double) * n3);
+        c->fg = (FgDev*)dalloc(c, sizeof(FgDev));
         c->sol = (double*)dalloc(c, sizeof(double) * n3);
         c->res = (double*)dalloc(c, sizeof(double) * n3);
         c->part = (double*)dalloc(c, sizeof(double) * NBLK * 128);
