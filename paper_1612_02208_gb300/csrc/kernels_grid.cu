@@ -637,10 +637,11 @@ __global__ void __launch_bounds__(256) k_sc_start(GridK<T> g, Cheb2<T> ka, const
     const int N = g.N, n = N * N;
     const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
     const int c = j * N + i;
-    const T ru = res_u(g, x, b, i, j), rv = res_v(g, x, b, i, j);
+    // x == nullptr: zero initial guess, the residual is b
+    const T ru = x ? res_u(g, x, b, i, j) : b[c], rv = x ? res_v(g, x, b, i, j) : b[n + c];
     r[c] = ru;
     r[n + c] = rv;
-    r[2 * n + c] = res_p(g, x, b, i, j);
+    r[2 * n + c] = x ? res_p(g, x, b, i, j) : b[2 * n + c];
     d[c] = ka.inv_theta * ru * g.dinv[c];
     d[n + c] = ka.inv_theta * rv * g.dinv[n + c];
 }
@@ -720,9 +721,9 @@ __global__ void __launch_bounds__(256) k_sc_finish(GridK<T> g, Cheb2<T> ka, cons
     for (int comp = 0; comp < 2; ++comp) {
         const int f = comp * n + c;
         const T yy = ka.one_c1 * dA[f] + ka.c2 * (gq[f] - Aib(g, dA, comp, i, j)) * g.dinv[f];
-        xo[f] = x[f] + g.omega * (y[f] - yy);
+        xo[f] = (x ? x[f] : T(0)) + g.omega * (y[f] - yy);
     }
-    xo[2 * n + c] = x[2 * n + c] + g.omega * dp[c];
+    xo[2 * n + c] = (x ? x[2 * n + c] : T(0)) + g.omega * dp[c];   // x == nullptr: zero initial guess
 }
 
 // power iterations: w = DA^{-1} A_IB v; gq = G v, dA = DA^{-1} gq / theta_A; w = DM^{-1} D ya

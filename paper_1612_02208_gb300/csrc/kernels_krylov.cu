@@ -134,49 +134,51 @@ void launch_subtract_means(double* x, int N, const double* partials, int nblk, i
 // ------------------------------------------------------------------------------------------
 // Coarsest level: dense L^0 + Z Z^T (Z = orthonormal kernel basis: the constant pressure, and
 // the constant velocity components when rho = 0), augmented with the identity: Aug = [L0+ZZ^T | I].
+// One thread per entry: momentum rows hold A = a0 I - mu Lap (5-point, periodic), + G and - dt [SKJ]^0;
+// pressure rows hold - D.  Coincident periodic neighbours add up (counted per offset).
 __global__ void k_assemble_L0(int N, double rho, double mu, double dt, const double* __restrict__ B,
                               double* __restrict__ Aug) {
     pdl_entry();
     const int n0 = N * N, n = 3 * n0, mk = N - 1;
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    double* row = Aug + (int64_t)r * 2 * n;
-    for (int c = 0; c < 2 * n; ++c) row[c] = 0.0;
-    row[n + r] = 1.0;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n * 2 * n) return;
+    const int r = (int)(q / (2 * n)), col = (int)(q % (2 * n));
+    if (col >= n) {
+        Aug[q] = (col - n == r) ? 1.0 : 0.0;
+        return;
+    }
     const double h = 1.0 / N, ih = (double)N;
     const double a0 = rho / dt + 4.0 * mu / (h * h), cc = mu / (h * h);
-    const int blk = r / n0, f = r % n0, i = f % N, j = f / N;
-    if (blk < 2) {
-        const int off = blk * n0;
-        row[off + f] += a0;
-        row[off + j * N + ((i + 1) & mk)] -= cc;
-        row[off + j * N + ((i - 1) & mk)] -= cc;
-        row[off + ((j + 1) & mk) * N + i] -= cc;
-        row[off + ((j - 1) & mk) * N + i] -= cc;
-        // G p: (p_ij - p_{i-1,j})/h on u faces, (p_ij - p_{i,j-1})/h on v faces
-        row[2 * n0 + f] += ih;
-        if (blk == 0)
-            row[2 * n0 + j * N + ((i - 1) & mk)] -= ih;
-        else
-            row[2 * n0 + ((j - 1) & mk) * N + i] -= ih;
-        // - dt [SKJ]^0
-        const double* Bc = B + (int64_t)blk * n0 * n0 + (int64_t)f * n0;
-        for (int g = 0; g < n0; ++g) row[off + g] -= dt * Bc[g];
-    } else {
-        // - D u
-        row[f] += ih;
-        row[j * N + ((i + 1) & mk)] -= ih;
-        row[n0 + f] += ih;
-        row[n0 + ((j + 1) & mk) * N + i] -= ih;
+    const int br = r / n0, f = r % n0, i = f % N, j = f / N;
+    const int bc = col / n0, gcell = col % n0;
+    double v = 0.0;
+    if (br < 2) {
+        if (bc == br) {
+            if (gcell == f) v += a0;
+            if (gcell == j * N + ((i + 1) & mk)) v -= cc;
+            if (gcell == j * N + ((i - 1) & mk)) v -= cc;
+            if (gcell == ((j + 1) & mk) * N + i) v -= cc;
+            if (gcell == ((j - 1) & mk) * N + i) v -= cc;
+            v -= dt * B[(int64_t)br * n0 * n0 + (int64_t)f * n0 + gcell];
+        } else if (bc == 2) {   // G p: (p_ij - p_{i-1,j})/h on u faces, (p_ij - p_{i,j-1})/h on v faces
+            if (gcell == f) v += ih;
+            if (gcell == (br == 0 ? j * N + ((i - 1) & mk) : ((j - 1) & mk) * N + i)) v -= ih;
+        }
+    } else if (bc < 2) {        // - D u
+        if (bc == 0) {
+            if (gcell == f) v += ih;
+            if (gcell == j * N + ((i + 1) & mk)) v -= ih;
+        } else {
+            if (gcell == f) v += ih;
+            if (gcell == ((j + 1) & mk) * N + i) v -= ih;
+        }
     }
-    if (rho == 0.0 || blk == 2) {
-        const double z = 1.0 / (double)n0;
-        for (int g = 0; g < n0; ++g) row[blk * n0 + g] += z;
-    }
+    if (bc == br && (rho == 0.0 || br == 2)) v += 1.0 / (double)n0;
+    Aug[q] = v;
 }
 void launch_assemble_L0(int N0, double rho, double mu, double dt, const double* B, double* Aug, cudaStream_t s) {
-    const int n = 3 * N0 * N0;
-    launch_pdl(k_assemble_L0, (n + 127) / 128, 128, 0, s, N0, rho, mu, dt, B, Aug);
+    const int64_t tot = (int64_t)3 * N0 * N0 * 6 * N0 * N0;
+    launch_pdl(k_assemble_L0, (int)((tot + 255) / 256), 256, 0, s, N0, rho, mu, dt, B, Aug);
 }
 
 // In-place Gauss-Jordan elimination with partial pivoting on Aug (n x 2n, row-major) by one
@@ -461,18 +463,31 @@ void launch_fg_init(FgDev* st, double beta, int m, int max_it, double tol, cudaS
     launch_pdl(k_fg_init, 1, 1, 0, s, st, beta, m, max_it, tol);
 }
 
+// Start of Arnoldi step j = st->jn: for j > 0 the new basis vector V_j = w / h_{j,j-1} (w, the
+// orthogonalised product of the previous step, and 1/h from its norm) is stored; V_j, cast to
+// the V-cycle precision, becomes the finest level's right-hand side.
 template <typename T>
-__global__ void k_fg_prep(const double* __restrict__ V, int64_t n, FgDev* st, T* __restrict__ dst) {
+__global__ void k_fg_prep(double* __restrict__ V, const double* __restrict__ w, int64_t n, FgDev* st,
+                          T* __restrict__ dst) {
     pdl_entry();
     const int j = st->jn;
-    const double* v = V + (int64_t)j * n;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        dst[e] = (T)v[e];
+    double* v = V + (int64_t)j * n;
+    const double inv = st->inv_hn;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        double x;
+        if (j == 0) {
+            x = v[e];
+        } else {
+            x = w[e] * inv;
+            v[e] = x;
+        }
+        dst[e] = (T)x;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) st->j = j;
 }
 template <typename T>
-void launch_fg_prep(const double* V, int64_t n, FgDev* st, T* dst, cudaStream_t s) {
-    launch_pdl(k_fg_prep<T>, num_blocks_for(n), 256, 0, s, V, n, st, dst);
+void launch_fg_prep(double* V, const double* w, int64_t n, FgDev* st, T* dst, cudaStream_t s) {
+    launch_pdl(k_fg_prep<T>, num_blocks_for(n), 256, 0, s, V, w, n, st, dst);
 }
 
 template <typename T>
@@ -490,65 +505,68 @@ template <typename T>
 void launch_fg_zstore(const T* src, double* Z, int64_t n, const FgDev* st, double* zcur, cudaStream_t s) {
     launch_pdl(k_fg_zstore<T>, num_blocks_for(n), 256, 0, s, src, Z, n, st, zcur);
 }
-template void launch_fg_prep<float>(const double*, int64_t, FgDev*, float*, cudaStream_t);
-template void launch_fg_prep<double>(const double*, int64_t, FgDev*, double*, cudaStream_t);
+template void launch_fg_prep<float>(double*, const double*, int64_t, FgDev*, float*, cudaStream_t);
+template void launch_fg_prep<double>(double*, const double*, int64_t, FgDev*, double*, cudaStream_t);
 template void launch_fg_zstore<float>(const float*, double*, int64_t, const FgDev*, double*, cudaStream_t);
 template void launch_fg_zstore<double>(const double*, double*, int64_t, const FgDev*, double*, cudaStream_t);
 
-// partials[i * nblk + b] = slice b of V_i . w for all i <= j.  Block (b, c) takes vectors
-// 8c .. 8c+7 (blocks past j return at once) and slice b of the elements, accumulates the eight
-// products in registers, and reduces them through warp shuffles and one shared-memory pass.
-constexpr int MD_CHUNK = 8;
+// partials[i * S + s] = slice s of V_i . w for all i <= j, one warp per (vector, slice).  The
+// launch has a fixed number of warps (MD_WARPS); the slice count S = md_slices(j) spreads them
+// over the j + 1 vectors, so a short basis gets many short slices (latency) and a long one few
+// long slices (the FP64 pipe is the limit there).  Lanes keep four independent sums.
+constexpr int MD_BLOCKS = 202;
+constexpr int MD_WARPS = MD_BLOCKS * 8;
+__device__ __forceinline__ int md_slices(int j) {
+    const int s = MD_WARPS / (j + 1);
+    return s < 16 ? 16 : (s > 512 ? 512 : s);
+}
 __global__ void __launch_bounds__(256) k_multidot_dev(const double* __restrict__ V, int64_t ld,
                                                       const double* __restrict__ w, int64_t n,
                                                       double* __restrict__ partials, const FgDev* st) {
     pdl_entry();
-    __shared__ double ws[8][MD_CHUNK];
     const int j = st->j;
-    const int i0 = blockIdx.y * MD_CHUNK;
-    if (i0 > j) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    double acc[MD_CHUNK];
-#pragma unroll
-    for (int q = 0; q < MD_CHUNK; ++q) acc[q] = 0.0;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += stride) {
-        const double we = w[e];
-#pragma unroll
-        for (int q = 0; q < MD_CHUNK; ++q)
-            if (i0 + q <= j) acc[q] += V[(int64_t)(i0 + q) * ld + e] * we;
-    }
-#pragma unroll
-    for (int q = 0; q < MD_CHUNK; ++q) {
-        double v = acc[q];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) ws[warp][q] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < MD_CHUNK && i0 + (int)threadIdx.x <= j) {
-        double v = 0.0;
-        for (int q = 0; q < 8; ++q) v += ws[q][threadIdx.x];
-        partials[(int64_t)(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = v;
+    const int S = md_slices(j);
+    const int lane = threadIdx.x & 31;
+    const int lanes_total = MD_WARPS * 32;
+    for (int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < (j + 1) * S; gw += lanes_total >> 5) {
+        const int i = gw / S, sl = gw - i * S;
+        const int64_t len = (n + S - 1) / S;
+        const int64_t e0 = sl * len, e1 = e0 + len < n ? e0 + len : n;
+        const double* v = V + (int64_t)i * ld;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int64_t e = e0 + lane;
+        for (; e + 96 < e1; e += 128) {
+            a0 += v[e] * w[e];
+            a1 += v[e + 32] * w[e + 32];
+            a2 += v[e + 64] * w[e + 64];
+            a3 += v[e + 96] * w[e + 96];
+        }
+        for (; e < e1; e += 32) a0 += v[e] * w[e];
+        double t = (a0 + a1) + (a2 + a3);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) partials[(int64_t)i * S + sl] = t;
     }
 }
-void launch_multidot_dev(const double* V, int64_t ld, const double* w, int64_t n, double* partials, int nblk,
+void launch_multidot_dev(const double* V, int64_t ld, const double* w, int64_t n, double* partials,
                          const FgDev* st, cudaStream_t s) {
-    (void)nblk;
-    launch_pdl(k_multidot_dev, dim3(MD_SLICES, (FG_MAXM + 1 + MD_CHUNK - 1) / MD_CHUNK), 256, 0, s, V, ld, w, n,
-               partials, st);
+    launch_pdl(k_multidot_dev, MD_BLOCKS, 256, 0, s, V, ld, w, n, partials, st);
 }
+// out[i] = sum of the partials of vector i in slice order: for i <= j with S = md_slices(j)
+// partials each (nblk = 0), or for i < count with nblk partials each
 __global__ void k_reduce_partials_dev(const double* __restrict__ partials, int nblk, double* __restrict__ out,
-                                      const FgDev* st) {
+                                      const FgDev* st, int count) {
     pdl_entry();
-    if ((int)blockIdx.x > st->j) return;
+    const int k = count > 0 ? count : st->j + 1;
+    const int S = nblk > 0 ? nblk : md_slices(st->j);
+    if ((int)blockIdx.x >= k) return;
     double s = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partials[(int64_t)blockIdx.x * nblk + b];
+    for (int b = threadIdx.x; b < S; b += blockDim.x) s += partials[(int64_t)blockIdx.x * S + b];
     s = block_sum(s);
     if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
-void launch_reduce_partials_dev(const double* partials, int nblk, double* out, const FgDev* st, cudaStream_t s) {
-    (void)nblk;
-    launch_pdl(k_reduce_partials_dev, FG_MAXM + 1, 128, 0, s, partials, MD_SLICES, out, st);
+void launch_reduce_partials_dev(const double* partials, int nblk, double* out, const FgDev* st, int count,
+                                cudaStream_t s) {
+    launch_pdl(k_reduce_partials_dev, count > 0 ? count : FG_MAXM + 1, 128, 0, s, partials, nblk, out, st, count);
 }
 // y += sign * sum_{i<k} coef[i] V_i with k = j + 1 (useK = 0) or k = st->k (useK = 1)
 __global__ void k_multi_axpy_dev(const double* __restrict__ V, int64_t ld, const double* __restrict__ coef,
@@ -567,6 +585,32 @@ __global__ void k_multi_axpy_dev(const double* __restrict__ V, int64_t ld, const
 void launch_multi_axpy_dev(const double* V, int64_t ld, const double* coef, double sign, double* y, int64_t n,
                            const FgDev* st, int useK, cudaStream_t s) {
     launch_pdl(k_multi_axpy_dev, num_blocks_for(n), 256, 0, s, V, ld, coef, sign, y, n, st, useK);
+}
+
+// The same update with k = j + 1, and the block partial sums of ||y||^2 of the result.
+__global__ void k_multi_axpy_norm_dev(const double* __restrict__ V, int64_t ld, const double* __restrict__ coef,
+                                      double sign, double* __restrict__ y, int64_t n, const FgDev* st,
+                                      double* __restrict__ partials) {
+    pdl_entry();
+    __shared__ double c[FG_MAXM + 1];
+    const int k = st->j + 1;
+    for (int t = threadIdx.x; t < k; t += blockDim.x) c[t] = sign * coef[t];
+    __syncthreads();
+    double ss = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = y[e];
+        for (int i = 0; i < k; ++i) acc += c[i] * V[(int64_t)i * ld + e];
+        y[e] = acc;
+        ss += acc * acc;
+    }
+    ss = block_sum(ss);
+    if (threadIdx.x == 0) partials[blockIdx.x] = ss;
+}
+int launch_multi_axpy_norm_dev(const double* V, int64_t ld, const double* coef, double sign, double* y, int64_t n,
+                               const FgDev* st, double* partials, cudaStream_t s) {
+    const int nb = num_blocks_for(n);
+    launch_pdl(k_multi_axpy_norm_dev, nb, 256, 0, s, V, ld, coef, sign, y, n, st, partials);
+    return nb;
 }
 
 // One thread: Hessenberg column j from the two Gram-Schmidt passes, previous and new Givens
@@ -610,17 +654,6 @@ __global__ void k_fg_arnoldi(FgDev* st, const double* __restrict__ h1, const dou
 void launch_fg_arnoldi(FgDev* st, const double* h1, const double* h2, const double* nrm,
                        cudaGraphConditionalHandle handle, cudaStream_t s) {
     launch_pdl(k_fg_arnoldi, 1, 32, 0, s, st, h1, h2, nrm, handle);
-}
-
-__global__ void k_fg_store_v(const double* __restrict__ w, double* __restrict__ V, int64_t n, const FgDev* st) {
-    pdl_entry();
-    const double inv = st->inv_hn;
-    double* v = V + (int64_t)(st->j + 1) * n;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        v[e] = w[e] * inv;
-}
-void launch_fg_store_v(const double* w, double* V, int64_t n, const FgDev* st, cudaStream_t s) {
-    launch_pdl(k_fg_store_v, num_blocks_for(n), 256, 0, s, w, V, n, st);
 }
 
 // y = H^{-1} g on the k x k upper triangle (one thread)

@@ -186,7 +186,6 @@ void launch_grad_X(const double* X, int M, int N, const double* w, const double*
 
 // Device-side state of one flexible-GMRES cycle (the loop runs as a conditional graph node).
 constexpr int FG_MAXM = 100;                 // restart length cap
-constexpr int MD_SLICES = 128;               // element slices of the device multi-dot
 struct FgDev {
     int j, jn, its, k, converged, m, max_it, pad;
     double tol, est, inv_hn, beta;
@@ -212,17 +211,20 @@ template <typename T> void launch_coarse_apply(const double* Pinv, int n, const 
 void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t s);
 
 void launch_fg_init(FgDev* st, double beta, int m, int max_it, double tol, cudaStream_t s);
-template <typename T> void launch_fg_prep(const double* V, int64_t n, FgDev* st, T* dst, cudaStream_t s);
+template <typename T> void launch_fg_prep(double* V, const double* w, int64_t n, FgDev* st, T* dst, cudaStream_t s);
 template <typename T> void launch_fg_zstore(const T* src, double* Z, int64_t n, const FgDev* st, double* zcur,
                                             cudaStream_t s);
-void launch_multidot_dev(const double* V, int64_t ld, const double* w, int64_t n, double* partials, int nblk,
+void launch_multidot_dev(const double* V, int64_t ld, const double* w, int64_t n, double* partials,
                          const FgDev* st, cudaStream_t s);
-void launch_reduce_partials_dev(const double* partials, int nblk, double* out, const FgDev* st, cudaStream_t s);
+void launch_reduce_partials_dev(const double* partials, int nblk, double* out, const FgDev* st, int count,
+                                cudaStream_t s);
 void launch_multi_axpy_dev(const double* V, int64_t ld, const double* coef, double sign, double* y, int64_t n,
                            const FgDev* st, int useK, cudaStream_t s);
+// returns the number of partial sums written
+int launch_multi_axpy_norm_dev(const double* V, int64_t ld, const double* coef, double sign, double* y, int64_t n,
+                               const FgDev* st, double* partials, cudaStream_t s);
 void launch_fg_arnoldi(FgDev* st, const double* h1, const double* h2, const double* nrm,
                        cudaGraphConditionalHandle handle, cudaStream_t s);
-void launch_fg_store_v(const double* w, double* V, int64_t n, const FgDev* st, cudaStream_t s);
 void launch_fg_backsolve(FgDev* st, cudaStream_t s);
 
 int num_blocks_for(int64_t n);

@@ -379,7 +379,7 @@ void sc_sweep_fused(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream
     T* sv = (T*)lv.p[pi].tp[0];
     T* dp = (T*)lv.p[pi].tp[1];
     T* dM = (T*)lv.p[pi].tp[2];
-    ib_apply<T>(c, l, x, s);
+    if (x) ib_apply<T>(c, l, x, s);   // x == nullptr: zero initial guess, r = b
     KL(c, launch_sc_start<T>(g, ka, x, b, r, d, s));
     ib_apply<T>(c, l, d, s);
     KL(c, launch_sc_chebA<T>(g, ka, r, d, y, s));
@@ -448,6 +448,10 @@ T* vcycle_level(sib_ctx* c, int l, cudaStream_t s) {
     int k0 = 0;
     if (c->opts.smoother == SIB_SMOOTHER_VANKA && c->opts.nu1 > 0) {
         KL(c, launch_vanka_zero<T>(gridk<T>(c, l), b, xt, s));   // first sweep from w = 0
+        std::swap(x, xt);
+        k0 = 1;
+    } else if (c->opts.smoother == SIB_SMOOTHER_SC && c->opts.cheb_iters == 2 && c->opts.nu1 > 0) {
+        sc_sweep_fused<T>(c, l, nullptr, b, xt, s);   // first sweep from w = 0: residual = b
         std::swap(x, xt);
         k0 = 1;
     } else {
@@ -1000,19 +1004,22 @@ void build_fg_graph(sib_ctx* c) {
         CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         try {
             Level& lv = c->L[c->lmax];
-            KL(c, launch_fg_prep<T>(c->V, n, c->fg, (T*)lv.p[pi].b, s));
+            // V_j (stored from the previous step's w), the V-cycle, z_j, w = L z_j, two classical
+            // Gram-Schmidt passes (the second also gives ||w||^2), the Hessenberg column and the
+            // loop decision
+            KL(c, launch_fg_prep<T>(c->V, c->res, n, c->fg, (T*)lv.p[pi].b, s));
             T* out = vcycle_level<T>(c, c->lmax, s);
             KL(c, launch_fg_zstore<T>(out, c->Z, n, c->fg, c->zcur, s));
             matvec(c, c->zcur, c->res, s);
-            KL(c, launch_multidot_dev(c->V, n, c->res, n, c->part, NBLK, c->fg, s));
-            KL(c, launch_reduce_partials_dev(c->part, NBLK, c->scal, c->fg, s));
+            KL(c, launch_multidot_dev(c->V, n, c->res, n, c->part, c->fg, s));
+            KL(c, launch_reduce_partials_dev(c->part, 0, c->scal, c->fg, 0, s));
             KL(c, launch_multi_axpy_dev(c->V, n, c->scal, -1.0, c->res, n, c->fg, 0, s));
-            KL(c, launch_multidot_dev(c->V, n, c->res, n, c->part, NBLK, c->fg, s));
-            KL(c, launch_reduce_partials_dev(c->part, NBLK, c->scal + 128, c->fg, s));
-            KL(c, launch_multi_axpy_dev(c->V, n, c->scal + 128, -1.0, c->res, n, c->fg, 0, s));
-            dot_into(c, c->res, c->res, n, c->scal + 256, s);
+            KL(c, launch_multidot_dev(c->V, n, c->res, n, c->part, c->fg, s));
+            KL(c, launch_reduce_partials_dev(c->part, 0, c->scal + 128, c->fg, 0, s));
+            int nb = 0;
+            KL(c, nb = launch_multi_axpy_norm_dev(c->V, n, c->scal + 128, -1.0, c->res, n, c->fg, c->part, s));
+            KL(c, launch_reduce_partials_dev(c->part, nb, c->scal + 256, c->fg, 1, s));
             KL(c, launch_fg_arnoldi(c->fg, c->scal, c->scal + 128, c->scal + 256, h, s));
-            KL(c, launch_fg_store_v(c->res, c->V, n, c->fg, s));
         } catch (...) {
             cudaGraph_t tmp;
             cudaStreamEndCapture(s, &tmp);
