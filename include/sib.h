@@ -75,6 +75,8 @@ typedef struct {
     int    restart;       /* FGMRES restart length (100)                                             */
     int    add_SKXn;      /* 1: right-hand side g + S K X^n (paper form), 0: g only (1)              */
     int    use_graphs;    /* 1: replay the V-cycle as a CUDA graph (1)                               */
+    int    fuse_small;    /* 1: levels 1 and 0 of the V-cycle run as one single-block kernel when
+                             level 1 (at most 16 x 16) fits in shared memory; 0: one kernel per step (1) */
 } sib_opts;
 
 typedef struct {

@@ -4,29 +4,9 @@
 // Layout: a level vector is [u | v | p], each N*N row-major [j][i]; u[j][i] on the x-face
 // (i-1/2, j), v[j][i] on the y-face (i, j-1/2), p[j][i] at the cell centre (Appendix,
 // "Eulerian discretization").  N is a power of two, so periodic wrap is a mask.
-#include "sib_internal.h"
+#include "grid_cells.cuh"
 
 namespace sib {
-
-// IB force ([S K J]^l fld) at face (i, j) of component comp, precomputed into g.fib by the IB
-// pass for the same field; zero outside IB-active tiles.
-template <typename T>
-__device__ __forceinline__ T ibf(const GridK<T>& g, const T* __restrict__ fld, int comp, int i, int j) {
-    (void)fld;
-    if (g.tile == nullptr) return T(0);
-    const int tile = (j >> g.lgty) * g.ntx + (i >> g.lgtx);
-    if (!g.tile[tile]) return T(0);
-    return g.fib[(size_t)comp * g.N * g.N + j * g.N + i];
-}
-
-// diagonal of A_IB on a face: a0 - dt B(f,f) (B(f,f) is zero outside IB-active tiles)
-template <typename T>
-__device__ __forceinline__ T diag_face(const GridK<T>& g, int comp, int i, int j) {
-    if (g.tile == nullptr) return g.a0;
-    const int tile = (j >> g.lgty) * g.ntx + (i >> g.lgtx);
-    if (!g.tile[tile]) return g.a0;
-    return g.a0 - g.dt * g.ibd[(size_t)2 * comp * g.N * g.N + j * g.N + i];
-}
 
 // ------------------------------------------------------------------------------------------
 // Residual r = b - L x, or y = L x when b == nullptr, with
@@ -318,45 +298,7 @@ void launch_vanka_zero(const GridK<T>& g, const T* b, T* xo, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Fine residual and its restriction in one pass (Sec. 3.2, Alg. 1): one thread per coarse cell
-// evaluates the sixteen fine residuals that R = diag(P_u^T / 4, P_v^T / 4, average) combines.
-template <typename T>
-__device__ __forceinline__ T res_u(const GridK<T>& g, const T* __restrict__ x, const T* __restrict__ b, int i, int j) {
-    const int N = g.N, m = N - 1;
-    const T* u = x;
-    const T* p = x + 2 * N * N;
-    i &= m;
-    j &= m;
-    const int c = j * N + i;
-    T Au = g.a0 * u[c] - g.c * ((u[j * N + ((i + 1) & m)] + u[j * N + ((i - 1) & m)]) +
-                                (u[((j + 1) & m) * N + i] + u[((j - 1) & m) * N + i])) +
-           (p[c] - p[j * N + ((i - 1) & m)]) * g.inv_h;
-    Au -= g.dt * ibf(g, x, 0, i, j);
-    return b[c] - Au;
-}
-template <typename T>
-__device__ __forceinline__ T res_v(const GridK<T>& g, const T* __restrict__ x, const T* __restrict__ b, int i, int j) {
-    const int N = g.N, n = N * N, m = N - 1;
-    const T* v = x + n;
-    const T* p = x + 2 * n;
-    i &= m;
-    j &= m;
-    const int c = j * N + i;
-    T Av = g.a0 * v[c] - g.c * ((v[j * N + ((i + 1) & m)] + v[j * N + ((i - 1) & m)]) +
-                                (v[((j + 1) & m) * N + i] + v[((j - 1) & m) * N + i])) +
-           (p[c] - p[((j - 1) & m) * N + i]) * g.inv_h;
-    Av -= g.dt * ibf(g, x, 1, i, j);
-    return b[n + c] - Av;
-}
-template <typename T>
-__device__ __forceinline__ T res_p(const GridK<T>& g, const T* __restrict__ x, const T* __restrict__ b, int i, int j) {
-    const int N = g.N, n = N * N, m = N - 1;
-    i &= m;
-    j &= m;
-    const int c = j * N + i;
-    return b[2 * n + c] + ((x[j * N + ((i + 1) & m)] - x[c]) + (x[n + ((j + 1) & m) * N + i] - x[n + c])) * g.inv_h;
-}
-
+// Fine residual and its restriction in one pass (Sec. 3.2, Alg. 1): one thread per coarse cell.
 template <typename T>
 __global__ void k_residual_restrict(GridK<T> g, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ bc) {
     pdl_entry();
@@ -364,18 +306,7 @@ __global__ void k_residual_restrict(GridK<T> g, const T* __restrict__ x, const T
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
     if (I >= Nc || J >= Nc) return;
-    const int i = 2 * I, j = 2 * J;
-    const T su = (res_u(g, x, b, i, j) + res_u(g, x, b, i, j + 1)) +
-                 T(0.5) * ((res_u(g, x, b, i + 1, j) + res_u(g, x, b, i + 1, j + 1)) +
-                           (res_u(g, x, b, i - 1, j) + res_u(g, x, b, i - 1, j + 1)));
-    const T sv = (res_v(g, x, b, i, j) + res_v(g, x, b, i + 1, j)) +
-                 T(0.5) * ((res_v(g, x, b, i, j + 1) + res_v(g, x, b, i + 1, j + 1)) +
-                           (res_v(g, x, b, i, j - 1) + res_v(g, x, b, i + 1, j - 1)));
-    const T sp = (res_p(g, x, b, i, j) + res_p(g, x, b, i + 1, j)) + (res_p(g, x, b, i, j + 1) + res_p(g, x, b, i + 1, j + 1));
-    const int nc = Nc * Nc, c = J * Nc + I;
-    bc[c] = T(0.25) * su;
-    bc[nc + c] = T(0.25) * sv;
-    bc[2 * nc + c] = T(0.25) * sp;
+    residual_restrict_cell(g, x, b, bc, I, J);
 }
 template <typename T>
 void launch_residual_restrict(const GridK<T>& g, const T* x, const T* b, T* bc, cudaStream_t s) {
@@ -425,24 +356,10 @@ void launch_restrict(int Nc, const T* rf, T* bc, cudaStream_t s) {
 template <typename T>
 __global__ void k_prolong_add(int Nc, const T* __restrict__ ec, T* __restrict__ xf) {
     pdl_entry();
-    const int Nf = 2 * Nc;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= Nf || j >= Nf) return;
-    const int nf = Nf * Nf, nc = Nc * Nc, mc = Nc - 1;
-    const T* eu = ec;
-    const T* ev = ec + nc;
-    const T* ep = ec + 2 * nc;
-    const int I = i >> 1, J = j >> 1;
-    const T pu = (i & 1) ? T(0.5) * (eu[J * Nc + I] + eu[J * Nc + ((I + 1) & mc)]) : eu[J * Nc + I];
-    const T pv = (j & 1) ? T(0.5) * (ev[J * Nc + I] + ev[((J + 1) & mc) * Nc + I]) : ev[J * Nc + I];
-    const int I2 = (I + ((i & 1) ? 1 : -1)) & mc, J2 = (J + ((j & 1) ? 1 : -1)) & mc;
-    const T pp = T(9.0 / 16.0) * ep[J * Nc + I] + T(3.0 / 16.0) * (ep[J * Nc + I2] + ep[J2 * Nc + I]) +
-                 T(1.0 / 16.0) * ep[J2 * Nc + I2];
-    const int c = j * Nf + i;
-    xf[c] += pu;
-    xf[nf + c] += pv;
-    xf[2 * nf + c] += pp;
+    if (i >= 2 * Nc || j >= 2 * Nc) return;
+    prolong_add_cell(Nc, ec, xf, i, j);
 }
 
 template <typename T>
@@ -486,12 +403,6 @@ void launch_axpby(T a, const T* x, T b, const T* y, T* z, int64_t n, cudaStream_
 
 // ------------------------------------------------------------------------------------------
 // Schur-complement smoother pieces (Eq. approx-fact-Stokes-IB).
-// diag(A_IB) on a face: a0 - dt B(f,f) (B(f,f) read only in IB-active tiles).
-template <typename T>
-__device__ __forceinline__ T diagA(const GridK<T>& g, bool act, int comp, int c, int n) {
-    return act ? g.a0 - g.dt * g.ibd[2 * comp * n + c] : g.a0;
-}
-
 // z = scale * diag(A_IB)^{-1} r on both velocity components
 template <typename T>
 __global__ void k_jacobi_A(GridK<T> g, const T* __restrict__ r, T* __restrict__ z, T scale) {
@@ -605,59 +516,17 @@ void launch_cheb_update(const T* dinvr, T* d, T* x, T ra, T rb, int64_t n, cudaS
 // diag(A_IB) and DM = diag(D DA^{-1} G).  A kernel that needs G of a cell-centred quantity
 // recomputes that quantity on the two neighbouring cells instead of synchronising.
 template <typename T>
-__device__ __forceinline__ T Aib(const GridK<T>& g, const T* __restrict__ d, int comp, int i, int j) {
-    const int N = g.N, m = N - 1;
-    const T* dc = d + (size_t)comp * N * N;
-    const T a = g.a0 * dc[j * N + i] - g.c * ((dc[j * N + ((i + 1) & m)] + dc[j * N + ((i - 1) & m)]) +
-                                             (dc[((j + 1) & m) * N + i] + dc[((j - 1) & m) * N + i]));
-    return a - g.dt * ibf(g, d, comp, i, j);
-}
-template <typename T>
-__device__ __forceinline__ T divg(const GridK<T>& g, const T* __restrict__ w, int i, int j) {
-    const int N = g.N, m = N - 1;
-    i &= m;
-    j &= m;
-    return ((w[j * N + ((i + 1) & m)] - w[j * N + i]) + (w[N * N + ((j + 1) & m) * N + i] - w[N * N + j * N + i])) *
-           g.inv_h;
-}
-template <typename T>
-__device__ __forceinline__ T dM_inv(const GridK<T>& g, int i, int j) {
-    const int m = g.N - 1;
-    i &= m;
-    j &= m;
-    const T s = T(1) / diag_face(g, 0, i, j) + T(1) / diag_face(g, 0, (i + 1) & m, j) + T(1) / diag_face(g, 1, i, j) +
-                T(1) / diag_face(g, 1, i, (j + 1) & m);
-    return T(1) / (-s * g.inv_h * g.inv_h);
-}
-
-template <typename T>
 __global__ void __launch_bounds__(256) k_sc_start(GridK<T> g, Cheb2<T> ka, const T* __restrict__ x,
                                                   const T* __restrict__ b, T* __restrict__ r, T* __restrict__ d) {
     pdl_entry();
-    const int N = g.N, n = N * N;
-    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
-    const int c = j * N + i;
-    // x == nullptr: zero initial guess, the residual is b
-    const T ru = x ? res_u(g, x, b, i, j) : b[c], rv = x ? res_v(g, x, b, i, j) : b[n + c];
-    r[c] = ru;
-    r[n + c] = rv;
-    r[2 * n + c] = x ? res_p(g, x, b, i, j) : b[2 * n + c];
-    d[c] = ka.inv_theta * ru * g.dinv[c];
-    d[n + c] = ka.inv_theta * rv * g.dinv[n + c];
+    sc_start_cell(g, ka, x, b, r, d, blockIdx.x * g.tx + threadIdx.x, blockIdx.y * g.ty + threadIdx.y);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_sc_chebA(GridK<T> g, Cheb2<T> ka, const T* __restrict__ q,
                                                   const T* __restrict__ d, T* __restrict__ y) {
     pdl_entry();
-    const int N = g.N, n = N * N;
-    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
-    const int c = j * N + i;
-    for (int comp = 0; comp < 2; ++comp) {
-        const int f = comp * n + c;
-        const T rr = q[f] - Aib(g, d, comp, i, j);
-        y[f] = ka.one_c1 * d[f] + ka.c2 * rr * g.dinv[f];
-    }
+    sc_chebA_cell(g, ka, q, d, y, blockIdx.x * g.tx + threadIdx.x, blockIdx.y * g.ty + threadIdx.y);
 }
 
 template <typename T>
@@ -665,25 +534,7 @@ __global__ void __launch_bounds__(256) k_sc_mstart(GridK<T> g, Cheb2<T> ka, Cheb
                                                    const T* __restrict__ y, T* __restrict__ sv, T* __restrict__ dMo,
                                                    T* __restrict__ gq, T* __restrict__ dA) {
     pdl_entry();
-    const int N = g.N, n = N * N, m = N - 1;
-    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
-    const int c = j * N + i;
-    auto e0 = [&](int ii, int jj, T* sOut) {
-        ii &= m;
-        jj &= m;
-        const T sval = rp[jj * N + ii] + divg(g, y, ii, jj);
-        if (sOut) *sOut = sval;
-        return km.inv_theta * sval * g.dinv[2 * n + jj * N + ii];
-    };
-    T sc;
-    const T ec = e0(i, j, &sc), ew = e0(i - 1, j, nullptr), es = e0(i, j - 1, nullptr);
-    sv[c] = sc;
-    dMo[c] = ec;
-    const T gu = (ec - ew) * g.inv_h, gv = (ec - es) * g.inv_h;
-    gq[c] = gu;
-    gq[n + c] = gv;
-    dA[c] = ka.inv_theta * gu * g.dinv[c];
-    dA[n + c] = ka.inv_theta * gv * g.dinv[n + c];
+    sc_mstart_cell(g, ka, km, rp, y, sv, dMo, gq, dA, blockIdx.x * g.tx + threadIdx.x, blockIdx.y * g.ty + threadIdx.y);
 }
 
 template <typename T>
@@ -691,22 +542,7 @@ __global__ void __launch_bounds__(256) k_sc_mfinish(GridK<T> g, Cheb2<T> ka, Che
                                                     const T* __restrict__ dM, const T* __restrict__ ya,
                                                     T* __restrict__ dp, T* __restrict__ gq, T* __restrict__ dA) {
     pdl_entry();
-    const int N = g.N, n = N * N, m = N - 1;
-    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
-    const int c = j * N + i;
-    auto pval = [&](int ii, int jj) {
-        ii &= m;
-        jj &= m;
-        const int cc = jj * N + ii;
-        return km.one_c1 * dM[cc] + km.c2 * (sv[cc] - divg(g, ya, ii, jj)) * g.dinv[2 * n + cc];
-    };
-    const T pc = pval(i, j), pw = pval(i - 1, j), ps = pval(i, j - 1);
-    dp[c] = pc;
-    const T gu = (pc - pw) * g.inv_h, gv = (pc - ps) * g.inv_h;
-    gq[c] = gu;
-    gq[n + c] = gv;
-    dA[c] = ka.inv_theta * gu * g.dinv[c];
-    dA[n + c] = ka.inv_theta * gv * g.dinv[n + c];
+    sc_mfinish_cell(g, ka, km, sv, dM, ya, dp, gq, dA, blockIdx.x * g.tx + threadIdx.x, blockIdx.y * g.ty + threadIdx.y);
 }
 
 template <typename T>
@@ -715,15 +551,7 @@ __global__ void __launch_bounds__(256) k_sc_finish(GridK<T> g, Cheb2<T> ka, cons
                                                    const T* __restrict__ dA, const T* __restrict__ dp,
                                                    T* __restrict__ xo) {
     pdl_entry();
-    const int N = g.N, n = N * N;
-    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
-    const int c = j * N + i;
-    for (int comp = 0; comp < 2; ++comp) {
-        const int f = comp * n + c;
-        const T yy = ka.one_c1 * dA[f] + ka.c2 * (gq[f] - Aib(g, dA, comp, i, j)) * g.dinv[f];
-        xo[f] = (x ? x[f] : T(0)) + g.omega * (y[f] - yy);
-    }
-    xo[2 * n + c] = (x ? x[2 * n + c] : T(0)) + g.omega * dp[c];   // x == nullptr: zero initial guess
+    sc_finish_cell(g, ka, x, y, gq, dA, dp, xo, blockIdx.x * g.tx + threadIdx.x, blockIdx.y * g.ty + threadIdx.y);
 }
 
 // power iterations: w = DA^{-1} A_IB v; gq = G v, dA = DA^{-1} gq / theta_A; w = DM^{-1} D ya

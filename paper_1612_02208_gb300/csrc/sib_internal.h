@@ -104,6 +104,21 @@ struct IBK {
 };
 
 // ------------------------------------------------------------------------------------------
+// Levels 1 and 0 of the V-cycle in one thread block (kernels_small.cu).
+template <typename T>
+struct SmallArgs {
+    GridK<T> g;                 // level 1; its set-up arrays (ibd, dinv, tile flags) in global memory
+    Cheb2<T> ka, km;            // SC Chebyshev coefficients of level 1
+    const T* b;                 // level-1 right-hand side
+    T* out;                     // level-1 result
+    const T* win;               // IB windows of the active tiles
+    const int* tiles;           // active-tile list
+    int nTiles, ntiles;         // its length (0 without IB); number of tiles of the level
+    int smoother, nu1, nu2, n0;
+    const double* Pinv;         // coarsest pseudo-inverse, n0 x n0
+};
+
+// ------------------------------------------------------------------------------------------
 // launchers (kernels_grid.cu)
 template <typename T> void launch_residual(const GridK<T>& g, const T* x, const T* b, T* r, cudaStream_t s);
 template <typename T> void launch_vanka(const GridK<T>& g, const T* x, const T* b, T* xo, cudaStream_t s);
@@ -137,6 +152,11 @@ template <typename T> void launch_power_A(const GridK<T>& g, const T* v, T* w, c
 template <typename T> void launch_power_Mstart(const GridK<T>& g, Cheb2<T> ka, const T* v, T* gq, T* dA,
                                                cudaStream_t s);
 template <typename T> void launch_power_Mfinish(const GridK<T>& g, const T* ya, T* w, cudaStream_t s);
+
+// launchers (kernels_small.cu)
+template <typename T> size_t vcycle_small_smem(int N1, int n0, int nTiles, int per, int ntiles);
+template <typename T> int vcycle_small_cluster(size_t smem);
+template <typename T> cudaError_t launch_vcycle_small(const SmallArgs<T>& a, size_t smem, cudaStream_t s);
 
 // launchers (kernels_ib.cu)
 void launch_stencils(const double* X, int M, int Nf, int lmax, int** base, double** w64, float** w32,

@@ -75,6 +75,7 @@ struct sib_ctx {
     sib_opts opts{};
     std::string err;
     int64_t launches = 0;
+    int smemOptin = 0;           // largest dynamic shared memory of one block
     int64_t bytes = 0;
     double setup_ms = 0.0;
     std::vector<void*> allocs;
@@ -432,11 +433,59 @@ void sweep(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream_t s) {
     }
 }
 
+// Levels 1 and 0 fit one thread block's shared memory (kernels_small.cu): level 1 of at most
+// 16 x 16 cells, its IB operator (if any) applied through windows, the fused SC sweep.
+template <typename T>
+size_t small_smem(const sib_ctx* c) {
+    const Level& lv = c->L[1];
+    const int nT = c->haveIB ? lv.hnTiles : 0;
+    return vcycle_small_smem<T>(lv.N, c->n0, nT, lv.tx * lv.ty, lv.ntiles);
+}
+template <typename T>
+bool small_ok(const sib_ctx* c) {
+    if (!c->opts.fuse_small || c->lmax < 1) return false;
+    const Level& lv = c->L[1];
+    if (lv.N > 16) return false;
+    if (c->opts.smoother == SIB_SMOOTHER_SC && c->opts.cheb_iters != 2) return false;
+    if (c->haveIB && lv.hnTiles > 0 && !lv.applyWindow) return false;
+    const size_t smem = small_smem<T>(c);
+    if (smem > (size_t)c->smemOptin) return false;
+    // the coarse-solve helpers hold the pseudo-inverse's rows in the same shared-memory size
+    if (sizeof(double) * ((size_t)(c->n0 + 6) / 7 + 1) * c->n0 > smem) return false;
+    return vcycle_small_cluster<T>(smem) > 0;
+}
+template <typename T>
+T* vcycle_small(sib_ctx* c, cudaStream_t s) {
+    Level& lv = c->L[1];
+    const int pi = Prec<T>::id;
+    SmallArgs<T> a{};
+    a.g = gridk<T>(c, 1);
+    if (c->opts.smoother == SIB_SMOOTHER_SC) {
+        a.ka = cheb2<T>(lv.lamA, c->opts.cheb_lo, c->opts.cheb_hi);
+        a.km = cheb2<T>(lv.lamM, c->opts.cheb_lo, c->opts.cheb_hi);
+    }
+    a.b = (const T*)lv.p[pi].b;
+    a.out = (T*)lv.p[pi].x;
+    a.win = (const T*)lv.win[pi];
+    a.tiles = lv.tiles;
+    a.nTiles = c->haveIB ? lv.hnTiles : 0;
+    a.ntiles = lv.ntiles;
+    a.smoother = c->opts.smoother;
+    a.nu1 = c->opts.nu1;
+    a.nu2 = c->opts.nu2;
+    a.n0 = c->n0;
+    a.Pinv = c->Pinv;
+    CK(launch_vcycle_small<T>(a, small_smem<T>(c), s));
+    ++c->launches;
+    return (T*)lv.p[pi].x;
+}
+
 // Alg. 1 on level l with right-hand side in the level's b; returns the buffer holding w.
 template <typename T>
 T* vcycle_level(sib_ctx* c, int l, cudaStream_t s) {
     Level& lv = c->L[l];
     const int pi = Prec<T>::id;
+    if (l == 1 && small_ok<T>(c)) return vcycle_small<T>(c, s);
     if (l == 0) {
         KL(c, launch_coarse_apply<T>(c->Pinv, c->n0, (const T*)lv.p[pi].b, (T*)lv.p[pi].x, s));
         return (T*)lv.p[pi].x;
@@ -1314,6 +1363,7 @@ void sib_default_opts(sib_opts* o) {
     o->restart = 100;
     o->add_SKXn = 1;
     o->use_graphs = 1;
+    o->fuse_small = 1;
 }
 
 static void resolve_opts(sib_opts* o) {
@@ -1346,6 +1396,11 @@ int sib_create(sib_ctx** out, int N, int n_min) {
             lv.nty = lv.N / lv.ty;
             lv.ntiles = lv.ntx * lv.nty;
             lv.W = l == lmax ? 4 : 3;
+        }
+        {
+            int dev = 0;
+            CK(cudaGetDevice(&dev));
+            CK(cudaDeviceGetAttribute(&c->smemOptin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         }
         CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
         CK(cudaEventCreate(&c->ev0));
@@ -1473,7 +1528,7 @@ int sib_set_options(sib_ctx* c, const sib_opts* o) {
     if ((n.smoother != SIB_SMOOTHER_VANKA && n.smoother != SIB_SMOOTHER_SC) || n.nu1 < 0 || n.nu2 < 0 ||
         n.nu1 + n.nu2 > 64 || n.cheb_iters < 1 || n.cheb_iters > 16 || !(n.cheb_lo > 0) || !(n.cheb_hi > n.cheb_lo) ||
         n.power_iters < 1 || n.power_iters > 1000 || !(n.rtol >= 0) || n.max_it < 1 || n.max_it > 100000 ||
-        n.restart < 1 || n.restart > 100)
+        n.restart < 1 || n.restart > 100 || (n.fuse_small != 0 && n.fuse_small != 1))
         throw SibError(SIB_ERR_ARG, "option out of range");
     resolve_opts(&n);
     const bool smootherChanged = n.smoother != c->opts.smoother;

@@ -396,6 +396,40 @@ def test_vanka_sweep_large_grid_against_oracle():
     assert rel(host(z32), ref0) < TOL32
 
 
+@pytest.mark.parametrize("name,smoother", [("ellipse32", "vanka"), ("disk64_stiff", "vanka"), ("loguniform64", "vanka"),
+                                           ("seam32", "sc"), ("ellipse64_re", "sc")])
+@pytest.mark.parametrize("fuse", [0, 1])
+def test_vcycle_small_levels_one_block(name, smoother, fuse):
+    """Levels 1 and 0 run either as one single-block kernel (shared-memory resident) or as one
+    kernel per step: both V-cycles match the oracle's."""
+    prob, H, S = setup_pair(name, smoother, fuse_small=fuse)
+    if smoother == "sc":
+        S.set_eigen_estimates(*S._oracle_lams)
+        S.setup()
+    b = system.rhs(prob)
+    assert rel(host(S.vcycle(cu(b))), H.vcycle(b)) < TOL64
+    b32 = b.astype(np.float32).astype(np.float64)
+    assert rel(host(S.vcycle(cu(b32, torch.float32))), H.vcycle(b32)) < 1e-4
+
+
+@pytest.mark.parametrize("smoother", ["vanka", "sc"])
+@pytest.mark.parametrize("nu1,nu2", [(0, 1), (1, 0), (3, 1)])
+def test_vcycle_small_levels_sweep_counts(smoother, nu1, nu2):
+    """Sweep counts other than (2, 2) -- no pre-smoothing, an odd number of sweeps -- through the
+    single-block kernel of levels 1 and 0."""
+    prob = I.disk_stokes(32, kappa=1e2)
+    H = multigrid.Hierarchy(prob, smoother=smoother, nu1=nu1, nu2=nu2)
+    S = sib.solver_for(prob, smoother=sib.SMOOTHER_SC if smoother == "sc" else sib.SMOOTHER_VANKA, nu1=nu1,
+                       nu2=nu2)
+    if smoother == "sc":
+        S.set_eigen_estimates([0.0] + [lv.lamA for lv in H.levels[1:]], [0.0] + [lv.lamM for lv in H.levels[1:]])
+        S.setup()
+    b = system.rhs(prob)
+    assert rel(host(S.vcycle(cu(b))), H.vcycle(b)) < TOL64
+    b32 = b.astype(np.float32).astype(np.float64)
+    assert rel(host(S.vcycle(cu(b32, torch.float32))), H.vcycle(b32)) < 1e-4
+
+
 def test_vcycle_large_grid_against_oracle():
     """One V-cycle at N = 512 (FP32 levels 512 and 256 use the pipelined and tiled sweep kernels,
     the first sweep of each level the zero-guess form) against the oracle's V-cycle."""
