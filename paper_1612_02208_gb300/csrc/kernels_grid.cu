@@ -172,17 +172,32 @@ VankaBulk<T> vanka_bulk(double a0, double c, double inv_h) {
 template <typename T, bool ZERO>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_vanka_tiled(GridK<T> g, VankaBulk<T> kb, const T* __restrict__ x,
                                                      const T* __restrict__ b, T* __restrict__ xo) {
-    pdl_entry();
     constexpr int SX = TX + 4, SY = TY + 4;   // staged x: tile plus two cells each side
     constexpr int RX = TX + 2, RY = TY + 2;   // residuals: tile plus one cell each side
     constexpr int PX = TX + 1, PY = TY + 1;   // patches: tile plus its left and bottom neighbours
     __shared__ T xs[3][SY][SX];
     __shared__ T rs[3][RY][RX];
     __shared__ T ds[5][PY][PX];
+    __shared__ T bs[6][PY][PX];   // IB entries of the patches of an active tile
     const int N = g.N, n = N * N, m = N - 1;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
     const int tid = threadIdx.y * TX + threadIdx.x;
+    // set-up data (tile flag, patch entries) before the wait for x and b
     const bool act = g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x];
+    if (act) {
+        for (int q = tid; q < PY * PX; q += TX * TY) {
+            const int pj = q / PX, pi = q - pj * PX;
+            const int i = (i0 - 1 + pi) & m, j = (j0 - 1 + pj) & m;
+            const int cc = j * N + i, ce = j * N + ((i + 1) & m), cn = ((j + 1) & m) * N + i;
+            bs[0][pj][pi] = g.ibd[cc];
+            bs[1][pj][pi] = g.ibd[ce];
+            bs[2][pj][pi] = g.ibd[n + cc];
+            bs[3][pj][pi] = g.ibd[2 * n + cc];
+            bs[4][pj][pi] = g.ibd[2 * n + cn];
+            bs[5][pj][pi] = g.ibd[3 * n + cc];
+        }
+    }
+    pdl_entry();
     if (!ZERO) {
         for (int q = tid; q < SY * SX; q += TX * TY) {
             const int jj = q / SX, ii = q - jj * SX;
@@ -234,11 +249,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_vanka_tiled(Gri
             d2 = tv0 - kb.s0 * dp;
             d3 = tv1 + kb.s0 * dp;
         } else {
-            const int i = (i0 - 1 + pi) & m, j = (j0 - 1 + pj) & m;
-            const int cc = j * N + i, ce = j * N + ((i + 1) & m), cn = ((j + 1) & m) * N + i;
-            const T au00 = g.a0 - g.dt * g.ibd[cc], au11 = g.a0 - g.dt * g.ibd[ce], au01 = -g.c - g.dt * g.ibd[n + cc];
-            const T av00 = g.a0 - g.dt * g.ibd[2 * n + cc], av11 = g.a0 - g.dt * g.ibd[2 * n + cn],
-                    av01 = -g.c - g.dt * g.ibd[3 * n + cc];
+            const T au00 = g.a0 - g.dt * bs[0][pj][pi], au11 = g.a0 - g.dt * bs[1][pj][pi],
+                    au01 = -g.c - g.dt * bs[2][pj][pi];
+            const T av00 = g.a0 - g.dt * bs[3][pj][pi], av11 = g.a0 - g.dt * bs[4][pj][pi],
+                    av01 = -g.c - g.dt * bs[5][pj][pi];
             const T idu = T(1) / (au00 * au11 - au01 * au01);
             const T idv = T(1) / (av00 * av11 - av01 * av01);
             const T su0 = (au11 + au01) * ih * idu, su1 = -(au01 + au00) * ih * idu;

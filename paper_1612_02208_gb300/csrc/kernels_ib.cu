@@ -869,8 +869,8 @@ template <typename T>
 __global__ void __launch_bounds__(32 * WD) k_ib_window(const T* __restrict__ win, const int* __restrict__ tiles,
                                                        const int* __restrict__ nTiles, int N, int tx, int ty, int ntx,
                                                        const T* __restrict__ u, T* __restrict__ f) {
-    pdl_entry();
     __shared__ T part[WD][32];
+    // the tile list and the window coefficients are set-up data: read before waiting for u
     const int slot = blockIdx.x;
     if (slot >= *nTiles) return;
     const int per = tx * ty;
@@ -881,12 +881,18 @@ __global__ void __launch_bounds__(32 * WD) k_ib_window(const T* __restrict__ win
     const int t = tiles[slot];
     const int i = (t % ntx) * tx + (live ? q % tx : 0), j = (t / ntx) * ty + (live ? q / tx : 0);
     const int n = N * N, mk = N - 1;
-    T acc = T(0);
+    T wv[WD];
     if (live) {
         const T* w = win + ((size_t)(slot * 2 + c) * WIN_SIZE + (size_t)threadIdx.y * WD) * per + q;
+#pragma unroll
+        for (int ox = 0; ox < WD; ++ox) wv[ox] = w[(size_t)ox * per];
+    }
+    pdl_entry();
+    T acc = T(0);
+    if (live) {
         const T* row = u + (size_t)c * n + (size_t)((j + oy) & mk) * N;
 #pragma unroll
-        for (int ox = -WR; ox <= WR; ++ox) acc += w[(size_t)(ox + WR) * per] * row[(i + ox) & mk];
+        for (int ox = -WR; ox <= WR; ++ox) acc += wv[ox + WR] * row[(i + ox) & mk];
     }
     part[threadIdx.y][threadIdx.x] = acc;
     __syncthreads();
