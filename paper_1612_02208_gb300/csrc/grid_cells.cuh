@@ -69,6 +69,38 @@ __device__ __forceinline__ T res_p(const GridK<T>& g, const T* __restrict__ x, c
     return b[2 * n + c] + ((x[j * N + ((i + 1) & m)] - x[c]) + (x[n + ((j + 1) & m) * N + i] - x[n + c])) * g.inv_h;
 }
 
+// The same residual entries at a face of a tile whose IB flag `act` the caller has already read.
+template <typename T>
+__device__ __forceinline__ T ibf_act(const GridK<T>& g, bool act, int comp, int i, int j) {
+    return act ? g.fib[(size_t)comp * g.N * g.N + j * g.N + i] : T(0);
+}
+template <typename T>
+__device__ __forceinline__ T res_u_act(const GridK<T>& g, bool act, const T* __restrict__ x, const T* __restrict__ b,
+                                       int i, int j) {
+    const int N = g.N, m = N - 1;
+    const T* u = x;
+    const T* p = x + 2 * N * N;
+    const int c = j * N + i;
+    T Au = g.a0 * u[c] - g.c * ((u[j * N + ((i + 1) & m)] + u[j * N + ((i - 1) & m)]) +
+                                (u[((j + 1) & m) * N + i] + u[((j - 1) & m) * N + i])) +
+           (p[c] - p[j * N + ((i - 1) & m)]) * g.inv_h;
+    Au -= g.dt * ibf_act(g, act, 0, i, j);
+    return b[c] - Au;
+}
+template <typename T>
+__device__ __forceinline__ T res_v_act(const GridK<T>& g, bool act, const T* __restrict__ x, const T* __restrict__ b,
+                                       int i, int j) {
+    const int N = g.N, n = N * N, m = N - 1;
+    const T* v = x + n;
+    const T* p = x + 2 * n;
+    const int c = j * N + i;
+    T Av = g.a0 * v[c] - g.c * ((v[j * N + ((i + 1) & m)] + v[j * N + ((i - 1) & m)]) +
+                                (v[((j + 1) & m) * N + i] + v[((j - 1) & m) * N + i])) +
+           (p[c] - p[((j - 1) & m) * N + i]) * g.inv_h;
+    Av -= g.dt * ibf_act(g, act, 1, i, j);
+    return b[n + c] - Av;
+}
+
 // Coarse right-hand side of coarse cell (I, J): R (b - L x) from the sixteen fine residuals that
 // R = diag(P_u^T / 4, P_v^T / 4, average) combines (Sec. 3.2, Alg. 1).
 template <typename T>
@@ -174,30 +206,65 @@ __device__ __forceinline__ T dM_inv(const GridK<T>& g, int i, int j) {
     return T(1) / (-s * g.inv_h * g.inv_h);
 }
 
+// Set-up values an SC stage needs at cell (i, j): the IB flag of the cell's tile (the IB force of
+// its faces is read only there) and the diagonal inverses of DA on its two faces and, with M, of DM
+// on the cell and its west and south neighbours.  The per-level kernels load them before waiting
+// for the stage's inputs.
+template <typename T>
+struct ScPre {
+    bool act;
+    T a0, a1, m, mw, ms;
+};
+template <typename T, bool M>
+__device__ __forceinline__ ScPre<T> sc_pre(const GridK<T>& g, int i, int j) {
+    const int N = g.N, n = N * N, mk = N - 1, c = j * N + i;
+    ScPre<T> p;
+    p.act = g.tile != nullptr && g.tile[(j >> g.lgty) * g.ntx + (i >> g.lgtx)];
+    p.a0 = g.dinv[c];
+    p.a1 = g.dinv[n + c];
+    if (M) {
+        p.m = g.dinv[2 * n + c];
+        p.mw = g.dinv[2 * n + j * N + ((i - 1) & mk)];
+        p.ms = g.dinv[2 * n + ((j - 1) & mk) * N + i];
+    } else {
+        p.m = p.mw = p.ms = T(0);
+    }
+    return p;
+}
+template <typename T>
+__device__ __forceinline__ T Aib_act(const GridK<T>& g, bool act, const T* __restrict__ d, int comp, int i, int j) {
+    const int N = g.N, m = N - 1;
+    const T* dc = d + (size_t)comp * N * N;
+    const T a = g.a0 * dc[j * N + i] - g.c * ((dc[j * N + ((i + 1) & m)] + dc[j * N + ((i - 1) & m)]) +
+                                             (dc[((j + 1) & m) * N + i] + dc[((j - 1) & m) * N + i]));
+    return a - g.dt * ibf_act(g, act, comp, i, j);
+}
+
 // r = b - L x (x == nullptr: zero initial guess, r = b);  d = DA^{-1} r_u / theta_A
 template <typename T>
 __device__ __forceinline__ void sc_start_cell(const GridK<T>& g, const Cheb2<T>& ka, const T* __restrict__ x,
                                               const T* __restrict__ b, T* __restrict__ r, T* __restrict__ d, int i,
-                                              int j) {
+                                              int j, const ScPre<T>& p) {
     const int N = g.N, n = N * N;
     const int c = j * N + i;
-    const T ru = x ? res_u(g, x, b, i, j) : b[c], rv = x ? res_v(g, x, b, i, j) : b[n + c];
+    const T ru = x ? res_u_act(g, p.act, x, b, i, j) : b[c], rv = x ? res_v_act(g, p.act, x, b, i, j) : b[n + c];
     r[c] = ru;
     r[n + c] = rv;
     r[2 * n + c] = x ? res_p(g, x, b, i, j) : b[2 * n + c];
-    d[c] = ka.inv_theta * ru * g.dinv[c];
-    d[n + c] = ka.inv_theta * rv * g.dinv[n + c];
+    d[c] = ka.inv_theta * ru * p.a0;
+    d[n + c] = ka.inv_theta * rv * p.a1;
 }
 // y = (1 + c1) d + c2 DA^{-1} (q - A_IB d)   (g.fib holds [SKJ] d)
 template <typename T>
 __device__ __forceinline__ void sc_chebA_cell(const GridK<T>& g, const Cheb2<T>& ka, const T* __restrict__ q,
-                                              const T* __restrict__ d, T* __restrict__ y, int i, int j) {
+                                              const T* __restrict__ d, T* __restrict__ y, int i, int j,
+                                              const ScPre<T>& p) {
     const int N = g.N, n = N * N;
     const int c = j * N + i;
     for (int comp = 0; comp < 2; ++comp) {
         const int f = comp * n + c;
-        const T rr = q[f] - Aib(g, d, comp, i, j);
-        y[f] = ka.one_c1 * d[f] + ka.c2 * rr * g.dinv[f];
+        const T rr = q[f] - Aib_act(g, p.act, d, comp, i, j);
+        y[f] = ka.one_c1 * d[f] + ka.c2 * rr * (comp ? p.a1 : p.a0);
     }
 }
 // s = r_p + D y;  e0 = DM^{-1} s / theta_M;  gq = G e0;  dA = DA^{-1} gq / theta_A
@@ -205,59 +272,59 @@ template <typename T>
 __device__ __forceinline__ void sc_mstart_cell(const GridK<T>& g, const Cheb2<T>& ka, const Cheb2<T>& km,
                                                const T* __restrict__ rp, const T* __restrict__ y, T* __restrict__ sv,
                                                T* __restrict__ dMo, T* __restrict__ gq, T* __restrict__ dA, int i,
-                                               int j) {
+                                               int j, const ScPre<T>& p) {
     const int N = g.N, n = N * N, m = N - 1;
     const int c = j * N + i;
-    auto e0 = [&](int ii, int jj, T* sOut) {
+    auto e0 = [&](int ii, int jj, T dm, T* sOut) {
         ii &= m;
         jj &= m;
         const T sval = rp[jj * N + ii] + divg(g, y, ii, jj);
         if (sOut) *sOut = sval;
-        return km.inv_theta * sval * g.dinv[2 * n + jj * N + ii];
+        return km.inv_theta * sval * dm;
     };
     T sc;
-    const T ec = e0(i, j, &sc), ew = e0(i - 1, j, nullptr), es = e0(i, j - 1, nullptr);
+    const T ec = e0(i, j, p.m, &sc), ew = e0(i - 1, j, p.mw, nullptr), es = e0(i, j - 1, p.ms, nullptr);
     sv[c] = sc;
     dMo[c] = ec;
     const T gu = (ec - ew) * g.inv_h, gv = (ec - es) * g.inv_h;
     gq[c] = gu;
     gq[n + c] = gv;
-    dA[c] = ka.inv_theta * gu * g.dinv[c];
-    dA[n + c] = ka.inv_theta * gv * g.dinv[n + c];
+    dA[c] = ka.inv_theta * gu * p.a0;
+    dA[n + c] = ka.inv_theta * gv * p.a1;
 }
 // dp = (1 + c1) e0 + c2 DM^{-1} (s - D ya);  gq = G dp;  dA = DA^{-1} gq / theta_A
 template <typename T>
 __device__ __forceinline__ void sc_mfinish_cell(const GridK<T>& g, const Cheb2<T>& ka, const Cheb2<T>& km,
                                                 const T* __restrict__ sv, const T* __restrict__ dM,
                                                 const T* __restrict__ ya, T* __restrict__ dp, T* __restrict__ gq,
-                                                T* __restrict__ dA, int i, int j) {
+                                                T* __restrict__ dA, int i, int j, const ScPre<T>& p) {
     const int N = g.N, n = N * N, m = N - 1;
     const int c = j * N + i;
-    auto pval = [&](int ii, int jj) {
+    auto pval = [&](int ii, int jj, T dm) {
         ii &= m;
         jj &= m;
         const int cc = jj * N + ii;
-        return km.one_c1 * dM[cc] + km.c2 * (sv[cc] - divg(g, ya, ii, jj)) * g.dinv[2 * n + cc];
+        return km.one_c1 * dM[cc] + km.c2 * (sv[cc] - divg(g, ya, ii, jj)) * dm;
     };
-    const T pc = pval(i, j), pw = pval(i - 1, j), ps = pval(i, j - 1);
+    const T pc = pval(i, j, p.m), pw = pval(i - 1, j, p.mw), ps = pval(i, j - 1, p.ms);
     dp[c] = pc;
     const T gu = (pc - pw) * g.inv_h, gv = (pc - ps) * g.inv_h;
     gq[c] = gu;
     gq[n + c] = gv;
-    dA[c] = ka.inv_theta * gu * g.dinv[c];
-    dA[n + c] = ka.inv_theta * gv * g.dinv[n + c];
+    dA[c] = ka.inv_theta * gu * p.a0;
+    dA[n + c] = ka.inv_theta * gv * p.a1;
 }
 // yy = (1 + c1) dA + c2 DA^{-1} (gq - A_IB dA);  xo = x + omega (y - yy, dp)  (x == nullptr: x = 0)
 template <typename T>
 __device__ __forceinline__ void sc_finish_cell(const GridK<T>& g, const Cheb2<T>& ka, const T* __restrict__ x,
                                                const T* __restrict__ y, const T* __restrict__ gq,
                                                const T* __restrict__ dA, const T* __restrict__ dp, T* __restrict__ xo,
-                                               int i, int j) {
+                                               int i, int j, const ScPre<T>& p) {
     const int N = g.N, n = N * N;
     const int c = j * N + i;
     for (int comp = 0; comp < 2; ++comp) {
         const int f = comp * n + c;
-        const T yy = ka.one_c1 * dA[f] + ka.c2 * (gq[f] - Aib(g, dA, comp, i, j)) * g.dinv[f];
+        const T yy = ka.one_c1 * dA[f] + ka.c2 * (gq[f] - Aib_act(g, p.act, dA, comp, i, j)) * (comp ? p.a1 : p.a0);
         xo[f] = (x ? x[f] : T(0)) + g.omega * (y[f] - yy);
     }
     xo[2 * n + c] = (x ? x[2 * n + c] : T(0)) + g.omega * dp[c];

@@ -17,6 +17,7 @@ namespace sib {
 template <typename T, bool HAS_B>
 __global__ void __launch_bounds__(256) k_residual(GridK<T> g, const T* __restrict__ x, const T* __restrict__ b,
                                                   T* __restrict__ r) {
+    const bool act = g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x];   // set-up data, before the wait
     pdl_entry();
     const int N = g.N, n = N * N, m = N - 1;
     const int i = blockIdx.x * g.tx + threadIdx.x;
@@ -33,8 +34,8 @@ __global__ void __launch_bounds__(256) k_residual(GridK<T> g, const T* __restric
     T Au = g.a0 * uc - g.c * ((uE + uW) + (uN + uS)) + (pc - pW) * g.inv_h;
     T Av = g.a0 * vc - g.c * ((vE + vW) + (vN + vS)) + (pc - pS) * g.inv_h;
     const T Dp = -((uE - uc) + (vN - vc)) * g.inv_h;
-    Au -= g.dt * ibf(g, x, 0, i, j);
-    Av -= g.dt * ibf(g, x, 1, i, j);
+    Au -= g.dt * ibf_act(g, act, 0, i, j);
+    Av -= g.dt * ibf_act(g, act, 1, i, j);
     if (HAS_B) {
         r[c] = b[c] - Au;
         r[n + c] = b[n + c] - Av;
@@ -529,34 +530,44 @@ void launch_cheb_update(const T* dinvr, T* d, T* x, T ra, T rb, int64_t n, cudaS
 // Mt^{-1} s = (1 + c1) e0 + c2 DM^{-1}(s - D At^{-1} G e0), e0 = DM^{-1} s / theta_M, where DA is
 // diag(A_IB) and DM = diag(D DA^{-1} G).  A kernel that needs G of a cell-centred quantity
 // recomputes that quantity on the two neighbouring cells instead of synchronising.
+// The SC stage kernels read their set-up values (tile flag, diagonal inverses) before waiting for
+// the stage's inputs.
 template <typename T>
 __global__ void __launch_bounds__(256) k_sc_start(GridK<T> g, Cheb2<T> ka, const T* __restrict__ x,
                                                   const T* __restrict__ b, T* __restrict__ r, T* __restrict__ d) {
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const ScPre<T> p = sc_pre<T, false>(g, i, j);
     pdl_entry();
-    sc_start_cell(g, ka, x, b, r, d, blockIdx.x * g.tx + threadIdx.x, blockIdx.y * g.ty + threadIdx.y);
+    sc_start_cell(g, ka, x, b, r, d, i, j, p);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_sc_chebA(GridK<T> g, Cheb2<T> ka, const T* __restrict__ q,
                                                   const T* __restrict__ d, T* __restrict__ y) {
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const ScPre<T> p = sc_pre<T, false>(g, i, j);
     pdl_entry();
-    sc_chebA_cell(g, ka, q, d, y, blockIdx.x * g.tx + threadIdx.x, blockIdx.y * g.ty + threadIdx.y);
+    sc_chebA_cell(g, ka, q, d, y, i, j, p);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_sc_mstart(GridK<T> g, Cheb2<T> ka, Cheb2<T> km, const T* __restrict__ rp,
                                                    const T* __restrict__ y, T* __restrict__ sv, T* __restrict__ dMo,
                                                    T* __restrict__ gq, T* __restrict__ dA) {
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const ScPre<T> p = sc_pre<T, true>(g, i, j);
     pdl_entry();
-    sc_mstart_cell(g, ka, km, rp, y, sv, dMo, gq, dA, blockIdx.x * g.tx + threadIdx.x, blockIdx.y * g.ty + threadIdx.y);
+    sc_mstart_cell(g, ka, km, rp, y, sv, dMo, gq, dA, i, j, p);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_sc_mfinish(GridK<T> g, Cheb2<T> ka, Cheb2<T> km, const T* __restrict__ sv,
                                                     const T* __restrict__ dM, const T* __restrict__ ya,
                                                     T* __restrict__ dp, T* __restrict__ gq, T* __restrict__ dA) {
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const ScPre<T> p = sc_pre<T, true>(g, i, j);
     pdl_entry();
-    sc_mfinish_cell(g, ka, km, sv, dM, ya, dp, gq, dA, blockIdx.x * g.tx + threadIdx.x, blockIdx.y * g.ty + threadIdx.y);
+    sc_mfinish_cell(g, ka, km, sv, dM, ya, dp, gq, dA, i, j, p);
 }
 
 template <typename T>
@@ -564,8 +575,10 @@ __global__ void __launch_bounds__(256) k_sc_finish(GridK<T> g, Cheb2<T> ka, cons
                                                    const T* __restrict__ y, const T* __restrict__ gq,
                                                    const T* __restrict__ dA, const T* __restrict__ dp,
                                                    T* __restrict__ xo) {
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const ScPre<T> p = sc_pre<T, false>(g, i, j);
     pdl_entry();
-    sc_finish_cell(g, ka, x, y, gq, dA, dp, xo, blockIdx.x * g.tx + threadIdx.x, blockIdx.y * g.ty + threadIdx.y);
+    sc_finish_cell(g, ka, x, y, gq, dA, dp, xo, i, j, p);
 }
 
 // power iterations: w = DA^{-1} A_IB v; gq = G v, dA = DA^{-1} gq / theta_A; w = DM^{-1} D ya

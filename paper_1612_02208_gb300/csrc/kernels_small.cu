@@ -202,31 +202,34 @@ __device__ void sm_sc(const GridK<T>& g, const SmallArgs<T>& a, const SmallSmem<
         sm_ib(g, s, a.nTiles, x, fib);
         __syncthreads();
     }
-    for (int c = threadIdx.x; c < n; c += NT) sc_start_cell(g, a.ka, x, b, s.r, s.d, c & m, c >> ilog2(N));
+    for (int c = threadIdx.x; c < n; c += NT) sc_start_cell(g, a.ka, x, b, s.r, s.d, c & m, c >> ilog2(N), sc_pre<T, false>(g, c & m, c >> ilog2(N)));
     __syncthreads();
     if (ib) {
         sm_ib(g, s, a.nTiles, s.d, fib);
         __syncthreads();
     }
-    for (int c = threadIdx.x; c < n; c += NT) sc_chebA_cell(g, a.ka, s.r, s.d, s.y, c & m, c >> ilog2(N));
+    for (int c = threadIdx.x; c < n; c += NT) sc_chebA_cell(g, a.ka, s.r, s.d, s.y, c & m, c >> ilog2(N), sc_pre<T, false>(g, c & m, c >> ilog2(N)));
     __syncthreads();
     for (int c = threadIdx.x; c < n; c += NT)
-        sc_mstart_cell(g, a.ka, a.km, s.r + 2 * n, s.y, s.sv, s.dM, s.gq, s.dA, c & m, c >> ilog2(N));
+        sc_mstart_cell(g, a.ka, a.km, s.r + 2 * n, s.y, s.sv, s.dM, s.gq, s.dA, c & m, c >> ilog2(N),
+                       sc_pre<T, true>(g, c & m, c >> ilog2(N)));
     __syncthreads();
     if (ib) {
         sm_ib(g, s, a.nTiles, s.dA, fib);
         __syncthreads();
     }
-    for (int c = threadIdx.x; c < n; c += NT) sc_chebA_cell(g, a.ka, s.gq, s.dA, s.ya, c & m, c >> ilog2(N));
+    for (int c = threadIdx.x; c < n; c += NT) sc_chebA_cell(g, a.ka, s.gq, s.dA, s.ya, c & m, c >> ilog2(N), sc_pre<T, false>(g, c & m, c >> ilog2(N)));
     __syncthreads();
     for (int c = threadIdx.x; c < n; c += NT)
-        sc_mfinish_cell(g, a.ka, a.km, s.sv, s.dM, s.ya, s.dp, s.gq2, s.dA2, c & m, c >> ilog2(N));
+        sc_mfinish_cell(g, a.ka, a.km, s.sv, s.dM, s.ya, s.dp, s.gq2, s.dA2, c & m, c >> ilog2(N),
+                        sc_pre<T, true>(g, c & m, c >> ilog2(N)));
     __syncthreads();
     if (ib) {
         sm_ib(g, s, a.nTiles, s.dA2, fib);
         __syncthreads();
     }
-    for (int c = threadIdx.x; c < n; c += NT) sc_finish_cell(g, a.ka, x, s.y, s.gq2, s.dA2, s.dp, xo, c & m, c >> ilog2(N));
+    for (int c = threadIdx.x; c < n; c += NT) sc_finish_cell(g, a.ka, x, s.y, s.gq2, s.dA2, s.dp, xo, c & m, c >> ilog2(N),
+                       sc_pre<T, false>(g, c & m, c >> ilog2(N)));
     __syncthreads();
 }
 
