@@ -229,6 +229,7 @@ def large_vcycle(sib, torch, reps=20, N=None):
     n3 = 3 * LARGE * LARGE
     b = torch.randn(n3, device=dev, dtype=torch.float32)
     z = torch.empty_like(b)
+    torch.cuda.nvtx.range_push("vcycles")
     for _ in range(3):
         S.vcycle(b, z)
     torch.cuda.synchronize()
@@ -238,12 +239,15 @@ def large_vcycle(sib, torch, reps=20, N=None):
         S.vcycle(b, z)
     e1.record()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     t_v = e0.elapsed_time(e1) / reps
     lmax = S.num_levels - 1
     out = {"workload": f"thin_ellipse_re_N{LARGE}_kappa1e4", "N": LARGE, "vcycle_ms": round(t_v, 4),
            "vcycle_mdofs": round(n3 / (t_v * 1e-3) / 1e6, 1), "kernels": {}}
     for name in ("vanka", "residual", "restrict", "prolong"):
+        torch.cuda.nvtx.range_push("roofline_large_" + name)
         ms, by = S.time_kernel(name, lmax, True, reps=20)
+        torch.cuda.nvtx.range_pop()
         out["kernels"][name] = {"ms": round(ms, 5), "bytes": by, "gbs": round(by / (ms * 1e-3) / 1e9, 1)}
     S.close()
     return out
@@ -309,7 +313,9 @@ def run_native(args):
     S.set_options(smoother=sib.SMOOTHER_VANKA, omega=-1.0)
     S.set_stiffness(torch.full((st.E,), 1e2, dtype=torch.float64, device=dev))
     S.setup()
+    torch.cuda.nvtx.range_push("roofline_vanka")
     dom_ms, dom_bytes = S.time_kernel("vanka", lmax, True, reps=50)
+    torch.cuda.nvtx.range_pop()
     peak, peak_kind = measured_peaks()
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": "k_vanka<float> (finest level)", "achieved": round(achieved, 1),
