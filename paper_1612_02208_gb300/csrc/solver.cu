@@ -80,6 +80,8 @@ struct sib_ctx {
     double setup_ms = 0.0;
     std::vector<void*> allocs;
     cudaStream_t cap = nullptr;
+    cudaStream_t aux = nullptr;          // set-up work that runs beside the main stream
+    cudaEvent_t evFork = nullptr, evJoin = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // structure
     int M = 0, E = 0;
@@ -834,17 +836,17 @@ void setup(sib_ctx* c, cudaStream_t s) {
         c->kappaDirty = false;
         c->fluidDirty = true;
     }
-    // coarsest pseudo-inverse (depends on rho, mu, dt and kappa)
+    // coarsest pseudo-inverse (depends on rho, mu, dt and kappa).  The Gauss-Jordan inversion holds
+    // one 16-block cluster for about a millisecond; it runs on the auxiliary stream, beside the SC
+    // eigenvalue estimates below (which do not use it), and the main stream joins it at the end.
     {
         const int n = c->n0;
         KL(c, launch_assemble_L0(c->L[0].N, c->rho, c->mu, c->dt, c->B0, c->Aug, s));
-        KL(c, launch_gauss_jordan(c->Aug, n, c->info, c->piv, s));
-        KL(c, launch_extract_pinv(c->Aug, c->piv, n, c->L[0].N, c->rho, c->Pinv, s));
-        int info = 0;
-        CK(cudaMemcpyAsync(&info, c->info, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        if (info != 0) throw SibError(SIB_ERR_ARG, "coarsest operator is singular beyond its gauge kernel");
-        c->fluidDirty = false;
+        CK(cudaEventRecord(c->evFork, s));
+        CK(cudaStreamWaitEvent(c->aux, c->evFork, 0));
+        KL(c, launch_gauss_jordan(c->Aug, n, c->info, c->piv, c->aux));
+        KL(c, launch_extract_pinv(c->Aug, c->piv, n, c->L[0].N, c->rho, c->Pinv, c->aux));
+        CK(cudaEventRecord(c->evJoin, c->aux));
     }
     if (c->opts.smoother == SIB_SMOOTHER_SC) {
         alloc_sc_bufs(c);
@@ -872,6 +874,14 @@ void setup(sib_ctx* c, cudaStream_t s) {
             CK(cudaStreamSynchronize(s));
             for (int l = 1; l <= L; ++l) c->L[l].lamM = std::sqrt(c->hbuf[320 + l]);
         }
+    }
+    CK(cudaStreamWaitEvent(s, c->evJoin, 0));
+    {
+        int info = 0;
+        CK(cudaMemcpyAsync(&info, c->info, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (info != 0) throw SibError(SIB_ERR_ARG, "coarsest operator is singular beyond its gauge kernel");
+        c->fluidDirty = false;
     }
     alloc_krylov(c);
     CK(cudaEventRecord(c->ev1, s));
@@ -1403,6 +1413,9 @@ int sib_create(sib_ctx** out, int N, int n_min) {
             CK(cudaDeviceGetAttribute(&c->smemOptin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         }
         CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->evFork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->evJoin, cudaEventDisableTiming));
         CK(cudaEventCreate(&c->ev0));
         CK(cudaEventCreate(&c->ev1));
         alloc_level_bufs(c);
@@ -1440,6 +1453,9 @@ void sib_destroy(sib_ctx* c) {
     c->allocs.clear();
     if (c->hbuf) cudaFreeHost(c->hbuf);
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->evFork) cudaEventDestroy(c->evFork);
+    if (c->evJoin) cudaEventDestroy(c->evJoin);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;
