@@ -181,32 +181,80 @@ void launch_assemble_L0(int N0, double rho, double mu, double dt, const double* 
     launch_pdl(k_assemble_L0, (int)((tot + 255) / 256), 256, 0, s, N0, rho, mu, dt, B, Aug);
 }
 
-// In-place Gauss-Jordan elimination with partial pivoting on Aug (n x 2n, row-major) by one
-// block; on exit the right half holds the inverse.  info = 0, or k+1 if pivot k is zero.
-// (Fallback for coarsest grids too large for the cluster version below.)
-__global__ void __launch_bounds__(1024) k_gauss_jordan(double* __restrict__ A, int n, int* __restrict__ info,
-                                                       int* __restrict__ piv) {
+// Blocked Gauss-Jordan inversion with partial pivoting of Aug = [A | I] (n x 2n, row-major), in
+// panels of GJ_B columns.  For the panel Q = columns [c0, c0 + GJ_B):
+//   1. one block selects the panel's pivot rows P by partial pivoting on a working copy of the
+//      panel's candidate rows (largest |a| among rows not yet pivots, ties to the lower row, the
+//      copy eliminated as unblocked elimination would), and inverts the pivot block A_PQ in FP64
+//      with its pivots on the diagonal in selection order.  The working copy only chooses rows --
+//      the result is computed from the FP64 panel and A_PQ^{-1} -- so it is kept in FP32: one SM's
+//      FP64 rate made an FP64 copy cost ~120 us a panel, and FP32 can change a choice only between
+//      candidates equal to rounding, which partial pivoting leaves free;
+//   2. column slabs form the new pivot rows  W = A_PQ^{-1} A_P  on the columns right of Q;
+//   3. every other row r becomes  A_r - A_rQ W  there (A_rQ: its panel entries before the panel's
+//      elimination), and its panel entries 0 (the pivot rows' panel entries become unit vectors).
+// Rows are never swapped: piv[k] is the pivot row of column k and row k of A^{-1} is
+// Aug[piv[k]][n:].  info = 0, or k + 1 for the first pivot column without a nonzero candidate.
+// The panel steps are sequential but tiny; the O(n^3) work of step 3 spreads over the GPU, whose
+// FP64 rate is low per SM.
+constexpr int GJ_B = 16;
+
+struct GjWork {
+    double* Q0;   // n x GJ_B: the panel before its elimination
+    double* G;    // GJ_B x GJ_B: A_PQ^{-1}
+    double* W;    // GJ_B x 2n: the new pivot rows
+    int* used;    // n: row already a pivot
+    int* prow;    // GJ_B: the panel's pivot rows in selection order
+};
+static GjWork gj_work(void* base, int n) {
+    GjWork w;
+    double* d = static_cast<double*>(base);
+    w.Q0 = d;
+    w.G = w.Q0 + (size_t)n * GJ_B;
+    w.W = w.G + GJ_B * GJ_B;
+    w.used = reinterpret_cast<int*>(w.W + (size_t)GJ_B * 2 * n);
+    w.prow = w.used + n;
+    return w;
+}
+size_t gauss_jordan_work_bytes(int n) {
+    return sizeof(double) * ((size_t)n * GJ_B + GJ_B * GJ_B + (size_t)GJ_B * 2 * n) + sizeof(int) * (size_t)(n + GJ_B);
+}
+
+__global__ void __launch_bounds__(512) k_gj_panel(const double* __restrict__ A, int n, int c0, GjWork w,
+                                                  int* __restrict__ piv, int* __restrict__ info) {
     pdl_entry();
-    extern __shared__ double fac[];   // n factors
-    __shared__ int pivs;
-    __shared__ double wv[32];
+    extern __shared__ float smf[];
+    float* Wp = smf;                                      // n x GJ_B working copy of the panel
+    float* fac = Wp + (size_t)n * GJ_B;                   // n: column t before the pivot's elimination
+    int* usedS = reinterpret_cast<int*>(fac + n);         // n
+    __shared__ float prowv[GJ_B];
+    __shared__ double Mx[GJ_B][2 * GJ_B];
+    __shared__ double colv[GJ_B], rowv[2 * GJ_B];
+    __shared__ float wv[32];
     __shared__ int wi[32];
-    const int ld = 2 * n;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) *info = 0;
-    for (int k = 0; k < n; ++k) {
-        // pivot search over rows k..n-1 of column k
-        double best = -1.0;
-        int bi = k;
-        for (int r = k + threadIdx.x; r < n; r += blockDim.x) {
-            const double a = fabs(A[(int64_t)r * ld + k]);
+    __shared__ int pS[GJ_B];
+    const int ld = 2 * n, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (c0 == 0 && threadIdx.x == 0) *info = 0;
+    for (int q = threadIdx.x; q < n * GJ_B; q += blockDim.x) {
+        const double v = A[(size_t)(q / GJ_B) * ld + c0 + (q % GJ_B)];
+        Wp[q] = (float)v;
+        w.Q0[q] = v;
+    }
+    for (int r = threadIdx.x; r < n; r += blockDim.x) usedS[r] = c0 == 0 ? 0 : w.used[r];
+    __syncthreads();
+    for (int t = 0; t < GJ_B; ++t) {
+        float best = -1.0f;
+        int bi = n;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            if (usedS[r]) continue;
+            const float a = fabsf(Wp[r * GJ_B + t]);
             if (a > best) {
                 best = a;
                 bi = r;
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ob > best || (ob == best && oi < bi)) {
                 best = ob;
@@ -218,175 +266,129 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(double* __restrict__ A, i
             wi[wid] = bi;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double b = wv[0];
-            int p = wi[0];
-            for (int w = 1; w < nw; ++w)
-                if (wv[w] > b || (wv[w] == b && wi[w] < p)) {
-                    b = wv[w];
-                    p = wi[w];
+        if (wid == 0) {
+            best = lane < nw ? wv[lane] : -1.0f;
+            bi = lane < nw ? wi[lane] : n;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
                 }
-            pivs = p;
-            if (!(b > 0.0) && *info == 0) *info = k + 1;
+            }
+            if (lane == 0) {
+                pS[t] = bi;
+                usedS[bi] = 1;
+            }
         }
         __syncthreads();
-        const int p = pivs;
-        if (p != k)
-            for (int c = threadIdx.x; c < ld; c += blockDim.x) {
-                const double t = A[(int64_t)k * ld + c];
-                A[(int64_t)k * ld + c] = A[(int64_t)p * ld + c];
-                A[(int64_t)p * ld + c] = t;
-            }
+        const int p = pS[t];
+        for (int r = threadIdx.x; r < n; r += blockDim.x) fac[r] = Wp[r * GJ_B + t];
+        if (threadIdx.x < GJ_B) prowv[threadIdx.x] = Wp[p * GJ_B + threadIdx.x];
         __syncthreads();
-        const double pv = A[(int64_t)k * ld + k];
-        const double ipv = pv != 0.0 ? 1.0 / pv : 0.0;
-        __syncthreads();
-        for (int c = threadIdx.x; c < ld; c += blockDim.x) A[(int64_t)k * ld + c] *= ipv;
-        for (int r = threadIdx.x; r < n; r += blockDim.x) fac[r] = (r == k) ? 0.0 : A[(int64_t)r * ld + k];
-        __syncthreads();
-        // eliminate column k from every other row (columns k.. of the left half, all of the right)
-        for (int r = 0; r < n; ++r) {
-            const double f = fac[r];
-            if (f == 0.0) continue;
-            for (int c = k + threadIdx.x; c < ld; c += blockDim.x) A[(int64_t)r * ld + c] -= f * A[(int64_t)k * ld + c];
+        const float pv = prowv[t];
+        const float ipv = pv != 0.0f ? 1.0f / pv : 0.0f;
+        for (int q = threadIdx.x; q < n * GJ_B; q += blockDim.x) {   // candidate rows only
+            const int r = q / GJ_B, tt = q % GJ_B;
+            if (tt <= t || usedS[r]) continue;
+            const float f = fac[r] * ipv;
+            if (f != 0.0f) Wp[q] -= f * prowv[tt];
         }
         __syncthreads();
     }
-    for (int r = threadIdx.x; r < n; r += blockDim.x) piv[r] = r;
-}
-// Gauss-Jordan elimination with partial pivoting by one thread-block cluster: block r of the
-// cluster keeps rows [r*rpc, (r+1)*rpc) of Aug in shared memory.  Pivot k: every block proposes
-// its largest |A[row][k]| among rows not yet used as pivots (ties: lower row), the cluster picks
-// the largest; every block copies the pivot row out of the owner's shared memory, and after a
-// cluster barrier eliminates column k from its rows while the owner scales the pivot row.  Rows
-// are not swapped: piv[k] records the pivot row of column k, so inverse row k = Aug[piv[k]][n:].
-__global__ void __launch_bounds__(256) k_gauss_jordan_cluster(double* __restrict__ A, int n, int rpc,
-                                                              int* __restrict__ info, int* __restrict__ piv) {
-    pdl_entry();
-    cg::cluster_group cluster = cg::this_cluster();
-    extern __shared__ double sm[];
-    const int ld = 2 * n;
-    double* rows = sm;                          // rpc x ld
-    double* prow = sm + (size_t)rpc * ld;       // ld
-    double* fac = prow + ld;                    // rpc
-    __shared__ double candVal;
-    __shared__ int candRow;
-    __shared__ double pivVal;
-    __shared__ int pivRow;
-    __shared__ int usedLocal[64];
-    const int rank = (int)cluster.block_rank();
-    const int csize = (int)cluster.num_blocks();
-    const int r0 = rank * rpc;
-    for (int q = threadIdx.x; q < rpc * ld; q += blockDim.x) rows[q] = A[(size_t)r0 * ld + q];
-    if (threadIdx.x < rpc) usedLocal[threadIdx.x] = 0;
-    if (rank == 0 && threadIdx.x == 0) *info = 0;
+    // G = A_PQ^{-1} in FP64: Gauss-Jordan on [A_PQ | I] with the pivots on the diagonal.  At step t
+    // the left columns < t are already unit vectors and the right columns > B + t still zero off
+    // the diagonal, so only columns [t, B + t] change (besides the diagonal's own unit entries).
+    for (int q = threadIdx.x; q < GJ_B * 2 * GJ_B; q += blockDim.x) {
+        const int t = q / (2 * GJ_B), u = q % (2 * GJ_B);
+        Mx[t][u] = u < GJ_B ? w.Q0[pS[t] * GJ_B + u] : (u - GJ_B == t ? 1.0 : 0.0);
+    }
     __syncthreads();
-    for (int k = 0; k < n; ++k) {
-        if (threadIdx.x < 32) {
-            double best = -1.0;
-            int bi = n;
-            for (int r = threadIdx.x; r < rpc; r += 32) {
-                if (usedLocal[r]) continue;
-                const double a = fabs(rows[(size_t)r * ld + k]);
-                if (a > best) {
-                    best = a;
-                    bi = r0 + r;
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) {
-                    best = ob;
-                    bi = oi;
-                }
-            }
-            if (threadIdx.x == 0) {
-                candVal = best;
-                candRow = bi;
-            }
-        }
-        cluster.sync();
-        // warp 0 gathers the cluster's candidates (lane b reads block b) and broadcasts the pivot
-        if (threadIdx.x < 32) {
-            double best = -1.0;
-            int bi = n;
-            if ((int)threadIdx.x < csize) {
-                best = *cluster.map_shared_rank(&candVal, (int)threadIdx.x);
-                bi = *cluster.map_shared_rank(&candRow, (int)threadIdx.x);
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) {
-                    best = ob;
-                    bi = oi;
-                }
-            }
-            if (threadIdx.x == 0) {
-                pivVal = best;
-                pivRow = bi;
-            }
-        }
+    for (int t = 0; t < GJ_B; ++t) {
+        if (threadIdx.x < GJ_B) colv[threadIdx.x] = Mx[threadIdx.x][t];
+        if (threadIdx.x < 2 * GJ_B) rowv[threadIdx.x] = Mx[t][threadIdx.x];
         __syncthreads();
-        const double best = pivVal;
-        const int p = pivRow;
-        const int owner = p / rpc, pl = p - owner * rpc;
-        const double* src = cluster.map_shared_rank(rows, owner) + (size_t)pl * ld;
-        for (int c = k + threadIdx.x; c < ld; c += blockDim.x) prow[c] = src[c];
-        for (int r = threadIdx.x; r < rpc; r += blockDim.x) fac[r] = (r0 + r == p) ? 0.0 : rows[(size_t)r * ld + k];
-        if (rank == 0 && threadIdx.x == 0) {
-            piv[k] = p;
-            if (!(best > 0.0) && *info == 0) *info = k + 1;
-        }
-        cluster.sync();
-        const double pv = prow[k];
-        const double ipv = pv != 0.0 ? 1.0 / pv : 0.0;
-        for (int r = 0; r < rpc; ++r) {
-            if (r0 + r == p) {
-                for (int c = k + threadIdx.x; c < ld; c += blockDim.x) rows[(size_t)r * ld + c] = prow[c] * ipv;
-                if (threadIdx.x == 0) usedLocal[r] = 1;
-                continue;
-            }
-            const double f = fac[r] * ipv;
-            if (f == 0.0) continue;
-            for (int c = k + threadIdx.x; c < ld; c += blockDim.x) rows[(size_t)r * ld + c] -= f * prow[c];
+        if (threadIdx.x == 0 && !(colv[t] != 0.0) && *info == 0) *info = c0 + t + 1;
+        const double ipv = colv[t] != 0.0 ? 1.0 / colv[t] : 0.0;
+        for (int q = threadIdx.x; q < GJ_B * 2 * GJ_B; q += blockDim.x) {
+            const int s2 = q / (2 * GJ_B), u = q % (2 * GJ_B);
+            if (u < t || u > GJ_B + t) continue;
+            if (s2 == t)
+                Mx[s2][u] = rowv[u] * ipv;
+            else
+                Mx[s2][u] -= colv[s2] * ipv * rowv[u];
         }
         __syncthreads();
     }
-    for (int q = threadIdx.x; q < rpc * ld; q += blockDim.x) A[(size_t)r0 * ld + q] = rows[q];
+    for (int q = threadIdx.x; q < GJ_B * GJ_B; q += blockDim.x) w.G[q] = Mx[q / GJ_B][GJ_B + q % GJ_B];
+    if (threadIdx.x < GJ_B) {
+        w.prow[threadIdx.x] = pS[threadIdx.x];
+        piv[c0 + threadIdx.x] = pS[threadIdx.x];
+    }
+    for (int r = threadIdx.x; r < n; r += blockDim.x) w.used[r] = usedS[r];
 }
 
-void launch_gauss_jordan(double* Aug, int n, int* info, int* piv, cudaStream_t s) {
-    for (int cs : {16, 8}) {
-        if (n % cs != 0) continue;
-        const int rpc = n / cs;
-        if (rpc > 64) continue;
-        const size_t smem = sizeof(double) * ((size_t)rpc * 2 * n + 2 * n + rpc);
-        if (smem > 200 * 1024) continue;
-        cudaFuncSetAttribute(k_gauss_jordan_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (cs > 8) cudaFuncSetAttribute(k_gauss_jordan_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(cs);
-        cfg.blockDim = dim3(256);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = cs;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, k_gauss_jordan_cluster, &cfg) != cudaSuccess || clusters < 1) {
-            cudaGetLastError();
-            continue;
-        }
-        if (cudaLaunchKernelEx(&cfg, k_gauss_jordan_cluster, Aug, n, rpc, info, piv) == cudaSuccess) return;
-        cudaGetLastError();
+// W = A_PQ^{-1} A_P on columns c >= c0 + GJ_B, written to the work array and into the pivot rows;
+// block (16 x 16): a slab of 16 columns, thread (x, y) = (column, pivot t)
+__global__ void __launch_bounds__(GJ_B * 16) k_gj_w(double* __restrict__ A, int n, int c0, GjWork w) {
+    pdl_entry();
+    __shared__ double ap[GJ_B][16];
+    __shared__ double g[GJ_B][GJ_B];
+    const int ld = 2 * n;
+    const int c = c0 + GJ_B + blockIdx.x * 16 + threadIdx.x;
+    const int t = threadIdx.y;
+    g[t][threadIdx.x] = w.G[t * GJ_B + threadIdx.x];
+    ap[t][threadIdx.x] = c < ld ? A[(size_t)w.prow[t] * ld + c] : 0.0;
+    __syncthreads();
+    if (c >= ld) return;
+    double acc = 0.0;
+#pragma unroll
+    for (int u = 0; u < GJ_B; ++u) acc += g[t][u] * ap[u][threadIdx.x];
+    w.W[(size_t)t * ld + c] = acc;
+    A[(size_t)w.prow[t] * ld + c] = acc;
+}
+
+// Other rows: A_r -= A_rQ W on columns right of the panel, and their panel entries 0;
+// the pivot rows' panel entries become unit vectors.  Block (row r, slab of 128 columns from c0).
+__global__ void __launch_bounds__(128) k_gj_rows(double* __restrict__ A, int n, int c0, GjWork w) {
+    pdl_entry();
+    __shared__ double m[GJ_B];
+    __shared__ int piv_t;
+    const int ld = 2 * n, r = blockIdx.x;
+    const int c = c0 + blockIdx.y * 128 + threadIdx.x;
+    if (threadIdx.x == 0) {
+        int pt = -1;
+        for (int t = 0; t < GJ_B; ++t)
+            if (w.prow[t] == r) pt = t;
+        piv_t = pt;
     }
-    launch_pdl(k_gauss_jordan, 1, 1024, sizeof(double) * n, s, Aug, n, info, piv);
+    if (threadIdx.x < GJ_B) m[threadIdx.x] = w.Q0[(size_t)r * GJ_B + threadIdx.x];
+    __syncthreads();
+    if (c >= ld) return;
+    const int pt = piv_t;
+    if (c < c0 + GJ_B) {
+        A[(size_t)r * ld + c] = (pt >= 0 && c - c0 == pt) ? 1.0 : 0.0;
+        return;
+    }
+    if (pt >= 0) return;   // pivot rows: written by k_gj_w
+    double acc = A[(size_t)r * ld + c];
+#pragma unroll
+    for (int u = 0; u < GJ_B; ++u) acc -= m[u] * w.W[(size_t)u * ld + c];
+    A[(size_t)r * ld + c] = acc;
+}
+
+void launch_gauss_jordan(double* Aug, int n, int* info, int* piv, void* work, cudaStream_t s) {
+    const GjWork w = gj_work(work, n);
+    const size_t smem = sizeof(float) * ((size_t)n * GJ_B + n) + sizeof(int) * (size_t)n;
+    cudaFuncSetAttribute(k_gj_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int ld = 2 * n;
+    for (int c0 = 0; c0 < n; c0 += GJ_B) {
+        launch_pdl(k_gj_panel, 1, 512, smem, s, (const double*)Aug, n, c0, w, piv, info);
+        const int R = ld - c0 - GJ_B;
+        launch_pdl(k_gj_w, dim3((R + 15) / 16), dim3(16, GJ_B), 0, s, Aug, n, c0, w);
+        launch_pdl(k_gj_rows, dim3(n, (ld - c0 + 127) / 128), dim3(128), 0, s, Aug, n, c0, w);
+    }
 }
 
 // Pinv = (L0 + Z Z^T)^{-1} - Z Z^T, the pseudo-inverse of the symmetric L0 whose kernel is span Z;

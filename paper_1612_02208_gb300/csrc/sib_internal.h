@@ -225,7 +225,9 @@ void launch_scale(double* x, const double* num_den, int idx, int64_t n, cudaStre
 void launch_block_means(const double* x, int N, int nblocks_vec, double* partials, int nblk, cudaStream_t s);
 void launch_subtract_means(double* x, int N, const double* partials, int nblk, int mask, cudaStream_t s);
 void launch_assemble_L0(int N0, double rho, double mu, double dt, const double* B, double* Aug, cudaStream_t s);
-void launch_gauss_jordan(double* Aug, int n, int* info, int* piv, cudaStream_t s);
+// blocked Gauss-Jordan inversion (n a multiple of 16); work: gauss_jordan_work_bytes(n) bytes
+size_t gauss_jordan_work_bytes(int n);
+void launch_gauss_jordan(double* Aug, int n, int* info, int* piv, void* work, cudaStream_t s);
 void launch_extract_pinv(const double* Aug, const int* piv, int n, int N0, double rho, double* Pinv, cudaStream_t s);
 template <typename T> void launch_coarse_apply(const double* Pinv, int n, const T* b, T* x, cudaStream_t s);
 void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t s);

@@ -80,6 +80,7 @@ struct sib_ctx {
     double setup_ms = 0.0;
     std::vector<void*> allocs;
     cudaStream_t cap = nullptr;
+    void* gjWork = nullptr;              // work arrays of the blocked Gauss-Jordan inversion
     cudaStream_t aux = nullptr;          // set-up work that runs beside the main stream
     cudaEvent_t evFork = nullptr, evJoin = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -844,7 +845,7 @@ void setup(sib_ctx* c, cudaStream_t s) {
         KL(c, launch_assemble_L0(c->L[0].N, c->rho, c->mu, c->dt, c->B0, c->Aug, s));
         CK(cudaEventRecord(c->evFork, s));
         CK(cudaStreamWaitEvent(c->aux, c->evFork, 0));
-        KL(c, launch_gauss_jordan(c->Aug, n, c->info, c->piv, c->aux));
+        KL(c, launch_gauss_jordan(c->Aug, n, c->info, c->piv, c->gjWork, c->aux));
         KL(c, launch_extract_pinv(c->Aug, c->piv, n, c->L[0].N, c->rho, c->Pinv, c->aux));
         CK(cudaEventRecord(c->evJoin, c->aux));
     }
@@ -1426,6 +1427,7 @@ int sib_create(sib_ctx** out, int N, int n_min) {
         c->Pinv = (double*)dalloc(c, sizeof(double) * (size_t)c->n0 * c->n0);
         c->info = (int*)dalloc(c, sizeof(int));
         c->piv = (int*)dalloc(c, sizeof(int) * c->n0);
+        c->gjWork = dalloc(c, gauss_jordan_work_bytes(c->n0));
         c->flag = (int*)dalloc(c, sizeof(int));
         const size_t n3 = 3 * (size_t)N * N;
         c->rhs = (double*)dalloc(c, sizeof(double) * n3);
