@@ -161,6 +161,15 @@ int sib_vcycle(sib_ctx* ctx, int prec, const void* b, void* z, void* stream);
  * (F: 2M doubles, f: 2N^2), FP64. */
 int sib_interp(sib_ctx* ctx, const double* u, double* U, void* stream);
 int sib_spread(sib_ctx* ctx, const double* F, double* f, void* stream);
+/* Structure update of the semi-implicit time step (Sec. 2.2, Eq. imp-X-new):
+ * X_next = X^n + dt J^n u^{n+1}.  w: 3N^2 device doubles, the solution [u | v | p] of the step (only
+ * u, v are read); J^n is the interpolation at the context's current markers X^n (the lagged
+ * configuration the solve used) and dt the context's.  X_next: M x 2 interleaved device doubles,
+ * caller-owned (it may not alias the context's own copy of X, which stays X^n until the next
+ * sib_set_structure).  Positions are not wrapped into the unit square; the periodic stencils accept
+ * any position.  Requires sib_setup since the last change of structure.  A time loop sets X_next as
+ * the next structure, sets up and solves again. */
+int sib_advance_markers(sib_ctx* ctx, const double* w, double* X_next, void* stream);
 
 /* ---- measurement ----------------------------------------------------------------------------- */
 #define SIB_KERNEL_VANKA     0   /* one additive Vanka sweep kernel (residual + patch solves + update) */

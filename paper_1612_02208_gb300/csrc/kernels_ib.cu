@@ -940,6 +940,21 @@ void launch_interleave(const double* in, int M, double* out, cudaStream_t s) {
     launch_pdl(k_interleave, (M + 255) / 256, 256, 0, s, in, M, out);
 }
 
+// Structure update of the semi-implicit scheme (Eq. imp-X-new): X^{n+1} = X^n + dt J^n u^{n+1}, with
+// U = J^n u^{n+1} component-major [x (M) | y (M)] and X, X^{n+1} interleaved (M x 2).
+__global__ void k_advance_markers(const double* __restrict__ X, const double* __restrict__ U, int M, double dt,
+                                  double* __restrict__ Xn) {
+    pdl_entry();
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    Xn[2 * m] = X[2 * m] + dt * U[m];
+    Xn[2 * m + 1] = X[2 * m + 1] + dt * U[M + m];
+}
+void launch_advance_markers(const double* X, const double* U, int M, double dt, double* Xn, cudaStream_t s) {
+    if (M == 0) return;
+    launch_pdl(k_advance_markers, (M + 255) / 256, 256, 0, s, X, U, M, dt, Xn);
+}
+
 // Deterministic start vector of the power iterations: Knuth's multiplicative hash of k+1,
 // (k+1) * 2654435761 mod 2^32, mapped to [-1/2, 1/2).
 __global__ void k_hash_vector(double* __restrict__ x, int64_t n) {

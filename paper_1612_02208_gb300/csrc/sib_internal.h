@@ -198,6 +198,7 @@ void launch_ib_window(const T* win, const int* tiles, const int* nTiles, int max
                       const T* u, T* f, cudaStream_t s);
 void launch_deinterleave(const double* in, int M, double* out, cudaStream_t s);
 void launch_interleave(const double* in, int M, double* out, cudaStream_t s);
+void launch_advance_markers(const double* X, const double* U, int M, double dt, double* Xn, cudaStream_t s);
 void launch_hash_vector(double* x, int64_t n, cudaStream_t s);
 void launch_grad_kappa(const int* edges, int E, int M, const double* Lam, const double* Y, double* dkappa,
                        cudaStream_t s);

@@ -1780,6 +1780,20 @@ int sib_interp(sib_ctx* c, const double* u, double* U, void* stream) {
     API_END(c)
 }
 
+int sib_advance_markers(sib_ctx* c, const double* w, double* X_next, void* stream) {
+    API_BEGIN(c)
+    require_setup(c);
+    if (!w || (c->M && !X_next)) throw SibError(SIB_ERR_ARG, "null pointer");
+    if (c->M == 0) return SIB_OK;
+    cudaStream_t s = S(stream);
+    IBK<double> k = ibk<double>(c, c->lmax);
+    KL(c, launch_interp<double>(k, w, (double*)c->U[0], s));   // J^n u^{n+1} at the lagged configuration
+    KL(c, launch_advance_markers(c->X, (const double*)c->U[0], c->M, c->dt, X_next, s));
+    kcheck(c);
+    return SIB_OK;
+    API_END(c)
+}
+
 int sib_spread(sib_ctx* c, const double* F, double* f, void* stream) {
     API_BEGIN(c)
     require_setup(c);

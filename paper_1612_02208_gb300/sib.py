@@ -38,7 +38,7 @@ EXPORTS = [
     "sib_solve", "sib_solve_host", "sib_solve_rhs", "sib_grad", "sib_num_levels", "sib_level_size",
     "sib_apply_operator", "sib_apply_ib", "sib_smooth", "sib_residual_restrict", "sib_prolong_add",
     "sib_coarse_solve", "sib_vcycle", "sib_interp", "sib_spread", "sib_time_kernel", "sib_launch_count",
-    "sib_device_bytes", "sib_spread_noalloc",
+    "sib_device_bytes", "sib_spread_noalloc", "sib_advance_markers",
 ]
 KERNELS = {"vanka": 0, "residual": 1, "spread": 2, "interp": 3, "restrict": 4, "prolong": 5}
 
@@ -124,6 +124,7 @@ def load(build_if_missing: bool = True):
         "sib_spread": (I, [ctx, P, P, P]),
         "sib_time_kernel": (I, [ctx, I, I, I, I, P, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "sib_launch_count": (ctypes.c_int64, [ctx]),
+        "sib_advance_markers": (I, [ctx, P, P, P]),
         "sib_device_bytes": (ctypes.c_int64, [ctx]),
         "sib_spread_noalloc": (I, [I, I, P, P, P, P]),
     }
@@ -320,6 +321,13 @@ class Solver:
         self._check(self.lib.sib_interp(self.ctx, _ptr(u), _ptr(U) if self.M else None, _stream()))
         return U
 
+    def advance_markers(self, w):
+        """X^{n+1} = X^n + dt J^n u^{n+1} for the solution w of the step (Eq. imp-X-new)."""
+        torch = _torch()
+        Xn = torch.empty((max(self.M, 1), 2), dtype=torch.float64, device=w.device)[: self.M]
+        self._check(self.lib.sib_advance_markers(self.ctx, _ptr(w), _ptr(Xn) if self.M else None, _stream()))
+        return Xn
+
     def spread(self, F):
         torch = _torch()
         f = torch.empty(2 * self.N * self.N, dtype=torch.float64, device=F.device)
@@ -341,6 +349,23 @@ class Solver:
     @property
     def device_bytes(self):
         return int(self.lib.sib_device_bytes(self.ctx))
+
+
+def time_loop(solver, g, X, edges, kappa, steps):
+    """`steps` semi-implicit time steps (Sec. 2.2): set the structure X^n, set up, solve
+    L_IB(X^n) w = (g + S K X^n, 0) and move the markers, X^{n+1} = X^n + dt J^n u^{n+1}
+    (Eq. imp-X-new).  g is the full momentum right-hand side of every step (steady forcing; with
+    rho > 0 a caller that wants the (rho/dt) u^n term puts it into g).  Every step runs in the
+    library; this only sequences its calls.  Returns [w^1 ..], [X^0, X^1 ..] (device tensors)."""
+    ws, Xs = [], [X]
+    for _ in range(steps):
+        solver.set_structure(X, edges, kappa)
+        solver.setup()
+        w = solver.solve(g)
+        X = solver.advance_markers(w)
+        ws.append(w)
+        Xs.append(X)
+    return ws, Xs
 
 
 def solver_for(problem, device="cuda", **opts):

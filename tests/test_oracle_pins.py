@@ -447,3 +447,18 @@ def test_iteration_trends():
         p.rho, p.mu = 1.0, mu
         its_re.append(_iters(p))
     assert all(a <= b for a, b in zip(its_re, its_re[1:])), its_re
+
+
+def test_time_loop_matches_chained_full_system_solves():
+    """Two semi-implicit steps (Eq. imp-X-new after each eliminated solve) give the same u, p and X
+    as solving the full (u, p, X^{n+1}) system of Eq. system-impib twice, each time at the new X."""
+    from oracle import timestep
+    prob = I.disk_stokes(16, kappa=30.0)
+    ws, Xs = timestep.run(prob, 2)
+    p = prob
+    for k in range(2):
+        w3, X3 = system.solve_full_system(p)
+        np.testing.assert_allclose(system.project(w3, 16, 0.0), ws[k], atol=1e-10 * np.abs(ws[k]).max())
+        np.testing.assert_allclose(X3, Xs[k + 1], atol=1e-12)
+        p = timestep.with_positions(p, X3)
+    assert np.abs(Xs[2] - Xs[0]).max() > 1e-6      # the structure moved
