@@ -77,6 +77,9 @@ typedef struct {
     int    use_graphs;    /* 1: replay the V-cycle as a CUDA graph (1)                               */
     int    fuse_small;    /* 1: levels 1 and 0 of the V-cycle run as one single-block kernel when
                              level 1 (at most 16 x 16) fits in shared memory; 0: one kernel per step (1) */
+    int    smooth_krylov; /* 1: every pre- and post-smoothing stage of nu sweeps is nu iterations of
+                             flexible GMRES on the level's residual equation, each preconditioned by
+                             one undamped basic sweep (Sec. 3.3; nu <= 8); 0: nu damped sweeps (0)    */
 } sib_opts;
 
 typedef struct {

@@ -37,14 +37,17 @@ class Level:
 
 class Hierarchy:
     def __init__(self, prob, n_min=8, smoother="vanka", omega=None, nu1=2, nu2=2,
-                 cheb_iters=2, cheb_lo=0.1, cheb_hi=1.1, power_iters=10, lam_override=None):
+                 cheb_iters=2, cheb_lo=0.1, cheb_hi=1.1, power_iters=10, lam_override=None, krylov=False):
         N = prob.N
         if N < n_min or (N // n_min) * n_min != N or (N // n_min) & (N // n_min - 1):
             raise ValueError("N must be n_min * 2^k")
         self.prob = prob
         self.rho, self.mu, self.dt = prob.rho, prob.mu, prob.dt
         self.smoother = smoother
-        self.omega = (0.8 if smoother == "vanka" else 1.0) if omega is None else omega
+        # krylov: each smoothing stage is FGMRES(nu) preconditioned by one undamped basic sweep
+        # (Sec. 3.3); otherwise nu damped sweeps
+        self.krylov = krylov
+        self.omega = 1.0 if krylov else ((0.8 if smoother == "vanka" else 1.0) if omega is None else omega)
         self.nu1, self.nu2 = nu1, nu2
         self.cheb_iters, self.cheb_lo, self.cheb_hi = cheb_iters, cheb_lo, cheb_hi
         self.power_iters = power_iters
@@ -89,8 +92,20 @@ class Hierarchy:
     def fine(self):
         return self.levels[-1]
 
+    def basic(self, l, x, b):
+        """One sweep of the basic smoother with the hierarchy's damping."""
+        lev = self.levels[l]
+        if self.smoother == "vanka":
+            return smoothers.vanka_sweep(lev.L, lev.dofs, lev.patches, x, b, self.omega)
+        return smoothers.sc_sweep(lev.L, lev.G, lev.D, lev.AIB, lev.dA, lev.dM, lev.lamA, lev.lamM,
+                                  x, b, self.omega, self.cheb_iters, self.cheb_lo, self.cheb_hi)
+
     def smooth(self, l, x, b, sweeps):
         lev = self.levels[l]
+        if self.krylov:
+            if sweeps == 0:
+                return x
+            return smoothers.fgmres_smooth(lev.L, lambda v: self.basic(l, np.zeros_like(v), v), x, b, sweeps)
         for _ in range(sweeps):
             if self.smoother == "vanka":
                 x = smoothers.vanka_sweep(lev.L, lev.dofs, lev.patches, x, b, self.omega)

@@ -121,3 +121,38 @@ def sc_sweep(L, G, D, AIB, dA, dM, lamA, lamM, x, b, omega, cheb_iters, lo=0.1, 
 
     r = b - L @ x
     return x + omega * sc_apply(r, nu, Ainv, Minv, G, D)
+
+
+def fgmres_smooth(L, B, x, b, k):
+    """The paper's smoothing step (Sec. 3.3): k iterations of flexible GMRES on the residual
+    equation L e = b - L x, preconditioned by the basic smoother B (B(v): one undamped sweep on
+    right-hand side v from a zero guess), then x + e.  Classical Gram-Schmidt applied twice; the
+    iterations stop early when the new Arnoldi vector vanishes.  k = the number of sweeps the
+    damped form would take, so both apply B the same number of times."""
+    r = b - L @ x
+    beta = np.linalg.norm(r)
+    if beta == 0.0:
+        return x.copy()
+    n = r.size
+    V = np.zeros((n, k + 1))
+    Z = np.zeros((n, k))
+    H = np.zeros((k + 1, k))
+    V[:, 0] = r / beta
+    m = 0
+    for j in range(k):
+        Z[:, j] = B(V[:, j])
+        w = L @ Z[:, j]
+        h = V[:, :j + 1].T @ w
+        w = w - V[:, :j + 1] @ h
+        h2 = V[:, :j + 1].T @ w
+        w = w - V[:, :j + 1] @ h2
+        H[:j + 1, j] = h + h2
+        H[j + 1, j] = np.linalg.norm(w)
+        m = j + 1
+        if H[j + 1, j] == 0.0:
+            break
+        V[:, j + 1] = w / H[j + 1, j]
+    rhs = np.zeros(m + 1)
+    rhs[0] = beta
+    y = np.linalg.lstsq(H[:m + 1, :m], rhs, rcond=None)[0]
+    return x + Z[:, :m] @ y

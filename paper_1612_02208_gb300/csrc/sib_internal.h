@@ -158,6 +158,18 @@ template <typename T> size_t vcycle_small_smem(int N1, int n0, int nTiles, int p
 template <typename T> int vcycle_small_cluster(size_t smem);
 template <typename T> cudaError_t launch_vcycle_small(const SmallArgs<T>& a, size_t smem, cudaStream_t s);
 
+// launchers (kernels_wrap.cu): the Krylov-wrapped smoothing step
+constexpr int WRAP_MAXK = 8;     // at most this many FGMRES iterations a smoothing stage
+constexpr int WRAP_BLK = 128;    // blocks of the partial inner products
+template <typename T> void launch_wdots(const T* V, int64_t ld, int cnt, const T* w, int64_t n, double* partials,
+                                        cudaStream_t s);
+void launch_wreduce(const double* partials, int cnt, double* out, cudaStream_t s);
+template <typename T> void launch_wmaxpy(const T* V, int64_t ld, int cnt, const double* coef, double sign, const T* yin,
+                                         T* yout, int64_t n, cudaStream_t s);
+template <typename T> void launch_wscale(const T* w, const double* nrm2, T* v, int64_t n, cudaStream_t s);
+void launch_wlsq(const double* hA, const double* hB, const double* nr, const double* beta2, int k, double* y,
+                 cudaStream_t s);
+
 // launchers (kernels_ib.cu)
 void launch_stencils(const double* X, int M, int Nf, int lmax, int** base, double** w64, float** w32,
                      cudaStream_t s);

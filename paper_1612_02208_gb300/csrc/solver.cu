@@ -46,6 +46,12 @@ struct LevelBuf {
     void* tv[8] = {};
     void* tp[6] = {};
     void* dinv = nullptr;   // 3 n: SC diagonals
+    // Krylov-wrapped smoothing: WRAP_MAXK + 1 Arnoldi vectors, WRAP_MAXK preconditioned ones, a work
+    // vector (3 n each) and the step's small FP64 arrays
+    void* wV = nullptr;
+    void* wZ = nullptr;
+    void* ww = nullptr;
+    double* wsmall = nullptr;
 };
 
 struct Level {
@@ -365,11 +371,12 @@ Cheb2<T> cheb2(double lam, double lo, double hi) {
 // fused sweep for two Chebyshev iterations per inner solve (6 kernels, plus IB passes on levels
 // that use the marker path)
 template <typename T>
-void sc_sweep_fused(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream_t s) {
+void sc_sweep_fused(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream_t s, double omega = -1.0) {
     Level& lv = c->L[l];
     const int pi = Prec<T>::id;
     const int64_t nv = 2LL * lv.N * lv.N;
     GridK<T> g = gridk<T>(c, l);
+    if (omega >= 0.0) g.omega = (T)omega;
     const Cheb2<T> ka = cheb2<T>(lv.lamA, c->opts.cheb_lo, c->opts.cheb_hi);
     const Cheb2<T> km = cheb2<T>(lv.lamM, c->opts.cheb_lo, c->opts.cheb_hi);
     T* r = (T*)lv.p[pi].r;
@@ -483,15 +490,85 @@ T* vcycle_small(sib_ctx* c, cudaStream_t s) {
     return (T*)lv.p[pi].x;
 }
 
+// Krylov-wrapped smoothing step (Sec. 3.3): xo = x + e, e from k iterations of flexible GMRES on
+// L e = b - L x (CGS2), each preconditioned by one undamped sweep of the basic smoother from zero;
+// x == nullptr: zero start.  The Hessenberg least-squares problem is solved on the device.
+template <typename T>
+void wrapped_smooth(sib_ctx* c, int l, const T* x, const T* b, T* xo, int k, cudaStream_t s) {
+    Level& lv = c->L[l];
+    const int pi = Prec<T>::id;
+    LevelBuf& lb = lv.p[pi];
+    const int64_t n3 = 3LL * lv.N * lv.N;
+    const int K1 = WRAP_MAXK + 1;
+    T* V = (T*)lb.wV;
+    T* Z = (T*)lb.wZ;
+    T* w = (T*)lb.ww;
+    double* hA = lb.wsmall;
+    double* hB = hA + K1 * WRAP_MAXK;
+    double* nr = hB + K1 * WRAP_MAXK;
+    double* beta2 = nr + WRAP_MAXK;
+    double* y = beta2 + 1;
+    double* part = y + WRAP_MAXK;
+    auto dots = [&](const T* Vs, int cnt, const T* v, double* out) {
+        KL(c, launch_wdots<T>(Vs, n3, cnt, v, n3, part, s));
+        KL(c, launch_wreduce(part, cnt, out, s));
+    };
+    const T* r0 = b;
+    if (x) {
+        apply_operator<T>(c, l, x, b, w, s);   // r = b - L x
+        r0 = w;
+    }
+    dots(r0, 1, r0, beta2);
+    KL(c, launch_wscale<T>(r0, beta2, V, n3, s));
+    GridK<T> g = gridk<T>(c, l);
+    g.omega = T(1);   // the basic smoother undamped
+    for (int j = 0; j < k; ++j) {
+        T* Vj = V + (size_t)j * n3;
+        T* Zj = Z + (size_t)j * n3;
+        if (c->opts.smoother == SIB_SMOOTHER_SC)
+            sc_sweep_fused<T>(c, l, nullptr, Vj, Zj, s, 1.0);
+        else
+            KL(c, launch_vanka_zero<T>(g, Vj, Zj, s));
+        ib_apply<T>(c, l, Zj, s);
+        KL(c, launch_residual<T>(gridk<T>(c, l), Zj, nullptr, w, s));   // w = L z_j
+        dots(V, j + 1, w, hA + j * K1);
+        KL(c, launch_wmaxpy<T>(V, n3, j + 1, hA + j * K1, -1.0, w, w, n3, s));
+        dots(V, j + 1, w, hB + j * K1);
+        KL(c, launch_wmaxpy<T>(V, n3, j + 1, hB + j * K1, -1.0, w, w, n3, s));
+        dots(w, 1, w, nr + j);
+        if (j + 1 < k) KL(c, launch_wscale<T>(w, nr + j, V + (size_t)(j + 1) * n3, n3, s));
+    }
+    KL(c, launch_wlsq(hA, hB, nr, beta2, k, y, s));
+    KL(c, launch_wmaxpy<T>(Z, n3, k, y, 1.0, x, xo, n3, s));
+}
+
 // Alg. 1 on level l with right-hand side in the level's b; returns the buffer holding w.
 template <typename T>
 T* vcycle_level(sib_ctx* c, int l, cudaStream_t s) {
     Level& lv = c->L[l];
     const int pi = Prec<T>::id;
-    if (l == 1 && small_ok<T>(c)) return vcycle_small<T>(c, s);
+    if (l == 1 && !c->opts.smooth_krylov && small_ok<T>(c)) return vcycle_small<T>(c, s);
     if (l == 0) {
         KL(c, launch_coarse_apply<T>(c->Pinv, c->n0, (const T*)lv.p[pi].b, (T*)lv.p[pi].x, s));
         return (T*)lv.p[pi].x;
+    }
+    if (c->opts.smooth_krylov) {   // each smoothing stage: FGMRES(nu) preconditioned by the basic sweep
+        T* x = (T*)lv.p[pi].x;
+        T* xt = (T*)lv.p[pi].xt;
+        const T* b = (const T*)lv.p[pi].b;
+        if (c->opts.nu1 > 0)
+            wrapped_smooth<T>(c, l, (const T*)nullptr, b, x, c->opts.nu1, s);
+        else
+            CK(cudaMemsetAsync(x, 0, sizeof(T) * 3 * (size_t)lv.N * lv.N, s));
+        ib_apply<T>(c, l, x, s);
+        KL(c, launch_residual_restrict<T>(gridk<T>(c, l), x, b, (T*)c->L[l - 1].p[pi].b, s));
+        T* ec = vcycle_level<T>(c, l - 1, s);
+        KL(c, launch_prolong_add<T>(c->L[l - 1].N, ec, x, s));
+        if (c->opts.nu2 > 0) {
+            wrapped_smooth<T>(c, l, (const T*)x, b, xt, c->opts.nu2, s);
+            std::swap(x, xt);
+        }
+        return x;
     }
     const int64_t n3 = 3LL * lv.N * lv.N;
     T* x = (T*)lv.p[pi].x;
@@ -575,6 +652,25 @@ void alloc_level_bufs(sib_ctx* c) {
         lv.nTiles = (int*)dalloc(c, sizeof(int));
         lv.binStart[0] = (int*)dalloc(c, sizeof(int) * (n + 1));
         lv.binStart[1] = (int*)dalloc(c, sizeof(int) * (n + 1));
+    }
+}
+
+// Krylov-wrapped smoothing buffers of every level >= 1, both precisions (once; WRAP_MAXK-sized)
+void alloc_wrap_bufs(sib_ctx* c) {
+    for (int l = 1; l <= c->lmax; ++l) {
+        Level& lv = c->L[l];
+        const size_t n3 = 3 * (size_t)lv.N * lv.N;
+        for (int pi = 0; pi < 2; ++pi) {
+            const size_t e = pi == 0 ? 8 : 4;
+            LevelBuf& b = lv.p[pi];
+            if (b.wV) continue;
+            b.wV = dalloc(c, e * n3 * (WRAP_MAXK + 1));
+            b.wZ = dalloc(c, e * n3 * WRAP_MAXK);
+            b.ww = dalloc(c, e * n3);
+            const size_t small = 2 * (size_t)(WRAP_MAXK + 1) * WRAP_MAXK + WRAP_MAXK + 1 + WRAP_MAXK +
+                                 (size_t)(WRAP_MAXK + 1) * WRAP_BLK;
+            b.wsmall = (double*)dalloc(c, sizeof(double) * small);
+        }
     }
 }
 
@@ -1255,9 +1351,16 @@ void smooth_impl(sib_ctx* c, int l, T* x, const T* b, int sweeps, cudaStream_t s
     T* xa = (T*)lv.p[pi].x;
     T* xb = (T*)lv.p[pi].xt;
     CK(cudaMemcpyAsync(xa, x, sizeof(T) * n3, cudaMemcpyDeviceToDevice, s));
-    for (int k = 0; k < sweeps; ++k) {
-        sweep<T>(c, l, xa, b, xb, s);
-        std::swap(xa, xb);
+    if (c->opts.smooth_krylov) {
+        if (sweeps > 0) {
+            wrapped_smooth<T>(c, l, (const T*)xa, b, xb, sweeps, s);
+            std::swap(xa, xb);
+        }
+    } else {
+        for (int k = 0; k < sweeps; ++k) {
+            sweep<T>(c, l, xa, b, xb, s);
+            std::swap(xa, xb);
+        }
     }
     CK(cudaMemcpyAsync(x, xa, sizeof(T) * n3, cudaMemcpyDeviceToDevice, s));
 }
@@ -1375,6 +1478,7 @@ void sib_default_opts(sib_opts* o) {
     o->add_SKXn = 1;
     o->use_graphs = 1;
     o->fuse_small = 1;
+    o->smooth_krylov = 0;
 }
 
 static void resolve_opts(sib_opts* o) {
@@ -1546,11 +1650,13 @@ int sib_set_options(sib_ctx* c, const sib_opts* o) {
     if ((n.smoother != SIB_SMOOTHER_VANKA && n.smoother != SIB_SMOOTHER_SC) || n.nu1 < 0 || n.nu2 < 0 ||
         n.nu1 + n.nu2 > 64 || n.cheb_iters < 1 || n.cheb_iters > 16 || !(n.cheb_lo > 0) || !(n.cheb_hi > n.cheb_lo) ||
         n.power_iters < 1 || n.power_iters > 1000 || !(n.rtol >= 0) || n.max_it < 1 || n.max_it > 100000 ||
-        n.restart < 1 || n.restart > 100 || (n.fuse_small != 0 && n.fuse_small != 1))
+        n.restart < 1 || n.restart > 100 || (n.fuse_small != 0 && n.fuse_small != 1) ||
+        (n.smooth_krylov != 0 && n.smooth_krylov != 1) || (n.smooth_krylov && (n.nu1 > WRAP_MAXK || n.nu2 > WRAP_MAXK)))
         throw SibError(SIB_ERR_ARG, "option out of range");
     resolve_opts(&n);
     const bool smootherChanged = n.smoother != c->opts.smoother;
     c->opts = n;
+    if (n.smooth_krylov) alloc_wrap_bufs(c);
     if (smootherChanged && n.smoother == SIB_SMOOTHER_SC) c->fluidDirty = true;   // needs eigen estimates
     invalidate_graphs(c);
     return SIB_OK;

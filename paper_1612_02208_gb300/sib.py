@@ -49,7 +49,7 @@ class SibOpts(ctypes.Structure):
         ("cheb_iters", ctypes.c_int), ("cheb_lo", ctypes.c_double), ("cheb_hi", ctypes.c_double),
         ("power_iters", ctypes.c_int), ("vcycle_fp32", ctypes.c_int), ("rtol", ctypes.c_double),
         ("max_it", ctypes.c_int), ("restart", ctypes.c_int), ("add_SKXn", ctypes.c_int), ("use_graphs", ctypes.c_int),
-        ("fuse_small", ctypes.c_int),
+        ("fuse_small", ctypes.c_int), ("smooth_krylov", ctypes.c_int),
     ]
 
 

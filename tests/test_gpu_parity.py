@@ -271,6 +271,64 @@ def test_gradients_match_oracle(add):
     assert rel(host(dX), dX_ref) < 1e-9, rel(host(dX), dX_ref)
 
 
+# ------------------------------------------------------------------ Krylov-wrapped smoothing
+def _wrapped_pair(name, smoother, **opts):
+    """Oracle hierarchy and solver with every smoothing stage as FGMRES(nu) preconditioned by one
+    undamped basic sweep (Sec. 3.3)."""
+    prob = PROBLEMS[name]()
+    H = multigrid.Hierarchy(prob, smoother=smoother, krylov=True)
+    S = sib.solver_for(prob, smoother=sib.SMOOTHER_SC if smoother == "sc" else sib.SMOOTHER_VANKA,
+                       smooth_krylov=1, **opts)
+    if smoother == "sc":
+        S.set_eigen_estimates([0.0] + [lv.lamA for lv in H.levels[1:]], [0.0] + [lv.lamM for lv in H.levels[1:]])
+        S.setup()
+    return prob, H, S
+
+
+@pytest.mark.parametrize("name,smoother", [("disk64_stiff", "vanka"), ("ellipse64_re", "vanka"),
+                                           ("disk64_stiff", "sc"), ("seam32", "sc")])
+def test_wrapped_smoothing_step_every_level(name, smoother):
+    """One wrapped smoothing stage (k = 1, 2, 3 FGMRES iterations) on every level matches the
+    oracle's, from a random iterate and from zero."""
+    prob, H, S = _wrapped_pair(name, smoother)
+    for l in range(1, len(H.levels)):
+        lev = H.levels[l]
+        for k in (1, 2, 3):
+            x = rand(3 * lev.n, 1000 + 10 * l + k) if k != 2 else np.zeros(3 * lev.n)
+            b = rand(3 * lev.n, 2000 + 10 * l + k, 10.0)
+            ref = H.smooth(l, x, b, k)
+            y = cu(x.copy())
+            S.smooth(l, y, cu(b), k)
+            assert rel(host(y), ref) < TOL64, (l, k, rel(host(y), ref))
+            x32 = x.astype(np.float32).astype(np.float64)
+            b32 = b.astype(np.float32).astype(np.float64)
+            ref32 = H.smooth(l, x32, b32, k)
+            y32 = cu(x32, torch.float32)
+            S.smooth(l, y32, cu(b32, torch.float32), k)
+            assert rel(host(y32), ref32) < 1e-4, (l, k, rel(host(y32), ref32))
+
+
+@pytest.mark.parametrize("name,smoother", [("disk64_stiff", "vanka"), ("disk64_stiff", "sc"), ("seam32", "sc")])
+def test_wrapped_vcycle_and_fgmres_iterations(name, smoother):
+    """The V-cycle with wrapped smoothing matches the oracle's (FP64 1e-10, FP32 1e-4), and FGMRES
+    preconditioned by it converges in the oracle's number of iterations (FP64 V-cycle)."""
+    prob, H, S = _wrapped_pair(name, smoother)
+    b = system.rhs(prob)
+    assert rel(host(S.vcycle(cu(b))), H.vcycle(b)) < TOL64
+    b32 = b.astype(np.float32).astype(np.float64)
+    assert rel(host(S.vcycle(cu(b32, torch.float32))), H.vcycle(b32)) < 1e-4
+    L = system.operator_of(prob)
+    _, its_ref, _, conv = krylov.fgmres(lambda z: L @ z, H.vcycle, b, rtol=1e-8, max_it=100, restart=100,
+                                        project=lambda v: system.project(v, prob.N, prob.rho))
+    assert conv
+    S.set_options(vcycle_fp32=0, rtol=1e-8)
+    S.solve(cu(prob.g))
+    assert S.stats.iterations == its_ref, (S.stats.iterations, its_ref)
+    S.set_options(vcycle_fp32=1)
+    S.solve(cu(prob.g))
+    assert abs(S.stats.iterations - its_ref) <= 1, (S.stats.iterations, its_ref)
+
+
 # ------------------------------------------------------------------ full-size configurations
 @pytest.mark.parametrize("maker,smoother", [(lambda: I.disk_stokes(128, kappa=1e2), "vanka"),
                                             (lambda: I.disk_stokes(128, kappa=1e2), "sc"),
