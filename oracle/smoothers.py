@@ -12,8 +12,8 @@ Schur-complement smoother (Eqs. fact-Stokes-IB and approx-fact-Stokes-IB):
 At^{-1}: a fixed number of Chebyshev iterations on A_IB with point (Jacobi) preconditioning;
 Mt^{-1}: a fixed number of Chebyshev iterations on D At^{-1} G preconditioned by the diagonal of
 the sparse approximate Schur complement Mh = D diag(A_IB)^{-1} G.  The paper relaxes with
-Gauss-Seidel; this build uses the diagonal (Jacobi) point relaxation so that every level is
-one parallel pass (a reading recorded with the design notes).
+Gauss-Seidel; here the diagonal (Jacobi) point relaxation is used instead, so that every level is
+one parallel pass.
 
 Chebyshev acceleration follows the textbook recurrence (Saad, Iterative Methods for Sparse
 Linear Systems, Algorithm 12.1) with x_0 = 0 on the interval [lo, hi] * lambda_max, where

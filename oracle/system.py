@@ -5,7 +5,7 @@ Eliminated system (Eq. matrix-impib):
     L_IB = [[A - dt S K J, G], [-D, 0]],   right-hand side (g + S K X^n, 0).
 With S = J^T/h^2, K symmetric and -D = G^T, L_IB is symmetric (indefinite).
 
-Periodic-domain reading (the paper's tests use Dirichlet cavity walls; this build's problems are
+Periodic-domain reading (the paper's tests use Dirichlet cavity walls; the problems here are
 periodic).  The kernel of L_IB is spanned by the constant pressure and, when rho = 0, by the two
 constant velocity components (J maps constants to constants and K annihilates translations).
 The right-hand side is made consistent by removing the mean of each velocity component when
