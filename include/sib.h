@@ -42,7 +42,7 @@ extern "C" {
 
 #define SIB_OK                  0
 #define SIB_ERR_ARG            -1  /* invalid argument (size, null pointer, option out of range)    */
-#define SIB_ERR_CUDA           -2  /* a CUDA runtime call failed                                      */
+#define SIB_ERR_CUDA           -2  /* a CUDA runtime call failed, or a kernel's bounded wait gave up  */
 #define SIB_ERR_NONFINITE      -3  /* a non-finite value in inputs or in the Krylov recurrence        */
 #define SIB_ERR_NOT_CONVERGED  -4  /* max_it reached; outputs and stats are still written             */
 #define SIB_ERR_BREAKDOWN      -5  /* reserved: Arnoldi breakdown that is not a converged solve      */

@@ -31,7 +31,7 @@ def _nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "sib_internal.h"), os.path.join(CSRC, "grid_cells.cuh"), os.path.join(INCLUDE, "sib.h"), os.path.abspath(__file__)]
+    files += [os.path.join(CSRC, "sib_internal.h"), os.path.join(CSRC, "grid_cells.cuh"), os.path.join(CSRC, "tma.cuh"), os.path.join(INCLUDE, "sib.h"), os.path.abspath(__file__)]
     return files
 
 

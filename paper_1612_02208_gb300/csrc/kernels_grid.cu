@@ -4,7 +4,10 @@
 // Layout: a level vector is [u | v | p], each N*N row-major [j][i]; u[j][i] on the x-face
 // (i-1/2, j), v[j][i] on the y-face (i, j-1/2), p[j][i] at the cell centre (Appendix,
 // "Eulerian discretization").  N is a power of two, so periodic wrap is a mask.
+#include <cstring>
+
 #include "grid_cells.cuh"
+#include "tma.cuh"
 
 namespace sib {
 
@@ -170,24 +173,39 @@ VankaBulk<T> vanka_bulk(double a0, double c, double inv_h) {
     return k;
 }
 
+// Shared-memory layout of the tiled sweep.  Staged b: rows j0-1 .. j0+8, staged x: rows j0-2 ..
+// j0+9, both over columns i0-4 .. i0+35 (40 wide, so that the TMA box starts on a 16-byte
+// boundary); the residual overwrites the staged b in place, the patch corrections reuse the x area.
+constexpr int VK_W = TX + 8;                   // staged row width
+constexpr int VK_BR = TY + 2, VK_XR = TY + 4;  // staged rows of b and of x
+constexpr int VK_PX = TX + 1, VK_PY = TY + 1;  // patches: tile plus its left and bottom neighbours
+constexpr int VK_SB = 3 * VK_BR * VK_W;        // 1200 words of b
+constexpr int VK_XOFF = ((VK_SB + 31) / 32) * 32;                       // x area, 128-byte aligned
+constexpr int VK_STAGE = VK_XOFF + (3 * VK_XR * VK_W > 5 * VK_PY * VK_PX ? 3 * VK_XR * VK_W : 5 * VK_PY * VK_PX);
+constexpr int VK_WAIT_LIMIT = 1 << 22;         // bounded wait for the tile copies
+
 template <typename T, bool ZERO>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_vanka_tiled(GridK<T> g, VankaBulk<T> kb, const T* __restrict__ x,
-                                                     const T* __restrict__ b, T* __restrict__ xo) {
-    constexpr int SX = TX + 4, SY = TY + 4;   // staged x: tile plus two cells each side
-    constexpr int RX = TX + 2, RY = TY + 2;   // residuals: tile plus one cell each side
-    constexpr int PX = TX + 1, PY = TY + 1;   // patches: tile plus its left and bottom neighbours
-    __shared__ T xs[3][SY][SX];
-    __shared__ T rs[3][RY][RX];
-    __shared__ T ds[5][PY][PX];
-    __shared__ T bs[6][PY][PX];   // IB entries of the patches of an active tile
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4)
+    k_vanka_tiled(GridK<T> g, VankaBulk<T> kb, const __grid_constant__ CUtensorMap mx,
+                  const __grid_constant__ CUtensorMap mb, int tma, const T* __restrict__ x, const T* __restrict__ b,
+                  T* __restrict__ xo) {
+    __shared__ __align__(128) T stage[VK_STAGE];
+    __shared__ T bs[6][VK_PY][VK_PX];   // IB entries of the patches of an active tile
+    __shared__ uint64_t bar;
+    T(*sb)[VK_BR][VK_W] = reinterpret_cast<T(*)[VK_BR][VK_W]>(stage);
+    T(*sx)[VK_XR][VK_W] = reinterpret_cast<T(*)[VK_XR][VK_W]>(stage + VK_XOFF);
+    T(*ds)[VK_PY][VK_PX] = reinterpret_cast<T(*)[VK_PY][VK_PX]>(stage + VK_XOFF);
     const int N = g.N, n = N * N, m = N - 1;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    // tiles whose staged window lies inside the grid take the TMA copies; the others (the periodic
+    // wrap) and grids without tensor maps gather element by element
+    const bool bulk = tma && i0 >= TX && i0 + 2 * TX <= N && j0 >= TY && j0 + 2 * TY <= N;
     // set-up data (tile flag, patch entries) before the wait for x and b
     const bool act = g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x];
     if (act) {
-        for (int q = tid; q < PY * PX; q += TX * TY) {
-            const int pj = q / PX, pi = q - pj * PX;
+        for (int q = tid; q < VK_PY * VK_PX; q += TX * TY) {
+            const int pj = q / VK_PX, pi = q - pj * VK_PX;
             const int i = (i0 - 1 + pi) & m, j = (j0 - 1 + pj) & m;
             const int cc = j * N + i, ce = j * N + ((i + 1) & m), cn = ((j + 1) & m) * N + i;
             bs[0][pj][pi] = g.ibd[cc];
@@ -198,48 +216,132 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_vanka_tiled(Gri
             bs[5][pj][pi] = g.ibd[3 * n + cc];
         }
     }
+    if (bulk && tid == 0) {
+        tma_prefetch_map(&mb);
+        if (!ZERO) tma_prefetch_map(&mx);
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
     pdl_entry();
-    if (!ZERO) {
-        for (int q = tid; q < SY * SX; q += TX * TY) {
-            const int jj = q / SX, ii = q - jj * SX;
-            const int gc = ((j0 - 2 + jj) & m) * N + ((i0 - 2 + ii) & m);
-            xs[0][jj][ii] = x[gc];
-            xs[1][jj][ii] = x[n + gc];
-            xs[2][jj][ii] = x[2 * n + gc];
+    // residual cells: this thread's own (ri, rj) = (tx + 1, ty + 1) and, for the first
+    // 2 (TX + TY) + 4 threads, one cell of the ring around the tile
+    constexpr int RING = 2 * (TX + 2) + 2 * TY;
+    int ri2 = 0, rj2 = 0;
+    if (tid < TX + 2) {
+        ri2 = tid;
+    } else if (tid < 2 * (TX + 2)) {
+        ri2 = tid - (TX + 2);
+        rj2 = TY + 1;
+    } else if (tid < 2 * (TX + 2) + TY) {
+        rj2 = tid - 2 * (TX + 2) + 1;
+    } else {
+        ri2 = TX + 1;
+        rj2 = tid - 2 * (TX + 2) - TY + 1;
+    }
+    if (bulk) {
+        if (tid == 0) {
+            constexpr uint32_t bb = 3 * VK_BR * VK_W * sizeof(T), bx = 3 * VK_XR * VK_W * sizeof(T);
+            mbar_expect_tx(&bar, ZERO ? bb : bb + bx);
+            tma_load_3d(&sb[0][0][0], &mb, &bar, i0 - 4, j0 - 1, 0);
+            if (!ZERO) tma_load_3d(&sx[0][0][0], &mx, &bar, i0 - 4, j0 - 2, 0);
+        }
+    }
+    // IB term of the residual cells of an active tile, fetched while the tile is in flight
+    T fu0 = T(0), fv0 = T(0), fu1 = T(0), fv1 = T(0);
+    if (!ZERO && act) {
+        const int c0 = (j0 + ty) * N + (i0 + tx);
+        fu0 = g.fib[c0];
+        fv0 = g.fib[n + c0];
+        if (tid < RING) {
+            const int c1 = ((j0 - 1 + rj2) & m) * N + ((i0 - 1 + ri2) & m);
+            fu1 = g.fib[c1];
+            fv1 = g.fib[n + c1];
+        }
+    }
+    if (bulk) {
+        const bool ok = mbar_wait_bounded(&bar, 0, VK_WAIT_LIMIT);
+        if (!__syncthreads_and(ok)) {   // copies never completed: report, let them drain, leave
+            if (tid == 0 && g.err) *(volatile int*)g.err = SIB_DEV_ERR_TMA_WAIT;
+            mbar_wait_bounded(&bar, 0, VK_WAIT_LIMIT);
+            return;
+        }
+    } else {   // b at rows j0-1.., columns i0-1..i0+32; x at rows j0-2.., columns i0-2..i0+33
+        constexpr int NB = VK_BR * (TX + 2), NX = VK_XR * (TX + 4), NT = TX * TY;
+        static_assert(NB <= 2 * NT && NX <= 2 * NT, "two staging passes");
+        T vb[2][3], vx[2][3];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {   // every load issued before the first store
+            const int q = tid + k * NT;
+            if (q < NB) {
+                const int rj = q / (TX + 2), ri = q - rj * (TX + 2);
+                const int gc = ((j0 - 1 + rj) & m) * N + ((i0 - 1 + ri) & m);
+                vb[k][0] = b[gc];
+                vb[k][1] = b[n + gc];
+                vb[k][2] = b[2 * n + gc];
+            }
+            if (!ZERO && q < NX) {
+                const int jj = q / (TX + 4), ii = q - jj * (TX + 4);
+                const int gc = ((j0 - 2 + jj) & m) * N + ((i0 - 2 + ii) & m);
+                vx[k][0] = x[gc];
+                vx[k][1] = x[n + gc];
+                vx[k][2] = x[2 * n + gc];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int q = tid + k * NT;
+            if (q < NB) {
+                const int rj = q / (TX + 2), ri = q - rj * (TX + 2);
+                sb[0][rj][ri + 3] = vb[k][0];
+                sb[1][rj][ri + 3] = vb[k][1];
+                sb[2][rj][ri + 3] = vb[k][2];
+            }
+            if (!ZERO && q < NX) {
+                const int jj = q / (TX + 4), ii = q - jj * (TX + 4);
+                sx[0][jj][ii + 2] = vx[k][0];
+                sx[1][jj][ii + 2] = vx[k][1];
+                sx[2][jj][ii + 2] = vx[k][2];
+            }
         }
         __syncthreads();
     }
-    for (int q = tid; q < RY * RX; q += TX * TY) {
-        const int rj = q / RX, ri = q - rj * RX;
-        const int gc = ((j0 - 1 + rj) & m) * N + ((i0 - 1 + ri) & m);
-        if (ZERO) {
-            rs[0][rj][ri] = b[gc];
-            rs[1][rj][ri] = b[n + gc];
-            rs[2][rj][ri] = b[2 * n + gc];
-            continue;
-        }
-        const int sx = ri + 1, sy = rj + 1;
-        const T uc = xs[0][sy][sx], vc = xs[1][sy][sx], pc = xs[2][sy][sx];
-        const T uE = xs[0][sy][sx + 1], vN = xs[1][sy + 1][sx];
-        T Au = g.a0 * uc - g.c * ((uE + xs[0][sy][sx - 1]) + (xs[0][sy + 1][sx] + xs[0][sy - 1][sx])) +
-               (pc - xs[2][sy][sx - 1]) * g.inv_h;
-        T Av = g.a0 * vc - g.c * ((xs[1][sy][sx + 1] + xs[1][sy][sx - 1]) + (vN + xs[1][sy - 1][sx])) +
-               (pc - xs[2][sy - 1][sx]) * g.inv_h;
-        if (act) {
-            Au -= g.dt * g.fib[gc];
-            Av -= g.dt * g.fib[n + gc];
-        }
-        rs[0][rj][ri] = b[gc] - Au;
-        rs[1][rj][ri] = b[n + gc] - Av;
-        rs[2][rj][ri] = b[2 * n + gc] + ((uE - uc) + (vN - vc)) * g.inv_h;
+    // residual r = b - L x on the tile plus one cell each side (rows rj = 0..TY+1 <-> j0-1+rj,
+    // columns ri = 0..TX+1 <-> i0-1+ri), written over the staged b
+    T xu = T(0), xv = T(0), xp = T(0);
+    if (!ZERO) {
+        auto residual = [&](int ri, int rj, T fu, T fv, bool own) {
+            const int sxc = ri + 3, sy = rj + 1, sbc = ri + 3;
+            const T uc = sx[0][sy][sxc], vc = sx[1][sy][sxc], pc = sx[2][sy][sxc];
+            const T uE = sx[0][sy][sxc + 1], vN = sx[1][sy + 1][sxc];
+            T Au = g.a0 * uc - g.c * ((uE + sx[0][sy][sxc - 1]) + (sx[0][sy + 1][sxc] + sx[0][sy - 1][sxc])) +
+                   (pc - sx[2][sy][sxc - 1]) * g.inv_h;
+            T Av = g.a0 * vc - g.c * ((sx[1][sy][sxc + 1] + sx[1][sy][sxc - 1]) + (vN + sx[1][sy - 1][sxc])) +
+                   (pc - sx[2][sy - 1][sxc]) * g.inv_h;
+            if (act) {
+                Au -= g.dt * fu;
+                Av -= g.dt * fv;
+            }
+            sb[0][rj][sbc] = sb[0][rj][sbc] - Au;
+            sb[1][rj][sbc] = sb[1][rj][sbc] - Av;
+            sb[2][rj][sbc] = sb[2][rj][sbc] + ((uE - uc) + (vN - vc)) * g.inv_h;
+            if (own) {
+                xu = uc;
+                xv = vc;
+                xp = pc;
+            }
+        };
+        residual(tx + 1, ty + 1, fu0, fv0, true);
+        if (tid < RING) residual(ri2, rj2, fu1, fv1, false);
+        __syncthreads();
     }
-    __syncthreads();
+    // patch solves for cells (i0-1+pi, j0-1+pj), pi = 0..TX, pj = 0..TY; the residual of patch
+    // (pi, pj) sits at (ri, rj) = (pi, pj) of the staged area (column offset 3)
     const T ih = g.inv_h;
-    for (int q = tid; q < PY * PX; q += TX * TY) {
-        const int pj = q / PX, pi = q - pj * PX;
-        const T r0 = rs[0][pj][pi], r1 = rs[0][pj][pi + 1];
-        const T r2 = rs[1][pj][pi], r3 = rs[1][pj + 1][pi];
-        const T r4 = rs[2][pj][pi];
+    auto patch = [&](int pi, int pj) {
+        const T r0 = sb[0][pj][pi + 3], r1 = sb[0][pj][pi + 4];
+        const T r2 = sb[1][pj][pi + 3], r3 = sb[1][pj + 1][pi + 3];
+        const T r4 = sb[2][pj][pi + 3];
         T d0, d1, d2, d3, dp;
         if (!act) {
             const T tu0 = kb.ai0 * r0 + kb.ai1 * r1, tu1 = kb.ai1 * r0 + kb.ai0 * r1;
@@ -272,23 +374,72 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_vanka_tiled(Gri
         ds[2][pj][pi] = d2;
         ds[3][pj][pi] = d3;
         ds[4][pj][pi] = dp;
+    };
+    patch(tx + 1, ty + 1);
+    if (tid < VK_PX + TY) {   // bottom row pj = 0, then left column pi = 0 (one call: no divergent copies)
+        const bool row = tid < VK_PX;
+        patch(row ? tid : 0, row ? 0 : tid - VK_PX + 1);
     }
     __syncthreads();
-    const int ci = threadIdx.x, cj = threadIdx.y;
-    const int c = (j0 + cj) * N + (i0 + ci);
+    const int c = (j0 + ty) * N + (i0 + tx);
     const T hw = T(0.5) * g.omega;
-    const T du = hw * (ds[0][cj + 1][ci + 1] + ds[1][cj + 1][ci]);
-    const T dv = hw * (ds[2][cj + 1][ci + 1] + ds[3][cj][ci + 1]);
-    const T dq = g.omega * ds[4][cj + 1][ci + 1];
+    const T du = hw * (ds[0][ty + 1][tx + 1] + ds[1][ty + 1][tx]);
+    const T dv = hw * (ds[2][ty + 1][tx + 1] + ds[3][ty][tx + 1]);
+    const T dq = g.omega * ds[4][ty + 1][tx + 1];
     if (ZERO) {
         xo[c] = du;
         xo[n + c] = dv;
         xo[2 * n + c] = dq;
     } else {
-        xo[c] = xs[0][cj + 2][ci + 2] + du;
-        xo[n + c] = xs[1][cj + 2][ci + 2] + dv;
-        xo[2 * n + c] = xs[2][cj + 2][ci + 2] + dq;
+        xo[c] = xu + du;
+        xo[n + c] = xv + dv;
+        xo[2 * n + c] = xp + dq;
     }
+}
+
+// Tensor map of a level vector [u | v | p] viewed as N x N x 3 (column fastest) with a box of
+// VK_W x rows x 3; false if the base is not 16-byte aligned or the driver cannot encode it.
+// Encoded maps are kept per thread, keyed by (base, N, element size, rows).
+static bool field_map(CUtensorMap* out, const void* base, int N, int es, int rows) {
+    struct Entry {
+        const void* p;
+        int N, es, rows;
+        CUtensorMap m;
+    };
+    constexpr int CACHE = 32;
+    static thread_local Entry cache[CACHE];
+    static thread_local int used = 0, next = 0;
+    for (int k = 0; k < used; ++k)
+        if (cache[k].p == base && cache[k].N == N && cache[k].es == es && cache[k].rows == rows) {
+            *out = cache[k].m;
+            return true;
+        }
+    static PFN_cuTensorMapEncodeTiled_v12000 enc = []() {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, 3};
+    const cuuint64_t strides[2] = {(cuuint64_t)N * es, (cuuint64_t)N * N * es};
+    const cuuint32_t box[3] = {(cuuint32_t)VK_W, (cuuint32_t)rows, 3};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUtensorMap m;
+    const CUresult r = enc(&m, es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                           const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    Entry& e = cache[next];
+    e = Entry{base, N, es, rows, m};
+    next = (next + 1) % CACHE;
+    if (used < CACHE) ++used;
+    *out = m;
+    return true;
 }
 
 template <typename T, bool ZERO>
@@ -299,7 +450,13 @@ void launch_vanka_any(const GridK<T>& g, const T* x, const T* b, T* xo, cudaStre
         return;
     }
     const VankaBulk<T> kb = vanka_bulk<T>(g.a0, g.c, g.inv_h);
-    launch_pdl(k_vanka_tiled<T, ZERO>, grd, blk, 0, s, g, kb, x, b, xo);
+    CUtensorMap mx, mb;
+    std::memset(&mx, 0, sizeof(mx));
+    std::memset(&mb, 0, sizeof(mb));
+    // interior tiles exist from N = 4 TX on; the maps are only read by those tiles
+    const int tma = g.N >= 4 * TX && field_map(&mb, b, g.N, sizeof(T), VK_BR) &&
+                    (ZERO || field_map(&mx, x, g.N, sizeof(T), VK_XR));
+    launch_pdl(k_vanka_tiled<T, ZERO>, grd, blk, 0, s, g, kb, mx, mb, tma, x, b, xo);
 }
 
 template <typename T>
@@ -377,8 +534,78 @@ __global__ void k_prolong_add(int Nc, const T* __restrict__ ec, T* __restrict__ 
     prolong_add_cell(Nc, ec, xf, i, j);
 }
 
+// The same correction with one thread per coarse cell (I, J) updating its 2 x 2 fine cells: the
+// coarse neighbourhood is read once, and each fine row pair (2I, 2I + 1) is read and written as one
+// two-word vector.  Each fine value is formed exactly as in prolong_add_cell.
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_add_quad(int Nc, const T* __restrict__ ec, T* __restrict__ xf) {
+    using V2 = typename Vec2<T>::type;
+    pdl_entry();
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    if (I >= Nc || J >= Nc) return;
+    const int Nf = 2 * Nc, nf = Nf * Nf, nc = Nc * Nc, mc = Nc - 1;
+    const int Ip = (I + 1) & mc, Im = (I - 1) & mc, Jp = (J + 1) & mc, Jm = (J - 1) & mc;
+    const T* eu = ec;
+    const T* ev = ec + nc;
+    const T* ep = ec + 2 * nc;
+    const T u0 = eu[J * Nc + I], u1 = T(0.5) * (eu[J * Nc + I] + eu[J * Nc + Ip]);
+    const T v0 = ev[J * Nc + I], v1 = T(0.5) * (ev[J * Nc + I] + ev[Jp * Nc + I]);
+    const T pc = ep[J * Nc + I];
+    const T pW = ep[J * Nc + Im], pE = ep[J * Nc + Ip], pS = ep[Jm * Nc + I], pN = ep[Jp * Nc + I];
+    const T pSW = ep[Jm * Nc + Im], pSE = ep[Jm * Nc + Ip], pNW = ep[Jp * Nc + Im], pNE = ep[Jp * Nc + Ip];
+    // fine (2I, 2J) uses neighbours I-1, J-1; (2I+1, 2J): I+1, J-1; (2I, 2J+1): I-1, J+1; (2I+1, 2J+1): I+1, J+1
+    const T p00 = T(9.0 / 16.0) * pc + T(3.0 / 16.0) * (pW + pS) + T(1.0 / 16.0) * pSW;
+    const T p10 = T(9.0 / 16.0) * pc + T(3.0 / 16.0) * (pE + pS) + T(1.0 / 16.0) * pSE;
+    const T p01 = T(9.0 / 16.0) * pc + T(3.0 / 16.0) * (pW + pN) + T(1.0 / 16.0) * pNW;
+    const T p11 = T(9.0 / 16.0) * pc + T(3.0 / 16.0) * (pE + pN) + T(1.0 / 16.0) * pNE;
+    const int r0 = (2 * J) * Nf + 2 * I, r1 = r0 + Nf;
+    V2* xu0 = reinterpret_cast<V2*>(xf + r0);
+    V2* xu1 = reinterpret_cast<V2*>(xf + r1);
+    V2* xv0 = reinterpret_cast<V2*>(xf + nf + r0);
+    V2* xv1 = reinterpret_cast<V2*>(xf + nf + r1);
+    V2* xp0 = reinterpret_cast<V2*>(xf + 2 * nf + r0);
+    V2* xp1 = reinterpret_cast<V2*>(xf + 2 * nf + r1);
+    V2 a = *xu0, b = *xu1, c = *xv0, d = *xv1, e = *xp0, f = *xp1;
+    a.x += u0;
+    a.y += u1;
+    b.x += u0;
+    b.y += u1;
+    c.x += v0;
+    c.y += v0;
+    d.x += v1;
+    d.y += v1;
+    e.x += p00;
+    e.y += p10;
+    f.x += p01;
+    f.y += p11;
+    *xu0 = a;
+    *xu1 = b;
+    *xv0 = c;
+    *xv1 = d;
+    *xp0 = e;
+    *xp1 = f;
+}
+
 template <typename T>
 void launch_prolong_add(int Nc, const T* ec, T* xf, cudaStream_t s) {
+    // the two-word accesses need xf aligned to two elements (a caller's pointer may be offset by one)
+    if (Nc >= 8 && (reinterpret_cast<uintptr_t>(xf) % (2 * sizeof(T))) == 0) {
+        dim3 blk(Nc < 32 ? Nc : 32, 8);
+        dim3 grd((Nc + blk.x - 1) / blk.x, (Nc + blk.y - 1) / blk.y);
+        launch_pdl(k_prolong_add_quad<T>, grd, blk, 0, s, Nc, ec, xf);
+        return;
+    }
     const int Nf = 2 * Nc;
     dim3 blk(Nf < 32 ? Nf : 32, Nf < 8 ? Nf : 8);
     dim3 grd((Nf + blk.x - 1) / blk.x, (Nf + blk.y - 1) / blk.y);

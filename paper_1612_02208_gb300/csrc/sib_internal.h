@@ -74,7 +74,11 @@ struct GridK {
     const T* ibd;                    // 4 n: B(f,f) on u faces, B(u_ij,u_i+1j), B(f,f) on v, B(v_ij,v_ij+1)
     const unsigned char* tile;       // per-tile IB flag (dilated by one tile), may be null
     const T* dinv;                   // SC: 1/diag(A_IB) on u and v faces, 1/diag(D diag(A_IB)^-1 G) on cells
+    int* err;                        // host-visible error word (SIB_DEV_ERR_*), may be null
 };
+
+// Codes a kernel writes to the context's error word when a bounded wait gives up.
+constexpr int SIB_DEV_ERR_TMA_WAIT = 1;   // a tile copy did not complete
 
 // Constants of the Vanka patch solve for cells without IB entries (the patch matrix is the same
 // for all of them): A^{-1} = [[ai0, ai1], [ai1, ai0]], s = A^{-1}(1/h, -1/h) = (s0, -s0), and the

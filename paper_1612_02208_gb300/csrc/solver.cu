@@ -132,6 +132,7 @@ struct sib_ctx {
     double* part = nullptr;      // NBLK * 128
     double* scal = nullptr;      // 3 * 128 scalars: h, h2, misc
     double* hbuf = nullptr;      // pinned host mirror
+    int* herr = nullptr;         // pinned, device-written error word (SIB_DEV_ERR_*), 0 while healthy
     int* flag = nullptr;
     // eigen estimate override
     bool lamOverride = false;
@@ -177,7 +178,12 @@ inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
 void kcheck(sib_ctx* c) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw SibError(SIB_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
-    (void)c;
+    if (c && c->herr && *(volatile int*)c->herr != 0) {   // a kernel gave up a bounded wait
+        const int code = *(volatile int*)c->herr;
+        *(volatile int*)c->herr = 0;
+        throw SibError(SIB_ERR_CUDA, "device wait ran past its limit (code " + std::to_string(code) +
+                                         "): results of the call are invalid");
+    }
 }
 
 // count one kernel launch (every launcher used on the solve path starts exactly one kernel)
@@ -222,6 +228,7 @@ GridK<T> gridk(sib_ctx* c, int l) {
     while ((1 << lg) < lv.ty) ++lg;
     g.lgty = lg;
     g.dinv = (const T*)lv.p[pi].dinv;
+    g.err = c->herr;
     return g;
 }
 
@@ -1542,6 +1549,8 @@ int sib_create(sib_ctx** out, int N, int n_min) {
         c->part = (double*)dalloc(c, sizeof(double) * NBLK * 128);
         c->scal = (double*)dalloc(c, sizeof(double) * 512);
         CK(cudaMallocHost(&c->hbuf, sizeof(double) * 512));
+        CK(cudaMallocHost(&c->herr, 64));
+        std::memset(c->herr, 0, 64);
         alloc_markers(c);
     } catch (const SibError& e) {
         std::fprintf(stderr, "sib_create: %s\n", e.what());
@@ -1558,6 +1567,7 @@ void sib_destroy(sib_ctx* c) {
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
     if (c->hbuf) cudaFreeHost(c->hbuf);
+    if (c->herr) cudaFreeHost(c->herr);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->aux) cudaStreamDestroy(c->aux);
     if (c->evFork) cudaEventDestroy(c->evFork);
