@@ -187,8 +187,8 @@ constexpr int VK_WAIT_LIMIT = 1 << 22;         // bounded wait for the tile copi
 template <typename T, bool ZERO>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4)
     k_vanka_tiled(GridK<T> g, VankaBulk<T> kb, const __grid_constant__ CUtensorMap mx,
-                  const __grid_constant__ CUtensorMap mb, int tma, const T* __restrict__ x, const T* __restrict__ b,
-                  T* __restrict__ xo) {
+                  const __grid_constant__ CUtensorMap mb, int tma, int first_wave, const T* __restrict__ x,
+                  const T* __restrict__ b, T* __restrict__ xo) {
     __shared__ __align__(128) T stage[VK_STAGE];
     __shared__ T bs[6][VK_PY][VK_PX];   // IB entries of the patches of an active tile
     __shared__ uint64_t bar;
@@ -201,9 +201,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4)
     // tiles whose staged window lies inside the grid take the TMA copies; the others (the periodic
     // wrap) and grids without tensor maps gather element by element
     const bool bulk = tma && i0 >= TX && i0 + 2 * TX <= N && j0 >= TY && j0 + 2 * TY <= N;
-    // set-up data (tile flag, patch entries) before the wait for x and b
-    const bool act = g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x];
-    if (act) {
+    // set-up data (tile flag, patch entries): blocks of the first wave load it before the wait for x
+    // and b, hidden behind the preceding kernel; later blocks issue their tile copies first and load
+    // it while the copies are in flight
+    const bool early = (int)(blockIdx.y * gridDim.x + blockIdx.x) < first_wave;
+    bool act = false;
+    auto load_patch_ib = [&]() {
         for (int q = tid; q < VK_PY * VK_PX; q += TX * TY) {
             const int pj = q / VK_PX, pi = q - pj * VK_PX;
             const int i = (i0 - 1 + pi) & m, j = (j0 - 1 + pj) & m;
@@ -215,6 +218,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4)
             bs[4][pj][pi] = g.ibd[2 * n + cn];
             bs[5][pj][pi] = g.ibd[3 * n + cc];
         }
+    };
+    if (early) {
+        act = g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x];
+        if (act) load_patch_ib();
     }
     if (bulk && tid == 0) {
         tma_prefetch_map(&mb);
@@ -222,8 +229,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4)
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
-    __syncthreads();
+    if (early) __syncthreads();   // patch entries and the barrier's initialisation complete
     pdl_entry();
+    if (bulk && tid == 0) {
+        constexpr uint32_t bb = 3 * VK_BR * VK_W * sizeof(T), bx = 3 * VK_XR * VK_W * sizeof(T);
+        mbar_expect_tx(&bar, ZERO ? bb : bb + bx);
+        tma_load_3d(&sb[0][0][0], &mb, &bar, i0 - 4, j0 - 1, 0);
+        if (!ZERO) tma_load_3d(&sx[0][0][0], &mx, &bar, i0 - 4, j0 - 2, 0);
+    }
+    if (!early) {
+        act = g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x];
+        if (act) load_patch_ib();
+    }
     // residual cells: this thread's own (ri, rj) = (tx + 1, ty + 1) and, for the first
     // 2 (TX + TY) + 4 threads, one cell of the ring around the tile
     constexpr int RING = 2 * (TX + 2) + 2 * TY;
@@ -239,14 +256,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4)
         ri2 = TX + 1;
         rj2 = tid - 2 * (TX + 2) - TY + 1;
     }
-    if (bulk) {
-        if (tid == 0) {
-            constexpr uint32_t bb = 3 * VK_BR * VK_W * sizeof(T), bx = 3 * VK_XR * VK_W * sizeof(T);
-            mbar_expect_tx(&bar, ZERO ? bb : bb + bx);
-            tma_load_3d(&sb[0][0][0], &mb, &bar, i0 - 4, j0 - 1, 0);
-            if (!ZERO) tma_load_3d(&sx[0][0][0], &mx, &bar, i0 - 4, j0 - 2, 0);
-        }
-    }
     // IB term of the residual cells of an active tile, fetched while the tile is in flight
     T fu0 = T(0), fv0 = T(0), fu1 = T(0), fv1 = T(0);
     if (!ZERO && act) {
@@ -259,6 +268,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4)
             fv1 = g.fib[n + c1];
         }
     }
+    if (!early) __syncthreads();   // the barrier's initialisation before the other threads wait on it
     if (bulk) {
         const bool ok = mbar_wait_bounded(&bar, 0, VK_WAIT_LIMIT);
         if (!__syncthreads_and(ok)) {   // copies never completed: report, let them drain, leave
@@ -442,6 +452,17 @@ static bool field_map(CUtensorMap* out, const void* base, int N, int es, int row
     return true;
 }
 
+// blocks of a kernel that are resident on the GPU at once (occupancy x SM count); 0 if unknown
+template <typename K>
+int resident_blocks(K kern) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, TX * TY, 0) != cudaSuccess)
+        return 0;
+    return sms * per;
+}
+
 template <typename T, bool ZERO>
 void launch_vanka_any(const GridK<T>& g, const T* x, const T* b, T* xo, cudaStream_t s) {
     dim3 blk(g.tx, g.ty), grd(g.N / g.tx, g.N / g.ty);
@@ -456,7 +477,8 @@ void launch_vanka_any(const GridK<T>& g, const T* x, const T* b, T* xo, cudaStre
     // interior tiles exist from N = 4 TX on; the maps are only read by those tiles
     const int tma = g.N >= 4 * TX && field_map(&mb, b, g.N, sizeof(T), VK_BR) &&
                     (ZERO || field_map(&mx, x, g.N, sizeof(T), VK_XR));
-    launch_pdl(k_vanka_tiled<T, ZERO>, grd, blk, 0, s, g, kb, mx, mb, tma, x, b, xo);
+    static const int first_wave = resident_blocks(k_vanka_tiled<T, ZERO>);
+    launch_pdl(k_vanka_tiled<T, ZERO>, grd, blk, 0, s, g, kb, mx, mb, tma, first_wave, x, b, xo);
 }
 
 template <typename T>
