@@ -80,7 +80,13 @@ typedef struct {
     int    smooth_krylov; /* 1: every pre- and post-smoothing stage of nu sweeps is nu iterations of
                              flexible GMRES on the level's residual equation, each preconditioned by
                              one undamped basic sweep (Sec. 3.3; nu <= 8); 0: nu damped sweeps (0)    */
+    int    sc_relax;      /* SC: point relaxation preconditioning both Chebyshev iterations (Sec. 3.3,
+                             SC smoothing): SIB_RELAX_JACOBI (diagonal, default) or SIB_RELAX_SGS (one
+                             symmetric red-black Gauss-Seidel sweep from zero, colours 0, 1, 1, 0)    */
 } sib_opts;
+
+#define SIB_RELAX_JACOBI 0
+#define SIB_RELAX_SGS    1
 
 typedef struct {
     int    iterations;          /* FGMRES iterations performed                                       */

@@ -37,7 +37,8 @@ class Level:
 
 class Hierarchy:
     def __init__(self, prob, n_min=8, smoother="vanka", omega=None, nu1=2, nu2=2,
-                 cheb_iters=2, cheb_lo=0.1, cheb_hi=1.1, power_iters=10, lam_override=None, krylov=False):
+                 cheb_iters=2, cheb_lo=0.1, cheb_hi=1.1, power_iters=10, lam_override=None, krylov=False,
+                 sc_relax="jacobi"):
         N = prob.N
         if N < n_min or (N // n_min) * n_min != N or (N // n_min) & (N // n_min - 1):
             raise ValueError("N must be n_min * 2^k")
@@ -47,6 +48,9 @@ class Hierarchy:
         # krylov: each smoothing stage is FGMRES(nu) preconditioned by one undamped basic sweep
         # (Sec. 3.3); otherwise nu damped sweeps
         self.krylov = krylov
+        # sc_relax: the point relaxation preconditioning the SC smoother's Chebyshev iterations,
+        # "jacobi" or "sgs" (symmetric red-black Gauss-Seidel)
+        self.sc_relax = sc_relax
         self.omega = 1.0 if krylov else ((0.8 if smoother == "vanka" else 1.0) if omega is None else omega)
         self.nu1, self.nu2 = nu1, nu2
         self.cheb_iters, self.cheb_lo, self.cheb_hi = cheb_iters, cheb_lo, cheb_hi
@@ -77,15 +81,14 @@ class Hierarchy:
                 lev.patches = smoothers.vanka_patches(lev.L, lev.dofs)
             else:
                 lev.dA = lev.AIB.diagonal()
-                Mh = (lev.D @ sp.diags(1.0 / lev.dA) @ lev.G).tocsr()
-                lev.dM = Mh.diagonal()
+                PA, PM, lev.dM = smoothers.sc_preconditioners(lev.AIB, lev.G, lev.D, lev.dA, sc_relax)
                 if lam_override is not None:
                     lev.lamA, lev.lamM = lam_override[l]
                 else:
-                    lev.lamA = smoothers.power_max(lambda z: lev.AIB @ z, 1.0 / lev.dA, 2 * lev.n, power_iters)
-                    Ainv = lambda q: smoothers.chebyshev(lambda z: lev.AIB @ z, 1.0 / lev.dA, q, lev.lamA,
+                    lev.lamA = smoothers.power_max(lambda z: lev.AIB @ z, PA, 2 * lev.n, power_iters)
+                    Ainv = lambda q: smoothers.chebyshev(lambda z: lev.AIB @ z, PA, q, lev.lamA,
                                                          cheb_iters, cheb_lo, cheb_hi)
-                    lev.lamM = smoothers.power_max(lambda q: lev.D @ Ainv(lev.G @ q), 1.0 / lev.dM, lev.n,
+                    lev.lamM = smoothers.power_max(lambda q: lev.D @ Ainv(lev.G @ q), PM, lev.n,
                                                    power_iters)
 
     @property
@@ -98,7 +101,7 @@ class Hierarchy:
         if self.smoother == "vanka":
             return smoothers.vanka_sweep(lev.L, lev.dofs, lev.patches, x, b, self.omega)
         return smoothers.sc_sweep(lev.L, lev.G, lev.D, lev.AIB, lev.dA, lev.dM, lev.lamA, lev.lamM,
-                                  x, b, self.omega, self.cheb_iters, self.cheb_lo, self.cheb_hi)
+                                  x, b, self.omega, self.cheb_iters, self.cheb_lo, self.cheb_hi, self.sc_relax)
 
     def smooth(self, l, x, b, sweeps):
         lev = self.levels[l]
@@ -111,7 +114,8 @@ class Hierarchy:
                 x = smoothers.vanka_sweep(lev.L, lev.dofs, lev.patches, x, b, self.omega)
             else:
                 x = smoothers.sc_sweep(lev.L, lev.G, lev.D, lev.AIB, lev.dA, lev.dM, lev.lamA, lev.lamM,
-                                       x, b, self.omega, self.cheb_iters, self.cheb_lo, self.cheb_hi)
+                                       x, b, self.omega, self.cheb_iters, self.cheb_lo, self.cheb_hi,
+                                       self.sc_relax)
         return x
 
     def mg(self, l, w, b):

@@ -9,11 +9,19 @@ and summed.  One sweep is x <- x + omega * sum_c W_c R_c^T L_c^{-1} R_c (b - L x
 
 Schur-complement smoother (Eqs. fact-Stokes-IB and approx-fact-Stokes-IB):
     y  = At^{-1} r_u,   dp = Mt^{-1}(r_p + D y),   du = y - At^{-1}(G dp),   x <- x + omega (du, dp)
-At^{-1}: a fixed number of Chebyshev iterations on A_IB with point (Jacobi) preconditioning;
-Mt^{-1}: a fixed number of Chebyshev iterations on D At^{-1} G preconditioned by the diagonal of
-the sparse approximate Schur complement Mh = D diag(A_IB)^{-1} G.  The paper relaxes with
-Gauss-Seidel; here the diagonal (Jacobi) point relaxation is used instead, so that every level is
-one parallel pass.
+At^{-1}: a fixed number of Chebyshev iterations on A_IB with a point-relaxation preconditioner;
+Mt^{-1}: a fixed number of Chebyshev iterations on D At^{-1} G preconditioned by point relaxation
+on the sparse approximate Schur complement Mh = D diag(A_IB)^{-1} G.  The paper relaxes with
+Gauss-Seidel.  Two relaxations are provided:
+- "jacobi": the diagonal inverse (every level is one parallel pass);
+- "sgs": one symmetric multicolour Gauss-Seidel sweep from a zero guess.  The dofs are coloured
+  red-black by (i + j) mod 2 (u and v faces alike, and the cells of Mh), which separates every pair
+  of unknowns coupled by the five-point stencils.  A colour pass updates its colour as
+  z_c <- z_c + (r - Op z)_c / diag_c with Op z taken from the iterate at the start of the pass; the
+  sweep runs the colours forward then backward (0, 1, 1, 0), so the preconditioner is symmetric.
+  For Mh, and for A_IB rows without IB couplings, this is exactly Gauss-Seidel in red-black order;
+  the IB couplings [S K J] also link faces of one colour, and those enter from the start of the
+  pass.
 
 Chebyshev acceleration follows the textbook recurrence (Saad, Iterative Methods for Sparse
 Linear Systems, Algorithm 12.1) with x_0 = 0 on the interval [lo, hi] * lambda_max, where
@@ -26,6 +34,7 @@ polynomial T_k((theta - t)/delta) / T_k(theta/delta) on diagonal operators; the 
 exact inner inverses reproduces L^{-1}.
 """
 import numpy as np
+import scipy.sparse as sp
 
 from .mac import cell_index
 
@@ -64,27 +73,38 @@ def hash_vector(n):
     return ((k * np.uint64(2654435761)) % np.uint64(2 ** 32)).astype(np.float64) / 2.0 ** 32 - 0.5
 
 
-def power_max(apply_op, dinv, n, iters):
-    """Estimate of the largest eigenvalue of diag^{-1} Op: ||w|| after `iters` normalised steps."""
+def _as_prec(prec):
+    """A preconditioner given as a vector is the diagonal scaling by it; a callable is applied."""
+    if callable(prec):
+        return prec
+    return lambda r: prec * r
+
+
+def power_max(apply_op, prec, n, iters):
+    """Estimate of the largest eigenvalue of P Op (P = diag(prec), or the callable prec):
+    ||w|| after `iters` normalised steps."""
+    P = _as_prec(prec)
     v = hash_vector(n)
     v = v / np.linalg.norm(v)
     lam = 0.0
     for _ in range(iters):
-        w = dinv * apply_op(v)
+        w = P(apply_op(v))
         lam = np.linalg.norm(w)
         v = w / lam
     return lam
 
 
-def chebyshev(apply_op, dinv, b, lam_max, iters, lo=0.1, hi=1.1):
-    """`iters` Chebyshev iterations for Op x = b from x_0 = 0, preconditioner diag^{-1}."""
+def chebyshev(apply_op, prec, b, lam_max, iters, lo=0.1, hi=1.1):
+    """`iters` Chebyshev iterations for Op x = b from x_0 = 0 with preconditioner P (diag(prec), or
+    the callable prec)."""
+    P = _as_prec(prec)
     lmin, lmax = lo * lam_max, hi * lam_max
     theta = 0.5 * (lmax + lmin)
     delta = 0.5 * (lmax - lmin)
     sigma = theta / delta
     rho = 1.0 / sigma
     r = b.copy()
-    d = (dinv * r) / theta
+    d = P(r) / theta
     x = np.zeros_like(b)
     for k in range(iters):
         x = x + d
@@ -92,9 +112,40 @@ def chebyshev(apply_op, dinv, b, lam_max, iters, lo=0.1, hi=1.1):
             break
         r = r - apply_op(d)
         rho_new = 1.0 / (2.0 * sigma - rho)
-        d = rho_new * rho * d + (2.0 * rho_new / delta) * (dinv * r)
+        d = rho_new * rho * d + (2.0 * rho_new / delta) * P(r)
         rho = rho_new
     return x
+
+
+def rb_colours(N, fields):
+    """Red-black colour (i + j) mod 2 of every dof of `fields` stacked N x N fields, row-major [j][i]."""
+    j, i = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    return np.tile(((i + j) % 2).ravel(), fields)
+
+
+def sgs_multicolour(Op, diag, colours, r):
+    """One symmetric multicolour Gauss-Seidel sweep for Op z = r from z = 0: colour passes 0, 1, 1, 0,
+    each z_c <- z_c + (r - Op z)_c / diag_c with Op z from the start of the pass."""
+    z = np.zeros_like(r)
+    for c in (0, 1, 1, 0):
+        sel = colours == c
+        res = r - Op @ z
+        z[sel] = z[sel] + res[sel] / diag[sel]
+    return z
+
+
+def sc_preconditioners(AIB, G, D, dA, relax):
+    """(P_A, P_M): the point relaxations of A_IB and of Mh = D diag(A_IB)^{-1} G used inside the
+    Chebyshev iterations; diag(Mh) is returned as the third value."""
+    Mh = (D @ sp.diags(1.0 / dA) @ G).tocsr()
+    dM = Mh.diagonal()
+    if relax == "jacobi":
+        return 1.0 / dA, 1.0 / dM, dM
+    if relax != "sgs":
+        raise ValueError("relax must be 'jacobi' or 'sgs'")
+    N = int(round(np.sqrt(G.shape[1])))
+    cu, cp = rb_colours(N, 2), rb_colours(N, 1)
+    return (lambda q: sgs_multicolour(AIB, dA, cu, q)), (lambda q: sgs_multicolour(Mh, dM, cp, q)), dM
 
 
 def sc_apply(r, nu, Ainv, Minv, G, D):
@@ -105,19 +156,18 @@ def sc_apply(r, nu, Ainv, Minv, G, D):
     return np.concatenate([du, dp])
 
 
-def sc_sweep(L, G, D, AIB, dA, dM, lamA, lamM, x, b, omega, cheb_iters, lo=0.1, hi=1.1):
+def sc_sweep(L, G, D, AIB, dA, dM, lamA, lamM, x, b, omega, cheb_iters, lo=0.1, hi=1.1, relax="jacobi"):
     nu = G.shape[0]
-    dAinv = 1.0 / dA
-    dMinv = 1.0 / dM
+    PA, PM, _ = sc_preconditioners(AIB, G, D, dA, relax)
 
     def Ainv(q):
-        return chebyshev(lambda z: AIB @ z, dAinv, q, lamA, cheb_iters, lo, hi)
+        return chebyshev(lambda z: AIB @ z, PA, q, lamA, cheb_iters, lo, hi)
 
     def Mop(q):
         return D @ Ainv(G @ q)
 
     def Minv(q):
-        return chebyshev(Mop, dMinv, q, lamM, cheb_iters, lo, hi)
+        return chebyshev(Mop, PM, q, lamM, cheb_iters, lo, hi)
 
     r = b - L @ x
     return x + omega * sc_apply(r, nu, Ainv, Minv, G, D)

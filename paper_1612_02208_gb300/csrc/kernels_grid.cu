@@ -754,6 +754,90 @@ void launch_jacobi_M(const GridK<T>& g, const T* r, T* z, T scale, cudaStream_t 
     launch_pdl(k_jacobi_M<T>, dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s, g, r, z, scale);
 }
 
+// ------------------------------------------------------------------------------------------
+// Symmetric multicolour Gauss-Seidel preconditioners of the SC smoother's Chebyshev iterations
+// (Sec. 3.3, SC smoothing: Gauss-Seidel on A_IB and on Mh = D diag(A_IB)^{-1} G).  The dofs are
+// coloured red-black by (i + j) mod 2 (u and v faces alike, and the cells of Mh), which separates
+// every pair of unknowns coupled by the five-point stencils.  One pass updates one colour,
+//   z_c <- z_c + (scale q - Op z)_c / diag_c,
+// with Op z from the iterate at the start of the pass (for A_IB the IB term comes from g.fib,
+// computed by an IB pass over that iterate: the IB couplings also link faces of one colour).  A
+// sweep from zero runs passes 0, 1, 1, 0; the first pass writes every entry (colour 1 gets 0).
+// Diagonal inverses come from g.dinv (faces: 1/diag(A_IB), cells: 1/diag(Mh)).
+template <typename T>
+__global__ void k_sgs_A_first(GridK<T> g, T scale, const T* __restrict__ q, T* __restrict__ z) {
+    pdl_entry();
+    const int N = g.N, n = N * N;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const int c = j * N + i;
+    const bool red = ((i + j) & 1) == 0;
+    z[c] = red ? scale * q[c] * g.dinv[c] : T(0);
+    z[n + c] = red ? scale * q[n + c] * g.dinv[n + c] : T(0);
+}
+// one pass over colour `colour`: thread (k, j) takes cell i = 2 k + ((j + colour) & 1) of row j
+template <typename T>
+__global__ void k_sgs_A_pass(GridK<T> g, int colour, T scale, const T* __restrict__ q, T* __restrict__ z) {
+    pdl_entry();
+    const int N = g.N, n = N * N;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (2 * k >= N || j >= N) return;
+    const int i = 2 * k + ((j + colour) & 1);
+    const int c = j * N + i;
+    const T ru = scale * q[c] - Aib(g, z, 0, i, j);
+    const T rv = scale * q[n + c] - Aib(g, z, 1, i, j);
+    z[c] += ru * g.dinv[c];
+    z[n + c] += rv * g.dinv[n + c];
+}
+
+// (Mh z) at cell (i, j): (1/h^2) sum over its faces f of a_f (z across f - z_ij), a = 1/diag(A_IB)
+template <typename T>
+__device__ __forceinline__ T mhat_cell(const GridK<T>& g, const T* __restrict__ z, int i, int j) {
+    const int N = g.N, n = N * N, m = N - 1;
+    const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m;
+    const int c = j * N + i;
+    const T zc = z[c];
+    const T fx = g.dinv[j * N + ip] * (z[j * N + ip] - zc) - g.dinv[c] * (zc - z[j * N + im]);
+    const T fy = g.dinv[n + jp * N + i] * (z[jp * N + i] - zc) - g.dinv[n + c] * (zc - z[jm * N + i]);
+    return (fx + fy) * g.inv_h * g.inv_h;
+}
+template <typename T>
+__global__ void k_sgs_M_first(GridK<T> g, T scale, const T* __restrict__ q, T* __restrict__ z) {
+    pdl_entry();
+    const int N = g.N, n = N * N;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const int c = j * N + i;
+    z[c] = ((i + j) & 1) == 0 ? scale * q[c] * g.dinv[2 * n + c] : T(0);
+}
+template <typename T>
+__global__ void k_sgs_M_pass(GridK<T> g, int colour, T scale, const T* __restrict__ q, T* __restrict__ z) {
+    pdl_entry();
+    const int N = g.N, n = N * N;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (2 * k >= N || j >= N) return;
+    const int i = 2 * k + ((j + colour) & 1);
+    const int c = j * N + i;
+    z[c] += (scale * q[c] - mhat_cell(g, z, i, j)) * g.dinv[2 * n + c];
+}
+
+template <typename T>
+void launch_sgs_pass(const GridK<T>& g, bool cells, int pass, T scale, const T* q, T* z, cudaStream_t s) {
+    if (pass < 0) {   // the first pass of a sweep from zero
+        const dim3 grd(g.N / g.tx, g.N / g.ty), blk(g.tx, g.ty);
+        if (cells)
+            launch_pdl(k_sgs_M_first<T>, grd, blk, 0, s, g, scale, q, z);
+        else
+            launch_pdl(k_sgs_A_first<T>, grd, blk, 0, s, g, scale, q, z);
+        return;
+    }
+    const int half = g.N / 2;
+    const dim3 blk(half < 32 ? half : 32, g.N < 8 ? g.N : 8);
+    const dim3 grd((half + blk.x - 1) / blk.x, (g.N + blk.y - 1) / blk.y);
+    if (cells)
+        launch_pdl(k_sgs_M_pass<T>, grd, blk, 0, s, g, pass, scale, q, z);
+    else
+        launch_pdl(k_sgs_A_pass<T>, grd, blk, 0, s, g, pass, scale, q, z);
+}
+
 // Chebyshev direction update d = ra * d + rb * dinvr, then x += d
 template <typename T>
 __global__ void k_cheb_update(const T* __restrict__ dinvr, T* __restrict__ d, T* __restrict__ x, T ra, T rb,
@@ -923,6 +1007,7 @@ void launch_power_Mfinish(const GridK<T>& g, const T* ya, T* w, cudaStream_t s) 
     template void launch_gradient<T>(const GridK<T>&, const T*, T*, cudaStream_t);                        \
     template void launch_divergence<T>(const GridK<T>&, const T*, T*, cudaStream_t);                      \
     template void launch_jacobi_M<T>(const GridK<T>&, const T*, T*, T, cudaStream_t);                     \
+    template void launch_sgs_pass<T>(const GridK<T>&, bool, int, T, const T*, T*, cudaStream_t);          \
     template void launch_cheb_update<T>(const T*, T*, T*, T, T, int64_t, cudaStream_t);                   \
     template void launch_vanka_zero<T>(const GridK<T>&, const T*, T*, cudaStream_t);                       \
     template void launch_residual_restrict<T>(const GridK<T>&, const T*, const T*, T*, cudaStream_t);       \

@@ -136,6 +136,10 @@ template <typename T> void launch_apply_AIB(const GridK<T>& g, const T* u, T* y,
 template <typename T> void launch_gradient(const GridK<T>& g, const T* p, T* gu, cudaStream_t s);
 template <typename T> void launch_divergence(const GridK<T>& g, const T* u, T* d, cudaStream_t s);
 template <typename T> void launch_jacobi_M(const GridK<T>& g, const T* r, T* z, T scale, cudaStream_t s);
+// one pass of a symmetric multicolour Gauss-Seidel sweep on A_IB (cells == false) or on
+// Mh = D diag(A_IB)^{-1} G (cells == true): pass = colour 0 or 1, or -1 for the first pass from zero
+template <typename T> void launch_sgs_pass(const GridK<T>& g, bool cells, int pass, T scale, const T* q, T* z,
+                                           cudaStream_t s);
 template <typename T> void launch_cheb_update(const T* dinvr, T* d, T* x, T ra, T rb, int64_t n, cudaStream_t s);
 // fused kernels
 template <typename T> void launch_vanka_zero(const GridK<T>& g, const T* b, T* xo, cudaStream_t s);

@@ -303,7 +303,37 @@ ChebCoef cheb_coef(double lam, double lo, double hi) {
     return k;
 }
 
-// out = At^{-1} q: cheb_iters Chebyshev iterations on A_IB, Jacobi-preconditioned, from 0.
+// z = scale * P_A q and z = scale * P_M q: the point relaxation preconditioning the SC smoother's
+// Chebyshev iterations on A_IB and on the Schur complement (option sc_relax): the diagonal inverse,
+// or one symmetric red-black Gauss-Seidel sweep from zero (colour passes 0, 1, 1, 0; each pass on
+// A_IB first applies the IB operator to the current iterate).
+template <typename T>
+void precond_A(sib_ctx* c, int l, const T* q, T* z, T scale, cudaStream_t s) {
+    GridK<T> g = gridk<T>(c, l);
+    if (c->opts.sc_relax != SIB_RELAX_SGS) {
+        KL(c, launch_sc_jacobi_A<T>(g, q, z, scale, s));
+        return;
+    }
+    KL(c, launch_sgs_pass<T>(g, false, -1, scale, q, z, s));
+    const int order[3] = {1, 1, 0};
+    for (int k = 0; k < 3; ++k) {
+        ib_apply<T>(c, l, z, s);
+        KL(c, launch_sgs_pass<T>(g, false, order[k], scale, q, z, s));
+    }
+}
+template <typename T>
+void precond_M(sib_ctx* c, int l, const T* q, T* z, T scale, cudaStream_t s) {
+    GridK<T> g = gridk<T>(c, l);
+    if (c->opts.sc_relax != SIB_RELAX_SGS) {
+        KL(c, launch_jacobi_M<T>(g, q, z, scale, s));
+        return;
+    }
+    KL(c, launch_sgs_pass<T>(g, true, -1, scale, q, z, s));
+    const int order[3] = {1, 1, 0};
+    for (int k = 0; k < 3; ++k) KL(c, launch_sgs_pass<T>(g, true, order[k], scale, q, z, s));
+}
+
+// out = At^{-1} q: cheb_iters Chebyshev iterations on A_IB, preconditioned by P_A, from 0.
 // Uses tv[0..3] of the level.
 template <typename T>
 void cheb_A(sib_ctx* c, int l, const T* q, T* out, cudaStream_t s) {
@@ -316,7 +346,7 @@ void cheb_A(sib_ctx* c, int l, const T* q, T* out, cudaStream_t s) {
     T* d = (T*)lv.p[pi].tv[3];
     GridK<T> g = gridk<T>(c, l);
     const ChebCoef k = cheb_coef(lv.lamA, c->opts.cheb_lo, c->opts.cheb_hi);
-    KL(c, launch_sc_jacobi_A<T>(g, q, d, (T)(1.0 / k.theta), s));
+    precond_A<T>(c, l, q, d, (T)(1.0 / k.theta), s);
     KL(c, launch_axpby<T>((T)1, d, (T)0, nullptr, out, nv, s));
     double rho = 1.0 / k.sigma;
     const int iters = c->opts.cheb_iters;
@@ -325,14 +355,14 @@ void cheb_A(sib_ctx* c, int l, const T* q, T* out, cudaStream_t s) {
         ib_apply<T>(c, l, d, s);
         KL(c, launch_apply_AIB<T>(g, d, t, s));
         KL(c, launch_axpby<T>((T)1, rr, (T)-1, t, rr, nv, s));
-        KL(c, launch_sc_jacobi_A<T>(g, rr, z, (T)1, s));
+        precond_A<T>(c, l, rr, z, (T)1, s);
         const double rn = 1.0 / (2.0 * k.sigma - rho);
         KL(c, launch_cheb_update<T>(z, d, out, (T)(rn * rho), (T)(2.0 * rn / k.delta), nv, s));
         rho = rn;
     }
 }
 
-// out = Mt^{-1} q: Chebyshev iterations on D At^{-1} G preconditioned by diag(D diag(A_IB)^{-1} G).
+// out = Mt^{-1} q: Chebyshev iterations on D At^{-1} G preconditioned by P_M (on D diag(A_IB)^{-1} G).
 // Uses tv[4..5] and tp[2..5].
 template <typename T>
 void cheb_M(sib_ctx* c, int l, const T* q, T* out, cudaStream_t s) {
@@ -347,7 +377,7 @@ void cheb_M(sib_ctx* c, int l, const T* q, T* out, cudaStream_t s) {
     T* md = (T*)lv.p[pi].tp[5];
     GridK<T> g = gridk<T>(c, l);
     const ChebCoef k = cheb_coef(lv.lamM, c->opts.cheb_lo, c->opts.cheb_hi);
-    KL(c, launch_jacobi_M<T>(g, q, d, (T)(1.0 / k.theta), s));
+    precond_M<T>(c, l, q, d, (T)(1.0 / k.theta), s);
     KL(c, launch_axpby<T>((T)1, d, (T)0, nullptr, out, np, s));
     double rho = 1.0 / k.sigma;
     const int iters = c->opts.cheb_iters;
@@ -357,7 +387,7 @@ void cheb_M(sib_ctx* c, int l, const T* q, T* out, cudaStream_t s) {
         cheb_A<T>(c, l, gq, ya, s);
         KL(c, launch_divergence<T>(g, ya, md, s));
         KL(c, launch_axpby<T>((T)1, rr, (T)-1, md, rr, np, s));
-        KL(c, launch_jacobi_M<T>(g, rr, z, (T)1, s));
+        precond_M<T>(c, l, rr, z, (T)1, s);
         const double rn = 1.0 / (2.0 * k.sigma - rho);
         KL(c, launch_cheb_update<T>(z, d, out, (T)(rn * rho), (T)(2.0 * rn / k.delta), np, s));
         rho = rn;
@@ -409,11 +439,14 @@ void sc_sweep_fused(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream
     KL(c, launch_sc_finish<T>(g, ka, x, y, gq2, dA2, dp, xo, s));
 }
 
-// xo = x + omega * Lt^{-1} (b - L x)
+// the fused SC sweep covers two Chebyshev iterations with Jacobi relaxation
+bool sc_fused(const sib_ctx* c) { return c->opts.cheb_iters == 2 && c->opts.sc_relax == SIB_RELAX_JACOBI; }
+
+// xo = x + omega * Lt^{-1} (b - L x)  (x == nullptr: zero initial guess; omega < 0: the option's)
 template <typename T>
-void sc_sweep(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream_t s) {
-    if (c->opts.cheb_iters == 2) {
-        sc_sweep_fused<T>(c, l, x, b, xo, s);
+void sc_sweep(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream_t s, double omega = -1.0) {
+    if (sc_fused(c)) {
+        sc_sweep_fused<T>(c, l, x, b, xo, s, omega);
         return;
     }
     Level& lv = c->L[l];
@@ -425,7 +458,10 @@ void sc_sweep(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream_t s) 
     T* sv = (T*)lv.p[pi].tp[0];
     T* dp = (T*)lv.p[pi].tp[1];
     GridK<T> g = gridk<T>(c, l);
-    apply_operator<T>(c, l, x, b, r, s);
+    if (x)
+        apply_operator<T>(c, l, x, b, r, s);
+    else
+        KL(c, launch_axpby<T>((T)1, b, (T)0, nullptr, r, nv + np, s));
     cheb_A<T>(c, l, r, y, s);                                        // y = At^{-1} r_u
     KL(c, launch_divergence<T>(g, y, sv, s));                        // s = r_p + D y
     KL(c, launch_axpby<T>((T)1, r + nv, (T)1, sv, sv, np, s));
@@ -433,10 +469,15 @@ void sc_sweep(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream_t s) 
     T* gq = (T*)lv.p[pi].tv[4];
     KL(c, launch_gradient<T>(g, dp, gq, s));                         // yy = At^{-1} G dp
     cheb_A<T>(c, l, gq, yy, s);
-    const T om = (T)c->opts.omega;
+    const T om = (T)(omega >= 0.0 ? omega : c->opts.omega);
     KL(c, launch_axpby<T>((T)1, y, (T)-1, yy, y, nv, s));            // du = y - yy
-    KL(c, launch_axpby<T>((T)1, x, om, y, xo, nv, s));               // xo_u = x_u + omega du
-    KL(c, launch_axpby<T>((T)1, x + nv, om, dp, xo + nv, np, s));    // xo_p = x_p + omega dp
+    if (x) {
+        KL(c, launch_axpby<T>((T)1, x, om, y, xo, nv, s));           // xo_u = x_u + omega du
+        KL(c, launch_axpby<T>((T)1, x + nv, om, dp, xo + nv, np, s));   // xo_p = x_p + omega dp
+    } else {
+        KL(c, launch_axpby<T>(om, y, (T)0, nullptr, xo, nv, s));
+        KL(c, launch_axpby<T>(om, dp, (T)0, nullptr, xo + nv, np, s));
+    }
 }
 
 // one smoothing sweep xo <- smooth(x, b)
@@ -463,7 +504,7 @@ bool small_ok(const sib_ctx* c) {
     if (!c->opts.fuse_small || c->lmax < 1) return false;
     const Level& lv = c->L[1];
     if (lv.N > 16) return false;
-    if (c->opts.smoother == SIB_SMOOTHER_SC && c->opts.cheb_iters != 2) return false;
+    if (c->opts.smoother == SIB_SMOOTHER_SC && !sc_fused(c)) return false;
     if (c->haveIB && lv.hnTiles > 0 && !lv.applyWindow) return false;
     const size_t smem = small_smem<T>(c);
     if (smem > (size_t)c->smemOptin) return false;
@@ -533,7 +574,7 @@ void wrapped_smooth(sib_ctx* c, int l, const T* x, const T* b, T* xo, int k, cud
         T* Vj = V + (size_t)j * n3;
         T* Zj = Z + (size_t)j * n3;
         if (c->opts.smoother == SIB_SMOOTHER_SC)
-            sc_sweep_fused<T>(c, l, nullptr, Vj, Zj, s, 1.0);
+            sc_sweep<T>(c, l, nullptr, Vj, Zj, s, 1.0);
         else
             KL(c, launch_vanka_zero<T>(g, Vj, Zj, s));
         ib_apply<T>(c, l, Zj, s);
@@ -586,8 +627,8 @@ T* vcycle_level(sib_ctx* c, int l, cudaStream_t s) {
         KL(c, launch_vanka_zero<T>(gridk<T>(c, l), b, xt, s));   // first sweep from w = 0
         std::swap(x, xt);
         k0 = 1;
-    } else if (c->opts.smoother == SIB_SMOOTHER_SC && c->opts.cheb_iters == 2 && c->opts.nu1 > 0) {
-        sc_sweep_fused<T>(c, l, nullptr, b, xt, s);   // first sweep from w = 0: residual = b
+    } else if (c->opts.smoother == SIB_SMOOTHER_SC && c->opts.nu1 > 0) {
+        sc_sweep<T>(c, l, nullptr, b, xt, s);   // first sweep from w = 0: residual = b
         std::swap(x, xt);
         k0 = 1;
     } else {
@@ -773,7 +814,13 @@ void power_A_enqueue(sib_ctx* c, int l, int slot, cudaStream_t s) {
     KL(c, launch_scale(v, c->scal, slot, nv, s));
     for (int it = 0; it < c->opts.power_iters; ++it) {
         ib_apply<double>(c, l, v, s);
-        KL(c, launch_power_A<double>(g, v, w, s));
+        if (c->opts.sc_relax == SIB_RELAX_SGS) {   // w = P_A A_IB v
+            double* t = (double*)lv.p[0].tv[0];
+            KL(c, launch_apply_AIB<double>(g, v, t, s));
+            precond_A<double>(c, l, t, w, 1.0, s);
+        } else {
+            KL(c, launch_power_A<double>(g, v, w, s));
+        }
         dot_into(c, w, w, nv, c->scal + slot, s);
         KL(c, launch_scale(w, c->scal, slot, nv, s));
         std::swap(v, w);
@@ -794,7 +841,7 @@ void power_M_enqueue(sib_ctx* c, int l, int slot, cudaStream_t s) {
     dot_into(c, v, v, np, c->scal + slot, s);
     KL(c, launch_scale(v, c->scal, slot, np, s));
     for (int it = 0; it < c->opts.power_iters; ++it) {
-        if (c->opts.cheb_iters == 2) {
+        if (sc_fused(c)) {
             KL(c, launch_power_Mstart<double>(g, ka, v, gq, dA, s));
             ib_apply<double>(c, l, dA, s);
             KL(c, launch_sc_chebA<double>(g, ka, gq, dA, ya, s));
@@ -803,7 +850,7 @@ void power_M_enqueue(sib_ctx* c, int l, int slot, cudaStream_t s) {
             KL(c, launch_gradient<double>(g, v, gq, s));
             cheb_A<double>(c, l, gq, ya, s);
             KL(c, launch_divergence<double>(g, ya, md, s));
-            KL(c, launch_jacobi_M<double>(g, md, w, 1.0, s));
+            precond_M<double>(c, l, md, w, 1.0, s);
         }
         dot_into(c, w, w, np, c->scal + slot, s);
         KL(c, launch_scale(w, c->scal, slot, np, s));
@@ -1486,6 +1533,7 @@ void sib_default_opts(sib_opts* o) {
     o->use_graphs = 1;
     o->fuse_small = 1;
     o->smooth_krylov = 0;
+    o->sc_relax = SIB_RELAX_JACOBI;
 }
 
 static void resolve_opts(sib_opts* o) {
@@ -1661,10 +1709,12 @@ int sib_set_options(sib_ctx* c, const sib_opts* o) {
         n.nu1 + n.nu2 > 64 || n.cheb_iters < 1 || n.cheb_iters > 16 || !(n.cheb_lo > 0) || !(n.cheb_hi > n.cheb_lo) ||
         n.power_iters < 1 || n.power_iters > 1000 || !(n.rtol >= 0) || n.max_it < 1 || n.max_it > 100000 ||
         n.restart < 1 || n.restart > 100 || (n.fuse_small != 0 && n.fuse_small != 1) ||
-        (n.smooth_krylov != 0 && n.smooth_krylov != 1) || (n.smooth_krylov && (n.nu1 > WRAP_MAXK || n.nu2 > WRAP_MAXK)))
+        (n.smooth_krylov != 0 && n.smooth_krylov != 1) || (n.smooth_krylov && (n.nu1 > WRAP_MAXK || n.nu2 > WRAP_MAXK)) ||
+        (n.sc_relax != SIB_RELAX_JACOBI && n.sc_relax != SIB_RELAX_SGS))
         throw SibError(SIB_ERR_ARG, "option out of range");
     resolve_opts(&n);
-    const bool smootherChanged = n.smoother != c->opts.smoother;
+    const bool smootherChanged = n.smoother != c->opts.smoother ||
+                                 (n.smoother == SIB_SMOOTHER_SC && n.sc_relax != c->opts.sc_relax);
     c->opts = n;
     if (n.smooth_krylov) alloc_wrap_bufs(c);
     if (smootherChanged && n.smoother == SIB_SMOOTHER_SC) c->fluidDirty = true;   // needs eigen estimates

@@ -27,6 +27,8 @@ ERROR_NAMES = {v: k for k, v in dict(globals()).items() if k.startswith("SIB_ERR
 
 SMOOTHER_VANKA = 0
 SMOOTHER_SC = 1
+RELAX_JACOBI = 0
+RELAX_SGS = 1
 PREC_FP64 = 0
 PREC_FP32 = 1
 MAX_LEVELS = 12
@@ -49,7 +51,7 @@ class SibOpts(ctypes.Structure):
         ("cheb_iters", ctypes.c_int), ("cheb_lo", ctypes.c_double), ("cheb_hi", ctypes.c_double),
         ("power_iters", ctypes.c_int), ("vcycle_fp32", ctypes.c_int), ("rtol", ctypes.c_double),
         ("max_it", ctypes.c_int), ("restart", ctypes.c_int), ("add_SKXn", ctypes.c_int), ("use_graphs", ctypes.c_int),
-        ("fuse_small", ctypes.c_int), ("smooth_krylov", ctypes.c_int),
+        ("fuse_small", ctypes.c_int), ("smooth_krylov", ctypes.c_int), ("sc_relax", ctypes.c_int),
     ]
 
 
