@@ -38,7 +38,7 @@ class Level:
 class Hierarchy:
     def __init__(self, prob, n_min=8, smoother="vanka", omega=None, nu1=2, nu2=2,
                  cheb_iters=2, cheb_lo=0.1, cheb_hi=1.1, power_iters=10, lam_override=None, krylov=False,
-                 sc_relax="jacobi"):
+                 sc_relax="jacobi", box=4, overlap=1):
         N = prob.N
         if N < n_min or (N // n_min) * n_min != N or (N // n_min) & (N // n_min - 1):
             raise ValueError("N must be n_min * 2^k")
@@ -52,6 +52,8 @@ class Hierarchy:
         # "jacobi" or "sgs" (symmetric red-black Gauss-Seidel)
         self.sc_relax = sc_relax
         self.omega = 1.0 if krylov else ((0.8 if smoother == "vanka" else 1.0) if omega is None else omega)
+        # smoother "ras": box subdomains of box x box cells with `overlap` cells on each side
+        self.box, self.overlap = box, overlap
         self.nu1, self.nu2 = nu1, nu2
         self.cheb_iters, self.cheb_lo, self.cheb_hi = cheb_iters, cheb_lo, cheb_hi
         self.power_iters = power_iters
@@ -79,6 +81,9 @@ class Hierarchy:
             if smoother == "vanka":
                 lev.dofs = smoothers.vanka_patch_dofs(lev.N)
                 lev.patches = smoothers.vanka_patches(lev.L, lev.dofs)
+            elif smoother == "ras":
+                lev.boxes = smoothers.ras_boxes(lev.N, box, overlap)
+                lev.factors = smoothers.ras_factors(lev.L, lev.boxes)
             else:
                 lev.dA = lev.AIB.diagonal()
                 PA, PM, lev.dM = smoothers.sc_preconditioners(lev.AIB, lev.G, lev.D, lev.dA, sc_relax)
@@ -100,6 +105,8 @@ class Hierarchy:
         lev = self.levels[l]
         if self.smoother == "vanka":
             return smoothers.vanka_sweep(lev.L, lev.dofs, lev.patches, x, b, self.omega)
+        if self.smoother == "ras":
+            return smoothers.ras_sweep(lev.L, lev.boxes, lev.factors, x, b, self.omega)
         return smoothers.sc_sweep(lev.L, lev.G, lev.D, lev.AIB, lev.dA, lev.dM, lev.lamA, lev.lamM,
                                   x, b, self.omega, self.cheb_iters, self.cheb_lo, self.cheb_hi, self.sc_relax)
 
@@ -112,6 +119,8 @@ class Hierarchy:
         for _ in range(sweeps):
             if self.smoother == "vanka":
                 x = smoothers.vanka_sweep(lev.L, lev.dofs, lev.patches, x, b, self.omega)
+            elif self.smoother == "ras":
+                x = smoothers.ras_sweep(lev.L, lev.boxes, lev.factors, x, b, self.omega)
             else:
                 x = smoothers.sc_sweep(lev.L, lev.G, lev.D, lev.AIB, lev.dA, lev.dM, lev.lamA, lev.lamM,
                                        x, b, self.omega, self.cheb_iters, self.cheb_lo, self.cheb_hi,

@@ -23,6 +23,11 @@ Gauss-Seidel.  Two relaxations are provided:
   the IB couplings [S K J] also link faces of one colour, and those enter from the start of the
   pass.
 
+Restricted additive Schwarz over boxes (Alg. 2 with b x b subdomains and overlap o, the paper's
+Vanka-type smoother): every box solves its local saddle-point problem (all faces of its extended
+cells and their pressures) on the current residual; each dof takes the correction of the box that
+owns it (no weights: the owned sets partition the dofs).
+
 Chebyshev acceleration follows the textbook recurrence (Saad, Iterative Methods for Sparse
 Linear Systems, Algorithm 12.1) with x_0 = 0 on the interval [lo, hi] * lambda_max, where
 lambda_max of the Jacobi-preconditioned operator is estimated by a fixed number of power
@@ -64,6 +69,63 @@ def vanka_sweep(L, dofs, patches, x, b, omega):
     delta = np.linalg.solve(patches, r[dofs][..., None])[..., 0]
     dx = np.zeros_like(x)
     np.add.at(dx, dofs.ravel(), (delta * VANKA_WEIGHTS).ravel())
+    return x + omega * dx
+
+
+def ras_boxes(N, b, o):
+    """Dof lists of the box subdomains of the restricted additive Schwarz smoother (Sec. 3.3, RAS).
+
+    The cells are tiled by b x b core boxes, box (I, J) covering cells I b .. I b + b - 1 by
+    J b .. J b + b - 1; its subdomain extends the core by o cells on each side (periodic), e = b + 2o
+    cells wide.  The subdomain's dofs are every face of its e x e cells and their pressures:
+        u(i, j), i = I b - o .. I b + b + o (e + 1 columns), j over the e rows,
+        v(i, j), i over the e columns, j = J b - o .. J b + b + o (e + 1 rows),
+        p(i, j) over the e x e cells,
+    in that order, row-major within each.  A dof is owned by the box whose core holds it: u(i, j) and
+    v(i, j) belong to cell (i, j) (its left and bottom faces), p(i, j) to the cell; every dof has one
+    owner.  Returns [(dofs, owned_mask)] over the boxes, row-major in (J, I)."""
+    if N % b or b + 2 * o + 1 > N:
+        raise ValueError("b must divide N and the subdomain must not wrap onto itself")
+    n, e = N * N, b + 2 * o
+    out = []
+    for J in range(N // b):
+        for I in range(N // b):
+            i0, j0 = I * b - o, J * b - o
+            core_i = lambda ii: I * b <= ii < I * b + b
+            core_j = lambda jj: J * b <= jj < J * b + b
+            dofs, own = [], []
+            for jj in range(j0, j0 + e):
+                for ii in range(i0, i0 + e + 1):
+                    dofs.append(cell_index(N, ii, jj))
+                    own.append(core_i(ii) and core_j(jj))
+            for jj in range(j0, j0 + e + 1):
+                for ii in range(i0, i0 + e):
+                    dofs.append(n + cell_index(N, ii, jj))
+                    own.append(core_i(ii) and core_j(jj))
+            for jj in range(j0, j0 + e):
+                for ii in range(i0, i0 + e):
+                    dofs.append(2 * n + cell_index(N, ii, jj))
+                    own.append(core_i(ii) and core_j(jj))
+            out.append((np.array(dofs), np.array(own)))
+    return out
+
+
+def ras_factors(L, boxes):
+    """LU factors of every subdomain operator L_k = R_k L R_k^T (dense)."""
+    import scipy.linalg as sla
+    Ld = L.tocsr()
+    return [sla.lu_factor(Ld[d][:, d].toarray()) for d, _ in boxes]
+
+
+def ras_sweep(L, boxes, factors, x, b, omega):
+    """x <- x + omega sum_k Rt_k^T L_k^{-1} R_k (b - L x): every subdomain solves its local problem on
+    the residual, and each dof takes the correction of the box that owns it."""
+    import scipy.linalg as sla
+    r = b - L @ x
+    dx = np.zeros_like(x)
+    for (d, own), f in zip(boxes, factors):
+        delta = sla.lu_solve(f, r[d])
+        dx[d[own]] = delta[own]
     return x + omega * dx
 
 

@@ -587,3 +587,72 @@ def test_sc_with_multicolour_gs_is_a_convergent_preconditioner():
         x, it, hist, conv = krylov.fgmres(lambda z: L @ z, H.vcycle, b, rtol=1e-8, max_it=100, restart=100,
                                           project=lambda v: system.project(v, 32, prob.rho))
         assert conv, it
+
+
+# ------------------------------------------------------ box RAS smoother (Sec. 3.3, Alg. 2 with boxes)
+def test_ras_one_cell_boxes_are_restricted_vanka():
+    """b = 1, o = 0: each subdomain is the 5-dof cell patch, and each face takes the correction of the
+    cell to its right (u) or above (v): the Vanka patch solve with weights (1, 0, 1, 0, 1)."""
+    prob = I.thin_ellipse_re(16, kappa=1e3)
+    L = system.operator_of(prob).tocsr()
+    N = 16
+    rng = np.random.default_rng(9)
+    x, bb = rng.standard_normal((2, 3 * N * N))
+    boxes = smoothers.ras_boxes(N, 1, 0)
+    got = smoothers.ras_sweep(L, boxes, smoothers.ras_factors(L, boxes), x, bb, 0.9)
+    dofs = smoothers.vanka_patch_dofs(N)
+    P = smoothers.vanka_patches(L, dofs)
+    r = bb - L @ x
+    delta = np.linalg.solve(P, r[dofs][..., None])[..., 0]
+    dx = np.zeros_like(x)
+    np.add.at(dx, dofs.ravel(), (delta * np.array([1.0, 0.0, 1.0, 0.0, 1.0])).ravel())
+    np.testing.assert_allclose(got, x + 0.9 * dx, rtol=0, atol=1e-10 * np.abs(x + 0.9 * dx).max())
+
+
+@pytest.mark.parametrize("b,o", [(4, 1), (2, 2), (4, 0), (2, 1)])
+def test_ras_subdomains_are_the_geometric_boxes(b, o):
+    """Each subdomain's dofs are exactly the faces and cell centres inside its extended square (faces on
+    its edges included), periodically; it owns those inside the core square (left and bottom edges
+    included); the owned sets partition all dofs.  Checked from dof positions, not index loops."""
+    N = 16
+    h = 1.0 / N
+    idx = np.arange(N * N)
+    i, j = idx % N, idx // N
+    pos = [(i * h, (j + 0.5) * h), ((i + 0.5) * h, j * h), ((i + 0.5) * h, (j + 0.5) * h)]
+    owners = np.zeros(3 * N * N, dtype=int)
+    for k, (d, own) in enumerate(smoothers.ras_boxes(N, b, o)):
+        I0, J0 = (k % (N // b)) * b, (k // (N // b)) * b
+        expect, expect_own = [], []
+        for comp, (px, py) in enumerate(pos):
+            rx = np.round(((px - (I0 - o) * h) % 1.0) / h * 2) / 2   # offsets in cells from the box corner
+            ry = np.round(((py - (J0 - o) * h) % 1.0) / h * 2) / 2
+            inside = (rx <= b + 2 * o) & (ry <= b + 2 * o)
+            if comp == 0:
+                inside &= ry > 0
+            elif comp == 1:
+                inside &= rx > 0
+            else:
+                inside &= (rx > 0) & (ry > 0)
+            core = inside & (rx >= o) & (rx < o + b) & (ry >= o) & (ry < o + b)
+            expect += list(comp * N * N + idx[inside])
+            expect_own += list(comp * N * N + idx[core])
+        assert sorted(d.tolist()) == sorted(expect)
+        assert sorted(d[own].tolist()) == sorted(expect_own)
+        owners[d[own]] += 1
+    assert (owners == 1).all()
+
+
+def test_ras_fixed_point_and_convergent_vcycle():
+    """The exact solution is a fixed point of a RAS sweep; FGMRES with the RAS V-cycle (4 x 4 boxes,
+    overlap 1) converges to 1e-8, including the 32^2 disk at kappa = 1e6."""
+    prob = I.disk_stokes(32, kappa=1e6, seed=1)
+    L = system.operator_of(prob)
+    b = system.rhs(prob)
+    H = multigrid.Hierarchy(prob, smoother="ras", box=4, overlap=1)
+    xs, _ = system.solve_direct(L, b, 32, prob.rho)
+    lev = H.fine
+    y = smoothers.ras_sweep(lev.L, lev.boxes, lev.factors, xs, b, 1.0)
+    assert np.abs(y - xs).max() <= 1e-9 * np.abs(xs).max()
+    x, it, hist, conv = krylov.fgmres(lambda z: L @ z, H.vcycle, b, rtol=1e-8, max_it=100, restart=100,
+                                      project=lambda v: system.project(v, 32, prob.rho))
+    assert conv, it
