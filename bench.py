@@ -222,6 +222,29 @@ def sc_gauss_seidel_cases(S, g, w, kap_dev, sib, torch, stream, smooth_krylov):
     return {"ms_per_solve": round(e0.elapsed_time(e1) / len(KAPPAS), 4), "cases": records}
 
 
+def box_ras_cases(S, g, w, kap_dev, sib, torch, stream, box=4, overlap=1):
+    """The step's kappa sweep with the box RAS smoother (Sec. 3.3, Alg. 2 with box x box subdomains and
+    `overlap` cells of overlap; FP32 V-cycle, undamped)."""
+    S.set_options(smoother=sib.SMOOTHER_RAS, vcycle_fp32=1, omega=-1.0, smooth_krylov=0, box=box,
+                  box_overlap=overlap)
+    records = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for kap in KAPPAS:
+        S.set_stiffness(kap_dev[kap])
+        S.setup()
+        S.solve(g, w, allow_unconverged=True)
+        d = S.stats.as_dict()
+        records.append(dict(kappa=kap, iterations=d["iterations"], converged=d["converged"],
+                            rel_residual=d["rel_residual"], setup_ms=round(d["setup_ms"], 4),
+                            solve_ms=round(d["solve_ms"], 4)))
+    e1.record(stream)
+    e1.synchronize()
+    S.set_options(smoother=sib.SMOOTHER_VANKA, box=4, box_overlap=1)
+    return {"box": box, "overlap": overlap, "ms_per_solve": round(e0.elapsed_time(e1) / len(KAPPAS), 4),
+            "cases": records}
+
+
 def e2e_step(S, g_host, w_host, kap_host, kap_dev, sib, torch):
     """Through the host-buffer call: stiffness uploaded from pinned memory, g in, w out."""
     for sm in SMOOTHERS:
@@ -271,6 +294,22 @@ def large_vcycle(sib, torch, reps=20, N=None):
         ms, by = S.time_kernel(name, lmax, True, reps=20)
         torch.cuda.nvtx.range_pop()
         out["kernels"][name] = {"ms": round(ms, 5), "bytes": by, "gbs": round(by / (ms * 1e-3) / 1e9, 1)}
+    # the box RAS smoother (4 x 4 boxes, overlap 1) on the same grid: V-cycle and correction kernel
+    S.set_options(smoother=sib.SMOOTHER_RAS, box=4, box_overlap=1, omega=-1.0)
+    S.setup()
+    for _ in range(3):
+        S.vcycle(b, z)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        S.vcycle(b, z)
+    e1.record()
+    torch.cuda.synchronize()
+    out["vcycle_ms_ras"] = round(e0.elapsed_time(e1) / reps, 4)
+    torch.cuda.nvtx.range_push("roofline_large_ras")
+    ms, by = S.time_kernel("ras", lmax, True, reps=20)
+    torch.cuda.nvtx.range_pop()
+    out["kernels"]["ras"] = {"ms": round(ms, 5), "bytes": by, "gbs": round(by / (ms * 1e-3) / 1e9, 1)}
     S.close()
     return out
 
@@ -396,6 +435,9 @@ def run_native(args):
     # SC with Gauss-Seidel (the paper's relaxation) instead of Jacobi inside its Chebyshev iterations
     sc_gs = {"damped": sc_gauss_seidel_cases(S, g, w, kap_dev, sib, torch, stream, 0),
              "wrapped": sc_gauss_seidel_cases(S, g, w, kap_dev, sib, torch, stream, 1)}
+    # the paper's box Vanka smoother: restricted additive Schwarz over 4 x 4 and 2 x 2 boxes, overlap 1
+    ras = [box_ras_cases(S, g, w, kap_dev, sib, torch, stream, 4, 1),
+           box_ras_cases(S, g, w, kap_dev, sib, torch, stream, 2, 1)]
 
     # end to end through the host-buffer C call, pinned host memory
     g_host = torch.as_tensor(prob.g).pin_memory().numpy()
@@ -446,6 +488,7 @@ def run_native(args):
             "cases": records, "fp64_vcycle": {"ms_per_solve": round(fp64_ms, 4), "cases": fp64_records},
             "krylov_smoothing": {"ms_per_solve": round(kry_ms, 4), "cases": kry_records},
             "sc_gauss_seidel": sc_gs,
+            "box_ras": ras,
             "roofline": roofline, "time_loop": tloop, "vcycle_large": large, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk, "wall_s": round(wall, 3),
         }

@@ -53,6 +53,7 @@ extern "C" {
 
 #define SIB_SMOOTHER_VANKA 0       /* additive per-cell Vanka (Alg. 2 with one-cell subdomains)     */
 #define SIB_SMOOTHER_SC    1       /* Schur-complement smoother (Eq. approx-fact-Stokes-IB)         */
+#define SIB_SMOOTHER_RAS   2       /* restricted additive Schwarz over box subdomains (Alg. 2, boxes) */
 
 #define SIB_PREC_FP64 0
 #define SIB_PREC_FP32 1
@@ -83,6 +84,8 @@ typedef struct {
     int    sc_relax;      /* SC: point relaxation preconditioning both Chebyshev iterations (Sec. 3.3,
                              SC smoothing): SIB_RELAX_JACOBI (diagonal, default) or SIB_RELAX_SGS (one
                              symmetric red-black Gauss-Seidel sweep from zero, colours 0, 1, 1, 0)    */
+    int    box;           /* RAS: cells per box side b, 1, 2 or 4 (4)                                */
+    int    box_overlap;   /* RAS: overlap o in cells on each side, b + 2 o <= 6 (1)                  */
 } sib_opts;
 
 #define SIB_RELAX_JACOBI 0
@@ -187,6 +190,7 @@ int sib_advance_markers(sib_ctx* ctx, const double* w, double* X_next, void* str
 #define SIB_KERNEL_INTERP    3   /* interpolation of the level                                       */
 #define SIB_KERNEL_RESTRICT  4   /* restriction of a residual from `level` to level-1                 */
 #define SIB_KERNEL_PROLONG   5   /* prolongation-correction from level-1 to `level`                   */
+#define SIB_KERNEL_RAS       6   /* box RAS correction from a residual (needs the RAS smoother's setup) */
 /* Times `reps` back-to-back launches of one kernel of the V-cycle on `level` (operands: the
  * level's own work buffers, zero-filled first) between two CUDA events recorded on `stream`,
  * and returns the mean device time of one launch (*ms) and the algorithmic DRAM bytes one

@@ -1,0 +1,301 @@
+// Restricted additive Schwarz smoother over box subdomains (Sec. 3.3, Alg. 2 with b x b boxes and
+// overlap o): every box solves its local saddle-point problem on the residual, and each dof takes
+// the correction of the box whose core owns it.
+//
+// Subdomain of box (I, J): the e x e cells from (I b - o, J b - o), e = b + 2o (periodic), with
+// all their faces and pressures, in the order
+//   u(i0 + ii, j0 + jj), jj < e, ii <= e;   v(i0 + ii, j0 + jj), jj <= e, ii < e;   p, jj < e, ii < e
+// (row-major within each); ne = 3 e^2 + 2 e dofs.  Owned dofs: the u, v and p of the core cells
+// (o <= ii, jj < o + b), nown = 3 b^2, ordered u, v, p and row-major.
+//
+// Set-up (FP64): the local operator L_k = R_k L R_k^T is assembled in shared memory from the
+// stencil (A, G, -D) and the IB windows, inverted by Gauss-Jordan with partial pivoting, and the
+// owned rows of the inverse are stored (column-major, FP64 and FP32).  Boxes whose subdomain meets
+// no IB window all have the same operator (the grid is uniform and periodic): one shared inverse
+// per level serves them.
+#include "sib_internal.h"
+
+namespace sib {
+
+namespace {
+
+struct RasGeo {
+    int N, b, o, e, ne, nown, nbs;   // nbs = N / b boxes per side
+};
+
+__host__ __device__ inline RasGeo ras_geo(int N, int b, int o) {
+    RasGeo g;
+    g.N = N;
+    g.b = b;
+    g.o = o;
+    g.e = b + 2 * o;
+    g.ne = 3 * g.e * g.e + 2 * g.e;
+    g.nown = 3 * b * b;
+    g.nbs = N / b;
+    return g;
+}
+
+// local dof q -> (component, ii, jj) in box coordinates
+__device__ __forceinline__ void ras_dof(const RasGeo& G, int q, int& comp, int& ii, int& jj) {
+    const int e = G.e, nu = e * (e + 1);
+    if (q < nu) {
+        comp = 0;
+        jj = q / (e + 1);
+        ii = q - jj * (e + 1);
+    } else if (q < 2 * nu) {
+        comp = 1;
+        q -= nu;
+        jj = q / e;
+        ii = q - jj * e;
+    } else {
+        comp = 2;
+        q -= 2 * nu;
+        jj = q / e;
+        ii = q - jj * e;
+    }
+}
+// (component, ii, jj) -> local dof, or -1 outside the subdomain
+__device__ __forceinline__ int ras_index(const RasGeo& G, int comp, int ii, int jj) {
+    const int e = G.e, nu = e * (e + 1);
+    if (comp == 0) return (ii >= 0 && ii <= e && jj >= 0 && jj < e) ? jj * (e + 1) + ii : -1;
+    if (comp == 1) return (ii >= 0 && ii < e && jj >= 0 && jj <= e) ? nu + jj * e + ii : -1;
+    return (ii >= 0 && ii < e && jj >= 0 && jj < e) ? 2 * nu + jj * e + ii : -1;
+}
+// owned dof r -> local dof
+__device__ __forceinline__ int ras_owned(const RasGeo& G, int r) {
+    const int bb = G.b * G.b, comp = r / bb, rem = r - comp * bb;
+    return ras_index(G, comp, G.o + rem % G.b, G.o + rem / G.b);
+}
+
+// window slot of the tile holding face (i, j) of the level (-1: no IB entries in that row)
+__device__ __forceinline__ int face_slot(const RasIB& ib, int i, int j) {
+    if (!ib.slotOf) return -1;
+    return ib.slotOf[(j / ib.ty) * ib.ntx + i / ib.tx];
+}
+
+// Box classification: flag[k] = 1 if any face of box k's subdomain lies in a tile with a window.
+__global__ void k_ras_classify(RasGeo G, RasIB ib, int* __restrict__ list, int* __restrict__ count) {
+    const int k = blockIdx.x;
+    const int I = k % G.nbs, J = k / G.nbs, m = G.N - 1;
+    const int i0 = I * G.b - G.o, j0 = J * G.b - G.o;
+    int hit = 0;
+    for (int t = threadIdx.x; t < (G.e + 1) * (G.e + 1); t += blockDim.x) {
+        const int ii = t % (G.e + 1), jj = t / (G.e + 1);
+        if (face_slot(ib, (i0 + ii) & m, (j0 + jj) & m) >= 0) hit = 1;
+    }
+    hit = __syncthreads_or(hit);
+    if (hit && threadIdx.x == 0) list[atomicAdd(count, 1)] = k;
+}
+
+// Assembles L_k in shared memory (row-major, ne x ne), inverts it in place and stores the owned rows
+// of the inverse.  Block 0 builds the shared IB-free operator (box 0 without IB terms); block s > 0
+// builds box list[s - 1] with its IB terms.  info != 0 on a zero pivot.
+__global__ void __launch_bounds__(256) k_ras_setup(RasGeo G, RasIB ib, double a0, double c, double inv_h, double dt,
+                                                  const int* __restrict__ list, double* __restrict__ inv64,
+                                                  float* __restrict__ inv32, int* __restrict__ info) {
+    extern __shared__ double smem_ras[];
+    const int n = G.ne, tid = threadIdx.x, nt = blockDim.x;
+    double* A = smem_ras;                 // n x n
+    double* colk = A + n * n;             // n
+    double* redv = colk + n;              // 32
+    int* redi = reinterpret_cast<int*>(redv + 32);   // 32
+    int* perm = redi + 32;                // n
+    const bool withIB = blockIdx.x > 0;
+    const int k = withIB ? list[blockIdx.x - 1] : 0;
+    const int I = k % G.nbs, J = k / G.nbs, m = G.N - 1;
+    const int i0 = I * G.b - G.o, j0 = J * G.b - G.o;
+    const int per = ib.tx * ib.ty;
+    for (int t = tid; t < n * n; t += nt) A[t] = 0.0;
+    __syncthreads();
+    for (int q = tid; q < n; q += nt) {   // row q of L_k
+        int comp, ii, jj;
+        ras_dof(G, q, comp, ii, jj);
+        double* row = A + (size_t)q * n;
+        if (comp < 2) {
+            row[q] = a0;
+            const int nb[4][2] = {{ii + 1, jj}, {ii - 1, jj}, {ii, jj + 1}, {ii, jj - 1}};
+            for (int s2 = 0; s2 < 4; ++s2) {
+                const int col = ras_index(G, comp, nb[s2][0], nb[s2][1]);
+                if (col >= 0) row[col] -= c;
+            }
+            // G p: u(i, j) -> (p(i, j) - p(i-1, j)) / h;  v(i, j) -> (p(i, j) - p(i, j-1)) / h
+            const int pc = ras_index(G, 2, ii, jj);
+            const int pm = comp == 0 ? ras_index(G, 2, ii - 1, jj) : ras_index(G, 2, ii, jj - 1);
+            if (pc >= 0) row[pc] += inv_h;
+            if (pm >= 0) row[pm] -= inv_h;
+            if (withIB) {   // -dt B(f, g) for g of the same component in the subdomain (window offsets)
+                const int gi = (i0 + ii) & m, gj = (j0 + jj) & m;
+                const int slot = face_slot(ib, gi, gj);
+                if (slot >= 0) {
+                    const double* w = ib.win + ((size_t)(slot * 2 + comp) * WIN_SIZE) * per;
+                    const int qt = (gj % ib.ty) * ib.tx + (gi % ib.tx);
+                    for (int dj = -WR; dj <= WR; ++dj)
+                        for (int di = -WR; di <= WR; ++di) {
+                            const int col = ras_index(G, comp, ii + di, jj + dj);
+                            if (col >= 0) row[col] -= dt * w[(size_t)((dj + WR) * WD + (di + WR)) * per + qt];
+                        }
+                }
+            }
+        } else {   // -D u: -(u(i+1, j) - u(i, j) + v(i, j+1) - v(i, j)) / h
+            row[ras_index(G, 0, ii + 1, jj)] -= inv_h;
+            row[ras_index(G, 0, ii, jj)] += inv_h;
+            row[ras_index(G, 1, ii, jj + 1)] -= inv_h;
+            row[ras_index(G, 1, ii, jj)] += inv_h;
+        }
+    }
+    __syncthreads();
+    // in-place Gauss-Jordan with partial (row) pivoting: A <- (P A)^{-1}
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    for (int kk = 0; kk < n; ++kk) {
+        double best = -1.0;
+        int bi = kk;
+        for (int i = kk + tid; i < n; i += nt) {
+            const double v = fabs(A[(size_t)i * n + kk]);
+            if (v > best) {
+                best = v;
+                bi = i;
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+            if (ov > best || (ov == best && oi < bi)) {
+                best = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            redv[wid] = best;
+            redi[wid] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double bv = redv[0];
+            int bx = redi[0];
+            for (int w2 = 1; w2 < nw; ++w2)
+                if (redv[w2] > bv || (redv[w2] == bv && redi[w2] < bx)) {
+                    bv = redv[w2];
+                    bx = redi[w2];
+                }
+            perm[kk] = bx;
+            if (!(bv > 0.0)) atomicExch(info, 1);
+        }
+        __syncthreads();
+        const int p = perm[kk];
+        if (p != kk)
+            for (int j = tid; j < n; j += nt) {
+                const double t = A[(size_t)kk * n + j];
+                A[(size_t)kk * n + j] = A[(size_t)p * n + j];
+                A[(size_t)p * n + j] = t;
+            }
+        __syncthreads();
+        const double piv = A[(size_t)kk * n + kk];
+        const double pinv = piv != 0.0 ? 1.0 / piv : 0.0;
+        for (int i = tid; i < n; i += nt) colk[i] = A[(size_t)i * n + kk];
+        __syncthreads();
+        for (int j = tid; j < n; j += nt) A[(size_t)kk * n + j] = (j == kk ? 1.0 : A[(size_t)kk * n + j]) * pinv;
+        __syncthreads();
+        for (int t = tid; t < n * n; t += nt) {
+            const int i = t / n, j = t - i * n;
+            if (i == kk) continue;
+            A[t] = (j == kk ? 0.0 : A[t]) - colk[i] * A[(size_t)kk * n + j];
+        }
+        __syncthreads();
+    }
+    // (P A)^{-1} P = A^{-1}: swap columns back in reverse order of the row interchanges
+    for (int kk = n - 1; kk >= 0; --kk) {
+        const int p = perm[kk];
+        if (p != kk)
+            for (int i = tid; i < n; i += nt) {
+                const double t = A[(size_t)i * n + kk];
+                A[(size_t)i * n + kk] = A[(size_t)i * n + p];
+                A[(size_t)i * n + p] = t;
+            }
+        __syncthreads();
+    }
+    // owned rows, column-major: out[q * nown + r] = A^{-1}(owned(r), q)
+    const size_t base = (size_t)blockIdx.x * n * G.nown;
+    for (int t = tid; t < n * G.nown; t += nt) {
+        const int q = t / G.nown, r = t - q * G.nown;
+        const double v = A[(size_t)ras_owned(G, r) * n + q];
+        inv64[base + t] = v;
+        inv32[base + t] = (float)v;
+    }
+}
+
+// One RAS correction: xo(owned) = x(owned) + omega (Inv_k r_k)(owned) for every box k, with r the
+// residual (x == nullptr: zero initial guess, xo = omega Inv r).  slot[k] < 0: the shared inverse.
+template <typename T>
+__global__ void k_ras_apply(RasGeo G, const int* __restrict__ slotOfBox, const T* __restrict__ inv, T omega,
+                            const T* __restrict__ r, const T* x, T* xo) {
+    extern __shared__ unsigned char smem_raw[];
+    T* rb = reinterpret_cast<T*>(smem_raw);
+    pdl_entry();
+    const int k = blockIdx.x;
+    const int I = k % G.nbs, J = k / G.nbs, N = G.N, n = N * N, m = N - 1;
+    const int i0 = I * G.b - G.o, j0 = J * G.b - G.o;
+    for (int q = threadIdx.x; q < G.ne; q += blockDim.x) {
+        int comp, ii, jj;
+        ras_dof(G, q, comp, ii, jj);
+        rb[q] = r[(size_t)comp * n + ((j0 + jj) & m) * N + ((i0 + ii) & m)];
+    }
+    __syncthreads();
+    const int s = slotOfBox ? slotOfBox[k] : -1;
+    const T* M = inv + (size_t)(s + 1) * G.ne * G.nown;
+    for (int rr = threadIdx.x; rr < G.nown; rr += blockDim.x) {
+        T acc = T(0);
+        for (int q = 0; q < G.ne; ++q) acc += M[(size_t)q * G.nown + rr] * rb[q];
+        const int bb = G.b * G.b, comp = rr / bb, rem = rr - comp * bb;
+        const int gi = I * G.b + rem % G.b, gj = J * G.b + rem / G.b;
+        const size_t d = (size_t)comp * n + gj * N + gi;
+        xo[d] = (x ? x[d] : T(0)) + omega * acc;
+    }
+}
+
+__global__ void k_box_slots(const int* __restrict__ list, const int* __restrict__ count, int* __restrict__ slotOfBox) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < *count) slotOfBox[list[s]] = s;
+}
+
+}  // namespace
+
+size_t ras_setup_smem(int b, int o) {
+    const RasGeo G = ras_geo(16, b, o);
+    return sizeof(double) * ((size_t)G.ne * G.ne + G.ne + 32) + sizeof(int) * (32 + G.ne);
+}
+int ras_ne(int b, int o) { return ras_geo(16, b, o).ne; }
+
+void launch_ras_classify(int N, int b, int o, const RasIB& ib, int* list, int* count, cudaStream_t s) {
+    const RasGeo G = ras_geo(N, b, o);
+    cudaMemsetAsync(count, 0, sizeof(int), s);
+    if (!ib.slotOf) return;
+    k_ras_classify<<<G.nbs * G.nbs, 128, 0, s>>>(G, ib, list, count);
+}
+
+void launch_box_slots(int nboxes, const int* list, const int* count, int* slotOfBox, cudaStream_t s) {
+    cudaMemsetAsync(slotOfBox, 0xff, sizeof(int) * (size_t)nboxes, s);
+    k_box_slots<<<(nboxes + 255) / 256, 256, 0, s>>>(list, count, slotOfBox);
+}
+
+void launch_ras_setup(int N, int b, int o, const RasIB& ib, double a0, double c, double inv_h, double dt,
+                      const int* list, int nIB, double* inv64, float* inv32, int* info, cudaStream_t s) {
+    const RasGeo G = ras_geo(N, b, o);
+    const size_t smem = ras_setup_smem(b, o);
+    cudaFuncSetAttribute(k_ras_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ras_setup<<<1 + nIB, 256, smem, s>>>(G, ib, a0, c, inv_h, dt, list, inv64, inv32, info);
+}
+
+template <typename T>
+void launch_ras_apply(int N, int b, int o, const int* slotOfBox, const T* inv, T omega, const T* r, const T* x, T* xo,
+                      cudaStream_t s) {
+    const RasGeo G = ras_geo(N, b, o);
+    const int threads = G.nown > 64 ? 128 : 64;
+    launch_pdl(k_ras_apply<T>, dim3(G.nbs * G.nbs), dim3(threads), sizeof(T) * G.ne, s, G, slotOfBox, inv, omega, r, x,
+               xo);
+}
+template void launch_ras_apply<float>(int, int, int, const int*, const float*, float, const float*, const float*,
+                                      float*, cudaStream_t);
+template void launch_ras_apply<double>(int, int, int, const int*, const double*, double, const double*,
+                                       const double*, double*, cudaStream_t);
+
+}  // namespace sib

@@ -108,6 +108,23 @@ struct IBK {
 };
 
 // ------------------------------------------------------------------------------------------
+// Box RAS smoother (kernels_ras.cu): where the level's IB windows live (slotOf == nullptr: no IB).
+struct RasIB {
+    const int* slotOf;       // tile -> window slot, -1 without IB entries
+    const double* win;       // FP64 windows of the level
+    int tx, ty, ntx;         // tile geometry of the level
+};
+size_t ras_setup_smem(int b, int o);
+int ras_ne(int b, int o);
+void launch_ras_classify(int N, int b, int o, const RasIB& ib, int* list, int* count, cudaStream_t s);
+void launch_box_slots(int nboxes, const int* list, const int* count, int* slotOfBox, cudaStream_t s);
+void launch_ras_setup(int N, int b, int o, const RasIB& ib, double a0, double c, double inv_h, double dt,
+                      const int* list, int nIB, double* inv64, float* inv32, int* info, cudaStream_t s);
+template <typename T>
+void launch_ras_apply(int N, int b, int o, const int* slotOfBox, const T* inv, T omega, const T* r, const T* x, T* xo,
+                      cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
 // Levels 1 and 0 of the V-cycle in one thread block (kernels_small.cu).
 template <typename T>
 struct SmallArgs {

@@ -73,6 +73,14 @@ struct Level {
     int* slotOf = nullptr;               // tile -> slot in the active-tile list, -1 if inactive
     int useWindow = 0;                   // windows valid on this level
     int applyWindow = 0;                 // the solve applies the IB operator through the windows
+    // box RAS smoother: boxes meeting IB windows, their slots, and the owned rows of the subdomain
+    // inverses (slot 0 the shared IB-free inverse), FP64 and FP32
+    int* rasList = nullptr;
+    int* rasSlot = nullptr;
+    int* rasCount = nullptr;
+    int rasBoxCap = 0;
+    void* rasInv[2] = {nullptr, nullptr};
+    size_t rasInvCap = 0;                // entries
 };
 
 struct sib_ctx {
@@ -120,6 +128,7 @@ struct sib_ctx {
     double* Aug = nullptr;
     double* Pinv = nullptr;
     int* info = nullptr;
+    int* rasInfo = nullptr;      // zero pivot in a box RAS subdomain inverse
     int* piv = nullptr;
     int n0 = 0;
     // FGMRES
@@ -480,11 +489,25 @@ void sc_sweep(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream_t s, 
     }
 }
 
+// one RAS correction on level l: xo = x + omega Rt^T L_k^{-1} r (x == nullptr: zero initial guess)
+template <typename T>
+void ras_apply(sib_ctx* c, int l, const T* r, const T* x, T* xo, double omega, cudaStream_t s) {
+    Level& lv = c->L[l];
+    const int pi = Prec<T>::id;
+    KL(c, launch_ras_apply<T>(lv.N, c->opts.box, c->opts.box_overlap, lv.rasSlot, (const T*)lv.rasInv[pi], (T)omega,
+                              r, x, xo, s));
+}
+
 // one smoothing sweep xo <- smooth(x, b)
 template <typename T>
 void sweep(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream_t s) {
     if (c->opts.smoother == SIB_SMOOTHER_SC) {
         sc_sweep<T>(c, l, x, b, xo, s);
+    } else if (c->opts.smoother == SIB_SMOOTHER_RAS) {   // r = b - L x, then the box corrections
+        T* r = (T*)c->L[l].p[Prec<T>::id].r;
+        ib_apply<T>(c, l, x, s);
+        KL(c, launch_residual<T>(gridk<T>(c, l), x, b, r, s));
+        ras_apply<T>(c, l, r, x, xo, c->opts.omega, s);
     } else {
         ib_apply<T>(c, l, x, s);
         KL(c, launch_vanka<T>(gridk<T>(c, l), x, b, xo, s));
@@ -505,6 +528,7 @@ bool small_ok(const sib_ctx* c) {
     const Level& lv = c->L[1];
     if (lv.N > 16) return false;
     if (c->opts.smoother == SIB_SMOOTHER_SC && !sc_fused(c)) return false;
+    if (c->opts.smoother == SIB_SMOOTHER_RAS) return false;
     if (c->haveIB && lv.hnTiles > 0 && !lv.applyWindow) return false;
     const size_t smem = small_smem<T>(c);
     if (smem > (size_t)c->smemOptin) return false;
@@ -575,6 +599,8 @@ void wrapped_smooth(sib_ctx* c, int l, const T* x, const T* b, T* xo, int k, cud
         T* Zj = Z + (size_t)j * n3;
         if (c->opts.smoother == SIB_SMOOTHER_SC)
             sc_sweep<T>(c, l, nullptr, Vj, Zj, s, 1.0);
+        else if (c->opts.smoother == SIB_SMOOTHER_RAS)
+            ras_apply<T>(c, l, Vj, nullptr, Zj, 1.0, s);
         else
             KL(c, launch_vanka_zero<T>(g, Vj, Zj, s));
         ib_apply<T>(c, l, Zj, s);
@@ -629,6 +655,10 @@ T* vcycle_level(sib_ctx* c, int l, cudaStream_t s) {
         k0 = 1;
     } else if (c->opts.smoother == SIB_SMOOTHER_SC && c->opts.nu1 > 0) {
         sc_sweep<T>(c, l, nullptr, b, xt, s);   // first sweep from w = 0: residual = b
+        std::swap(x, xt);
+        k0 = 1;
+    } else if (c->opts.smoother == SIB_SMOOTHER_RAS && c->opts.nu1 > 0) {
+        ras_apply<T>(c, l, b, nullptr, xt, c->opts.omega, s);   // first sweep from w = 0: residual = b
         std::swap(x, xt);
         k0 = 1;
     } else {
@@ -858,6 +888,58 @@ void power_M_enqueue(sib_ctx* c, int l, int slot, cudaStream_t s) {
     }
 }
 
+// Box RAS set-up on levels 1..lmax (Sec. 3.3, Alg. 2 with boxes): classify the boxes by whether
+// their subdomain meets an IB window, then assemble and invert the shared IB-free subdomain operator
+// and one per IB box (FP64), keeping the owned rows of each inverse.
+void ras_setup_all(sib_ctx* c, cudaStream_t s) {
+    const int b = c->opts.box, o = c->opts.box_overlap;
+    const int ne = ras_ne(b, o), nown = 3 * b * b;
+    std::vector<int> cnt(c->lmax + 1, 0);
+    for (int l = 1; l <= c->lmax; ++l) {
+        Level& lv = c->L[l];
+        if (c->haveIB && !lv.useWindow)
+            throw SibError(SIB_ERR_UNIMPLEMENTED, "the box smoother needs the assembled IB windows on every level");
+        const int nboxes = (lv.N / b) * (lv.N / b);
+        if (nboxes > lv.rasBoxCap) {
+            dfree(c, lv.rasList);
+            dfree(c, lv.rasSlot);
+            lv.rasList = (int*)dalloc(c, sizeof(int) * nboxes);
+            lv.rasSlot = (int*)dalloc(c, sizeof(int) * nboxes);
+            lv.rasBoxCap = nboxes;
+        }
+        if (!lv.rasCount) lv.rasCount = (int*)dalloc(c, sizeof(int));
+        const RasIB ib{c->haveIB ? lv.slotOf : nullptr, (const double*)lv.win[0], lv.tx, lv.ty, lv.ntx};
+        launch_ras_classify(lv.N, b, o, ib, lv.rasList, lv.rasCount, s);
+        if (ib.slotOf) ++c->launches;
+        CK(cudaMemcpyAsync(&cnt[l], lv.rasCount, sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemsetAsync(c->rasInfo, 0, sizeof(int), s));
+    for (int l = 1; l <= c->lmax; ++l) {
+        Level& lv = c->L[l];
+        const int nboxes = (lv.N / b) * (lv.N / b);
+        const size_t ent = (size_t)(1 + cnt[l]) * ne * nown;
+        if (ent > lv.rasInvCap) {
+            dfree(c, lv.rasInv[0]);
+            dfree(c, lv.rasInv[1]);
+            lv.rasInv[0] = dalloc(c, sizeof(double) * ent);
+            lv.rasInv[1] = dalloc(c, sizeof(float) * ent);
+            lv.rasInvCap = ent;
+        }
+        const RasIB ib{c->haveIB ? lv.slotOf : nullptr, (const double*)lv.win[0], lv.tx, lv.ty, lv.ntx};
+        launch_box_slots(nboxes, lv.rasList, lv.rasCount, lv.rasSlot, s);
+        const double h = lv.h;
+        launch_ras_setup(lv.N, b, o, ib, c->rho / c->dt + 4.0 * c->mu / (h * h), c->mu / (h * h), 1.0 / h, c->dt,
+                         lv.rasList, cnt[l], (double*)lv.rasInv[0], (float*)lv.rasInv[1], c->rasInfo, s);
+        c->launches += 2;
+    }
+    int info = 0;
+    CK(cudaMemcpyAsync(&info, c->rasInfo, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    kcheck(c);
+    if (info != 0) throw SibError(SIB_ERR_ARG, "a box subdomain operator is singular");
+}
+
 void setup(sib_ctx* c, cudaStream_t s) {
     CK(cudaEventRecord(c->ev0, s));
     invalidate_graphs(c);
@@ -999,6 +1081,7 @@ void setup(sib_ctx* c, cudaStream_t s) {
         KL(c, launch_extract_pinv(c->Aug, c->piv, n, c->L[0].N, c->rho, c->Pinv, c->aux));
         CK(cudaEventRecord(c->evJoin, c->aux));
     }
+    if (c->opts.smoother == SIB_SMOOTHER_RAS && c->lmax > 0) ras_setup_all(c, s);
     if (c->opts.smoother == SIB_SMOOTHER_SC) {
         alloc_sc_bufs(c);
         for (int l = 1; l <= c->lmax; ++l) {
@@ -1456,6 +1539,10 @@ void time_kernel(sib_ctx* c, int kernel, int l, int reps, cudaStream_t s, double
             case SIB_KERNEL_PROLONG:
                 launch_prolong_add<T>(c->L[l - 1].N, (const T*)c->L[l - 1].p[pi].x, (T*)b.x, s);
                 break;
+            case SIB_KERNEL_RAS:
+                launch_ras_apply<T>(lv.N, c->opts.box, c->opts.box_overlap, lv.rasSlot, (const T*)lv.rasInv[pi],
+                                    (T)1, (const T*)b.r, (const T*)b.x, (T*)b.xt, s);
+                break;
             default:
                 throw SibError(SIB_ERR_ARG, "unknown kernel id");
         }
@@ -1478,6 +1565,9 @@ void time_kernel(sib_ctx* c, int kernel, int l, int reps, cudaStream_t s, double
             break;
         case SIB_KERNEL_PROLONG:
             by = 0.75 * n * w + 6.0 * n * w;
+            break;
+        case SIB_KERNEL_RAS:   // r and x read, xo written (the shared inverse stays on chip)
+            by = 9.0 * n * w;
             break;
         default:
             throw SibError(SIB_ERR_ARG, "unknown kernel id");
@@ -1534,10 +1624,12 @@ void sib_default_opts(sib_opts* o) {
     o->fuse_small = 1;
     o->smooth_krylov = 0;
     o->sc_relax = SIB_RELAX_JACOBI;
+    o->box = 4;
+    o->box_overlap = 1;
 }
 
 static void resolve_opts(sib_opts* o) {
-    if (o->omega < 0) o->omega = o->smoother == SIB_SMOOTHER_SC ? 1.0 : 0.8;
+    if (o->omega < 0) o->omega = o->smoother == SIB_SMOOTHER_VANKA ? 0.8 : 1.0;
 }
 
 int sib_create(sib_ctx** out, int N, int n_min) {
@@ -1585,6 +1677,7 @@ int sib_create(sib_ctx** out, int N, int n_min) {
         c->Aug = (double*)dalloc(c, sizeof(double) * 2 * (size_t)c->n0 * c->n0);
         c->Pinv = (double*)dalloc(c, sizeof(double) * (size_t)c->n0 * c->n0);
         c->info = (int*)dalloc(c, sizeof(int));
+        c->rasInfo = (int*)dalloc(c, sizeof(int));
         c->piv = (int*)dalloc(c, sizeof(int) * c->n0);
         c->gjWork = dalloc(c, gauss_jordan_work_bytes(c->n0));
         c->flag = (int*)dalloc(c, sizeof(int));
@@ -1705,7 +1798,9 @@ int sib_set_options(sib_ctx* c, const sib_opts* o) {
     API_BEGIN(c)
     if (!o) throw SibError(SIB_ERR_ARG, "null options");
     sib_opts n = *o;
-    if ((n.smoother != SIB_SMOOTHER_VANKA && n.smoother != SIB_SMOOTHER_SC) || n.nu1 < 0 || n.nu2 < 0 ||
+    if ((n.smoother != SIB_SMOOTHER_VANKA && n.smoother != SIB_SMOOTHER_SC && n.smoother != SIB_SMOOTHER_RAS) ||
+        n.nu1 < 0 || n.nu2 < 0 || (n.box != 1 && n.box != 2 && n.box != 4) || n.box_overlap < 0 ||
+        n.box + 2 * n.box_overlap > 6 || n.box + 2 * n.box_overlap + 1 > 2 * c->n_min ||
         n.nu1 + n.nu2 > 64 || n.cheb_iters < 1 || n.cheb_iters > 16 || !(n.cheb_lo > 0) || !(n.cheb_hi > n.cheb_lo) ||
         n.power_iters < 1 || n.power_iters > 1000 || !(n.rtol >= 0) || n.max_it < 1 || n.max_it > 100000 ||
         n.restart < 1 || n.restart > 100 || (n.fuse_small != 0 && n.fuse_small != 1) ||
@@ -1714,10 +1809,13 @@ int sib_set_options(sib_ctx* c, const sib_opts* o) {
         throw SibError(SIB_ERR_ARG, "option out of range");
     resolve_opts(&n);
     const bool smootherChanged = n.smoother != c->opts.smoother ||
-                                 (n.smoother == SIB_SMOOTHER_SC && n.sc_relax != c->opts.sc_relax);
+                                 (n.smoother == SIB_SMOOTHER_SC && n.sc_relax != c->opts.sc_relax) ||
+                                 (n.smoother == SIB_SMOOTHER_RAS &&
+                                  (n.box != c->opts.box || n.box_overlap != c->opts.box_overlap));
     c->opts = n;
     if (n.smooth_krylov) alloc_wrap_bufs(c);
-    if (smootherChanged && n.smoother == SIB_SMOOTHER_SC) c->fluidDirty = true;   // needs eigen estimates
+    // SC needs eigen estimates, RAS its subdomain inverses: both come from sib_setup
+    if (smootherChanged && n.smoother != SIB_SMOOTHER_VANKA) c->fluidDirty = true;
     invalidate_graphs(c);
     return SIB_OK;
     API_END(c)
@@ -1987,8 +2085,11 @@ int sib_time_kernel(sib_ctx* c, int kernel, int l, int prec, int reps, void* str
     require_setup(c);
     check_level(c, l, 0);
     if (!valid_prec(prec) || reps < 1 || !ms || !bytes) throw SibError(SIB_ERR_ARG, "bad argument");
-    if ((kernel == SIB_KERNEL_RESTRICT || kernel == SIB_KERNEL_PROLONG || kernel == SIB_KERNEL_VANKA) && l < 1)
+    if ((kernel == SIB_KERNEL_RESTRICT || kernel == SIB_KERNEL_PROLONG || kernel == SIB_KERNEL_VANKA ||
+         kernel == SIB_KERNEL_RAS) && l < 1)
         throw SibError(SIB_ERR_ARG, "kernel needs level >= 1");
+    if (kernel == SIB_KERNEL_RAS && c->opts.smoother != SIB_SMOOTHER_RAS)
+        throw SibError(SIB_ERR_STATE, "the RAS kernel needs the RAS smoother set up");
     if ((kernel == SIB_KERNEL_SPREAD || kernel == SIB_KERNEL_INTERP) && !c->haveIB)
         throw SibError(SIB_ERR_ARG, "no immersed structure");
     if (prec == SIB_PREC_FP64)

@@ -27,6 +27,7 @@ ERROR_NAMES = {v: k for k, v in dict(globals()).items() if k.startswith("SIB_ERR
 
 SMOOTHER_VANKA = 0
 SMOOTHER_SC = 1
+SMOOTHER_RAS = 2
 RELAX_JACOBI = 0
 RELAX_SGS = 1
 PREC_FP64 = 0
@@ -42,7 +43,7 @@ EXPORTS = [
     "sib_coarse_solve", "sib_vcycle", "sib_interp", "sib_spread", "sib_time_kernel", "sib_launch_count",
     "sib_device_bytes", "sib_spread_noalloc", "sib_advance_markers",
 ]
-KERNELS = {"vanka": 0, "residual": 1, "spread": 2, "interp": 3, "restrict": 4, "prolong": 5}
+KERNELS = {"vanka": 0, "residual": 1, "spread": 2, "interp": 3, "restrict": 4, "prolong": 5, "ras": 6}
 
 
 class SibOpts(ctypes.Structure):
@@ -52,6 +53,7 @@ class SibOpts(ctypes.Structure):
         ("power_iters", ctypes.c_int), ("vcycle_fp32", ctypes.c_int), ("rtol", ctypes.c_double),
         ("max_it", ctypes.c_int), ("restart", ctypes.c_int), ("add_SKXn", ctypes.c_int), ("use_graphs", ctypes.c_int),
         ("fuse_small", ctypes.c_int), ("smooth_krylov", ctypes.c_int), ("sc_relax", ctypes.c_int),
+        ("box", ctypes.c_int), ("box_overlap", ctypes.c_int),
     ]
 
 
