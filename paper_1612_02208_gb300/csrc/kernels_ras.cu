@@ -73,15 +73,23 @@ __device__ __forceinline__ int face_slot(const RasIB& ib, int i, int j) {
     return ib.slotOf[(j / ib.ty) * ib.ntx + i / ib.tx];
 }
 
-// Box classification: flag[k] = 1 if any face of box k's subdomain lies in a tile with a window.
+// Box classification: box k is listed if some face of its subdomain has a nonzero row of the IB
+// operator (a window entry != 0); the other boxes' local operators have no IB terms.
 __global__ void k_ras_classify(RasGeo G, RasIB ib, int* __restrict__ list, int* __restrict__ count) {
     const int k = blockIdx.x;
     const int I = k % G.nbs, J = k / G.nbs, m = G.N - 1;
     const int i0 = I * G.b - G.o, j0 = J * G.b - G.o;
+    const int nu = G.e * (G.e + 1), per = ib.tx * ib.ty;
     int hit = 0;
-    for (int t = threadIdx.x; t < (G.e + 1) * (G.e + 1); t += blockDim.x) {
-        const int ii = t % (G.e + 1), jj = t / (G.e + 1);
-        if (face_slot(ib, (i0 + ii) & m, (j0 + jj) & m) >= 0) hit = 1;
+    for (int t = threadIdx.x; t < 2 * nu * WIN_SIZE && !hit; t += blockDim.x) {
+        const int q = t / WIN_SIZE, kw = t - q * WIN_SIZE;   // velocity dof q of the subdomain, window entry kw
+        int comp, ii, jj;
+        ras_dof(G, q, comp, ii, jj);
+        const int gi = (i0 + ii) & m, gj = (j0 + jj) & m;
+        const int slot = face_slot(ib, gi, gj);
+        if (slot < 0) continue;
+        const double* w = ib.win + ((size_t)(slot * 2 + comp) * WIN_SIZE) * per;
+        if (w[(size_t)kw * per + (gj % ib.ty) * ib.tx + (gi % ib.tx)] != 0.0) hit = 1;
     }
     hit = __syncthreads_or(hit);
     if (hit && threadIdx.x == 0) list[atomicAdd(count, 1)] = k;
@@ -224,15 +232,113 @@ __global__ void __launch_bounds__(256) k_ras_setup(RasGeo G, RasIB ib, double a0
 }
 
 // One RAS correction: xo(owned) = x(owned) + omega (Inv_k r_k)(owned) for every box k, with r the
-// residual (x == nullptr: zero initial guess, xo = omega Inv r).  slot[k] < 0: the shared inverse.
+// residual (x == nullptr: zero initial guess, xo = omega Inv r).  The boxes without IB terms
+// (slotOfBox[k] < 0) share one inverse, staged once per block in shared memory (k_ras_apply); the
+// others, listed at set-up, use their own (k_ras_apply_ib, one block per box).
+// Every warp takes groups of RAS_GB consecutive boxes (grid-stride over the groups):
+// the group's residuals are gathered into shared memory as [q][box], and lane l accumulates owned
+// rows l and l + 32 for all boxes of the group, so one read of an inverse entry serves RAS_GB boxes.
+constexpr int RAS_GB = 4;
+constexpr int RAS_WARPS = 4;
+constexpr int RAS_QL = 4;   // subdomain dofs per lane: ne <= 32 RAS_QL (ne <= 120 for b + 2o <= 6)
 template <typename T>
-__global__ void k_ras_apply(RasGeo G, const int* __restrict__ slotOfBox, const T* __restrict__ inv, T omega,
-                            const T* __restrict__ r, const T* x, T* xo) {
-    extern __shared__ unsigned char smem_raw[];
-    T* rb = reinterpret_cast<T*>(smem_raw);
+struct alignas(4 * sizeof(T)) Quad {
+    T v[4];
+};
+template <typename T>
+__global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_apply(RasGeo G, const int* __restrict__ slotOfBox,
+                                                              const T* __restrict__ inv, T omega,
+                                                              const T* __restrict__ r, const T* x, T* xo) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* Ms = reinterpret_cast<T*>(smem_raw);                                  // ne x nown, [q][row]
+    T* rbAll = Ms + ((G.ne * G.nown + 3) & ~3);                              // per warp: ne x RAS_GB
+    int* qtab = reinterpret_cast<int*>(rbAll + (size_t)RAS_WARPS * G.ne * RAS_GB);   // ne: comp | ii << 8 | jj << 16
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T* rb = rbAll + (size_t)warp * G.ne * RAS_GB;
+    for (int t = threadIdx.x; t < G.ne * G.nown; t += blockDim.x) Ms[t] = inv[t];   // set-up data
+    for (int q = threadIdx.x; q < G.ne; q += blockDim.x) {
+        int comp, ii, jj;
+        ras_dof(G, q, comp, ii, jj);
+        qtab[q] = comp | (ii << 8) | (jj << 16);
+    }
+    __syncthreads();
     pdl_entry();
-    const int k = blockIdx.x;
-    const int I = k % G.nbs, J = k / G.nbs, N = G.N, n = N * N, m = N - 1;
+    const int N = G.N, n = N * N, m = N - 1, bb = G.b * G.b;
+    const int ngroups = G.nbs * G.nbs / RAS_GB;
+    const int r0 = lane, r1 = lane + 32;
+    for (int grp = blockIdx.x * RAS_WARPS + warp; grp < ngroups; grp += gridDim.x * RAS_WARPS) {
+        const int k0 = grp * RAS_GB;
+        // gather the group's residuals: every load of the lane is issued before the first store
+        T gv[RAS_GB][RAS_QL];
+#pragma unroll
+        for (int j = 0; j < RAS_GB; ++j) {
+            const int kb = k0 + j;
+            const int ib0 = (kb % G.nbs) * G.b - G.o, jb0 = (kb / G.nbs) * G.b - G.o;
+#pragma unroll
+            for (int sq = 0; sq < RAS_QL; ++sq) {
+                const int q = lane + 32 * sq;
+                if (q < G.ne) {
+                    const int code = qtab[q];
+                    const int gi = (ib0 + ((code >> 8) & 0xff)) & m, gj = (jb0 + (code >> 16)) & m;
+                    gv[j][sq] = r[(size_t)(code & 0xff) * n + gj * N + gi];
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < RAS_GB; ++j)
+#pragma unroll
+            for (int sq = 0; sq < RAS_QL; ++sq) {
+                const int q = lane + 32 * sq;
+                if (q < G.ne) rb[q * RAS_GB + j] = gv[j][sq];
+            }
+        __syncwarp();
+        int sl[RAS_GB];
+#pragma unroll
+        for (int j = 0; j < RAS_GB; ++j) sl[j] = slotOfBox ? slotOfBox[k0 + j] : -1;
+        T acc0[RAS_GB], acc1[RAS_GB];
+#pragma unroll
+        for (int j = 0; j < RAS_GB; ++j) acc0[j] = acc1[j] = T(0);
+        {   // the shared inverse for the whole group (boxes with their own are stored by k_ras_apply_ib)
+            const int c0 = r0 < G.nown ? r0 : 0, c1 = r1 < G.nown ? r1 : 0;   // rows past nown compute, unused
+            const Quad<T>* rq = reinterpret_cast<const Quad<T>*>(rb);
+#pragma unroll 8
+            for (int q = 0; q < G.ne; ++q) {
+                const T m0 = Ms[q * G.nown + c0];
+                const T m1 = Ms[q * G.nown + c1];
+                const Quad<T> v = rq[q];
+#pragma unroll
+                for (int j = 0; j < RAS_GB; ++j) {
+                    acc0[j] += m0 * v.v[j];
+                    acc1[j] += m1 * v.v[j];
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < RAS_GB; ++j) {
+            if (sl[j] >= 0) continue;
+            const int I = (k0 + j) % G.nbs, J = (k0 + j) / G.nbs;
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const int rr = h2 ? r1 : r0;
+                if (rr >= G.nown) continue;
+                const int comp = rr / bb, rem = rr - comp * bb;
+                const int gi = I * G.b + rem % G.b, gj = J * G.b + rem / G.b;
+                const size_t d = (size_t)comp * n + gj * N + gi;
+                xo[d] = (x ? x[d] : T(0)) + omega * (h2 ? acc1[j] : acc0[j]);
+            }
+        }
+        __syncwarp();   // the group's residual buffer is reused by the next group
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(64) k_ras_apply_ib(RasGeo G, const int* __restrict__ list, const T* __restrict__ inv,
+                                                    T omega, const T* __restrict__ r, const T* x, T* xo) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* rb = reinterpret_cast<T*>(smem_raw);
+    const int s = blockIdx.x, k = list[s];   // set-up data
+    pdl_entry();
+    const int I = k % G.nbs, J = k / G.nbs, N = G.N, n = N * N, m = N - 1, bb = G.b * G.b;
     const int i0 = I * G.b - G.o, j0 = J * G.b - G.o;
     for (int q = threadIdx.x; q < G.ne; q += blockDim.x) {
         int comp, ii, jj;
@@ -240,14 +346,13 @@ __global__ void k_ras_apply(RasGeo G, const int* __restrict__ slotOfBox, const T
         rb[q] = r[(size_t)comp * n + ((j0 + jj) & m) * N + ((i0 + ii) & m)];
     }
     __syncthreads();
-    const int s = slotOfBox ? slotOfBox[k] : -1;
     const T* M = inv + (size_t)(s + 1) * G.ne * G.nown;
     for (int rr = threadIdx.x; rr < G.nown; rr += blockDim.x) {
         T acc = T(0);
+#pragma unroll 8
         for (int q = 0; q < G.ne; ++q) acc += M[(size_t)q * G.nown + rr] * rb[q];
-        const int bb = G.b * G.b, comp = rr / bb, rem = rr - comp * bb;
-        const int gi = I * G.b + rem % G.b, gj = J * G.b + rem / G.b;
-        const size_t d = (size_t)comp * n + gj * N + gi;
+        const int comp = rr / bb, rem = rr - comp * bb;
+        const size_t d = (size_t)comp * n + (J * G.b + rem / G.b) * N + I * G.b + rem % G.b;
         xo[d] = (x ? x[d] : T(0)) + omega * acc;
     }
 }
@@ -286,16 +391,32 @@ void launch_ras_setup(int N, int b, int o, const RasIB& ib, double a0, double c,
 }
 
 template <typename T>
-void launch_ras_apply(int N, int b, int o, const int* slotOfBox, const T* inv, T omega, const T* r, const T* x, T* xo,
-                      cudaStream_t s) {
+void launch_ras_apply(int N, int b, int o, const int* slotOfBox, const int* list, int nIB, const T* inv, T omega,
+                      const T* r, const T* x, T* xo, cudaStream_t s) {
     const RasGeo G = ras_geo(N, b, o);
-    const int threads = G.nown > 64 ? 128 : 64;
-    launch_pdl(k_ras_apply<T>, dim3(G.nbs * G.nbs), dim3(threads), sizeof(T) * G.ne, s, G, slotOfBox, inv, omega, r, x,
-               xo);
+    const size_t smem = sizeof(T) * (((size_t)G.ne * G.nown + 3) / 4 * 4 + (size_t)RAS_WARPS * G.ne * RAS_GB) +
+                        sizeof(int) * G.ne;
+    static size_t cachedSmem = 0;   // persistent grid: the blocks resident at once, per shared-memory size
+    static int resident = 1;
+    if (smem != cachedSmem) {
+        cudaFuncSetAttribute(k_ras_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ras_apply<T>, 32 * RAS_WARPS, smem);
+        resident = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+        cachedSmem = smem;
+    }
+    const int ngroups = G.nbs * G.nbs / RAS_GB;
+    const int want = (ngroups + RAS_WARPS - 1) / RAS_WARPS;
+    const int blocks = want < resident ? want : resident;
+    launch_pdl(k_ras_apply<T>, dim3(blocks), dim3(32 * RAS_WARPS), smem, s, G, slotOfBox, inv, omega, r, x, xo);
+    if (nIB > 0)
+        launch_pdl(k_ras_apply_ib<T>, dim3(nIB), dim3(64), sizeof(T) * G.ne, s, G, list, inv, omega, r, x, xo);
 }
-template void launch_ras_apply<float>(int, int, int, const int*, const float*, float, const float*, const float*,
-                                      float*, cudaStream_t);
-template void launch_ras_apply<double>(int, int, int, const int*, const double*, double, const double*,
-                                       const double*, double*, cudaStream_t);
+template void launch_ras_apply<float>(int, int, int, const int*, const int*, int, const float*, float, const float*,
+                                      const float*, float*, cudaStream_t);
+template void launch_ras_apply<double>(int, int, int, const int*, const int*, int, const double*, double,
+                                       const double*, const double*, double*, cudaStream_t);
 
 }  // namespace sib

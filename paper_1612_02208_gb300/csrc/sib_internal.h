@@ -120,9 +120,10 @@ void launch_ras_classify(int N, int b, int o, const RasIB& ib, int* list, int* c
 void launch_box_slots(int nboxes, const int* list, const int* count, int* slotOfBox, cudaStream_t s);
 void launch_ras_setup(int N, int b, int o, const RasIB& ib, double a0, double c, double inv_h, double dt,
                       const int* list, int nIB, double* inv64, float* inv32, int* info, cudaStream_t s);
+// the shared-inverse kernel, then (nIB > 0) one block per listed IB box
 template <typename T>
-void launch_ras_apply(int N, int b, int o, const int* slotOfBox, const T* inv, T omega, const T* r, const T* x, T* xo,
-                      cudaStream_t s);
+void launch_ras_apply(int N, int b, int o, const int* slotOfBox, const int* list, int nIB, const T* inv, T omega,
+                      const T* r, const T* x, T* xo, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
 // Levels 1 and 0 of the V-cycle in one thread block (kernels_small.cu).

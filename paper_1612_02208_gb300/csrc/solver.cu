@@ -81,6 +81,7 @@ struct Level {
     int rasBoxCap = 0;
     void* rasInv[2] = {nullptr, nullptr};
     size_t rasInvCap = 0;                // entries
+    int rasNIB = 0;                      // boxes with their own inverse
 };
 
 struct sib_ctx {
@@ -494,8 +495,9 @@ template <typename T>
 void ras_apply(sib_ctx* c, int l, const T* r, const T* x, T* xo, double omega, cudaStream_t s) {
     Level& lv = c->L[l];
     const int pi = Prec<T>::id;
-    KL(c, launch_ras_apply<T>(lv.N, c->opts.box, c->opts.box_overlap, lv.rasSlot, (const T*)lv.rasInv[pi], (T)omega,
-                              r, x, xo, s));
+    KL(c, launch_ras_apply<T>(lv.N, c->opts.box, c->opts.box_overlap, lv.rasSlot, lv.rasList, lv.rasNIB,
+                              (const T*)lv.rasInv[pi], (T)omega, r, x, xo, s));
+    if (lv.rasNIB > 0) ++c->launches;
 }
 
 // one smoothing sweep xo <- smooth(x, b)
@@ -928,6 +930,7 @@ void ras_setup_all(sib_ctx* c, cudaStream_t s) {
         }
         const RasIB ib{c->haveIB ? lv.slotOf : nullptr, (const double*)lv.win[0], lv.tx, lv.ty, lv.ntx};
         launch_box_slots(nboxes, lv.rasList, lv.rasCount, lv.rasSlot, s);
+        lv.rasNIB = cnt[l];
         const double h = lv.h;
         launch_ras_setup(lv.N, b, o, ib, c->rho / c->dt + 4.0 * c->mu / (h * h), c->mu / (h * h), 1.0 / h, c->dt,
                          lv.rasList, cnt[l], (double*)lv.rasInv[0], (float*)lv.rasInv[1], c->rasInfo, s);
@@ -1540,8 +1543,8 @@ void time_kernel(sib_ctx* c, int kernel, int l, int reps, cudaStream_t s, double
                 launch_prolong_add<T>(c->L[l - 1].N, (const T*)c->L[l - 1].p[pi].x, (T*)b.x, s);
                 break;
             case SIB_KERNEL_RAS:
-                launch_ras_apply<T>(lv.N, c->opts.box, c->opts.box_overlap, lv.rasSlot, (const T*)lv.rasInv[pi],
-                                    (T)1, (const T*)b.r, (const T*)b.x, (T*)b.xt, s);
+                launch_ras_apply<T>(lv.N, c->opts.box, c->opts.box_overlap, lv.rasSlot, lv.rasList, lv.rasNIB,
+                                    (const T*)lv.rasInv[pi], (T)1, (const T*)b.r, (const T*)b.x, (T*)b.xt, s);
                 break;
             default:
                 throw SibError(SIB_ERR_ARG, "unknown kernel id");
