@@ -48,6 +48,7 @@ def parse_args(argv=None):
     p.add_argument("--impl", choices=["native", "reference"], default="native")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-large", action="store_true", help="skip the large-grid V-cycle roofline")
+    p.add_argument("--no-paper", action="store_true", help="skip the paper-workload iteration table")
     p.add_argument("--kappas", default=",".join(str(k) for k in KAPPAS),
                    help="comma-separated stiffness values of the sweep (default: the full workload)")
     p.add_argument("--smoothers", default=",".join(SMOOTHERS), help="comma-separated subset of vanka,sc")
@@ -245,6 +246,39 @@ def box_ras_cases(S, g, w, kap_dev, sib, torch, stream, box=4, overlap=1):
             "cases": records}
 
 
+def paper_workloads(sib, torch, dev):
+    """The paper's thick annulus and thin circle (Sec. 5.1, 5.2) in the periodic box: one linear solve
+    each (dt = 0.32 h, g = 0, tolerance 1e-12, at most 100 iterations, FP32 V-cycle), over gamma,
+    Stokes and mu = 0.01, and the smoothers; plus the annulus under grid refinement."""
+    from paper_1612_02208_gb300 import inputs
+    smoothers = {"vanka": dict(smoother=sib.SMOOTHER_VANKA), "sc": dict(smoother=sib.SMOOTHER_SC),
+                 "ras4o1": dict(smoother=sib.SMOOTHER_RAS, box=4, box_overlap=1),
+                 "ras2o2": dict(smoother=sib.SMOOTHER_RAS, box=2, box_overlap=2)}
+    runs = [(kind, 128, gamma, mu, sm) for kind in ("annulus", "circle") for mu in (None, 0.01)
+            for gamma in (5.0, 50.0, 500.0) for sm in smoothers]
+    runs += [("annulus", N, gamma, None, sm) for N in (64, 256) for gamma in (5.0, 500.0) for sm in ("vanka", "ras4o1")]
+    cases = []
+    for kind, N, gamma, mu, sm in runs:
+        prob = inputs.paper_problem(kind, N, gamma, mu)
+        st = prob.structure
+        S = sib.Solver(N)
+        S.set_fluid(prob.rho, prob.mu, prob.dt)
+        S.set_structure(torch.as_tensor(st.X, device=dev), torch.as_tensor(st.edges, device=dev),
+                        torch.as_tensor(st.kappa, device=dev))
+        S.set_options(rtol=1e-12, max_it=100, **smoothers[sm])
+        S.setup()
+        g = torch.zeros(3 * N * N, dtype=torch.float64, device=dev)
+        w = torch.empty_like(g)
+        S.solve(g, w, allow_unconverged=True)
+        d = S.stats.as_dict()
+        cases.append(dict(kind=kind, N=N, gamma=gamma, flow="stokes" if mu is None else f"mu={mu}", smoother=sm,
+                          iterations=d["iterations"], converged=d["converged"], setup_ms=round(d["setup_ms"], 3),
+                          solve_ms=round(d["solve_ms"], 3)))
+        S.close()
+    return {"tol": 1e-12, "max_it": 100, "dt": "0.32 h", "g": "0 (elastic force of the initial configuration)",
+            "boundary": "periodic (the paper's lid-driven cavity walls are not modelled)", "cases": cases}
+
+
 def e2e_step(S, g_host, w_host, kap_host, kap_dev, sib, torch):
     """Through the host-buffer call: stiffness uploaded from pinned memory, g in, w out."""
     for sm in SMOOTHERS:
@@ -438,6 +472,7 @@ def run_native(args):
     # the paper's box Vanka smoother: restricted additive Schwarz over 4 x 4 and 2 x 2 boxes, overlap 1
     ras = [box_ras_cases(S, g, w, kap_dev, sib, torch, stream, 4, 1),
            box_ras_cases(S, g, w, kap_dev, sib, torch, stream, 2, 1)]
+    paper = paper_workloads(sib, torch, dev) if not args.no_paper else None
 
     # end to end through the host-buffer C call, pinned host memory
     g_host = torch.as_tensor(prob.g).pin_memory().numpy()
@@ -489,6 +524,7 @@ def run_native(args):
             "krylov_smoothing": {"ms_per_solve": round(kry_ms, 4), "cases": kry_records},
             "sc_gauss_seidel": sc_gs,
             "box_ras": ras,
+            "paper_workloads": paper,
             "roofline": roofline, "time_loop": tloop, "vcycle_large": large, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk, "wall_s": round(wall, 3),
         }

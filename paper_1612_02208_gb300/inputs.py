@@ -26,6 +26,19 @@ marker spacing of one half grid cell):
     Tangential springs close every ring; each ring-k marker is joined radially to the
     ring-(k-1) marker nearest in angle (index round-half-down of m*n_{k-1}/n_k, modulo
     n_{k-1}); ring-1 markers join the centre.  E = 2*(M-1).
+
+The paper's own structures (Sec. 5.1 thick annulus, Sec. 5.2 thin circle), in the periodic box:
+  * thick annulus, Eq. (annulus): X(s1, s2) = c + (r + s2)(cos s1, sin s1), (s1, s2) in
+    [0, 2 pi) x [0, w], w = 1/16, r = 1/4, c = (1/2, 1/2); M1 = 19N/8 points in s1 (s1_k = 2 pi k/M1)
+    and M2 = 3N/32 + 1 in s2 (s2_m = m w/(M2 - 1)); fibres along s1 only.  The force
+    F = alpha d^2X/ds1^2 with alpha = gamma 3.93/0.005, taken with the nodal quadrature weight
+    ds1 ds2 per marker, is the force of zero-rest-length springs between s1-neighbours of one fibre
+    with kappa_e = alpha ds2/ds1 (ds1 = 2 pi/M1, ds2 = w/(M2 - 1)).
+  * thin circle, Eq. (circle): X(s1) = c + r (cos s1, sin s1), M1 = 19N/8 points,
+    alpha = 7 gamma 3.93/0.005, weight ds1 per marker: kappa_e = alpha/ds1.
+  The paper's single linear solve: dt = 0.32 h, no external forcing (g = 0), so the right-hand side
+  is the elastic force S K X^n of the initial configuration; Stokes (rho = 0, mu = 1) or rho = 1
+  with mu in {1, 0.1, 0.01}; tolerance 1e-12, at most 100 iterations.
 """
 from __future__ import annotations
 
@@ -114,6 +127,50 @@ def elastic_disk(N: int, center=(0.5, 0.5), R: float = 0.25, kappa: float = 1e2)
     X = np.stack([np.concatenate(xs), np.concatenate(ys)], axis=1).astype(np.float64)
     E = np.concatenate(edges, axis=0).astype(np.int32)
     return Structure(np.ascontiguousarray(X), np.ascontiguousarray(E), np.full(E.shape[0], float(kappa)))
+
+
+ALPHA_UNIT = 3.93 / 0.005   # the explicit-stability stiffness that gamma is measured in (Sec. 5.1)
+
+
+def thick_annulus(N: int, gamma: float, center=(0.5, 0.5), r: float = 0.25, w: float = 1.0 / 16) -> Structure:
+    """The paper's thick annulus (Eq. annulus) with s1 fibres; recipe in the module docstring."""
+    if N % 32:
+        raise ValueError("N must be a multiple of 32 (M1 = 19N/8, M2 = 3N/32 + 1)")
+    M1, M2 = 19 * N // 8, 3 * N // 32 + 1
+    s1 = 2.0 * np.pi * np.arange(M1) / M1
+    s2 = w * np.arange(M2) / (M2 - 1)
+    rr = r + s2[:, None]                                        # (M2, M1)
+    X = np.stack([(center[0] + rr * np.cos(s1)).ravel(), (center[1] + rr * np.sin(s1)).ravel()], axis=1)
+    k = np.arange(M1)
+    edges = np.concatenate([np.stack([m * M1 + k, m * M1 + (k + 1) % M1], axis=1) for m in range(M2)])
+    alpha = gamma * ALPHA_UNIT
+    kappa = alpha * (w / (M2 - 1)) / (2.0 * np.pi / M1)
+    return Structure(np.ascontiguousarray(X, dtype=np.float64), edges.astype(np.int32),
+                     np.full(edges.shape[0], kappa))
+
+
+def thin_circle(N: int, gamma: float, center=(0.5, 0.5), r: float = 0.25) -> Structure:
+    """The paper's thin circular membrane (Eq. circle); recipe in the module docstring."""
+    if N % 8:
+        raise ValueError("N must be a multiple of 8 (M1 = 19N/8)")
+    M1 = 19 * N // 8
+    s1 = 2.0 * np.pi * np.arange(M1) / M1
+    X = np.stack([center[0] + r * np.cos(s1), center[1] + r * np.sin(s1)], axis=1)
+    k = np.arange(M1)
+    edges = np.stack([k, (k + 1) % M1], axis=1).astype(np.int32)
+    kappa = 7.0 * gamma * ALPHA_UNIT / (2.0 * np.pi / M1)
+    return Structure(np.ascontiguousarray(X, dtype=np.float64), edges, np.full(M1, kappa))
+
+
+def paper_problem(kind: str, N: int, gamma: float, mu: float | None = None) -> Problem:
+    """One linear solve of the paper's tests: structure `kind` ("annulus" or "circle"), dt = 0.32 h,
+    g = 0 (the elastic force of the initial configuration drives the flow); mu None: Stokes
+    (rho = 0, mu = 1), else rho = 1 with that mu."""
+    s = thick_annulus(N, gamma) if kind == "annulus" else thin_circle(N, gamma)
+    rho, mu_ = (0.0, 1.0) if mu is None else (1.0, float(mu))
+    flow = "stokes" if mu is None else f"mu{mu:g}"
+    return Problem(N, rho, mu_, 0.32 / N, s, np.zeros(3 * N * N), name=f"paper_{kind}_N{N}_gamma{gamma:g}_{flow}",
+                   meta=dict(gamma=gamma, kind=kind))
 
 
 def merge(*parts: Structure) -> Structure:

@@ -656,3 +656,68 @@ def test_ras_fixed_point_and_convergent_vcycle():
     x, it, hist, conv = krylov.fgmres(lambda z: L @ z, H.vcycle, b, rtol=1e-8, max_it=100, restart=100,
                                       project=lambda v: system.project(v, 32, prob.rho))
     assert conv, it
+
+
+# ------------------------------------------------ the paper's structures (Sec. 5.1, 5.2), periodic box
+def test_paper_structures_geometry():
+    """Thick annulus: M1 = 19N/8 by M2 = 3N/32 + 1 markers on circles of radius r + s2_m, fibres closed
+    along s1 only; thin circle: M1 markers on radius r; marker spacing about 2h/3 (Sec. 5.1)."""
+    N = 64
+    a = I.thick_annulus(N, 50.0)
+    M1, M2 = 19 * N // 8, 3 * N // 32 + 1
+    assert a.M == M1 * M2 and a.E == M1 * M2
+    rad = np.hypot(a.X[:, 0] - 0.5, a.X[:, 1] - 0.5).reshape(M2, M1)
+    np.testing.assert_allclose(rad, (0.25 + np.arange(M2) / (M2 - 1) / 16)[:, None] * np.ones(M1), atol=1e-15)
+    e = a.edges
+    assert ((e[:, 0] // M1) == (e[:, 1] // M1)).all()                 # links stay on one fibre
+    assert (((e[:, 1] - e[:, 0]) % M1) == 1).all()                    # s1 neighbours, closed
+    c = I.thin_circle(N, 50.0)
+    assert c.M == M1
+    spacing = np.linalg.norm(c.X - np.roll(c.X, -1, axis=0), axis=1)
+    np.testing.assert_allclose(spacing, 2 * 0.25 * np.sin(np.pi / M1), rtol=1e-13)   # chord of the step
+    assert 0.6 < spacing.mean() * N < 0.7                             # about 2h/3
+
+
+@pytest.mark.parametrize("kind", ["circle", "annulus"])
+def test_paper_structures_force_continuum_limit(kind):
+    """The spring force of the initial configuration is the discrete alpha d^2X/ds1^2 with the nodal
+    quadrature weight: on a circle of radius R each marker's force points to the centre with magnitude
+    alpha R ds1 wq (2 sin(ds1/2)/ds1)^2, so the total magnitude tends to 2 pi R alpha wq (wq = 1 for
+    the thin circle; ds2 per fibre of the annulus).  Checked with the oracle's spring operator."""
+    N, gamma = 64, 5.0
+    st = I.thin_circle(N, gamma) if kind == "circle" else I.thick_annulus(N, gamma)
+    F = ib.spring_force(st.X, st.edges, st.kappa)
+    M1 = 19 * N // 8
+    ds1 = 2 * np.pi / M1
+    alpha = (7.0 if kind == "circle" else 1.0) * gamma * I.ALPHA_UNIT
+    radial = st.X - 0.5
+    rad = np.linalg.norm(radial, axis=1)
+    cosang = -(F * radial).sum(1) / (np.linalg.norm(F, axis=1) * rad)
+    np.testing.assert_allclose(cosang, 1.0, atol=1e-12)                # points to the centre
+    if kind == "circle":
+        wq, radii = np.ones(M1), np.full(M1, 0.25)
+    else:
+        M2 = 3 * N // 32 + 1
+        wq = np.full(M1 * M2, (1.0 / 16) / (M2 - 1))
+        radii = rad
+    expect = alpha * radii * ds1 * wq * (2 * np.sin(ds1 / 2) / ds1) ** 2
+    np.testing.assert_allclose(np.linalg.norm(F, axis=1), expect, rtol=1e-12)
+
+
+def test_paper_workload_trends_on_the_oracle():
+    """Iteration trends the paper states (Sec. 5.1, 5.2), at 32^2 with box RAS (4 x 4, overlap 1) to
+    1e-12: more iterations for the thin circle than for the annulus at the same gamma, and no fewer
+    as gamma grows (5 -> 500)."""
+    its = {}
+    for kind in ("annulus", "circle"):
+        for gamma in (5.0, 500.0):
+            prob = I.paper_problem(kind, 32, gamma)
+            L = system.operator_of(prob)
+            b = system.rhs(prob)
+            H = multigrid.Hierarchy(prob, smoother="ras", box=4, overlap=1)
+            _, it, _, conv = krylov.fgmres(lambda z: L @ z, H.vcycle, b, rtol=1e-12, max_it=100, restart=100,
+                                           project=lambda v: system.project(v, 32, prob.rho))
+            its[kind, gamma] = it
+    assert its["annulus", 500.0] >= its["annulus", 5.0], its
+    assert its["circle", 500.0] >= its["circle", 5.0], its
+    assert its["circle", 500.0] >= its["annulus", 500.0], its
