@@ -334,11 +334,13 @@ def large_vcycle(sib, torch, reps=20, N=None):
     for _ in range(3):
         S.vcycle(b, z)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("vcycles_ras")
     e0.record()
     for _ in range(reps):
         S.vcycle(b, z)
     e1.record()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     out["vcycle_ms_ras"] = round(e0.elapsed_time(e1) / reps, 4)
     torch.cuda.nvtx.range_push("roofline_large_ras")
     ms, by = S.time_kernel("ras", lmax, True, reps=20)

@@ -255,7 +255,15 @@ __global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_apply(RasGeo G, const in
     int* qtab = reinterpret_cast<int*>(rbAll + (size_t)RAS_WARPS * G.ne * RAS_GB);   // ne: comp | ii << 8 | jj << 16
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T* rb = rbAll + (size_t)warp * G.ne * RAS_GB;
-    for (int t = threadIdx.x; t < G.ne * G.nown; t += blockDim.x) Ms[t] = inv[t];   // set-up data
+    {   // stage the shared inverse (set-up data): 16-byte asynchronous copies, all in flight at once
+        const int words = G.ne * G.nown, per16 = 16 / (int)sizeof(T), chunks = words / per16;
+        for (int t = threadIdx.x; t < chunks; t += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(Ms + t * per16)),
+                         "l"(inv + (size_t)t * per16)
+                         : "memory");
+        for (int t = chunks * per16 + threadIdx.x; t < words; t += blockDim.x) Ms[t] = inv[t];
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+    }
     for (int q = threadIdx.x; q < G.ne; q += blockDim.x) {
         int comp, ii, jj;
         ras_dof(G, q, comp, ii, jj);
@@ -331,12 +339,17 @@ __global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_apply(RasGeo G, const in
     }
 }
 
+// One block per listed IB box: RAS_QS groups of threads each take a quarter of the q range for every
+// owned row, and the partial sums are added in shared memory in a fixed order.
+constexpr int RAS_QS = 4;
 template <typename T>
-__global__ void __launch_bounds__(64) k_ras_apply_ib(RasGeo G, const int* __restrict__ list, const T* __restrict__ inv,
-                                                    T omega, const T* __restrict__ r, const T* x, T* xo) {
+__global__ void __launch_bounds__(64 * RAS_QS) k_ras_apply_ib(RasGeo G, const int* __restrict__ list,
+                                                             const T* __restrict__ inv, T omega,
+                                                             const T* __restrict__ r, const T* x, T* xo) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    T* rb = reinterpret_cast<T*>(smem_raw);
-    const int s = blockIdx.x, k = list[s];   // set-up data
+    T* rb = reinterpret_cast<T*>(smem_raw);   // ne
+    T* part = rb + G.ne;                      // RAS_QS x 64
+    const int s = blockIdx.x, k = list[s];    // set-up data
     pdl_entry();
     const int I = k % G.nbs, J = k / G.nbs, N = G.N, n = N * N, m = N - 1, bb = G.b * G.b;
     const int i0 = I * G.b - G.o, j0 = J * G.b - G.o;
@@ -347,13 +360,22 @@ __global__ void __launch_bounds__(64) k_ras_apply_ib(RasGeo G, const int* __rest
     }
     __syncthreads();
     const T* M = inv + (size_t)(s + 1) * G.ne * G.nown;
-    for (int rr = threadIdx.x; rr < G.nown; rr += blockDim.x) {
-        T acc = T(0);
-#pragma unroll 8
-        for (int q = 0; q < G.ne; ++q) acc += M[(size_t)q * G.nown + rr] * rb[q];
+    const int rr = threadIdx.x & 63, part_id = threadIdx.x >> 6;
+    const int qchunk = (G.ne + RAS_QS - 1) / RAS_QS;
+    const int qa = part_id * qchunk, qb = min(G.ne, qa + qchunk);
+    T acc = T(0);
+    if (rr < G.nown) {
+#pragma unroll 6
+        for (int q = qa; q < qb; ++q) acc += M[(size_t)q * G.nown + rr] * rb[q];
+    }
+    part[part_id * 64 + rr] = acc;
+    __syncthreads();
+    if (part_id == 0 && rr < G.nown) {
+        T sum = part[rr];
+        for (int p2 = 1; p2 < RAS_QS; ++p2) sum += part[p2 * 64 + rr];
         const int comp = rr / bb, rem = rr - comp * bb;
         const size_t d = (size_t)comp * n + (J * G.b + rem / G.b) * N + I * G.b + rem % G.b;
-        xo[d] = (x ? x[d] : T(0)) + omega * acc;
+        xo[d] = (x ? x[d] : T(0)) + omega * sum;
     }
 }
 
@@ -412,7 +434,8 @@ void launch_ras_apply(int N, int b, int o, const int* slotOfBox, const int* list
     const int blocks = want < resident ? want : resident;
     launch_pdl(k_ras_apply<T>, dim3(blocks), dim3(32 * RAS_WARPS), smem, s, G, slotOfBox, inv, omega, r, x, xo);
     if (nIB > 0)
-        launch_pdl(k_ras_apply_ib<T>, dim3(nIB), dim3(64), sizeof(T) * G.ne, s, G, list, inv, omega, r, x, xo);
+        launch_pdl(k_ras_apply_ib<T>, dim3(nIB), dim3(64 * RAS_QS), sizeof(T) * (G.ne + 64 * RAS_QS), s, G, list, inv,
+                   omega, r, x, xo);
 }
 template void launch_ras_apply<float>(int, int, int, const int*, const int*, int, const float*, float, const float*,
                                       const float*, float*, cudaStream_t);
