@@ -418,8 +418,8 @@ void launch_ras_apply(int N, int b, int o, const int* slotOfBox, const int* list
     const RasGeo G = ras_geo(N, b, o);
     const size_t smem = sizeof(T) * (((size_t)G.ne * G.nown + 3) / 4 * 4 + (size_t)RAS_WARPS * G.ne * RAS_GB) +
                         sizeof(int) * G.ne;
-    static size_t cachedSmem = 0;   // persistent grid: the blocks resident at once, per shared-memory size
-    static int resident = 1;
+    static thread_local size_t cachedSmem = 0;   // persistent grid: the blocks resident at once, per size
+    static thread_local int resident = 1;
     if (smem != cachedSmem) {
         cudaFuncSetAttribute(k_ras_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int dev = 0, sms = 0, per = 0;
