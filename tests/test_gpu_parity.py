@@ -1,7 +1,7 @@
 """GPU parity: every step of the CUDA path against the CPU oracle on identical seeded inputs.
 
 Tolerances: FP64 results agree with the FP64 oracle to 1e-10 (relative, max norm); FP32 results
-agree to 1e-5 per operation / smoother sweep (spec requirement), which leaves room for the
+agree to 1e-5 per operation / smoother sweep (the required FP32 accuracy), which leaves room for the
 ~1e-7 rounding of single precision applied over a handful of dependent steps.
 """
 import numpy as np
