@@ -133,3 +133,25 @@ def test_ras_options_validated():
         with pytest.raises(sib.SibError):
             S.set_options(**kw)
         S.set_options(box=4, box_overlap=1)
+
+
+def test_ras_small_coarse_grid_boxes_span_rows():
+    """n_min = 4: level 1 is 8 x 8, two 4 x 4 boxes per row, so a group of four boxes in the
+    correction kernel spans two box rows; one sweep per level and one V-cycle against the oracle."""
+    prob = I.thin_ellipse_stokes(32, kappa=1e2)
+    H = multigrid.Hierarchy(prob, n_min=4, smoother="ras", box=4, overlap=1)
+    S = sib.Solver(32, 4)
+    S.set_fluid(prob.rho, prob.mu, prob.dt)
+    st = prob.structure
+    S.set_structure(cu(st.X), torch.as_tensor(st.edges, device="cuda"), cu(st.kappa))
+    S.set_options(smoother=sib.SMOOTHER_RAS, box=4, box_overlap=1)
+    S.setup()
+    for l in range(1, len(H.levels)):
+        lev = H.levels[l]
+        x = rand(3 * lev.n, 3800 + l)
+        bb = rand(3 * lev.n, 3900 + l, 10.0)
+        y = cu(x.copy())
+        S.smooth(l, y, cu(bb), 1)
+        assert rel(host(y), H.smooth(l, x, bb, 1)) < TOL64, l
+    b = system.rhs(prob)
+    assert rel(host(S.vcycle(cu(b))), H.vcycle(b)) < TOL64
