@@ -165,6 +165,27 @@ __device__ __forceinline__ void prolong_add_cell(int Nc, const T* __restrict__ e
 }
 
 // ------------------------------------------------------------------------------------------
+// Vanka patch solve from the cell's set-up factors (Alg. 2, one-cell subdomain): with
+// A_u^{-1} = [[a00u, a01u], [a01u, a11u]] and A_v^{-1} likewise (the inverses of the 2 x 2 velocity
+// blocks) and invS = 1 / (g^T A_u^{-1} g + g^T A_v^{-1} g), g = (1/h, -1/h), the patch system
+// [[A_u, 0, g], [0, A_v, g], [g^T, g^T, 0]] (d0, d1, d2, d3, dp) = (r0, r1, r2, r3, r4) is solved by
+// block elimination on the pressure: t = A^{-1} r, s = A^{-1} g, dp = (g^T t - r4) invS, d = t - s dp.
+template <typename T>
+__device__ __forceinline__ void patch_solve(const T* f, T ih, T r0, T r1, T r2, T r3, T r4, T& d0, T& d1, T& d2,
+                                            T& d3, T& dp) {
+    const T a00u = f[0], a01u = f[1], a11u = f[2], a00v = f[3], a01v = f[4], a11v = f[5], invS = f[6];
+    const T tu0 = a00u * r0 + a01u * r1, tu1 = a01u * r0 + a11u * r1;
+    const T tv0 = a00v * r2 + a01v * r3, tv1 = a01v * r2 + a11v * r3;
+    const T su0 = ih * (a00u - a01u), su1 = ih * (a01u - a11u);
+    const T sv0 = ih * (a00v - a01v), sv1 = ih * (a01v - a11v);
+    dp = (ih * ((tu0 - tu1) + (tv0 - tv1)) - r4) * invS;
+    d0 = tu0 - su0 * dp;
+    d1 = tu1 - su1 * dp;
+    d2 = tv0 - sv0 * dp;
+    d3 = tv1 - sv1 * dp;
+}
+
+// ------------------------------------------------------------------------------------------
 // Schur-complement smoother pieces (Eq. approx-fact-Stokes-IB).
 // diag(A_IB) on a face: a0 - dt B(f,f) (B(f,f) read only in IB-active tiles).
 template <typename T>

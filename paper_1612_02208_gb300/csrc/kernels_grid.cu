@@ -117,29 +117,16 @@ __global__ void __launch_bounds__(256) k_vanka(GridK<T> g, const T* __restrict__
         const T r0 = sru[pj * RW + pi], r1 = sru[pj * RW + pi + 1];
         const T r2 = srv[pj * RW + pi], r3 = srv[(pj + 1) * RW + pi];
         const T r4 = srp[pj * RW + pi];
-        T au00 = g.a0, au11 = g.a0, au01 = -g.c, av00 = g.a0, av11 = g.a0, av01 = -g.c;
-        if (act) {
-            const int cc = j * N + i, ce = j * N + ((i + 1) & m), cn = ((j + 1) & m) * N + i;
-            au00 -= g.dt * g.ibd[cc];
-            au11 -= g.dt * g.ibd[ce];
-            au01 -= g.dt * g.ibd[n + cc];
-            av00 -= g.dt * g.ibd[2 * n + cc];
-            av11 -= g.dt * g.ibd[2 * n + cn];
-            av01 -= g.dt * g.ibd[3 * n + cc];
-        }
-        const T idu = T(1) / (au00 * au11 - au01 * au01);
-        const T idv = T(1) / (av00 * av11 - av01 * av01);
-        // s = A^{-1} (ih, -ih), t = A^{-1} r
-        const T su0 = (au11 + au01) * ih * idu, su1 = -(au01 + au00) * ih * idu;
-        const T sv0 = (av11 + av01) * ih * idv, sv1 = -(av01 + av00) * ih * idv;
-        const T tu0 = (au11 * r0 - au01 * r1) * idu, tu1 = (au00 * r1 - au01 * r0) * idu;
-        const T tv0 = (av11 * r2 - av01 * r3) * idv, tv1 = (av00 * r3 - av01 * r2) * idv;
-        const T S = ih * ((su0 - su1) + (sv0 - sv1));
-        const T dp = (ih * ((tu0 - tu1) + (tv0 - tv1)) - r4) / S;
-        sd[0][q] = tu0 - su0 * dp;
-        sd[1][q] = tu1 - su1 * dp;
-        sd[2][q] = tv0 - sv0 * dp;
-        sd[3][q] = tv1 - sv1 * dp;
+        T f[7];
+        const int cc = j * N + i;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) f[k] = g.pf[(size_t)k * n + cc];
+        T d0, d1, d2, d3, dp;
+        patch_solve(f, ih, r0, r1, r2, r3, r4, d0, d1, d2, d3, dp);
+        sd[0][q] = d0;
+        sd[1][q] = d1;
+        sd[2][q] = d2;
+        sd[3][q] = d3;
         sd[4][q] = dp;
     }
     __syncthreads();
@@ -190,7 +177,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4)
                   const __grid_constant__ CUtensorMap mb, int tma, int first_wave, const T* __restrict__ x,
                   const T* __restrict__ b, T* __restrict__ xo) {
     __shared__ __align__(128) T stage[VK_STAGE];
-    __shared__ T bs[6][VK_PY][VK_PX];   // IB entries of the patches of an active tile
+    __shared__ T bs[7][VK_PY][VK_PX];   // patch factors of the patches of an active tile
     __shared__ uint64_t bar;
     T(*sb)[VK_BR][VK_W] = reinterpret_cast<T(*)[VK_BR][VK_W]>(stage);
     T(*sx)[VK_XR][VK_W] = reinterpret_cast<T(*)[VK_XR][VK_W]>(stage + VK_XOFF);
@@ -209,14 +196,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4)
     auto load_patch_ib = [&]() {
         for (int q = tid; q < VK_PY * VK_PX; q += TX * TY) {
             const int pj = q / VK_PX, pi = q - pj * VK_PX;
-            const int i = (i0 - 1 + pi) & m, j = (j0 - 1 + pj) & m;
-            const int cc = j * N + i, ce = j * N + ((i + 1) & m), cn = ((j + 1) & m) * N + i;
-            bs[0][pj][pi] = g.ibd[cc];
-            bs[1][pj][pi] = g.ibd[ce];
-            bs[2][pj][pi] = g.ibd[n + cc];
-            bs[3][pj][pi] = g.ibd[2 * n + cc];
-            bs[4][pj][pi] = g.ibd[2 * n + cn];
-            bs[5][pj][pi] = g.ibd[3 * n + cc];
+            const int cc = ((j0 - 1 + pj) & m) * N + ((i0 - 1 + pi) & m);
+#pragma unroll
+            for (int k = 0; k < 7; ++k) bs[k][pj][pi] = g.pf[(size_t)k * n + cc];
         }
     };
     if (early) {
@@ -362,22 +344,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4)
             d2 = tv0 - kb.s0 * dp;
             d3 = tv1 + kb.s0 * dp;
         } else {
-            const T au00 = g.a0 - g.dt * bs[0][pj][pi], au11 = g.a0 - g.dt * bs[1][pj][pi],
-                    au01 = -g.c - g.dt * bs[2][pj][pi];
-            const T av00 = g.a0 - g.dt * bs[3][pj][pi], av11 = g.a0 - g.dt * bs[4][pj][pi],
-                    av01 = -g.c - g.dt * bs[5][pj][pi];
-            const T idu = T(1) / (au00 * au11 - au01 * au01);
-            const T idv = T(1) / (av00 * av11 - av01 * av01);
-            const T su0 = (au11 + au01) * ih * idu, su1 = -(au01 + au00) * ih * idu;
-            const T sv0 = (av11 + av01) * ih * idv, sv1 = -(av01 + av00) * ih * idv;
-            const T tu0 = (au11 * r0 - au01 * r1) * idu, tu1 = (au00 * r1 - au01 * r0) * idu;
-            const T tv0 = (av11 * r2 - av01 * r3) * idv, tv1 = (av00 * r3 - av01 * r2) * idv;
-            const T S = ih * ((su0 - su1) + (sv0 - sv1));
-            dp = (ih * ((tu0 - tu1) + (tv0 - tv1)) - r4) / S;
-            d0 = tu0 - su0 * dp;
-            d1 = tu1 - su1 * dp;
-            d2 = tv0 - sv0 * dp;
-            d3 = tv1 - sv1 * dp;
+            T f[7];
+#pragma unroll
+            for (int k = 0; k < 7; ++k) f[k] = bs[k][pj][pi];
+            patch_solve(f, ih, r0, r1, r2, r3, r4, d0, d1, d2, d3, dp);
         }
         ds[0][pj][pi] = d0;
         ds[1][pj][pi] = d1;
@@ -956,6 +926,35 @@ __global__ void k_sc_diag(GridK<double> g, double* __restrict__ dinv) {
 }
 void launch_sc_diag(const GridK<double>& g, double* dinv, cudaStream_t s) {
     launch_pdl(k_sc_diag, dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s, g, dinv);
+}
+
+// Vanka patch factors of every cell (read by patch_solve): the 2 x 2 velocity blocks of the patch,
+// A_u = [[a0 - dt B(uL,uL), -c - dt B(uL,uR)], [., a0 - dt B(uR,uR)]] and A_v likewise (B from the
+// patch entries, zero outside IB-active tiles), inverted in closed form, and 1 / S with
+// S = g^T A_u^{-1} g + g^T A_v^{-1} g, g = (1/h, -1/h).
+__global__ void k_patch_factors(GridK<double> g, double* __restrict__ pf) {
+    pdl_entry();
+    const int N = g.N, n = N * N, m = N - 1;
+    const int i = blockIdx.x * g.tx + threadIdx.x, j = blockIdx.y * g.ty + threadIdx.y;
+    const int c = j * N + i, ce = j * N + ((i + 1) & m), cn = ((j + 1) & m) * N + i;
+    const double au00 = g.a0 - g.dt * g.ibd[c], au11 = g.a0 - g.dt * g.ibd[ce], au01 = -g.c - g.dt * g.ibd[n + c];
+    const double av00 = g.a0 - g.dt * g.ibd[2 * n + c], av11 = g.a0 - g.dt * g.ibd[2 * n + cn],
+                 av01 = -g.c - g.dt * g.ibd[3 * n + c];
+    const double idu = 1.0 / (au00 * au11 - au01 * au01), idv = 1.0 / (av00 * av11 - av01 * av01);
+    const double a00u = au11 * idu, a01u = -au01 * idu, a11u = au00 * idu;
+    const double a00v = av11 * idv, a01v = -av01 * idv, a11v = av00 * idv;
+    const double ih = g.inv_h;
+    const double S = ih * ih * ((a00u - 2.0 * a01u + a11u) + (a00v - 2.0 * a01v + a11v));
+    pf[c] = a00u;
+    pf[n + c] = a01u;
+    pf[2 * n + c] = a11u;
+    pf[3 * n + c] = a00v;
+    pf[4 * n + c] = a01v;
+    pf[5 * n + c] = a11v;
+    pf[6 * n + c] = 1.0 / S;
+}
+void launch_patch_factors(const GridK<double>& g, double* pf, cudaStream_t s) {
+    launch_pdl(k_patch_factors, dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s, g, pf);
 }
 
 #define SIB_GRID_LAUNCH(kern, ...) launch_pdl(kern<T>, dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s, __VA_ARGS__)

@@ -121,9 +121,12 @@ __global__ void __launch_bounds__(256) k_ras_setup(RasGeo G, RasIB ib, double a0
         double* row = A + (size_t)q * n;
         if (comp < 2) {
             row[q] = a0;
+            // couplings to dofs of the subdomain, at local coordinates taken modulo N (on small grids a
+            // neighbour or window offset can wrap around onto the far side of the same subdomain; the
+            // subdomain itself never wraps onto itself, so the local index is unique)
             const int nb[4][2] = {{ii + 1, jj}, {ii - 1, jj}, {ii, jj + 1}, {ii, jj - 1}};
             for (int s2 = 0; s2 < 4; ++s2) {
-                const int col = ras_index(G, comp, nb[s2][0], nb[s2][1]);
+                const int col = ras_index(G, comp, nb[s2][0] & m, nb[s2][1] & m);
                 if (col >= 0) row[col] -= c;
             }
             // G p: u(i, j) -> (p(i, j) - p(i-1, j)) / h;  v(i, j) -> (p(i, j) - p(i, j-1)) / h
@@ -139,7 +142,7 @@ __global__ void __launch_bounds__(256) k_ras_setup(RasGeo G, RasIB ib, double a0
                     const int qt = (gj % ib.ty) * ib.tx + (gi % ib.tx);
                     for (int dj = -WR; dj <= WR; ++dj)
                         for (int di = -WR; di <= WR; ++di) {
-                            const int col = ras_index(G, comp, ii + di, jj + dj);
+                            const int col = ras_index(G, comp, (ii + di) & m, (jj + dj) & m);
                             if (col >= 0) row[col] -= dt * w[(size_t)((dj + WR) * WD + (di + WR)) * per + qt];
                         }
                 }

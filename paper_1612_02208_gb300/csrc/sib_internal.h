@@ -74,6 +74,8 @@ struct GridK {
     const T* ibd;                    // 4 n: B(f,f) on u faces, B(u_ij,u_i+1j), B(f,f) on v, B(v_ij,v_ij+1)
     const unsigned char* tile;       // per-tile IB flag (dilated by one tile), may be null
     const T* dinv;                   // SC: 1/diag(A_IB) on u and v faces, 1/diag(D diag(A_IB)^-1 G) on cells
+    const T* pf;                     // Vanka: 7 n patch factors per cell (A_u^{-1}: 00, 01, 11; A_v^{-1}: 00, 01,
+                                     // 11; 1 / pressure Schur complement), computed at set-up
     int* err;                        // host-visible error word (SIB_DEV_ERR_*), may be null
 };
 
@@ -154,6 +156,8 @@ template <typename T> void launch_apply_AIB(const GridK<T>& g, const T* u, T* y,
 template <typename T> void launch_gradient(const GridK<T>& g, const T* p, T* gu, cudaStream_t s);
 template <typename T> void launch_divergence(const GridK<T>& g, const T* u, T* d, cudaStream_t s);
 template <typename T> void launch_jacobi_M(const GridK<T>& g, const T* r, T* z, T scale, cudaStream_t s);
+// Vanka patch factors of every cell of the level from its patch entries (FP64, set-up)
+void launch_patch_factors(const GridK<double>& g, double* pf, cudaStream_t s);
 // one pass of a symmetric multicolour Gauss-Seidel sweep on A_IB (cells == false) or on
 // Mh = D diag(A_IB)^{-1} G (cells == true): pass = colour 0 or 1, or -1 for the first pass from zero
 template <typename T> void launch_sgs_pass(const GridK<T>& g, bool cells, int pass, T scale, const T* q, T* z,

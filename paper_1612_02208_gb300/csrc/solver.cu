@@ -46,6 +46,7 @@ struct LevelBuf {
     void* tv[8] = {};
     void* tp[6] = {};
     void* dinv = nullptr;   // 3 n: SC diagonals
+    void* pf = nullptr;     // 7 n: Vanka patch factors
     // Krylov-wrapped smoothing: WRAP_MAXK + 1 Arnoldi vectors, WRAP_MAXK preconditioned ones, a work
     // vector (3 n each) and the step's small FP64 arrays
     void* wV = nullptr;
@@ -238,6 +239,7 @@ GridK<T> gridk(sib_ctx* c, int l) {
     while ((1 << lg) < lv.ty) ++lg;
     g.lgty = lg;
     g.dinv = (const T*)lv.p[pi].dinv;
+    g.pf = (const T*)lv.p[pi].pf;
     g.err = c->herr;
     return g;
 }
@@ -725,6 +727,7 @@ void alloc_level_bufs(sib_ctx* c) {
             b.r = dalloc(c, e * 3 * n);
             b.fib = dalloc(c, e * 2 * n);
             b.ibd = dalloc(c, e * 4 * n);
+            b.pf = dalloc(c, e * 7 * n);
         }
         lv.tileFlag = (unsigned char*)dalloc(c, 2 * (size_t)lv.ntiles);
         lv.tiles = (int*)dalloc(c, sizeof(int) * (size_t)lv.ntiles);
@@ -1083,6 +1086,13 @@ void setup(sib_ctx* c, cudaStream_t s) {
         KL(c, launch_gauss_jordan(c->Aug, n, c->info, c->piv, c->gjWork, c->aux));
         KL(c, launch_extract_pinv(c->Aug, c->piv, n, c->L[0].N, c->rho, c->Pinv, c->aux));
         CK(cudaEventRecord(c->evJoin, c->aux));
+    }
+    // Vanka patch factors (they depend on the fluid parameters and the patch entries)
+    for (int l = 1; l <= c->lmax; ++l) {
+        Level& lv = c->L[l];
+        const int64_t n7 = 7LL * lv.N * lv.N;
+        KL(c, launch_patch_factors(gridk<double>(c, l), (double*)lv.p[0].pf, s));
+        KL(c, (launch_convert<double, float>((const double*)lv.p[0].pf, (float*)lv.p[1].pf, n7, s)));
     }
     if (c->opts.smoother == SIB_SMOOTHER_RAS && c->lmax > 0) ras_setup_all(c, s);
     if (c->opts.smoother == SIB_SMOOTHER_SC) {
@@ -1551,8 +1561,8 @@ void time_kernel(sib_ctx* c, int kernel, int l, int reps, cudaStream_t s, double
         }
     };
     switch (kernel) {
-        case SIB_KERNEL_VANKA:   // x, b read; xo written; fib (2) + ibd (4) words in active tiles
-            by = 9.0 * n * w + 6.0 * active * w;
+        case SIB_KERNEL_VANKA:   // x, b read; xo written; fib (2) + patch factors (7) words in active tiles
+            by = 9.0 * n * w + 9.0 * active * w;
             break;
         case SIB_KERNEL_RESIDUAL:
             by = 9.0 * n * w + 2.0 * active * w;
