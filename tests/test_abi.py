@@ -53,3 +53,32 @@ def test_create_fails_loudly_without_a_gpu():
     c = ctypes.c_void_p()
     rc = lib.sib_create(ctypes.byref(c), 32, 8)
     assert rc in (sib.SIB_ERR_CUDA, sib.SIB_ERR_ALLOC) and not c.value
+
+
+def header_struct_fields(name):
+    """(member, type) pairs of `typedef struct { ... } name;` in include/sib.h, in declaration order."""
+    text = open(os.path.join(ROOT, "include", "sib.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct\s*\{(.*?)\}\s*" + name + r"\s*;", text, flags=re.S).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        m = re.match(r"(int|double)\s+(.*)", decl)
+        assert m, decl
+        for member in m.group(2).split(","):
+            out.append((member.strip(), m.group(1)))
+    return out
+
+
+def test_options_struct_layout_matches_the_header():
+    """The ctypes mirror of sib_opts has the header's members in the same order with the same types
+    (a shorter or reordered mirror would let sib_default_opts write past it or scramble options)."""
+    ctype = {"int": ctypes.c_int, "double": ctypes.c_double}
+    want = [(n, ctype[t]) for n, t in header_struct_fields("sib_opts")]
+    assert [(n, t) for n, t in sib.SibOpts._fields_] == want
+    lib = sib.load()
+    o = sib.SibOpts()
+    lib.sib_default_opts(ctypes.byref(o))
+    assert (o.fuse_small, o.smooth_krylov, o.sc_relax, o.box, o.box_overlap) == (1, 0, sib.RELAX_JACOBI, 4, 1)
