@@ -23,7 +23,7 @@ namespace {
 
 template <typename T>
 struct SmallSmem {
-    T *x, *xt, *b, *r, *fib, *ibd, *dinv, *pd;
+    T *x, *xt, *b, *r, *fib, *pf, *dinv, *pd;
     T *y, *d, *gq, *ya, *gq2, *dA2, *dA, *sv, *dp, *dM;
     T *b0, *x0, *win;
     int* tiles;
@@ -47,7 +47,7 @@ __host__ __device__ inline size_t small_layout(int n, int n0, int nTiles, int pe
     take(&q->b, 3 * n);
     take(&q->r, 3 * n);
     take(&q->fib, 2 * n);
-    take(&q->ibd, 4 * n);
+    take(&q->pf, 7 * n);
     take(&q->dinv, 3 * n);
     const size_t tmp = off;   // SC temporaries, or the Vanka corrections (5 n <= 17 n)
     take(&q->y, 2 * n);
@@ -152,28 +152,15 @@ __device__ void sm_vanka(const GridK<T>& g, const SmallSmem<T>& s, const T* x, c
         const int i = c & m, j = c >> ilog2(N);
         const int ce = j * N + ((i + 1) & m), cn = ((j + 1) & m) * N + i;
         const T r0 = s.r[c], r1 = s.r[ce], r2 = s.r[n + c], r3 = s.r[n + cn], r4 = s.r[2 * n + c];
-        const bool act = g.tile != nullptr && g.tile[(j >> g.lgty) * g.ntx + (i >> g.lgtx)];
-        T au00 = g.a0, au11 = g.a0, au01 = -g.c, av00 = g.a0, av11 = g.a0, av01 = -g.c;
-        if (act) {
-            au00 -= g.dt * g.ibd[c];
-            au11 -= g.dt * g.ibd[ce];
-            au01 -= g.dt * g.ibd[n + c];
-            av00 -= g.dt * g.ibd[2 * n + c];
-            av11 -= g.dt * g.ibd[2 * n + cn];
-            av01 -= g.dt * g.ibd[3 * n + c];
-        }
-        const T idu = T(1) / (au00 * au11 - au01 * au01);
-        const T idv = T(1) / (av00 * av11 - av01 * av01);
-        const T su0 = (au11 + au01) * ih * idu, su1 = -(au01 + au00) * ih * idu;
-        const T sv0 = (av11 + av01) * ih * idv, sv1 = -(av01 + av00) * ih * idv;
-        const T tu0 = (au11 * r0 - au01 * r1) * idu, tu1 = (au00 * r1 - au01 * r0) * idu;
-        const T tv0 = (av11 * r2 - av01 * r3) * idv, tv1 = (av00 * r3 - av01 * r2) * idv;
-        const T S = ih * ((su0 - su1) + (sv0 - sv1));
-        const T dp = (ih * ((tu0 - tu1) + (tv0 - tv1)) - r4) / S;
-        s.pd[c] = tu0 - su0 * dp;
-        s.pd[n + c] = tu1 - su1 * dp;
-        s.pd[2 * n + c] = tv0 - sv0 * dp;
-        s.pd[3 * n + c] = tv1 - sv1 * dp;
+        T f[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) f[k] = g.pf[k * n + c];   // the cell's set-up patch factors
+        T d0, d1, d2, d3, dp;
+        patch_solve(f, ih, r0, r1, r2, r3, r4, d0, d1, d2, d3, dp);
+        s.pd[c] = d0;
+        s.pd[n + c] = d1;
+        s.pd[2 * n + c] = d2;
+        s.pd[3 * n + c] = d3;
         s.pd[4 * n + c] = dp;
     }
     __syncthreads();
@@ -300,7 +287,7 @@ __global__ void __launch_bounds__(NT, 1) k_vcycle_small(const __grid_constant__ 
     small_layout<T>(n, a.n0, a.nTiles, per, a.ntiles, &s, smraw);
     // set-up data: not written by the kernels this one waits for (every array is a multiple of
     // 16 bytes: n is a multiple of 16)
-    block_copy16(s.ibd, G.ibd, sizeof(T) * 4 * n);
+    if (a.smoother == SIB_SMOOTHER_VANKA) block_copy16(s.pf, G.pf, sizeof(T) * 7 * n);
     if (a.smoother == SIB_SMOOTHER_SC) block_copy16(s.dinv, G.dinv, sizeof(T) * 3 * n);
     if (a.nTiles > 0) block_copy16(s.win, a.win, sizeof(T) * (size_t)a.nTiles * 2 * WIN_SIZE * per);
     for (int q = threadIdx.x; q < a.nTiles; q += NT) s.tiles[q] = a.tiles[q];
@@ -311,7 +298,7 @@ __global__ void __launch_bounds__(NT, 1) k_vcycle_small(const __grid_constant__ 
     __syncthreads();
     GridK<T> g = G;
     g.fib = s.fib;
-    g.ibd = s.ibd;
+    g.pf = s.pf;
     g.dinv = s.dinv;
     g.tile = G.tile ? s.tile : nullptr;
     const bool ib = a.nTiles > 0 && g.tile != nullptr;
