@@ -74,7 +74,9 @@ __device__ __forceinline__ int face_slot(const RasIB& ib, int i, int j) {
 }
 
 // Box classification: box k is listed if some face of its subdomain has a nonzero row of the IB
-// operator (a window entry != 0); the other boxes' local operators have no IB terms.
+// operator (a window entry != 0); the other boxes' local operators have no IB terms.  The list is
+// filled through an atomic counter, so its order (and each box's storage slot) can differ between
+// set-ups; every listed box's inverse depends only on that box, so the results do not.
 __global__ void k_ras_classify(RasGeo G, RasIB ib, int* __restrict__ list, int* __restrict__ count) {
     const int k = blockIdx.x;
     const int I = k % G.nbs, J = k / G.nbs, m = G.N - 1;
