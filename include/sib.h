@@ -156,6 +156,11 @@ int sib_num_levels(const sib_ctx* ctx);                  /* lmax + 1; level 0 is
 int sib_level_size(const sib_ctx* ctx, int level);       /* N_l                                 */
 /* y = L^l x (prec: SIB_PREC_FP64 -> double*, SIB_PREC_FP32 -> float*). */
 int sib_apply_operator(sib_ctx* ctx, int level, int prec, const void* x, void* y, void* stream);
+/* y = L^l x for the lid-driven cavity (Sec. 5: no-slip walls) instead of the periodic box.  Same
+ * layout; the seam faces u(0, j) and v(i, 0) are the wall faces: x must hold 0 there and y gets 0
+ * there.  Tangential wall rows use the ghost value -q_inside (the lid enters the right-hand side
+ * only); the structure must keep its Peskin support 2.5 h away from the walls. */
+int sib_cavity_apply_operator(sib_ctx* ctx, int level, int prec, const void* x, void* y, void* stream);
 /* f = [S K J]^l u on the velocity faces: u and f hold 2 N_l^2 values [u | v]. */
 int sib_apply_ib(sib_ctx* ctx, int level, int prec, const void* u, void* f, void* stream);
 /* x <- `sweeps` smoothing sweeps for L^l x = b (in place), level >= 1. */

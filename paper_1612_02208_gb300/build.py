@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libsib.so")
 OBJDIR = os.path.join(PKG, "_build")
-SOURCES = ["kernels_grid.cu", "kernels_ib.cu", "kernels_krylov.cu", "kernels_small.cu", "kernels_wrap.cu", "kernels_ras.cu", "solver.cu", "noalloc.cu"]
+SOURCES = ["kernels_grid.cu", "kernels_ib.cu", "kernels_krylov.cu", "kernels_small.cu", "kernels_wrap.cu", "kernels_ras.cu", "kernels_cavity.cu", "solver.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

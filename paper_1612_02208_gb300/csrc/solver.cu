@@ -1943,6 +1943,24 @@ int sib_apply_operator(sib_ctx* c, int l, int prec, const void* x, void* y, void
     API_END(c)
 }
 
+int sib_cavity_apply_operator(sib_ctx* c, int l, int prec, const void* x, void* y, void* stream) {
+    API_BEGIN(c)
+    require_setup(c);
+    check_level(c, l, 0);
+    if (!valid_prec(prec) || !x || !y) throw SibError(SIB_ERR_ARG, "bad precision or null pointer");
+    cudaStream_t s = S(stream);
+    if (prec == SIB_PREC_FP64) {
+        ib_apply<double>(c, l, (const double*)x, s);
+        KL(c, launch_cavity_apply<double>(gridk<double>(c, l), (const double*)x, (double*)y, s));
+    } else {
+        ib_apply<float>(c, l, (const float*)x, s);
+        KL(c, launch_cavity_apply<float>(gridk<float>(c, l), (const float*)x, (float*)y, s));
+    }
+    kcheck(c);
+    return SIB_OK;
+    API_END(c)
+}
+
 int sib_apply_ib(sib_ctx* c, int l, int prec, const void* u, void* f, void* stream) {
     API_BEGIN(c)
     require_setup(c);
