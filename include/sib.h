@@ -161,6 +161,9 @@ int sib_apply_operator(sib_ctx* ctx, int level, int prec, const void* x, void* y
  * there.  Tangential wall rows use the ghost value -q_inside (the lid enters the right-hand side
  * only); the structure must keep its Peskin support 2.5 h away from the walls. */
 int sib_cavity_apply_operator(sib_ctx* ctx, int level, int prec, const void* x, void* y, void* stream);
+/* x <- `sweeps` additive Vanka sweeps (Alg. 2, one-cell patches; damping: the Vanka omega of the options,
+ * 0.8 by default) for the lid-driven cavity's L^l x = b, in place, level >= 1; wall-face entries stay 0. */
+int sib_cavity_smooth(sib_ctx* ctx, int level, int prec, void* x, const void* b, int sweeps, void* stream);
 /* f = [S K J]^l u on the velocity faces: u and f hold 2 N_l^2 values [u | v]. */
 int sib_apply_ib(sib_ctx* ctx, int level, int prec, const void* u, void* f, void* stream);
 /* x <- `sweeps` smoothing sweeps for L^l x = b (in place), level >= 1. */

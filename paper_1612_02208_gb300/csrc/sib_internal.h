@@ -147,6 +147,10 @@ struct SmallArgs {
 template <typename T> void launch_residual(const GridK<T>& g, const T* x, const T* b, T* r, cudaStream_t s);
 // y = L x of the lid-driven cavity on the periodic layout (kernels_cavity.cu); wall-face entries 0
 template <typename T> void launch_cavity_apply(const GridK<T>& g, const T* x, T* y, cudaStream_t s);
+// one additive Vanka sweep of the cavity: r = b - L x, per-cell patch solves into d (5 n), xo = x + omega
+// (weighted corrections); g.fib must hold [S K J] x (kernels_cavity.cu)
+template <typename T>
+void launch_cavity_vanka(const GridK<T>& g, const T* x, const T* b, T* r, T* d, T* xo, T omega, cudaStream_t s);
 template <typename T> void launch_vanka(const GridK<T>& g, const T* x, const T* b, T* xo, cudaStream_t s);
 template <typename T> void launch_restrict(int Nc, const T* rf, T* bc, cudaStream_t s);
 template <typename T> void launch_prolong_add(int Nc, const T* ec, T* xf, cudaStream_t s);

@@ -47,6 +47,7 @@ struct LevelBuf {
     void* tp[6] = {};
     void* dinv = nullptr;   // 3 n: SC diagonals
     void* pf = nullptr;     // 7 n: Vanka patch factors
+    void* cav = nullptr;    // 5 n: cavity Vanka patch corrections (allocated on first use)
     // Krylov-wrapped smoothing: WRAP_MAXK + 1 Arnoldi vectors, WRAP_MAXK preconditioned ones, a work
     // vector (3 n each) and the step's small FP64 arrays
     void* wV = nullptr;
@@ -1616,6 +1617,28 @@ void time_kernel(sib_ctx* c, int kernel, int l, int reps, cudaStream_t s, double
 }  // namespace
 
 // ============================================================================================
+namespace {
+template <typename T>
+void cavity_smooth_impl(sib_ctx* c, int l, T* x, const T* b, int sweeps, cudaStream_t s) {
+    Level& lv = c->L[l];
+    LevelBuf& lb = lv.p[Prec<T>::id];
+    const size_t n = (size_t)lv.N * lv.N;
+    if (!lb.cav) lb.cav = dalloc(c, sizeof(T) * 5 * n);
+    const double om = c->opts.smoother == SIB_SMOOTHER_VANKA ? c->opts.omega : 0.8;
+    GridK<T> g = gridk<T>(c, l);
+    T* cur = x;
+    T* nxt = (T*)lb.xt;
+    for (int k = 0; k < sweeps; ++k) {
+        ib_apply<T>(c, l, cur, s);
+        launch_cavity_vanka<T>(g, cur, b, (T*)lb.r, (T*)lb.cav, nxt, (T)om, s);
+        c->launches += 3;
+        std::swap(cur, nxt);
+    }
+    if (cur != x) CK(cudaMemcpyAsync(x, cur, sizeof(T) * 3 * n, cudaMemcpyDeviceToDevice, s));
+}
+
+}  // namespace
+
 extern "C" {
 
 void sib_default_opts(sib_opts* o) {
@@ -1956,6 +1979,20 @@ int sib_cavity_apply_operator(sib_ctx* c, int l, int prec, const void* x, void* 
         ib_apply<float>(c, l, (const float*)x, s);
         KL(c, launch_cavity_apply<float>(gridk<float>(c, l), (const float*)x, (float*)y, s));
     }
+    kcheck(c);
+    return SIB_OK;
+    API_END(c)
+}
+
+int sib_cavity_smooth(sib_ctx* c, int l, int prec, void* x, const void* b, int sweeps, void* stream) {
+    API_BEGIN(c)
+    require_setup(c);
+    check_level(c, l, 1);
+    if (!valid_prec(prec) || !x || !b || sweeps < 0) throw SibError(SIB_ERR_ARG, "bad argument");
+    if (prec == SIB_PREC_FP64)
+        cavity_smooth_impl<double>(c, l, (double*)x, (const double*)b, sweeps, S(stream));
+    else
+        cavity_smooth_impl<float>(c, l, (float*)x, (const float*)b, sweeps, S(stream));
     kcheck(c);
     return SIB_OK;
     API_END(c)

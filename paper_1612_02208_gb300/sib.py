@@ -39,7 +39,7 @@ EXPORTS = [
     "sib_default_opts", "sib_create", "sib_destroy", "sib_last_error", "sib_set_fluid", "sib_set_structure",
     "sib_set_stiffness", "sib_set_options", "sib_set_eigen_estimates", "sib_get_eigen_estimates", "sib_setup",
     "sib_solve", "sib_solve_host", "sib_solve_rhs", "sib_grad", "sib_num_levels", "sib_level_size",
-    "sib_apply_operator", "sib_cavity_apply_operator", "sib_apply_ib", "sib_smooth", "sib_residual_restrict", "sib_prolong_add",
+    "sib_apply_operator", "sib_cavity_apply_operator", "sib_cavity_smooth", "sib_apply_ib", "sib_smooth", "sib_residual_restrict", "sib_prolong_add",
     "sib_coarse_solve", "sib_vcycle", "sib_interp", "sib_spread", "sib_time_kernel", "sib_launch_count",
     "sib_device_bytes", "sib_spread_noalloc", "sib_advance_markers",
 ]
@@ -119,6 +119,7 @@ def load(build_if_missing: bool = True):
         "sib_level_size": (I, [ctx, I]),
         "sib_apply_operator": (I, [ctx, I, I, P, P, P]),
         "sib_cavity_apply_operator": (I, [ctx, I, I, P, P, P]),
+        "sib_cavity_smooth": (I, [ctx, I, I, P, P, I, P]),
         "sib_apply_ib": (I, [ctx, I, I, P, P, P]),
         "sib_smooth": (I, [ctx, I, I, P, P, I, P]),
         "sib_residual_restrict": (I, [ctx, I, I, P, P, P, P]),
@@ -292,6 +293,12 @@ class Solver:
         y = torch.empty_like(x) if y is None else y
         self._check(self.lib.sib_cavity_apply_operator(self.ctx, int(l), self._prec(x), _ptr(x), _ptr(y), _stream()))
         return y
+
+    def cavity_smooth(self, l, x, b, sweeps=1):
+        """x <- `sweeps` additive Vanka sweeps of the lid-driven cavity, in place."""
+        self._check(self.lib.sib_cavity_smooth(self.ctx, int(l), self._prec(x), _ptr(x), _ptr(b), int(sweeps),
+                                               _stream()))
+        return x
 
     def apply_ib(self, l, u, f=None):
         torch = _torch()
