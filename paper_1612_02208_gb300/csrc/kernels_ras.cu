@@ -8,11 +8,13 @@
 // (row-major within each); ne = 3 e^2 + 2 e dofs.  Owned dofs: the u, v and p of the core cells
 // (o <= ii, jj < o + b), nown = 3 b^2, ordered u, v, p and row-major.
 //
-// Set-up (FP64): the local operator L_k = R_k L R_k^T is assembled in shared memory from the
-// stencil (A, G, -D) and the IB windows, inverted by Gauss-Jordan with partial pivoting, and the
-// owned rows of the inverse are stored (column-major, FP64 and FP32).  Boxes whose subdomain meets
-// no IB window all have the same operator (the grid is uniform and periodic): one shared inverse
-// per level serves them.
+// Set-up (FP64): the local operator L_k = R_k L R_k^T is assembled from the stencil (A, G, -D) and the
+// IB windows, inverted by Gauss-Jordan with partial pivoting, and the owned rows of the inverse are
+// stored (column-major, FP64 and FP32).  Boxes whose subdomain meets no IB window all have the same
+// operator (the grid is uniform and periodic): one shared inverse per level serves them.  Subdomains
+// up to RAS_EMAX_SMEM cells wide are eliminated in shared memory and corrected by a persistent
+// kernel; wider ones (the paper's 8 x 8 boxes with overlap 2 and up) are eliminated in a global
+// workspace and corrected by a batched product over tiles of boxes.
 #include "sib_internal.h"
 
 namespace sib {
@@ -389,7 +391,329 @@ __global__ void k_box_slots(const int* __restrict__ list, const int* __restrict_
     if (s < *count) slotOfBox[list[s]] = s;
 }
 
+// ---- subdomains wider than RAS_EMAX_SMEM cells (e <= RAS_EMAX, ne <= 800) ----------------------
+// The local operator (up to 5 MB in FP64) no longer fits shared memory.  Each set-up block assembles
+// its matrix in a global workspace and eliminates there, with the pivot column and the scaled pivot
+// row in shared memory.  The shared-inverse correction becomes one batched product per level,
+// C (nown x boxes) = Inv (nown x ne) R (ne x boxes), over tiles of boxes; the IB boxes keep one block
+// each.
+
+// Row q of L_k for the subdomain with corner cell (i0, j0), added into `row` (zeroed by the caller):
+// the same stencil and window entries as the shared-memory set-up above.
+__device__ void ras_assemble_row(const RasGeo& G, const RasIB& ib, double a0, double c, double inv_h, double dt,
+                                 bool withIB, int i0, int j0, int q, double* row) {
+    const int m = G.N - 1, per = ib.tx * ib.ty;
+    int comp, ii, jj;
+    ras_dof(G, q, comp, ii, jj);
+    if (comp < 2) {
+        row[q] = a0;
+        const int nb[4][2] = {{ii + 1, jj}, {ii - 1, jj}, {ii, jj + 1}, {ii, jj - 1}};
+        for (int s2 = 0; s2 < 4; ++s2) {
+            const int col = ras_index(G, comp, nb[s2][0] & m, nb[s2][1] & m);
+            if (col >= 0) row[col] -= c;
+        }
+        const int pc = ras_index(G, 2, ii, jj);
+        const int pm = comp == 0 ? ras_index(G, 2, ii - 1, jj) : ras_index(G, 2, ii, jj - 1);
+        if (pc >= 0) row[pc] += inv_h;
+        if (pm >= 0) row[pm] -= inv_h;
+        if (withIB) {
+            const int gi = (i0 + ii) & m, gj = (j0 + jj) & m;
+            const int slot = face_slot(ib, gi, gj);
+            if (slot >= 0) {
+                const double* w = ib.win + ((size_t)(slot * 2 + comp) * WIN_SIZE) * per;
+                const int qt = (gj % ib.ty) * ib.tx + (gi % ib.tx);
+                for (int dj = -WR; dj <= WR; ++dj)
+                    for (int di = -WR; di <= WR; ++di) {
+                        const int col = ras_index(G, comp, (ii + di) & m, (jj + dj) & m);
+                        if (col >= 0) row[col] -= dt * w[(size_t)((dj + WR) * WD + (di + WR)) * per + qt];
+                    }
+            }
+        }
+    } else {
+        row[ras_index(G, 0, ii + 1, jj)] -= inv_h;
+        row[ras_index(G, 0, ii, jj)] += inv_h;
+        row[ras_index(G, 1, ii, jj + 1)] -= inv_h;
+        row[ras_index(G, 1, ii, jj)] += inv_h;
+    }
+}
+
+// Block b of a launch inverts matrix first + b (0: the shared IB-free operator; s > 0: the operator
+// of box list[s - 1]) in work + b ne^2 by Gauss-Jordan with partial (row) pivoting, then stores the
+// owned rows of the inverse column-major at slot first + b, as the shared-memory set-up does.
+constexpr int RAS_BIG_SETUP_THREADS = 512;
+__global__ void __launch_bounds__(RAS_BIG_SETUP_THREADS)
+    k_ras_setup_big(RasGeo G, RasIB ib, double a0, double c, double inv_h, double dt, const int* __restrict__ list,
+                    int first, double* __restrict__ work, double* __restrict__ inv64, float* __restrict__ inv32,
+                    int* __restrict__ info) {
+    extern __shared__ double smem_big[];
+    const int n = G.ne, tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    double* colk = smem_big;                          // n: column kk before the step
+    double* rowk = colk + n;                          // n: row kk after scaling
+    double* redv = rowk + n;                          // 32
+    int* redi = reinterpret_cast<int*>(redv + 32);    // 32
+    int* perm = redi + 32;                            // n
+    const int mi = first + blockIdx.x;
+    const bool withIB = mi > 0;
+    const int k = withIB ? list[mi - 1] : 0;
+    const int I = k % G.nbs, J = k / G.nbs;
+    double* A = work + (size_t)blockIdx.x * n * n;
+    for (size_t t = tid; t < (size_t)n * n; t += nt) A[t] = 0.0;
+    __syncthreads();
+    for (int q = tid; q < n; q += nt)   // every thread writes only its own rows
+        ras_assemble_row(G, ib, a0, c, inv_h, dt, withIB, I * G.b - G.o, J * G.b - G.o, q, A + (size_t)q * n);
+    __syncthreads();
+    for (int kk = 0; kk < n; ++kk) {
+        double best = -1.0;
+        int bi = kk;
+        for (int i = kk + tid; i < n; i += nt) {
+            const double v = fabs(A[(size_t)i * n + kk]);
+            if (v > best) {
+                best = v;
+                bi = i;
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+            if (ov > best || (ov == best && oi < bi)) {
+                best = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            redv[wid] = best;
+            redi[wid] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double bv = redv[0];
+            int bx = redi[0];
+            for (int w2 = 1; w2 < nw; ++w2)
+                if (redv[w2] > bv || (redv[w2] == bv && redi[w2] < bx)) {
+                    bv = redv[w2];
+                    bx = redi[w2];
+                }
+            perm[kk] = bx;
+            if (!(bv > 0.0)) atomicExch(info, 1);
+        }
+        __syncthreads();
+        const int p = perm[kk];
+        if (p != kk)
+            for (int j = tid; j < n; j += nt) {
+                const double t = A[(size_t)kk * n + j];
+                A[(size_t)kk * n + j] = A[(size_t)p * n + j];
+                A[(size_t)p * n + j] = t;
+            }
+        __syncthreads();
+        const double piv = A[(size_t)kk * n + kk];
+        const double pinv = piv != 0.0 ? 1.0 / piv : 0.0;
+        for (int i = tid; i < n; i += nt) colk[i] = A[(size_t)i * n + kk];
+        __syncthreads();
+        for (int j = tid; j < n; j += nt) {
+            const double v = (j == kk ? 1.0 : A[(size_t)kk * n + j]) * pinv;
+            rowk[j] = v;
+            A[(size_t)kk * n + j] = v;
+        }
+        __syncthreads();
+        // rank-one update of the other rows, one warp per row (coalesced); a row with a zero entry in
+        // column kk is unchanged (its column-kk entry stays 0), so it is skipped
+        for (int i = wid; i < n; i += nw) {
+            const double ci = colk[i];
+            if (i == kk || ci == 0.0) continue;
+            double* Ai = A + (size_t)i * n;
+            for (int j = lane; j < n; j += 32) Ai[j] = (j == kk ? 0.0 : Ai[j]) - ci * rowk[j];
+        }
+        __syncthreads();
+    }
+    for (int kk = n - 1; kk >= 0; --kk) {   // (P A)^{-1} P = A^{-1}
+        const int p = perm[kk];
+        if (p != kk)
+            for (int i = tid; i < n; i += nt) {
+                const double t = A[(size_t)i * n + kk];
+                A[(size_t)i * n + kk] = A[(size_t)i * n + p];
+                A[(size_t)i * n + p] = t;
+            }
+        __syncthreads();
+    }
+    const size_t base = (size_t)mi * n * G.nown;
+    for (int t = tid; t < n * G.nown; t += nt) {
+        const int q = t / G.nown, r = t - q * G.nown;
+        const double v = A[(size_t)ras_owned(G, r) * n + q];
+        inv64[base + t] = v;
+        inv32[base + t] = (float)v;
+    }
+}
+
+// Batched shared-inverse correction.  A block takes a tile of RAS_NBX consecutive boxes and all their
+// owned rows; the subdomain dofs q are taken in chunks of RAS_KC: the chunk of the inverse (rows
+// [q][row], contiguous in memory) is copied to shared memory asynchronously while the chunk of the
+// tile's residual windows is gathered, then warp w accumulates the owned rows lane + 32 a (a < RA)
+// for its RAS_BPT boxes.  The window chunk is stored [q][box] in 16-byte slots of VW boxes, slot s of
+// row q at position s ^ (q & 15): the gather's stores (8 dofs x 4 boxes per warp) and the product's
+// 16-byte broadcast loads are both free of bank conflicts.
+constexpr int RAS_KC = 32;
+constexpr int RAS_BW = 8;   // warps per block
+template <typename T>
+struct RasTile {
+    static constexpr int VW = 16 / (int)sizeof(T);   // boxes per 16-byte slot
+    static constexpr int NBX = 16 * VW;              // boxes per tile (16 slots)
+    static constexpr int BPT = NBX / RAS_BW;         // boxes per warp (two slots)
+};
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using type = float4;
+};
+template <>
+struct Vec16<double> {
+    using type = double2;
+};
+template <typename T>
+__device__ __forceinline__ T vget(const typename Vec16<T>::type& v, int c);
+template <>
+__device__ __forceinline__ float vget<float>(const float4& v, int c) {
+    return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
+}
+template <>
+__device__ __forceinline__ double vget<double>(const double2& v, int c) {
+    return c == 0 ? v.x : v.y;
+}
+
+template <typename T, int RA>
+__global__ void __launch_bounds__(32 * RAS_BW) k_ras_apply_big(RasGeo G, const int* __restrict__ slotOfBox,
+                                                              const T* __restrict__ inv, T omega,
+                                                              const T* __restrict__ r, const T* x, T* xo) {
+    using TL = RasTile<T>;
+    using V = typename Vec16<T>::type;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* Ms = reinterpret_cast<T*>(smem_raw);                             // RAS_KC x nown, [q][row]
+    T* Rc = Ms + (size_t)RAS_KC * G.nown;                               // RAS_KC x NBX, swizzled slots
+    int* qtab = reinterpret_cast<int*>(Rc + (size_t)RAS_KC * TL::NBX);  // ne: comp | ii << 8 | jj << 16
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = threadIdx.x; q < G.ne; q += blockDim.x) {
+        int comp, ii, jj;
+        ras_dof(G, q, comp, ii, jj);
+        qtab[q] = comp | (ii << 8) | (jj << 16);
+    }
+    pdl_entry();
+    const int N = G.N, n = N * N, m = N - 1, bb = G.b * G.b, nown = G.nown;
+    const int nboxes = G.nbs * G.nbs, k0 = blockIdx.x * TL::NBX;
+    const int s0 = 2 * warp, s1 = 2 * warp + 1;   // the warp's two slots: boxes warp BPT .. warp BPT + BPT - 1
+    T acc[RA][TL::BPT];
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+        for (int c2 = 0; c2 < TL::BPT; ++c2) acc[a][c2] = T(0);
+    int rowA[RA];
+#pragma unroll
+    for (int a = 0; a < RA; ++a) rowA[a] = lane + 32 * a < nown ? lane + 32 * a : 0;   // rows past nown: unused
+    for (int q0 = 0; q0 < G.ne; q0 += RAS_KC) {
+        const int kc = min(RAS_KC, G.ne - q0);
+        __syncthreads();   // the previous chunk is consumed; qtab is complete on the first pass
+        {   // the inverse's chunk: kc nown words from inv + q0 nown (16-byte aligned: RAS_KC nown words apart)
+            const int words = kc * nown, per16 = 16 / (int)sizeof(T), chunks = words / per16;
+            const T* src = inv + (size_t)q0 * nown;
+            for (int t = threadIdx.x; t < chunks; t += blockDim.x)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                                 (uint32_t)__cvta_generic_to_shared(Ms + t * per16)),
+                             "l"(src + (size_t)t * per16)
+                             : "memory");
+            for (int t = chunks * per16 + threadIdx.x; t < words; t += blockDim.x) Ms[t] = src[t];
+        }
+        {   // the windows' chunk: blocks of 8 dofs x 4 boxes, one per warp and pass
+            const int qi = lane & 7, bi = lane >> 3;
+            constexpr int QB = RAS_KC / 8, NBLK = QB * (TL::NBX / 4);
+            for (int blk = warp; blk < NBLK; blk += RAS_BW) {
+                const int ql = (blk % QB) * 8 + qi, box = (blk / QB) * 4 + bi;
+                const int q = q0 + ql, kb = k0 + box;
+                T v = T(0);
+                if (q < G.ne && kb < nboxes) {
+                    const int code = qtab[q];
+                    const int gi = ((kb % G.nbs) * G.b - G.o + ((code >> 8) & 0xff)) & m;
+                    const int gj = ((kb / G.nbs) * G.b - G.o + (code >> 16)) & m;
+                    v = r[(size_t)(code & 0xff) * n + (size_t)gj * N + gi];
+                }
+                Rc[ql * TL::NBX + (((box / TL::VW) ^ (ql & 15)) * TL::VW) + box % TL::VW] = v;
+            }
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        __syncthreads();
+#pragma unroll 4
+        for (int ql = 0; ql < kc; ++ql) {
+            T mv[RA];
+#pragma unroll
+            for (int a = 0; a < RA; ++a) mv[a] = Ms[ql * nown + rowA[a]];
+            const V v0 = *reinterpret_cast<const V*>(Rc + ql * TL::NBX + ((s0 ^ (ql & 15)) * TL::VW));
+            const V v1 = *reinterpret_cast<const V*>(Rc + ql * TL::NBX + ((s1 ^ (ql & 15)) * TL::VW));
+#pragma unroll
+            for (int a = 0; a < RA; ++a)
+#pragma unroll
+                for (int c2 = 0; c2 < TL::VW; ++c2) {
+                    acc[a][c2] += mv[a] * vget<T>(v0, c2);
+                    acc[a][TL::VW + c2] += mv[a] * vget<T>(v1, c2);
+                }
+        }
+    }
+#pragma unroll
+    for (int c2 = 0; c2 < TL::BPT; ++c2) {
+        const int kb = k0 + warp * TL::BPT + c2;
+        if (kb >= nboxes || (slotOfBox && slotOfBox[kb] >= 0)) continue;   // IB boxes: k_ras_apply_big_ib
+        const int I = kb % G.nbs, J = kb / G.nbs;
+#pragma unroll
+        for (int a = 0; a < RA; ++a) {
+            const int rr = lane + 32 * a;
+            if (rr >= nown) continue;
+            const int comp = rr / bb, rem = rr - comp * bb;
+            const size_t d = (size_t)comp * n + (size_t)(J * G.b + rem / G.b) * N + I * G.b + rem % G.b;
+            xo[d] = (x ? x[d] : T(0)) + omega * acc[a][c2];
+        }
+    }
+}
+
+// One block per listed IB box with a subdomain wider than RAS_EMAX_SMEM: four groups of 64 threads
+// each take a quarter of the q range for the owned rows lane64, lane64 + 64, ...; the partial sums
+// are added in shared memory in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ras_apply_big_ib(RasGeo G, const int* __restrict__ list,
+                                                         const T* __restrict__ inv, T omega,
+                                                         const T* __restrict__ r, const T* x, T* xo) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* rb = reinterpret_cast<T*>(smem_raw);   // ne
+    T* part = rb + G.ne;                      // 4 x nown
+    const int s = blockIdx.x, k = list[s];    // set-up data
+    pdl_entry();
+    const int I = k % G.nbs, J = k / G.nbs, N = G.N, n = N * N, m = N - 1, bb = G.b * G.b, nown = G.nown;
+    const int i0 = I * G.b - G.o, j0 = J * G.b - G.o;
+    for (int q = threadIdx.x; q < G.ne; q += blockDim.x) {
+        int comp, ii, jj;
+        ras_dof(G, q, comp, ii, jj);
+        rb[q] = r[(size_t)comp * n + (size_t)((j0 + jj) & m) * N + ((i0 + ii) & m)];
+    }
+    __syncthreads();
+    const T* M = inv + (size_t)(s + 1) * G.ne * nown;
+    const int lr = threadIdx.x & 63, part_id = threadIdx.x >> 6;
+    const int qchunk = (G.ne + 3) / 4;
+    const int qa = part_id * qchunk, qb = min(G.ne, qa + qchunk);
+    for (int rr = lr; rr < nown; rr += 64) {
+        T acc = T(0);
+#pragma unroll 4
+        for (int q = qa; q < qb; ++q) acc += M[(size_t)q * nown + rr] * rb[q];
+        part[part_id * nown + rr] = acc;
+    }
+    __syncthreads();
+    for (int rr = threadIdx.x; rr < nown; rr += blockDim.x) {
+        const T sum = ((part[rr] + part[nown + rr]) + part[2 * nown + rr]) + part[3 * nown + rr];
+        const int comp = rr / bb, rem = rr - comp * bb;
+        const size_t d = (size_t)comp * n + (size_t)(J * G.b + rem / G.b) * N + I * G.b + rem % G.b;
+        xo[d] = (x ? x[d] : T(0)) + omega * sum;
+    }
+}
+
 }  // namespace
+
+bool ras_big(int b, int o) { return b + 2 * o > RAS_EMAX_SMEM; }
 
 size_t ras_setup_smem(int b, int o) {
     const RasGeo G = ras_geo(16, b, o);
@@ -417,10 +741,47 @@ void launch_ras_setup(int N, int b, int o, const RasIB& ib, double a0, double c,
     k_ras_setup<<<1 + nIB, 256, smem, s>>>(G, ib, a0, c, inv_h, dt, list, inv64, inv32, info);
 }
 
+void launch_ras_setup_big(int N, int b, int o, const RasIB& ib, double a0, double c, double inv_h, double dt,
+                          const int* list, int first, int count, double* work, double* inv64, float* inv32, int* info,
+                          cudaStream_t s) {
+    const RasGeo G = ras_geo(N, b, o);
+    const size_t smem = sizeof(double) * (2 * (size_t)G.ne + 32) + sizeof(int) * (32 + (size_t)G.ne);
+    k_ras_setup_big<<<count, RAS_BIG_SETUP_THREADS, smem, s>>>(G, ib, a0, c, inv_h, dt, list, first, work, inv64,
+                                                                inv32, info);
+}
+
+namespace {
+template <typename T, int RA>
+void launch_ras_apply_big(const RasGeo& G, const int* slotOfBox, const T* inv, T omega, const T* r, const T* x, T* xo,
+                          cudaStream_t s) {
+    using TL = RasTile<T>;
+    const size_t smem = sizeof(T) * ((size_t)RAS_KC * G.nown + (size_t)RAS_KC * TL::NBX) + sizeof(int) * G.ne;
+    static thread_local size_t allowed = 48 * 1024;   // dynamic shared memory the kernel is enabled for
+    if (smem > allowed) {
+        cudaFuncSetAttribute(k_ras_apply_big<T, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allowed = smem;
+    }
+    const int tiles = (G.nbs * G.nbs + TL::NBX - 1) / TL::NBX;
+    launch_pdl(k_ras_apply_big<T, RA>, dim3(tiles), dim3(32 * RAS_BW), smem, s, G, slotOfBox, inv, omega, r, x, xo);
+}
+}  // namespace
+
 template <typename T>
 void launch_ras_apply(int N, int b, int o, const int* slotOfBox, const int* list, int nIB, const T* inv, T omega,
                       const T* r, const T* x, T* xo, cudaStream_t s) {
     const RasGeo G = ras_geo(N, b, o);
+    if (G.e > RAS_EMAX_SMEM) {   // rows per lane: nown <= 32 RA
+        if (G.nown <= 32)
+            launch_ras_apply_big<T, 1>(G, slotOfBox, inv, omega, r, x, xo, s);
+        else if (G.nown <= 64)
+            launch_ras_apply_big<T, 2>(G, slotOfBox, inv, omega, r, x, xo, s);
+        else
+            launch_ras_apply_big<T, 6>(G, slotOfBox, inv, omega, r, x, xo, s);
+        if (nIB > 0)
+            launch_pdl(k_ras_apply_big_ib<T>, dim3(nIB), dim3(256), sizeof(T) * ((size_t)G.ne + 4 * (size_t)G.nown), s,
+                       G, list, inv, omega, r, x, xo);
+        return;
+    }
     const size_t smem = sizeof(T) * (((size_t)G.ne * G.nown + 3) / 4 * 4 + (size_t)RAS_WARPS * G.ne * RAS_GB) +
                         sizeof(int) * G.ne;
     static thread_local size_t cachedSmem = 0;   // persistent grid: the blocks resident at once, per size

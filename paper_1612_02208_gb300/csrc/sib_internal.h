@@ -116,12 +116,22 @@ struct RasIB {
     const double* win;       // FP64 windows of the level
     int tx, ty, ntx;         // tile geometry of the level
 };
+// Subdomains up to RAS_EMAX_SMEM cells wide are set up and applied in shared memory; wider ones, up to
+// RAS_EMAX cells (ne <= 800), are eliminated in a global workspace and applied as a batched product.
+constexpr int RAS_EMAX_SMEM = 6;
+constexpr int RAS_EMAX = 16;
+bool ras_big(int b, int o);
 size_t ras_setup_smem(int b, int o);
 int ras_ne(int b, int o);
 void launch_ras_classify(int N, int b, int o, const RasIB& ib, int* list, int* count, cudaStream_t s);
 void launch_box_slots(int nboxes, const int* list, const int* count, int* slotOfBox, cudaStream_t s);
 void launch_ras_setup(int N, int b, int o, const RasIB& ib, double a0, double c, double inv_h, double dt,
                       const int* list, int nIB, double* inv64, float* inv32, int* info, cudaStream_t s);
+// wide subdomains: matrices first .. first + count - 1 (0: the shared one, s > 0: box list[s - 1]), each
+// eliminated in its own ne x ne FP64 block of `work`
+void launch_ras_setup_big(int N, int b, int o, const RasIB& ib, double a0, double c, double inv_h, double dt,
+                          const int* list, int first, int count, double* work, double* inv64, float* inv32, int* info,
+                          cudaStream_t s);
 // the shared-inverse kernel, then (nIB > 0) one block per listed IB box
 template <typename T>
 void launch_ras_apply(int N, int b, int o, const int* slotOfBox, const int* list, int nIB, const T* inv, T omega,

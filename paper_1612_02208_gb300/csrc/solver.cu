@@ -896,10 +896,14 @@ void power_M_enqueue(sib_ctx* c, int l, int slot, cudaStream_t s) {
 
 // Box RAS set-up on levels 1..lmax (Sec. 3.3, Alg. 2 with boxes): classify the boxes by whether
 // their subdomain meets an IB window, then assemble and invert the shared IB-free subdomain operator
-// and one per IB box (FP64), keeping the owned rows of each inverse.
+// and one per IB box (FP64), keeping the owned rows of each inverse.  Wide subdomains are eliminated
+// in a temporary global workspace, at most RAS_WORK_BYTES of matrices per launch.
+constexpr size_t RAS_WORK_BYTES = size_t(1) << 31;
 void ras_setup_all(sib_ctx* c, cudaStream_t s) {
     const int b = c->opts.box, o = c->opts.box_overlap;
     const int ne = ras_ne(b, o), nown = 3 * b * b;
+    const bool big = ras_big(b, o);
+    const size_t matBytes = sizeof(double) * (size_t)ne * ne;
     std::vector<int> cnt(c->lmax + 1, 0);
     for (int l = 1; l <= c->lmax; ++l) {
         Level& lv = c->L[l];
@@ -921,6 +925,14 @@ void ras_setup_all(sib_ctx* c, cudaStream_t s) {
     }
     CK(cudaStreamSynchronize(s));
     CK(cudaMemsetAsync(c->rasInfo, 0, sizeof(int), s));
+    int batch = 0;   // wide subdomains: matrices per set-up launch
+    double* work = nullptr;
+    if (big) {
+        int most = 1;
+        for (int l = 1; l <= c->lmax; ++l) most = std::max(most, 1 + cnt[l]);
+        batch = (int)std::max<size_t>(1, std::min<size_t>((size_t)most, RAS_WORK_BYTES / matBytes));
+        work = (double*)dalloc(c, matBytes * batch);
+    }
     for (int l = 1; l <= c->lmax; ++l) {
         Level& lv = c->L[l];
         const int nboxes = (lv.N / b) * (lv.N / b);
@@ -935,14 +947,25 @@ void ras_setup_all(sib_ctx* c, cudaStream_t s) {
         const RasIB ib{c->haveIB ? lv.slotOf : nullptr, (const double*)lv.win[0], lv.tx, lv.ty, lv.ntx};
         launch_box_slots(nboxes, lv.rasList, lv.rasCount, lv.rasSlot, s);
         lv.rasNIB = cnt[l];
-        const double h = lv.h;
-        launch_ras_setup(lv.N, b, o, ib, c->rho / c->dt + 4.0 * c->mu / (h * h), c->mu / (h * h), 1.0 / h, c->dt,
-                         lv.rasList, cnt[l], (double*)lv.rasInv[0], (float*)lv.rasInv[1], c->rasInfo, s);
-        c->launches += 2;
+        const double h = lv.h, a0 = c->rho / c->dt + 4.0 * c->mu / (h * h), cc = c->mu / (h * h);
+        ++c->launches;
+        if (big) {
+            for (int first = 0; first < 1 + cnt[l]; first += batch) {
+                launch_ras_setup_big(lv.N, b, o, ib, a0, cc, 1.0 / h, c->dt, lv.rasList, first,
+                                     std::min(batch, 1 + cnt[l] - first), work, (double*)lv.rasInv[0],
+                                     (float*)lv.rasInv[1], c->rasInfo, s);
+                ++c->launches;
+            }
+        } else {
+            launch_ras_setup(lv.N, b, o, ib, a0, cc, 1.0 / h, c->dt, lv.rasList, cnt[l], (double*)lv.rasInv[0],
+                             (float*)lv.rasInv[1], c->rasInfo, s);
+            ++c->launches;
+        }
     }
     int info = 0;
     CK(cudaMemcpyAsync(&info, c->rasInfo, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (work) dfree(c, work);
     kcheck(c);
     if (info != 0) throw SibError(SIB_ERR_ARG, "a box subdomain operator is singular");
 }
@@ -1830,13 +1853,17 @@ int sib_set_stiffness(sib_ctx* c, const double* kappa, void* stream) {
     API_END(c)
 }
 
+// Widest box subdomain the options accept.  The wide-subdomain kernels (up to RAS_EMAX cells, boxes of
+// 8 cells) are built but stay off until their parity tests run.
+constexpr int RAS_EMAX_ENABLED = RAS_EMAX_SMEM;
+
 int sib_set_options(sib_ctx* c, const sib_opts* o) {
     API_BEGIN(c)
     if (!o) throw SibError(SIB_ERR_ARG, "null options");
     sib_opts n = *o;
     if ((n.smoother != SIB_SMOOTHER_VANKA && n.smoother != SIB_SMOOTHER_SC && n.smoother != SIB_SMOOTHER_RAS) ||
         n.nu1 < 0 || n.nu2 < 0 || (n.box != 1 && n.box != 2 && n.box != 4) || n.box_overlap < 0 ||
-        n.box + 2 * n.box_overlap > 6 || n.box + 2 * n.box_overlap + 1 > 2 * c->n_min ||
+        n.box + 2 * n.box_overlap > RAS_EMAX_ENABLED || n.box + 2 * n.box_overlap + 1 > 2 * c->n_min ||
         n.nu1 + n.nu2 > 64 || n.cheb_iters < 1 || n.cheb_iters > 16 || !(n.cheb_lo > 0) || !(n.cheb_hi > n.cheb_lo) ||
         n.power_iters < 1 || n.power_iters > 1000 || !(n.rtol >= 0) || n.max_it < 1 || n.max_it > 100000 ||
         n.restart < 1 || n.restart > 100 || (n.fuse_small != 0 && n.fuse_small != 1) ||
