@@ -1,0 +1,109 @@
+"""GPU parity of the box RAS smoother on subdomains wider than six cells (Sec. 3.3 / Alg. 2 with the
+paper's 8 x 8 boxes and overlap 2, Sec. 5.1.1 and 5.2.1), against the CPU oracle: the global-memory
+set-up and the batched correction.  Every test is skipped while the options reject these shapes.
+
+Tolerances as in test_gpu_parity: FP64 to 1e-10 relative (max norm); FP32 to 1e-5 per sweep.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import krylov, multigrid, system  # noqa: E402
+from paper_1612_02208_gb300 import inputs as I  # noqa: E402
+from paper_1612_02208_gb300 import sib  # noqa: E402
+
+from tests.test_gpu_parity import TOL32, TOL64, cu, host, rand, rel  # noqa: E402
+
+PROBLEMS = {
+    "ellipse32": lambda: I.thin_ellipse_stokes(32),
+    "disk32_stiff": lambda: I.disk_stokes(32, kappa=1e4, seed=1),
+    "ellipse64_re": lambda: I.thin_ellipse_re(64, kappa=1e4),
+    "fluid32": lambda: I.no_structure(32, seed=3),
+    "circle32_g500": lambda: I.paper_problem("circle", 32, 500.0),
+}
+
+_enabled = None
+
+
+def wide_enabled():
+    global _enabled
+    if _enabled is None:
+        S = sib.solver_for(I.no_structure(32, seed=3))
+        try:
+            S.set_options(smoother=sib.SMOOTHER_RAS, box=8, box_overlap=2)
+            _enabled = True
+        except sib.SibError:
+            _enabled = False
+    return _enabled
+
+
+@pytest.fixture(autouse=True)
+def _needs_wide_boxes():
+    if not wide_enabled():
+        pytest.skip("the options do not accept subdomains wider than six cells")
+
+
+_cache = {}
+
+
+def pair(name, b, o, **opts):
+    key = (name, b, o, tuple(sorted(opts.items())))
+    if key not in _cache:
+        prob = PROBLEMS[name]()
+        H = multigrid.Hierarchy(prob, smoother="ras", box=b, overlap=o)
+        S = sib.solver_for(prob, smoother=sib.SMOOTHER_RAS, box=b, box_overlap=o, **opts)
+        _cache[key] = (prob, H, S)
+    return _cache[key]
+
+
+@pytest.mark.parametrize("name,b,o", [("ellipse32", 8, 2), ("ellipse64_re", 8, 2), ("disk32_stiff", 4, 2),
+                                      ("fluid32", 8, 2), ("ellipse32", 2, 3), ("ellipse64_re", 4, 4),
+                                      ("circle32_g500", 8, 2)])
+def test_wide_ras_sweep_every_level(name, b, o):
+    """One sweep per level, FP64 and FP32: the 16 x 16 level 1 holds 4 boxes (a partial tile of the
+    batched correction), the 64 x 64 fine level 64, with IB and IB-free boxes."""
+    prob, H, S = pair(name, b, o)
+    for l in range(1, len(H.levels)):
+        lev = H.levels[l]
+        x = rand(3 * lev.n, 3800 + l)
+        bb = rand(3 * lev.n, 3900 + l, 10.0)
+        ref = H.smooth(l, x, bb, 1)
+        y = cu(x.copy())
+        S.smooth(l, y, cu(bb), 1)
+        assert rel(host(y), ref) < TOL64, (l, rel(host(y), ref))
+        x32 = x.astype(np.float32).astype(np.float64)
+        b32 = bb.astype(np.float32).astype(np.float64)
+        ref32 = H.smooth(l, x32, b32, 1)
+        y32 = cu(x32, torch.float32)
+        S.smooth(l, y32, cu(b32, torch.float32), 1)
+        assert rel(host(y32), ref32) < TOL32, (l, rel(host(y32), ref32))
+
+
+@pytest.mark.parametrize("name", ["ellipse64_re", "circle32_g500"])
+def test_wide_ras_vcycle(name):
+    prob, H, S = pair(name, 8, 2)
+    b = system.rhs(prob)
+    z = host(S.vcycle(cu(b)))
+    assert rel(z, H.vcycle(b)) < TOL64, rel(z, H.vcycle(b))
+    b32 = b.astype(np.float32).astype(np.float64)
+    z32 = host(S.vcycle(cu(b32, torch.float32)))
+    assert rel(z32, H.vcycle(b32)) < 1e-4, rel(z32, H.vcycle(b32))
+
+
+def test_wide_ras_thin_circle_converges():
+    """The thin circle at gamma = 500 in Stokes flow (Sec. 5.2): 4 x 4 boxes with overlap 1 do not
+    converge within 100 iterations on the oracle, 8 x 8 boxes with overlap 2 do.  FP64 V-cycle: the
+    iteration count to 1e-12 is the oracle's within one, and the solution is the direct solve's."""
+    prob, H, S = pair("circle32_g500", 8, 2, vcycle_fp32=0, rtol=1e-12, max_it=100)
+    N = prob.N
+    w = host(S.solve(cu(prob.g)))
+    L = system.operator_of(prob)
+    b = system.rhs(prob)
+    _, its, _, conv = krylov.fgmres(lambda z: L @ z, H.vcycle, b, rtol=1e-12, max_it=100, restart=100,
+                                    project=lambda v: system.project(v, N, prob.rho))
+    assert conv and S.stats.converged, (its, S.stats.iterations)
+    assert abs(S.stats.iterations - its) <= 1, (S.stats.iterations, its)
+    ref, _ = system.solve_direct(L, b, N, prob.rho)
+    assert rel(w, system.project(ref, N, prob.rho)) < 1e-8
