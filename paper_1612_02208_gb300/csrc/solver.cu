@@ -1862,7 +1862,7 @@ int sib_set_options(sib_ctx* c, const sib_opts* o) {
     if (!o) throw SibError(SIB_ERR_ARG, "null options");
     sib_opts n = *o;
     if ((n.smoother != SIB_SMOOTHER_VANKA && n.smoother != SIB_SMOOTHER_SC && n.smoother != SIB_SMOOTHER_RAS) ||
-        n.nu1 < 0 || n.nu2 < 0 || (n.box != 1 && n.box != 2 && n.box != 4) || n.box_overlap < 0 ||
+        n.nu1 < 0 || n.nu2 < 0 || (n.box != 1 && n.box != 2 && n.box != 4 && n.box != 8) || n.box_overlap < 0 ||
         n.box + 2 * n.box_overlap > RAS_EMAX_ENABLED || n.box + 2 * n.box_overlap + 1 > 2 * c->n_min ||
         n.nu1 + n.nu2 > 64 || n.cheb_iters < 1 || n.cheb_iters > 16 || !(n.cheb_lo > 0) || !(n.cheb_hi > n.cheb_lo) ||
         n.power_iters < 1 || n.power_iters > 1000 || !(n.rtol >= 0) || n.max_it < 1 || n.max_it > 100000 ||
