@@ -246,6 +246,21 @@ def box_ras_cases(S, g, w, kap_dev, sib, torch, stream, box=4, overlap=1):
             "cases": records}
 
 
+WIDE_BOX = (8, 2)   # the paper's 8 x 8 boxes with overlap 2 (Sec. 5.1.1, 5.2.1)
+
+
+def wide_boxes_accepted(sib):
+    """Whether the library's options accept the paper's 8 x 8 boxes with overlap 2."""
+    S = sib.Solver(32)
+    try:
+        S.set_options(smoother=sib.SMOOTHER_RAS, box=WIDE_BOX[0], box_overlap=WIDE_BOX[1])
+        return True
+    except sib.SibError:
+        return False
+    finally:
+        S.close()
+
+
 def paper_workloads(sib, torch, dev):
     """The paper's thick annulus and thin circle (Sec. 5.1, 5.2) in the periodic box: one linear solve
     each (dt = 0.32 h, g = 0, tolerance 1e-12, at most 100 iterations, FP32 V-cycle), over gamma,
@@ -254,6 +269,8 @@ def paper_workloads(sib, torch, dev):
     smoothers = {"vanka": dict(smoother=sib.SMOOTHER_VANKA), "sc": dict(smoother=sib.SMOOTHER_SC),
                  "ras4o1": dict(smoother=sib.SMOOTHER_RAS, box=4, box_overlap=1),
                  "ras2o2": dict(smoother=sib.SMOOTHER_RAS, box=2, box_overlap=2)}
+    if wide_boxes_accepted(sib):
+        smoothers["ras8o2"] = dict(smoother=sib.SMOOTHER_RAS, box=WIDE_BOX[0], box_overlap=WIDE_BOX[1])
     runs = [(kind, 128, gamma, mu, sm) for kind in ("annulus", "circle") for mu in (None, 0.01)
             for gamma in (5.0, 50.0, 500.0) for sm in smoothers]
     runs += [("annulus", N, gamma, None, sm) for N in (64, 256) for gamma in (5.0, 500.0) for sm in ("vanka", "ras4o1")]
@@ -328,24 +345,27 @@ def large_vcycle(sib, torch, reps=20, N=None):
         ms, by = S.time_kernel(name, lmax, True, reps=20)
         torch.cuda.nvtx.range_pop()
         out["kernels"][name] = {"ms": round(ms, 5), "bytes": by, "gbs": round(by / (ms * 1e-3) / 1e9, 1)}
-    # the box RAS smoother (4 x 4 boxes, overlap 1) on the same grid: V-cycle and correction kernel
-    S.set_options(smoother=sib.SMOOTHER_RAS, box=4, box_overlap=1, omega=-1.0)
-    S.setup()
-    for _ in range(3):
-        S.vcycle(b, z)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_push("vcycles_ras")
-    e0.record()
-    for _ in range(reps):
-        S.vcycle(b, z)
-    e1.record()
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    out["vcycle_ms_ras"] = round(e0.elapsed_time(e1) / reps, 4)
-    torch.cuda.nvtx.range_push("roofline_large_ras")
-    ms, by = S.time_kernel("ras", lmax, True, reps=20)
-    torch.cuda.nvtx.range_pop()
-    out["kernels"]["ras"] = {"ms": round(ms, 5), "bytes": by, "gbs": round(by / (ms * 1e-3) / 1e9, 1)}
+    # the box RAS smoother on the same grid: V-cycle and correction kernel, 4 x 4 boxes with overlap 1
+    # and, where the options accept them, the paper's 8 x 8 boxes with overlap 2
+    shapes = [((4, 1), "ras")] + ([(WIDE_BOX, "ras8o2")] if wide_boxes_accepted(sib) else [])
+    for (bx, ov), key in shapes:
+        S.set_options(smoother=sib.SMOOTHER_RAS, box=bx, box_overlap=ov, omega=-1.0)
+        S.setup()
+        for _ in range(3):
+            S.vcycle(b, z)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("vcycles_" + key)
+        e0.record()
+        for _ in range(reps):
+            S.vcycle(b, z)
+        e1.record()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        out["vcycle_ms_" + key] = round(e0.elapsed_time(e1) / reps, 4)
+        torch.cuda.nvtx.range_push("roofline_large_" + key)
+        ms, by = S.time_kernel("ras", lmax, True, reps=20)
+        torch.cuda.nvtx.range_pop()
+        out["kernels"][key] = {"ms": round(ms, 5), "bytes": by, "gbs": round(by / (ms * 1e-3) / 1e9, 1)}
     S.close()
     return out
 
@@ -474,6 +494,11 @@ def run_native(args):
     # the paper's box Vanka smoother: restricted additive Schwarz over 4 x 4 and 2 x 2 boxes, overlap 1
     ras = [box_ras_cases(S, g, w, kap_dev, sib, torch, stream, 4, 1),
            box_ras_cases(S, g, w, kap_dev, sib, torch, stream, 2, 1)]
+    if wide_boxes_accepted(sib):
+        ras.append(box_ras_cases(S, g, w, kap_dev, sib, torch, stream, *WIDE_BOX))
+    else:
+        ras.append({"box": WIDE_BOX[0], "overlap": WIDE_BOX[1],
+                    "unavailable": "the options accept subdomains up to 6 cells wide"})
     paper = paper_workloads(sib, torch, dev) if not args.no_paper else None
 
     # end to end through the host-buffer C call, pinned host memory
