@@ -22,9 +22,11 @@ Readings (the paper treats its physical boundaries as in earlier work that it do
   walls), so interpolation and spreading never meet a wall.
 
 Pinned by (tests/test_oracle_cavity.py): D = -G^T and symmetry; the operator equals the periodic
-operator on rows away from the walls; second-order convergence to a manufactured divergence-free
-Stokes solution with no-slip walls; Cauchy convergence of the lid-driven flow; the RT0 identity
-D_f P_u = Inj D_c; V-cycle and FGMRES convergence with an immersed structure.
+operator on rows away from the walls; second-order convergence to manufactured divergence-free
+Stokes solutions with no-slip walls, one of them driven by the lid (which fixes the lid's
+right-hand side term); Cauchy convergence of the lid-driven flow; the RT0 identity
+D_f P_u = Inj D_c; the pressure prolongation's linear reproduction and locality at the walls;
+V-cycle and FGMRES convergence with an immersed structure.
 """
 import numpy as np
 import scipy.sparse as sp

@@ -89,6 +89,63 @@ def test_cavity_manufactured_stokes_converges_at_second_order():
     assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0, errs
 
 
+def test_cavity_manufactured_lid_converges_at_second_order():
+    """A manufactured Stokes flow (mu = 1) whose top-wall velocity is the regularised lid: stream
+    function psi = u_lid(x) (y^3 - y^2), so u = psi_y equals u_lid on y = 1 and vanishes on the other
+    walls, v = -psi_x vanishes on all walls (u_lid' = 0 at x = 0, 1), and the flow is divergence-free.
+    With the lid's right-hand side term the solve converges at second order; a wrong factor, sign or
+    face position of that term leaves an O(1) or O(h) error."""
+    import sympy as sy
+    x, y = sy.symbols("x y")
+    lid = (1 - sy.cos(2 * sy.pi * x)) / 2
+    psi = lid * (y ** 3 - y ** 2)
+    u, v = sy.diff(psi, y), -sy.diff(psi, x)
+    p = sy.cos(sy.pi * x) * sy.cos(sy.pi * y)
+    fu = -(sy.diff(u, x, 2) + sy.diff(u, y, 2)) + sy.diff(p, x)
+    fv = -(sy.diff(v, x, 2) + sy.diff(v, y, 2)) + sy.diff(p, y)
+    F = lambda e: sy.lambdify((x, y), e, "numpy")
+    ue, ve, fue, fve = F(u), F(v), F(fu), F(fv)
+    xs = np.linspace(0.0, 1.0, 11)
+    np.testing.assert_allclose(cavity.lid_velocity(xs), F(lid)(xs, 0.0), atol=1e-15)   # the oracle's lid
+    errs = []
+    for N in (16, 32, 64):
+        (xu, yu), (xv, yv) = _faces(N)
+        n = N * N
+        idx = cavity.interior(N)
+        b = np.concatenate([fue(xu, yu), fve(xv, yv), np.zeros(n)])[idx] + cavity.lid_rhs(N, 1.0)
+        L = cavity.operator(N, 0.0, 1.0, 1.0, np.zeros((0, 2)), np.zeros((0, 2), np.int32), np.zeros(0))
+        w = cavity.solve_direct(L, b, N)
+        exact = np.concatenate([ue(xu, yu) * np.ones(n), ve(xv, yv) * np.ones(n), np.zeros(n)])[idx]
+        nv = 2 * n - 2 * N
+        errs.append(np.abs(w[:nv] - exact[:nv]).max())
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5, errs
+
+
+def test_cavity_pressure_prolongation_is_local_and_reproduces_linears():
+    """Bilinear prolongation reproduces linear fields on fine cells whose four coarse neighbours lie
+    inside, and fields linear in one coordinate away from the walls across that coordinate; no fine
+    cell takes a value from a coarse cell on the far side of a wall (the periodic wrap is gone), and
+    every row sums to 1, so a zero or wrapped ghost fails."""
+    Nc = 8
+    Nf = 2 * Nc
+    P = cavity.prolong_pressure(Nc)
+    Xc = (np.arange(Nc) + 0.5) / Nc
+    Xf = (np.arange(Nf) + 0.5) / Nf
+    YYc, XXc = np.meshgrid(Xc, Xc, indexing="ij")
+    YYf, XXf = np.meshgrid(Xf, Xf, indexing="ij")
+    inner = (slice(1, Nf - 1), slice(1, Nf - 1))
+    lin = (P @ (0.3 + 1.7 * XXc - 0.9 * YYc).ravel()).reshape(Nf, Nf)
+    np.testing.assert_allclose(lin[inner], (0.3 + 1.7 * XXf - 0.9 * YYf)[inner], atol=1e-14)
+    fy = (P @ (2.0 * YYc).ravel()).reshape(Nf, Nf)
+    np.testing.assert_allclose(fy[1:Nf - 1, :], (2.0 * YYf)[1:Nf - 1, :], atol=1e-14)
+    fx = (P @ (2.0 * XXc).ravel()).reshape(Nf, Nf)
+    np.testing.assert_allclose(fx[:, 1:Nf - 1], (2.0 * XXf)[:, 1:Nf - 1], atol=1e-14)
+    C = P.tocoo()
+    fi, fj, ci, cj = C.row % Nf, C.row // Nf, C.col % Nc, C.col // Nc
+    assert np.all(np.abs(Xf[fi] - Xc[ci]) < 1.0 / Nc) and np.all(np.abs(Xf[fj] - Xc[cj]) < 1.0 / Nc)
+    np.testing.assert_allclose(np.asarray(P.sum(axis=1)).ravel(), 1.0, atol=1e-15)
+
+
 def test_cavity_lid_driven_flow_cauchy_convergence():
     """Stokes flow driven by the regularised lid alone: u sampled on the coarse u faces (the mean of the
     two fine faces around each coarse face centre) converges at about second order."""
