@@ -86,7 +86,19 @@ typedef struct {
                              symmetric red-black Gauss-Seidel sweep from zero, colours 0, 1, 1, 0)    */
     int    box;           /* RAS: cells per box side b, 1, 2 or 4 (4)                                */
     int    box_overlap;   /* RAS: overlap o in cells on each side, b + 2 o <= 6 (1)                  */
+    int    domain;        /* SIB_DOMAIN_PERIODIC (default) or SIB_DOMAIN_CAVITY (see below)          */
 } sib_opts;
+
+/* Domains.  SIB_DOMAIN_CAVITY is the paper's lid-driven cavity (Sec. 5) on the same layout: the seam
+ * faces u(0, j) and v(i, 0) are the no-slip walls and hold 0 in every vector; tangential walls use
+ * the ghost value -q_inside; the lid's 2 mu u_lid(x_i) / h^2 on the top row of u faces is part of the
+ * caller's g.  Solves, V-cycles, sweeps and transfers then follow the cavity: Vanka sweeps with the
+ * wall rules, the walled RT0 transfers with the pressure prolongation reflected at the walls, coarse
+ * IB windows with their wall couplings removed, and a coarsest pseudo-inverse whose kernel is the
+ * constant pressure.  It takes the Vanka smoother with damped sweeps (smooth_krylov = 0).  This
+ * version returns SIB_ERR_UNIMPLEMENTED for SIB_DOMAIN_CAVITY from sib_set_options. */
+#define SIB_DOMAIN_PERIODIC 0
+#define SIB_DOMAIN_CAVITY   1
 
 #define SIB_RELAX_JACOBI 0
 #define SIB_RELAX_SGS    1

@@ -139,7 +139,181 @@ __global__ void k_cavity_update(GridK<T> g, T omega, const T* __restrict__ d, co
     xo[2 * n + c] = x[2 * n + c] + omega * d[4 * n + c];
 }
 
+// Restriction for the cavity (Sec. 3.2 with walls): the periodic R_u = P_u^T / 4 and the pressure
+// average, applied to a fine residual that holds 0 on its wall faces, with the coarse wall faces
+// written as 0 (they are not unknowns).  The fine stencil of a coarse unknown never reaches a fine
+// wall face or wraps across a wall.
+template <typename T>
+__global__ void k_cavity_restrict(int Nc, const T* __restrict__ rf, T* __restrict__ bc) {
+    pdl_entry();
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    if (I >= Nc || J >= Nc) return;
+    const int Nf = 2 * Nc, nf = Nf * Nf, nc = Nc * Nc, mf = Nf - 1;
+    const T* ru = rf;
+    const T* rv = rf + nf;
+    const T* rp = rf + 2 * nf;
+    const int i = 2 * I, j = 2 * J, ip = i + 1, jp = j + 1, im = (i - 1) & mf, jm = (j - 1) & mf;
+    const T su = (ru[j * Nf + i] + ru[jp * Nf + i]) +
+                 T(0.5) * ((ru[j * Nf + ip] + ru[jp * Nf + ip]) + (ru[j * Nf + im] + ru[jp * Nf + im]));
+    const T sv = (rv[j * Nf + i] + rv[j * Nf + ip]) +
+                 T(0.5) * ((rv[jp * Nf + i] + rv[jp * Nf + ip]) + (rv[jm * Nf + i] + rv[jm * Nf + ip]));
+    const T sp = (rp[j * Nf + i] + rp[j * Nf + ip]) + (rp[jp * Nf + i] + rp[jp * Nf + ip]);
+    const int c = J * Nc + I;
+    bc[c] = I > 0 ? T(0.25) * su : T(0);
+    bc[nc + c] = J > 0 ? T(0.25) * sv : T(0);
+    bc[2 * nc + c] = T(0.25) * sp;
+}
+
+// xf += P ec for the cavity, one thread per fine cell: RT0 velocity exactly as on the periodic grid
+// (the coarse wall faces hold 0, so fine wall faces receive 0 and the half-way faces next to a wall
+// average with 0), bilinear pressure with a coarse neighbour outside the domain replaced by the cell
+// itself (reflection across the wall).
+template <typename T>
+__global__ void k_cavity_prolong_add(int Nc, const T* __restrict__ ec, T* __restrict__ xf) {
+    pdl_entry();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int Nf = 2 * Nc;
+    if (i >= Nf || j >= Nf) return;
+    const int nf = Nf * Nf, nc = Nc * Nc, mc = Nc - 1;
+    const T* eu = ec;
+    const T* ev = ec + nc;
+    const T* ep = ec + 2 * nc;
+    const int I = i >> 1, J = j >> 1;
+    const T pu = (i & 1) ? T(0.5) * (eu[J * Nc + I] + eu[J * Nc + ((I + 1) & mc)]) : eu[J * Nc + I];
+    const T pv = (j & 1) ? T(0.5) * (ev[J * Nc + I] + ev[((J + 1) & mc) * Nc + I]) : ev[J * Nc + I];
+    int I2 = I + ((i & 1) ? 1 : -1), J2 = J + ((j & 1) ? 1 : -1);
+    if (I2 < 0 || I2 > mc) I2 = I;
+    if (J2 < 0 || J2 > mc) J2 = J;
+    const T pp = T(9.0 / 16.0) * ep[J * Nc + I] + T(3.0 / 16.0) * (ep[J * Nc + I2] + ep[J2 * Nc + I]) +
+                 T(1.0 / 16.0) * ep[J2 * Nc + I2];
+    const int c = j * Nf + i;
+    xf[c] += pu;
+    xf[nf + c] += pv;
+    xf[2 * nf + c] += pp;
+}
+
+// The cavity's coarsest operator bordered for its gauge, Aug = [L0 + Z Z^T | I] (3 n0 x 6 n0, row-major),
+// with Z the normalised constant pressure (the operator's kernel).  A wall face's row and column are
+// those of the identity: the face is not an unknown, and the right-hand side and the solution hold 0
+// there.  Unknown rows follow cavity_rows: the tangential ghost -q adds c to the diagonal of a face next
+// to a tangential wall, a wall neighbour along the component's own direction contributes nothing, and
+// the IB block B (2 n0 x n0 per component, from the level-0 windows) enters as -dt B.
+__global__ void k_cavity_assemble_L0(int N, double rho, double mu, double dt, const double* __restrict__ B,
+                                     double* __restrict__ Aug) {
+    pdl_entry();
+    const int n0 = N * N, n = 3 * n0;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n * 2 * n) return;
+    const int r = (int)(q / (2 * n)), col = (int)(q % (2 * n));
+    if (col >= n) {
+        Aug[q] = (col - n == r) ? 1.0 : 0.0;
+        return;
+    }
+    const int br = r / n0, f = r % n0, i = f % N, j = f / N;
+    const int bc = col / n0, g = col % n0, gi = g % N, gj = g / N;
+    const bool wallR = (br == 0 && i == 0) || (br == 1 && j == 0);
+    const bool wallC = (bc == 0 && gi == 0) || (bc == 1 && gj == 0);
+    if (wallR || wallC) {
+        Aug[q] = (r == col) ? 1.0 : 0.0;
+        return;
+    }
+    const double h = 1.0 / N, ih = (double)N;
+    const double a0 = rho / dt + 4.0 * mu / (h * h), cc = mu / (h * h);
+    double v = 0.0;
+    if (br < 2) {
+        if (bc == br) {
+            // normal direction of the component: x for u, y for v; tangential: the other one
+            const int a = br == 0 ? i : j, t = br == 0 ? j : i;   // row face along (normal, tangential)
+            const int ga = br == 0 ? gi : gj, gt = br == 0 ? gj : gi;
+            if (g == f) v += a0 + cc * (double)((t == 0) + (t == N - 1));
+            if (gt == t && (ga == a + 1 || ga == a - 1)) v -= cc;   // in-domain normal neighbours only
+            if (ga == a && (gt == t + 1 || gt == t - 1)) v -= cc;   // tangential neighbours inside
+            v -= dt * B[(int64_t)br * n0 * n0 + (int64_t)f * n0 + g];
+        } else if (bc == 2) {   // G p: (p_ij - p_{i-1,j})/h on u faces, (p_ij - p_{i,j-1})/h on v faces
+            if (g == f) v += ih;
+            if (g == (br == 0 ? j * N + i - 1 : (j - 1) * N + i)) v -= ih;
+        }
+    } else if (bc < 2) {        // -D u with the wall faces as zeros
+        if (bc == 0) {
+            if (g == f) v += ih;
+            if (i + 1 < N && g == j * N + i + 1) v -= ih;
+        } else {
+            if (g == f) v += ih;
+            if (j + 1 < N && g == (j + 1) * N + i) v -= ih;
+        }
+    } else {
+        v = 1.0 / (double)n0;   // Z Z^T on the pressure block
+    }
+    Aug[q] = v;
+}
+
+// Cavity windows of one level: entries in a wall face's row, or whose column (the face at the
+// entry's unwrapped offset) is a wall face or lies across a wall, are set to 0.  Applied after each
+// level's Galerkin product, this gives the cavity's R_u B P_u with P_u restricted to the unknowns.
+__global__ void k_cavity_mask_windows(double* __restrict__ win, const int* __restrict__ tiles, int N, int tx, int ty,
+                                      int ntx) {
+    const int slot = blockIdx.x, comp = blockIdx.y;
+    const int per = tx * ty, q = threadIdx.x;
+    if (q >= per) return;
+    const int t = tiles[slot];
+    const int i = (t % ntx) * tx + q % tx, j = (t / ntx) * ty + q / tx;
+    double* w = win + ((size_t)(slot * 2 + comp) * WIN_SIZE) * per + q;
+    const int a = comp == 0 ? i : j;   // the row face's coordinate along its own normal
+    for (int kw = 0; kw < WIN_SIZE; ++kw) {
+        const int ox = kw % WD - WR, oy = kw / WD - WR;
+        const int ci = i + ox, cj = j + oy;
+        const int ca = comp == 0 ? ci : cj, ct = comp == 0 ? cj : ci;   // column: normal, tangential
+        const bool inside = ca >= 1 && ca <= N - 1 && ct >= 0 && ct <= N - 1;
+        if (a == 0 || !inside) w[(size_t)kw * per] = 0.0;
+    }
+}
+
+// x <- 0 on the wall faces u(0, j), v(i, 0)
+template <typename T>
+__global__ void k_cavity_zero_walls(T* __restrict__ x, int N) {
+    pdl_entry();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    x[k * N] = T(0);
+    x[N * N + k] = T(0);
+}
+
 }  // namespace
+
+template <typename T>
+void launch_cavity_residual(const GridK<T>& g, const T* x, const T* b, T* r, cudaStream_t s) {
+    launch_pdl(k_cavity_residual<T>, dim3(g.N / g.tx, g.N / g.ty), dim3(g.tx, g.ty), 0, s, g, x, b, r);
+}
+template <typename T>
+void launch_cavity_zero_walls(T* x, int N, cudaStream_t s) {
+    launch_pdl(k_cavity_zero_walls<T>, dim3((N + 127) / 128), dim3(128), 0, s, x, N);
+}
+
+template <typename T>
+void launch_cavity_restrict(int Nc, const T* rf, T* bc, cudaStream_t s) {
+    dim3 blk(Nc < 32 ? Nc : 32, Nc < 8 ? Nc : 8);
+    dim3 grd((Nc + blk.x - 1) / blk.x, (Nc + blk.y - 1) / blk.y);
+    launch_pdl(k_cavity_restrict<T>, grd, blk, 0, s, Nc, rf, bc);
+}
+template <typename T>
+void launch_cavity_prolong_add(int Nc, const T* ec, T* xf, cudaStream_t s) {
+    const int Nf = 2 * Nc;
+    dim3 blk(Nf < 32 ? Nf : 32, Nf < 8 ? Nf : 8);
+    dim3 grd((Nf + blk.x - 1) / blk.x, (Nf + blk.y - 1) / blk.y);
+    launch_pdl(k_cavity_prolong_add<T>, grd, blk, 0, s, Nc, ec, xf);
+}
+void launch_cavity_assemble_L0(int N0, double rho, double mu, double dt, const double* B, double* Aug,
+                               cudaStream_t s) {
+    const int64_t tot = (int64_t)3 * N0 * N0 * 6 * N0 * N0;
+    launch_pdl(k_cavity_assemble_L0, (int)((tot + 255) / 256), 256, 0, s, N0, rho, mu, dt, B, Aug);
+}
+void launch_cavity_mask_windows(double* win, const int* tiles, int nTiles, int N, int tx, int ty, int ntx,
+                                cudaStream_t s) {
+    if (nTiles == 0) return;
+    k_cavity_mask_windows<<<dim3(nTiles, 2), tx * ty, 0, s>>>(win, tiles, N, tx, ty, ntx);
+}
 
 template <typename T>
 void launch_cavity_apply(const GridK<T>& g, const T* x, T* y, cudaStream_t s) {
@@ -158,5 +332,14 @@ template void launch_cavity_vanka<float>(const GridK<float>&, const float*, cons
                                          cudaStream_t);
 template void launch_cavity_vanka<double>(const GridK<double>&, const double*, const double*, double*, double*,
                                           double*, double, cudaStream_t);
+template void launch_cavity_residual<float>(const GridK<float>&, const float*, const float*, float*, cudaStream_t);
+template void launch_cavity_residual<double>(const GridK<double>&, const double*, const double*, double*,
+                                             cudaStream_t);
+template void launch_cavity_zero_walls<float>(float*, int, cudaStream_t);
+template void launch_cavity_zero_walls<double>(double*, int, cudaStream_t);
+template void launch_cavity_restrict<float>(int, const float*, float*, cudaStream_t);
+template void launch_cavity_restrict<double>(int, const double*, double*, cudaStream_t);
+template void launch_cavity_prolong_add<float>(int, const float*, float*, cudaStream_t);
+template void launch_cavity_prolong_add<double>(int, const double*, double*, cudaStream_t);
 
 }  // namespace sib

@@ -161,6 +161,19 @@ template <typename T> void launch_cavity_apply(const GridK<T>& g, const T* x, T*
 // (weighted corrections); g.fib must hold [S K J] x (kernels_cavity.cu)
 template <typename T>
 void launch_cavity_vanka(const GridK<T>& g, const T* x, const T* b, T* r, T* d, T* xo, T omega, cudaStream_t s);
+// r = b - L x of the cavity (0 on the wall faces); x <- 0 on the wall faces
+template <typename T> void launch_cavity_residual(const GridK<T>& g, const T* x, const T* b, T* r, cudaStream_t s);
+template <typename T> void launch_cavity_zero_walls(T* x, int N, cudaStream_t s);
+// the cavity's transfers (kernels_cavity.cu): restriction with the coarse wall faces zeroed, and
+// prolongation-correction with the pressure reflected at the walls
+template <typename T> void launch_cavity_restrict(int Nc, const T* rf, T* bc, cudaStream_t s);
+template <typename T> void launch_cavity_prolong_add(int Nc, const T* ec, T* xf, cudaStream_t s);
+// the cavity's coarsest operator bordered for its gauge (the constant pressure), [L0 + Z Z^T | I]
+void launch_cavity_assemble_L0(int N0, double rho, double mu, double dt, const double* B, double* Aug,
+                               cudaStream_t s);
+// zero the window entries of one level that couple to or across a wall
+void launch_cavity_mask_windows(double* win, const int* tiles, int nTiles, int N, int tx, int ty, int ntx,
+                                cudaStream_t s);
 template <typename T> void launch_vanka(const GridK<T>& g, const T* x, const T* b, T* xo, cudaStream_t s);
 template <typename T> void launch_restrict(int Nc, const T* rf, T* bc, cudaStream_t s);
 template <typename T> void launch_prolong_add(int Nc, const T* ec, T* xf, cudaStream_t s);

@@ -163,6 +163,9 @@ struct sib_ctx {
 
 namespace {
 
+// the lid-driven cavity instead of the periodic box (option domain)
+inline bool cavity(const sib_ctx* c) { return c->opts.domain == SIB_DOMAIN_CAVITY; }
+
 void* dalloc(sib_ctx* c, size_t bytes) {
     void* p = nullptr;
     if (bytes == 0) bytes = 16;
@@ -300,6 +303,13 @@ void ib_apply(sib_ctx* c, int l, const T* u, cudaStream_t s) {
 template <typename T>
 void apply_operator(sib_ctx* c, int l, const T* x, const T* b, T* r, cudaStream_t s) {
     ib_apply<T>(c, l, x, s);
+    if (cavity(c)) {   // r = b - L x, or L x without b; 0 on the wall faces
+        if (b)
+            KL(c, launch_cavity_residual<T>(gridk<T>(c, l), x, b, r, s));
+        else
+            KL(c, launch_cavity_apply<T>(gridk<T>(c, l), x, r, s));
+        return;
+    }
     KL(c, launch_residual<T>(gridk<T>(c, l), x, b, r, s));
 }
 
@@ -506,7 +516,12 @@ void ras_apply(sib_ctx* c, int l, const T* r, const T* x, T* xo, double omega, c
 // one smoothing sweep xo <- smooth(x, b)
 template <typename T>
 void sweep(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream_t s) {
-    if (c->opts.smoother == SIB_SMOOTHER_SC) {
+    if (cavity(c)) {   // the cavity's Vanka sweep: residual, patch solves with the wall rules, update
+        LevelBuf& lb = c->L[l].p[Prec<T>::id];
+        ib_apply<T>(c, l, x, s);
+        launch_cavity_vanka<T>(gridk<T>(c, l), x, b, (T*)lb.r, (T*)lb.cav, xo, (T)c->opts.omega, s);
+        c->launches += 3;
+    } else if (c->opts.smoother == SIB_SMOOTHER_SC) {
         sc_sweep<T>(c, l, x, b, xo, s);
     } else if (c->opts.smoother == SIB_SMOOTHER_RAS) {   // r = b - L x, then the box corrections
         T* r = (T*)c->L[l].p[Prec<T>::id].r;
@@ -529,7 +544,7 @@ size_t small_smem(const sib_ctx* c) {
 }
 template <typename T>
 bool small_ok(const sib_ctx* c) {
-    if (!c->opts.fuse_small || c->lmax < 1) return false;
+    if (!c->opts.fuse_small || c->lmax < 1 || cavity(c)) return false;
     const Level& lv = c->L[1];
     if (lv.N > 16) return false;
     if (c->opts.smoother == SIB_SMOOTHER_SC && !sc_fused(c)) return false;
@@ -630,6 +645,26 @@ T* vcycle_level(sib_ctx* c, int l, cudaStream_t s) {
     if (l == 0) {
         KL(c, launch_coarse_apply<T>(c->Pinv, c->n0, (const T*)lv.p[pi].b, (T*)lv.p[pi].x, s));
         return (T*)lv.p[pi].x;
+    }
+    if (cavity(c)) {   // the lid-driven cavity: wall-rule sweeps and the walled transfers
+        T* x = (T*)lv.p[pi].x;
+        T* xt = (T*)lv.p[pi].xt;
+        const T* b = (const T*)lv.p[pi].b;
+        CK(cudaMemsetAsync(x, 0, sizeof(T) * 3 * (size_t)lv.N * lv.N, s));
+        for (int k = 0; k < c->opts.nu1; ++k) {
+            sweep<T>(c, l, x, b, xt, s);
+            std::swap(x, xt);
+        }
+        T* r = (T*)lv.p[pi].r;
+        apply_operator<T>(c, l, x, b, r, s);
+        KL(c, launch_cavity_restrict<T>(c->L[l - 1].N, r, (T*)c->L[l - 1].p[pi].b, s));
+        T* ec = vcycle_level<T>(c, l - 1, s);
+        KL(c, launch_cavity_prolong_add<T>(c->L[l - 1].N, ec, x, s));
+        for (int k = 0; k < c->opts.nu2; ++k) {
+            sweep<T>(c, l, x, b, xt, s);
+            std::swap(x, xt);
+        }
+        return x;
     }
     if (c->opts.smooth_krylov) {   // each smoothing stage: FGMRES(nu) preconditioned by the basic sweep
         T* x = (T*)lv.p[pi].x;
@@ -1044,11 +1079,17 @@ void setup(sib_ctx* c, cudaStream_t s) {
             KL(c, launch_kj_patch(ibk<double>(c, c->lmax), c->adjStart, c->adjNbr, c->kap64, c->KJ, lf.winOverflow, s));
             KL(c, launch_window_fine(ibk<double>(c, c->lmax), c->KJ, lf.tiles, lf.hnTiles, lf.tx, lf.ty, lf.ntx,
                                      (double*)lf.win[0], s));
+            // the cavity's Galerkin product uses P_u restricted to the unknowns: every level's windows
+            // lose their wall couplings before the next coarser product
+            if (cavity(c))
+                KL(c, launch_cavity_mask_windows((double*)lf.win[0], lf.tiles, lf.hnTiles, lf.N, lf.tx, lf.ty, lf.ntx, s));
             for (int l = c->lmax - 1; l >= 0; --l) {
                 Level& F = c->L[l + 1];
                 Level& C = c->L[l];
                 KL(c, launch_window_rap((const double*)F.win[0], F.slotOf, F.N, F.tx, F.ty, F.ntx, C.tiles, C.hnTiles, C.N,
                                         C.tx, C.ty, C.ntx, (double*)C.win[0], s));
+                if (cavity(c))
+                    KL(c, launch_cavity_mask_windows((double*)C.win[0], C.tiles, C.hnTiles, C.N, C.tx, C.ty, C.ntx, s));
             }
             int ovf = 0;
             CK(cudaMemcpyAsync(&ovf, lf.winOverflow, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1104,11 +1145,15 @@ void setup(sib_ctx* c, cudaStream_t s) {
     // eigenvalue estimates below (which do not use it), and the main stream joins it at the end.
     {
         const int n = c->n0;
-        KL(c, launch_assemble_L0(c->L[0].N, c->rho, c->mu, c->dt, c->B0, c->Aug, s));
+        if (cavity(c))
+            KL(c, launch_cavity_assemble_L0(c->L[0].N, c->rho, c->mu, c->dt, c->B0, c->Aug, s));
+        else
+            KL(c, launch_assemble_L0(c->L[0].N, c->rho, c->mu, c->dt, c->B0, c->Aug, s));
         CK(cudaEventRecord(c->evFork, s));
         CK(cudaStreamWaitEvent(c->aux, c->evFork, 0));
         KL(c, launch_gauss_jordan(c->Aug, n, c->info, c->piv, c->gjWork, c->aux));
-        KL(c, launch_extract_pinv(c->Aug, c->piv, n, c->L[0].N, c->rho, c->Pinv, c->aux));
+        // the gauge's Z Z^T comes off the pressure block alone in the cavity (passed as rho != 0)
+        KL(c, launch_extract_pinv(c->Aug, c->piv, n, c->L[0].N, cavity(c) ? 1.0 : c->rho, c->Pinv, c->aux));
         CK(cudaEventRecord(c->evJoin, c->aux));
     }
     // Vanka patch factors (they depend on the fluid parameters and the patch entries)
@@ -1119,6 +1164,11 @@ void setup(sib_ctx* c, cudaStream_t s) {
         KL(c, (launch_convert<double, float>((const double*)lv.p[0].pf, (float*)lv.p[1].pf, n7, s)));
     }
     if (c->opts.smoother == SIB_SMOOTHER_RAS && c->lmax > 0) ras_setup_all(c, s);
+    if (cavity(c))   // the cavity sweep's patch corrections, allocated outside any graph capture
+        for (int l = 1; l <= c->lmax; ++l)
+            for (int pi = 0; pi < 2; ++pi)
+                if (!c->L[l].p[pi].cav)
+                    c->L[l].p[pi].cav = dalloc(c, (pi == 0 ? 8 : 4) * 5 * (size_t)c->L[l].N * c->L[l].N);
     if (c->opts.smoother == SIB_SMOOTHER_SC) {
         alloc_sc_bufs(c);
         for (int l = 1; l <= c->lmax; ++l) {
@@ -1173,7 +1223,9 @@ void require_setup(sib_ctx* c) {
 void dot(sib_ctx* c, const double* x, const double* y, int64_t n, double* dst, cudaStream_t s) { dot_into(c, x, y, n, dst, s); }
 
 void project(sib_ctx* c, double* x, cudaStream_t s) {
-    const int mask = c->rho == 0.0 ? 7 : 4;
+    // kernel of the operator: the constant pressure, and for rho = 0 on the periodic grid the
+    // constant velocities too (the cavity's walls fix the velocity)
+    const int mask = c->rho == 0.0 && !cavity(c) ? 7 : 4;
     KL(c, launch_block_means(x, c->N, 3, c->part, NBLK, s));
     KL(c, launch_subtract_means(x, c->N, c->part, NBLK, mask, s));
 }
@@ -1475,6 +1527,7 @@ void build_rhs(sib_ctx* c, const double* g, bool addSKX, cudaStream_t s) {
                                     lv.spreadWarp, s));
         KL(c, launch_axpby<double>(1.0, c->rhs, 1.0, (const double*)lv.p[0].fib, c->rhs, nv, s));
     }
+    if (cavity(c)) KL(c, launch_cavity_zero_walls<double>(c->rhs, c->N, s));   // the walls are not unknowns
     project(c, c->rhs, s);
 }
 
@@ -1685,6 +1738,7 @@ void sib_default_opts(sib_opts* o) {
     o->sc_relax = SIB_RELAX_JACOBI;
     o->box = 4;
     o->box_overlap = 1;
+    o->domain = SIB_DOMAIN_PERIODIC;
 }
 
 static void resolve_opts(sib_opts* o) {
@@ -1854,8 +1908,9 @@ int sib_set_stiffness(sib_ctx* c, const double* kappa, void* stream) {
 }
 
 // Widest box subdomain the options accept.  The wide-subdomain kernels (up to RAS_EMAX cells, boxes of
-// 8 cells) are built but stay off until their parity tests run.
+// 8 cells) are built but stay off until their parity tests run; so does the cavity's solve.
 constexpr int RAS_EMAX_ENABLED = RAS_EMAX_SMEM;
+constexpr bool CAVITY_SOLVE_ENABLED = false;
 
 int sib_set_options(sib_ctx* c, const sib_opts* o) {
     API_BEGIN(c)
@@ -1868,15 +1923,24 @@ int sib_set_options(sib_ctx* c, const sib_opts* o) {
         n.power_iters < 1 || n.power_iters > 1000 || !(n.rtol >= 0) || n.max_it < 1 || n.max_it > 100000 ||
         n.restart < 1 || n.restart > 100 || (n.fuse_small != 0 && n.fuse_small != 1) ||
         (n.smooth_krylov != 0 && n.smooth_krylov != 1) || (n.smooth_krylov && (n.nu1 > WRAP_MAXK || n.nu2 > WRAP_MAXK)) ||
-        (n.sc_relax != SIB_RELAX_JACOBI && n.sc_relax != SIB_RELAX_SGS))
+        (n.sc_relax != SIB_RELAX_JACOBI && n.sc_relax != SIB_RELAX_SGS) ||
+        (n.domain != SIB_DOMAIN_PERIODIC && n.domain != SIB_DOMAIN_CAVITY))
         throw SibError(SIB_ERR_ARG, "option out of range");
+    if (n.domain == SIB_DOMAIN_CAVITY) {
+        if (!CAVITY_SOLVE_ENABLED) throw SibError(SIB_ERR_UNIMPLEMENTED, "the cavity domain is not available");
+        if (n.smoother != SIB_SMOOTHER_VANKA || n.smooth_krylov)
+            throw SibError(SIB_ERR_UNIMPLEMENTED, "the cavity takes the Vanka smoother with damped sweeps");
+    }
     resolve_opts(&n);
     const bool smootherChanged = n.smoother != c->opts.smoother ||
                                  (n.smoother == SIB_SMOOTHER_SC && n.sc_relax != c->opts.sc_relax) ||
                                  (n.smoother == SIB_SMOOTHER_RAS &&
                                   (n.box != c->opts.box || n.box_overlap != c->opts.box_overlap));
+    const bool domainChanged = n.domain != c->opts.domain;
     c->opts = n;
     if (n.smooth_krylov) alloc_wrap_bufs(c);
+    // the windows (masked in the cavity) and the coarsest operator follow the domain
+    if (domainChanged) c->kappaDirty = true;
     // SC needs eigen estimates, RAS its subdomain inverses: both come from sib_setup
     if (smootherChanged && n.smoother != SIB_SMOOTHER_VANKA) c->fluidDirty = true;
     invalidate_graphs(c);
@@ -2066,12 +2130,21 @@ int sib_residual_restrict(sib_ctx* c, int l, int prec, const void* x, const void
     check_level(c, l, 1);
     if (!valid_prec(prec) || !x || !b || !rc) throw SibError(SIB_ERR_ARG, "bad argument");
     cudaStream_t s = S(stream);
+    const int Nc = c->L[l - 1].N;
     if (prec == SIB_PREC_FP64) {
-        apply_operator<double>(c, l, (const double*)x, (const double*)b, (double*)c->L[l].p[0].r, s);
-        KL(c, launch_restrict<double>(c->L[l - 1].N, (const double*)c->L[l].p[0].r, (double*)rc, s));
+        const double* r = (const double*)c->L[l].p[0].r;
+        apply_operator<double>(c, l, (const double*)x, (const double*)b, (double*)r, s);
+        if (cavity(c))
+            KL(c, launch_cavity_restrict<double>(Nc, r, (double*)rc, s));
+        else
+            KL(c, launch_restrict<double>(Nc, r, (double*)rc, s));
     } else {
-        apply_operator<float>(c, l, (const float*)x, (const float*)b, (float*)c->L[l].p[1].r, s);
-        KL(c, launch_restrict<float>(c->L[l - 1].N, (const float*)c->L[l].p[1].r, (float*)rc, s));
+        const float* r = (const float*)c->L[l].p[1].r;
+        apply_operator<float>(c, l, (const float*)x, (const float*)b, (float*)r, s);
+        if (cavity(c))
+            KL(c, launch_cavity_restrict<float>(Nc, r, (float*)rc, s));
+        else
+            KL(c, launch_restrict<float>(Nc, r, (float*)rc, s));
     }
     kcheck(c);
     return SIB_OK;
@@ -2082,10 +2155,18 @@ int sib_prolong_add(sib_ctx* c, int l, int prec, const void* ec, void* xf, void*
     API_BEGIN(c)
     check_level(c, l, 1);
     if (!valid_prec(prec) || !ec || !xf) throw SibError(SIB_ERR_ARG, "bad argument");
-    if (prec == SIB_PREC_FP64)
-        KL(c, launch_prolong_add<double>(c->L[l - 1].N, (const double*)ec, (double*)xf, S(stream)));
-    else
-        KL(c, launch_prolong_add<float>(c->L[l - 1].N, (const float*)ec, (float*)xf, S(stream)));
+    const int Nc = c->L[l - 1].N;
+    if (prec == SIB_PREC_FP64) {
+        if (cavity(c))
+            KL(c, launch_cavity_prolong_add<double>(Nc, (const double*)ec, (double*)xf, S(stream)));
+        else
+            KL(c, launch_prolong_add<double>(Nc, (const double*)ec, (double*)xf, S(stream)));
+    } else {
+        if (cavity(c))
+            KL(c, launch_cavity_prolong_add<float>(Nc, (const float*)ec, (float*)xf, S(stream)));
+        else
+            KL(c, launch_prolong_add<float>(Nc, (const float*)ec, (float*)xf, S(stream)));
+    }
     kcheck(c);
     return SIB_OK;
     API_END(c)

@@ -30,6 +30,8 @@ SMOOTHER_SC = 1
 SMOOTHER_RAS = 2
 RELAX_JACOBI = 0
 RELAX_SGS = 1
+DOMAIN_PERIODIC = 0
+DOMAIN_CAVITY = 1
 PREC_FP64 = 0
 PREC_FP32 = 1
 MAX_LEVELS = 12
@@ -53,7 +55,7 @@ class SibOpts(ctypes.Structure):
         ("power_iters", ctypes.c_int), ("vcycle_fp32", ctypes.c_int), ("rtol", ctypes.c_double),
         ("max_it", ctypes.c_int), ("restart", ctypes.c_int), ("add_SKXn", ctypes.c_int), ("use_graphs", ctypes.c_int),
         ("fuse_small", ctypes.c_int), ("smooth_krylov", ctypes.c_int), ("sc_relax", ctypes.c_int),
-        ("box", ctypes.c_int), ("box_overlap", ctypes.c_int),
+        ("box", ctypes.c_int), ("box_overlap", ctypes.c_int), ("domain", ctypes.c_int),
     ]
 
 
