@@ -249,9 +249,13 @@ __global__ void k_cavity_assemble_L0(int N, double rho, double mu, double dt, co
     Aug[q] = v;
 }
 
-// Cavity windows of one level: entries in a wall face's row, or whose column (the face at the
-// entry's unwrapped offset) is a wall face or lies across a wall, are set to 0.  Applied after each
-// level's Galerkin product, this gives the cavity's R_u B P_u with P_u restricted to the unknowns.
+// Cavity windows of one level: the entries in a wall face's row or column are set to 0.  Applied after
+// each level's Galerkin product (and to the finest windows), this gives the cavity's R_u B P_u with
+// P_u restricted to the unknowns.  Columns are taken modulo N, as the windows store them: on an 8 x 8
+// level the offsets +4 and -4 name the same face.  No entry couples two unknowns through a wall:
+// the finest windows join faces within one marker's support, which stays inside the domain, and
+// the product for an unknown row only reaches fine faces inside the domain, so every coupling it
+// forms runs inside the domain or ends on a wall face, which this mask removes.
 __global__ void k_cavity_mask_windows(double* __restrict__ win, const int* __restrict__ tiles, int N, int tx, int ty,
                                       int ntx) {
     const int slot = blockIdx.x, comp = blockIdx.y;
@@ -260,13 +264,12 @@ __global__ void k_cavity_mask_windows(double* __restrict__ win, const int* __res
     const int t = tiles[slot];
     const int i = (t % ntx) * tx + q % tx, j = (t / ntx) * ty + q / tx;
     double* w = win + ((size_t)(slot * 2 + comp) * WIN_SIZE) * per + q;
-    const int a = comp == 0 ? i : j;   // the row face's coordinate along its own normal
+    const int m = N - 1;
+    const bool wallRow = comp == 0 ? i == 0 : j == 0;
     for (int kw = 0; kw < WIN_SIZE; ++kw) {
         const int ox = kw % WD - WR, oy = kw / WD - WR;
-        const int ci = i + ox, cj = j + oy;
-        const int ca = comp == 0 ? ci : cj, ct = comp == 0 ? cj : ci;   // column: normal, tangential
-        const bool inside = ca >= 1 && ca <= N - 1 && ct >= 0 && ct <= N - 1;
-        if (a == 0 || !inside) w[(size_t)kw * per] = 0.0;
+        const bool wallCol = comp == 0 ? ((i + ox) & m) == 0 : ((j + oy) & m) == 0;
+        if (wallRow || wallCol) w[(size_t)kw * per] = 0.0;
     }
 }
 

@@ -171,7 +171,7 @@ template <typename T> void launch_cavity_prolong_add(int Nc, const T* ec, T* xf,
 // the cavity's coarsest operator bordered for its gauge (the constant pressure), [L0 + Z Z^T | I]
 void launch_cavity_assemble_L0(int N0, double rho, double mu, double dt, const double* B, double* Aug,
                                cudaStream_t s);
-// zero the window entries of one level that couple to or across a wall
+// zero the window entries of one level in a wall face's row or column
 void launch_cavity_mask_windows(double* win, const int* tiles, int nTiles, int N, int tx, int ty, int ntx,
                                 cudaStream_t s);
 template <typename T> void launch_vanka(const GridK<T>& g, const T* x, const T* b, T* xo, cudaStream_t s);

@@ -38,8 +38,9 @@ def _needs_cavity():
         pytest.skip("the options do not accept the cavity domain")
 
 
-def make_case(N, rho, mu, gamma=5.0, **opts):
-    st = I.thick_annulus(N, gamma)
+def make_case(N, rho, mu, gamma=5.0, wide=False, **opts):
+    # wide: a thin circle of radius 0.38, 3.8 h from the walls at 32^2, whose 8 x 8 windows reach them
+    st = I.thin_circle(N, gamma, r=0.38) if wide else I.thick_annulus(N, gamma)
     dt = 0.32 / N
     S = sib.Solver(N)
     S.set_fluid(rho, mu, dt)
@@ -73,9 +74,9 @@ def test_cavity_transfers_and_coarse_solve(rho, mu):
     assert rel(z[id0], H.coarse_pinv @ b0) < TOL64
 
 
-@pytest.mark.parametrize("rho,mu", [(0.0, 1.0), (1.0, 1e-2)])
-def test_cavity_vcycle(rho, mu):
-    st, dt, S, H = make_case(32, rho, mu, vcycle_fp32=0)
+@pytest.mark.parametrize("rho,mu,wide", [(0.0, 1.0, False), (1.0, 1e-2, False), (0.0, 1.0, True)])
+def test_cavity_vcycle(rho, mu, wide):
+    st, dt, S, H = make_case(32, rho, mu, wide=wide, vcycle_fp32=0)
     N = 32
     idx = cavity.interior(N)
     b = cavity.lid_rhs(N, mu) + np.random.default_rng(7).standard_normal(idx.size)
