@@ -296,6 +296,48 @@ def paper_workloads(sib, torch, dev):
             "boundary": "periodic (the paper's lid-driven cavity walls are not modelled)", "cases": cases}
 
 
+def cavity_accepted(sib):
+    """Whether the library's options accept the lid-driven cavity domain."""
+    S = sib.Solver(32)
+    try:
+        S.set_options(domain=sib.DOMAIN_CAVITY)
+        return True
+    except sib.SibError:
+        return False
+    finally:
+        S.close()
+
+
+def cavity_workloads(sib, torch, dev):
+    """The paper's lid-driven cavity (Sec. 5: no-slip walls, regularised lid) with its thick annulus and
+    thin circle, Stokes flow, one linear solve each (dt = 0.32 h, g = 0: the lid and the elastic force
+    of the initial configuration drive the flow; tolerance 1e-12, at most 100 iterations, FP32 V-cycle,
+    Vanka), over gamma."""
+    if not cavity_accepted(sib):
+        return {"unavailable": "the options do not accept the cavity domain"}
+    from paper_1612_02208_gb300 import inputs
+    cases = []
+    for kind in ("annulus", "circle"):
+        for gamma in (5.0, 50.0, 500.0):
+            prob = inputs.paper_problem(kind, 128, gamma)
+            st = prob.structure
+            S = sib.Solver(prob.N)
+            S.set_fluid(prob.rho, prob.mu, prob.dt)
+            S.set_structure(torch.as_tensor(st.X, device=dev), torch.as_tensor(st.edges, device=dev),
+                            torch.as_tensor(st.kappa, device=dev))
+            S.set_options(domain=sib.DOMAIN_CAVITY, rtol=1e-12, max_it=100)
+            S.setup()
+            g = torch.zeros(3 * prob.N * prob.N, dtype=torch.float64, device=dev)
+            w = torch.empty_like(g)
+            S.solve(g, w, allow_unconverged=True)
+            d = S.stats.as_dict()
+            cases.append(dict(kind=kind, N=prob.N, gamma=gamma, flow="stokes", smoother="vanka",
+                              iterations=d["iterations"], converged=d["converged"],
+                              setup_ms=round(d["setup_ms"], 3), solve_ms=round(d["solve_ms"], 3)))
+            S.close()
+    return {"tol": 1e-12, "max_it": 100, "dt": "0.32 h", "boundary": "lid-driven cavity", "cases": cases}
+
+
 def e2e_step(S, g_host, w_host, kap_host, kap_dev, sib, torch):
     """Through the host-buffer call: stiffness uploaded from pinned memory, g in, w out."""
     for sm in SMOOTHERS:
@@ -500,6 +542,7 @@ def run_native(args):
         ras.append({"box": WIDE_BOX[0], "overlap": WIDE_BOX[1],
                     "unavailable": "the options accept subdomains up to 6 cells wide"})
     paper = paper_workloads(sib, torch, dev) if not args.no_paper else None
+    cav = cavity_workloads(sib, torch, dev) if not args.no_paper else None
 
     # end to end through the host-buffer C call, pinned host memory
     g_host = torch.as_tensor(prob.g).pin_memory().numpy()
@@ -551,7 +594,7 @@ def run_native(args):
             "krylov_smoothing": {"ms_per_solve": round(kry_ms, 4), "cases": kry_records},
             "sc_gauss_seidel": sc_gs,
             "box_ras": ras,
-            "paper_workloads": paper,
+            "paper_workloads": paper, "cavity_workloads": cav,
             "roofline": roofline, "time_loop": tloop, "vcycle_large": large, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk, "wall_s": round(wall, 3),
         }

@@ -91,12 +91,14 @@ typedef struct {
 
 /* Domains.  SIB_DOMAIN_CAVITY is the paper's lid-driven cavity (Sec. 5) on the same layout: the seam
  * faces u(0, j) and v(i, 0) are the no-slip walls and hold 0 in every vector; tangential walls use
- * the ghost value -q_inside; the lid's 2 mu u_lid(x_i) / h^2 on the top row of u faces is part of the
- * caller's g.  Solves, V-cycles, sweeps and transfers then follow the cavity: Vanka sweeps with the
- * wall rules, the walled RT0 transfers with the pressure prolongation reflected at the walls, coarse
- * IB windows with their wall couplings removed, and a coarsest pseudo-inverse whose kernel is the
- * constant pressure.  It takes the Vanka smoother with damped sweeps (smooth_krylov = 0).  This
- * version returns SIB_ERR_UNIMPLEMENTED for SIB_DOMAIN_CAVITY from sib_set_options. */
+ * the ghost value 2 q_wall - q_inside.  The solve's right-hand side is g with its wall faces set to 0,
+ * plus S K X^n, plus the regularised lid u_lid(x) = (1 - cos 2 pi x) / 2 at y = 1 as its ghost term
+ * 2 mu u_lid(x_i) / h^2 on the top row of u faces.  Solves, V-cycles, sweeps and transfers then
+ * follow the cavity: Vanka sweeps with the wall rules, the walled RT0 transfers with the pressure
+ * prolongation reflected at the walls, coarse IB windows without wall couplings, and a coarsest
+ * pseudo-inverse whose kernel is the constant pressure.  The cavity takes the Vanka smoother with
+ * damped sweeps (smooth_krylov = 0), and its structure must keep its Peskin support 2.5 h away from
+ * the walls.  This version returns SIB_ERR_UNIMPLEMENTED for SIB_DOMAIN_CAVITY from sib_set_options. */
 #define SIB_DOMAIN_PERIODIC 0
 #define SIB_DOMAIN_CAVITY   1
 

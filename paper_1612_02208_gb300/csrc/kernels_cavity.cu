@@ -283,7 +283,22 @@ __global__ void k_cavity_zero_walls(T* __restrict__ x, int N) {
     x[N * N + k] = T(0);
 }
 
+// rhs(u(i, N-1)) += 2 mu u_lid(i h) / h^2 for i = 1 .. N-1: the known part of the ghost value across
+// the lid, u_lid(x) = (1 - cos 2 pi x) / 2 (the regularised lid of Sec. 5)
+__global__ void k_cavity_add_lid(double* __restrict__ rhs, int N, double mu) {
+    pdl_entry();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 1 || i >= N) return;
+    const double h = 1.0 / N, x = i * h;
+    const double ulid = 0.5 * (1.0 - cospi(2.0 * x));
+    rhs[(N - 1) * N + i] += 2.0 * mu * ulid / (h * h);
+}
+
 }  // namespace
+
+void launch_cavity_add_lid(double* rhs, int N, double mu, cudaStream_t s) {
+    launch_pdl(k_cavity_add_lid, dim3((N + 127) / 128), dim3(128), 0, s, rhs, N, mu);
+}
 
 template <typename T>
 void launch_cavity_residual(const GridK<T>& g, const T* x, const T* b, T* r, cudaStream_t s) {

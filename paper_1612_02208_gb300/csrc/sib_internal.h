@@ -164,6 +164,8 @@ void launch_cavity_vanka(const GridK<T>& g, const T* x, const T* b, T* r, T* d, 
 // r = b - L x of the cavity (0 on the wall faces); x <- 0 on the wall faces
 template <typename T> void launch_cavity_residual(const GridK<T>& g, const T* x, const T* b, T* r, cudaStream_t s);
 template <typename T> void launch_cavity_zero_walls(T* x, int N, cudaStream_t s);
+// rhs += the regularised lid's term 2 mu u_lid(x_i) / h^2 on the top row of u faces
+void launch_cavity_add_lid(double* rhs, int N, double mu, cudaStream_t s);
 // the cavity's transfers (kernels_cavity.cu): restriction with the coarse wall faces zeroed, and
 // prolongation-correction with the pressure reflected at the walls
 template <typename T> void launch_cavity_restrict(int Nc, const T* rf, T* bc, cudaStream_t s);

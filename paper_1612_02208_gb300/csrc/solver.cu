@@ -1527,7 +1527,10 @@ void build_rhs(sib_ctx* c, const double* g, bool addSKX, cudaStream_t s) {
                                     lv.spreadWarp, s));
         KL(c, launch_axpby<double>(1.0, c->rhs, 1.0, (const double*)lv.p[0].fib, c->rhs, nv, s));
     }
-    if (cavity(c)) KL(c, launch_cavity_zero_walls<double>(c->rhs, c->N, s));   // the walls are not unknowns
+    if (cavity(c)) {   // the walls are not unknowns; the moving lid enters through the ghost values
+        KL(c, launch_cavity_zero_walls<double>(c->rhs, c->N, s));
+        KL(c, launch_cavity_add_lid(c->rhs, c->N, c->mu, s));
+    }
     project(c, c->rhs, s);
 }
 
