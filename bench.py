@@ -408,6 +408,10 @@ def large_vcycle(sib, torch, reps=20, N=None):
         ms, by = S.time_kernel("ras", lmax, True, reps=20)
         torch.cuda.nvtx.range_pop()
         out["kernels"][key] = {"ms": round(ms, 5), "bytes": by, "gbs": round(by / (ms * 1e-3) / 1e9, 1)}
+        # the correction is a dense product: 2 ne flops per owned dof, ne = 3 e^2 + 2 e, e = b + 2 o
+        e = bx + 2 * ov
+        flops = 2.0 * (3 * e * e + 2 * e) * 3.0 * LARGE * LARGE
+        out["kernels"][key]["tflops"] = round(flops / (ms * 1e-3) / 1e12, 2)
     S.close()
     return out
 
