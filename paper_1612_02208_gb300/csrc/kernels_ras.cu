@@ -601,11 +601,14 @@ __global__ void __launch_bounds__(32 * RAS_BW) k_ras_apply_big(RasGeo G, const i
     const int N = G.N, n = N * N, m = N - 1, bb = G.b * G.b, nown = G.nown;
     const int nboxes = G.nbs * G.nbs, k0 = blockIdx.x * TL::NBX;
     const int s0 = 2 * warp, s1 = 2 * warp + 1;   // the warp's two slots: boxes warp BPT .. warp BPT + BPT - 1
-    T acc[RA][TL::BPT];
+    // each chunk's products are summed apart and then added to the total: the terms cancel heavily
+    // (their magnitudes sum to about 10^2 times the result), and blocked summation keeps the FP32
+    // rounding error at about half that of one running sum over all ne terms
+    T tot[RA][TL::BPT];
 #pragma unroll
     for (int a = 0; a < RA; ++a)
 #pragma unroll
-        for (int c2 = 0; c2 < TL::BPT; ++c2) acc[a][c2] = T(0);
+        for (int c2 = 0; c2 < TL::BPT; ++c2) tot[a][c2] = T(0);
     int rowA[RA];
 #pragma unroll
     for (int a = 0; a < RA; ++a) rowA[a] = lane + 32 * a < nown ? lane + 32 * a : 0;   // rows past nown: unused
@@ -640,6 +643,11 @@ __global__ void __launch_bounds__(32 * RAS_BW) k_ras_apply_big(RasGeo G, const i
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         __syncthreads();
+        T acc[RA][TL::BPT];
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+#pragma unroll
+            for (int c2 = 0; c2 < TL::BPT; ++c2) acc[a][c2] = T(0);
 #pragma unroll 4
         for (int ql = 0; ql < kc; ++ql) {
             T mv[RA];
@@ -655,6 +663,10 @@ __global__ void __launch_bounds__(32 * RAS_BW) k_ras_apply_big(RasGeo G, const i
                     acc[a][TL::VW + c2] += mv[a] * vget<T>(v1, c2);
                 }
         }
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+#pragma unroll
+            for (int c2 = 0; c2 < TL::BPT; ++c2) tot[a][c2] += acc[a][c2];
     }
 #pragma unroll
     for (int c2 = 0; c2 < TL::BPT; ++c2) {
@@ -667,7 +679,7 @@ __global__ void __launch_bounds__(32 * RAS_BW) k_ras_apply_big(RasGeo G, const i
             if (rr >= nown) continue;
             const int comp = rr / bb, rem = rr - comp * bb;
             const size_t d = (size_t)comp * n + (size_t)(J * G.b + rem / G.b) * N + I * G.b + rem % G.b;
-            xo[d] = (x ? x[d] : T(0)) + omega * acc[a][c2];
+            xo[d] = (x ? x[d] : T(0)) + omega * tot[a][c2];
         }
     }
 }
