@@ -721,3 +721,22 @@ def test_paper_workload_trends_on_the_oracle():
     assert its["annulus", 500.0] >= its["annulus", 5.0], its
     assert its["circle", 500.0] >= its["circle", 5.0], its
     assert its["circle", 500.0] >= its["annulus", 500.0], its
+
+
+def test_ras_overlap_trend_on_the_thin_membrane():
+    """The paper's finding for the thin membrane in Stokes flow at gamma = 500 (Sec. 5.2.1): solver
+    performance depends strongly on the overlap width, and only larger subdomains with more overlap
+    converge.  At 32^2 to 1e-12: 4 x 4 boxes with overlap 1 hit the 100-iteration cap, 8 x 8 boxes
+    with overlap 2 converge, and more overlap on the 4 x 4 boxes helps."""
+    prob = I.paper_problem("circle", 32, 500.0)
+    L = system.operator_of(prob)
+    b = system.rhs(prob)
+    its = {}
+    for bx, o in ((4, 1), (4, 2), (8, 2)):
+        H = multigrid.Hierarchy(prob, smoother="ras", box=bx, overlap=o)
+        _, it, _, conv = krylov.fgmres(lambda z: L @ z, H.vcycle, b, rtol=1e-12, max_it=100, restart=100,
+                                       project=lambda v: system.project(v, 32, prob.rho))
+        its[bx, o] = (it, conv)
+    assert not its[4, 1][1], its
+    assert its[4, 2][1] and its[8, 2][1], its
+    assert its[8, 2][0] < its[4, 2][0] < 100, its
