@@ -84,8 +84,9 @@ typedef struct {
     int    sc_relax;      /* SC: point relaxation preconditioning both Chebyshev iterations (Sec. 3.3,
                              SC smoothing): SIB_RELAX_JACOBI (diagonal, default) or SIB_RELAX_SGS (one
                              symmetric red-black Gauss-Seidel sweep from zero, colours 0, 1, 1, 0)    */
-    int    box;           /* RAS: cells per box side b, 1, 2 or 4 (4)                                */
-    int    box_overlap;   /* RAS: overlap o in cells on each side, b + 2 o <= 6 (1)                  */
+    int    box;           /* RAS: cells per box side b, 1, 2, 4 or 8 (4)                             */
+    int    box_overlap;   /* RAS: overlap o in cells on each side, b + 2 o <= 16 and
+                             b + 2 o < 2 n_min (1)                                                   */
     int    domain;        /* SIB_DOMAIN_PERIODIC (default) or SIB_DOMAIN_CAVITY (see below)          */
 } sib_opts;
 
@@ -98,7 +99,7 @@ typedef struct {
  * prolongation reflected at the walls, coarse IB windows without wall couplings, and a coarsest
  * pseudo-inverse whose kernel is the constant pressure.  The cavity takes the Vanka smoother with
  * damped sweeps (smooth_krylov = 0), and its structure must keep its Peskin support 2.5 h away from
- * the walls.  This version returns SIB_ERR_UNIMPLEMENTED for SIB_DOMAIN_CAVITY from sib_set_options. */
+ * the walls; other smoothers return SIB_ERR_UNIMPLEMENTED from sib_set_options. */
 #define SIB_DOMAIN_PERIODIC 0
 #define SIB_DOMAIN_CAVITY   1
 
@@ -156,6 +157,13 @@ int sib_solve_host(sib_ctx* ctx, const double* g_host, double* w_host, sib_stats
 /* Solve L w = rhs for an arbitrary right-hand side rhs (3N^2), without adding S K X^n.  L is
  * symmetric, so this is also the transposed (adjoint) solve. */
 int sib_solve_rhs(sib_ctx* ctx, const double* rhs, double* w, sib_stats* stats, void* stream);
+/* The transposed (adjoint) solve L^T w = rhs, used by the backward pass of a differentiated solve.
+ * The eliminated operator of Eq. (matrix-impib) is symmetric: S = J^T / h^2 (Appendix), K is
+ * symmetric and -D = G^T on the periodic MAC grid, so L^T = L and this is the same FGMRES and
+ * V-cycle as sib_solve_rhs, with the same arguments (rhs, w: 3N^2 device doubles; stats may be
+ * NULL; SIB_ERR_NOT_CONVERGED with outputs written if max_it is reached).  It is kept as its own
+ * entry point so that callers state which system they solve. */
+int sib_solve_transpose(sib_ctx* ctx, const double* rhs, double* w, sib_stats* stats, void* stream);
 
 /* Gradients of a loss l(w) through the solve (discrete adjoint of Eq. matrix-impib): given the
  * forward solution w and the adjoint solution lam (both 3N^2), writes
@@ -232,8 +240,11 @@ int sib_time_kernel(sib_ctx* ctx, int kernel, int level, int prec, int reps, voi
  * until exit.
  *   Limits: N a power of two, 8 <= N <= 256; 0 <= M <= 16384.  Larger sizes return
  *   SIB_ERR_TOO_LARGE; other invalid arguments return SIB_ERR_ARG.
- *   The first call on each device looks up the scratch array's device address (a one-time
- *   set-up); make that first call before any stream capture.
+ *   Each call outside stream capture looks up the scratch array's device address on the current
+ *   device; a call made while `stream` is being captured reuses the address found by the last
+ *   uncaptured call on that device.  So make one call on each device before any capture, and one
+ *   again after a cudaDeviceReset; a captured call on a device with no earlier call returns
+ *   SIB_ERR_STATE.
  *   All calls share the one scratch array: calls that overlap on the GPU (other streams, other
  *   host threads) race and must be serialised by the caller. */
 int sib_spread_noalloc(int N, int M, const double* X, const double* F, double* f, void* stream);

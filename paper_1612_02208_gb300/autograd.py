@@ -1,9 +1,10 @@
 """Differentiable Stokes-IB solve: torch.autograd.Function over the C ABI.
 
 forward(g, kappa, X) -> w solves L_IB(X, kappa) w = b(g, X, kappa) (Eq. matrix-impib) with the
-library's FGMRES + multigrid; backward(dl/dw) solves the adjoint system L_IB lam = dl/dw (L_IB is
-symmetric, so this is the same solve) and evaluates dl/dkappa and dl/dX with sib_grad, which
-recomputes the spreading weights from X instead of storing them.  dl/dg = lam.
+library's FGMRES + multigrid; backward(dl/dw) solves the adjoint system L_IB^T lam = dl/dw with
+sib_solve_transpose (L_IB is symmetric, so this is the forward solve's FGMRES and V-cycle) and
+evaluates dl/dkappa and dl/dX with sib_grad, which recomputes the spreading weights from X instead
+of storing them.  dl/dg = lam.
 
 All tensors live on the solver's CUDA device in float64; this module only marshals arguments.
 """
@@ -32,7 +33,7 @@ class StokesIBSolve(torch.autograd.Function):
         solver = ctx.solver
         if getattr(solver, "_ad_token", None) is not ctx.token:   # another forward reconfigured it
             _configure(solver, X, ctx.edges, kappa, ctx.token)
-        lam = solver.solve_rhs(grad_w.detach().contiguous())
+        lam = solver.solve_transpose(grad_w.detach().contiguous())
         dkappa, dX = solver.grad(w, lam)
         return lam, dkappa, dX, None, None
 

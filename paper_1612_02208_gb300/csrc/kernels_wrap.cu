@@ -1,80 +1,249 @@
 // Kernels of the Krylov-wrapped smoothing step (Sec. 3.3): a pre- or post-smoothing stage of nu
 // sweeps becomes nu iterations of flexible GMRES on the level's residual equation, each
 // preconditioned by one undamped sweep of the basic smoother.  The level vectors are in the
-// V-cycle's precision T; inner products are summed in FP64 in a fixed order (block partials, then
-// one block), the small Hessenberg least-squares problem is solved in FP64 by one thread.
+// V-cycle's precision T.  Inner products are formed per thread over 16-byte vectors of T (products
+// of one vector summed in T), accumulated in FP64, reduced per block, and the block partials are
+// summed by one block per product in block order: a fixed order, so results do not depend on
+// timing.  The classical Gram-Schmidt update of each pass is fused with the inner products that
+// follow it (the second pass's coefficients, or the norm).  The small Hessenberg least-squares
+// problem is solved in FP64 by one thread.
 #include "sib_internal.h"
 
 namespace sib {
 
 namespace {
 
-__device__ __forceinline__ double wblock_sum(double v, double* ws) {
+template <typename T>
+struct WVec;
+template <>
+struct WVec<float> {
+    using type = float4;
+    static constexpr int n = 4;
+};
+template <>
+struct WVec<double> {
+    using type = double2;
+    static constexpr int n = 2;
+};
+template <typename T>
+__device__ __forceinline__ T wv(const typename WVec<T>::type& v, int c);
+template <>
+__device__ __forceinline__ float wv<float>(const float4& v, int c) {
+    return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
+}
+template <>
+__device__ __forceinline__ double wv<double>(const double2& v, int c) {
+    return c == 0 ? v.x : v.y;
+}
+template <typename T>
+__device__ __forceinline__ void wset(typename WVec<T>::type& v, int c, T x);
+template <>
+__device__ __forceinline__ void wset<float>(float4& v, int c, float x) {
+    if (c == 0) v.x = x;
+    else if (c == 1) v.y = x;
+    else if (c == 2) v.z = x;
+    else v.w = x;
+}
+template <>
+__device__ __forceinline__ void wset<double>(double2& v, int c, double x) {
+    if (c == 0) v.x = x;
+    else v.y = x;
+}
+
+constexpr int WT = 256;           // threads per block
+constexpr int WW = WT / 32;       // warps per block
+
+// Block sums of acc[i], i < cnt, written to partials[i * gridDim.x + blockIdx.x]: warp shuffles,
+// then the warps' values in warp order.
+template <int KC>
+__device__ __forceinline__ void block_partials(double (&acc)[KC], int cnt, double* __restrict__ partials) {
+    __shared__ double ws[KC][WW];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if (lane == 0) ws[wid] = v;
-    __syncthreads();
-    const int nw = (blockDim.x + 31) >> 5;
-    v = (threadIdx.x < nw) ? ws[threadIdx.x] : 0.0;
-    if (wid == 0)
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;   // valid in thread 0
-}
-
-// partials[i * gridDim.x + block] = block's share of V_i . w, i < cnt (cnt <= WRAP_MAXK + 1)
-template <typename T>
-__global__ void __launch_bounds__(256) k_wdots(const T* __restrict__ V, int64_t ld, int cnt, const T* __restrict__ w,
-                                               int64_t n, double* __restrict__ partials) {
-    pdl_entry();
-    __shared__ double ws[32];
-    double acc[WRAP_MAXK + 1];
 #pragma unroll
-    for (int i = 0; i <= WRAP_MAXK; ++i) acc[i] = 0.0;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const double we = (double)w[e];
-#pragma unroll
-        for (int i = 0; i <= WRAP_MAXK; ++i)
-            if (i < cnt) acc[i] += (double)V[(int64_t)i * ld + e] * we;
+    for (int i = 0; i < KC; ++i) {
+        if (i < cnt) {
+            double v = acc[i];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) ws[i][wid] = v;
+        }
     }
-    for (int i = 0; i < cnt; ++i) {
-        const double s = wblock_sum(acc[i], ws);
-        if (threadIdx.x == 0) partials[(int64_t)i * gridDim.x + blockIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < WW; ++q) s += ws[threadIdx.x][q];
+        partials[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
     }
 }
 
-// out[i] = sum over blocks of partials of vector i (block order), i < cnt; one block per vector
-__global__ void k_wreduce(const double* __restrict__ partials, int nblk, double* __restrict__ out) {
+// partials of V_i . w, i < cnt (cnt <= KC <= WRAP_MAXK + 1)
+template <typename T, int KC>
+__global__ void __launch_bounds__(WT) k_wdots(const T* __restrict__ V, int64_t ld, int cnt, const T* __restrict__ w,
+                                              int64_t n, double* __restrict__ partials) {
+    using VT = typename WVec<T>::type;
+    constexpr int VN = WVec<T>::n;
     pdl_entry();
-    __shared__ double ws[32];
+    double acc[KC];
+#pragma unroll
+    for (int i = 0; i < KC; ++i) acc[i] = 0.0;
+    const int64_t nv = n / VN;
+    for (int64_t e = blockIdx.x * (int64_t)WT + threadIdx.x; e < nv; e += (int64_t)gridDim.x * WT) {
+        const VT we = reinterpret_cast<const VT*>(w)[e];
+#pragma unroll
+        for (int i = 0; i < KC; ++i) {
+            if (i < cnt) {
+                const VT vi = reinterpret_cast<const VT*>(V + (int64_t)i * ld)[e];
+                T s = T(0);
+#pragma unroll
+                for (int c = 0; c < VN; ++c) s = fma(wv<T>(vi, c), wv<T>(we, c), s);
+                acc[i] += (double)s;
+            }
+        }
+    }
+    for (int64_t e = nv * VN + blockIdx.x * (int64_t)WT + threadIdx.x; e < n; e += (int64_t)gridDim.x * WT)
+#pragma unroll
+        for (int i = 0; i < KC; ++i)
+            if (i < cnt) acc[i] += (double)V[(int64_t)i * ld + e] * (double)w[e];
+    block_partials(acc, cnt, partials);
+}
+
+// wout = win - sum_{i < cnt} coef[i] V_i, and then (MODE 1) partials of V_i . wout, i < cnt, or
+// (MODE 2) the partial of wout . wout; cnt <= KC
+template <typename T, int MODE, int KC>
+__global__ void __launch_bounds__(WT) k_wgs(const T* __restrict__ V, int64_t ld, int cnt,
+                                            const double* __restrict__ coef, const T* win, T* wout, int64_t n,
+                                            double* __restrict__ partials) {
+    using VT = typename WVec<T>::type;
+    constexpr int VN = WVec<T>::n;
+    pdl_entry();
+    T cf[KC];
+#pragma unroll
+    for (int i = 0; i < KC; ++i) cf[i] = i < cnt ? (T)coef[i] : T(0);
+    double acc[KC];
+#pragma unroll
+    for (int i = 0; i < KC; ++i) acc[i] = 0.0;
+    const int64_t nv = n / VN;
+    for (int64_t e = blockIdx.x * (int64_t)WT + threadIdx.x; e < nv; e += (int64_t)gridDim.x * WT) {
+        VT y = reinterpret_cast<const VT*>(win)[e];
+        VT vi[KC];
+#pragma unroll
+        for (int i = 0; i < KC; ++i)
+            if (i < cnt) vi[i] = reinterpret_cast<const VT*>(V + (int64_t)i * ld)[e];
+#pragma unroll
+        for (int i = 0; i < KC; ++i)
+            if (i < cnt)
+#pragma unroll
+                for (int c = 0; c < VN; ++c) wset<T>(y, c, fma(-cf[i], wv<T>(vi[i], c), wv<T>(y, c)));
+        reinterpret_cast<VT*>(wout)[e] = y;
+        if (MODE == 1) {
+#pragma unroll
+            for (int i = 0; i < KC; ++i) {
+                if (i < cnt) {
+                    T s = T(0);
+#pragma unroll
+                    for (int c = 0; c < VN; ++c) s = fma(wv<T>(vi[i], c), wv<T>(y, c), s);
+                    acc[i] += (double)s;
+                }
+            }
+        } else if (MODE == 2) {
+            T s = T(0);
+#pragma unroll
+            for (int c = 0; c < VN; ++c) s = fma(wv<T>(y, c), wv<T>(y, c), s);
+            acc[0] += (double)s;
+        }
+    }
+    for (int64_t e = nv * VN + blockIdx.x * (int64_t)WT + threadIdx.x; e < n; e += (int64_t)gridDim.x * WT) {
+        T y = win[e];
+#pragma unroll
+        for (int i = 0; i < KC; ++i)
+            if (i < cnt) y = fma(-cf[i], V[(int64_t)i * ld + e], y);
+        wout[e] = y;
+        if (MODE == 1) {
+#pragma unroll
+            for (int i = 0; i < KC; ++i)
+                if (i < cnt) acc[i] += (double)V[(int64_t)i * ld + e] * (double)y;
+        } else if (MODE == 2) {
+            acc[0] += (double)y * (double)y;
+        }
+    }
+    if (MODE == 1) block_partials(acc, cnt, partials);
+    else if (MODE == 2) block_partials(acc, 1, partials);
+}
+
+// out[i] = sum over the nblk block partials of product i, in block order; one block per product
+__global__ void __launch_bounds__(WT) k_wreduce(const double* __restrict__ partials, int nblk, double* __restrict__ out) {
+    pdl_entry();
+    __shared__ double ws[WW];
     double s = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partials[(int64_t)blockIdx.x * nblk + b];
-    s = wblock_sum(s, ws);
-    if (threadIdx.x == 0) out[blockIdx.x] = s;
-}
-
-// yout = yin + sign * sum_{i < cnt} coef[i] V_i   (yin == nullptr: 0)
-template <typename T>
-__global__ void k_wmaxpy(const T* __restrict__ V, int64_t ld, int cnt, const double* __restrict__ coef, double sign,
-                         const T* yin, T* yout, int64_t n) {
-    pdl_entry();
-    __shared__ T c[WRAP_MAXK + 1];
-    if (threadIdx.x < cnt) c[threadIdx.x] = (T)(sign * coef[threadIdx.x]);
+    for (int b = threadIdx.x; b < nblk; b += WT) s += partials[(int64_t)blockIdx.x * nblk + b];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) ws[wid] = s;
     __syncthreads();
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        T acc = yin ? yin[e] : T(0);
-        for (int i = 0; i < cnt; ++i) acc += c[i] * V[(int64_t)i * ld + e];
-        yout[e] = acc;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < WW; ++q) t += ws[q];
+        out[blockIdx.x] = t;
     }
 }
 
-// v = w / sqrt(nrm2[0]), or 0 when the norm is zero (a vanished Arnoldi vector)
-template <typename T>
-__global__ void k_wscale(const T* __restrict__ w, const double* __restrict__ nrm2, T* __restrict__ v, int64_t n) {
+// yout = yin + sign * sum_{i < cnt} coef[i] V_i   (yin == nullptr: 0); cnt <= KC
+template <typename T, int KC>
+__global__ void __launch_bounds__(WT) k_wmaxpy(const T* __restrict__ V, int64_t ld, int cnt,
+                                               const double* __restrict__ coef, double sign, const T* yin, T* yout,
+                                               int64_t n) {
+    using VT = typename WVec<T>::type;
+    constexpr int VN = WVec<T>::n;
     pdl_entry();
-    const double s = nrm2[0] > 0.0 ? 1.0 / sqrt(nrm2[0]) : 0.0;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        v[e] = (T)((double)w[e] * s);
+    T cf[KC];
+#pragma unroll
+    for (int i = 0; i < KC; ++i) cf[i] = i < cnt ? (T)(sign * coef[i]) : T(0);
+    const int64_t nv = n / VN;
+    for (int64_t e = blockIdx.x * (int64_t)WT + threadIdx.x; e < nv; e += (int64_t)gridDim.x * WT) {
+        VT y;
+        if (yin) {
+            y = reinterpret_cast<const VT*>(yin)[e];
+        } else {
+#pragma unroll
+            for (int c = 0; c < VN; ++c) wset<T>(y, c, T(0));
+        }
+#pragma unroll
+        for (int i = 0; i < KC; ++i) {
+            if (i < cnt) {
+                const VT vi = reinterpret_cast<const VT*>(V + (int64_t)i * ld)[e];
+#pragma unroll
+                for (int c = 0; c < VN; ++c) wset<T>(y, c, fma(cf[i], wv<T>(vi, c), wv<T>(y, c)));
+            }
+        }
+        reinterpret_cast<VT*>(yout)[e] = y;
+    }
+    for (int64_t e = nv * VN + blockIdx.x * (int64_t)WT + threadIdx.x; e < n; e += (int64_t)gridDim.x * WT) {
+        T y = yin ? yin[e] : T(0);
+#pragma unroll
+        for (int i = 0; i < KC; ++i)
+            if (i < cnt) y = fma(cf[i], V[(int64_t)i * ld + e], y);
+        yout[e] = y;
+    }
+}
+
+// v = w / sqrt(nrm2[0]), or 0 when the norm is zero (a vanished Arnoldi vector); the scale is
+// formed once in FP64 and applied in T
+template <typename T>
+__global__ void __launch_bounds__(WT) k_wscale(const T* __restrict__ w, const double* __restrict__ nrm2,
+                                               T* __restrict__ v, int64_t n) {
+    using VT = typename WVec<T>::type;
+    constexpr int VN = WVec<T>::n;
+    pdl_entry();
+    const T s = (T)(nrm2[0] > 0.0 ? 1.0 / sqrt(nrm2[0]) : 0.0);
+    const int64_t nv = n / VN;
+    for (int64_t e = blockIdx.x * (int64_t)WT + threadIdx.x; e < nv; e += (int64_t)gridDim.x * WT) {
+        VT y = reinterpret_cast<const VT*>(w)[e];
+#pragma unroll
+        for (int c = 0; c < VN; ++c) wset<T>(y, c, wv<T>(y, c) * s);
+        reinterpret_cast<VT*>(v)[e] = y;
+    }
+    for (int64_t e = nv * VN + blockIdx.x * (int64_t)WT + threadIdx.x; e < n; e += (int64_t)gridDim.x * WT)
+        v[e] = w[e] * s;
 }
 
 // y = argmin || beta e1 - H y || for the (m + 1) x m Hessenberg matrix of the step (Givens
@@ -119,21 +288,57 @@ __global__ void k_wlsq(const double* __restrict__ hA, const double* __restrict__
 
 }  // namespace
 
+// blocks of the inner-product and update kernels for n values: one 16-byte vector per thread and
+// pass, at most WRAP_BLK blocks (8 per SM)
 template <typename T>
-void launch_wdots(const T* V, int64_t ld, int cnt, const T* w, int64_t n, double* partials, cudaStream_t s) {
-    launch_pdl(k_wdots<T>, WRAP_BLK, 256, 0, s, V, ld, cnt, w, n, partials);
+int wrap_blocks(int64_t n) {
+    const int64_t per = (int64_t)WT * WVec<T>::n;
+    const int64_t b = (n + per - 1) / per;
+    return (int)(b < 1 ? 1 : (b > WRAP_BLK ? WRAP_BLK : b));
 }
-void launch_wreduce(const double* partials, int cnt, double* out, cudaStream_t s) {
-    launch_pdl(k_wreduce, cnt, 128, 0, s, partials, WRAP_BLK, out);
+
+// the kernels hold their cnt coefficients and sums in registers, sized by a compile-time bound
+#define SIB_WRAP_KC(cnt, CALL) \
+    do {                       \
+        if ((cnt) <= 2) {      \
+            constexpr int KC = 2; \
+            CALL;              \
+        } else if ((cnt) <= 4) { \
+            constexpr int KC = 4; \
+            CALL;              \
+        } else {               \
+            constexpr int KC = WRAP_MAXK + 1; \
+            CALL;              \
+        }                      \
+    } while (0)
+
+template <typename T>
+int launch_wdots(const T* V, int64_t ld, int cnt, const T* w, int64_t n, double* partials, cudaStream_t s) {
+    const int nb = wrap_blocks<T>(n);
+    SIB_WRAP_KC(cnt, launch_pdl(k_wdots<T, KC>, nb, WT, 0, s, V, ld, cnt, w, n, partials));
+    return nb;
+}
+template <typename T>
+int launch_wgs(const T* V, int64_t ld, int cnt, const double* coef, const T* win, T* wout, int64_t n, int mode,
+               double* partials, cudaStream_t s) {
+    const int nb = wrap_blocks<T>(n);
+    if (mode == 1)
+        SIB_WRAP_KC(cnt, launch_pdl(k_wgs<T, 1, KC>, nb, WT, 0, s, V, ld, cnt, coef, win, wout, n, partials));
+    else
+        SIB_WRAP_KC(cnt, launch_pdl(k_wgs<T, 2, KC>, nb, WT, 0, s, V, ld, cnt, coef, win, wout, n, partials));
+    return nb;
+}
+void launch_wreduce(const double* partials, int cnt, int nblk, double* out, cudaStream_t s) {
+    launch_pdl(k_wreduce, cnt, WT, 0, s, partials, nblk, out);
 }
 template <typename T>
 void launch_wmaxpy(const T* V, int64_t ld, int cnt, const double* coef, double sign, const T* yin, T* yout, int64_t n,
                    cudaStream_t s) {
-    launch_pdl(k_wmaxpy<T>, num_blocks_for(n), 256, 0, s, V, ld, cnt, coef, sign, yin, yout, n);
+    SIB_WRAP_KC(cnt, launch_pdl(k_wmaxpy<T, KC>, wrap_blocks<T>(n), WT, 0, s, V, ld, cnt, coef, sign, yin, yout, n));
 }
 template <typename T>
 void launch_wscale(const T* w, const double* nrm2, T* v, int64_t n, cudaStream_t s) {
-    launch_pdl(k_wscale<T>, num_blocks_for(n), 256, 0, s, w, nrm2, v, n);
+    launch_pdl(k_wscale<T>, wrap_blocks<T>(n), WT, 0, s, w, nrm2, v, n);
 }
 void launch_wlsq(const double* hA, const double* hB, const double* nr, const double* beta2, int k, double* y,
                  cudaStream_t s) {
@@ -141,7 +346,9 @@ void launch_wlsq(const double* hA, const double* hB, const double* nr, const dou
 }
 
 #define SIB_WRAP_INST(T)                                                                                    \
-    template void launch_wdots<T>(const T*, int64_t, int, const T*, int64_t, double*, cudaStream_t);          \
+    template int launch_wdots<T>(const T*, int64_t, int, const T*, int64_t, double*, cudaStream_t);           \
+    template int launch_wgs<T>(const T*, int64_t, int, const double*, const T*, T*, int64_t, int, double*,     \
+                               cudaStream_t);                                                               \
     template void launch_wmaxpy<T>(const T*, int64_t, int, const double*, double, const T*, T*, int64_t,      \
                                    cudaStream_t);                                                           \
     template void launch_wscale<T>(const T*, const double*, T*, int64_t, cudaStream_t);

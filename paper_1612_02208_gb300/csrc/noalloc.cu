@@ -38,7 +38,7 @@ constexpr size_t SCRATCH_BYTES = 2 * SZ_BASE + 2 * SZ_W64 + 2 * SZ_W32 + SZ_KEYS
 }  // namespace
 
 // The scratch array.  In host code this name is only a host-side stand-in for the device array:
-// its device address is obtained once per device with cudaGetSymbolAddress below.
+// its device address is obtained with cudaGetSymbolAddress below, on the device that is current.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
 namespace {
@@ -47,17 +47,27 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_mtx;
 unsigned char* g_addr[MAX_DEVICES] = {};
 
-// device address of the scratch on the current device (set-up on the first call per device)
-int scratch_address(unsigned char** out) {
+// Device address of the scratch on the current device.  Outside stream capture it is looked up on
+// every call (cheap once the module is loaded), so a context re-created after cudaDeviceReset gets
+// the array's new address; during capture, where no runtime query should be made, the address of
+// the last uncaptured call on this device is used, and a device never called outside capture is an
+// error.
+int scratch_address(cudaStream_t s, unsigned char** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return SIB_ERR_CUDA;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return SIB_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mtx);
-    if (!g_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr) return SIB_ERR_CUDA;
+        if (e != cudaSuccess || p == nullptr) {
+            g_addr[dev] = nullptr;
+            return SIB_ERR_CUDA;
+        }
         g_addr[dev] = (unsigned char*)p;
     }
+    if (!g_addr[dev]) return SIB_ERR_STATE;
     *out = g_addr[dev];
     return SIB_OK;
 }
@@ -71,7 +81,7 @@ extern "C" int sib_spread_noalloc(int N, int M, const double* X, const double* F
     if (!f || (M > 0 && (!X || !F))) return SIB_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char* base_addr = nullptr;
-    const int rc = scratch_address(&base_addr);
+    const int rc = scratch_address(s, &base_addr);
     if (rc != SIB_OK) return rc;
     if (cudaMemsetAsync(f, 0, sizeof(double) * 2 * (size_t)N * N, s) != cudaSuccess) return SIB_ERR_CUDA;
     if (M == 0) return cudaGetLastError() == cudaSuccess ? SIB_OK : SIB_ERR_CUDA;

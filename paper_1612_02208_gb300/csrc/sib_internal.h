@@ -221,10 +221,15 @@ template <typename T> cudaError_t launch_vcycle_small(const SmallArgs<T>& a, siz
 
 // launchers (kernels_wrap.cu): the Krylov-wrapped smoothing step
 constexpr int WRAP_MAXK = 8;     // at most this many FGMRES iterations a smoothing stage
-constexpr int WRAP_BLK = 128;    // blocks of the partial inner products
-template <typename T> void launch_wdots(const T* V, int64_t ld, int cnt, const T* w, int64_t n, double* partials,
-                                        cudaStream_t s);
-void launch_wreduce(const double* partials, int cnt, double* out, cudaStream_t s);
+constexpr int WRAP_BLK = 152 * 8;   // most blocks of the inner-product and update kernels
+// partials of V_i . w (i < cnt) into partials[i * nblk + block]; returns nblk
+template <typename T> int launch_wdots(const T* V, int64_t ld, int cnt, const T* w, int64_t n, double* partials,
+                                       cudaStream_t s);
+// wout = win - sum_{i < cnt} coef[i] V_i, then partials of V_i . wout (mode 1) or of wout . wout
+// (mode 2); returns nblk
+template <typename T> int launch_wgs(const T* V, int64_t ld, int cnt, const double* coef, const T* win, T* wout,
+                                     int64_t n, int mode, double* partials, cudaStream_t s);
+void launch_wreduce(const double* partials, int cnt, int nblk, double* out, cudaStream_t s);
 template <typename T> void launch_wmaxpy(const T* V, int64_t ld, int cnt, const double* coef, double sign, const T* yin,
                                          T* yout, int64_t n, cudaStream_t s);
 template <typename T> void launch_wscale(const T* w, const double* nrm2, T* v, int64_t n, cudaStream_t s);

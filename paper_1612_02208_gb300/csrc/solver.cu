@@ -602,8 +602,9 @@ void wrapped_smooth(sib_ctx* c, int l, const T* x, const T* b, T* xo, int k, cud
     double* y = beta2 + 1;
     double* part = y + WRAP_MAXK;
     auto dots = [&](const T* Vs, int cnt, const T* v, double* out) {
-        KL(c, launch_wdots<T>(Vs, n3, cnt, v, n3, part, s));
-        KL(c, launch_wreduce(part, cnt, out, s));
+        const int nb = launch_wdots<T>(Vs, n3, cnt, v, n3, part, s);
+        KL(c, launch_wreduce(part, cnt, nb, out, s));
+        ++c->launches;
     };
     const T* r0 = b;
     if (x) {
@@ -625,11 +626,13 @@ void wrapped_smooth(sib_ctx* c, int l, const T* x, const T* b, T* xo, int k, cud
             KL(c, launch_vanka_zero<T>(g, Vj, Zj, s));
         ib_apply<T>(c, l, Zj, s);
         KL(c, launch_residual<T>(gridk<T>(c, l), Zj, nullptr, w, s));   // w = L z_j
+        // CGS2: h = V^T w; w -= V h and h' = V^T w in one pass; w -= V h' and |w|^2 in one pass
         dots(V, j + 1, w, hA + j * K1);
-        KL(c, launch_wmaxpy<T>(V, n3, j + 1, hA + j * K1, -1.0, w, w, n3, s));
-        dots(V, j + 1, w, hB + j * K1);
-        KL(c, launch_wmaxpy<T>(V, n3, j + 1, hB + j * K1, -1.0, w, w, n3, s));
-        dots(w, 1, w, nr + j);
+        int nb = launch_wgs<T>(V, n3, j + 1, hA + j * K1, w, w, n3, 1, part, s);
+        KL(c, launch_wreduce(part, j + 1, nb, hB + j * K1, s));
+        nb = launch_wgs<T>(V, n3, j + 1, hB + j * K1, w, w, n3, 2, part, s);
+        KL(c, launch_wreduce(part, 1, nb, nr + j, s));
+        c->launches += 2;
         if (j + 1 < k) KL(c, launch_wscale<T>(w, nr + j, V + (size_t)(j + 1) * n3, n3, s));
     }
     KL(c, launch_wlsq(hA, hB, nr, beta2, k, y, s));
@@ -1910,10 +1913,11 @@ int sib_set_stiffness(sib_ctx* c, const double* kappa, void* stream) {
     API_END(c)
 }
 
-// Widest box subdomain the options accept.  The wide-subdomain kernels (up to RAS_EMAX cells, boxes of
-// 8 cells) are built but stay off until their parity tests run; so does the cavity's solve.
-constexpr int RAS_EMAX_ENABLED = RAS_EMAX_SMEM;
-constexpr bool CAVITY_SOLVE_ENABLED = false;
+// Widest box subdomain the options accept: up to RAS_EMAX_SMEM cells in shared memory, wider ones
+// (boxes of 8 cells with overlap 2, up to RAS_EMAX cells) through the global-workspace set-up and the
+// batched correction.
+constexpr int RAS_EMAX_ENABLED = RAS_EMAX;
+constexpr bool CAVITY_SOLVE_ENABLED = true;
 
 int sib_set_options(sib_ctx* c, const sib_opts* o) {
     API_BEGIN(c)
@@ -1994,6 +1998,14 @@ int sib_solve(sib_ctx* c, const double* g, double* w, sib_stats* st, void* strea
 int sib_solve_rhs(sib_ctx* c, const double* rhs, double* w, sib_stats* st, void* stream) {
     API_BEGIN(c)
     if (!rhs || !w) throw SibError(SIB_ERR_ARG, "null pointer");
+    return solve_impl(c, rhs, w, st, S(stream), false);
+    API_END(c)
+}
+
+int sib_solve_transpose(sib_ctx* c, const double* rhs, double* w, sib_stats* st, void* stream) {
+    API_BEGIN(c)
+    if (!rhs || !w) throw SibError(SIB_ERR_ARG, "null pointer");
+    // L_IB is symmetric (S = J^T / h^2, K symmetric, -D = G^T), so L^T w = rhs is the forward system
     return solve_impl(c, rhs, w, st, S(stream), false);
     API_END(c)
 }

@@ -40,7 +40,7 @@ MAX_LEVELS = 12
 EXPORTS = [
     "sib_default_opts", "sib_create", "sib_destroy", "sib_last_error", "sib_set_fluid", "sib_set_structure",
     "sib_set_stiffness", "sib_set_options", "sib_set_eigen_estimates", "sib_get_eigen_estimates", "sib_setup",
-    "sib_solve", "sib_solve_host", "sib_solve_rhs", "sib_grad", "sib_num_levels", "sib_level_size",
+    "sib_solve", "sib_solve_host", "sib_solve_rhs", "sib_solve_transpose", "sib_grad", "sib_num_levels", "sib_level_size",
     "sib_apply_operator", "sib_cavity_apply_operator", "sib_cavity_smooth", "sib_apply_ib", "sib_smooth", "sib_residual_restrict", "sib_prolong_add",
     "sib_coarse_solve", "sib_vcycle", "sib_interp", "sib_spread", "sib_time_kernel", "sib_launch_count",
     "sib_device_bytes", "sib_spread_noalloc", "sib_advance_markers",
@@ -116,6 +116,7 @@ def load(build_if_missing: bool = True):
         "sib_solve": (I, [ctx, P, P, ctypes.POINTER(SibStats), P]),
         "sib_solve_host": (I, [ctx, P, P, ctypes.POINTER(SibStats), P]),
         "sib_solve_rhs": (I, [ctx, P, P, ctypes.POINTER(SibStats), P]),
+        "sib_solve_transpose": (I, [ctx, P, P, ctypes.POINTER(SibStats), P]),
         "sib_grad": (I, [ctx, P, P, P, P, P]),
         "sib_num_levels": (I, [ctx]),
         "sib_level_size": (I, [ctx, I]),
@@ -251,6 +252,15 @@ class Solver:
         if w is None:
             w = torch.empty_like(rhs)
         rc = self.lib.sib_solve_rhs(self.ctx, _ptr(rhs), _ptr(w), ctypes.byref(self.stats), _stream())
+        self._check(rc, (SIB_ERR_NOT_CONVERGED,) if allow_unconverged else ())
+        return w
+
+    def solve_transpose(self, rhs, w=None, allow_unconverged=False):
+        """Solves L^T w = rhs (the adjoint solve; L_IB is symmetric)."""
+        torch = _torch()
+        if w is None:
+            w = torch.empty_like(rhs)
+        rc = self.lib.sib_solve_transpose(self.ctx, _ptr(rhs), _ptr(w), ctypes.byref(self.stats), _stream())
         self._check(rc, (SIB_ERR_NOT_CONVERGED,) if allow_unconverged else ())
         return w
 

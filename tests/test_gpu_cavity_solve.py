@@ -1,7 +1,6 @@
 """GPU parity of the lid-driven cavity's solve (Sec. 5: no-slip walls, regularised lid; option
 domain = SIB_DOMAIN_CAVITY) against the cavity oracle: the walled transfers, the coarsest
-pseudo-inverse, one V-cycle, and FGMRES to 1e-8 with the annulus immersed.  Every test is skipped
-while the options reject the cavity domain.
+pseudo-inverse, one V-cycle, and FGMRES to 1e-8 with the annulus immersed.
 
 Tolerances as in test_gpu_parity: FP64 to 1e-10 relative (max norm); a whole FP32 V-cycle to 1e-4.
 """
@@ -16,26 +15,6 @@ from paper_1612_02208_gb300 import inputs as I  # noqa: E402
 from paper_1612_02208_gb300 import sib  # noqa: E402
 
 from tests.test_gpu_parity import TOL64, cu, host, rel  # noqa: E402
-
-_enabled = None
-
-
-def cavity_enabled():
-    global _enabled
-    if _enabled is None:
-        S = sib.solver_for(I.no_structure(32, seed=3))
-        try:
-            S.set_options(domain=sib.DOMAIN_CAVITY)
-            _enabled = True
-        except sib.SibError:
-            _enabled = False
-    return _enabled
-
-
-@pytest.fixture(autouse=True)
-def _needs_cavity():
-    if not cavity_enabled():
-        pytest.skip("the options do not accept the cavity domain")
 
 
 def make_case(N, rho, mu, gamma=5.0, wide=False, **opts):

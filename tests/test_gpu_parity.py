@@ -263,8 +263,10 @@ def test_gradients_match_oracle(add):
     n = prob.N ** 2
     adj_rhs = torch.zeros_like(w)
     adj_rhs[:2 * n] = 2.0 * (w[:2 * n] - cu(target[:2 * n]))
-    lam = S.solve_rhs(adj_rhs)
+    lam = S.solve_transpose(adj_rhs)
     dk, dX = S.grad(w, lam)
+    # the transposed solve is the forward solve of the symmetric L_IB: same iterate, bit for bit
+    assert torch.equal(lam, S.solve_rhs(adj_rhs))
     assert rel(host(w), w_ref) < TOL64
     assert rel(host(lam), lam_ref) < 1e-9
     assert rel(host(dk), dk_ref) < 1e-9, rel(host(dk), dk_ref)
@@ -484,8 +486,9 @@ def test_errors_are_reported_not_raised_from_cuda():
 
 
 def test_vanka_sweep_large_grid_against_oracle():
-    """One fine-level sweep at N = 512, where the FP32 path runs the persistent cp.async-pipelined
-    kernel and the FP64 path the tiled kernel; the oracle sweep is built for the finest level only."""
+    """One fine-level sweep at N = 512, where both precisions run the tiled sweep with its interior
+    tiles staged by TMA box copies (the tiles on the periodic wrap gather element by element); the
+    oracle sweep is built for the finest level only."""
     prob = I.thin_ellipse_re(512, kappa=1e4)
     S = sib.solver_for(prob)
     L = system.operator_of(prob)

@@ -1,8 +1,9 @@
 """GPU parity of the box RAS smoother on subdomains wider than six cells (Sec. 3.3 / Alg. 2 with the
 paper's 8 x 8 boxes and overlap 2, Sec. 5.1.1 and 5.2.1), against the CPU oracle: the global-memory
-set-up and the batched correction.  Every test is skipped while the options reject these shapes.
+set-up and the batched correction.
 
-Tolerances as in test_gpu_parity: FP64 to 1e-10 relative (max norm); FP32 to 1e-5 per sweep.
+Tolerances as in test_gpu_parity: FP64 to 1e-10 relative (max norm); FP32 to 1e-5 per sweep, except
+the stiff thin circle (TOL32_STIFF_CIRCLE below); a whole FP32 V-cycle to 1e-4.
 """
 import numpy as np
 import pytest
@@ -10,7 +11,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from oracle import krylov, multigrid, smoothers, system  # noqa: E402
+from oracle import krylov, multigrid, system  # noqa: E402
 from paper_1612_02208_gb300 import inputs as I  # noqa: E402
 from paper_1612_02208_gb300 import sib  # noqa: E402
 
@@ -23,27 +24,6 @@ PROBLEMS = {
     "fluid32": lambda: I.no_structure(32, seed=3),
     "circle32_g500": lambda: I.paper_problem("circle", 32, 500.0),
 }
-
-_enabled = None
-
-
-def wide_enabled():
-    global _enabled
-    if _enabled is None:
-        S = sib.solver_for(I.no_structure(32, seed=3))
-        try:
-            S.set_options(smoother=sib.SMOOTHER_RAS, box=8, box_overlap=2)
-            _enabled = True
-        except sib.SibError:
-            _enabled = False
-    return _enabled
-
-
-@pytest.fixture(autouse=True)
-def _needs_wide_boxes():
-    if not wide_enabled():
-        pytest.skip("the options do not accept subdomains wider than six cells")
-
 
 _cache = {}
 
@@ -58,35 +38,25 @@ def pair(name, b, o, **opts):
     return _cache[key]
 
 
-def fp32_tolerance(lev, x, b):
-    """TOL32, or the first-order bound that FP32 rounding sets on one sweep, whichever is larger.  The
-    residual r = b - L x is formed in FP32, so each of its entries carries an error of a few units of
-    2^-24 (|b| + |L| |x|); each owned value is then a sum of ne terms Inv_qr r_r, whose rounding (the
-    inverse's entry, the product, the sum) adds a few units of 2^-24 |Inv_qr| |r_r|.  Both pass
-    through |Inv|, so the sweep's error relative to its largest value is bounded by a few units of
-    2^-24 max_q (|Inv| (|r| + |b| + |L| |x|))_q / max |x_out|: on stiff problems the residual's own
-    cancellation dominates.  The sums of magnitudes already overstate random-sign rounding, so two
-    units are taken: on the oracle's inverses the bound is 9e-4 on the stiff circle's fine level,
-    where an FP32 transcription of the sweep errs by 5e-5, and within 2e-5 elsewhere."""
-    import scipy.linalg as sla
-    r = b - lev.L @ x
-    s = np.abs(r) + np.abs(b) + abs(lev.L) @ np.abs(x)
-    dx = np.zeros_like(x)
-    out = np.abs(smoothers.ras_sweep(lev.L, lev.boxes, lev.factors, x, b, 1.0)).max()
-    for (d, own), f in zip(lev.boxes, lev.factors):
-        inv_own = sla.lu_solve(f, np.eye(len(d)))[own]
-        dx[d[own]] = np.abs(inv_own) @ s[d]
-    return max(TOL32, 2.0 * 2.0 ** -24 * dx.max() / out)
+# FP32 bar of one sweep on the stiff thin circle (gamma = 500), where 1e-5 cannot hold in FP32: on the
+# CPU, with the oracle's operator and inverses, rounding only the operator's entries to FP32 already
+# moves the fine-level sweep by 1.2e-5 relative, rounding only the stored inverse by 1.9e-5, forming
+# only the residual in FP32 arithmetic by 7.4e-5 and accumulating only the box products in FP32 by
+# 9.6e-5 (the box solves amplify relative rounding: the stiff IB blocks make the subdomain operators
+# badly conditioned).  Measured on the GPU:
+# 1.3e-5 on level 1 and 2.9e-4 on the fine level.  The FP64 sweep (1e-10) is this case's parity path;
+# the FP32 sweep keeps a bound a little above its measured error, and the whole FP32 V-cycle, where
+# the sweeps' rounding is smoothed out, keeps the V-cycle bar.
+TOL32_STIFF_CIRCLE = 5e-4
 
 
 @pytest.mark.parametrize("name,b,o", [("ellipse32", 8, 2), ("ellipse64_re", 8, 2), ("disk32_stiff", 4, 2),
                                       ("fluid32", 8, 2), ("ellipse32", 2, 3), ("ellipse64_re", 4, 4),
                                       ("circle32_g500", 8, 2)])
 def test_wide_ras_sweep_every_level(name, b, o):
-    """One sweep per level, FP64 and FP32: the 16 x 16 level 1 holds 4 boxes (a partial tile of the
-    batched correction), the 64 x 64 fine level 64 boxes, with IB and IB-free boxes.  On the stiff
-    thin circle (gamma = 500) the FP32 inverse's rounding alone costs about 1e-4 relative on its IB
-    boxes (measured on the oracle's inverses), so the FP32 bound there comes from fp32_tolerance."""
+    """One sweep per level, FP64 to 1e-10 and FP32 to 1e-5: the 16 x 16 level 1 holds 4 boxes (a
+    partial tile of the batched correction), the 64 x 64 fine level 64 boxes, with IB and IB-free
+    boxes.  On the stiff thin circle (gamma = 500) the FP32 sweep is held to TOL32_STIFF_CIRCLE."""
     prob, H, S = pair(name, b, o)
     for l in range(1, len(H.levels)):
         lev = H.levels[l]
@@ -101,19 +71,17 @@ def test_wide_ras_sweep_every_level(name, b, o):
         ref32 = H.smooth(l, x32, b32, 1)
         y32 = cu(x32, torch.float32)
         S.smooth(l, y32, cu(b32, torch.float32), 1)
-        tol = fp32_tolerance(lev, x32, b32)
+        tol = TOL32_STIFF_CIRCLE if name == "circle32_g500" else TOL32
         assert rel(host(y32), ref32) < tol, (l, rel(host(y32), ref32), tol)
 
 
 @pytest.mark.parametrize("name", ["ellipse64_re", "circle32_g500"])
 def test_wide_ras_vcycle(name):
-    """One V-cycle in FP64; in FP32 too where the sweeps keep the 1e-5 bar (not the stiff circle)."""
+    """One V-cycle, FP64 to 1e-10 and FP32 to the V-cycle bar 1e-4 (the stiff circle included)."""
     prob, H, S = pair(name, 8, 2)
     b = system.rhs(prob)
     z = host(S.vcycle(cu(b)))
     assert rel(z, H.vcycle(b)) < TOL64, rel(z, H.vcycle(b))
-    if name == "circle32_g500":
-        return
     b32 = b.astype(np.float32).astype(np.float64)
     z32 = host(S.vcycle(cu(b32, torch.float32)))
     assert rel(z32, H.vcycle(b32)) < 1e-4, rel(z32, H.vcycle(b32))
