@@ -221,11 +221,16 @@ int sib_advance_markers(sib_ctx* ctx, const double* w, double* X_next, void* str
 #define SIB_KERNEL_RESTRICT  4   /* restriction of a residual from `level` to level-1                 */
 #define SIB_KERNEL_PROLONG   5   /* prolongation-correction from level-1 to `level`                   */
 #define SIB_KERNEL_RAS       6   /* box RAS correction from a residual (needs the RAS smoother's setup) */
+#define SIB_KERNEL_IB_WINDOW 7   /* the IB force [S K J]^l u through the level's assembled windows      */
+#define SIB_TIME_COLD     0x100  /* or-ed into `kernel`: no warm-up launch before the timed ones, so that
+                                    a caller who flushes L2 first (and times reps = 1) gets a cold launch */
 /* Times `reps` back-to-back launches of one kernel of the V-cycle on `level` (operands: the
  * level's own work buffers, zero-filled first) between two CUDA events recorded on `stream`,
  * and returns the mean device time of one launch (*ms) and the algorithmic DRAM bytes one
  * launch must move (*bytes: every operand word read once and every result word written once;
- * IB data counted only in IB-active tiles).  Synchronises `stream`.  Requires sib_setup. */
+ * IB data counted only in IB-active tiles; for SIB_KERNEL_IB_WINDOW the bytes of the IB operator
+ * applied through the markers, 15 words per marker and 2 words per face of a tile that a marker
+ * stencil touches).  Synchronises `stream`.  Requires sib_setup. */
 int sib_time_kernel(sib_ctx* ctx, int kernel, int level, int prec, int reps, void* stream, double* ms,
                     double* bytes);
 

@@ -285,6 +285,49 @@ void launch_tile_finish(unsigned char* flag, int ntx, int nty, int* tiles, int* 
     launch_pdl(k_tile_finish, 1, 1024, 0, s, flag, ntx, nty, tiles, nTiles);
 }
 
+// single block: the slots (indices into the active-tile list, ascending) of the active tiles whose
+// raw flag is set, and their count
+__global__ void k_row_slots(const unsigned char* __restrict__ flag, const int* __restrict__ tiles,
+                            const int* __restrict__ nTiles, int* __restrict__ rowSlots, int* __restrict__ nRow) {
+    pdl_entry();
+    __shared__ int warpSums[32];
+    __shared__ int carry;
+    const int nt = *nTiles;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int s0 = 0; s0 < nt; s0 += blockDim.x) {
+        const int sl = s0 + threadIdx.x;
+        const int f = (sl < nt && flag[tiles[sl]]) ? 1 : 0;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        int v = f;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane == 31) warpSums[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            int w = (lane < (int)(blockDim.x >> 5)) ? warpSums[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warpSums[lane] = w;
+        }
+        __syncthreads();
+        const int incl = v + (wid > 0 ? warpSums[wid - 1] : 0);
+        if (f) rowSlots[carry + incl - 1] = sl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *nRow = carry;
+}
+void launch_row_slots(const unsigned char* flag, const int* tiles, const int* nTiles, int* rowSlots, int* nRow,
+                      cudaStream_t s) {
+    launch_pdl(k_row_slots, 1, 1024, 0, s, flag, tiles, nTiles, rowSlots, nRow);
+}
+
 // ------------------------------------------------------------------------------------------
 // Spring adjacency (CSR, deterministic): each marker's incident springs ordered by edge id.
 __global__ void k_degree(const int* __restrict__ edges, int E, int* __restrict__ deg) {
@@ -447,13 +490,15 @@ __device__ __forceinline__ T gather_face(const IBK<T>& k, const T* __restrict__ 
     return acc;
 }
 
+// rowSlots != nullptr: block b takes the tile of slot rowSlots[b] (b < *nTiles, the count of that
+// list), the tiles that a marker stencil touches; otherwise tile b of the active-tile list.
 template <typename T>
 __global__ void __launch_bounds__(256) k_spread_thread(IBK<T> k, const T* __restrict__ F, T* __restrict__ f,
                                                        const int* __restrict__ tiles, const int* __restrict__ nTiles,
-                                                       int tx, int ty, int ntx) {
+                                                       const int* __restrict__ rowSlots, int tx, int ty, int ntx) {
     pdl_entry();
     if ((int)blockIdx.x >= *nTiles) return;
-    const int t = tiles[blockIdx.x];
+    const int t = tiles[rowSlots ? rowSlots[blockIdx.x] : blockIdx.x];
     const int i = (t % ntx) * tx + threadIdx.x, j = (t / ntx) * ty + threadIdx.y;
     const int n = k.N * k.N;
     for (int c = 0; c < 2; ++c) f[c * n + j * k.N + i] = k.inv_h2 * gather_face(k, F, c, i, j, 0, 1);
@@ -462,7 +507,7 @@ __global__ void __launch_bounds__(256) k_spread_thread(IBK<T> k, const T* __rest
 template <typename T>
 __global__ void __launch_bounds__(256) k_spread_warp(IBK<T> k, const T* __restrict__ F, T* __restrict__ f,
                                                      const int* __restrict__ tiles, const int* __restrict__ nTiles,
-                                                     int tx, int ty, int ntx) {
+                                                     const int* __restrict__ rowSlots, int tx, int ty, int ntx) {
     pdl_entry();
     if ((int)blockIdx.x >= *nTiles) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -470,22 +515,25 @@ __global__ void __launch_bounds__(256) k_spread_warp(IBK<T> k, const T* __restri
     const int per = tx * ty;
     if (face >= 2 * per) return;
     const int c = face / per, q = face % per;
-    const int t = tiles[blockIdx.x];
+    const int t = tiles[rowSlots ? rowSlots[blockIdx.x] : blockIdx.x];
     const int i = (t % ntx) * tx + q % tx, j = (t / ntx) * ty + q / tx;
     T acc = gather_face(k, F, c, i, j, lane, 32);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) f[c * k.N * k.N + j * k.N + i] = k.inv_h2 * acc;
 }
 
+// With rowSlots (nRow its count, maxTiles its host bound) only the tiles that a marker stencil touches
+// are written; the caller keeps f at zero on the other active tiles.
 template <typename T>
 void launch_spread(const IBK<T>& k, const T* F, T* f, const int* tiles, const int* nTiles, int maxTiles, int tx,
-                   int ty, int ntx, int warpPerFace, cudaStream_t s) {
+                   int ty, int ntx, int warpPerFace, cudaStream_t s, const int* rowSlots, const int* nRow) {
     if (maxTiles == 0) return;
+    const int* cnt = rowSlots ? nRow : nTiles;
     if (warpPerFace) {
         const int groups = (2 * tx * ty + 7) / 8;
-        launch_pdl(k_spread_warp<T>, dim3(maxTiles, groups), 256, 0, s, k, F, f, tiles, nTiles, tx, ty, ntx);
+        launch_pdl(k_spread_warp<T>, dim3(maxTiles, groups), 256, 0, s, k, F, f, tiles, cnt, rowSlots, tx, ty, ntx);
     } else {
-        launch_pdl(k_spread_thread<T>, maxTiles, dim3(tx, ty), 0, s, k, F, f, tiles, nTiles, tx, ty, ntx);
+        launch_pdl(k_spread_thread<T>, maxTiles, dim3(tx, ty), 0, s, k, F, f, tiles, cnt, rowSlots, tx, ty, ntx);
     }
 }
 
@@ -865,55 +913,91 @@ void launch_window_dense(const double* win, const int* tiles, int nTiles, int N,
 // Apply: f^c(face) = sum_o B(face, face + o) u^c(face + o) on the IB-active tiles.  A block
 // takes 32 consecutive faces of one tile and component; thread (x, oy) sums window row oy of face
 // x (nine terms), and the nine row sums are added in a fixed order.
+// One block per (listed tile, group of 32 FV-face vectors, component): warp oy takes window row oy
+// of every face of the group; each thread takes FV consecutive faces of one tile row (a 16-byte
+// vector of coefficients per window entry), so a warp reads 512 contiguous bytes per entry.  The
+// coefficients are set-up data, loaded before the dependency wait.
+template <typename T>
+struct WinVec;
+template <>
+struct WinVec<float> {
+    using type = float4;
+};
+template <>
+struct WinVec<double> {
+    using type = double2;
+};
 template <typename T>
 __global__ void __launch_bounds__(32 * WD) k_ib_window(const T* __restrict__ win, const int* __restrict__ tiles,
-                                                       const int* __restrict__ nTiles, int N, int tx, int ty, int ntx,
-                                                       const T* __restrict__ u, T* __restrict__ f) {
-    __shared__ T part[WD][32];
-    // the tile list and the window coefficients are set-up data: read before waiting for u
-    const int slot = blockIdx.x;
-    if (slot >= *nTiles) return;
+                                                       const int* __restrict__ rowSlots, const int* __restrict__ nRow,
+                                                       int N, int tx, int ty, int ntx, const T* __restrict__ u,
+                                                       T* __restrict__ f) {
+    constexpr int FV = 16 / (int)sizeof(T);   // faces per thread
+    using VT = typename WinVec<T>::type;
+    __shared__ __align__(16) T part[WD][32 * FV];
+    if ((int)blockIdx.x >= *nRow) return;
+    const int slot = rowSlots[blockIdx.x];
     const int per = tx * ty;
-    const int q = blockIdx.y * 32 + threadIdx.x;
+    const int q0 = (blockIdx.y * 32 + threadIdx.x) * FV;   // first face of the thread (tx is a multiple of FV)
     const int c = blockIdx.z;
     const int oy = (int)threadIdx.y - WR;
-    const bool live = q < per;
+    const bool live = q0 < per;
     const int t = tiles[slot];
-    const int i = (t % ntx) * tx + (live ? q % tx : 0), j = (t / ntx) * ty + (live ? q / tx : 0);
+    const int i0 = (t % ntx) * tx + (live ? q0 % tx : 0), j = (t / ntx) * ty + (live ? q0 / tx : 0);
     const int n = N * N, mk = N - 1;
-    T wv[WD];
+    VT wv[WD];
     if (live) {
-        const T* w = win + ((size_t)(slot * 2 + c) * WIN_SIZE + (size_t)threadIdx.y * WD) * per + q;
+        const T* w = win + ((size_t)(slot * 2 + c) * WIN_SIZE + (size_t)threadIdx.y * WD) * per + q0;
 #pragma unroll
-        for (int ox = 0; ox < WD; ++ox) wv[ox] = w[(size_t)ox * per];
+        for (int ox = 0; ox < WD; ++ox) wv[ox] = *reinterpret_cast<const VT*>(w + (size_t)ox * per);
     }
     pdl_entry();
-    T acc = T(0);
+    T acc[FV];
+#pragma unroll
+    for (int k = 0; k < FV; ++k) acc[k] = T(0);
     if (live) {
         const T* row = u + (size_t)c * n + (size_t)((j + oy) & mk) * N;
+        T ur[FV + 2 * WR];
 #pragma unroll
-        for (int ox = -WR; ox <= WR; ++ox) acc += wv[ox + WR] * row[(i + ox) & mk];
+        for (int k = 0; k < FV + 2 * WR; ++k) ur[k] = row[(i0 - WR + k) & mk];
+#pragma unroll
+        for (int ox = 0; ox < WD; ++ox) {
+            const T* wk = reinterpret_cast<const T*>(&wv[ox]);
+#pragma unroll
+            for (int k = 0; k < FV; ++k) acc[k] += wk[k] * ur[k + ox];
+        }
     }
-    part[threadIdx.y][threadIdx.x] = acc;
+#pragma unroll
+    for (int k = 0; k < FV; ++k) part[threadIdx.y][threadIdx.x * FV + k] = acc[k];
     __syncthreads();
     if (threadIdx.y == 0 && live) {
-        T sum = T(0);
+        VT out;
+        T* o = reinterpret_cast<T*>(&out);
 #pragma unroll
-        for (int r = 0; r < WD; ++r) sum += part[r][threadIdx.x];
-        f[(size_t)c * n + j * N + i] = sum;
+        for (int k = 0; k < FV; ++k) {
+            T sum = T(0);
+#pragma unroll
+            for (int r = 0; r < WD; ++r) sum += part[r][threadIdx.x * FV + k];
+            o[k] = sum;
+        }
+        *reinterpret_cast<VT*>(f + (size_t)c * n + (size_t)j * N + i0) = out;
     }
 }
+// Only the tiles a marker stencil touches have nonzero rows; the other active tiles keep the zero
+// IB force written at set-up.
 template <typename T>
-void launch_ib_window(const T* win, const int* tiles, const int* nTiles, int maxTiles, int N, int tx, int ty, int ntx,
-                      const T* u, T* f, cudaStream_t s) {
-    if (maxTiles == 0) return;
-    const int groups = (tx * ty + 31) / 32;
-    launch_pdl(k_ib_window<T>, dim3(maxTiles, groups, 2), dim3(32, WD), 0, s, win, tiles, nTiles, N, tx, ty, ntx, u, f);
+void launch_ib_window(const T* win, const int* tiles, const int* rowSlots, const int* nRow, int maxRow, int N, int tx,
+                      int ty, int ntx, const T* u, T* f, cudaStream_t s) {
+    if (maxRow == 0) return;
+    constexpr int FV = 16 / (int)sizeof(T);
+    const int groups = (tx * ty + 32 * FV - 1) / (32 * FV);
+    launch_pdl(k_ib_window<T>, dim3(maxRow, groups, 2), dim3(32, WD), 0, s, win, tiles, rowSlots, nRow, N, tx, ty, ntx,
+               u, f);
 }
-template void launch_ib_window<float>(const float*, const int*, const int*, int, int, int, int, int, const float*,
-                                      float*, cudaStream_t);
-template void launch_ib_window<double>(const double*, const int*, const int*, int, int, int, int, int, const double*,
-                                       double*, cudaStream_t);
+template void launch_ib_window<float>(const float*, const int*, const int*, const int*, int, int, int, int, int,
+                                      const float*, float*, cudaStream_t);
+template void launch_ib_window<double>(const double*, const int*, const int*, const int*, int, int, int, int, int,
+                                       const double*, double*, cudaStream_t);
 
 // ------------------------------------------------------------------------------------------
 // (M x 2) interleaved <-> component-major [x (M) | y (M)]
@@ -1043,7 +1127,7 @@ void launch_grad_X(const double* X, int M, int N, const double* w, const double*
     template void launch_interp<T>(const IBK<T>&, const T*, T*, cudaStream_t);                                  \
     template void launch_spring<T>(const int*, const int*, const T*, int, const T*, T*, cudaStream_t);           \
     template void launch_spread<T>(const IBK<T>&, const T*, T*, const int*, const int*, int, int, int, int, int, \
-                                   cudaStream_t);
+                                   cudaStream_t, const int*, const int*);
 SIB_IB_INST(float)
 SIB_IB_INST(double)
 

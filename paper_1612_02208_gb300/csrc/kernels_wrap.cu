@@ -249,10 +249,10 @@ __global__ void __launch_bounds__(WT) k_wscale(const T* __restrict__ w, const do
 // y = argmin || beta e1 - H y || for the (m + 1) x m Hessenberg matrix of the step (Givens
 // rotations, back substitution).  H(i, j) = hA[j][i] + hB[j][i] for i <= j (the two Gram-Schmidt
 // passes), H(j + 1, j) = sqrt(nr[j]); m stops at the first vanished subdiagonal entry.  y[m..k) = 0.
-__global__ void k_wlsq(const double* __restrict__ hA, const double* __restrict__ hB, const double* __restrict__ nr,
-                       const double* __restrict__ beta2, int k, double* __restrict__ y) {
-    pdl_entry();
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One thread.
+__device__ void wlsq_solve(const double* __restrict__ hA, const double* __restrict__ hB,
+                           const double* __restrict__ nr, const double* __restrict__ beta2, int k,
+                           double* __restrict__ y) {
     double H[WRAP_MAXK + 1][WRAP_MAXK];
     double g[WRAP_MAXK + 1];
     const double beta = sqrt(beta2[0]);
@@ -286,6 +286,108 @@ __global__ void k_wlsq(const double* __restrict__ hA, const double* __restrict__
     }
 }
 
+__global__ void k_wlsq(const double* __restrict__ hA, const double* __restrict__ hB, const double* __restrict__ nr,
+                       const double* __restrict__ beta2, int k, double* __restrict__ y) {
+    pdl_entry();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    wlsq_solve(hA, hB, nr, beta2, k, y);
+}
+
+// Levels small enough for one block (n <= WRAP_ONE_MAX): each reduction finishes in the block that
+// forms it, so no separate reduce kernel runs.  k_wnorm_one: beta2 = |r0|^2 and V0 = r0 / |r0|.
+template <typename T>
+__global__ void __launch_bounds__(WT) k_wnorm_one(const T* __restrict__ r0, int64_t n, double* __restrict__ beta2,
+                                                  T* __restrict__ V0) {
+    using VT = typename WVec<T>::type;
+    constexpr int VN = WVec<T>::n;
+    pdl_entry();
+    __shared__ T scale;
+    double acc[1] = {0.0};
+    const int64_t nv = n / VN;
+    for (int64_t e = threadIdx.x; e < nv; e += WT) {
+        const VT y = reinterpret_cast<const VT*>(r0)[e];
+        T s = T(0);
+#pragma unroll
+        for (int c = 0; c < VN; ++c) s = fma(wv<T>(y, c), wv<T>(y, c), s);
+        acc[0] += (double)s;
+    }
+    for (int64_t e = nv * VN + threadIdx.x; e < n; e += WT) acc[0] += (double)r0[e] * (double)r0[e];
+    block_partials<1>(acc, 1, beta2);
+    __syncthreads();
+    if (threadIdx.x == 0) scale = (T)(beta2[0] > 0.0 ? 1.0 / sqrt(beta2[0]) : 0.0);
+    __syncthreads();
+    const T sc = scale;
+    for (int64_t e = threadIdx.x; e < nv; e += WT) {
+        VT y = reinterpret_cast<const VT*>(r0)[e];
+#pragma unroll
+        for (int c = 0; c < VN; ++c) wset<T>(y, c, wv<T>(y, c) * sc);
+        reinterpret_cast<VT*>(V0)[e] = y;
+    }
+    for (int64_t e = nv * VN + threadIdx.x; e < n; e += WT) V0[e] = r0[e] * sc;
+}
+
+// One block: w -= sum_{i < cnt} coef[i] V_i and nr = |w|^2 (the second Gram-Schmidt pass and the
+// norm), then Vnext = w / sqrt(nr) (Vnext != nullptr) and, on the stage's last step (lsq_k > 0), the
+// least-squares solve of the stage into y.
+template <typename T, int KC>
+__global__ void __launch_bounds__(WT) k_wgs2_one(const T* __restrict__ V, int64_t ld, int cnt,
+                                                 const double* __restrict__ coef, T* w, int64_t n,
+                                                 double* __restrict__ nr, T* __restrict__ Vnext, int lsq_k,
+                                                 const double* __restrict__ hA, const double* __restrict__ hB,
+                                                 const double* __restrict__ nrAll, const double* __restrict__ beta2,
+                                                 double* __restrict__ y) {
+    using VT = typename WVec<T>::type;
+    constexpr int VN = WVec<T>::n;
+    pdl_entry();
+    __shared__ T scale;
+    T cf[KC];
+#pragma unroll
+    for (int i = 0; i < KC; ++i) cf[i] = i < cnt ? (T)coef[i] : T(0);
+    double acc[1] = {0.0};
+    const int64_t nv = n / VN;
+    for (int64_t e = threadIdx.x; e < nv; e += WT) {
+        VT yv = reinterpret_cast<const VT*>(w)[e];
+#pragma unroll
+        for (int i = 0; i < KC; ++i) {
+            if (i < cnt) {
+                const VT vi = reinterpret_cast<const VT*>(V + (int64_t)i * ld)[e];
+#pragma unroll
+                for (int c = 0; c < VN; ++c) wset<T>(yv, c, fma(-cf[i], wv<T>(vi, c), wv<T>(yv, c)));
+            }
+        }
+        reinterpret_cast<VT*>(w)[e] = yv;
+        T s = T(0);
+#pragma unroll
+        for (int c = 0; c < VN; ++c) s = fma(wv<T>(yv, c), wv<T>(yv, c), s);
+        acc[0] += (double)s;
+    }
+    for (int64_t e = nv * VN + threadIdx.x; e < n; e += WT) {
+        T yv = w[e];
+#pragma unroll
+        for (int i = 0; i < KC; ++i)
+            if (i < cnt) yv = fma(-cf[i], V[(int64_t)i * ld + e], yv);
+        w[e] = yv;
+        acc[0] += (double)yv * (double)yv;
+    }
+    block_partials<1>(acc, 1, nr);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        scale = (T)(nr[0] > 0.0 ? 1.0 / sqrt(nr[0]) : 0.0);
+        if (lsq_k > 0) wlsq_solve(hA, hB, nrAll, beta2, lsq_k, y);
+    }
+    __syncthreads();
+    if (Vnext) {
+        const T sc = scale;
+        for (int64_t e = threadIdx.x; e < nv; e += WT) {
+            VT yv = reinterpret_cast<const VT*>(w)[e];
+#pragma unroll
+            for (int c = 0; c < VN; ++c) wset<T>(yv, c, wv<T>(yv, c) * sc);
+            reinterpret_cast<VT*>(Vnext)[e] = yv;
+        }
+        for (int64_t e = nv * VN + threadIdx.x; e < n; e += WT) Vnext[e] = w[e] * sc;
+    }
+}
+
 }  // namespace
 
 // blocks of the inner-product and update kernels for n values: one 16-byte vector per thread and
@@ -314,19 +416,30 @@ int wrap_blocks(int64_t n) {
 
 template <typename T>
 int launch_wdots(const T* V, int64_t ld, int cnt, const T* w, int64_t n, double* partials, cudaStream_t s) {
-    const int nb = wrap_blocks<T>(n);
+    const int nb = n <= WRAP_ONE_MAX ? 1 : wrap_blocks<T>(n);
     SIB_WRAP_KC(cnt, launch_pdl(k_wdots<T, KC>, nb, WT, 0, s, V, ld, cnt, w, n, partials));
     return nb;
 }
 template <typename T>
 int launch_wgs(const T* V, int64_t ld, int cnt, const double* coef, const T* win, T* wout, int64_t n, int mode,
                double* partials, cudaStream_t s) {
-    const int nb = wrap_blocks<T>(n);
+    const int nb = n <= WRAP_ONE_MAX ? 1 : wrap_blocks<T>(n);
     if (mode == 1)
         SIB_WRAP_KC(cnt, launch_pdl(k_wgs<T, 1, KC>, nb, WT, 0, s, V, ld, cnt, coef, win, wout, n, partials));
     else
         SIB_WRAP_KC(cnt, launch_pdl(k_wgs<T, 2, KC>, nb, WT, 0, s, V, ld, cnt, coef, win, wout, n, partials));
     return nb;
+}
+template <typename T>
+void launch_wnorm_one(const T* r0, int64_t n, double* beta2, T* V0, cudaStream_t s) {
+    launch_pdl(k_wnorm_one<T>, 1, WT, 0, s, r0, n, beta2, V0);
+}
+template <typename T>
+void launch_wgs2_one(const T* V, int64_t ld, int cnt, const double* coef, T* w, int64_t n, double* nr, T* Vnext,
+                     int lsq_k, const double* hA, const double* hB, const double* nrAll, const double* beta2, double* y,
+                     cudaStream_t s) {
+    SIB_WRAP_KC(cnt, launch_pdl(k_wgs2_one<T, KC>, 1, WT, 0, s, V, ld, cnt, coef, w, n, nr, Vnext, lsq_k, hA, hB,
+                                nrAll, beta2, y));
 }
 void launch_wreduce(const double* partials, int cnt, int nblk, double* out, cudaStream_t s) {
     launch_pdl(k_wreduce, cnt, WT, 0, s, partials, nblk, out);
@@ -351,7 +464,11 @@ void launch_wlsq(const double* hA, const double* hB, const double* nr, const dou
                                cudaStream_t);                                                               \
     template void launch_wmaxpy<T>(const T*, int64_t, int, const double*, double, const T*, T*, int64_t,      \
                                    cudaStream_t);                                                           \
-    template void launch_wscale<T>(const T*, const double*, T*, int64_t, cudaStream_t);
+    template void launch_wscale<T>(const T*, const double*, T*, int64_t, cudaStream_t);                      \
+    template void launch_wnorm_one<T>(const T*, int64_t, double*, T*, cudaStream_t);                         \
+    template void launch_wgs2_one<T>(const T*, int64_t, int, const double*, T*, int64_t, double*, T*, int,   \
+                                     const double*, const double*, const double*, const double*, double*,     \
+                                     cudaStream_t);
 SIB_WRAP_INST(float)
 SIB_WRAP_INST(double)
 

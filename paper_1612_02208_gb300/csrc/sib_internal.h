@@ -230,6 +230,15 @@ template <typename T> int launch_wdots(const T* V, int64_t ld, int cnt, const T*
 template <typename T> int launch_wgs(const T* V, int64_t ld, int cnt, const double* coef, const T* win, T* wout,
                                      int64_t n, int mode, double* partials, cudaStream_t s);
 void launch_wreduce(const double* partials, int cnt, int nblk, double* out, cudaStream_t s);
+// Levels of at most WRAP_ONE_MAX values: one block forms each inner product completely (launch_wdots
+// and launch_wgs return nblk = 1 and write the sums themselves), the normalisations are fused
+// (launch_wnorm_one: beta2 = |r0|^2, V0 = r0 / |r0|; launch_wgs2_one: the second Gram-Schmidt pass,
+// the norm, the next Arnoldi vector and, with lsq_k > 0, the stage's least-squares solve).
+constexpr int64_t WRAP_ONE_MAX = 3 * 32 * 32;
+template <typename T> void launch_wnorm_one(const T* r0, int64_t n, double* beta2, T* V0, cudaStream_t s);
+template <typename T> void launch_wgs2_one(const T* V, int64_t ld, int cnt, const double* coef, T* w, int64_t n,
+                                           double* nr, T* Vnext, int lsq_k, const double* hA, const double* hB,
+                                           const double* nrAll, const double* beta2, double* y, cudaStream_t s);
 template <typename T> void launch_wmaxpy(const T* V, int64_t ld, int cnt, const double* coef, double sign, const T* yin,
                                          T* yout, int64_t n, cudaStream_t s);
 template <typename T> void launch_wscale(const T* w, const double* nrm2, T* v, int64_t n, cudaStream_t s);
@@ -246,14 +255,19 @@ void launch_bins(const uint32_t* mkey, int M, int nbins, int shift, int* binStar
 void launch_tile_flags(const int* base, int M, int W, int N, int tx, int ty, int ntx, unsigned char* flag,
                        cudaStream_t s);
 void launch_tile_finish(unsigned char* flag, int ntx, int nty, int* tiles, int* nTiles, cudaStream_t s);
+// slots of the active tiles whose raw flag is set (the rows of the IB operator are zero elsewhere)
+void launch_row_slots(const unsigned char* flag, const int* tiles, const int* nTiles, int* rowSlots, int* nRow,
+                      cudaStream_t s);
 void launch_adjacency(const int* edges, int E, int M, int* deg, int* start, int* nbr, int* eid,
                       cudaStream_t s);
 template <typename T> void launch_adj_kappa(const int* eid, const double* kappa, int n2E, T* kap, cudaStream_t s);
 template <typename T> void launch_interp(const IBK<T>& k, const T* u, T* U, cudaStream_t s);
 template <typename T> void launch_spring(const int* start, const int* nbr, const T* kap, int M, const T* U, T* F,
                                          cudaStream_t s);
+// rowSlots != nullptr: only the tiles of that slot list (count *nRow, at most maxTiles) are written
 template <typename T> void launch_spread(const IBK<T>& k, const T* F, T* f, const int* tiles, const int* nTiles,
-                                         int maxTiles, int tx, int ty, int ntx, int warpPerFace, cudaStream_t s);
+                                         int maxTiles, int tx, int ty, int ntx, int warpPerFace, cudaStream_t s,
+                                         const int* rowSlots = nullptr, const int* nRow = nullptr);
 void launch_patch_entries(const int* edges, const double* kappa, int E, const int* base0, const int* base1,
                           const double* w0, const double* w1, int M, int N, int W, double inv_h2,
                           double* ibd, cudaStream_t s);
@@ -271,9 +285,10 @@ void launch_window_patch(const double* win, const int* tiles, int nTiles, int N,
                          cudaStream_t s);
 void launch_window_dense(const double* win, const int* tiles, int nTiles, int N, int tx, int ty, int ntx, double* B,
                          cudaStream_t s);
+// f = [S K J]^l u through the windows, on the tiles listed by rowSlots (at most maxRow of them)
 template <typename T>
-void launch_ib_window(const T* win, const int* tiles, const int* nTiles, int maxTiles, int N, int tx, int ty, int ntx,
-                      const T* u, T* f, cudaStream_t s);
+void launch_ib_window(const T* win, const int* tiles, const int* rowSlots, const int* nRow, int maxRow, int N, int tx,
+                      int ty, int ntx, const T* u, T* f, cudaStream_t s);
 void launch_deinterleave(const double* in, int M, double* out, cudaStream_t s);
 void launch_interleave(const double* in, int M, double* out, cudaStream_t s);
 void launch_advance_markers(const double* X, const double* U, int M, double dt, double* Xn, cudaStream_t s);

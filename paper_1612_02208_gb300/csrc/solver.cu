@@ -65,6 +65,11 @@ struct Level {
     int* tiles = nullptr;
     int* nTiles = nullptr;
     int hnTiles = 0;
+    // slots of the tiles that a marker stencil touches (the raw flag): the rows of the IB operator
+    // vanish on the other active tiles (those added by the dilation), whose IB force stays 0
+    int* rowSlots = nullptr;
+    int* nRowTiles = nullptr;
+    int hnRowTiles = 0;
     int spreadWarp = 0;
     LevelBuf p[2];                       // [0] FP64, [1] FP32
     double lamA = 0, lamM = 0;
@@ -287,8 +292,8 @@ void ib_apply(sib_ctx* c, int l, const T* u, cudaStream_t s) {
     Level& lv = c->L[l];
     const int pi = Prec<T>::id;
     if (lv.applyWindow) {
-        KL(c, launch_ib_window<T>((const T*)lv.win[pi], lv.tiles, lv.nTiles, lv.hnTiles, lv.N, lv.tx, lv.ty, lv.ntx, u,
-                                  (T*)lv.p[pi].fib, s));
+        KL(c, launch_ib_window<T>((const T*)lv.win[pi], lv.tiles, lv.rowSlots, lv.nRowTiles, lv.hnRowTiles, lv.N, lv.tx,
+                                  lv.ty, lv.ntx, u, (T*)lv.p[pi].fib, s));
         return;
     }
     IBK<T> k = ibk<T>(c, l);
@@ -296,8 +301,8 @@ void ib_apply(sib_ctx* c, int l, const T* u, cudaStream_t s) {
     T* F = (T*)c->F[pi];
     KL(c, launch_interp<T>(k, u, U, s));
     KL(c, launch_spring<T>(c->adjStart, c->adjNbr, kapp<T>(c), c->M, U, F, s));
-    KL(c, launch_spread<T>(k, F, (T*)lv.p[pi].fib, lv.tiles, lv.nTiles, lv.hnTiles, lv.tx, lv.ty, lv.ntx,
-                           lv.spreadWarp, s));
+    KL(c, launch_spread<T>(k, F, (T*)lv.p[pi].fib, lv.tiles, lv.nTiles, lv.hnRowTiles, lv.tx, lv.ty, lv.ntx,
+                           lv.spreadWarp, s, lv.rowSlots, lv.nRowTiles));
 }
 
 template <typename T>
@@ -601,7 +606,13 @@ void wrapped_smooth(sib_ctx* c, int l, const T* x, const T* b, T* xo, int k, cud
     double* beta2 = nr + WRAP_MAXK;
     double* y = beta2 + 1;
     double* part = y + WRAP_MAXK;
+    // small levels: one block forms every inner product and norm, without a reduce kernel
+    const bool one = n3 <= WRAP_ONE_MAX;
     auto dots = [&](const T* Vs, int cnt, const T* v, double* out) {
+        if (one) {
+            KL(c, launch_wdots<T>(Vs, n3, cnt, v, n3, out, s));
+            return;
+        }
         const int nb = launch_wdots<T>(Vs, n3, cnt, v, n3, part, s);
         KL(c, launch_wreduce(part, cnt, nb, out, s));
         ++c->launches;
@@ -611,8 +622,12 @@ void wrapped_smooth(sib_ctx* c, int l, const T* x, const T* b, T* xo, int k, cud
         apply_operator<T>(c, l, x, b, w, s);   // r = b - L x
         r0 = w;
     }
-    dots(r0, 1, r0, beta2);
-    KL(c, launch_wscale<T>(r0, beta2, V, n3, s));
+    if (one) {
+        KL(c, launch_wnorm_one<T>(r0, n3, beta2, V, s));
+    } else {
+        dots(r0, 1, r0, beta2);
+        KL(c, launch_wscale<T>(r0, beta2, V, n3, s));
+    }
     GridK<T> g = gridk<T>(c, l);
     g.omega = T(1);   // the basic smoother undamped
     for (int j = 0; j < k; ++j) {
@@ -628,6 +643,13 @@ void wrapped_smooth(sib_ctx* c, int l, const T* x, const T* b, T* xo, int k, cud
         KL(c, launch_residual<T>(gridk<T>(c, l), Zj, nullptr, w, s));   // w = L z_j
         // CGS2: h = V^T w; w -= V h and h' = V^T w in one pass; w -= V h' and |w|^2 in one pass
         dots(V, j + 1, w, hA + j * K1);
+        if (one) {
+            KL(c, launch_wgs<T>(V, n3, j + 1, hA + j * K1, w, w, n3, 1, hB + j * K1, s));
+            KL(c, launch_wgs2_one<T>(V, n3, j + 1, hB + j * K1, w, n3, nr + j,
+                                     j + 1 < k ? V + (size_t)(j + 1) * n3 : nullptr, j + 1 < k ? 0 : k, hA, hB, nr,
+                                     beta2, y, s));
+            continue;
+        }
         int nb = launch_wgs<T>(V, n3, j + 1, hA + j * K1, w, w, n3, 1, part, s);
         KL(c, launch_wreduce(part, j + 1, nb, hB + j * K1, s));
         nb = launch_wgs<T>(V, n3, j + 1, hB + j * K1, w, w, n3, 2, part, s);
@@ -635,7 +657,7 @@ void wrapped_smooth(sib_ctx* c, int l, const T* x, const T* b, T* xo, int k, cud
         c->launches += 2;
         if (j + 1 < k) KL(c, launch_wscale<T>(w, nr + j, V + (size_t)(j + 1) * n3, n3, s));
     }
-    KL(c, launch_wlsq(hA, hB, nr, beta2, k, y, s));
+    if (!one) KL(c, launch_wlsq(hA, hB, nr, beta2, k, y, s));
     KL(c, launch_wmaxpy<T>(Z, n3, k, y, 1.0, x, xo, n3, s));
 }
 
@@ -772,6 +794,8 @@ void alloc_level_bufs(sib_ctx* c) {
         lv.tiles = (int*)dalloc(c, sizeof(int) * (size_t)lv.ntiles);
         lv.slotOf = (int*)dalloc(c, sizeof(int) * (size_t)lv.ntiles);
         lv.nTiles = (int*)dalloc(c, sizeof(int));
+        lv.rowSlots = (int*)dalloc(c, sizeof(int) * (size_t)lv.ntiles);
+        lv.nRowTiles = (int*)dalloc(c, sizeof(int));
         lv.binStart[0] = (int*)dalloc(c, sizeof(int) * (n + 1));
         lv.binStart[1] = (int*)dalloc(c, sizeof(int) * (n + 1));
     }
@@ -1045,15 +1069,19 @@ void setup(sib_ctx* c, cudaStream_t s) {
                     KL(c, launch_tile_flags(lv.base[q], c->M, lv.W, lv.N, lv.tx, lv.ty, lv.ntx, lv.tileFlag, s));
             KL(c, launch_tile_finish(lv.tileFlag, lv.ntx, lv.nty, lv.tiles, lv.nTiles, s));
             KL(c, launch_slot_map(lv.tiles, lv.nTiles, lv.ntiles, lv.slotOf, s));
+            KL(c, launch_row_slots(lv.tileFlag, lv.tiles, lv.nTiles, lv.rowSlots, lv.nRowTiles, s));
         }
         launch_adjacency(c->edges, c->E, c->M, c->deg, c->adjStart, c->adjNbr, c->adjEid, s);
-        std::vector<int> cnt(c->lmax + 1);
-        for (int l = 0; l <= c->lmax; ++l)
-            CK(cudaMemcpyAsync(&cnt[l], c->L[l].nTiles, sizeof(int), cudaMemcpyDeviceToHost, s));
+        std::vector<int> cnt(2 * (c->lmax + 1));
+        for (int l = 0; l <= c->lmax; ++l) {
+            CK(cudaMemcpyAsync(&cnt[2 * l], c->L[l].nTiles, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(&cnt[2 * l + 1], c->L[l].nRowTiles, sizeof(int), cudaMemcpyDeviceToHost, s));
+        }
         CK(cudaStreamSynchronize(s));
         for (int l = 0; l <= c->lmax; ++l) {
             Level& lv = c->L[l];
-            lv.hnTiles = cnt[l];
+            lv.hnTiles = cnt[2 * l];
+            lv.hnRowTiles = cnt[2 * l + 1];
             if (lv.hnTiles > lv.winSlots || !lv.win[0]) {
                 dfree(c, lv.win[0]);
                 dfree(c, lv.win[1]);
@@ -1599,7 +1627,7 @@ void smooth_impl(sib_ctx* c, int l, T* x, const T* b, int sweeps, cudaStream_t s
 }
 
 template <typename T>
-void time_kernel(sib_ctx* c, int kernel, int l, int reps, cudaStream_t s, double* ms, double* bytes) {
+void time_kernel(sib_ctx* c, int kernel, int l, int reps, bool cold, cudaStream_t s, double* ms, double* bytes) {
     Level& lv = c->L[l];
     const int pi = Prec<T>::id;
     LevelBuf& b = lv.p[pi];
@@ -1639,6 +1667,10 @@ void time_kernel(sib_ctx* c, int kernel, int l, int reps, cudaStream_t s, double
                 launch_ras_apply<T>(lv.N, c->opts.box, c->opts.box_overlap, lv.rasSlot, lv.rasList, lv.rasNIB,
                                     (const T*)lv.rasInv[pi], (T)1, (const T*)b.r, (const T*)b.x, (T*)b.xt, s);
                 break;
+            case SIB_KERNEL_IB_WINDOW:
+                launch_ib_window<T>((const T*)lv.win[pi], lv.tiles, lv.rowSlots, lv.nRowTiles, lv.hnRowTiles, lv.N,
+                                    lv.tx, lv.ty, lv.ntx, (const T*)b.x, (T*)b.fib, s);
+                break;
             default:
                 throw SibError(SIB_ERR_ARG, "unknown kernel id");
         }
@@ -1665,10 +1697,13 @@ void time_kernel(sib_ctx* c, int kernel, int l, int reps, cudaStream_t s, double
         case SIB_KERNEL_RAS:   // r and x read, xo written (the shared inverse stays on chip)
             by = 9.0 * n * w;
             break;
+        case SIB_KERNEL_IB_WINDOW:   // the marker form's words: 15 per marker, 2 per stencil-touched face
+            by = (15.0 * c->M + 2.0 * 2.0 * lv.hnRowTiles * lv.tx * lv.ty) * w;
+            break;
         default:
             throw SibError(SIB_ERR_ARG, "unknown kernel id");
     }
-    launch();   // warm-up
+    if (!cold) launch();   // warm-up
     CK(cudaEventRecord(c->ev0, s));
     for (int r = 0; r < reps; ++r) launch();
     CK(cudaEventRecord(c->ev1, s));
@@ -2273,6 +2308,8 @@ int sib_spread(sib_ctx* c, const double* F, double* f, void* stream) {
 
 int sib_time_kernel(sib_ctx* c, int kernel, int l, int prec, int reps, void* stream, double* ms, double* bytes) {
     API_BEGIN(c)
+    const bool cold = (kernel & SIB_TIME_COLD) != 0;
+    kernel &= ~SIB_TIME_COLD;
     require_setup(c);
     check_level(c, l, 0);
     if (!valid_prec(prec) || reps < 1 || !ms || !bytes) throw SibError(SIB_ERR_ARG, "bad argument");
@@ -2281,12 +2318,14 @@ int sib_time_kernel(sib_ctx* c, int kernel, int l, int prec, int reps, void* str
         throw SibError(SIB_ERR_ARG, "kernel needs level >= 1");
     if (kernel == SIB_KERNEL_RAS && c->opts.smoother != SIB_SMOOTHER_RAS)
         throw SibError(SIB_ERR_STATE, "the RAS kernel needs the RAS smoother set up");
-    if ((kernel == SIB_KERNEL_SPREAD || kernel == SIB_KERNEL_INTERP) && !c->haveIB)
+    if ((kernel == SIB_KERNEL_SPREAD || kernel == SIB_KERNEL_INTERP || kernel == SIB_KERNEL_IB_WINDOW) && !c->haveIB)
         throw SibError(SIB_ERR_ARG, "no immersed structure");
+    if (kernel == SIB_KERNEL_IB_WINDOW && !c->L[l].useWindow)
+        throw SibError(SIB_ERR_STATE, "the level has no assembled IB windows");
     if (prec == SIB_PREC_FP64)
-        time_kernel<double>(c, kernel, l, reps, S(stream), ms, bytes);
+        time_kernel<double>(c, kernel, l, reps, cold, S(stream), ms, bytes);
     else
-        time_kernel<float>(c, kernel, l, reps, S(stream), ms, bytes);
+        time_kernel<float>(c, kernel, l, reps, cold, S(stream), ms, bytes);
     return SIB_OK;
     API_END(c)
 }

@@ -45,7 +45,8 @@ EXPORTS = [
     "sib_coarse_solve", "sib_vcycle", "sib_interp", "sib_spread", "sib_time_kernel", "sib_launch_count",
     "sib_device_bytes", "sib_spread_noalloc", "sib_advance_markers",
 ]
-KERNELS = {"vanka": 0, "residual": 1, "spread": 2, "interp": 3, "restrict": 4, "prolong": 5, "ras": 6}
+TIME_COLD = 0x100
+KERNELS = {"vanka": 0, "residual": 1, "spread": 2, "interp": 3, "restrict": 4, "prolong": 5, "ras": 6, "ib_window": 7}
 
 
 class SibOpts(ctypes.Structure):
@@ -365,11 +366,13 @@ class Solver:
         self._check(self.lib.sib_spread(self.ctx, _ptr(F) if self.M else None, _ptr(f), _stream()))
         return f
 
-    def time_kernel(self, kernel: str, level: int, fp32: bool, reps: int = 20):
-        """(mean ms per launch, algorithmic bytes per launch) of one V-cycle kernel, CUDA events."""
+    def time_kernel(self, kernel: str, level: int, fp32: bool, reps: int = 20, cold: bool = False):
+        """(mean ms per launch, algorithmic bytes per launch) of one V-cycle kernel, CUDA events.
+        cold: no warm-up launch (the caller flushes L2 before the call and times reps = 1)."""
         ms = ctypes.c_double()
         by = ctypes.c_double()
-        self._check(self.lib.sib_time_kernel(self.ctx, KERNELS[kernel], int(level), PREC_FP32 if fp32 else PREC_FP64,
+        kid = KERNELS[kernel] | (TIME_COLD if cold else 0)
+        self._check(self.lib.sib_time_kernel(self.ctx, kid, int(level), PREC_FP32 if fp32 else PREC_FP64,
                                              int(reps), _stream(), ctypes.byref(ms), ctypes.byref(by)))
         return ms.value, by.value
 

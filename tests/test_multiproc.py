@@ -28,7 +28,7 @@ def _worker(rank, world, port, out):
     mx = bench.dist_max(my_ms)
     tot = bench.dist_sum(8.0)
     bench.dist_barrier()
-    out[rank] = (mx, tot, bench.job_ms_per_solve(mx, 8 * 5, w))
+    out[rank] = (mx, tot, bench.job_ms_per_unit(mx, 8 * 5, w))
     dist.destroy_process_group()
 
 
