@@ -57,7 +57,11 @@ HEAD_ITERATIONS = (38, 38)
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
 BREADTH_FILE = os.path.join(ROOT, "profiles", "oracle_cpu_baseline_configs0-3.md")
 CSRC = os.path.join(ROOT, "paper_1612_02208_gb300", "csrc")
-KERNEL_SOURCES = {"k_ib_window_f32": "kernels_ib.cu", "k_vanka_f32": "kernels_grid.cu"}
+# the source text of each roofline kernel: file, first and last marker (the kernel and its launcher)
+KERNEL_SOURCES = {
+    "k_ib_window_f32": ("kernels_ib.cu", "struct WinVec;", "template void launch_ib_window<float>"),
+    "k_vanka_f32": ("kernels_grid.cu", "k_vanka_tiled(GridK<T> g", "void launch_vanka("),
+}
 
 
 def parse_args(argv=None):
@@ -80,7 +84,8 @@ def parse_args(argv=None):
                         "'solve', so that ncu lists the Krylov kernels that the device graph otherwise hides")
     p.add_argument("--cpu-breadth", action="store_true",
                    help="time the oracle on configurations 0-3 (direct and FGMRES, 1 thread and all threads) "
-                        "and write the table under profiles/")
+                        "and write the table (--breadth-out, default under profiles/)")
+    p.add_argument("--breadth-out", default=BREADTH_FILE, help="where --cpu-breadth writes its table")
     return p.parse_args(argv)
 
 
@@ -190,8 +195,12 @@ def measured_peaks():
 
 
 def source_hash(kernel: str):
-    """Hash of the source file that holds the kernel (a recorded capture is valid only on that source)."""
-    return hashlib.sha256(open(os.path.join(CSRC, KERNEL_SOURCES[kernel]), "rb").read()).hexdigest()[:12]
+    """Hash of the kernel's source text (its definition and launcher): a recorded capture is valid only
+    while that text is unchanged."""
+    fname, first, last = KERNEL_SOURCES[kernel]
+    text = open(os.path.join(CSRC, fname)).read()
+    i = text.index(first)
+    return hashlib.sha256(text[i:text.index(last, i)].encode()).hexdigest()[:12]
 
 
 def recorded_traffic(kernel: str, workload: str):
@@ -941,9 +950,9 @@ def _breadth_case(name):
     return out
 
 
-def run_cpu_breadth():
+def run_cpu_breadth(out=BREADTH_FILE):
     """Times the oracle on configurations 0-3 with one thread and with every thread (each case in a
-    fresh process), and writes the table under profiles/."""
+    fresh process), and writes the table (by default under profiles/)."""
     cases = ["config0_ellipse32_vanka", "config1_disk128_kappa1e2_vanka", "config1_disk128_kappa1e2_sc",
              "config3_ellipse256_loguniform_vanka", "config2_ellipse512_re_kappa1e2_vanka"]
     rows = []
@@ -958,21 +967,27 @@ def run_cpu_breadth():
             rec["threads"] = threads
             rows.append(rec)
             print(json.dumps(rec), flush=True)
-    d = {"nproc": os.cpu_count(), "cpu_model": cpu_model(), "rtol": 1e-8,
+    write_breadth(rows, os.cpu_count(), cpu_model(), out)
+
+
+def write_breadth(rows, nproc, model, path):
+    """The breadth table (markdown, with a machine-readable JSON line that bench.py reads back)."""
+    d = {"nproc": nproc, "cpu_model": model, "rtol": 1e-8,
          "note": "oracle (numpy/scipy FP64) on the host cores; direct = sparse LU of the bordered operator "
                  "(skipped at 512^2 and for SC, where it repeats another row); FGMRES = the oracle's FGMRES "
                  "with its V-cycle; setup = operator and hierarchy", "rows": rows}
     lines = ["# Oracle CPU baseline on configurations 0-3", "",
-             "Command: `python bench.py --cpu-breadth` (run on the GPU box's host cores).", "",
+             "Command: `python bench.py --cpu-breadth` (run on the GPU box's host cores; each case in a fresh "
+             "process, one thread = OMP/OpenBLAS/MKL limited to 1).", "",
              f"Host: {d['nproc']} cores, {d['cpu_model']}.", "",
              "| case | threads | set-up s | FGMRES s | iterations | direct s |", "|---|---|---:|---:|---:|---:|"]
     for r in rows:
         lines.append(f"| {r['case']} | {r['threads']} | {r.get('setup_s')} | {r.get('fgmres_s')} | "
                      f"{r.get('iterations')} | {r.get('direct_s')} |")
     lines += ["", "Machine-readable copy (read by bench.py into `cpu_baseline.breadth`):", "", json.dumps(d), ""]
-    os.makedirs(os.path.dirname(BREADTH_FILE), exist_ok=True)
-    open(BREADTH_FILE, "w").write("\n".join(lines))
-    print(f"wrote {BREADTH_FILE}")
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    open(path, "w").write("\n".join(lines))
+    print(f"wrote {path}")
 
 
 # ------------------------------------------------------------------------------------ reference arm
@@ -1086,7 +1101,7 @@ def main(argv=None):
     elif args.profile_solve:
         run_profile_solve()
     elif args.cpu_breadth:
-        run_cpu_breadth()
+        run_cpu_breadth(args.breadth_out)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -472,9 +472,166 @@ __global__ void k_residual_restrict(GridK<T> g, const T* __restrict__ x, const T
     if (I >= Nc || J >= Nc) return;
     residual_restrict_cell(g, x, b, bc, I, J);
 }
+// The same residual and restriction for N >= 64, tiled: one block per 32 x 8 coarse cells (64 x 16
+// fine cells).  The block stages x (three components, fine rows fj0-2 .. fj0+17), b and the IB force
+// (rows fj0-1 .. fj0+16), all over columns fi0-4 .. fi0+67, in shared memory, forms each fine residual
+// the restriction needs once (u faces on columns fi0-1 .. fi0+64, v faces on rows fj0-1 .. fj0+15,
+// every cell) with the arithmetic of res_u / res_v / res_p, then restricts as residual_restrict_cell
+// does.  Blocks whose staged rows and columns lie inside the grid load 16-byte vectors, every load
+// issued before the first shared store; the others (the periodic wrap) gather element by element.  The
+// IB force is read where one of the tile's four fine tiles is IB-active: their flags are dilated by
+// one tile and cover the one-cell halo, and the force is zero on inactive tiles.
+constexpr int RR_CX = 32, RR_CY = 8;                 // coarse cells per block
+constexpr int RR_FX = 2 * RR_CX, RR_FY = 2 * RR_CY;  // fine cells per block
+constexpr int RR_W = RR_FX + 8;                      // staged row width (columns fi0-4 .. fi0+67)
+constexpr int RR_XH = RR_FY + 4, RR_BH = RR_FY + 2;  // staged rows of x (fj0-2 ..) and of b, f (fj0-1 ..)
+constexpr int RR_RU = RR_FX + 2;                     // u residuals per row (columns fi0-1 .. fi0+64)
+constexpr int RR_WORDS = (3 * RR_XH + 3 * RR_BH + 2 * RR_BH) * RR_W + RR_FY * RR_RU + (RR_FY + 1) * RR_FX +
+                         RR_FY * RR_FX;
+template <typename T>
+struct RRVec;
+template <>
+struct RRVec<float> {
+    using type = float4;
+};
+template <>
+struct RRVec<double> {
+    using type = double2;
+};
+template <typename T>
+__global__ void __launch_bounds__(RR_CX * RR_CY) k_residual_restrict_tiled(GridK<T> g, const T* __restrict__ x,
+                                                                           const T* __restrict__ b,
+                                                                           T* __restrict__ bc) {
+    using VT = typename RRVec<T>::type;
+    constexpr int VN = 16 / (int)sizeof(T);
+    constexpr int RV = RR_W / VN;                             // vectors per staged row
+    constexpr int NROWS = 3 * RR_XH + 3 * RR_BH + 2 * RR_BH;  // staged rows: x, b, f
+    constexpr int NT = RR_CX * RR_CY;
+    constexpr int PER = (NROWS * RV + NT - 1) / NT;            // vectors per thread
+    extern __shared__ __align__(16) unsigned char rr_smem[];
+    T* st = reinterpret_cast<T*>(rr_smem);   // NROWS x RR_W: x (3 x RR_XH rows), b (3 x RR_BH), f (2 x RR_BH)
+    T* sx = st;
+    T* sb = st + 3 * RR_XH * RR_W;
+    T* sf = sb + 3 * RR_BH * RR_W;
+    T* ru = st + NROWS * RR_W;               // [RR_FY][RR_RU]
+    T* rv = ru + RR_FY * RR_RU;              // [RR_FY + 1][RR_FX]
+    T* rp = rv + (RR_FY + 1) * RR_FX;        // [RR_FY][RR_FX]
+    const int N = g.N, n = N * N, m = N - 1, Nc = N / 2;
+    const int tid = threadIdx.y * RR_CX + threadIdx.x;
+    const int fi0 = blockIdx.x * RR_FX, fj0 = blockIdx.y * RR_FY;
+    // IB flags of the four fine tiles (set-up data, read before the dependency wait)
+    bool act = false;
+    if (g.tile) {
+        const int ti = fi0 >> g.lgtx, tj = fj0 >> g.lgty;
+        act = g.tile[tj * g.ntx + ti] || g.tile[tj * g.ntx + ti + 1] || g.tile[(tj + 1) * g.ntx + ti] ||
+              g.tile[(tj + 1) * g.ntx + ti + 1];
+    }
+    const int rows = act ? NROWS : 3 * RR_XH + 3 * RR_BH;
+    // staged row r: source array, component and grid row
+    auto src_row = [&](int r, const T*& base, int& gj) {
+        if (r < 3 * RR_XH) {
+            const int comp = r / RR_XH;
+            base = x + (size_t)comp * n;
+            gj = fj0 - 2 + (r - comp * RR_XH);
+        } else if (r < 3 * RR_XH + 3 * RR_BH) {
+            const int rr = r - 3 * RR_XH, comp = rr / RR_BH;
+            base = b + (size_t)comp * n;
+            gj = fj0 - 1 + (rr - comp * RR_BH);
+        } else {
+            const int rr = r - 3 * RR_XH - 3 * RR_BH, comp = rr / RR_BH;
+            base = g.fib + (size_t)comp * n;
+            gj = fj0 - 1 + (rr - comp * RR_BH);
+        }
+    };
+    pdl_entry();
+    const bool interior = fi0 >= 4 && fi0 + RR_FX + 4 <= N && fj0 >= 2 && fj0 + RR_FY + 2 <= N;
+    if (interior) {
+        VT v[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {   // every load issued before the first store
+            const int q = tid + k * NT;
+            if (q < rows * RV) {
+                const int r = q / RV, cv = q - r * RV;
+                const T* base;
+                int gj;
+                src_row(r, base, gj);
+                v[k] = *reinterpret_cast<const VT*>(base + (size_t)gj * N + fi0 - 4 + cv * VN);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int q = tid + k * NT;
+            if (q < rows * RV) reinterpret_cast<VT*>(st)[q] = v[k];
+        }
+    } else {
+        for (int q = tid; q < rows * RR_W; q += NT) {
+            const int r = q / RR_W, cc = q - r * RR_W;
+            const T* base;
+            int gj;
+            src_row(r, base, gj);
+            st[q] = base[(size_t)(gj & m) * N + ((fi0 - 4 + cc) & m)];
+        }
+    }
+    __syncthreads();
+    const T* U = sx;
+    const T* V = sx + RR_XH * RR_W;
+    const T* P = sx + 2 * RR_XH * RR_W;
+    auto X = [](const T* a, int xi, int xj) { return a[xj * RR_W + xi]; };
+    // u residuals at fine (fi0 - 1 + a, fj0 + r): staged column a + 3; x row r + 2, b and f row r + 1
+    for (int q = tid; q < RR_FY * RR_RU; q += NT) {
+        const int r = q / RR_RU, a = q - r * RR_RU;
+        const int xi = a + 3, xj = r + 2;
+        T Au = g.a0 * X(U, xi, xj) - g.c * ((X(U, xi + 1, xj) + X(U, xi - 1, xj)) + (X(U, xi, xj + 1) + X(U, xi, xj - 1))) +
+               (X(P, xi, xj) - X(P, xi - 1, xj)) * g.inv_h;
+        Au -= g.dt * (act ? sf[(r + 1) * RR_W + xi] : T(0));
+        ru[q] = sb[(r + 1) * RR_W + xi] - Au;
+    }
+    // v residuals at fine (fi0 + a, fj0 - 1 + r): staged column a + 4; x row r + 1, b and f row r
+    for (int q = tid; q < (RR_FY + 1) * RR_FX; q += NT) {
+        const int r = q / RR_FX, a = q - r * RR_FX;
+        const int xi = a + 4, xj = r + 1;
+        T Av = g.a0 * X(V, xi, xj) - g.c * ((X(V, xi + 1, xj) + X(V, xi - 1, xj)) + (X(V, xi, xj + 1) + X(V, xi, xj - 1))) +
+               (X(P, xi, xj) - X(P, xi, xj - 1)) * g.inv_h;
+        Av -= g.dt * (act ? sf[RR_BH * RR_W + r * RR_W + xi] : T(0));
+        rv[q] = sb[RR_BH * RR_W + r * RR_W + xi] - Av;
+    }
+    // p residuals at fine (fi0 + a, fj0 + r): staged column a + 4; x row r + 2, b row r + 1
+    for (int q = tid; q < RR_FY * RR_FX; q += NT) {
+        const int r = q / RR_FX, a = q - r * RR_FX;
+        const int xi = a + 4, xj = r + 2;
+        rp[q] = sb[2 * RR_BH * RR_W + (r + 1) * RR_W + xi] +
+                ((X(U, xi + 1, xj) - X(U, xi, xj)) + (X(V, xi, xj + 1) - X(V, xi, xj))) * g.inv_h;
+    }
+    __syncthreads();
+    // restriction of coarse cell (I, J): fine cells fx = 2 tx, fy = 2 ty of the tile
+    const int fx = 2 * threadIdx.x, fy = 2 * threadIdx.y;
+    const T su = (ru[fy * RR_RU + fx + 1] + ru[(fy + 1) * RR_RU + fx + 1]) +
+                 T(0.5) * ((ru[fy * RR_RU + fx + 2] + ru[(fy + 1) * RR_RU + fx + 2]) +
+                           (ru[fy * RR_RU + fx] + ru[(fy + 1) * RR_RU + fx]));
+    const T sv = (rv[(fy + 1) * RR_FX + fx] + rv[(fy + 1) * RR_FX + fx + 1]) +
+                 T(0.5) * ((rv[(fy + 2) * RR_FX + fx] + rv[(fy + 2) * RR_FX + fx + 1]) +
+                           (rv[fy * RR_FX + fx] + rv[fy * RR_FX + fx + 1]));
+    const T sp = (rp[fy * RR_FX + fx] + rp[fy * RR_FX + fx + 1]) + (rp[(fy + 1) * RR_FX + fx] + rp[(fy + 1) * RR_FX + fx + 1]);
+    const int I = blockIdx.x * RR_CX + threadIdx.x, J = blockIdx.y * RR_CY + threadIdx.y;
+    const int nc = Nc * Nc, c = J * Nc + I;
+    bc[c] = T(0.25) * su;
+    bc[nc + c] = T(0.25) * sv;
+    bc[2 * nc + c] = T(0.25) * sp;
+}
+
 template <typename T>
 void launch_residual_restrict(const GridK<T>& g, const T* x, const T* b, T* bc, cudaStream_t s) {
     const int Nc = g.N / 2;
+    if (Nc >= RR_CX && g.tx == TX && g.ty == TY) {   // fine tiles of 32 x 8: two by two per block
+        const size_t smem = sizeof(T) * (size_t)RR_WORDS;
+        static thread_local bool enabled = false;
+        if (!enabled) {
+            cudaFuncSetAttribute(k_residual_restrict_tiled<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            enabled = true;
+        }
+        launch_pdl(k_residual_restrict_tiled<T>, dim3(Nc / RR_CX, Nc / RR_CY), dim3(RR_CX, RR_CY), smem, s, g, x, b, bc);
+        return;
+    }
     dim3 blk(Nc < 32 ? Nc : 32, Nc < 8 ? Nc : 8);
     dim3 grd((Nc + blk.x - 1) / blk.x, (Nc + blk.y - 1) / blk.y);
     launch_pdl(k_residual_restrict<T>, grd, blk, 0, s, g, x, b, bc);

@@ -538,124 +538,136 @@ void launch_spread(const IBK<T>& k, const T* F, T* f, const int* tiles, const in
 }
 
 // ------------------------------------------------------------------------------------------
-// Set-up assembly of IB operator entries, B = [S K J]^l = -(1/h^2) sum_e kappa_e d_e d_e^T with
-// d_e = J_l[a] - J_l[b] (the level-l stencil rows of the spring's two markers).  One thread per
-// (spring, component) scatters with FP64 atomics (set-up only; the solve never uses atomics).
-struct EdgeStencil {
-    int face[32];
-    double coef[32];
-    int n;
-};
-__device__ __forceinline__ void edge_stencil(EdgeStencil& es, int a, int b, const int* base, const double* w,
-                                             int N, int W) {
-    const int mk = N - 1;
-    es.n = 0;
-    for (int side = 0; side < 2; ++side) {
-        const int m = side == 0 ? a : b;
-        const double sg = side == 0 ? 1.0 : -1.0;
-        const int bb = base[m], bi = bb & 0xffff, bj = (bb >> 16) & 0xffff;
-        for (int q = 0; q < W; ++q)
-            for (int p = 0; p < W; ++p) {
-                es.face[es.n] = ((bj + q) & mk) * N + ((bi + p) & mk);
-                es.coef[es.n] = sg * w[8 * m + p] * w[8 * m + 4 + q];
-                ++es.n;
-            }
-    }
+// Set-up assembly of IB operator entries from the markers, B = [S K J]^l =
+// -(1/h^2) sum_e kappa_e d_e d_e^T with d_e = J_l[a] - J_l[b] (the level-l stencil rows of the
+// spring's two markers), used where the assembled windows overflow.
+// Weight J_mf of marker m's level stencil at face (fi, fj), or 0 outside the stencil (covered = false).
+__device__ __forceinline__ double stencil_weight(const IBK<double>& k, int c, int m, int fi, int fj, bool& covered) {
+    const int mk = k.N - 1, bb = k.base[c][m];
+    const int a = (fi - (bb & 0xffff)) & mk, b = (fj - ((bb >> 16) & 0xffff)) & mk;
+    covered = a < k.W && b < k.W;
+    return covered ? k.wgt[c][8 * m + a] * k.wgt[c][8 * m + 4 + b] : 0.0;
 }
 
-// Diagonal B(f,f) and the patch off-diagonal B(f, f+e) (e = +x for u faces, +y for v faces).
-__global__ void k_patch_entries(const int* __restrict__ edges, const double* __restrict__ kappa, int E,
-                                const int* __restrict__ base0, const int* __restrict__ base1,
-                                const double* __restrict__ w0, const double* __restrict__ w1, int N, int W,
-                                double inv_h2, double* __restrict__ ibd) {
+// Diagonal B(f, f) and the patch off-diagonal B(f, f + e) (e = +x for u faces, +y for v faces) of
+// [S K J] on one level, where the assembled windows are not available:
+//   B(f, g) = -(1/h^2) sum_e kappa_e d_e(f) d_e(g),   d_e(f) = J_af - J_bf  (spring e = (a, b), a != b).
+// One thread per face of the tiles a marker stencil touches, per component.  The face gathers the
+// markers whose stencil covers it from the level's cell bins (bin offsets in a fixed order, markers of a
+// bin in Morton order) and each marker's springs from its adjacency list (ordered by spring id); a
+// spring whose two markers both cover f is taken once, from the marker with the smaller index.  The
+// summation order is fixed: repeated set-ups give the same bits.
+__global__ void k_patch_entries(IBK<double> k, const int* __restrict__ adjStart, const int* __restrict__ adjNbr,
+                                const double* __restrict__ adjKap, const int* __restrict__ tiles,
+                                const int* __restrict__ rowSlots, const int* __restrict__ nRow, int tx, int ty,
+                                int ntx, double* __restrict__ ibd) {
     pdl_entry();
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if ((int)blockIdx.x >= *nRow) return;
     const int c = blockIdx.y;
-    if (e >= E) return;
-    const int a = edges[2 * e], b = edges[2 * e + 1];
-    if (a == b) return;
-    const double kap = kappa[e];
-    EdgeStencil es;
-    edge_stencil(es, a, b, c == 0 ? base0 : base1, c == 0 ? w0 : w1, N, W);
-    const int n = N * N, mk = N - 1;
-    double* diag = ibd + 2 * c * n;
-    double* off = ibd + (2 * c + 1) * n;
-    for (int p = 0; p < es.n; ++p) {
-        const int f = es.face[p];
-        bool owner = true;
-        for (int q = 0; q < p; ++q)
-            if (es.face[q] == f) owner = false;
-        if (!owner) continue;
-        const int fi = f % N, fj = f / N;
-        const int fn = c == 0 ? fj * N + ((fi + 1) & mk) : ((fj + 1) & mk) * N + fi;
-        double d = 0.0, dn = 0.0;
-        for (int q = 0; q < es.n; ++q) {
-            if (es.face[q] == f) d += es.coef[q];
-            if (es.face[q] == fn) dn += es.coef[q];
-        }
-        if (d != 0.0) {
-            atomicAdd(&diag[f], -kap * d * d * inv_h2);
-            if (dn != 0.0) atomicAdd(&off[f], -kap * d * dn * inv_h2);
-        }
-    }
-}
-void launch_patch_entries(const int* edges, const double* kappa, int E, const int* base0, const int* base1,
-                          const double* w0, const double* w1, int M, int N, int W, double inv_h2, double* ibd,
-                          cudaStream_t s) {
-    (void)M;
-    if (E == 0) return;
-    launch_pdl(k_patch_entries, dim3((E + 127) / 128, 2), 128, 0, s, edges, kappa, E, base0, base1, w0, w1, N, W, inv_h2,
-                                                             ibd);
-}
-
-// Dense coarsest-level IB block B (2 x n0 x n0, per component) accumulated per block in shared
-// memory when it fits, then added to global memory.
-__global__ void k_dense_ib(const int* __restrict__ edges, const double* __restrict__ kappa, int E,
-                           const int* __restrict__ base0, const int* __restrict__ base1,
-                           const double* __restrict__ w0, const double* __restrict__ w1, int N, int W,
-                           double inv_h2, double* __restrict__ B, int useSmem) {
-    pdl_entry();
-    extern __shared__ double sB[];
-    const int n0 = N * N;
-    const int tot = 2 * n0 * n0;
-    if (useSmem) {
-        for (int t = threadIdx.x; t < tot; t += blockDim.x) sB[t] = 0.0;
-        __syncthreads();
-    }
-    double* acc = useSmem ? sB : B;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
-        const int a = edges[2 * e], b = edges[2 * e + 1];
-        if (a == b) continue;
-        const double kap = kappa[e];
-        for (int c = 0; c < 2; ++c) {
-            EdgeStencil es;
-            edge_stencil(es, a, b, c == 0 ? base0 : base1, c == 0 ? w0 : w1, N, W);
-            double* Bc = acc + (size_t)c * n0 * n0;
-            for (int p = 0; p < es.n; ++p) {
-                const double cp = -kap * es.coef[p] * inv_h2;
-                if (cp == 0.0) continue;
-                for (int q = 0; q < es.n; ++q)
-                    if (es.coef[q] != 0.0) atomicAdd(&Bc[(size_t)es.face[p] * n0 + es.face[q]], cp * es.coef[q]);
+    const int t = tiles[rowSlots[blockIdx.x]];
+    const int N = k.N, n = N * N, mk = N - 1;
+    const int fi = (t % ntx) * tx + threadIdx.x, fj = (t / ntx) * ty + threadIdx.y;
+    const int ni = c == 0 ? ((fi + 1) & mk) : fi, nj = c == 0 ? fj : ((fj + 1) & mk);   // f + e
+    const int* bs = k.binStart[c];
+    const int* srt = k.sorted[c];
+    double dsum = 0.0, osum = 0.0;
+    for (int b = 0; b < k.W; ++b)
+        for (int a = 0; a < k.W; ++a) {
+            const uint32_t bin = morton((fi - a) & mk, (fj - b) & mk);
+            for (int q = bs[bin]; q < bs[bin + 1]; ++q) {
+                const int m = srt[q];
+                bool cm, cmn;
+                const double jm = stencil_weight(k, c, m, fi, fj, cm);
+                const double jmn = stencil_weight(k, c, m, ni, nj, cmn);
+                if (!cm) continue;   // another level's origin bin (cannot happen on a consistent set-up)
+                for (int p = adjStart[m]; p < adjStart[m + 1]; ++p) {
+                    const int o = adjNbr[p];
+                    if (o == m) continue;
+                    bool co, con;
+                    const double jo = stencil_weight(k, c, o, fi, fj, co);
+                    if (co && o < m) continue;   // taken from o
+                    const double jon = stencil_weight(k, c, o, ni, nj, con);
+                    const double d = jm - jo, dn = jmn - jon;
+                    dsum += adjKap[p] * d * d;
+                    osum += adjKap[p] * d * dn;
+                }
             }
         }
-    }
-    if (useSmem) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < tot; t += blockDim.x)
-            if (sB[t] != 0.0) atomicAdd(&B[t], sB[t]);
+    const int f = fj * N + fi;
+    ibd[(size_t)2 * c * n + f] = -dsum * k.inv_h2;
+    ibd[(size_t)(2 * c + 1) * n + f] = -osum * k.inv_h2;
+}
+void launch_patch_entries(const IBK<double>& k, const int* adjStart, const int* adjNbr, const double* adjKap,
+                          const int* tiles, const int* rowSlots, const int* nRow, int maxRow, int tx, int ty, int ntx,
+                          double* ibd, cudaStream_t s) {
+    if (maxRow == 0) return;
+    launch_pdl(k_patch_entries, dim3(maxRow, 2), dim3(tx, ty), 0, s, k, adjStart, adjNbr, adjKap, tiles, rowSlots,
+               nRow, tx, ty, ntx, ibd);
+}
+
+// Dense coarsest-level IB block B (2 x n0 x n0, per component), where the assembled windows are not
+// available.  One block per row face p and component: its threads take the markers covering p (the
+// markers of each bin in a fixed strided assignment) and their springs, as k_patch_entries does, and
+// add kappa_e d_e(p) d_e(q) for the faces q of both markers' stencils into a row of their own in
+// shared memory; the rows are then summed over the threads in thread order.  No atomics.
+__global__ void k_dense_ib(IBK<double> k, const int* __restrict__ adjStart, const int* __restrict__ adjNbr,
+                           const double* __restrict__ adjKap, double* __restrict__ B) {
+    pdl_entry();
+    extern __shared__ double rowacc[];   // blockDim.x x n0
+    const int N = k.N, n0 = N * N, mk = N - 1, T = blockDim.x, tid = threadIdx.x;
+    const int p = blockIdx.x, c = blockIdx.y;
+    const int pi = p % N, pj = p / N;
+    double* acc = rowacc + (size_t)tid * n0;
+    for (int q = 0; q < n0; ++q) acc[q] = 0.0;
+    const int* bs = k.binStart[c];
+    const int* srt = k.sorted[c];
+    for (int b = 0; b < k.W; ++b)
+        for (int a = 0; a < k.W; ++a) {
+            const uint32_t bin = morton((pi - a) & mk, (pj - b) & mk);
+            for (int q = bs[bin] + tid; q < bs[bin + 1]; q += T) {
+                const int m = srt[q];
+                bool cm;
+                const double jm = stencil_weight(k, c, m, pi, pj, cm);
+                if (!cm) continue;
+                const int bm = k.base[c][m];
+                for (int e = adjStart[m]; e < adjStart[m + 1]; ++e) {
+                    const int o = adjNbr[e];
+                    if (o == m) continue;
+                    bool co;
+                    const double jo = stencil_weight(k, c, o, pi, pj, co);
+                    if (co && o < m) continue;
+                    const double kd = adjKap[e] * (jm - jo);
+                    if (kd == 0.0) continue;
+                    const int bo = k.base[c][o];
+                    for (int y = 0; y < k.W; ++y)      // + kappa d_e(p) J_mq over m's stencil
+                        for (int x = 0; x < k.W; ++x) {
+                            const int qf = (((bm >> 16) + y) & mk) * N + (((bm & 0xffff) + x) & mk);
+                            acc[qf] += kd * k.wgt[c][8 * m + x] * k.wgt[c][8 * m + 4 + y];
+                        }
+                    for (int y = 0; y < k.W; ++y)      // - kappa d_e(p) J_oq over o's stencil
+                        for (int x = 0; x < k.W; ++x) {
+                            const int qf = (((bo >> 16) + y) & mk) * N + (((bo & 0xffff) + x) & mk);
+                            acc[qf] -= kd * k.wgt[c][8 * o + x] * k.wgt[c][8 * o + 4 + y];
+                        }
+                }
+            }
+        }
+    __syncthreads();
+    for (int q = tid; q < n0; q += T) {
+        double sum = 0.0;
+        for (int r = 0; r < T; ++r) sum += rowacc[(size_t)r * n0 + q];
+        B[(size_t)c * n0 * n0 + (size_t)p * n0 + q] = -sum * k.inv_h2;
     }
 }
-void launch_dense_ib(const int* edges, const double* kappa, int E, const int* base0, const int* base1,
-                     const double* w0, const double* w1, int N, int W, double inv_h2, double* B, cudaStream_t s) {
-    if (E == 0) return;
-    const int n0 = N * N;
-    const size_t bytes = sizeof(double) * 2 * (size_t)n0 * n0;
-    const int useSmem = bytes <= 96 * 1024 ? 1 : 0;
-    int blocks = (E + 255) / 256;
-    if (blocks > 304) blocks = 304;
-    if (useSmem) cudaFuncSetAttribute(k_dense_ib, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    launch_pdl(k_dense_ib, blocks, 256, useSmem ? bytes : 0, s, edges, kappa, E, base0, base1, w0, w1, N, W, inv_h2, B,
-                                                         useSmem);
+void launch_dense_ib(const IBK<double>& k, const int* adjStart, const int* adjNbr, const double* adjKap, double* B,
+                     cudaStream_t s) {
+    if (k.M == 0) return;
+    const int n0 = k.N * k.N;
+    int threads = 256;
+    while (threads > 32 && (size_t)threads * n0 * sizeof(double) > 128 * 1024) threads /= 2;
+    const size_t smem = (size_t)threads * n0 * sizeof(double);
+    cudaFuncSetAttribute(k_dense_ib, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    launch_pdl(k_dense_ib, dim3(n0, 2), dim3(threads), smem, s, k, adjStart, adjNbr, adjKap, B);
 }
 
 // ------------------------------------------------------------------------------------------

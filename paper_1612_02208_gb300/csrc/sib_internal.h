@@ -268,11 +268,12 @@ template <typename T> void launch_spring(const int* start, const int* nbr, const
 template <typename T> void launch_spread(const IBK<T>& k, const T* F, T* f, const int* tiles, const int* nTiles,
                                          int maxTiles, int tx, int ty, int ntx, int warpPerFace, cudaStream_t s,
                                          const int* rowSlots = nullptr, const int* nRow = nullptr);
-void launch_patch_entries(const int* edges, const double* kappa, int E, const int* base0, const int* base1,
-                          const double* w0, const double* w1, int M, int N, int W, double inv_h2,
+// the patch entries B(f, f), B(f, f + e) and the coarsest dense IB block from the markers and springs
+// (where the assembled windows are not available), by fixed-order gathers
+void launch_patch_entries(const IBK<double>& k, const int* adjStart, const int* adjNbr, const double* adjKap,
+                          const int* tiles, const int* rowSlots, const int* nRow, int maxRow, int tx, int ty, int ntx,
                           double* ibd, cudaStream_t s);
-void launch_dense_ib(const int* edges, const double* kappa, int E, const int* base0, const int* base1,
-                     const double* w0, const double* w1, int N, int W, double inv_h2, double* B,
+void launch_dense_ib(const IBK<double>& k, const int* adjStart, const int* adjNbr, const double* adjKap, double* B,
                      cudaStream_t s);
 void launch_kj_patch(const IBK<double>& k, const int* adjStart, const int* adjNbr, const double* adjKap, double* KJ,
                      int* overflow, cudaStream_t s);

@@ -1142,9 +1142,9 @@ void setup(sib_ctx* c, cudaStream_t s) {
                     KL(c, launch_window_patch((const double*)lv.win[0], lv.tiles, lv.hnTiles, lv.N, lv.tx, lv.ty, lv.ntx,
                                               (double*)lv.p[0].ibd, s));
                 else
-                    KL(c, launch_patch_entries(c->edges, c->kappa, c->E, lv.base[0], lv.base[1],
-                                               (const double*)lv.p[0].w[0], (const double*)lv.p[0].w[1], c->M, lv.N,
-                                               lv.W, 1.0 / (lv.h * lv.h), (double*)lv.p[0].ibd, s));
+                    KL(c, launch_patch_entries(ibk<double>(c, l), c->adjStart, c->adjNbr, c->kap64, lv.tiles,
+                                               lv.rowSlots, lv.nRowTiles, lv.hnRowTiles, lv.tx, lv.ty, lv.ntx,
+                                               (double*)lv.p[0].ibd, s));
             }
             KL(c, (launch_convert<double, float>((const double*)lv.p[0].ibd, (float*)lv.p[1].ibd, 4 * (int64_t)n,
                                                  s)));
@@ -1165,8 +1165,7 @@ void setup(sib_ctx* c, cudaStream_t s) {
                 KL(c, launch_window_dense((const double*)l0.win[0], l0.tiles, l0.hnTiles, l0.N, l0.tx, l0.ty, l0.ntx,
                                           c->B0, s));
             else
-                KL(c, launch_dense_ib(c->edges, c->kappa, c->E, l0.base[0], l0.base[1], (const double*)l0.p[0].w[0],
-                                      (const double*)l0.p[0].w[1], l0.N, l0.W, 1.0 / (l0.h * l0.h), c->B0, s));
+                KL(c, launch_dense_ib(ibk<double>(c, 0), c->adjStart, c->adjNbr, c->kap64, c->B0, s));
         }
         c->kappaDirty = false;
         c->fluidDirty = true;
