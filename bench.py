@@ -75,10 +75,11 @@ def parse_args(argv=None):
     p.add_argument("--no-paper", action="store_true", help="skip the paper-workload and cavity tables")
     p.add_argument("--quick", action="store_true", help="headline only (no other legs)")
     p.add_argument("--large-n", type=int, default=LARGE_N, help="grid of the large-grid V-cycle roofline")
-    p.add_argument("--profile-vcycle", choices=["headline", "large"], default=None,
+    p.add_argument("--profile-vcycle", choices=["headline", "large", "ras8o2"], default=None,
                    help="two FP32 V-cycles in an NVTX range 'vcycle', with a one-vector FGMRES basis (the small-memory "
                         "case for ncu captures): 'headline' = the headline workload and smoother, 'large' = the "
-                        "4096^2 thin ellipse with Vanka")
+                        "4096^2 thin ellipse with Vanka, 'ras8o2' = the 2048^2 thin ellipse with 8 x 8 boxes of "
+                        "overlap 2, their correction on the tensor cores")
     p.add_argument("--profile-solve", action="store_true",
                    help="one FGMRES solve of the 128^2 disk (Vanka, kappa = 1e2) without CUDA graphs, in an NVTX range "
                         "'solve', so that ncu lists the Krylov kernels that the device graph otherwise hides")
@@ -586,15 +587,18 @@ def large_vcycle(sib, torch, reps=20, N=None):
         ms, by = S.time_kernel(name, lmax, True, reps=20)
         out["kernels"][name] = {"ms": round(ms, 5), "bytes": by, "gbs": round(by / (ms * 1e-3) / 1e9, 1)}
     for (bx, ov), key in (((4, 1), "ras"), (WIDE_BOX, "ras8o2")):
-        S.set_options(smoother=sib.SMOOTHER_RAS, box=bx, box_overlap=ov, omega=-1.0)
+        S.set_options(smoother=sib.SMOOTHER_RAS, box=bx, box_overlap=ov, omega=-1.0, ras_tc=1)
         S.setup()
-        out["vcycle_ms_" + key] = round(time_cycles(), 4)
-        ms, by = S.time_kernel("ras", lmax, True, reps=20)
-        out["kernels"][key] = {"ms": round(ms, 5), "bytes": by, "gbs": round(by / (ms * 1e-3) / 1e9, 1)}
         # the correction is a dense product: 2 ne flops per owned dof, ne = 3 e^2 + 2 e, e = b + 2 o
         e = bx + 2 * ov
         flops = 2.0 * (3 * e * e + 2 * e) * 3.0 * LARGE * LARGE
-        out["kernels"][key]["tflops"] = round(flops / (ms * 1e-3) / 1e12, 2)
+        for tc, suffix in ((2, ""), (0, "_cuda_cores")):
+            S.set_options(ras_tc=tc)
+            out["vcycle_ms_" + key + suffix] = round(time_cycles(), 4)
+            ms, by = S.time_kernel("ras", lmax, True, reps=20)
+            out["kernels"][key + suffix] = {"ms": round(ms, 5), "bytes": by, "gbs": round(by / (ms * 1e-3) / 1e9, 1),
+                                            "tflops": round(flops / (ms * 1e-3) / 1e12, 2)}
+        S.set_options(ras_tc=1)
     S.close()
     return out
 
@@ -1045,12 +1049,16 @@ def run_reference(args):
 def run_profile_vcycle(which):
     """Two FP32 V-cycles with a one-vector FGMRES basis, so that the device holds little memory: the
     case ncu captures of the V-cycle kernels use.  'headline': the headline workload and smoother;
-    'large': the 4096^2 thin ellipse (rho = 1, kappa = 1e4) with Vanka, the roofline leg's V-cycle."""
+    'large': the 4096^2 thin ellipse (rho = 1, kappa = 1e4) with Vanka, the roofline leg's V-cycle;
+    'ras8o2': the same body on 2048^2 with RAS, 8 x 8 boxes of overlap 2, tensor-core correction."""
     import torch
     from paper_1612_02208_gb300 import inputs, sib
     if which == "headline":
         prob = inputs.disk_and_ellipse_re(N_HEAD)
         opts = dict(smoother=sib.SMOOTHER_SC, smooth_krylov=1)
+    elif which == "ras8o2":
+        prob = inputs.thin_ellipse_re(LARGE_N // 2, kappa=1e4, seed=2)
+        opts = dict(smoother=sib.SMOOTHER_RAS, box=WIDE_BOX[0], box_overlap=WIDE_BOX[1], ras_tc=2)
     else:
         prob = inputs.thin_ellipse_re(LARGE_N, kappa=1e4, seed=2)
         opts = dict(smoother=sib.SMOOTHER_VANKA)

@@ -15,7 +15,11 @@
 // up to RAS_EMAX_SMEM cells wide are eliminated in shared memory and corrected by a persistent
 // kernel; wider ones (the paper's 8 x 8 boxes with overlap 2 and up) are eliminated in a global
 // workspace and corrected by a batched product over tiles of boxes.
+#include <algorithm>
+
 #include "sib_internal.h"
+#include "tcgen05.cuh"
+#include "tma.cuh"
 
 namespace sib {
 
@@ -723,6 +727,244 @@ __global__ void __launch_bounds__(256) k_ras_apply_big_ib(RasGeo G, const int* _
     }
 }
 
+// ---- tensor-core correction of the IB-free boxes on FP32 levels ---------------------------------
+// The boxes without IB terms share one inverse, so their correction is the product
+//   C^T (boxes x owned rows) = R^T (boxes x ne) Inv^T (ne x owned rows).
+// A tile of RT_NB = 128 boxes is the M of a tcgen05 TF32 MMA, the owned rows (padded to npad, a multiple
+// of 16) its N, the subdomain dofs its K, taken in chunks of RT_KC = 32.  Three TF32 products per pair
+// keep FP32 accuracy: a b = a_hi b_hi + a_hi b_lo + a_lo b_hi, a_hi = tf32(a), a_lo = tf32(a - a_hi)
+// (the dropped a_lo b_lo is below FP32 rounding).  The accumulator lives in TMEM.  Both operands use the
+// K-major layout of tcgen05.cuh with LBO = 144 bytes (a 128-byte row of core matrices plus 16 bytes, so
+// that the residual gather stores into shared memory without bank conflicts) and SBO = 8 LBO.
+constexpr int RT_NB = 128, RT_KC = 32;
+constexpr int RT_LBO = 144, RT_SBO = 8 * RT_LBO;
+constexpr int RT_THREADS = 256;
+constexpr int RT_WAIT = 1 << 22;   // bounded waits on the copies and the MMAs
+constexpr int RT_ABYTES = (RT_NB / 8) * RT_SBO;   // one of hi, lo of the residual tile's chunk
+
+// byte offset of (row, k) in a K-major chunk of RT_KC values per row
+__host__ __device__ inline int rt_off(int row, int k) {
+    return (row >> 3) * RT_SBO + (k >> 2) * RT_LBO + (row & 7) * 16 + (k & 3) * 4;
+}
+
+// Packs the shared inverse's owned rows (slot 0 of inv64, [q][row]) for k_ras_apply_tc: chunk c holds
+// rows 0 .. npad - 1 and dofs q = 32 c .. 32 c + 31 in the K-major layout, its hi part then its lo
+// part; rows past nown, dofs past ne and the 16-byte gaps hold zeros.
+__global__ void k_ras_tc_pack(const double* __restrict__ inv64, int ne, int nown, int npad, int nch,
+                              float* __restrict__ out) {
+    const int chunkWords = (npad / 8) * RT_SBO / 4;
+    const int64_t total = (int64_t)nch * 2 * chunkWords;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx / (2 * chunkWords));
+        const int rem = (int)(idx - (int64_t)c * 2 * chunkWords);
+        const int part = rem / chunkWords, byte = (rem - part * chunkWords) * 4;
+        const int grp = byte / RT_SBO, b2 = byte - grp * RT_SBO, k4 = b2 / RT_LBO, b3 = b2 - k4 * RT_LBO;
+        float val = 0.0f;
+        if (b3 < 128) {
+            const int row = grp * 8 + b3 / 16, q = c * RT_KC + k4 * 4 + (b3 & 15) / 4;
+            if (row < nown && q < ne) {
+                const double v = inv64[(size_t)q * nown + row];
+                const float hi = tf32_rna((float)v);
+                val = part == 0 ? hi : tf32_rna((float)(v - (double)hi));
+            }
+        }
+        out[idx] = val;
+    }
+}
+
+// One correction of the IB-free boxes: xo(owned) = x(owned) + omega (Inv r_k)(owned) (x == nullptr: 0).
+// Persistent blocks over tiles of RT_NB boxes.  Per K chunk (two shared-memory stages): the block
+// gathers the tile's residual windows (warp w: boxes w + 8 j, lane: the chunk's dof), split into hi and
+// lo; one thread fetches the inverse's packed chunk by a bulk copy, waits for it, and issues the
+// chunk's 3 x 4 MMAs into a TMEM slot of its own (two slots, alternating), committed to the stage's
+// barrier.  While the next chunk's MMAs run, every thread adds the previous chunk's slot into FP32
+// totals in registers: each chunk is summed apart and then added to the total, as the CUDA-core form
+// does (one long accumulation over all ne terms loses accuracy to their cancellation).  Warps 0-3 hold
+// the owned rows 0 .. npad/2 - 1 of boxes 32 w + lane, warps 4-7 the others.  After a tile, the totals
+// are written.  Every wait is bounded: a block that gives up writes SIB_DEV_ERR_TMA_WAIT into the error
+// word, waits again (bounded) for its last MMAs and copy, frees its TMEM and leaves.
+constexpr int RT_MAXCOL = 96;   // owned rows per thread: npad / 2 <= 96 (npad <= 192)
+template <int NC>
+__global__ void __launch_bounds__(RT_THREADS, 1)
+    k_ras_apply_tc(RasGeo G, const int* __restrict__ slotOfBox, const float* __restrict__ pack, int npad, int nch,
+                   float omega, const float* __restrict__ r, const float* x, float* xo, int* err) {
+    extern __shared__ __align__(1024) unsigned char rt_smem[];
+    __shared__ __align__(8) uint64_t tma_bar[2];
+    __shared__ __align__(8) uint64_t mma_bar[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int bBytes = (npad / 8) * RT_SBO;
+    const int stageBytes = 2 * RT_ABYTES + 2 * bBytes;
+    int* qtab = reinterpret_cast<int*>(rt_smem + 2 * stageBytes);
+    for (int q = tid; q < G.ne; q += RT_THREADS) {
+        int comp, ii, jj;
+        ras_dof(G, q, comp, ii, jj);
+        qtab[q] = comp | (ii << 8) | (jj << 16);
+    }
+    if (tid == 0) {
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(&tma_bar[k], 1);
+            mbar_init(&mma_bar[k], 1);
+        }
+        fence_mbar_init();
+    }
+    // two accumulator slots of npad columns each
+    const uint32_t slotCols = npad <= 32 ? 32u : npad <= 64 ? 64u : npad <= 128 ? 128u : 256u;
+    const uint32_t ncols = 2 * slotCols;
+    if (warp == 0) tmem_alloc(&tmem_base, ncols);
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = umma_idesc_tf32(RT_NB, npad);
+    pdl_entry();
+    const int N = G.N, n = N * N, m = N - 1, bb = G.b * G.b, nown = G.nown;
+    const int nboxes = G.nbs * G.nbs, ntiles = (nboxes + RT_NB - 1) / RT_NB;
+    const int half = npad / 2;                       // a multiple of 8
+    const int cbase = warp < 4 ? 0 : half;           // this thread's first owned row
+    const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+    uint32_t g = 0;          // chunks this block has staged (stage and slot g & 1); every one is committed
+    bool ok = true;
+    // adds the accumulator slot of chunk gc into the totals (its MMAs complete and waited for)
+    auto add_slot = [&](uint32_t gc, float (&tot)[NC]) {
+        const uint32_t base = tmem + lanes + (gc & 1) * slotCols + (uint32_t)cbase;
+#pragma unroll
+        for (int c0 = 0; c0 < NC; c0 += 16) {
+            if (c0 < half) {
+                uint32_t a[16];
+                tmem_ld16(base + (uint32_t)c0, a);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (c0 + j < NC) tot[c0 + j] += __uint_as_float(a[j]);
+            }
+        }
+    };
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int k0 = tile * RT_NB;
+        float tot[NC];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) tot[j] = 0.0f;
+        for (int c = 0; c < nch; ++c, ++g) {
+            const int st = g & 1;
+            unsigned char* base = rt_smem + st * stageBytes;
+            unsigned char* Ahi = base;
+            unsigned char* Alo = base + RT_ABYTES;
+            unsigned char* Bhi = base + 2 * RT_ABYTES;
+            unsigned char* Blo = Bhi + bBytes;
+            if (g >= 2) {   // the MMAs of chunk g - 2 read this stage (and its slot was added up)
+                const bool w = mbar_wait_bounded(&mma_bar[st], ((g >> 1) - 1) & 1, RT_WAIT);
+                if (!__syncthreads_and(w)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after_sync();
+            }
+            if (tid == 0) {
+                mbar_expect_tx(&tma_bar[st], (uint32_t)(2 * bBytes));
+                bulk_load(Bhi, reinterpret_cast<const unsigned char*>(pack) + (size_t)c * 2 * bBytes,
+                          (uint32_t)(2 * bBytes), &tma_bar[st]);
+            }
+            const int q = c * RT_KC + lane;
+            const int code = q < G.ne ? qtab[q] : 0;
+            float v[RT_NB / 8];
+#pragma unroll
+            for (int j = 0; j < RT_NB / 8; ++j) {   // every load issued before the first store
+                const int kb = k0 + warp + 8 * j;
+                v[j] = 0.0f;
+                if (q < G.ne && kb < nboxes) {
+                    const int gi = ((kb % G.nbs) * G.b - G.o + ((code >> 8) & 0xff)) & m;
+                    const int gj = ((kb / G.nbs) * G.b - G.o + (code >> 16)) & m;
+                    v[j] = r[(size_t)(code & 0xff) * n + (size_t)gj * N + gi];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < RT_NB / 8; ++j) {
+                const float hi = tf32_rna(v[j]);
+                const int off = rt_off(warp + 8 * j, lane);
+                *reinterpret_cast<float*>(Ahi + off) = hi;
+                *reinterpret_cast<float*>(Alo + off) = tf32_rna(v[j] - hi);
+            }
+            fence_proxy_async_smem();
+            tc_fence_before_sync();
+            __syncthreads();   // the stage is written; the slot of chunk g - 2 has been read by everyone
+            bool w0 = true;
+            if (tid == 0) {
+                w0 = mbar_wait_bounded(&tma_bar[st], (g >> 1) & 1, RT_WAIT);
+                if (w0) {
+                    tc_fence_after_sync();
+                    const uint32_t d = tmem + (uint32_t)st * slotCols;
+                    const uint32_t ah = tc_smem_u32(Ahi), al = tc_smem_u32(Alo);
+                    const uint32_t bh = tc_smem_u32(Bhi), bl = tc_smem_u32(Blo);
+#pragma unroll
+                    for (int t = 0; t < RT_KC / 8; ++t) {
+                        const uint32_t o = (uint32_t)(t * 2 * RT_LBO);
+                        const uint64_t dah = umma_desc(ah + o, RT_LBO, RT_SBO), dal = umma_desc(al + o, RT_LBO, RT_SBO);
+                        const uint64_t dbh = umma_desc(bh + o, RT_LBO, RT_SBO), dbl = umma_desc(bl + o, RT_LBO, RT_SBO);
+                        umma_tf32(d, dah, dbh, idesc, t > 0);   // the chunk's slot starts from zero
+                        umma_tf32(d, dah, dbl, idesc, true);
+                        umma_tf32(d, dal, dbh, idesc, true);
+                    }
+                }
+                umma_commit(&mma_bar[st]);   // arrives once the MMAs issued so far are complete
+            }
+            if (!__syncthreads_and(w0)) {
+                ok = false;
+                ++g;   // this chunk's commit was issued
+                break;
+            }
+            if (c > 0) {   // the previous chunk's slot, while this chunk's MMAs run
+                const uint32_t gp = g - 1;
+                const bool w = mbar_wait_bounded(&mma_bar[gp & 1], (gp >> 1) & 1, RT_WAIT);
+                if (!__syncthreads_and(w)) {
+                    ok = false;
+                    ++g;
+                    break;
+                }
+                tc_fence_after_sync();
+                add_slot(gp, tot);
+            }
+        }
+        if (!ok) break;
+        // the tile's last chunk
+        const uint32_t gl = g - 1;
+        const bool w = mbar_wait_bounded(&mma_bar[gl & 1], (gl >> 1) & 1, RT_WAIT);
+        if (!__syncthreads_and(w)) {
+            ok = false;
+            break;
+        }
+        tc_fence_after_sync();
+        add_slot(gl, tot);
+        const int kb = k0 + 32 * (warp & 3) + lane;
+        if (kb < nboxes && !(slotOfBox && slotOfBox[kb] >= 0)) {
+            const int I = kb % G.nbs, J = kb / G.nbs;
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                const int rr = cbase + j;
+                if (j < half && rr < nown) {
+                    const int comp = rr / bb, rem = rr - comp * bb;
+                    const size_t d = (size_t)comp * n + (size_t)(J * G.b + rem / G.b) * N + I * G.b + rem % G.b;
+                    xo[d] = (x ? x[d] : 0.0f) + omega * tot[j];
+                }
+            }
+        }
+        tc_fence_before_sync();
+        __syncthreads();   // the slots are read before the next tile's MMAs overwrite them
+        tc_fence_after_sync();
+    }
+    if (!ok) {   // report, then let this block's last MMAs and copy drain before the TMEM is freed
+        if (tid == 0 && err) *(volatile int*)err = SIB_DEV_ERR_TMA_WAIT;
+        if (g > 0) {
+            const uint32_t gl = g - 1;
+            mbar_wait_bounded(&mma_bar[gl & 1], (gl >> 1) & 1, RT_WAIT);
+            mbar_wait_bounded(&tma_bar[gl & 1], (gl >> 1) & 1, RT_WAIT);
+        }
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
 }  // namespace
 
 bool ras_big(int b, int o) { return b + 2 * o > RAS_EMAX_SMEM; }
@@ -778,10 +1020,68 @@ void launch_ras_apply_big(const RasGeo& G, const int* slotOfBox, const T* inv, T
 }
 }  // namespace
 
+int ras_tc_npad(int b) { return (3 * b * b + 15) / 16 * 16; }
+size_t ras_tc_pack_floats(int b, int o) {
+    const RasGeo G = ras_geo(16, b, o);
+    const int nch = (G.ne + RT_KC - 1) / RT_KC;
+    return (size_t)nch * 2 * (ras_tc_npad(b) / 8) * RT_SBO / 4;
+}
+void launch_ras_tc_pack(int b, int o, const double* inv64, float* pack, cudaStream_t s) {
+    const RasGeo G = ras_geo(16, b, o);
+    const int nch = (G.ne + RT_KC - 1) / RT_KC;
+    const int64_t total = (int64_t)ras_tc_pack_floats(b, o);
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+    k_ras_tc_pack<<<blocks, 256, 0, s>>>(inv64, G.ne, G.nown, ras_tc_npad(b), nch, pack);
+}
+// the IB-free boxes' correction on the tensor cores (FP32 levels): persistent blocks, one per SM
+void launch_ras_apply_tc(int N, int b, int o, const int* slotOfBox, const float* pack, float omega, const float* r,
+                         const float* x, float* xo, int* err, cudaStream_t s) {
+    const RasGeo G = ras_geo(N, b, o);
+    const int npad = ras_tc_npad(b), nch = (G.ne + RT_KC - 1) / RT_KC;
+    const size_t smem = 2 * (2 * (size_t)RT_ABYTES + 2 * (size_t)(npad / 8) * RT_SBO) + sizeof(int) * (size_t)G.ne;
+    static thread_local size_t allowed = 48 * 1024;
+    static thread_local int sms = 0;
+    if (smem > allowed) {
+        cudaFuncSetAttribute(k_ras_apply_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_ras_apply_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_ras_apply_tc<RT_MAXCOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allowed = smem;
+    }
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    const int ntiles = (G.nbs * G.nbs + RT_NB - 1) / RT_NB;
+    const dim3 grd(std::min(ntiles, sms)), blk(RT_THREADS);
+    // each thread keeps npad / 2 owned rows of one box: a compile-time bound for the register totals
+    if (npad <= 32)
+        launch_pdl(k_ras_apply_tc<16>, grd, blk, smem, s, G, slotOfBox, pack, npad, nch, omega, r, x, xo, err);
+    else if (npad <= 64)
+        launch_pdl(k_ras_apply_tc<32>, grd, blk, smem, s, G, slotOfBox, pack, npad, nch, omega, r, x, xo, err);
+    else
+        launch_pdl(k_ras_apply_tc<RT_MAXCOL>, grd, blk, smem, s, G, slotOfBox, pack, npad, nch, omega, r, x, xo, err);
+}
+
 template <typename T>
 void launch_ras_apply(int N, int b, int o, const int* slotOfBox, const int* list, int nIB, const T* inv, T omega,
-                      const T* r, const T* x, T* xo, cudaStream_t s) {
+                      const T* r, const T* x, T* xo, cudaStream_t s, const float* tcPack, int* err) {
     const RasGeo G = ras_geo(N, b, o);
+    if constexpr (sizeof(T) == 4) {
+        if (tcPack) {   // IB-free boxes on the tensor cores, IB boxes by their own inverses
+            launch_ras_apply_tc(N, b, o, slotOfBox, tcPack, omega, r, x, xo, err, s);
+            if (nIB > 0) {
+                if (G.e > RAS_EMAX_SMEM)
+                    launch_pdl(k_ras_apply_big_ib<T>, dim3(nIB), dim3(256), sizeof(T) * ((size_t)G.ne + 4 * (size_t)G.nown),
+                               s, G, list, inv, omega, r, x, xo);
+                else
+                    launch_pdl(k_ras_apply_ib<T>, dim3(nIB), dim3(64 * RAS_QS), sizeof(T) * (G.ne + 64 * RAS_QS), s, G, list,
+                               inv, omega, r, x, xo);
+            }
+            return;
+        }
+    }
     if (G.e > RAS_EMAX_SMEM) {   // rows per lane: nown <= 32 RA
         if (G.nown <= 32)
             launch_ras_apply_big<T, 1>(G, slotOfBox, inv, omega, r, x, xo, s);
@@ -816,8 +1116,8 @@ void launch_ras_apply(int N, int b, int o, const int* slotOfBox, const int* list
                    omega, r, x, xo);
 }
 template void launch_ras_apply<float>(int, int, int, const int*, const int*, int, const float*, float, const float*,
-                                      const float*, float*, cudaStream_t);
+                                      const float*, float*, cudaStream_t, const float*, int*);
 template void launch_ras_apply<double>(int, int, int, const int*, const int*, int, const double*, double,
-                                       const double*, const double*, double*, cudaStream_t);
+                                       const double*, const double*, double*, cudaStream_t, const float*, int*);
 
 }  // namespace sib

@@ -133,9 +133,16 @@ void launch_ras_setup_big(int N, int b, int o, const RasIB& ib, double a0, doubl
                           const int* list, int first, int count, double* work, double* inv64, float* inv32, int* info,
                           cudaStream_t s);
 // the shared-inverse kernel, then (nIB > 0) one block per listed IB box
+// tcPack != nullptr (FP32): the IB-free boxes' correction runs on the tensor cores from the packed
+// shared inverse (launch_ras_tc_pack); err receives SIB_DEV_ERR_TMA_WAIT if one of its waits gives up
 template <typename T>
 void launch_ras_apply(int N, int b, int o, const int* slotOfBox, const int* list, int nIB, const T* inv, T omega,
-                      const T* r, const T* x, T* xo, cudaStream_t s);
+                      const T* r, const T* x, T* xo, cudaStream_t s, const float* tcPack = nullptr,
+                      int* err = nullptr);
+// the shared inverse (slot 0 of the FP64 inverses) packed for the tensor-core correction: hi and lo
+// TF32 parts in K-major chunks of 32 dofs; ras_tc_pack_floats gives its size
+size_t ras_tc_pack_floats(int b, int o);
+void launch_ras_tc_pack(int b, int o, const double* inv64, float* pack, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
 // Levels 1 and 0 of the V-cycle in one thread block (kernels_small.cu).

@@ -89,6 +89,8 @@ struct Level {
     void* rasInv[2] = {nullptr, nullptr};
     size_t rasInvCap = 0;                // entries
     int rasNIB = 0;                      // boxes with their own inverse
+    float* rasTC = nullptr;              // the shared inverse packed for the tensor-core correction
+    size_t rasTCCap = 0;                 // floats
 };
 
 struct sib_ctx {
@@ -508,13 +510,24 @@ void sc_sweep(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream_t s, 
     }
 }
 
+// the packed shared inverse when the IB-free boxes of an FP32 level take the tensor-core correction:
+// ras_tc = 2 for every box size, ras_tc = 1 for boxes of 8 x 8 cells (smaller boxes are faster on the
+// CUDA cores: a 4 x 4 box's product is 48 x 108)
+template <typename T>
+const float* ras_tc_pack_for(const sib_ctx* c, const Level& lv) {
+    if (Prec<T>::id != 1) return nullptr;
+    const int m = c->opts.ras_tc;
+    return (m == 2 || (m == 1 && c->opts.box >= 8)) ? lv.rasTC : nullptr;
+}
+
 // one RAS correction on level l: xo = x + omega Rt^T L_k^{-1} r (x == nullptr: zero initial guess)
 template <typename T>
 void ras_apply(sib_ctx* c, int l, const T* r, const T* x, T* xo, double omega, cudaStream_t s) {
     Level& lv = c->L[l];
     const int pi = Prec<T>::id;
+    const float* tc = ras_tc_pack_for<T>(c, lv);
     KL(c, launch_ras_apply<T>(lv.N, c->opts.box, c->opts.box_overlap, lv.rasSlot, lv.rasList, lv.rasNIB,
-                              (const T*)lv.rasInv[pi], (T)omega, r, x, xo, s));
+                              (const T*)lv.rasInv[pi], (T)omega, r, x, xo, s, tc, c->herr));
     if (lv.rasNIB > 0) ++c->launches;
 }
 
@@ -1023,6 +1036,15 @@ void ras_setup_all(sib_ctx* c, cudaStream_t s) {
                              (float*)lv.rasInv[1], c->rasInfo, s);
             ++c->launches;
         }
+        // the shared inverse (slot 0) packed for the tensor-core correction of FP32 levels
+        const size_t pf = ras_tc_pack_floats(b, o);
+        if (pf > lv.rasTCCap) {
+            dfree(c, lv.rasTC);
+            lv.rasTC = (float*)dalloc(c, sizeof(float) * pf);
+            lv.rasTCCap = pf;
+        }
+        launch_ras_tc_pack(b, o, (const double*)lv.rasInv[0], lv.rasTC, s);
+        ++c->launches;
     }
     int info = 0;
     CK(cudaMemcpyAsync(&info, c->rasInfo, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1664,7 +1686,8 @@ void time_kernel(sib_ctx* c, int kernel, int l, int reps, bool cold, cudaStream_
                 break;
             case SIB_KERNEL_RAS:
                 launch_ras_apply<T>(lv.N, c->opts.box, c->opts.box_overlap, lv.rasSlot, lv.rasList, lv.rasNIB,
-                                    (const T*)lv.rasInv[pi], (T)1, (const T*)b.r, (const T*)b.x, (T*)b.xt, s);
+                                    (const T*)lv.rasInv[pi], (T)1, (const T*)b.r, (const T*)b.x, (T*)b.xt, s,
+                                    ras_tc_pack_for<T>(c, lv), c->herr);
                 break;
             case SIB_KERNEL_IB_WINDOW:
                 launch_ib_window<T>((const T*)lv.win[pi], lv.tiles, lv.rowSlots, lv.nRowTiles, lv.hnRowTiles, lv.N,
@@ -1779,6 +1802,7 @@ void sib_default_opts(sib_opts* o) {
     o->box = 4;
     o->box_overlap = 1;
     o->domain = SIB_DOMAIN_PERIODIC;
+    o->ras_tc = 1;
 }
 
 static void resolve_opts(sib_opts* o) {
@@ -1965,7 +1989,7 @@ int sib_set_options(sib_ctx* c, const sib_opts* o) {
         n.restart < 1 || n.restart > 100 || (n.fuse_small != 0 && n.fuse_small != 1) ||
         (n.smooth_krylov != 0 && n.smooth_krylov != 1) || (n.smooth_krylov && (n.nu1 > WRAP_MAXK || n.nu2 > WRAP_MAXK)) ||
         (n.sc_relax != SIB_RELAX_JACOBI && n.sc_relax != SIB_RELAX_SGS) ||
-        (n.domain != SIB_DOMAIN_PERIODIC && n.domain != SIB_DOMAIN_CAVITY))
+        (n.domain != SIB_DOMAIN_PERIODIC && n.domain != SIB_DOMAIN_CAVITY) || (n.ras_tc < 0 || n.ras_tc > 2))
         throw SibError(SIB_ERR_ARG, "option out of range");
     if (n.domain == SIB_DOMAIN_CAVITY) {
         if (!CAVITY_SOLVE_ENABLED) throw SibError(SIB_ERR_UNIMPLEMENTED, "the cavity domain is not available");

@@ -102,3 +102,24 @@ def test_wide_ras_thin_circle_converges():
     assert abs(S.stats.iterations - its) <= 1, (S.stats.iterations, its)
     ref, _ = system.solve_direct(L, b, N, prob.rho)
     assert rel(w, system.project(ref, N, prob.rho)) < 1e-8
+
+
+@pytest.mark.parametrize("name,b,o", [("ellipse64_re", 8, 2), ("fluid32", 8, 2), ("ellipse64_re", 4, 4)])
+def test_wide_ras_tensor_core_correction_matches_cuda_core_form(name, b, o):
+    """FP32 levels, wide subdomains: the shared-inverse correction on the tensor cores (tcgen05, three
+    TF32 products per pair, K = 456 in 15 chunks) against the FP32 CUDA-core form and the oracle."""
+    prob, H, S = pair(name, b, o)
+    for l in range(1, len(H.levels)):
+        lev = H.levels[l]
+        x32 = rand(3 * lev.n, 6800 + l).astype(np.float32).astype(np.float64)
+        b32 = rand(3 * lev.n, 6900 + l, 10.0).astype(np.float32).astype(np.float64)
+        ref = H.smooth(l, x32, b32, 1)
+        outs = []
+        for tc in (2, 0):
+            S.set_options(ras_tc=tc)
+            y = cu(x32, torch.float32)
+            S.smooth(l, y, cu(b32, torch.float32), 1)
+            outs.append(host(y))
+        S.set_options(ras_tc=1)
+        assert rel(outs[0], ref) < TOL32, (l, rel(outs[0], ref))
+        assert rel(outs[0], outs[1]) < TOL32, (l, rel(outs[0], outs[1]))
