@@ -88,10 +88,9 @@ typedef struct {
     int    box_overlap;   /* RAS: overlap o in cells on each side, b + 2 o <= 16 and
                              b + 2 o < 2 n_min (1)                                                   */
     int    domain;        /* SIB_DOMAIN_PERIODIC (default) or SIB_DOMAIN_CAVITY (see below)          */
-    int    ras_tc;        /* RAS, FP32 levels: where the correction of the boxes that share one
-                             inverse runs: 0 the FP32 CUDA cores; 1 the tensor cores (tcgen05, three
-                             TF32 products per pair for FP32 accuracy) for boxes of 8 x 8 cells, the
-                             CUDA cores for smaller ones; 2 the tensor cores for every box size (1)  */
+    int    ras_tc;        /* RAS, FP32 levels: the correction of the boxes that share one inverse runs
+                             on the tensor cores (tcgen05, three TF32 products per pair for FP32
+                             accuracy) (1) or on the FP32 CUDA cores (0) (1)                         */
 } sib_opts;
 
 /* Domains.  SIB_DOMAIN_CAVITY is the paper's lid-driven cavity (Sec. 5) on the same layout: the seam

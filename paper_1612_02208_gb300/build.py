@@ -31,7 +31,8 @@ def _nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "sib_internal.h"), os.path.join(CSRC, "grid_cells.cuh"), os.path.join(CSRC, "tma.cuh"), os.path.join(INCLUDE, "sib.h"), os.path.abspath(__file__)]
+    files += [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".h", ".cuh"))]
+    files += [os.path.join(INCLUDE, "sib.h"), os.path.abspath(__file__)]
     return files
 
 

@@ -734,234 +734,386 @@ __global__ void __launch_bounds__(256) k_ras_apply_big_ib(RasGeo G, const int* _
 // of 16) its N, the subdomain dofs its K, taken in chunks of RT_KC = 32.  Three TF32 products per pair
 // keep FP32 accuracy: a b = a_hi b_hi + a_hi b_lo + a_lo b_hi, a_hi = tf32(a), a_lo = tf32(a - a_hi)
 // (the dropped a_lo b_lo is below FP32 rounding).  The accumulator lives in TMEM.  Both operands use the
-// K-major layout of tcgen05.cuh with LBO = 144 bytes (a 128-byte row of core matrices plus 16 bytes, so
-// that the residual gather stores into shared memory without bank conflicts) and SBO = 8 LBO.
+// K-major layout of tcgen05.cuh: the residual chunk with LBO = 144 bytes (a 128-byte row of core
+// matrices plus 16 bytes, so that the gather stores into shared memory without bank conflicts) and
+// SBO = 8 LBO; the inverse chunk, written by bulk copies, packed (LBO = 128, SBO = 1024).
 constexpr int RT_NB = 128, RT_KC = 32;
-constexpr int RT_LBO = 144, RT_SBO = 8 * RT_LBO;
-constexpr int RT_THREADS = 256;
+constexpr int RT_LBO = 144, RT_SBO = 8 * RT_LBO;      // residual chunk (A): rows padded by 16 bytes
+constexpr int RT_BLBO = 128, RT_BSBO = 8 * RT_BLBO;   // inverse chunk (B): packed
+constexpr int RT_THREADS = 512, RT_WARPS = RT_THREADS / 32;
+constexpr int RT_BPW = RT_NB / RT_WARPS;          // boxes per warp in the residual gather
+constexpr int RT_MAXSB = 16;                      // inverse stages at most
 constexpr int RT_WAIT = 1 << 22;   // bounded waits on the copies and the MMAs
+constexpr uint32_t RT_SLEEP_NS = 2000;   // sleep hint of one attempt in the pipeline's waits
+constexpr int RT_SLEEP_WAIT = 1 << 18;   // attempts: at most about half a second of sleeping
 constexpr int RT_ABYTES = (RT_NB / 8) * RT_SBO;   // one of hi, lo of the residual tile's chunk
 
-// byte offset of (row, k) in a K-major chunk of RT_KC values per row
+// byte offset of (row, k) in a residual chunk of RT_KC values per row
 __host__ __device__ inline int rt_off(int row, int k) {
     return (row >> 3) * RT_SBO + (k >> 2) * RT_LBO + (row & 7) * 16 + (k & 3) * 4;
 }
+// bytes of one of hi, lo of an inverse chunk (npad rows)
+__host__ __device__ inline int rt_bbytes(int npad) { return (npad / 8) * RT_BSBO; }
 
 // Packs the shared inverse's owned rows (slot 0 of inv64, [q][row]) for k_ras_apply_tc: chunk c holds
-// rows 0 .. npad - 1 and dofs q = 32 c .. 32 c + 31 in the K-major layout, its hi part then its lo
-// part; rows past nown, dofs past ne and the 16-byte gaps hold zeros.
+// rows 0 .. npad - 1 and dofs q = 32 c .. 32 c + 31 in the packed K-major layout, its hi part then its
+// lo part; rows past nown and dofs past ne hold zeros.
 __global__ void k_ras_tc_pack(const double* __restrict__ inv64, int ne, int nown, int npad, int nch,
                               float* __restrict__ out) {
-    const int chunkWords = (npad / 8) * RT_SBO / 4;
+    const int chunkWords = rt_bbytes(npad) / 4;
     const int64_t total = (int64_t)nch * 2 * chunkWords;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(idx / (2 * chunkWords));
         const int rem = (int)(idx - (int64_t)c * 2 * chunkWords);
         const int part = rem / chunkWords, byte = (rem - part * chunkWords) * 4;
-        const int grp = byte / RT_SBO, b2 = byte - grp * RT_SBO, k4 = b2 / RT_LBO, b3 = b2 - k4 * RT_LBO;
+        const int grp = byte / RT_BSBO, b2 = byte - grp * RT_BSBO, k4 = b2 / RT_BLBO, b3 = b2 - k4 * RT_BLBO;
+        const int row = grp * 8 + b3 / 16, q = c * RT_KC + k4 * 4 + (b3 & 15) / 4;
         float val = 0.0f;
-        if (b3 < 128) {
-            const int row = grp * 8 + b3 / 16, q = c * RT_KC + k4 * 4 + (b3 & 15) / 4;
-            if (row < nown && q < ne) {
-                const double v = inv64[(size_t)q * nown + row];
-                const float hi = tf32_rna((float)v);
-                val = part == 0 ? hi : tf32_rna((float)(v - (double)hi));
-            }
+        if (row < nown && q < ne) {
+            const double v = inv64[(size_t)q * nown + row];
+            const float hi = tf32_rna((float)v);
+            val = part == 0 ? hi : tf32_rna((float)(v - (double)hi));
         }
         out[idx] = val;
     }
 }
 
 // One correction of the IB-free boxes: xo(owned) = x(owned) + omega (Inv r_k)(owned) (x == nullptr: 0).
-// Persistent blocks over tiles of RT_NB boxes.  Per K chunk (two shared-memory stages): the block
-// gathers the tile's residual windows (warp w: boxes w + 8 j, lane: the chunk's dof), split into hi and
-// lo; one thread fetches the inverse's packed chunk by a bulk copy, waits for it, and issues the
-// chunk's 3 x 4 MMAs into a TMEM slot of its own (two slots, alternating), committed to the stage's
-// barrier.  While the next chunk's MMAs run, every thread adds the previous chunk's slot into FP32
-// totals in registers: each chunk is summed apart and then added to the total, as the CUDA-core form
-// does (one long accumulation over all ne terms loses accuracy to their cancellation).  Warps 0-3 hold
-// the owned rows 0 .. npad/2 - 1 of boxes 32 w + lane, warps 4-7 the others.  After a tile, the totals
-// are written.  Every wait is bounded: a block that gives up writes SIB_DEV_ERR_TMA_WAIT into the error
-// word, waits again (bounded) for its last MMAs and copy, frees its TMEM and leaves.
-constexpr int RT_MAXCOL = 96;   // owned rows per thread: npad / 2 <= 96 (npad <= 192)
-template <int NC>
-__global__ void __launch_bounds__(RT_THREADS, 1)
+// Persistent blocks over tiles of RT_NB boxes; 16 worker warps and one issuing warp.  The residual
+// chunks go through ns shared-memory stages and as many TMEM accumulator slots (chunk g uses stage and
+// slot g % ns; ns = 2 for 8 x 8 boxes, whose slots fill the TMEM, 4 for smaller ones), the inverse
+// chunks through nsb stages of their own (chunk g uses stage g % nsb): with nsb = nch the whole inverse
+// stays resident and is fetched once, otherwise a chunk's copy is issued nsb - 1 chunks ahead of its MMAs.
+//   Workers, for chunk g: wait for chunk g - ns's MMAs, add its slot into FP32 totals in registers (and
+// write the tile when g - ns was its last chunk); store chunk g's residuals, gathered earlier (warp w:
+// boxes w + 16 j, lane: the chunk's dof), split into hi and lo, into stage g % ns, and arrive on the
+// stage's barrier; issue the loads of chunk g + 1's residuals.
+//   Issuer (one thread), for chunk g: wait for the stage and the inverse chunk, issue the chunk's 3 x 4
+// MMAs into slot g % ns starting from zero, commit them to the slot's barrier; in the ring, once chunk
+// g - 1's MMAs are complete, fetch chunk g + nsb - 1 of the inverse into their inverse stage.
+// Each chunk is thus summed apart and added to the total, as in the CUDA-core form (one long
+// accumulation over all ne terms loses accuracy to their cancellation).  The worker of warp w and lane t
+// holds owned rows (w / 4) npad / 4 .. of box 32 (w % 4) + t, the TMEM lanes its warp may read.  Every
+// wait is bounded: a thread that gives up raises the block's error flag, every other wait then ends
+// within its own bound, the block writes SIB_DEV_ERR_TMA_WAIT into the error word, the issuer waits
+// (bounded) for its last MMAs and its copies in flight, and the TMEM is freed.
+constexpr int RT_MAXNS = 4;   // residual stages and TMEM slots at most
+
+// barrier of the four worker warps that share TMEM lane quadrant q (named barriers 1 .. 4)
+__device__ __forceinline__ void quad_bar(int q) { asm volatile("bar.sync %0, 128;\n" ::"r"(1 + q) : "memory"); }
+static_assert(MAX_N <= (1 << 15), "k_ras_apply_tc packs a box origin's two coordinates into one word");
+template <int NC, int PF>
+__global__ void __launch_bounds__(RT_THREADS + 32, 1)
     k_ras_apply_tc(RasGeo G, const int* __restrict__ slotOfBox, const float* __restrict__ pack, int npad, int nch,
-                   float omega, const float* __restrict__ r, const float* x, float* xo, int* err) {
+                   int nsb, int ns, float omega, const float* __restrict__ r, const float* x, float* xo, int* err) {
     extern __shared__ __align__(1024) unsigned char rt_smem[];
-    __shared__ __align__(8) uint64_t tma_bar[2];
-    __shared__ __align__(8) uint64_t mma_bar[2];
+    __shared__ __align__(8) uint64_t tma_bar[RT_MAXSB];
+    __shared__ __align__(8) uint64_t mma_bar[RT_MAXNS];    // the slot's MMAs are complete (one commit)
+    __shared__ __align__(8) uint64_t full_bar[RT_MAXNS];   // the stage is stored and the slot read (every worker)
     __shared__ uint32_t tmem_base;
+    __shared__ int s_err;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int bBytes = (npad / 8) * RT_SBO;
-    const int stageBytes = 2 * RT_ABYTES + 2 * bBytes;
-    int* qtab = reinterpret_cast<int*>(rt_smem + 2 * stageBytes);
-    for (int q = tid; q < G.ne; q += RT_THREADS) {
-        int comp, ii, jj;
-        ras_dof(G, q, comp, ii, jj);
-        qtab[q] = comp | (ii << 8) | (jj << 16);
+    const int aStage = 2 * RT_ABYTES;                  // hi and lo of one residual chunk
+    const int bB = rt_bbytes(npad), bChunk = 2 * bB;   // hi and lo of one inverse chunk
+    const int nq = nch * RT_KC;                        // dofs, padded to whole chunks
+    unsigned char* bBase = rt_smem + ns * aStage;
+    int* qoff = reinterpret_cast<int*>(bBase + nsb * bChunk);   // dof q: comp n + jj N + ii (-1: padding)
+    int* qcode = qoff + nq;                                     // dof q: comp | ii << 8 | jj << 16
+    int2* rowtab = reinterpret_cast<int2*>(qcode + nq);         // owned row: {comp, dy N + dx}
+    int* linTab = reinterpret_cast<int*>(rowtab + G.nown);      // 2 x RT_NB gathered-box origins
+    const bool resident = nsb == nch;
+    const int N = G.N, n = N * N, m = N - 1, b = G.b, bb = b * b, nown = G.nown, e = G.e;
+    for (int q = tid; q < nq; q += blockDim.x) {
+        int comp = 0, ii = 0, jj = 0;
+        if (q < G.ne) ras_dof(G, q, comp, ii, jj);
+        qoff[q] = q < G.ne ? comp * n + jj * N + ii : -1;
+        qcode[q] = comp | (ii << 8) | (jj << 16);
+    }
+    for (int rr = tid; rr < nown; rr += blockDim.x) {
+        const int comp = rr / bb, rem = rr - comp * bb;
+        rowtab[rr] = make_int2(comp, (rem / b) * N + rem % b);
     }
     if (tid == 0) {
-        for (int k = 0; k < 2; ++k) {
-            mbar_init(&tma_bar[k], 1);
+        for (int k = 0; k < nsb; ++k) mbar_init(&tma_bar[k], 1);
+        for (int k = 0; k < ns; ++k) {
             mbar_init(&mma_bar[k], 1);
+            mbar_init(&full_bar[k], RT_THREADS);
         }
+        s_err = 0;
         fence_mbar_init();
     }
-    // two accumulator slots of npad columns each
+    // ns accumulator slots of npad columns each (a power of two, 32 at least)
     const uint32_t slotCols = npad <= 32 ? 32u : npad <= 64 ? 64u : npad <= 128 ? 128u : 256u;
-    const uint32_t ncols = 2 * slotCols;
+    const uint32_t ncols = ns * slotCols <= 32 ? 32u : ns * slotCols <= 64 ? 64u : ns * slotCols <= 128 ? 128u
+                           : ns * slotCols <= 256 ? 256u : 512u;
     if (warp == 0) tmem_alloc(&tmem_base, ncols);
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = umma_idesc_tf32(RT_NB, npad);
     pdl_entry();
-    const int N = G.N, n = N * N, m = N - 1, bb = G.b * G.b, nown = G.nown;
     const int nboxes = G.nbs * G.nbs, ntiles = (nboxes + RT_NB - 1) / RT_NB;
-    const int half = npad / 2;                       // a multiple of 8
-    const int cbase = warp < 4 ? 0 : half;           // this thread's first owned row
-    const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
-    uint32_t g = 0;          // chunks this block has staged (stage and slot g & 1); every one is committed
-    bool ok = true;
-    // adds the accumulator slot of chunk gc into the totals (its MMAs complete and waited for)
-    auto add_slot = [&](uint32_t gc, float (&tot)[NC]) {
-        const uint32_t base = tmem + lanes + (gc & 1) * slotCols + (uint32_t)cbase;
+    const int myTiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const uint32_t gEnd = (uint32_t)myTiles * nch;   // this block's chunks
+    volatile int* verr = &s_err;
+    if (warp == RT_WARPS) {   // ---- the issuing warp
+        if (lane == 0) {
+            const uint32_t idesc = umma_idesc_tf32(RT_NB, npad);
+            // descriptors of the stages' first K step; step t adds t * 2 LBO bytes (the 14-bit address
+            // field holds every shared-memory address, so the sums never carry out of it)
+            const uint64_t dA0 = umma_desc(tc_smem_u32(rt_smem), RT_LBO, RT_SBO);
+            const uint64_t dB0 = umma_desc(tc_smem_u32(bBase), RT_BLBO, RT_BSBO);
+            auto fetch_inverse = [&](int st, int c) {   // chunk c of the inverse into inverse stage st
+                mbar_expect_tx(&tma_bar[st], (uint32_t)bChunk);
+                bulk_load(bBase + st * bChunk, reinterpret_cast<const unsigned char*>(pack) + (size_t)c * bChunk,
+                          (uint32_t)bChunk, &tma_bar[st]);
+            };
+            uint32_t nM = 0, nT = 0;   // MMA commits and inverse copies issued
+            for (uint32_t gc = 0; gc < (uint32_t)nsb && gc < gEnd; ++gc) {
+                fetch_inverse((int)gc, (int)(gc % nch));
+                nT = gc + 1;
+            }
+            int sa = 0, sb = 0;                     // stage/slot g % ns, inverse stage g % nsb
+            uint32_t pa = 0, pb = 0;                // phase parities (g / ns) & 1, (g / nsb) & 1
+            int sbNext = nsb - 1, cNext = (nsb - 1) % nch;   // where chunk g + nsb - 1's inverse goes
+            int saPrev = ns - 1;                    // slot of chunk g - 1 and its parity
+            uint32_t paPrev = 1;
+            for (uint32_t g = 0; g < gEnd && !*verr; ++g) {
+                if (!mbar_wait_sleep_bounded(&full_bar[sa], pa, RT_SLEEP_NS, RT_SLEEP_WAIT) ||
+                    !mbar_wait_sleep_bounded(&tma_bar[sb], resident ? 0u : pb, RT_SLEEP_NS, RT_SLEEP_WAIT)) {
+                    *verr = 1;
+                    break;
+                }
+                tc_fence_after_sync();
+                const uint32_t d = tmem + (uint32_t)sa * slotCols;
+                const uint64_t ah = dA0 + (uint64_t)((sa * aStage) >> 4), al = ah + (RT_ABYTES >> 4);
+                const uint64_t bh = dB0 + (uint64_t)((sb * bChunk) >> 4), bl = bh + (uint64_t)(bB >> 4);
 #pragma unroll
-        for (int c0 = 0; c0 < NC; c0 += 16) {
-            if (c0 < half) {
-                uint32_t a[16];
-                tmem_ld16(base + (uint32_t)c0, a);
-#pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (c0 + j < NC) tot[c0 + j] += __uint_as_float(a[j]);
+                for (int t = 0; t < RT_KC / 8; ++t) {
+                    const uint64_t ta = (uint64_t)(t * 2 * RT_LBO / 16), tb = (uint64_t)(t * 2 * RT_BLBO / 16);
+                    umma_tf32(d, ah + ta, bh + tb, idesc, t > 0);   // the chunk's slot starts from zero
+                    umma_tf32(d, ah + ta, bl + tb, idesc, true);
+                    umma_tf32(d, al + ta, bh + tb, idesc, true);
+                }
+                umma_commit(&mma_bar[sa]);   // arrives once the MMAs issued so far are complete
+                nM = g + 1;
+                if (!resident && g >= 1 && g + nsb - 1 < gEnd) {   // chunk g - 1's inverse stage
+                    if (!mbar_wait_sleep_bounded(&mma_bar[saPrev], paPrev, RT_SLEEP_NS, RT_SLEEP_WAIT)) {
+                        *verr = 1;
+                        break;
+                    }
+                    fetch_inverse(sbNext, cNext);
+                    nT = g + nsb;
+                }
+                if (++sbNext == nsb) sbNext = 0;   // the inverse stage and chunk of g + nsb, for the next fetch
+                if (++cNext == nch) cNext = 0;
+                saPrev = sa;
+                paPrev = pa;
+                if (++sa == ns) {
+                    sa = 0;
+                    pa ^= 1u;
+                }
+                if (++sb == nsb) {
+                    sb = 0;
+                    pb ^= 1u;
+                }
+            }
+            if (*verr) {   // the last MMAs and the copies in flight drain before the TMEM is freed
+                if (nM > 0) mbar_wait_bounded(&mma_bar[(nM - 1) % ns], ((nM - 1) / ns) & 1, RT_WAIT);
+                for (uint32_t gc = nT > (uint32_t)nsb ? nT - nsb : 0; gc < nT; ++gc)
+                    mbar_wait_bounded(&tma_bar[gc % nsb], resident ? 0u : (gc / nsb) & 1u, RT_WAIT);
             }
         }
-    };
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int k0 = tile * RT_NB;
+        __syncwarp();
+    } else {   // ---- the workers
+        const int q4 = npad / 4;                         // owned rows per thread
+        const int cbase = (warp >> 2) * q4;              // this thread's first owned row
+        const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+        // the gathered boxes' subdomain origins, one table per tile parity, each warp writing and reading
+        // only its own boxes' entries: oy N + ox where the subdomain lies inside the grid; for the periodic
+        // wrap 2^31 | x | y << 16 taken mod N (N <= 2^15); -1 past the last box
+        float v0[RT_BPW], v1[RT_BPW];                    // gathered residuals: PF chunks in flight
+        int* lt = linTab;                                // the table of the tile being gathered
+        int tilePar = 0;
+        auto origins = [&](int tile) {
+            lt = linTab + tilePar * RT_NB;
+            tilePar ^= 1;
+            if (lane < RT_BPW) {
+                const int kb = tile * RT_NB + warp + RT_WARPS * lane;
+                const int J = kb / G.nbs;
+                const int ox = (kb - J * G.nbs) * b - G.o, oy = J * b - G.o;
+                const bool in = ox >= 0 && oy >= 0 && ox + e < N && oy + e < N;   // faces ox .. ox + e
+                lt[warp + RT_WARPS * lane] =
+                    kb >= nboxes ? -1
+                    : in         ? oy * N + ox
+                                 : (int)(0x80000000u | ((uint32_t)ox & m) | (((uint32_t)oy & m) << 16));
+            }
+            __syncwarp();
+        };
+        auto gather = [&](int c, float (&v)[RT_BPW]) {
+            const int q = c * RT_KC + lane;
+            const int off = qoff[q];
+#pragma unroll
+            for (int j = 0; j < RT_BPW; ++j) {
+                const int lin = lt[warp + RT_WARPS * j];
+                v[j] = 0.0f;
+                if (lin >= 0) {
+                    if (off >= 0) v[j] = __ldg(r + (lin + off));
+                } else if (lin != -1 && off >= 0) {
+                    const int code = qcode[q];
+                    const int ii = (code >> 8) & 0xff, jj = code >> 16;
+                    const int gx = ((lin & 0xffff) + ii) & m, gy = ((((uint32_t)lin >> 16) & 0x7fffu) + jj) & m;
+                    v[j] = __ldg(r + ((size_t)(code & 0xff) * n + (size_t)gy * N + gx));
+                }
+            }
+        };
+        // the gather cursor: the next chunk to gather (tile, chunk); origins() when it enters a tile
+        int tileG = blockIdx.x, cG = 0;
+        auto gather_next = [&](float (&v)[RT_BPW]) {
+            if (tileG >= ntiles) return;
+            if (cG == 0) origins(tileG);
+            gather(cG, v);
+            if (++cG == nch) {
+                cG = 0;
+                tileG += gridDim.x;
+            }
+        };
         float tot[NC];
 #pragma unroll
         for (int j = 0; j < NC; ++j) tot[j] = 0.0f;
-        for (int c = 0; c < nch; ++c, ++g) {
-            const int st = g & 1;
-            unsigned char* base = rt_smem + st * stageBytes;
-            unsigned char* Ahi = base;
-            unsigned char* Alo = base + RT_ABYTES;
-            unsigned char* Bhi = base + 2 * RT_ABYTES;
-            unsigned char* Blo = Bhi + bBytes;
-            if (g >= 2) {   // the MMAs of chunk g - 2 read this stage (and its slot was added up)
-                const bool w = mbar_wait_bounded(&mma_bar[st], ((g >> 1) - 1) & 1, RT_WAIT);
-                if (!__syncthreads_and(w)) {
+        int tileD = blockIdx.x, cD = 0;   // the chunk being added
+        int sS = 0, sD = 0;               // their stages / slots
+        uint32_t pD = 0;                  // the added chunk's phase parity
+        bool ok = true;                   // warp-uniform; after a failed wait the workers only keep step
+        const int lb = __ffs(b) - 1;      // b = 2^lb
+        const int quad = warp & 3;        // TMEM lane quadrant: boxes 32 quad .. 32 quad + 31 of the tile
+        const int boxl = 32 * quad + lane;
+        // a quadrant's 32 boxes lie in one row of boxes, next to each other, when nbs is a multiple of 32:
+        // the tile is then written row by row through the TMEM
+        const bool rowWrite = (G.nbs & 31) == 0;
+        gather_next(v0);
+        if (PF == 2) gather_next(v1);
+        // Every worker runs every iteration, so that the quadrant barriers of the tile writes are reached
+        // by all of them whatever the waits returned.
+        for (uint32_t g = 0; g < gEnd + ns; ++g) {
+            if (g >= (uint32_t)ns) {   // chunk g - ns: its slot into the totals, then the tile after its last chunk
+                // warp-uniform: the slot loads below are warp-collective
+                const bool w = __all_sync(0xffffffffu, ok && !*verr &&
+                                                           mbar_wait_sleep_bounded(&mma_bar[sD], pD, RT_SLEEP_NS,
+                                                                                   RT_SLEEP_WAIT));
+                if (!w && ok) {
                     ok = false;
-                    break;
+                    *verr = 1;
                 }
-                tc_fence_after_sync();
-            }
-            if (tid == 0) {
-                mbar_expect_tx(&tma_bar[st], (uint32_t)(2 * bBytes));
-                bulk_load(Bhi, reinterpret_cast<const unsigned char*>(pack) + (size_t)c * 2 * bBytes,
-                          (uint32_t)(2 * bBytes), &tma_bar[st]);
-            }
-            const int q = c * RT_KC + lane;
-            const int code = q < G.ne ? qtab[q] : 0;
-            float v[RT_NB / 8];
-#pragma unroll
-            for (int j = 0; j < RT_NB / 8; ++j) {   // every load issued before the first store
-                const int kb = k0 + warp + 8 * j;
-                v[j] = 0.0f;
-                if (q < G.ne && kb < nboxes) {
-                    const int gi = ((kb % G.nbs) * G.b - G.o + ((code >> 8) & 0xff)) & m;
-                    const int gj = ((kb / G.nbs) * G.b - G.o + (code >> 16)) & m;
-                    v[j] = r[(size_t)(code & 0xff) * n + (size_t)gj * N + gi];
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < RT_NB / 8; ++j) {
-                const float hi = tf32_rna(v[j]);
-                const int off = rt_off(warp + 8 * j, lane);
-                *reinterpret_cast<float*>(Ahi + off) = hi;
-                *reinterpret_cast<float*>(Alo + off) = tf32_rna(v[j] - hi);
-            }
-            fence_proxy_async_smem();
-            tc_fence_before_sync();
-            __syncthreads();   // the stage is written; the slot of chunk g - 2 has been read by everyone
-            bool w0 = true;
-            if (tid == 0) {
-                w0 = mbar_wait_bounded(&tma_bar[st], (g >> 1) & 1, RT_WAIT);
-                if (w0) {
+                const uint32_t slot = tmem + (uint32_t)sD * slotCols;   // free until chunk g's MMAs
+                if (ok) {
                     tc_fence_after_sync();
-                    const uint32_t d = tmem + (uint32_t)st * slotCols;
-                    const uint32_t ah = tc_smem_u32(Ahi), al = tc_smem_u32(Alo);
-                    const uint32_t bh = tc_smem_u32(Bhi), bl = tc_smem_u32(Blo);
+                    const uint32_t base = slot + lanes + (uint32_t)cbase;
 #pragma unroll
-                    for (int t = 0; t < RT_KC / 8; ++t) {
-                        const uint32_t o = (uint32_t)(t * 2 * RT_LBO);
-                        const uint64_t dah = umma_desc(ah + o, RT_LBO, RT_SBO), dal = umma_desc(al + o, RT_LBO, RT_SBO);
-                        const uint64_t dbh = umma_desc(bh + o, RT_LBO, RT_SBO), dbl = umma_desc(bl + o, RT_LBO, RT_SBO);
-                        umma_tf32(d, dah, dbh, idesc, t > 0);   // the chunk's slot starts from zero
-                        umma_tf32(d, dah, dbl, idesc, true);
-                        umma_tf32(d, dal, dbh, idesc, true);
+                    for (int c0 = 0; c0 < NC; c0 += 8) {
+                        uint32_t a[8];
+                        tmem_ld8(base + (uint32_t)c0, a);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) tot[c0 + j] += __uint_as_float(a[j]);
                     }
                 }
-                umma_commit(&mma_bar[st]);   // arrives once the MMAs issued so far are complete
-            }
-            if (!__syncthreads_and(w0)) {
-                ok = false;
-                ++g;   // this chunk's commit was issued
-                break;
-            }
-            if (c > 0) {   // the previous chunk's slot, while this chunk's MMAs run
-                const uint32_t gp = g - 1;
-                const bool w = mbar_wait_bounded(&mma_bar[gp & 1], (gp >> 1) & 1, RT_WAIT);
-                if (!__syncthreads_and(w)) {
-                    ok = false;
-                    ++g;
-                    break;
+                if (++sD == ns) {
+                    sD = 0;
+                    pD ^= 1u;
                 }
-                tc_fence_after_sync();
-                add_slot(gp, tot);
-            }
-        }
-        if (!ok) break;
-        // the tile's last chunk
-        const uint32_t gl = g - 1;
-        const bool w = mbar_wait_bounded(&mma_bar[gl & 1], (gl >> 1) & 1, RT_WAIT);
-        if (!__syncthreads_and(w)) {
-            ok = false;
-            break;
-        }
-        tc_fence_after_sync();
-        add_slot(gl, tot);
-        const int kb = k0 + 32 * (warp & 3) + lane;
-        if (kb < nboxes && !(slotOfBox && slotOfBox[kb] >= 0)) {
-            const int I = kb % G.nbs, J = kb / G.nbs;
+                if (++cD == nch) {   // the tile
+                    const int k0 = tileD * RT_NB;
+                    const int kb = k0 + boxl;
+                    const bool wr = ok && kb < nboxes && !(slotOfBox && slotOfBox[kb] >= 0);
+                    if (rowWrite) {
+                        // the totals back into the slot, then read 16 boxes x 8 rows at a time: consecutive
+                        // threads hold consecutive rows of a box, consecutive boxes follow, so the writes run
+                        // along x
+                        const unsigned wmask = __ballot_sync(0xffffffffu, wr);
+                        if (ok) {
 #pragma unroll
-            for (int j = 0; j < NC; ++j) {
-                const int rr = cbase + j;
-                if (j < half && rr < nown) {
-                    const int comp = rr / bb, rem = rr - comp * bb;
-                    const size_t d = (size_t)comp * n + (size_t)(J * G.b + rem / G.b) * N + I * G.b + rem % G.b;
-                    xo[d] = (x ? x[d] : 0.0f) + omega * tot[j];
+                            for (int j = 0; j < NC; j += 4)
+                                if (j < q4) tmem_st4(slot + lanes + (uint32_t)(cbase + j), tot[j], tot[j + 1], tot[j + 2], tot[j + 3]);
+                            tmem_wait_st();
+                        }
+                        tc_fence_before_sync();
+                        quad_bar(quad);
+                        tc_fence_after_sync();
+                        const int kq = k0 + 32 * quad;
+                        const int J = kq / G.nbs, I0 = kq - J * G.nbs;
+                        const size_t rowBase = (size_t)(J * b) * N + (size_t)(I0 * b);
+                        for (int grp = warp >> 2; grp < npad / 8 && ok; grp += 4) {
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                uint32_t a[4];
+                                tmem_ld16x256(slot + ((uint32_t)(32 * quad + 16 * h) << 16) + (uint32_t)(8 * grp), a);
+                                float xv[4];
+                                int dd[4];   // offset within the component, or -1
+                                int cc[4];
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) {
+                                    const int l = 16 * h + (lane >> 2) + 8 * (u >> 1);   // box within the quadrant
+                                    const int rr = 8 * grp + 2 * (lane & 3) + (u & 1);    // owned row
+                                    const int comp = rr >> (2 * lb), rem = rr & (bb - 1);
+                                    cc[u] = comp;
+                                    dd[u] = (rr < nown && ((wmask >> l) & 1u))
+                                                ? (int)rowBase + ((rem >> lb) * N) + l * b + (rem & (b - 1))
+                                                : -1;
+                                    xv[u] = (dd[u] >= 0 && x) ? x[(size_t)comp * n + dd[u]] : 0.0f;
+                                }
+#pragma unroll
+                                for (int u = 0; u < 4; ++u)
+                                    if (dd[u] >= 0) xo[(size_t)cc[u] * n + dd[u]] = xv[u] + omega * __uint_as_float(a[u]);
+                            }
+                        }
+                    } else if (wr) {   // boxes across rows of boxes: each thread writes its own rows
+                        const int J = kb / G.nbs, I = kb - J * G.nbs;
+                        const size_t org0 = (size_t)(J * b) * N + (size_t)(I * b);
+#pragma unroll
+                        for (int j = 0; j < NC; ++j) {
+                            const int rr = cbase + j;
+                            if (j < q4 && rr < nown) {
+                                const int2 t = rowtab[rr];
+                                const size_t d = (size_t)t.x * n + org0 + (size_t)t.y;
+                                xo[d] = (x ? x[d] : 0.0f) + omega * tot[j];
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < NC; ++j) tot[j] = 0.0f;
+                    cD = 0;
+                    tileD += gridDim.x;
                 }
             }
-        }
-        tc_fence_before_sync();
-        __syncthreads();   // the slots are read before the next tile's MMAs overwrite them
-        tc_fence_after_sync();
-    }
-    if (!ok) {   // report, then let this block's last MMAs and copy drain before the TMEM is freed
-        if (tid == 0 && err) *(volatile int*)err = SIB_DEV_ERR_TMA_WAIT;
-        if (g > 0) {
-            const uint32_t gl = g - 1;
-            mbar_wait_bounded(&mma_bar[gl & 1], (gl >> 1) & 1, RT_WAIT);
-            mbar_wait_bounded(&tma_bar[gl & 1], (gl >> 1) & 1, RT_WAIT);
+            if (g < gEnd) {   // chunk g into its stage (free: chunk g - ns's MMAs are complete)
+                unsigned char* Ahi = rt_smem + sS * aStage;
+                // chunk g's residuals are in v0 (in v1 for odd g when two chunks are in flight); their
+                // array then takes the loads of chunk g + PF, in flight until its stores
+                auto store_refill = [&](float (&v)[RT_BPW]) {
+#pragma unroll
+                    for (int j = 0; j < RT_BPW; ++j) {
+                        const float hi = tf32_rna(v[j]);
+                        const int off = rt_off(warp + RT_WARPS * j, lane);
+                        *reinterpret_cast<float*>(Ahi + off) = hi;
+                        *reinterpret_cast<float*>(Ahi + RT_ABYTES + off) = tf32_rna(v[j] - hi);
+                    }
+                    fence_proxy_async_smem();
+                    tc_fence_before_sync();
+                    mbar_arrive(&full_bar[sS]);
+                    gather_next(v);
+                };
+                if (PF == 1 || (g & 1) == 0)
+                    store_refill(v0);
+                else
+                    store_refill(v1);
+                if (++sS == ns) sS = 0;
+            }
         }
     }
     tc_fence_before_sync();
     __syncthreads();
+    if (tid == 0 && s_err && err) *(volatile int*)err = SIB_DEV_ERR_TMA_WAIT;
     if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
@@ -1024,7 +1176,7 @@ int ras_tc_npad(int b) { return (3 * b * b + 15) / 16 * 16; }
 size_t ras_tc_pack_floats(int b, int o) {
     const RasGeo G = ras_geo(16, b, o);
     const int nch = (G.ne + RT_KC - 1) / RT_KC;
-    return (size_t)nch * 2 * (ras_tc_npad(b) / 8) * RT_SBO / 4;
+    return (size_t)nch * 2 * rt_bbytes(ras_tc_npad(b)) / 4;
 }
 void launch_ras_tc_pack(int b, int o, const double* inv64, float* pack, cudaStream_t s) {
     const RasGeo G = ras_geo(16, b, o);
@@ -1033,35 +1185,57 @@ void launch_ras_tc_pack(int b, int o, const double* inv64, float* pack, cudaStre
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
     k_ras_tc_pack<<<blocks, 256, 0, s>>>(inv64, G.ne, G.nown, ras_tc_npad(b), nch, pack);
 }
-// the IB-free boxes' correction on the tensor cores (FP32 levels): persistent blocks, one per SM
-void launch_ras_apply_tc(int N, int b, int o, const int* slotOfBox, const float* pack, float omega, const float* r,
+// the IB-free boxes' correction on the tensor cores (FP32 levels): persistent blocks, one per SM, with
+// as many inverse stages as the shared memory holds (all nch chunks where they fit).  False, and nothing
+// launched, where the shared memory cannot hold two inverse stages.
+bool launch_ras_apply_tc(int N, int b, int o, const int* slotOfBox, const float* pack, float omega, const float* r,
                          const float* x, float* xo, int* err, cudaStream_t s) {
     const RasGeo G = ras_geo(N, b, o);
     const int npad = ras_tc_npad(b), nch = (G.ne + RT_KC - 1) / RT_KC;
-    const size_t smem = 2 * (2 * (size_t)RT_ABYTES + 2 * (size_t)(npad / 8) * RT_SBO) + sizeof(int) * (size_t)G.ne;
-    static thread_local size_t allowed = 48 * 1024;
-    static thread_local int sms = 0;
-    if (smem > allowed) {
-        cudaFuncSetAttribute(k_ras_apply_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_ras_apply_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_ras_apply_tc<RT_MAXCOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        allowed = smem;
-    }
+    // owned rows per thread, rounded up to whole TMEM loads; narrow boxes keep two chunks of residual
+    // loads in flight, 8 x 8 boxes (48 rows a thread) one
+    const int nc = npad / 4 <= 16 ? 16 : 48;
+    static thread_local int sms = 0, optin = 0, staticSmem[2] = {-1, -1};
     if (!sms) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (sms <= 0) sms = 1;
+        cudaFuncAttributes fa;
+        staticSmem[0] = cudaFuncGetAttributes(&fa, k_ras_apply_tc<16, 2>) == cudaSuccess ? (int)fa.sharedSizeBytes : 1024;
+        staticSmem[1] = cudaFuncGetAttributes(&fa, k_ras_apply_tc<48, 1>) == cudaSuccess ? (int)fa.sharedSizeBytes : 1024;
+    }
+    const size_t tables =
+        2 * sizeof(int) * (size_t)nch * RT_KC + sizeof(int2) * (size_t)G.nown + 2 * sizeof(int) * RT_NB;
+    const size_t aStage = 2 * (size_t)RT_ABYTES, bChunk = 2 * (size_t)rt_bbytes(npad);
+    const size_t avail = (size_t)optin - (size_t)staticSmem[nc == 48];
+    const int slotCols = npad <= 32 ? 32 : npad <= 64 ? 64 : npad <= 128 ? 128 : 256;
+    // residual stages (= TMEM slots): as many as 512 TMEM columns and the shared memory left after the
+    // whole inverse (or three of its stages) allow, 2 to RT_MAXNS
+    int ns = std::min(RT_MAXNS, 512 / slotCols);
+    const size_t bWant = (size_t)std::min(nch, 3) * bChunk;
+    while (ns > 2 && tables + ns * aStage + bWant > avail) --ns;
+    const size_t fixed = tables + (size_t)ns * aStage;
+    int nsb = avail > fixed ? (int)std::min<size_t>((size_t)nch, (avail - fixed) / bChunk) : 0;
+    nsb = std::min(nsb, RT_MAXSB);
+    if (nsb < 2) return false;   // b + 2 o <= 16 leaves room for three inverse stages in 227 KB
+    const size_t smem = fixed + (size_t)nsb * bChunk;
+    static thread_local size_t allowed[2] = {48 * 1024, 48 * 1024};
+    if (smem > allowed[nc == 48]) {
+        if (nc == 48)
+            cudaFuncSetAttribute(k_ras_apply_tc<48, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        else
+            cudaFuncSetAttribute(k_ras_apply_tc<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allowed[nc == 48] = smem;
     }
     const int ntiles = (G.nbs * G.nbs + RT_NB - 1) / RT_NB;
-    const dim3 grd(std::min(ntiles, sms)), blk(RT_THREADS);
-    // each thread keeps npad / 2 owned rows of one box: a compile-time bound for the register totals
-    if (npad <= 32)
-        launch_pdl(k_ras_apply_tc<16>, grd, blk, smem, s, G, slotOfBox, pack, npad, nch, omega, r, x, xo, err);
-    else if (npad <= 64)
-        launch_pdl(k_ras_apply_tc<32>, grd, blk, smem, s, G, slotOfBox, pack, npad, nch, omega, r, x, xo, err);
+    const dim3 grd(std::min(ntiles, sms)), blk(RT_THREADS + 32);   // 16 worker warps and the issuing warp
+    if (nc == 16)
+        launch_pdl(k_ras_apply_tc<16, 2>, grd, blk, smem, s, G, slotOfBox, pack, npad, nch, nsb, ns, omega, r, x, xo, err);
     else
-        launch_pdl(k_ras_apply_tc<RT_MAXCOL>, grd, blk, smem, s, G, slotOfBox, pack, npad, nch, omega, r, x, xo, err);
+        launch_pdl(k_ras_apply_tc<48, 1>, grd, blk, smem, s, G, slotOfBox, pack, npad, nch, nsb, ns, omega, r, x, xo, err);
+    return true;
 }
 
 template <typename T>
@@ -1069,8 +1243,8 @@ void launch_ras_apply(int N, int b, int o, const int* slotOfBox, const int* list
                       const T* r, const T* x, T* xo, cudaStream_t s, const float* tcPack, int* err) {
     const RasGeo G = ras_geo(N, b, o);
     if constexpr (sizeof(T) == 4) {
-        if (tcPack) {   // IB-free boxes on the tensor cores, IB boxes by their own inverses
-            launch_ras_apply_tc(N, b, o, slotOfBox, tcPack, omega, r, x, xo, err, s);
+        // IB-free boxes on the tensor cores, IB boxes by their own inverses
+        if (tcPack && launch_ras_apply_tc(N, b, o, slotOfBox, tcPack, omega, r, x, xo, err, s)) {
             if (nIB > 0) {
                 if (G.e > RAS_EMAX_SMEM)
                     launch_pdl(k_ras_apply_big_ib<T>, dim3(nIB), dim3(256), sizeof(T) * ((size_t)G.ne + 4 * (size_t)G.nown),

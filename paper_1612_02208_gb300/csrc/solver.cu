@@ -510,14 +510,10 @@ void sc_sweep(sib_ctx* c, int l, const T* x, const T* b, T* xo, cudaStream_t s, 
     }
 }
 
-// the packed shared inverse when the IB-free boxes of an FP32 level take the tensor-core correction:
-// ras_tc = 2 for every box size, ras_tc = 1 for boxes of 8 x 8 cells (smaller boxes are faster on the
-// CUDA cores: a 4 x 4 box's product is 48 x 108)
+// the packed shared inverse when the IB-free boxes of an FP32 level take the tensor-core correction
 template <typename T>
 const float* ras_tc_pack_for(const sib_ctx* c, const Level& lv) {
-    if (Prec<T>::id != 1) return nullptr;
-    const int m = c->opts.ras_tc;
-    return (m == 2 || (m == 1 && c->opts.box >= 8)) ? lv.rasTC : nullptr;
+    return (Prec<T>::id == 1 && c->opts.ras_tc) ? lv.rasTC : nullptr;
 }
 
 // one RAS correction on level l: xo = x + omega Rt^T L_k^{-1} r (x == nullptr: zero initial guess)
@@ -1989,7 +1985,7 @@ int sib_set_options(sib_ctx* c, const sib_opts* o) {
         n.restart < 1 || n.restart > 100 || (n.fuse_small != 0 && n.fuse_small != 1) ||
         (n.smooth_krylov != 0 && n.smooth_krylov != 1) || (n.smooth_krylov && (n.nu1 > WRAP_MAXK || n.nu2 > WRAP_MAXK)) ||
         (n.sc_relax != SIB_RELAX_JACOBI && n.sc_relax != SIB_RELAX_SGS) ||
-        (n.domain != SIB_DOMAIN_PERIODIC && n.domain != SIB_DOMAIN_CAVITY) || (n.ras_tc < 0 || n.ras_tc > 2))
+        (n.domain != SIB_DOMAIN_PERIODIC && n.domain != SIB_DOMAIN_CAVITY) || (n.ras_tc != 0 && n.ras_tc != 1))
         throw SibError(SIB_ERR_ARG, "option out of range");
     if (n.domain == SIB_DOMAIN_CAVITY) {
         if (!CAVITY_SOLVE_ENABLED) throw SibError(SIB_ERR_UNIMPLEMENTED, "the cavity domain is not available");

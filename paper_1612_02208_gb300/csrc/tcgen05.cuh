@@ -74,11 +74,38 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
-// round to the nearest TF32 value (10 explicit mantissa bits; the low 13 bits become zero)
+// warp-collective: 8 consecutive 32-bit TMEM columns of the warp's 32 lanes, one lane per thread
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// warp-collective: stores 4 consecutive 32-bit TMEM columns of the warp's 32 lanes, one lane per thread
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, float v0, float v1, float v2, float v3) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(taddr), "r"(__float_as_uint(v0)),
+                 "r"(__float_as_uint(v1)), "r"(__float_as_uint(v2)), "r"(__float_as_uint(v3))
+                 : "memory");
+}
+// the thread's TMEM stores issued so far are complete
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
+// warp-collective: 16 lanes x 8 columns of 32 bits.  Thread t receives lane t / 4 and lane t / 4 + 8 (of
+// the 16), columns 2 (t % 4) and 2 (t % 4) + 1 of each: v = {(t/4, 2 (t%4)), (t/4, 2 (t%4) + 1),
+// (t/4 + 8, 2 (t%4)), (t/4 + 8, 2 (t%4) + 1)}
+__device__ __forceinline__ void tmem_ld16x256(uint32_t taddr, uint32_t (&v)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// round to the nearest TF32 value, ties away from zero (10 explicit mantissa bits; the low 13 bits
+// become zero): half a TF32 unit added to the magnitude bits, then the low bits cleared.  A carry into
+// the exponent is the correct rounding up to the next binade (or to infinity past the largest value).
 __device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t y;
-    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(y) : "f"(x));
-    return __uint_as_float(y);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 }  // namespace sib

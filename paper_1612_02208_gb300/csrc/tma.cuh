@@ -17,6 +17,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 // makes the initialised barrier visible to the asynchronous (TMA) proxy
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
 
+// one arrival (release: this thread's earlier writes are visible to the thread that sees the phase end)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // one arrival that also announces `bytes` of transactions still to complete this phase
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
@@ -64,6 +69,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int limit) {
     for (int k = 0; k < limit; ++k)
         if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// as mbar_try_wait, but the thread may sleep up to `ns` nanoseconds inside one attempt (it wakes when the
+// phase completes): long waits then take no issue slots from the other warps
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_sleep_bounded(uint64_t* bar, uint32_t parity, uint32_t ns, int limit) {
+    for (int k = 0; k < limit; ++k)
+        if (mbar_try_wait_sleep(bar, parity, ns)) return true;
     return false;
 }
 

@@ -215,11 +215,15 @@ class Solver:
         self._check(self.lib.sib_set_stiffness(self.ctx, _ptr(kappa) if self.E else None, _stream()))
 
     def set_options(self, **kw):
+        """Changes the named fields; a set the library rejects leaves the previous options in force."""
+        new = SibOpts()
+        ctypes.pointer(new)[0] = self.opts
         for k, v in kw.items():
-            if not hasattr(self.opts, k):
+            if not hasattr(new, k):
                 raise KeyError(k)
-            setattr(self.opts, k, v)
-        self._check(self.lib.sib_set_options(self.ctx, ctypes.byref(self.opts)))
+            setattr(new, k, v)
+        self._check(self.lib.sib_set_options(self.ctx, ctypes.byref(new)))
+        self.opts = new
 
     def set_eigen_estimates(self, lamA=None, lamM=None):
         if lamA is None:

@@ -129,10 +129,10 @@ def test_ras_stiff_disk_converges_where_vanka_caps():
 
 def test_ras_options_validated():
     """Box sides 1, 2, 4, 8; a subdomain (b + 2 o cells) at most 16 wide and narrower than level 1's
-    2 n_min cells, so that it never wraps onto itself; the tensor-core choice 0, 1 or 2."""
+    2 n_min cells, so that it never wraps onto itself; the tensor-core choice 0 or 1."""
     prob, H, S = pair("ellipse32")
     for kw in (dict(box=3), dict(box=16, box_overlap=0), dict(box=8, box_overlap=4), dict(box_overlap=-1),
-               dict(ras_tc=3), dict(ras_tc=-1)):
+               dict(ras_tc=2), dict(ras_tc=-1)):
         with pytest.raises(sib.SibError):
             S.set_options(**kw)
         S.set_options(box=4, box_overlap=1)
@@ -178,14 +178,13 @@ def test_ras_tensor_core_correction_matches_cuda_core_form(name, b, o):
         b32 = rand(3 * lev.n, 5900 + l, 10.0).astype(np.float32).astype(np.float64)
         ref = H.smooth(l, x32, b32, 1)
         outs = []
-        for tc in (2, 0):
+        for tc in (1, 0):
             S.set_options(ras_tc=tc)
             y = cu(x32, torch.float32)
             S.smooth(l, y, cu(b32, torch.float32), 1)
             outs.append(host(y))
         assert rel(outs[0], ref) < TOL32, (l, rel(outs[0], ref))
         assert rel(outs[0], outs[1]) < TOL32, (l, rel(outs[0], outs[1]))
-    S.set_options(ras_tc=2)
+    S.set_options(ras_tc=1)
     bb = system.rhs(prob).astype(np.float32).astype(np.float64)
     assert rel(host(S.vcycle(cu(bb, torch.float32))), H.vcycle(bb)) < 1e-4
-    S.set_options(ras_tc=1)

@@ -115,7 +115,7 @@ def test_wide_ras_tensor_core_correction_matches_cuda_core_form(name, b, o):
         b32 = rand(3 * lev.n, 6900 + l, 10.0).astype(np.float32).astype(np.float64)
         ref = H.smooth(l, x32, b32, 1)
         outs = []
-        for tc in (2, 0):
+        for tc in (1, 0):
             S.set_options(ras_tc=tc)
             y = cu(x32, torch.float32)
             S.smooth(l, y, cu(b32, torch.float32), 1)
