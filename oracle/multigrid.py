@@ -8,6 +8,11 @@ The coarsest level is solved exactly with the pseudo-inverse of the dense L^0, w
 orthonormal kernel basis Z as (L^0 + Z Z^T)^{-1} - Z Z^T (valid for symmetric L^0 whose kernel is
 exactly span Z), which is the gauge-fixed exact coarse solve.
 
+With the box RAS smoother, a level too small for the boxes (b does not divide N_l, or a subdomain's
+e + 1 = b + 2o + 1 face columns would wrap onto themselves: 16 x 16 boxes with overlap 4 on 16^2) is
+smoothed by the exact level solve with its gauge-fixed pseudo-inverse: the paper's cavity clips such a
+box to the domain (Sec. 5), which makes the one box the whole level (smoothers.exact_level_sweep).
+
 V-cycle (Alg. 1): on level l > 0 apply nu1 pre-smoothing sweeps, form r = b - L w, restrict,
 recurse with a zero initial guess, prolong and add the correction, apply nu2 post-smoothing
 sweeps; on level 0 solve exactly.
@@ -82,8 +87,13 @@ class Hierarchy:
                 lev.dofs = smoothers.vanka_patch_dofs(lev.N)
                 lev.patches = smoothers.vanka_patches(lev.L, lev.dofs)
             elif smoother == "ras":
-                lev.boxes = smoothers.ras_boxes(lev.N, box, overlap)
-                lev.factors = smoothers.ras_factors(lev.L, lev.boxes)
+                if smoothers.ras_wraps(lev.N, box, overlap):   # exact level solve (smoothers.exact_level_sweep)
+                    Z = system.null_basis(lev.N, self.rho)
+                    lev.pinv = np.linalg.inv(lev.L.toarray() + Z @ Z.T) - Z @ Z.T
+                    lev.boxes = None
+                else:
+                    lev.boxes = smoothers.ras_boxes(lev.N, box, overlap)
+                    lev.factors = smoothers.ras_factors(lev.L, lev.boxes)
             else:
                 lev.dA = lev.AIB.diagonal()
                 PA, PM, lev.dM = smoothers.sc_preconditioners(lev.AIB, lev.G, lev.D, lev.dA, sc_relax)
@@ -106,9 +116,14 @@ class Hierarchy:
         if self.smoother == "vanka":
             return smoothers.vanka_sweep(lev.L, lev.dofs, lev.patches, x, b, self.omega)
         if self.smoother == "ras":
-            return smoothers.ras_sweep(lev.L, lev.boxes, lev.factors, x, b, self.omega)
+            return self._ras(lev, x, b)
         return smoothers.sc_sweep(lev.L, lev.G, lev.D, lev.AIB, lev.dA, lev.dM, lev.lamA, lev.lamM,
                                   x, b, self.omega, self.cheb_iters, self.cheb_lo, self.cheb_hi, self.sc_relax)
+
+    def _ras(self, lev, x, b):
+        if lev.boxes is None:
+            return smoothers.exact_level_sweep(lev.L, lev.pinv, x, b, self.omega)
+        return smoothers.ras_sweep(lev.L, lev.boxes, lev.factors, x, b, self.omega)
 
     def smooth(self, l, x, b, sweeps):
         lev = self.levels[l]
@@ -120,7 +135,7 @@ class Hierarchy:
             if self.smoother == "vanka":
                 x = smoothers.vanka_sweep(lev.L, lev.dofs, lev.patches, x, b, self.omega)
             elif self.smoother == "ras":
-                x = smoothers.ras_sweep(lev.L, lev.boxes, lev.factors, x, b, self.omega)
+                x = self._ras(lev, x, b)
             else:
                 x = smoothers.sc_sweep(lev.L, lev.G, lev.D, lev.AIB, lev.dA, lev.dM, lev.lamA, lev.lamM,
                                        x, b, self.omega, self.cheb_iters, self.cheb_lo, self.cheb_hi,

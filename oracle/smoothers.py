@@ -117,6 +117,21 @@ def ras_factors(L, boxes):
     return [sla.lu_factor(Ld[d][:, d].toarray()) for d, _ in boxes]
 
 
+def ras_wraps(N, b, o):
+    """True where a b x b box with overlap o has no subdomain on an N x N level: b does not divide N, or
+    the e + 1 = b + 2o + 1 face columns of a subdomain would wrap onto themselves."""
+    return N % b != 0 or b + 2 * o + 1 > N
+
+
+def exact_level_sweep(L, pinv, x, b, omega):
+    """The RAS sweep's reading on a level too small for its boxes (`ras_wraps`): the box, clipped to the
+    periodic level, is the whole level, so its local solve is the exact level solve; the level operator
+    is singular (its kernel: the constant pressure, and the constant velocities when rho = 0), and the
+    solve is the gauge-fixed pseudo-inverse, as for the coarsest level:
+        x <- x + omega L^+ (b - L x)."""
+    return x + omega * (pinv @ (b - L @ x))
+
+
 def ras_sweep(L, boxes, factors, x, b, omega):
     """x <- x + omega sum_k Rt_k^T L_k^{-1} R_k (b - L x): every subdomain solves its local problem on
     the residual, and each dof takes the correction of the box that owns it."""

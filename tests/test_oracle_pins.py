@@ -658,6 +658,37 @@ def test_ras_fixed_point_and_convergent_vcycle():
     assert conv, it
 
 
+def test_ras_16x16_boxes_and_the_exact_level_reading():
+    """16 x 16 boxes with overlap 4 (Sec. 5.1.1, 5.2.1) on the 32^2 disk: level 2 (32^2) holds four
+    boxes of 1,776 dofs whose subdomains are the geometric extended squares and whose owned sets
+    partition the dofs; level 1 (16^2) is too small for them (`ras_wraps`), and its sweep is the exact
+    level solve: from any x, the new residual lies in the operator's kernel (constant pressure, and
+    constant velocities at rho = 0), and a second sweep leaves x unchanged up to that kernel.  The exact
+    solution is a fixed point on both levels."""
+    prob = I.disk_stokes(32, kappa=1e2, seed=1)
+    H = multigrid.Hierarchy(prob, smoother="ras", box=16, overlap=4)
+    lev2, lev1 = H.levels[2], H.levels[1]
+    assert lev1.boxes is None and smoothers.ras_wraps(16, 16, 4) and not smoothers.ras_wraps(32, 16, 4)
+    assert len(lev2.boxes) == 4 and all(len(d) == 3 * 24 * 24 + 2 * 24 for d, _ in lev2.boxes)
+    owners = np.zeros(3 * 32 * 32, dtype=int)
+    for d, own in lev2.boxes:
+        owners[d[own]] += 1
+    assert (owners == 1).all()
+    rng = np.random.default_rng(16)
+    x = rng.standard_normal(3 * lev1.n)
+    b = rng.standard_normal(3 * lev1.n)
+    y = H.smooth(1, x, b, 1)
+    r = b - lev1.L @ y
+    Z = system.null_basis(16, prob.rho)
+    assert np.abs(r - Z @ (Z.T @ r)).max() <= 1e-10 * np.abs(b).max()
+    y2 = H.smooth(1, y, b, 1)
+    assert np.abs(y2 - y).max() <= 1e-10 * np.abs(y).max()
+    L = system.operator_of(prob)
+    bf = system.rhs(prob)
+    xs, _ = system.solve_direct(L, bf, 32, prob.rho)
+    assert np.abs(H.smooth(2, xs, bf, 1) - xs).max() <= 1e-9 * np.abs(xs).max()
+
+
 # ------------------------------------------------ the paper's structures (Sec. 5.1, 5.2), periodic box
 def test_paper_structures_geometry():
     """Thick annulus: M1 = 19N/8 by M2 = 3N/32 + 1 markers on circles of radius r + s2_m, fibres closed
