@@ -51,6 +51,7 @@ L2_BYTES = 129 * 2 ** 20
 KAPPAS = [1e0, 1e2, 1e4, 1e6]
 SMOOTHERS = ["vanka", "sc"]
 WIDE_BOX = (8, 2)           # the paper's 8 x 8 boxes with overlap 2 (Sec. 5.1.1, 5.2.1)
+HUGE_BOX = (16, 4)          # and its 16 x 16 boxes with overlap 4
 # FGMRES iterations of the headline's forward and adjoint solves: the oracle's time per iteration is
 # scaled by these to the time of one differentiated solve (the CPU baseline is a bounded sample)
 HEAD_ITERATIONS = (38, 38)
@@ -493,11 +494,12 @@ def paper_workloads(sib, torch, dev):
     smoothers = {"vanka": dict(smoother=sib.SMOOTHER_VANKA), "sc": dict(smoother=sib.SMOOTHER_SC),
                  "ras4o1": dict(smoother=sib.SMOOTHER_RAS, box=4, box_overlap=1),
                  "ras2o2": dict(smoother=sib.SMOOTHER_RAS, box=2, box_overlap=2),
-                 "ras8o2": dict(smoother=sib.SMOOTHER_RAS, box=WIDE_BOX[0], box_overlap=WIDE_BOX[1])}
+                 "ras8o2": dict(smoother=sib.SMOOTHER_RAS, box=WIDE_BOX[0], box_overlap=WIDE_BOX[1]),
+                 "ras16o4": dict(smoother=sib.SMOOTHER_RAS, box=HUGE_BOX[0], box_overlap=HUGE_BOX[1])}
     runs = [(kind, 128, gamma, mu, sm) for kind in ("annulus", "circle") for mu in (None, 0.01)
             for gamma in (5.0, 50.0, 500.0) for sm in smoothers]
     runs += [("annulus", N, gamma, None, sm) for N in (64, 256) for gamma in (5.0, 500.0) for sm in ("vanka", "ras4o1")]
-    runs += [("circle", N, 500.0, None, "ras8o2") for N in (64, 256)]
+    runs += [("circle", N, 500.0, None, sm) for N in (64, 256) for sm in ("ras8o2", "ras16o4")]
     cases = []
     for kind, N, gamma, mu, sm in runs:
         prob = inputs.paper_problem(kind, N, gamma, mu)

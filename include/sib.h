@@ -84,9 +84,13 @@ typedef struct {
     int    sc_relax;      /* SC: point relaxation preconditioning both Chebyshev iterations (Sec. 3.3,
                              SC smoothing): SIB_RELAX_JACOBI (diagonal, default) or SIB_RELAX_SGS (one
                              symmetric red-black Gauss-Seidel sweep from zero, colours 0, 1, 1, 0)    */
-    int    box;           /* RAS: cells per box side b, 1, 2, 4 or 8 (4)                             */
-    int    box_overlap;   /* RAS: overlap o in cells on each side, b + 2 o <= 16 and
-                             b + 2 o < 2 n_min (1)                                                   */
+    int    box;           /* RAS: cells per box side b, 1, 2, 4, 8 or 16 (4)                         */
+    int    box_overlap;   /* RAS: overlap o in cells on each side: b + 2 o <= 16 for b <= 8, o <= 4
+                             for b = 16 (1).  A level too small for the boxes (b does not divide
+                             N_l, or b + 2 o + 1 > N_l: the subdomain would wrap onto itself) is
+                             smoothed by its exact level solve, x + omega L_l^+ (b - L_l x), the one
+                             box clipped to the periodic level; with b = 16 the IB boxes' subdomain
+                             inverses are a low-rank update of the shared one                       */
     int    domain;        /* SIB_DOMAIN_PERIODIC (default) or SIB_DOMAIN_CAVITY (see below)          */
     int    ras_tc;        /* RAS, FP32 levels: the correction of the boxes that share one inverse runs
                              on the tensor cores (tcgen05, three TF32 products per pair for FP32

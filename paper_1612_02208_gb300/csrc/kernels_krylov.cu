@@ -429,6 +429,28 @@ void launch_coarse_apply(const double* Pinv, int n, const T* b, T* x, cudaStream
 template void launch_coarse_apply<float>(const double*, int, const float*, float*, cudaStream_t);
 template void launch_coarse_apply<double>(const double*, int, const double*, double*, cudaStream_t);
 
+// xo = x + omega P r, one warp per row, FP64 accumulation (x == nullptr: 0)
+template <typename T>
+__global__ void k_dense_correct(const double* __restrict__ P, int n, const T* __restrict__ r, const T* x, T omega,
+                                T* xo) {
+    pdl_entry();
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= n) return;
+    const double* pr = P + (int64_t)row * n;
+    double s = 0.0;
+    for (int c = lane; c < n; c += 32) s += pr[c] * (double)r[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) xo[row] = (T)((x ? (double)x[row] : 0.0) + (double)omega * s);
+}
+template <typename T>
+void launch_dense_correct(const double* P, int n, const T* r, const T* x, T omega, T* xo, cudaStream_t s) {
+    launch_pdl(k_dense_correct<T>, (n + 7) / 8, 256, 0, s, P, n, r, x, omega, xo);
+}
+template void launch_dense_correct<float>(const double*, int, const float*, const float*, float, float*, cudaStream_t);
+template void launch_dense_correct<double>(const double*, int, const double*, const double*, double, double*,
+                                           cudaStream_t);
+
 __global__ void k_check_finite(const double* __restrict__ x, int64_t n, int* __restrict__ flag) {
     pdl_entry();
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)

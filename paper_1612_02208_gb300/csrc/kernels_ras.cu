@@ -806,7 +806,8 @@ static_assert(MAX_N <= (1 << 15), "k_ras_apply_tc packs a box origin's two coord
 template <int NC, int PF>
 __global__ void __launch_bounds__(RT_THREADS + 32, 1)
     k_ras_apply_tc(RasGeo G, const int* __restrict__ slotOfBox, const float* __restrict__ pack, int npad, int nch,
-                   int nsb, int ns, float omega, const float* __restrict__ r, const float* x, float* xo, int* err) {
+                   int nsb, int ns, int rowOff, float omega, const float* __restrict__ r, const float* x, float* xo,
+                   int* err) {
     extern __shared__ __align__(1024) unsigned char rt_smem[];
     __shared__ __align__(8) uint64_t tma_bar[RT_MAXSB];
     __shared__ __align__(8) uint64_t mma_bar[RT_MAXNS];    // the slot's MMAs are complete (one commit)
@@ -1054,7 +1055,7 @@ __global__ void __launch_bounds__(RT_THREADS + 32, 1)
 #pragma unroll
                                 for (int u = 0; u < 4; ++u) {
                                     const int l = 16 * h + (lane >> 2) + 8 * (u >> 1);   // box within the quadrant
-                                    const int rr = 8 * grp + 2 * (lane & 3) + (u & 1);    // owned row
+                                    const int rr = rowOff + 8 * grp + 2 * (lane & 3) + (u & 1);   // owned row
                                     const int comp = rr >> (2 * lb), rem = rr & (bb - 1);
                                     cc[u] = comp;
                                     dd[u] = (rr < nown && ((wmask >> l) & 1u))
@@ -1072,7 +1073,7 @@ __global__ void __launch_bounds__(RT_THREADS + 32, 1)
                         const size_t org0 = (size_t)(J * b) * N + (size_t)(I * b);
 #pragma unroll
                         for (int j = 0; j < NC; ++j) {
-                            const int rr = cbase + j;
+                            const int rr = rowOff + cbase + j;
                             if (j < q4 && rr < nown) {
                                 const int2 t = rowtab[rr];
                                 const size_t d = (size_t)t.x * n + org0 + (size_t)t.y;
@@ -1115,6 +1116,426 @@ __global__ void __launch_bounds__(RT_THREADS + 32, 1)
     __syncthreads();
     if (tid == 0 && s_err && err) *(volatile int*)err = SIB_DEV_ERR_TMA_WAIT;
     if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+// ---- 16 x 16 boxes: the shared inverse by the blocked Gauss-Jordan, and a low-rank (Woodbury)
+// update of it for the IB boxes ------------------------------------------------------------------
+// An IB box's local operator is L_k = L_0 + P E P^T: P selects the subdomain's IB-touched velocity dofs
+// T (rows with a nonzero window entry at a column of the subdomain), E = -dt B on T x T.  Then
+//   L_k^{-1} = L_0^{-1} - L_0^{-1} P W P^T L_0^{-1},   W = (I + E Q)^{-1} E,   Q = P^T L_0^{-1} P,
+// so an IB box's correction is the shared one minus (L_0^{-1})_{own,T} W (L_0^{-1})_{T,:} r_k.  Set-up
+// costs |T|^3 flops per IB box instead of ne^3, and |T|^2 words instead of ne nown.
+
+// Aug = [L_0 | I] (n x 2n, zeroed by the caller; n >= ne a multiple of 16, rows and columns past ne the
+// identity).  L_0 is the IB-free subdomain operator, the same for every box of the level.
+__global__ void k_ras_huge_assemble(RasGeo G, double a0, double c, double inv_h, int n, double* __restrict__ Aug) {
+    const RasIB none{nullptr, nullptr, 1, 1, 1};
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        double* row = Aug + (size_t)q * 2 * n;
+        if (q < G.ne)
+            ras_assemble_row(G, none, a0, c, inv_h, 0.0, false, 0, 0, q, row);
+        else
+            row[q] = 1.0;
+        row[n + q] = 1.0;
+    }
+}
+
+// the full inverse, row-major ne x ne: row r is Aug[piv[r]][n ..] (the elimination swaps no rows)
+__global__ void k_ras_huge_extract(const double* __restrict__ Aug, const int* __restrict__ piv, int n, int ne,
+                                   double* __restrict__ inv64, float* __restrict__ inv32) {
+    const int r = blockIdx.y;
+    const double* src = Aug + (size_t)piv[r] * 2 * n + n;
+    for (int cc = blockIdx.x * blockDim.x + threadIdx.x; cc < ne; cc += gridDim.x * blockDim.x) {
+        const double v = src[cc];
+        inv64[(size_t)r * ne + cc] = v;
+        inv32[(size_t)r * ne + cc] = (float)v;
+    }
+}
+
+// whether local dof q of the subdomain with corner (i0, j0) is IB-touched: a velocity face with a
+// nonzero window entry at a column of the subdomain
+__device__ bool ras_ib_row(const RasGeo& G, const RasIB& ib, int i0, int j0, int q) {
+    int comp, ii, jj;
+    ras_dof(G, q, comp, ii, jj);
+    if (comp == 2) return false;
+    const int m = G.N - 1, per = ib.tx * ib.ty;
+    const int gi = (i0 + ii) & m, gj = (j0 + jj) & m;
+    const int slot = face_slot(ib, gi, gj);
+    if (slot < 0) return false;
+    const double* w = ib.win + ((size_t)(slot * 2 + comp) * WIN_SIZE) * per;
+    const int qt = (gj % ib.ty) * ib.tx + (gi % ib.tx);
+    for (int dj = -WR; dj <= WR; ++dj)
+        for (int di = -WR; di <= WR; ++di)
+            if (w[(size_t)((dj + WR) * WD + (di + WR)) * per + qt] != 0.0 &&
+                ras_index(G, comp, (ii + di) & m, (jj + dj) & m) >= 0)
+                return true;
+    return false;
+}
+
+// |T| of each listed IB box (one block per box)
+__global__ void k_ras_wb_count(RasGeo G, RasIB ib, const int* __restrict__ list, int* __restrict__ cnt) {
+    __shared__ int total;
+    const int k = list[blockIdx.x];
+    const int i0 = (k % G.nbs) * G.b - G.o, j0 = (k / G.nbs) * G.b - G.o;
+    if (threadIdx.x == 0) total = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int q = threadIdx.x; q < 2 * G.e * (G.e + 1); q += blockDim.x) mine += ras_ib_row(G, ib, i0, j0, q) ? 1 : 0;
+    if (mine) atomicAdd(&total, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) cnt[blockIdx.x] = total;
+}
+
+// the T lists, ascending local dof (one block per box; an ordered compaction over chunks of dofs)
+__global__ void k_ras_wb_fill(RasGeo G, RasIB ib, const int* __restrict__ list, const int* __restrict__ offT,
+                              int* __restrict__ T) {
+    __shared__ int wcount[32], woff[32], base;
+    const int k = list[blockIdx.x];
+    const int i0 = (k % G.nbs) * G.b - G.o, j0 = (k / G.nbs) * G.b - G.o;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nv = 2 * G.e * (G.e + 1);
+    int* out = T + offT[blockIdx.x];
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int q0 = 0; q0 < nv; q0 += blockDim.x) {
+        const int q = q0 + threadIdx.x;
+        const bool f = q < nv && ras_ib_row(G, ib, i0, j0, q);
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wcount[warp] = __popc(bal);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = base;
+            for (int w = 0; w < nw; ++w) {
+                woff[w] = acc;
+                acc += wcount[w];
+            }
+            base = acc;
+        }
+        __syncthreads();
+        if (f) out[woff[warp] + __popc(bal & ((1u << lane) - 1u))] = q;
+        __syncthreads();
+    }
+}
+
+// One block per IB box: Mx = [I + E Q | E] (m x 2m, row-major, at work + 2 offW), eliminated by
+// Gauss-Jordan with partial (row) pivoting to [I | W]; W (m x m, row-major) is stored at offW.
+// E = -dt B on T x T (the window entries), Q = (L_0^{-1})_{T,T} from the full shared inverse.
+// info != 0 on a zero pivot.
+constexpr int RAS_WB_THREADS = 256;
+__global__ void __launch_bounds__(RAS_WB_THREADS)
+    k_ras_wb_setup(RasGeo G, RasIB ib, double dt, const int* __restrict__ list, const int* __restrict__ offT,
+                   const int* __restrict__ Tl, const long long* __restrict__ offW, const double* __restrict__ inv0,
+                   double* __restrict__ work, double* __restrict__ W, int* __restrict__ info) {
+    extern __shared__ double smem_wb[];
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int k = list[blockIdx.x];
+    const int i0 = (k % G.nbs) * G.b - G.o, j0 = (k / G.nbs) * G.b - G.o;
+    const int t0 = offT[blockIdx.x], m = offT[blockIdx.x + 1] - t0, n2 = 2 * m;
+    const int* Ts = Tl + t0;
+    double* Mx = work + 2 * offW[blockIdx.x];
+    double* rowk = smem_wb;                           // 2m: pivot row after scaling
+    double* colk = rowk + n2;                         // m: pivot column before the step
+    double* redv = colk + m;                          // 32
+    int* redi = reinterpret_cast<int*>(redv + 32);    // 32
+    int* ent = redi + 32;                             // nw x WIN_SIZE: a row's nonzero positions in T
+    double* ev = reinterpret_cast<double*>(ent + nw * WIN_SIZE + (nw * WIN_SIZE & 1));   // nw x WIN_SIZE values
+    __shared__ int pivS;
+    for (size_t t = tid; t < (size_t)m * n2; t += nt) Mx[t] = 0.0;
+    __syncthreads();
+    const int mk = G.N - 1, per = ib.tx * ib.ty;
+    for (int a = warp; a < m; a += nw) {   // one warp per row a: E's row, then I + E Q's row
+        int* me = ent + warp * WIN_SIZE;
+        double* mv = ev + warp * WIN_SIZE;
+        int comp, ii, jj;
+        ras_dof(G, Ts[a], comp, ii, jj);
+        const int gi = (i0 + ii) & mk, gj = (j0 + jj) & mk;
+        const int slot = face_slot(ib, gi, gj);
+        int cnt = 0;
+        if (slot >= 0) {
+            const double* w = ib.win + ((size_t)(slot * 2 + comp) * WIN_SIZE) * per;
+            const int qt = (gj % ib.ty) * ib.tx + (gi % ib.tx);
+            for (int kw0 = 0; kw0 < WIN_SIZE; kw0 += 32) {   // window entries whose column is in T
+                const int kw = kw0 + lane;
+                int pos = -1;
+                double coef = 0.0;
+                if (kw < WIN_SIZE) {
+                    const int dj = kw / WD - WR, di = kw % WD - WR;
+                    coef = w[(size_t)kw * per + qt];
+                    const int col = ras_index(G, comp, (ii + di) & mk, (jj + dj) & mk);
+                    if (coef != 0.0 && col >= 0) {
+                        int lo = 0, hi = m;   // lower bound of col in the ascending T
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (Ts[mid] < col) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        if (lo < m && Ts[lo] == col) pos = lo;
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, pos >= 0);
+                if (pos >= 0) {
+                    const int at = cnt + __popc(bal & ((1u << lane) - 1u));
+                    me[at] = pos;
+                    mv[at] = -dt * coef;
+                }
+                cnt += __popc(bal);
+            }
+        }
+        __syncwarp();
+        double* Ma = Mx + (size_t)a * n2;
+        for (int t = lane; t < cnt; t += 32) Ma[m + me[t]] += mv[t];   // distinct positions per row
+        for (int bcol = lane; bcol < m; bcol += 32) {
+            const int Tb = Ts[bcol];
+            double acc = a == bcol ? 1.0 : 0.0;
+            for (int t = 0; t < cnt; ++t) acc += mv[t] * inv0[(size_t)Ts[me[t]] * G.ne + Tb];
+            Ma[bcol] = acc;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int kk = 0; kk < m; ++kk) {
+        double best = -1.0;
+        int bi = kk;
+        for (int i = kk + tid; i < m; i += nt) {
+            const double v = fabs(Mx[(size_t)i * n2 + kk]);
+            if (v > best) {
+                best = v;
+                bi = i;
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+            if (ov > best || (ov == best && oi < bi)) {
+                best = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            redv[warp] = best;
+            redi[warp] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double bv = redv[0];
+            int bx = redi[0];
+            for (int w2 = 1; w2 < nw; ++w2)
+                if (redv[w2] > bv || (redv[w2] == bv && redi[w2] < bx)) {
+                    bv = redv[w2];
+                    bx = redi[w2];
+                }
+            pivS = bx;
+            if (!(bv > 0.0)) atomicExch(info, 1);
+        }
+        __syncthreads();
+        const int p = pivS;
+        if (p != kk)
+            for (int j = kk + tid; j < n2; j += nt) {
+                const double t = Mx[(size_t)kk * n2 + j];
+                Mx[(size_t)kk * n2 + j] = Mx[(size_t)p * n2 + j];
+                Mx[(size_t)p * n2 + j] = t;
+            }
+        __syncthreads();
+        const double piv = Mx[(size_t)kk * n2 + kk];
+        const double pinv = piv != 0.0 ? 1.0 / piv : 0.0;
+        for (int i = tid; i < m; i += nt) colk[i] = Mx[(size_t)i * n2 + kk];
+        for (int j = kk + tid; j < n2; j += nt) rowk[j] = Mx[(size_t)kk * n2 + j] * pinv;
+        __syncthreads();
+        for (size_t t = tid; t < (size_t)m * (n2 - kk); t += nt) {
+            const int i = (int)(t / (n2 - kk)), j = kk + (int)(t % (n2 - kk));
+            Mx[(size_t)i * n2 + j] = i == kk ? rowk[j] : Mx[(size_t)i * n2 + j] - colk[i] * rowk[j];
+        }
+        __syncthreads();
+    }
+    double* Wb = W + offW[blockIdx.x];
+    for (size_t t = tid; t < (size_t)m * m; t += nt) Wb[t] = Mx[(t / m) * n2 + m + t % m];
+}
+
+// Shared correction of every box with 16 x 16 boxes, on the CUDA cores: a block takes RH_BX boxes,
+// gathers their windows into shared memory, and each warp walks owned rows: row own(r) of the shared
+// inverse, read once per block, against the RH_BX windows.  xo(owned) = x(owned) + omega c
+// (x == nullptr: 0).
+constexpr int RH_BX = 8, RH_THREADS = 256;
+template <typename T>
+__global__ void __launch_bounds__(RH_THREADS)
+    k_ras_huge_apply(RasGeo G, const T* __restrict__ inv, T omega, const T* __restrict__ r, const T* x, T* xo) {
+    extern __shared__ unsigned char smem_rh[];
+    T* win = reinterpret_cast<T*>(smem_rh);   // RH_BX x ne
+    const int N = G.N, n = N * N, m = N - 1, ne = G.ne;
+    const int nboxes = G.nbs * G.nbs, k0 = blockIdx.x * RH_BX;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    pdl_entry();
+    for (int t = threadIdx.x; t < RH_BX * ne; t += blockDim.x) {
+        const int j = t / ne, q = t - j * ne, kb = k0 + j;
+        T v = T(0);
+        if (kb < nboxes) {
+            int comp, ii, jj;
+            ras_dof(G, q, comp, ii, jj);
+            const int gi = ((kb % G.nbs) * G.b - G.o + ii) & m, gj = ((kb / G.nbs) * G.b - G.o + jj) & m;
+            v = r[(size_t)comp * n + (size_t)gj * N + gi];
+        }
+        win[t] = v;
+    }
+    __syncthreads();
+    for (int rr = warp; rr < G.nown; rr += nw) {
+        const T* row = inv + (size_t)ras_owned(G, rr) * ne;
+        T acc[RH_BX];
+#pragma unroll
+        for (int j = 0; j < RH_BX; ++j) acc[j] = T(0);
+        for (int q = lane; q < ne; q += 32) {
+            const T a = row[q];
+#pragma unroll
+            for (int j = 0; j < RH_BX; ++j) acc[j] += a * win[j * ne + q];
+        }
+#pragma unroll
+        for (int j = 0; j < RH_BX; ++j)
+            for (int off = 16; off > 0; off >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], off);
+        if (lane < RH_BX && k0 + lane < nboxes) {
+            T a = acc[0];
+#pragma unroll
+            for (int j = 1; j < RH_BX; ++j)
+                if (lane == j) a = acc[j];
+            const int kb = k0 + lane, bb = G.b * G.b;
+            const int comp = rr / bb, rem = rr - comp * bb;
+            const size_t d = (size_t)comp * n + (size_t)((kb / G.nbs) * G.b + rem / G.b) * N + (kb % G.nbs) * G.b +
+                             rem % G.b;
+            xo[d] = (x ? x[d] : T(0)) + omega * a;
+        }
+    }
+}
+
+// (L_k v)_q for the subdomain with corner (i0, j0): the entries of ras_assemble_row (withIB: with the IB
+// windows' -dt B), applied to v without forming the row
+__device__ double ras_row_dot(const RasGeo& G, const RasIB& ib, double a0, double c, double inv_h, double dt,
+                              int i0, int j0, int q, const double* v) {
+    const int m = G.N - 1, per = ib.tx * ib.ty;
+    int comp, ii, jj;
+    ras_dof(G, q, comp, ii, jj);
+    double acc = 0.0;
+    if (comp < 2) {
+        acc = a0 * v[q];
+        const int nb[4][2] = {{ii + 1, jj}, {ii - 1, jj}, {ii, jj + 1}, {ii, jj - 1}};
+        for (int s2 = 0; s2 < 4; ++s2) {
+            const int col = ras_index(G, comp, nb[s2][0] & m, nb[s2][1] & m);
+            if (col >= 0) acc -= c * v[col];
+        }
+        const int pc = ras_index(G, 2, ii, jj);
+        const int pm = comp == 0 ? ras_index(G, 2, ii - 1, jj) : ras_index(G, 2, ii, jj - 1);
+        if (pc >= 0) acc += inv_h * v[pc];
+        if (pm >= 0) acc -= inv_h * v[pm];
+        const int gi = (i0 + ii) & m, gj = (j0 + jj) & m;
+        const int slot = face_slot(ib, gi, gj);
+        if (slot >= 0) {
+            const double* w = ib.win + ((size_t)(slot * 2 + comp) * WIN_SIZE) * per;
+            const int qt = (gj % ib.ty) * ib.tx + (gi % ib.tx);
+            for (int dj = -WR; dj <= WR; ++dj)
+                for (int di = -WR; di <= WR; ++di) {
+                    const int col = ras_index(G, comp, (ii + di) & m, (jj + dj) & m);
+                    if (col >= 0) acc -= dt * w[(size_t)((dj + WR) * WD + (di + WR)) * per + qt] * v[col];
+                }
+        }
+    } else {
+        acc = -inv_h * v[ras_index(G, 0, ii + 1, jj)] + inv_h * v[ras_index(G, 0, ii, jj)] -
+              inv_h * v[ras_index(G, 1, ii, jj + 1)] + inv_h * v[ras_index(G, 1, ii, jj)];
+    }
+    return acc;
+}
+
+// IB boxes with 16 x 16 boxes, one block per box, in FP64, after the shared correction wrote
+// xo = x + omega (L_0^{-1} r_k)(owned) for every box.  The box's own local solve delta = L_k^{-1} r_k comes
+// from the Woodbury form M r = y - (L_0^{-1})_{:,T} W y_T, y = L_0^{-1} r, refined once against the
+// local operator itself: delta_0 = M r_k, delta = delta_0 + M (r_k - L_k delta_0).  With a stiff structure
+// W is large and the two terms of M nearly cancel; the refinement recovers the digits they lose.  Then
+// xo(owned) += omega (delta - L_0^{-1} r_k)(owned).  L_0^{-1} is symmetric (L_0 is), so its columns T are
+// read as rows.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_ras_wb_apply(RasGeo G, RasIB ib, double a0, double c, double inv_h, double dt, const int* __restrict__ list,
+                   const int* __restrict__ offT, const int* __restrict__ Tl, const long long* __restrict__ offW,
+                   const double* __restrict__ Wd, const double* __restrict__ inv0, T omega, const T* __restrict__ r,
+                   T* xo) {
+    extern __shared__ double smem_wa[];
+    const int N = G.N, n = N * N, mk = N - 1, ne = G.ne;
+    const int k = list[blockIdx.x];
+    const int I = k % G.nbs, J = k / G.nbs, i0 = I * G.b - G.o, j0 = J * G.b - G.o;
+    const int t0 = offT[blockIdx.x], m = offT[blockIdx.x + 1] - t0;
+    const int* Ts = Tl + t0;
+    const double* Wb = Wd + offW[blockIdx.x];
+    double* rk = smem_wa;     // ne: r_k, then the refinement's residual
+    double* y0 = rk + ne;     // ne: L_0^{-1} r_k
+    double* d0 = y0 + ne;     // ne: delta_0
+    double* y1 = d0 + ne;     // ne: L_0^{-1} of the residual
+    double* z = y1 + ne;      // m
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    pdl_entry();
+    for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+        int comp, ii, jj;
+        ras_dof(G, q, comp, ii, jj);
+        rk[q] = (double)r[(size_t)comp * n + (size_t)((j0 + jj) & mk) * N + ((i0 + ii) & mk)];
+    }
+    __syncthreads();
+    // out = M in (full vector); y holds L_0^{-1} in on return
+    auto woodbury = [&](const double* in, double* y, double* out) {
+        for (int q = warp; q < ne; q += nw) {   // y = L_0^{-1} in
+            const double* row = inv0 + (size_t)q * ne;
+            double acc = 0.0;
+            for (int t = lane; t < ne; t += 32) acc += row[t] * in[t];
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if (lane == 0) y[q] = acc;
+        }
+        __syncthreads();
+        for (int a = warp; a < m; a += nw) {   // z = W y_T
+            const double* row = Wb + (size_t)a * m;
+            double acc = 0.0;
+            for (int t = lane; t < m; t += 32) acc += row[t] * y[Ts[t]];
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if (lane == 0) z[a] = acc;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < ne; q += blockDim.x) {   // out = y - (L_0^{-1})_{:,T} z
+            double acc = 0.0;
+            for (int a = 0; a < m; ++a) acc += inv0[(size_t)Ts[a] * ne + q] * z[a];
+            out[q] = y[q] - acc;
+        }
+        __syncthreads();
+    };
+    woodbury(rk, y0, d0);
+    for (int q = threadIdx.x; q < ne; q += blockDim.x)   // the residual of delta_0 in the local problem
+        y1[q] = rk[q] - ras_row_dot(G, ib, a0, c, inv_h, dt, i0, j0, q, d0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < ne; q += blockDim.x) rk[q] = y1[q];
+    __syncthreads();
+    woodbury(rk, y1, rk);   // rk <- M (residual)
+    const int bb = G.b * G.b;
+    for (int rr = threadIdx.x; rr < G.nown; rr += blockDim.x) {
+        const int q = ras_owned(G, rr);
+        const int comp = rr / bb, rem = rr - comp * bb;
+        const size_t d = (size_t)comp * n + (size_t)(J * G.b + rem / G.b) * N + I * G.b + rem % G.b;
+        xo[d] = (T)((double)xo[d] + (double)omega * (d0[q] + rk[q] - y0[q]));
+    }
+}
+
+// Packs owned rows rowOff .. rowOff + npad - 1 of the full shared inverse (row-major ne x ne) for the
+// tensor-core correction, in the layout of k_ras_tc_pack (rows past nown hold zeros)
+__global__ void k_ras_tc_pack_rows(RasGeo G, const double* __restrict__ inv0, int rowOff, int npad, int nch,
+                                   float* __restrict__ out) {
+    const int chunkWords = rt_bbytes(npad) / 4;
+    const int64_t total = (int64_t)nch * 2 * chunkWords;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx / (2 * chunkWords));
+        const int rem = (int)(idx - (int64_t)c * 2 * chunkWords);
+        const int part = rem / chunkWords, byte = (rem - part * chunkWords) * 4;
+        const int grp = byte / RT_BSBO, b2 = byte - grp * RT_BSBO, k4 = b2 / RT_BLBO, b3 = b2 - k4 * RT_BLBO;
+        const int row = rowOff + grp * 8 + b3 / 16, q = c * RT_KC + k4 * 4 + (b3 & 15) / 4;
+        float val = 0.0f;
+        if (row < G.nown && q < G.ne) {
+            const double v = inv0[(size_t)ras_owned(G, row) * G.ne + q];
+            const float hi = tf32_rna((float)v);
+            val = part == 0 ? hi : tf32_rna((float)(v - (double)hi));
+        }
+        out[idx] = val;
+    }
 }
 
 }  // namespace
@@ -1189,9 +1610,9 @@ void launch_ras_tc_pack(int b, int o, const double* inv64, float* pack, cudaStre
 // as many inverse stages as the shared memory holds (all nch chunks where they fit).  False, and nothing
 // launched, where the shared memory cannot hold two inverse stages.
 bool launch_ras_apply_tc(int N, int b, int o, const int* slotOfBox, const float* pack, float omega, const float* r,
-                         const float* x, float* xo, int* err, cudaStream_t s) {
+                         const float* x, float* xo, int* err, cudaStream_t s, int rowOff = 0, int npadGroup = 0) {
     const RasGeo G = ras_geo(N, b, o);
-    const int npad = ras_tc_npad(b), nch = (G.ne + RT_KC - 1) / RT_KC;
+    const int npad = npadGroup > 0 ? npadGroup : ras_tc_npad(b), nch = (G.ne + RT_KC - 1) / RT_KC;
     // owned rows per thread, rounded up to whole TMEM loads; narrow boxes keep two chunks of residual
     // loads in flight, 8 x 8 boxes (48 rows a thread) one
     const int nc = npad / 4 <= 16 ? 16 : 48;
@@ -1232,10 +1653,98 @@ bool launch_ras_apply_tc(int N, int b, int o, const int* slotOfBox, const float*
     const int ntiles = (G.nbs * G.nbs + RT_NB - 1) / RT_NB;
     const dim3 grd(std::min(ntiles, sms)), blk(RT_THREADS + 32);   // 16 worker warps and the issuing warp
     if (nc == 16)
-        launch_pdl(k_ras_apply_tc<16, 2>, grd, blk, smem, s, G, slotOfBox, pack, npad, nch, nsb, ns, omega, r, x, xo, err);
+        launch_pdl(k_ras_apply_tc<16, 2>, grd, blk, smem, s, G, slotOfBox, pack, npad, nch, nsb, ns, rowOff, omega, r, x,
+                   xo, err);
     else
-        launch_pdl(k_ras_apply_tc<48, 1>, grd, blk, smem, s, G, slotOfBox, pack, npad, nch, nsb, ns, omega, r, x, xo, err);
+        launch_pdl(k_ras_apply_tc<48, 1>, grd, blk, smem, s, G, slotOfBox, pack, npad, nch, nsb, ns, rowOff, omega, r, x,
+                   xo, err);
     return true;
+}
+
+// ---- 16 x 16 boxes --------------------------------------------------------------------------
+bool ras_huge(int b) { return b == RAS_BOX_HUGE; }
+int ras_huge_n(int b, int o) { return (ras_ne(b, o) + 15) / 16 * 16; }
+void launch_ras_huge_assemble(int N, int b, int o, double a0, double c, double inv_h, double* Aug, cudaStream_t s) {
+    const RasGeo G = ras_geo(N, b, o);
+    const int n = ras_huge_n(b, o);
+    cudaMemsetAsync(Aug, 0, sizeof(double) * (size_t)n * 2 * n, s);
+    k_ras_huge_assemble<<<(n + 255) / 256, 256, 0, s>>>(G, a0, c, inv_h, n, Aug);
+}
+void launch_ras_huge_extract(const double* Aug, const int* piv, int b, int o, double* inv64, float* inv32,
+                             cudaStream_t s) {
+    const int ne = ras_ne(b, o), n = ras_huge_n(b, o);
+    k_ras_huge_extract<<<dim3((ne + 255) / 256, ne), 256, 0, s>>>(Aug, piv, n, ne, inv64, inv32);
+}
+void launch_ras_wb_count(int N, int b, int o, const RasIB& ib, const int* list, int nIB, int* cnt, cudaStream_t s) {
+    if (nIB > 0) k_ras_wb_count<<<nIB, 256, 0, s>>>(ras_geo(N, b, o), ib, list, cnt);
+}
+void launch_ras_wb_fill(int N, int b, int o, const RasIB& ib, const int* list, int nIB, const int* offT, int* T,
+                        cudaStream_t s) {
+    if (nIB > 0) k_ras_wb_fill<<<nIB, 256, 0, s>>>(ras_geo(N, b, o), ib, list, offT, T);
+}
+void launch_ras_wb_setup(int N, int b, int o, const RasIB& ib, double dt, const int* list, int nIB, const int* offT,
+                         const int* T, const long long* offW, const double* inv0, double* work, double* W, int* info,
+                         int mmax, cudaStream_t s) {
+    if (nIB <= 0) return;
+    const int nw = RAS_WB_THREADS / 32;
+    const size_t smem = sizeof(double) * (3 * (size_t)mmax + 32) +
+                        sizeof(int) * (32 + nw * WIN_SIZE + ((nw * WIN_SIZE) & 1)) + sizeof(double) * nw * WIN_SIZE;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_ras_wb_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ras_wb_setup<<<nIB, RAS_WB_THREADS, smem, s>>>(ras_geo(N, b, o), ib, dt, list, offT, T, offW, inv0, work, W,
+                                                     info);
+}
+template <typename T>
+void launch_ras_huge_apply(int N, int b, int o, const T* inv, T omega, const T* r, const T* x, T* xo, cudaStream_t s) {
+    const RasGeo G = ras_geo(N, b, o);
+    const size_t smem = sizeof(T) * RH_BX * (size_t)G.ne;
+    static thread_local size_t allowed = 48 * 1024;
+    if (smem > allowed) {
+        cudaFuncSetAttribute(k_ras_huge_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allowed = smem;
+    }
+    launch_pdl(k_ras_huge_apply<T>, dim3((G.nbs * G.nbs + RH_BX - 1) / RH_BX), dim3(RH_THREADS), smem, s, G, inv, omega,
+               r, x, xo);
+}
+template void launch_ras_huge_apply<float>(int, int, int, const float*, float, const float*, const float*, float*,
+                                           cudaStream_t);
+template void launch_ras_huge_apply<double>(int, int, int, const double*, double, const double*, const double*,
+                                            double*, cudaStream_t);
+template <typename T>
+void launch_ras_wb_apply(int N, int b, int o, const RasIB& ib, double a0, double c, double inv_h, double dt,
+                         const int* list, int nIB, const int* offT, const int* Tl, const long long* offW,
+                         const double* W, const double* inv0, int mmax, T omega, const T* r, T* xo, cudaStream_t s) {
+    if (nIB <= 0) return;
+    const RasGeo G = ras_geo(N, b, o);
+    const size_t smem = sizeof(double) * (4 * (size_t)G.ne + (size_t)mmax);
+    static thread_local size_t allowed = 48 * 1024;
+    if (smem > allowed) {
+        cudaFuncSetAttribute(k_ras_wb_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allowed = smem;
+    }
+    launch_pdl(k_ras_wb_apply<T>, dim3(nIB), dim3(256), smem, s, G, ib, a0, c, inv_h, dt, list, offT, Tl, offW, W,
+               inv0, omega, r, xo);
+}
+template void launch_ras_wb_apply<float>(int, int, int, const RasIB&, double, double, double, double, const int*, int,
+                                         const int*, const int*, const long long*, const double*, const double*, int,
+                                         float, const float*, float*, cudaStream_t);
+template void launch_ras_wb_apply<double>(int, int, int, const RasIB&, double, double, double, double, const int*,
+                                          int, const int*, const int*, const long long*, const double*,
+                                          const double*, int, double, const double*, double*, cudaStream_t);
+size_t ras_tc_group_floats(int b, int o) {
+    const RasGeo G = ras_geo(16, b, o);
+    const int nch = (G.ne + RT_KC - 1) / RT_KC;
+    return (size_t)nch * 2 * rt_bbytes(RAS_TC_GROUP) / 4;
+}
+void launch_ras_tc_pack_rows(int b, int o, const double* inv0, int g, float* out, cudaStream_t s) {
+    const RasGeo G = ras_geo(16, b, o);
+    const int nch = (G.ne + RT_KC - 1) / RT_KC;
+    const int64_t total = (int64_t)ras_tc_group_floats(b, o);
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+    k_ras_tc_pack_rows<<<blocks, 256, 0, s>>>(G, inv0, g * RAS_TC_GROUP, RAS_TC_GROUP, nch, out);
+}
+bool launch_ras_apply_tc_group(int N, int b, int o, const float* pack, int g, float omega, const float* r,
+                               const float* x, float* xo, int* err, cudaStream_t s) {
+    return launch_ras_apply_tc(N, b, o, nullptr, pack, omega, r, x, xo, err, s, g * RAS_TC_GROUP, RAS_TC_GROUP);
 }
 
 template <typename T>

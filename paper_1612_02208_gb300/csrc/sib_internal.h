@@ -143,6 +143,33 @@ void launch_ras_apply(int N, int b, int o, const int* slotOfBox, const int* list
 // TF32 parts in K-major chunks of 32 dofs; ras_tc_pack_floats gives its size
 size_t ras_tc_pack_floats(int b, int o);
 void launch_ras_tc_pack(int b, int o, const double* inv64, float* pack, cudaStream_t s);
+// 16 x 16 boxes (subdomains up to 24 cells, ne <= 1,776): the full shared inverse of the IB-free
+// subdomain operator by the blocked Gauss-Jordan (order ras_huge_n, ne padded to a multiple of 16) and a
+// low-rank (Woodbury) update of it for the IB boxes: T lists (IB-touched dofs, ascending), W = (I + E Q)^-1 E
+// per box (row-major |T| x |T| at offW); the shared correction of every box, then the IB boxes' update
+constexpr int RAS_BOX_HUGE = 16;
+constexpr int RAS_TC_GROUP = 192;   // owned rows per tensor-core launch with 16 x 16 boxes (768 = 4 x 192)
+bool ras_huge(int b);
+int ras_huge_n(int b, int o);
+void launch_ras_huge_assemble(int N, int b, int o, double a0, double c, double inv_h, double* Aug, cudaStream_t s);
+void launch_ras_huge_extract(const double* Aug, const int* piv, int b, int o, double* inv64, float* inv32,
+                             cudaStream_t s);
+void launch_ras_wb_count(int N, int b, int o, const RasIB& ib, const int* list, int nIB, int* cnt, cudaStream_t s);
+void launch_ras_wb_fill(int N, int b, int o, const RasIB& ib, const int* list, int nIB, const int* offT, int* T,
+                        cudaStream_t s);
+void launch_ras_wb_setup(int N, int b, int o, const RasIB& ib, double dt, const int* list, int nIB, const int* offT,
+                         const int* T, const long long* offW, const double* inv0, double* work, double* W, int* info,
+                         int mmax, cudaStream_t s);
+template <typename T>
+void launch_ras_huge_apply(int N, int b, int o, const T* inv, T omega, const T* r, const T* x, T* xo, cudaStream_t s);
+template <typename T>
+void launch_ras_wb_apply(int N, int b, int o, const RasIB& ib, double a0, double c, double inv_h, double dt,
+                         const int* list, int nIB, const int* offT, const int* Tl, const long long* offW,
+                         const double* W, const double* inv0, int mmax, T omega, const T* r, T* xo, cudaStream_t s);
+size_t ras_tc_group_floats(int b, int o);
+void launch_ras_tc_pack_rows(int b, int o, const double* inv0, int g, float* out, cudaStream_t s);
+bool launch_ras_apply_tc_group(int N, int b, int o, const float* pack, int g, float omega, const float* r,
+                               const float* x, float* xo, int* err, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
 // Levels 1 and 0 of the V-cycle in one thread block (kernels_small.cu).
@@ -332,6 +359,10 @@ size_t gauss_jordan_work_bytes(int n);
 void launch_gauss_jordan(double* Aug, int n, int* info, int* piv, void* work, cudaStream_t s);
 void launch_extract_pinv(const double* Aug, const int* piv, int n, int N0, double rho, double* Pinv, cudaStream_t s);
 template <typename T> void launch_coarse_apply(const double* Pinv, int n, const T* b, T* x, cudaStream_t s);
+// xo = x + omega P r (x == nullptr: 0), P dense n x n FP64: the exact level solve of a level too small
+// for the RAS boxes
+template <typename T>
+void launch_dense_correct(const double* P, int n, const T* r, const T* x, T omega, T* xo, cudaStream_t s);
 void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t s);
 
 void launch_fg_init(FgDev* st, double beta, int m, int max_it, double tol, cudaStream_t s);

@@ -91,6 +91,16 @@ struct Level {
     int rasNIB = 0;                      // boxes with their own inverse
     float* rasTC = nullptr;              // the shared inverse packed for the tensor-core correction
     size_t rasTCCap = 0;                 // floats
+    // a level too small for the boxes: the exact level solve (gauge-fixed pseudo-inverse, FP64)
+    bool rasExact = false;
+    double* rasPinv = nullptr;
+    // 16 x 16 boxes: the full shared inverse (ne x ne, FP64 and FP32) and the IB boxes' Woodbury data
+    void* hugeInv[2] = {nullptr, nullptr};
+    int* wbOffT = nullptr;               // nIB + 1 offsets into wbT
+    int* wbT = nullptr;                  // the IB-touched local dofs of every IB box, ascending
+    long long* wbOffW = nullptr;         // nIB offsets into wbW
+    double* wbW = nullptr;               // W = (I + E Q)^-1 E per IB box
+    int wbMmax = 0;                      // largest |T|
 };
 
 struct sib_ctx {
@@ -521,6 +531,32 @@ template <typename T>
 void ras_apply(sib_ctx* c, int l, const T* r, const T* x, T* xo, double omega, cudaStream_t s) {
     Level& lv = c->L[l];
     const int pi = Prec<T>::id;
+    const int b = c->opts.box, o = c->opts.box_overlap;
+    if (lv.rasExact) {   // a level too small for the boxes: the exact level solve
+        KL(c, launch_dense_correct<T>(lv.rasPinv, 3 * lv.N * lv.N, r, x, (T)omega, xo, s));
+        return;
+    }
+    if (ras_huge(b)) {   // 16 x 16 boxes: the shared correction of every box, then the IB boxes' update
+        bool done = false;
+        if (Prec<T>::id == 1 && c->opts.ras_tc) {
+            const size_t gf = ras_tc_group_floats(b, o);
+            done = true;
+            for (int g = 0; g < 3 * b * b / RAS_TC_GROUP && done; ++g) {
+                done = launch_ras_apply_tc_group(lv.N, b, o, lv.rasTC + g * gf, g, (float)omega, (const float*)r,
+                                                 (const float*)x, (float*)xo, c->herr, s);
+                if (done) ++c->launches;
+            }
+        }
+        if (!done) KL(c, launch_ras_huge_apply<T>(lv.N, b, o, (const T*)lv.hugeInv[pi], (T)omega, r, x, xo, s));
+        if (lv.rasNIB > 0) {
+            const RasIB ib{lv.slotOf, (const double*)lv.win[0], lv.tx, lv.ty, lv.ntx};
+            const double h = lv.h, a0 = c->rho / c->dt + 4.0 * c->mu / (h * h), cc = c->mu / (h * h);
+            KL(c, launch_ras_wb_apply<T>(lv.N, b, o, ib, a0, cc, 1.0 / h, c->dt, lv.rasList, lv.rasNIB, lv.wbOffT,
+                                         lv.wbT, lv.wbOffW, lv.wbW, (const double*)lv.hugeInv[0], lv.wbMmax,
+                                         (T)omega, r, xo, s));
+        }
+        return;
+    }
     const float* tc = ras_tc_pack_for<T>(c, lv);
     KL(c, launch_ras_apply<T>(lv.N, c->opts.box, c->opts.box_overlap, lv.rasSlot, lv.rasList, lv.rasNIB,
                               (const T*)lv.rasInv[pi], (T)omega, r, x, xo, s, tc, c->herr));
@@ -970,14 +1006,108 @@ void power_M_enqueue(sib_ctx* c, int l, int slot, cudaStream_t s) {
 // and one per IB box (FP64), keeping the owned rows of each inverse.  Wide subdomains are eliminated
 // in a temporary global workspace, at most RAS_WORK_BYTES of matrices per launch.
 constexpr size_t RAS_WORK_BYTES = size_t(1) << 31;
+// The RAS reading on a level too small for the boxes (b does not divide N_l, or a subdomain's b + 2o + 1
+// face columns would wrap onto themselves): the box clipped to the periodic level is the whole level, and
+// its local solve the exact level solve with the gauge-fixed pseudo-inverse (as for the coarsest level).
+bool ras_wraps(int N, int b, int o) { return N % b != 0 || b + 2 * o + 1 > N; }
+
+// exact level solve of level l: L_l (from the stencils and the dense IB operator of its windows) + Z Z^T,
+// inverted by the blocked Gauss-Jordan, minus Z Z^T.  Temporaries go to `tmp`, freed by the caller.
+void ras_exact_setup(sib_ctx* c, int l, std::vector<void*>& tmp, int* ginfo, cudaStream_t s) {
+    Level& lv = c->L[l];
+    const int N = lv.N, n0 = N * N, n = 3 * n0;
+    double* Bd = (double*)dalloc(c, sizeof(double) * 2 * (size_t)n0 * n0);
+    double* Aug = (double*)dalloc(c, sizeof(double) * (size_t)n * 2 * n);
+    void* work = dalloc(c, gauss_jordan_work_bytes(n));
+    int* piv = (int*)dalloc(c, sizeof(int) * (size_t)n);
+    tmp.insert(tmp.end(), {Bd, Aug, work, piv});
+    CK(cudaMemsetAsync(Bd, 0, sizeof(double) * 2 * (size_t)n0 * n0, s));
+    if (c->haveIB)
+        KL(c, launch_window_dense((const double*)lv.win[0], lv.tiles, lv.hnTiles, N, lv.tx, lv.ty, lv.ntx, Bd, s));
+    KL(c, launch_assemble_L0(N, c->rho, c->mu, c->dt, Bd, Aug, s));
+    KL(c, launch_gauss_jordan(Aug, n, ginfo, piv, work, s));
+    dfree(c, lv.rasPinv);
+    lv.rasPinv = (double*)dalloc(c, sizeof(double) * (size_t)n * n);
+    KL(c, launch_extract_pinv(Aug, piv, n, N, c->rho, lv.rasPinv, s));
+    c->launches += 3;
+}
+
+// 16 x 16 boxes on level l: the full shared inverse by the blocked Gauss-Jordan, its tensor-core packs,
+// and the Woodbury data of the level's nIB IB boxes (listed in lv.rasList)
+void ras_huge_setup(sib_ctx* c, int l, int nIB, std::vector<void*>& tmp, int* ginfo, cudaStream_t s) {
+    Level& lv = c->L[l];
+    const int b = c->opts.box, o = c->opts.box_overlap;
+    const int ne = ras_ne(b, o), n = ras_huge_n(b, o);
+    double* Aug = (double*)dalloc(c, sizeof(double) * (size_t)n * 2 * n);
+    void* work = dalloc(c, gauss_jordan_work_bytes(n));
+    int* piv = (int*)dalloc(c, sizeof(int) * (size_t)n);
+    tmp.insert(tmp.end(), {Aug, work, piv});
+    const double h = lv.h, a0 = c->rho / c->dt + 4.0 * c->mu / (h * h), cc = c->mu / (h * h);
+    KL(c, launch_ras_huge_assemble(lv.N, b, o, a0, cc, 1.0 / h, Aug, s));
+    KL(c, launch_gauss_jordan(Aug, n, ginfo, piv, work, s));
+    for (int p = 0; p < 2; ++p) dfree(c, lv.hugeInv[p]);
+    lv.hugeInv[0] = dalloc(c, sizeof(double) * (size_t)ne * ne);
+    lv.hugeInv[1] = dalloc(c, sizeof(float) * (size_t)ne * ne);
+    KL(c, launch_ras_huge_extract(Aug, piv, b, o, (double*)lv.hugeInv[0], (float*)lv.hugeInv[1], s));
+    const size_t gf = ras_tc_group_floats(b, o);
+    const int groups = 3 * b * b / RAS_TC_GROUP;
+    dfree(c, lv.rasTC);
+    lv.rasTC = (float*)dalloc(c, sizeof(float) * gf * groups);
+    lv.rasTCCap = gf * groups;
+    for (int g = 0; g < groups; ++g) KL(c, launch_ras_tc_pack_rows(b, o, (const double*)lv.hugeInv[0], g, lv.rasTC + g * gf, s));
+    c->launches += 3 + groups;
+    lv.rasNIB = nIB;
+    dfree(c, lv.wbOffT);
+    dfree(c, lv.wbT);
+    dfree(c, lv.wbOffW);
+    dfree(c, lv.wbW);
+    lv.wbOffT = nullptr;
+    lv.wbT = nullptr;
+    lv.wbOffW = nullptr;
+    lv.wbW = nullptr;
+    lv.wbMmax = 0;
+    if (nIB == 0) return;
+    const RasIB ib{lv.slotOf, (const double*)lv.win[0], lv.tx, lv.ty, lv.ntx};
+    int* dcnt = (int*)dalloc(c, sizeof(int) * (size_t)nIB);
+    tmp.push_back(dcnt);
+    KL(c, launch_ras_wb_count(lv.N, b, o, ib, lv.rasList, nIB, dcnt, s));
+    std::vector<int> cnt(nIB), offT(nIB + 1, 0);
+    std::vector<long long> offW(nIB, 0);
+    CK(cudaMemcpyAsync(cnt.data(), dcnt, sizeof(int) * (size_t)nIB, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    long long wTot = 0;
+    for (int k = 0; k < nIB; ++k) {
+        offT[k + 1] = offT[k] + cnt[k];
+        offW[k] = wTot;
+        wTot += (long long)cnt[k] * cnt[k];
+        lv.wbMmax = std::max(lv.wbMmax, cnt[k]);
+    }
+    lv.wbOffT = (int*)dalloc(c, sizeof(int) * (size_t)(nIB + 1));
+    lv.wbOffW = (long long*)dalloc(c, sizeof(long long) * (size_t)nIB);
+    lv.wbT = (int*)dalloc(c, sizeof(int) * (size_t)std::max(1, offT[nIB]));
+    lv.wbW = (double*)dalloc(c, sizeof(double) * (size_t)std::max(1LL, wTot));
+    double* wwork = (double*)dalloc(c, sizeof(double) * (size_t)std::max(1LL, 2 * wTot));
+    tmp.push_back(wwork);
+    CK(cudaMemcpyAsync(lv.wbOffT, offT.data(), sizeof(int) * (size_t)(nIB + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(lv.wbOffW, offW.data(), sizeof(long long) * (size_t)nIB, cudaMemcpyHostToDevice, s));
+    KL(c, launch_ras_wb_fill(lv.N, b, o, ib, lv.rasList, nIB, lv.wbOffT, lv.wbT, s));
+    KL(c, launch_ras_wb_setup(lv.N, b, o, ib, c->dt, lv.rasList, nIB, lv.wbOffT, lv.wbT, lv.wbOffW,
+                              (const double*)lv.hugeInv[0], wwork, lv.wbW, c->rasInfo, lv.wbMmax, s));
+    CK(cudaStreamSynchronize(s));   // the host vectors above are the copies' sources
+    c->launches += 3;
+}
+
 void ras_setup_all(sib_ctx* c, cudaStream_t s) {
     const int b = c->opts.box, o = c->opts.box_overlap;
     const int ne = ras_ne(b, o), nown = 3 * b * b;
-    const bool big = ras_big(b, o);
+    const bool huge = ras_huge(b);
+    const bool big = !huge && ras_big(b, o);
     const size_t matBytes = sizeof(double) * (size_t)ne * ne;
     std::vector<int> cnt(c->lmax + 1, 0);
     for (int l = 1; l <= c->lmax; ++l) {
         Level& lv = c->L[l];
+        lv.rasExact = ras_wraps(lv.N, b, o);
+        if (lv.rasExact) continue;
         if (c->haveIB && !lv.useWindow)
             throw SibError(SIB_ERR_UNIMPLEMENTED, "the box smoother needs the assembled IB windows on every level");
         const int nboxes = (lv.N / b) * (lv.N / b);
@@ -996,6 +1126,10 @@ void ras_setup_all(sib_ctx* c, cudaStream_t s) {
     }
     CK(cudaStreamSynchronize(s));
     CK(cudaMemsetAsync(c->rasInfo, 0, sizeof(int), s));
+    std::vector<void*> tmp;   // set-up temporaries, freed at the end
+    int* ginfo = (int*)dalloc(c, sizeof(int));
+    tmp.push_back(ginfo);
+    CK(cudaMemsetAsync(ginfo, 0, sizeof(int), s));
     int batch = 0;   // wide subdomains: matrices per set-up launch
     double* work = nullptr;
     if (big) {
@@ -1003,10 +1137,21 @@ void ras_setup_all(sib_ctx* c, cudaStream_t s) {
         for (int l = 1; l <= c->lmax; ++l) most = std::max(most, 1 + cnt[l]);
         batch = (int)std::max<size_t>(1, std::min<size_t>((size_t)most, RAS_WORK_BYTES / matBytes));
         work = (double*)dalloc(c, matBytes * batch);
+        tmp.push_back(work);
     }
     for (int l = 1; l <= c->lmax; ++l) {
         Level& lv = c->L[l];
+        if (lv.rasExact) {
+            ras_exact_setup(c, l, tmp, ginfo, s);
+            continue;
+        }
         const int nboxes = (lv.N / b) * (lv.N / b);
+        launch_box_slots(nboxes, lv.rasList, lv.rasCount, lv.rasSlot, s);
+        ++c->launches;
+        if (huge) {
+            ras_huge_setup(c, l, cnt[l], tmp, ginfo, s);
+            continue;
+        }
         const size_t ent = (size_t)(1 + cnt[l]) * ne * nown;
         if (ent > lv.rasInvCap) {
             dfree(c, lv.rasInv[0]);
@@ -1016,10 +1161,8 @@ void ras_setup_all(sib_ctx* c, cudaStream_t s) {
             lv.rasInvCap = ent;
         }
         const RasIB ib{c->haveIB ? lv.slotOf : nullptr, (const double*)lv.win[0], lv.tx, lv.ty, lv.ntx};
-        launch_box_slots(nboxes, lv.rasList, lv.rasCount, lv.rasSlot, s);
         lv.rasNIB = cnt[l];
         const double h = lv.h, a0 = c->rho / c->dt + 4.0 * c->mu / (h * h), cc = c->mu / (h * h);
-        ++c->launches;
         if (big) {
             for (int first = 0; first < 1 + cnt[l]; first += batch) {
                 launch_ras_setup_big(lv.N, b, o, ib, a0, cc, 1.0 / h, c->dt, lv.rasList, first,
@@ -1042,12 +1185,13 @@ void ras_setup_all(sib_ctx* c, cudaStream_t s) {
         launch_ras_tc_pack(b, o, (const double*)lv.rasInv[0], lv.rasTC, s);
         ++c->launches;
     }
-    int info = 0;
+    int info = 0, gj = 0;
     CK(cudaMemcpyAsync(&info, c->rasInfo, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&gj, ginfo, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (work) dfree(c, work);
+    for (void* p : tmp) dfree(c, p);
     kcheck(c);
-    if (info != 0) throw SibError(SIB_ERR_ARG, "a box subdomain operator is singular");
+    if (info != 0 || gj != 0) throw SibError(SIB_ERR_ARG, "a box subdomain operator is singular");
 }
 
 void setup(sib_ctx* c, cudaStream_t s) {
@@ -1681,9 +1825,7 @@ void time_kernel(sib_ctx* c, int kernel, int l, int reps, bool cold, cudaStream_
                 launch_prolong_add<T>(c->L[l - 1].N, (const T*)c->L[l - 1].p[pi].x, (T*)b.x, s);
                 break;
             case SIB_KERNEL_RAS:
-                launch_ras_apply<T>(lv.N, c->opts.box, c->opts.box_overlap, lv.rasSlot, lv.rasList, lv.rasNIB,
-                                    (const T*)lv.rasInv[pi], (T)1, (const T*)b.r, (const T*)b.x, (T*)b.xt, s,
-                                    ras_tc_pack_for<T>(c, lv), c->herr);
+                ras_apply<T>(c, l, (const T*)b.r, (const T*)b.x, (T*)b.xt, 1.0, s);
                 break;
             case SIB_KERNEL_IB_WINDOW:
                 launch_ib_window<T>((const T*)lv.win[pi], lv.tiles, lv.rowSlots, lv.nRowTiles, lv.hnRowTiles, lv.N,
@@ -1978,8 +2120,9 @@ int sib_set_options(sib_ctx* c, const sib_opts* o) {
     if (!o) throw SibError(SIB_ERR_ARG, "null options");
     sib_opts n = *o;
     if ((n.smoother != SIB_SMOOTHER_VANKA && n.smoother != SIB_SMOOTHER_SC && n.smoother != SIB_SMOOTHER_RAS) ||
-        n.nu1 < 0 || n.nu2 < 0 || (n.box != 1 && n.box != 2 && n.box != 4 && n.box != 8) || n.box_overlap < 0 ||
-        n.box + 2 * n.box_overlap > RAS_EMAX_ENABLED || n.box + 2 * n.box_overlap + 1 > 2 * c->n_min ||
+        n.nu1 < 0 || n.nu2 < 0 || (n.box != 1 && n.box != 2 && n.box != 4 && n.box != 8 && n.box != 16) ||
+        n.box_overlap < 0 || (n.box < 16 && n.box + 2 * n.box_overlap > RAS_EMAX_ENABLED) ||
+        (n.box == 16 && n.box_overlap > 4) ||
         n.nu1 + n.nu2 > 64 || n.cheb_iters < 1 || n.cheb_iters > 16 || !(n.cheb_lo > 0) || !(n.cheb_hi > n.cheb_lo) ||
         n.power_iters < 1 || n.power_iters > 1000 || !(n.rtol >= 0) || n.max_it < 1 || n.max_it > 100000 ||
         n.restart < 1 || n.restart > 100 || (n.fuse_small != 0 && n.fuse_small != 1) ||

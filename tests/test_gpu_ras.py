@@ -128,15 +128,15 @@ def test_ras_stiff_disk_converges_where_vanka_caps():
 
 
 def test_ras_options_validated():
-    """Box sides 1, 2, 4, 8; a subdomain (b + 2 o cells) at most 16 wide and narrower than level 1's
-    2 n_min cells, so that it never wraps onto itself; the tensor-core choice 0 or 1."""
+    """Box sides 1, 2, 4, 8, 16; a subdomain (b + 2 o cells) at most 16 wide for b <= 8, overlap at most
+    4 for b = 16; the tensor-core choice 0 or 1."""
     prob, H, S = pair("ellipse32")
-    for kw in (dict(box=3), dict(box=16, box_overlap=0), dict(box=8, box_overlap=4), dict(box_overlap=-1),
-               dict(ras_tc=2), dict(ras_tc=-1)):
+    for kw in (dict(box=3), dict(box=32, box_overlap=0), dict(box=8, box_overlap=5), dict(box=16, box_overlap=5),
+               dict(box_overlap=-1), dict(ras_tc=2), dict(ras_tc=-1)):
         with pytest.raises(sib.SibError):
             S.set_options(**kw)
         S.set_options(box=4, box_overlap=1)
-    for b, o in ((4, 2), (8, 2), (2, 6)):
+    for b, o in ((4, 2), (8, 2), (2, 6), (8, 4), (16, 4)):
         S.set_options(box=b, box_overlap=o)
     S.set_options(box=4, box_overlap=1)
     S.setup()   # the cached solver serves the other tests
