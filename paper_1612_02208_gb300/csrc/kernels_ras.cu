@@ -1442,12 +1442,14 @@ __device__ double ras_row_dot(const RasGeo& G, const RasIB& ib, double a0, doubl
 }
 
 // IB boxes with 16 x 16 boxes, one block per box, in FP64, after the shared correction wrote
-// xo = x + omega (L_0^{-1} r_k)(owned) for every box.  The box's own local solve delta = L_k^{-1} r_k comes
-// from the Woodbury form M r = y - (L_0^{-1})_{:,T} W y_T, y = L_0^{-1} r, refined once against the
-// local operator itself: delta_0 = M r_k, delta = delta_0 + M (r_k - L_k delta_0).  With a stiff structure
-// W is large and the two terms of M nearly cancel; the refinement recovers the digits they lose.  Then
-// xo(owned) += omega (delta - L_0^{-1} r_k)(owned).  L_0^{-1} is symmetric (L_0 is), so its columns T are
-// read as rows.
+// xo = x + omega (L_0^{-1} r_k)(owned) for every box.  The box's own local solve is L_k^{-1} r_k = M r_k, the
+// Woodbury form M r = y - (L_0^{-1})_{:,T} W y_T, y = L_0^{-1} r.
+// FP64 levels: delta_0 = M r_k is refined once against the local operator itself, delta = delta_0 +
+// M (r_k - L_k delta_0): with a stiff structure W is large and the two terms of M nearly cancel, and the
+// refinement recovers the digits they lose; then xo(owned) += omega (delta - L_0^{-1} r_k)(owned).
+// FP32 levels: the low-rank term alone, xo(owned) -= omega (L_0^{-1})_{own,T} W (L_0^{-1})_{T,:} r_k (what
+// the cancellation costs stays below FP32 rounding; m (ne + nown) flops instead of 2 ne^2).
+// L_0^{-1} is symmetric (L_0 is), so its columns T are read as rows.
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_ras_wb_apply(RasGeo G, RasIB ib, double a0, double c, double inv_h, double dt, const int* __restrict__ list,
@@ -1499,6 +1501,34 @@ __global__ void __launch_bounds__(256)
         }
         __syncthreads();
     };
+    const int bb = G.b * G.b;
+    if constexpr (sizeof(T) == 4) {
+        for (int a = warp; a < m; a += nw) {   // y_T = (L_0^{-1})_{T,:} r_k
+            const double* row = inv0 + (size_t)Ts[a] * ne;
+            double acc = 0.0;
+            for (int t = lane; t < ne; t += 32) acc += row[t] * rk[t];
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if (lane == 0) y0[a] = acc;
+        }
+        __syncthreads();
+        for (int a = warp; a < m; a += nw) {   // z = W y_T
+            const double* row = Wb + (size_t)a * m;
+            double acc = 0.0;
+            for (int t = lane; t < m; t += 32) acc += row[t] * y0[t];
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if (lane == 0) z[a] = acc;
+        }
+        __syncthreads();
+        for (int rr = threadIdx.x; rr < G.nown; rr += blockDim.x) {
+            const double* row = inv0 + (size_t)ras_owned(G, rr) * ne;
+            double acc = 0.0;
+            for (int a = 0; a < m; ++a) acc += row[Ts[a]] * z[a];
+            const int comp = rr / bb, rem = rr - comp * bb;
+            const size_t d = (size_t)comp * n + (size_t)(J * G.b + rem / G.b) * N + I * G.b + rem % G.b;
+            xo[d] = (T)((double)xo[d] - (double)omega * acc);
+        }
+        return;
+    }
     woodbury(rk, y0, d0);
     for (int q = threadIdx.x; q < ne; q += blockDim.x)   // the residual of delta_0 in the local problem
         y1[q] = rk[q] - ras_row_dot(G, ib, a0, c, inv_h, dt, i0, j0, q, d0);
@@ -1506,7 +1536,6 @@ __global__ void __launch_bounds__(256)
     for (int q = threadIdx.x; q < ne; q += blockDim.x) rk[q] = y1[q];
     __syncthreads();
     woodbury(rk, y1, rk);   // rk <- M (residual)
-    const int bb = G.b * G.b;
     for (int rr = threadIdx.x; rr < G.nown; rr += blockDim.x) {
         const int q = ras_owned(G, rr);
         const int comp = rr / bb, rem = rr - comp * bb;
