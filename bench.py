@@ -76,10 +76,11 @@ def parse_args(argv=None):
     p.add_argument("--no-paper", action="store_true", help="skip the paper-workload and cavity tables")
     p.add_argument("--quick", action="store_true", help="headline only (no other legs)")
     p.add_argument("--large-n", type=int, default=LARGE_N, help="grid of the large-grid V-cycle roofline")
-    p.add_argument("--profile-vcycle", choices=["headline", "large", "ras8o2"], default=None,
+    p.add_argument("--profile-vcycle", choices=["headline", "large", "large64", "ras8o2"], default=None,
                    help="two FP32 V-cycles in an NVTX range 'vcycle', with a one-vector FGMRES basis (the small-memory "
                         "case for ncu captures): 'headline' = the headline workload and smoother, 'large' = the "
-                        "4096^2 thin ellipse with Vanka, 'ras8o2' = the 2048^2 grid without a structure, RAS with "
+                        "4096^2 thin ellipse with Vanka, 'large64' = the same body on 2048^2 with the FP64 V-cycle, "
+                        "'ras8o2' = the 2048^2 grid without a structure, RAS with "
                         "8 x 8 boxes of overlap 2 corrected on the tensor cores")
     p.add_argument("--profile-solve", action="store_true",
                    help="one FGMRES solve of the 128^2 disk (Vanka, kappa = 1e2) without CUDA graphs, in an NVTX range "
@@ -1049,16 +1050,22 @@ def run_reference(args):
 
 
 def run_profile_vcycle(which):
-    """Two FP32 V-cycles with a one-vector FGMRES basis, so that the device holds little memory: the
+    """Two V-cycles (FP32 unless stated) with a one-vector FGMRES basis, so that the device holds little
+    memory: the
     case ncu captures of the V-cycle kernels use.  'headline': the headline workload and smoother;
     'large': the 4096^2 thin ellipse (rho = 1, kappa = 1e4) with Vanka, the roofline leg's V-cycle;
-    'ras8o2': the 2048^2 grid without a structure (rho = 1), RAS with 8 x 8 boxes of overlap 2, their
-    correction on the tensor cores."""
+    'large64': that body on 2048^2 with the FP64 V-cycle; 'ras8o2': the 2048^2 grid without a structure
+    (rho = 1), RAS with 8 x 8 boxes of overlap 2, their correction on the tensor cores."""
     import torch
     from paper_1612_02208_gb300 import inputs, sib
+    fp32 = 1
     if which == "headline":
         prob = inputs.disk_and_ellipse_re(N_HEAD)
         opts = dict(smoother=sib.SMOOTHER_SC, smooth_krylov=1)
+    elif which == "large64":   # the FP64 V-cycle (FP64 pipe), on 2048^2 to keep the device memory small
+        prob = inputs.thin_ellipse_re(LARGE_N // 2, kappa=1e4, seed=2)
+        opts = dict(smoother=sib.SMOOTHER_VANKA)
+        fp32 = 0
     elif which == "ras8o2":   # no structure: every box takes the tensor-core correction, about 3 GB on the device
         prob = inputs.no_structure(LARGE_N // 2, rho=1.0, seed=2)
         opts = dict(smoother=sib.SMOOTHER_RAS, box=WIDE_BOX[0], box_overlap=WIDE_BOX[1], ras_tc=1)
@@ -1067,8 +1074,9 @@ def run_profile_vcycle(which):
         opts = dict(smoother=sib.SMOOTHER_VANKA)
     N = prob.N
     dev = torch.device("cuda")
-    S = sib.solver_for(prob, vcycle_fp32=1, omega=-1.0, restart=1, max_it=1, **opts)
-    b = torch.as_tensor(np.random.default_rng(5).standard_normal(3 * N * N), device=dev).float()
+    S = sib.solver_for(prob, vcycle_fp32=fp32, omega=-1.0, restart=1, max_it=1, **opts)
+    b = torch.as_tensor(np.random.default_rng(5).standard_normal(3 * N * N), device=dev)
+    b = b.float() if fp32 else b
     z = torch.empty_like(b)
     S.vcycle(b, z)   # the graph is captured outside the range
     torch.cuda.synchronize()
