@@ -951,6 +951,20 @@ __global__ void __launch_bounds__(RT_THREADS + 32, 1)
                                  : (int)(0x80000000u | ((uint32_t)ox & m) | (((uint32_t)oy & m) << 16));
             }
             __syncwarp();
+            // the tile's owned cells of x into L2, ahead of its writes (nch + ns chunks later): with rows
+            // of boxes a multiple of RT_NB long, its 128 boxes cover 3 b rows of 128 b cells, 12 b^2 lines of
+            // 128 bytes, spread over the workers
+            if (x && (G.nbs % RT_NB) == 0) {
+                const int J = (tile * RT_NB) / G.nbs, I0 = tile * RT_NB - J * G.nbs;
+                for (int ln = tid; ln < 12 * b * b; ln += RT_THREADS) {
+                    const int perRow = 4 * b;   // 128-byte lines in a row of 128 b FP32 cells
+                    const int row = ln / perRow, k = ln - row * perRow;
+                    const int comp = row / b, dy = row - comp * b;
+                    const float* pa =
+                        x + (size_t)comp * n + (size_t)(J * b + dy) * N + (size_t)I0 * b + (size_t)k * 32;
+                    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(pa));
+                }
+            }
         };
         auto gather = [&](int c, float (&v)[RT_BPW]) {
             const int q = c * RT_KC + lane;
@@ -1045,28 +1059,28 @@ __global__ void __launch_bounds__(RT_THREADS + 32, 1)
                         const int J = kq / G.nbs, I0 = kq - J * G.nbs;
                         const size_t rowBase = (size_t)(J * b) * N + (size_t)(I0 * b);
                         for (int grp = warp >> 2; grp < npad / 8 && ok; grp += 4) {
+                            // both 16-lane halves of the group: the eight x loads go out before any store
+                            uint32_t a[8];
+                            tmem_ld16x256(slot + ((uint32_t)(32 * quad) << 16) + (uint32_t)(8 * grp), *(uint32_t(*)[4])a);
+                            tmem_ld16x256(slot + ((uint32_t)(32 * quad + 16) << 16) + (uint32_t)(8 * grp),
+                                          *(uint32_t(*)[4])(a + 4));
+                            float xv[8];
+                            int dd[8];   // offset within the component, or -1
+                            int cc[8];
 #pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                uint32_t a[4];
-                                tmem_ld16x256(slot + ((uint32_t)(32 * quad + 16 * h) << 16) + (uint32_t)(8 * grp), a);
-                                float xv[4];
-                                int dd[4];   // offset within the component, or -1
-                                int cc[4];
-#pragma unroll
-                                for (int u = 0; u < 4; ++u) {
-                                    const int l = 16 * h + (lane >> 2) + 8 * (u >> 1);   // box within the quadrant
-                                    const int rr = rowOff + 8 * grp + 2 * (lane & 3) + (u & 1);   // owned row
-                                    const int comp = rr >> (2 * lb), rem = rr & (bb - 1);
-                                    cc[u] = comp;
-                                    dd[u] = (rr < nown && ((wmask >> l) & 1u))
-                                                ? (int)rowBase + ((rem >> lb) * N) + l * b + (rem & (b - 1))
-                                                : -1;
-                                    xv[u] = (dd[u] >= 0 && x) ? x[(size_t)comp * n + dd[u]] : 0.0f;
-                                }
-#pragma unroll
-                                for (int u = 0; u < 4; ++u)
-                                    if (dd[u] >= 0) xo[(size_t)cc[u] * n + dd[u]] = xv[u] + omega * __uint_as_float(a[u]);
+                            for (int u = 0; u < 8; ++u) {
+                                const int l = 16 * (u >> 2) + (lane >> 2) + 8 * ((u >> 1) & 1);   // box in the quadrant
+                                const int rr = rowOff + 8 * grp + 2 * (lane & 3) + (u & 1);           // owned row
+                                const int comp = rr >> (2 * lb), rem = rr & (bb - 1);
+                                cc[u] = comp;
+                                dd[u] = (rr < nown && ((wmask >> l) & 1u))
+                                            ? (int)rowBase + ((rem >> lb) * N) + l * b + (rem & (b - 1))
+                                            : -1;
+                                xv[u] = (dd[u] >= 0 && x) ? x[(size_t)comp * n + dd[u]] : 0.0f;
                             }
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (dd[u] >= 0) xo[(size_t)cc[u] * n + dd[u]] = xv[u] + omega * __uint_as_float(a[u]);
                         }
                     } else if (wr) {   // boxes across rows of boxes: each thread writes its own rows
                         const int J = kb / G.nbs, I = kb - J * G.nbs;
