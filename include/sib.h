@@ -95,6 +95,9 @@ typedef struct {
     int    ras_tc;        /* RAS, FP32 levels: the correction of the boxes that share one inverse runs
                              on the tensor cores (tcgen05, three TF32 products per pair for FP32
                              accuracy) (1) or on the FP32 CUDA cores (0) (1)                         */
+    int    l2_persist;    /* the graphs' kernels keep the finest level's FP32 IB windows in the L2
+                             cache (an access-policy window, with this process's persisting L2 limit
+                             set to their size) (1) or treat them as any other data (0) (1)         */
 } sib_opts;
 
 /* Domains.  SIB_DOMAIN_CAVITY is the paper's lid-driven cavity (Sec. 5) on the same layout: the seam

@@ -789,6 +789,34 @@ T* vcycle_level(sib_ctx* c, int l, cudaStream_t s) {
     return x;
 }
 
+// The capture stream's L2 access policy, which the captured kernels keep: the finest level's FP32 IB
+// windows, read by several passes of every sweep, persist in L2 (option l2_persist), within this
+// process's persisting-L2 limit (set to their size, at most the device's maximum).
+void apply_l2_policy(sib_ctx* c) {
+    cudaStreamAttrValue v{};
+    const Level& lv = c->L[c->lmax];
+    const size_t bytes = c->haveIB && lv.applyWindow && lv.win[1]
+                             ? sizeof(float) * (size_t)lv.hnTiles * 2 * WIN_SIZE * lv.tx * lv.ty
+                             : 0;
+    if (c->opts.l2_persist && bytes > 0) {
+        int dev = 0, maxPersist = 0, maxWin = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&maxPersist, cudaDevAttrMaxPersistingL2CacheSize, dev));
+        CK(cudaDeviceGetAttribute(&maxWin, cudaDevAttrMaxAccessPolicyWindowSize, dev));
+        const size_t win = std::min(bytes, (size_t)maxWin);
+        const size_t persist = std::min(win, (size_t)maxPersist);
+        if (persist > 0) {
+            CK(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, persist));
+            v.accessPolicyWindow.base_ptr = lv.win[1];
+            v.accessPolicyWindow.num_bytes = win;
+            v.accessPolicyWindow.hitRatio = (float)((double)persist / (double)win);
+            v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+            v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        }
+    }
+    CK(cudaStreamSetAttribute(c->cap, cudaStreamAttributeAccessPolicyWindow, &v));
+}
+
 // Run one V-cycle on the finest level's b; returns the output buffer.
 template <typename T>
 T* vcycle(sib_ctx* c, cudaStream_t s) {
@@ -797,6 +825,7 @@ T* vcycle(sib_ctx* c, cudaStream_t s) {
     if (!c->vg[pi]) {
         const int64_t before = c->launches;
         cudaGraph_t graph;
+        apply_l2_policy(c);
         CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
         T* out = nullptr;
         try {
@@ -1575,6 +1604,7 @@ void build_fg_graph(sib_ctx* c) {
         CK(cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &p));
         cudaGraph_t body = p.conditional.phGraph_out[0];
         cudaStream_t s = c->cap;
+        apply_l2_policy(c);
         CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         try {
             Level& lv = c->L[c->lmax];
@@ -1941,6 +1971,7 @@ void sib_default_opts(sib_opts* o) {
     o->box_overlap = 1;
     o->domain = SIB_DOMAIN_PERIODIC;
     o->ras_tc = 1;
+    o->l2_persist = 1;
 }
 
 static void resolve_opts(sib_opts* o) {
@@ -2128,7 +2159,7 @@ int sib_set_options(sib_ctx* c, const sib_opts* o) {
         n.restart < 1 || n.restart > 100 || (n.fuse_small != 0 && n.fuse_small != 1) ||
         (n.smooth_krylov != 0 && n.smooth_krylov != 1) || (n.smooth_krylov && (n.nu1 > WRAP_MAXK || n.nu2 > WRAP_MAXK)) ||
         (n.sc_relax != SIB_RELAX_JACOBI && n.sc_relax != SIB_RELAX_SGS) ||
-        (n.domain != SIB_DOMAIN_PERIODIC && n.domain != SIB_DOMAIN_CAVITY) || (n.ras_tc != 0 && n.ras_tc != 1))
+        (n.domain != SIB_DOMAIN_PERIODIC && n.domain != SIB_DOMAIN_CAVITY) || (n.ras_tc != 0 && n.ras_tc != 1) || (n.l2_persist != 0 && n.l2_persist != 1))
         throw SibError(SIB_ERR_ARG, "option out of range");
     if (n.domain == SIB_DOMAIN_CAVITY) {
         if (!CAVITY_SOLVE_ENABLED) throw SibError(SIB_ERR_UNIMPLEMENTED, "the cavity domain is not available");

@@ -57,6 +57,7 @@ class SibOpts(ctypes.Structure):
         ("max_it", ctypes.c_int), ("restart", ctypes.c_int), ("add_SKXn", ctypes.c_int), ("use_graphs", ctypes.c_int),
         ("fuse_small", ctypes.c_int), ("smooth_krylov", ctypes.c_int), ("sc_relax", ctypes.c_int),
         ("box", ctypes.c_int), ("box_overlap", ctypes.c_int), ("domain", ctypes.c_int), ("ras_tc", ctypes.c_int),
+        ("l2_persist", ctypes.c_int),
     ]
 
 

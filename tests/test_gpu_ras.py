@@ -132,7 +132,7 @@ def test_ras_options_validated():
     4 for b = 16; the tensor-core choice 0 or 1."""
     prob, H, S = pair("ellipse32")
     for kw in (dict(box=3), dict(box=32, box_overlap=0), dict(box=8, box_overlap=5), dict(box=16, box_overlap=5),
-               dict(box_overlap=-1), dict(ras_tc=2), dict(ras_tc=-1)):
+               dict(box_overlap=-1), dict(ras_tc=2), dict(ras_tc=-1), dict(l2_persist=2)):
         with pytest.raises(sib.SibError):
             S.set_options(**kw)
         S.set_options(box=4, box_overlap=1)
