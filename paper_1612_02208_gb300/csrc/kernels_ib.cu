@@ -945,6 +945,7 @@ __global__ void __launch_bounds__(32 * WD) k_ib_window(const T* __restrict__ win
                                                        int N, int tx, int ty, int ntx, const T* __restrict__ u,
                                                        T* __restrict__ f) {
     constexpr int FV = 16 / (int)sizeof(T);   // faces per thread
+    static_assert(WR % FV == 0, "the u row's 16-byte loads start at i0 - WR");
     using VT = typename WinVec<T>::type;
     __shared__ __align__(16) T part[WD][32 * FV];
     if ((int)blockIdx.x >= *nRow) return;
@@ -969,9 +970,20 @@ __global__ void __launch_bounds__(32 * WD) k_ib_window(const T* __restrict__ win
     for (int k = 0; k < FV; ++k) acc[k] = T(0);
     if (live) {
         const T* row = u + (size_t)c * n + (size_t)((j + oy) & mk) * N;
-        T ur[FV + 2 * WR];
+        T ur[FV + 2 * WR];   // u at i0 - WR .. i0 + FV + WR - 1 of the row
+        if (i0 >= WR && i0 + FV + WR <= N) {   // inside the row: 16-byte loads (i0 - WR is a multiple of FV)
+            constexpr int NV = (FV + 2 * WR) / FV;
 #pragma unroll
-        for (int k = 0; k < FV + 2 * WR; ++k) ur[k] = row[(i0 - WR + k) & mk];
+            for (int v = 0; v < NV; ++v) {
+                const VT q = *reinterpret_cast<const VT*>(row + i0 - WR + v * FV);
+                const T* qv = reinterpret_cast<const T*>(&q);
+#pragma unroll
+                for (int k = 0; k < FV; ++k) ur[v * FV + k] = qv[k];
+            }
+        } else {   // across the periodic seam
+#pragma unroll
+            for (int k = 0; k < FV + 2 * WR; ++k) ur[k] = row[(i0 - WR + k) & mk];
+        }
 #pragma unroll
         for (int ox = 0; ox < WD; ++ox) {
             const T* wk = reinterpret_cast<const T*>(&wv[ox]);
