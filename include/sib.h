@@ -97,7 +97,9 @@ typedef struct {
                              accuracy) (1) or on the FP32 CUDA cores (0) (1)                         */
     int    l2_persist;    /* the graphs' kernels keep the finest level's FP32 IB windows in the L2
                              cache (an access-policy window, with this process's persisting L2 limit
-                             set to their size) (1) or treat them as any other data (0) (1)         */
+                             set to their size) (1) or treat them as any other data (0) (0: on the
+                             1024^2 differentiated solve the set-aside L2 slows the other passes
+                             more than it speeds the window passes, 232 against 220 ms a step)    */
 } sib_opts;
 
 /* Domains.  SIB_DOMAIN_CAVITY is the paper's lid-driven cavity (Sec. 5) on the same layout: the seam

@@ -149,6 +149,7 @@ struct sib_ctx {
     double* Pinv = nullptr;
     int* info = nullptr;
     int* rasInfo = nullptr;      // zero pivot in a box RAS subdomain inverse
+    size_t l2Limit = 0;          // the persisting-L2 limit this context set last
     int* piv = nullptr;
     int n0 = 0;
     // FGMRES
@@ -794,6 +795,7 @@ T* vcycle_level(sib_ctx* c, int l, cudaStream_t s) {
 // process's persisting-L2 limit (set to their size, at most the device's maximum).
 void apply_l2_policy(sib_ctx* c) {
     cudaStreamAttrValue v{};
+    size_t limit = 0;
     const Level& lv = c->L[c->lmax];
     const size_t bytes = c->haveIB && lv.applyWindow && lv.win[1]
                              ? sizeof(float) * (size_t)lv.hnTiles * 2 * WIN_SIZE * lv.tx * lv.ty
@@ -806,13 +808,17 @@ void apply_l2_policy(sib_ctx* c) {
         const size_t win = std::min(bytes, (size_t)maxWin);
         const size_t persist = std::min(win, (size_t)maxPersist);
         if (persist > 0) {
-            CK(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, persist));
+            limit = persist;
             v.accessPolicyWindow.base_ptr = lv.win[1];
             v.accessPolicyWindow.num_bytes = win;
             v.accessPolicyWindow.hitRatio = (float)((double)persist / (double)win);
             v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
             v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
         }
+    }
+    if (limit != c->l2Limit) {   // the limit reconfigures the L2: set (or release) it only when it changes
+        CK(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, limit));
+        c->l2Limit = limit;
     }
     CK(cudaStreamSetAttribute(c->cap, cudaStreamAttributeAccessPolicyWindow, &v));
 }
@@ -1971,7 +1977,7 @@ void sib_default_opts(sib_opts* o) {
     o->box_overlap = 1;
     o->domain = SIB_DOMAIN_PERIODIC;
     o->ras_tc = 1;
-    o->l2_persist = 1;
+    o->l2_persist = 0;
 }
 
 static void resolve_opts(sib_opts* o) {
@@ -2159,7 +2165,8 @@ int sib_set_options(sib_ctx* c, const sib_opts* o) {
         n.restart < 1 || n.restart > 100 || (n.fuse_small != 0 && n.fuse_small != 1) ||
         (n.smooth_krylov != 0 && n.smooth_krylov != 1) || (n.smooth_krylov && (n.nu1 > WRAP_MAXK || n.nu2 > WRAP_MAXK)) ||
         (n.sc_relax != SIB_RELAX_JACOBI && n.sc_relax != SIB_RELAX_SGS) ||
-        (n.domain != SIB_DOMAIN_PERIODIC && n.domain != SIB_DOMAIN_CAVITY) || (n.ras_tc != 0 && n.ras_tc != 1) || (n.l2_persist != 0 && n.l2_persist != 1))
+        (n.domain != SIB_DOMAIN_PERIODIC && n.domain != SIB_DOMAIN_CAVITY) || (n.ras_tc != 0 && n.ras_tc != 1) ||
+        (n.l2_persist != 0 && n.l2_persist != 1))
         throw SibError(SIB_ERR_ARG, "option out of range");
     if (n.domain == SIB_DOMAIN_CAVITY) {
         if (!CAVITY_SOLVE_ENABLED) throw SibError(SIB_ERR_UNIMPLEMENTED, "the cavity domain is not available");
