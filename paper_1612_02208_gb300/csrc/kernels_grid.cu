@@ -474,29 +474,31 @@ __global__ void k_residual_restrict(GridK<T> g, const T* __restrict__ x, const T
 }
 // The same residual and restriction for N >= 64, tiled: one block per 32 x 8 coarse cells (64 x 16
 // fine cells).  The block stages x (three components, fine rows fj0-2 .. fj0+17), b and the IB force
-// (rows fj0-1 .. fj0+16), all over columns fi0-4 .. fi0+67, in shared memory, forms each fine residual
-// the restriction needs once (u faces on columns fi0-1 .. fi0+64, v faces on rows fj0-1 .. fj0+15,
-// every cell) with the arithmetic of res_u / res_v / res_p, then restricts as residual_restrict_cell
-// does.  Blocks whose staged rows and columns lie inside the grid load 16-byte vectors, every load
-// issued before the first shared store; the others (the periodic wrap) gather element by element.  The
-// IB force is read where one of the tile's four fine tiles is IB-active: their flags are dilated by
-// one tile and cover the one-cell halo, and the force is zero on inactive tiles.
+// (rows fj0-1 .. fj0+16), all over columns fi0-4 .. fi0+67, in shared memory.  Blocks whose staged
+// rows and columns lie inside the grid load 16-byte vectors, every load issued before the first
+// shared store; the others (the periodic wrap) gather element by element.  Each thread then forms, in
+// registers, the fine residuals its coarse cell's restriction needs (u faces of columns 2I-1 .. 2I+1,
+// v faces of rows 2J-1 .. 2J+1, p of its four cells; the faces it shares with a neighbour are formed
+// by both) with the arithmetic of res_u / res_v / res_p, reading the staged rows as column pairs, and
+// restricts them as residual_restrict_cell does.  The IB force is read where one of the tile's four
+// fine tiles is IB-active: their flags are dilated by one tile and cover the one-cell halo, and the
+// force is zero on inactive tiles.
 constexpr int RR_CX = 32, RR_CY = 8;                 // coarse cells per block
 constexpr int RR_FX = 2 * RR_CX, RR_FY = 2 * RR_CY;  // fine cells per block
 constexpr int RR_W = RR_FX + 8;                      // staged row width (columns fi0-4 .. fi0+67)
 constexpr int RR_XH = RR_FY + 4, RR_BH = RR_FY + 2;  // staged rows of x (fj0-2 ..) and of b, f (fj0-1 ..)
-constexpr int RR_RU = RR_FX + 2;                     // u residuals per row (columns fi0-1 .. fi0+64)
-constexpr int RR_WORDS = (3 * RR_XH + 3 * RR_BH + 2 * RR_BH) * RR_W + RR_FY * RR_RU + (RR_FY + 1) * RR_FX +
-                         RR_FY * RR_FX;
+constexpr int RR_WORDS = (3 * RR_XH + 3 * RR_BH + 2 * RR_BH) * RR_W;
 template <typename T>
 struct RRVec;
 template <>
 struct RRVec<float> {
     using type = float4;
+    using pair = float2;
 };
 template <>
 struct RRVec<double> {
     using type = double2;
+    using pair = double2;
 };
 template <typename T>
 __global__ void __launch_bounds__(RR_CX * RR_CY) k_residual_restrict_tiled(GridK<T> g, const T* __restrict__ x,
@@ -513,9 +515,6 @@ __global__ void __launch_bounds__(RR_CX * RR_CY) k_residual_restrict_tiled(GridK
     T* sx = st;
     T* sb = st + 3 * RR_XH * RR_W;
     T* sf = sb + 3 * RR_BH * RR_W;
-    T* ru = st + NROWS * RR_W;               // [RR_FY][RR_RU]
-    T* rv = ru + RR_FY * RR_RU;              // [RR_FY + 1][RR_FX]
-    T* rp = rv + (RR_FY + 1) * RR_FX;        // [RR_FY][RR_FX]
     const int N = g.N, n = N * N, m = N - 1, Nc = N / 2;
     const int tid = threadIdx.y * RR_CX + threadIdx.x;
     const int fi0 = blockIdx.x * RR_FX, fj0 = blockIdx.y * RR_FY;
@@ -573,45 +572,96 @@ __global__ void __launch_bounds__(RR_CX * RR_CY) k_residual_restrict_tiled(GridK
         }
     }
     __syncthreads();
+    using P2 = typename RRVec<T>::pair;
     const T* U = sx;
     const T* V = sx + RR_XH * RR_W;
     const T* P = sx + 2 * RR_XH * RR_W;
-    auto X = [](const T* a, int xi, int xj) { return a[xj * RR_W + xi]; };
-    // u residuals at fine (fi0 - 1 + a, fj0 + r): staged column a + 3; x row r + 2, b and f row r + 1
-    for (int q = tid; q < RR_FY * RR_RU; q += NT) {
-        const int r = q / RR_RU, a = q - r * RR_RU;
-        const int xi = a + 3, xj = r + 2;
-        T Au = g.a0 * X(U, xi, xj) - g.c * ((X(U, xi + 1, xj) + X(U, xi - 1, xj)) + (X(U, xi, xj + 1) + X(U, xi, xj - 1))) +
-               (X(P, xi, xj) - X(P, xi - 1, xj)) * g.inv_h;
-        Au -= g.dt * (act ? sf[(r + 1) * RR_W + xi] : T(0));
-        ru[q] = sb[(r + 1) * RR_W + xi] - Au;
+    const T* Bu = sb;
+    const T* Bv = sb + RR_BH * RR_W;
+    const T* Bp = sb + 2 * RR_BH * RR_W;
+    const T* Fu = sf;
+    const T* Fv = sf + RR_BH * RR_W;
+    // coarse cell (I, J): fine cells 2I, 2I + 1 of rows 2J, 2J + 1 of the tile.  Staged column
+    // c0 + k holds fine column 2I - 2 + k (k = 0 .. 5); staged x row 2J + r holds fine row 2J - 2 + r,
+    // staged b / f row 2J + r fine row 2J - 1 + r.
+    const int c0 = 2 * threadIdx.x + 2, r0 = 2 * threadIdx.y;
+    auto pairs = [&](const T* a, int xr, int k0, int np, T* out) {   // np pairs of row xr from column c0 + k0
+#pragma unroll
+        for (int q = 0; q < np; ++q) {
+            const P2 v = *reinterpret_cast<const P2*>(a + xr * RR_W + c0 + k0 + 2 * q);
+            out[2 * q] = v.x;
+            out[2 * q + 1] = v.y;
+        }
+    };
+    // u residuals at fine columns 2I - 1 + a (k = 1 + a), rows 2J + r: x rows 2J + 2 + r (u rows 1 + r
+    // of u[], loaded from staged rows 2J + 1 ..), b and f rows 2J + 1 + r
+    T su, sv, sp;
+    T du[2][2];   // U(xi + 1) - U(xi) of the p residuals, rows 2J, 2J + 1, columns 2I, 2I + 1
+    {
+        T u[4][6], pp[2][4], bu[2][4], fu[2][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) pairs(U, r0 + 1 + r, 0, 3, u[r]);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            pairs(P, r0 + 2 + r, 0, 2, pp[r]);
+            pairs(Bu, r0 + 1 + r, 0, 2, bu[r]);
+            if (act) pairs(Fu, r0 + 1 + r, 0, 2, fu[r]);
+        }
+        T ru[2][3];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int k = 1 + a, ur = 1 + r;
+                T Au = g.a0 * u[ur][k] - g.c * ((u[ur][k + 1] + u[ur][k - 1]) + (u[ur + 1][k] + u[ur - 1][k])) +
+                       (pp[r][k] - pp[r][k - 1]) * g.inv_h;
+                Au -= g.dt * (act ? fu[r][k] : T(0));
+                ru[r][a] = bu[r][k] - Au;
+            }
+        // ru[r][a]: fine column 2I - 1 + a
+        su = (ru[0][1] + ru[1][1]) + T(0.5) * ((ru[0][2] + ru[1][2]) + (ru[0][0] + ru[1][0]));
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) du[r][a] = u[1 + r][3 + a] - u[1 + r][2 + a];
     }
-    // v residuals at fine (fi0 + a, fj0 - 1 + r): staged column a + 4; x row r + 1, b and f row r
-    for (int q = tid; q < (RR_FY + 1) * RR_FX; q += NT) {
-        const int r = q / RR_FX, a = q - r * RR_FX;
-        const int xi = a + 4, xj = r + 1;
-        T Av = g.a0 * X(V, xi, xj) - g.c * ((X(V, xi + 1, xj) + X(V, xi - 1, xj)) + (X(V, xi, xj + 1) + X(V, xi, xj - 1))) +
-               (X(P, xi, xj) - X(P, xi, xj - 1)) * g.inv_h;
-        Av -= g.dt * (act ? sf[RR_BH * RR_W + r * RR_W + xi] : T(0));
-        rv[q] = sb[RR_BH * RR_W + r * RR_W + xi] - Av;
+    {
+        // v residuals at fine columns 2I + a (k = 2 + a), rows 2J - 1 + r: x rows 2J + 1 + r (v rows
+        // 1 + r of v[], loaded from staged rows 2J ..), b and f rows 2J + r
+        T v[5][6], pp[4][2], bv[3][2], fv[3][2], bp[2][2];
+#pragma unroll
+        for (int r = 0; r < 5; ++r) pairs(V, r0 + r, 0, 3, v[r]);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) pairs(P, r0 + r, 2, 1, pp[r]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            pairs(Bv, r0 + r, 2, 1, bv[r]);
+            if (act) pairs(Fv, r0 + r, 2, 1, fv[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) pairs(Bp, r0 + 1 + r, 2, 1, bp[r]);
+        // v[vr][j]: staged column c0 + j (fine column 2I - 2 + j), staged row 2J + vr
+        T rv[3][2];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int k = 2 + a, vr = 1 + r;
+                T Av = g.a0 * v[vr][k] - g.c * ((v[vr][k + 1] + v[vr][k - 1]) + (v[vr + 1][k] + v[vr - 1][k])) +
+                       (pp[vr][a] - pp[vr - 1][a]) * g.inv_h;
+                Av -= g.dt * (act ? fv[r][a] : T(0));
+                rv[r][a] = bv[r][a] - Av;
+            }
+        // rv[r][a]: fine row 2J - 1 + r, column 2I + a
+        sv = (rv[1][0] + rv[1][1]) + T(0.5) * ((rv[2][0] + rv[2][1]) + (rv[0][0] + rv[0][1]));
+        T rp[2][2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+                rp[r][a] = bp[r][a] + (du[r][a] + (v[3 + r][2 + a] - v[2 + r][2 + a])) * g.inv_h;
+        sp = (rp[0][0] + rp[0][1]) + (rp[1][0] + rp[1][1]);
     }
-    // p residuals at fine (fi0 + a, fj0 + r): staged column a + 4; x row r + 2, b row r + 1
-    for (int q = tid; q < RR_FY * RR_FX; q += NT) {
-        const int r = q / RR_FX, a = q - r * RR_FX;
-        const int xi = a + 4, xj = r + 2;
-        rp[q] = sb[2 * RR_BH * RR_W + (r + 1) * RR_W + xi] +
-                ((X(U, xi + 1, xj) - X(U, xi, xj)) + (X(V, xi, xj + 1) - X(V, xi, xj))) * g.inv_h;
-    }
-    __syncthreads();
-    // restriction of coarse cell (I, J): fine cells fx = 2 tx, fy = 2 ty of the tile
-    const int fx = 2 * threadIdx.x, fy = 2 * threadIdx.y;
-    const T su = (ru[fy * RR_RU + fx + 1] + ru[(fy + 1) * RR_RU + fx + 1]) +
-                 T(0.5) * ((ru[fy * RR_RU + fx + 2] + ru[(fy + 1) * RR_RU + fx + 2]) +
-                           (ru[fy * RR_RU + fx] + ru[(fy + 1) * RR_RU + fx]));
-    const T sv = (rv[(fy + 1) * RR_FX + fx] + rv[(fy + 1) * RR_FX + fx + 1]) +
-                 T(0.5) * ((rv[(fy + 2) * RR_FX + fx] + rv[(fy + 2) * RR_FX + fx + 1]) +
-                           (rv[fy * RR_FX + fx] + rv[fy * RR_FX + fx + 1]));
-    const T sp = (rp[fy * RR_FX + fx] + rp[fy * RR_FX + fx + 1]) + (rp[(fy + 1) * RR_FX + fx] + rp[(fy + 1) * RR_FX + fx + 1]);
     const int I = blockIdx.x * RR_CX + threadIdx.x, J = blockIdx.y * RR_CY + threadIdx.y;
     const int nc = Nc * Nc, c = J * Nc + I;
     bc[c] = T(0.25) * su;

@@ -426,14 +426,21 @@ __global__ void k_interp(IBK<T> k, const T* __restrict__ u, T* __restrict__ U) {
     const int c = blockIdx.y;
     if (m >= k.M) return;
     const int N = k.N, mk = N - 1;
-    const int b = k.base[c][m], bi = b & 0xffff, bj = (b >> 16) & 0xffff;
-    const T* w = k.wgt[c] + 8 * m;
+    // the component's arrays chosen by selects: indexing the parameter arrays by c would copy the
+    // parameters to local memory
+    const int b = (c ? k.base[1] : k.base[0])[m], bi = b & 0xffff, bj = (b >> 16) & 0xffff;
+    const T* w = (c ? k.wgt[1] : k.wgt[0]) + 8 * m;
     const T* uc = u + (size_t)c * N * N;
+    // W <= 4: the loops unrolled to four, so that every load of the stencil is in flight at once
     T acc = T(0);
-    for (int q = 0; q < k.W; ++q) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (q >= k.W) break;
         const int row = ((bj + q) & mk) * N;
         T s = T(0);
-        for (int p = 0; p < k.W; ++p) s += w[p] * uc[row + ((bi + p) & mk)];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+            if (p < k.W) s += w[p] * uc[row + ((bi + p) & mk)];
         acc += w[4 + q] * s;
     }
     U[c * k.M + m] = acc;
@@ -473,25 +480,40 @@ template <typename T>
 __device__ __forceinline__ T gather_face(const IBK<T>& k, const T* __restrict__ F, int c, int i, int j, int lane,
                                          int stride) {
     const int mk = k.N - 1;
-    const int* bs = k.binStart[c];
-    const int* srt = k.sorted[c];
-    const T* wg = k.wgt[c];
+    const int* bs = c ? k.binStart[1] : k.binStart[0];
+    const int* srt = c ? k.sorted[1] : k.sorted[0];
+    const T* wg = c ? k.wgt[1] : k.wgt[0];
     const T* Fc = F + c * k.M;
+    // the W x W bin ranges first (independent loads, W <= 4), then the markers of each bin in the
+    // same order (b, a, q) as a bin-by-bin walk
+    int s[16], e[16];
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            s[4 * b + a] = 0;
+            e[4 * b + a] = 0;
+            if (a < k.W && b < k.W) {
+                const uint32_t bin = morton((i - a) & mk, (j - b) & mk);
+                s[4 * b + a] = bs[bin];
+                e[4 * b + a] = bs[bin + 1];
+            }
+        }
     T acc = T(0);
-    for (int b = 0; b < k.W; ++b)
-        for (int a = 0; a < k.W; ++a) {
-            const uint32_t bin = morton((i - a) & mk, (j - b) & mk);
-            const int s = bs[bin], e = bs[bin + 1];
-            for (int q = s + lane; q < e; q += stride) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            for (int q = s[4 * b + a] + lane; q < e[4 * b + a]; q += stride) {
                 const int m = srt[q];
                 acc += wg[8 * m + a] * wg[8 * m + 4 + b] * Fc[m];
             }
-        }
     return acc;
 }
 
 // rowSlots != nullptr: block b takes the tile of slot rowSlots[b] (b < *nTiles, the count of that
-// list), the tiles that a marker stencil touches; otherwise tile b of the active-tile list.
+// list), the tiles that a marker stencil touches; otherwise tile b of the active-tile list.  One thread
+// per face of component blockIdx.y.
 template <typename T>
 __global__ void __launch_bounds__(256) k_spread_thread(IBK<T> k, const T* __restrict__ F, T* __restrict__ f,
                                                        const int* __restrict__ tiles, const int* __restrict__ nTiles,
@@ -500,8 +522,8 @@ __global__ void __launch_bounds__(256) k_spread_thread(IBK<T> k, const T* __rest
     if ((int)blockIdx.x >= *nTiles) return;
     const int t = tiles[rowSlots ? rowSlots[blockIdx.x] : blockIdx.x];
     const int i = (t % ntx) * tx + threadIdx.x, j = (t / ntx) * ty + threadIdx.y;
-    const int n = k.N * k.N;
-    for (int c = 0; c < 2; ++c) f[c * n + j * k.N + i] = k.inv_h2 * gather_face(k, F, c, i, j, 0, 1);
+    const int n = k.N * k.N, c = blockIdx.y;
+    f[c * n + j * k.N + i] = k.inv_h2 * gather_face(k, F, c, i, j, 0, 1);
 }
 
 template <typename T>
@@ -533,7 +555,8 @@ void launch_spread(const IBK<T>& k, const T* F, T* f, const int* tiles, const in
         const int groups = (2 * tx * ty + 7) / 8;
         launch_pdl(k_spread_warp<T>, dim3(maxTiles, groups), 256, 0, s, k, F, f, tiles, cnt, rowSlots, tx, ty, ntx);
     } else {
-        launch_pdl(k_spread_thread<T>, maxTiles, dim3(tx, ty), 0, s, k, F, f, tiles, cnt, rowSlots, tx, ty, ntx);
+        launch_pdl(k_spread_thread<T>, dim3(maxTiles, 2), dim3(tx, ty), 0, s, k, F, f, tiles, cnt, rowSlots, tx, ty,
+                   ntx);
     }
 }
 

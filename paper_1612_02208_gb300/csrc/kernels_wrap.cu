@@ -249,48 +249,98 @@ __global__ void __launch_bounds__(WT) k_wscale(const T* __restrict__ w, const do
 // y = argmin || beta e1 - H y || for the (m + 1) x m Hessenberg matrix of the step (Givens
 // rotations, back substitution).  H(i, j) = hA[j][i] + hB[j][i] for i <= j (the two Gram-Schmidt
 // passes), H(j + 1, j) = sqrt(nr[j]); m stops at the first vanished subdiagonal entry.  y[m..k) = 0.
-// One thread.
+// One thread.  The loops run to a compile-time bound KM >= k, predicated on k and m, so that H stays in
+// registers and every entry is loaded at once.
+template <int KM>
+__device__ void wlsq_solve_t(const double* __restrict__ hA, const double* __restrict__ hB,
+                             const double* __restrict__ nr, const double* __restrict__ beta2, int k,
+                             double* __restrict__ y) {
+    double H[KM + 1][KM];
+    double g[KM + 1], yv[KM];
+#pragma unroll
+    for (int j = 0; j < KM; ++j) {
+        yv[j] = 0.0;
+#pragma unroll
+        for (int i = 0; i <= KM; ++i) H[i][j] = 0.0;
+        if (j < k) {
+#pragma unroll
+            for (int i = 0; i <= j; ++i) H[i][j] = hA[j * (WRAP_MAXK + 1) + i] + hB[j * (WRAP_MAXK + 1) + i];
+            H[j + 1][j] = sqrt(nr[j]);
+        }
+    }
+    const double beta = sqrt(beta2[0]);
+    int m = k;
+#pragma unroll
+    for (int j = KM - 1; j >= 0; --j)
+        if (j < k && !(H[j + 1][j] > 0.0)) m = j + 1;
+    if (beta > 0.0) {
+#pragma unroll
+        for (int i = 0; i <= KM; ++i) g[i] = i == 0 ? beta : 0.0;
+#pragma unroll
+        for (int j = 0; j < KM; ++j) {   // rotate H(j, j), H(j + 1, j) to (r, 0)
+            if (j < m) {
+                const double a = H[j][j], b = H[j + 1][j];
+                const double d = hypot(a, b);
+                const double cs = d > 0.0 ? a / d : 1.0, sn = d > 0.0 ? b / d : 0.0;
+#pragma unroll
+                for (int q = j; q < KM; ++q) {
+                    if (q < m) {
+                        const double u = H[j][q], v = H[j + 1][q];
+                        H[j][q] = cs * u + sn * v;
+                        H[j + 1][q] = -sn * u + cs * v;
+                    }
+                }
+                const double gu = g[j], gv = g[j + 1];
+                g[j] = cs * gu + sn * gv;
+                g[j + 1] = -sn * gu + cs * gv;
+            }
+        }
+#pragma unroll
+        for (int i = KM - 1; i >= 0; --i) {
+            if (i < m) {
+                double acc = g[i];
+#pragma unroll
+                for (int q = i + 1; q < KM; ++q)
+                    if (q < m) acc -= H[i][q] * yv[q];
+                yv[i] = H[i][i] != 0.0 ? acc / H[i][i] : 0.0;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < KM; ++j)
+        if (j < k) y[j] = yv[j];
+}
 __device__ void wlsq_solve(const double* __restrict__ hA, const double* __restrict__ hB,
                            const double* __restrict__ nr, const double* __restrict__ beta2, int k,
                            double* __restrict__ y) {
-    double H[WRAP_MAXK + 1][WRAP_MAXK];
-    double g[WRAP_MAXK + 1];
-    const double beta = sqrt(beta2[0]);
-    int m = 0;
-    for (int j = 0; j < k; ++j) {
-        for (int i = 0; i <= j; ++i) H[i][j] = hA[j * (WRAP_MAXK + 1) + i] + hB[j * (WRAP_MAXK + 1) + i];
-        H[j + 1][j] = sqrt(nr[j]);
-        m = j + 1;
-        if (!(H[j + 1][j] > 0.0)) break;
-    }
-    for (int j = 0; j < k; ++j) y[j] = 0.0;
-    if (!(beta > 0.0)) return;
-    for (int i = 0; i <= m; ++i) g[i] = i == 0 ? beta : 0.0;
-    for (int j = 0; j < m; ++j) {   // rotate H(j, j), H(j + 1, j) to (r, 0)
-        const double a = H[j][j], b = H[j + 1][j];
-        const double d = hypot(a, b);
-        const double cs = d > 0.0 ? a / d : 1.0, sn = d > 0.0 ? b / d : 0.0;
-        for (int q = j; q < m; ++q) {
-            const double u = H[j][q], v = H[j + 1][q];
-            H[j][q] = cs * u + sn * v;
-            H[j + 1][q] = -sn * u + cs * v;
-        }
-        const double gu = g[j], gv = g[j + 1];
-        g[j] = cs * gu + sn * gv;
-        g[j + 1] = -sn * gu + cs * gv;
-    }
-    for (int i = m - 1; i >= 0; --i) {
-        double acc = g[i];
-        for (int q = i + 1; q < m; ++q) acc -= H[i][q] * y[q];
-        y[i] = H[i][i] != 0.0 ? acc / H[i][i] : 0.0;
-    }
+    if (k <= 2)
+        wlsq_solve_t<2>(hA, hB, nr, beta2, k, y);
+    else if (k <= 4)
+        wlsq_solve_t<4>(hA, hB, nr, beta2, k, y);
+    else
+        wlsq_solve_t<WRAP_MAXK>(hA, hB, nr, beta2, k, y);
 }
 
-__global__ void k_wlsq(const double* __restrict__ hA, const double* __restrict__ hB, const double* __restrict__ nr,
-                       const double* __restrict__ beta2, int k, double* __restrict__ y) {
+// The stage's last norm, out = sum of the nblk partials (as k_wreduce with one product), then the
+// stage's least-squares solve into y by the thread that wrote it
+__global__ void __launch_bounds__(WT) k_wreduce_lsq(const double* __restrict__ partials, int nblk, double* out,
+                                                    const double* __restrict__ hA, const double* __restrict__ hB,
+                                                    const double* nrAll, const double* __restrict__ beta2, int k,
+                                                    double* __restrict__ y) {
     pdl_entry();
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    wlsq_solve(hA, hB, nr, beta2, k, y);
+    __shared__ double ws[WW];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += WT) s += partials[b];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) ws[wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < WW; ++q) t += ws[q];
+        out[0] = t;
+        wlsq_solve(hA, hB, nrAll, beta2, k, y);
+    }
 }
 
 // Levels small enough for one block (n <= WRAP_ONE_MAX): each reduction finishes in the block that
@@ -453,9 +503,9 @@ template <typename T>
 void launch_wscale(const T* w, const double* nrm2, T* v, int64_t n, cudaStream_t s) {
     launch_pdl(k_wscale<T>, wrap_blocks<T>(n), WT, 0, s, w, nrm2, v, n);
 }
-void launch_wlsq(const double* hA, const double* hB, const double* nr, const double* beta2, int k, double* y,
-                 cudaStream_t s) {
-    launch_pdl(k_wlsq, 1, 32, 0, s, hA, hB, nr, beta2, k, y);
+void launch_wreduce_lsq(const double* partials, int nblk, double* out, const double* hA, const double* hB,
+                        const double* nrAll, const double* beta2, int k, double* y, cudaStream_t s) {
+    launch_pdl(k_wreduce_lsq, 1, WT, 0, s, partials, nblk, out, hA, hB, nrAll, beta2, k, y);
 }
 
 #define SIB_WRAP_INST(T)                                                                                    \

@@ -264,6 +264,9 @@ template <typename T> int launch_wdots(const T* V, int64_t ld, int cnt, const T*
 template <typename T> int launch_wgs(const T* V, int64_t ld, int cnt, const double* coef, const T* win, T* wout,
                                      int64_t n, int mode, double* partials, cudaStream_t s);
 void launch_wreduce(const double* partials, int cnt, int nblk, double* out, cudaStream_t s);
+// the stage's last norm (one product) and then its least-squares solve, in one single-block launch
+void launch_wreduce_lsq(const double* partials, int nblk, double* out, const double* hA, const double* hB,
+                        const double* nrAll, const double* beta2, int k, double* y, cudaStream_t s);
 // Levels of at most WRAP_ONE_MAX values: one block forms each inner product completely (launch_wdots
 // and launch_wgs return nblk = 1 and write the sums themselves), the normalisations are fused
 // (launch_wnorm_one: beta2 = |r0|^2, V0 = r0 / |r0|; launch_wgs2_one: the second Gram-Schmidt pass,
@@ -276,8 +279,6 @@ template <typename T> void launch_wgs2_one(const T* V, int64_t ld, int cnt, cons
 template <typename T> void launch_wmaxpy(const T* V, int64_t ld, int cnt, const double* coef, double sign, const T* yin,
                                          T* yout, int64_t n, cudaStream_t s);
 template <typename T> void launch_wscale(const T* w, const double* nrm2, T* v, int64_t n, cudaStream_t s);
-void launch_wlsq(const double* hA, const double* hB, const double* nr, const double* beta2, int k, double* y,
-                 cudaStream_t s);
 
 // launchers (kernels_ib.cu)
 void launch_stencils(const double* X, int M, int Nf, int lmax, int** base, double** w64, float** w32,

@@ -699,11 +699,13 @@ void wrapped_smooth(sib_ctx* c, int l, const T* x, const T* b, T* xo, int k, cud
         int nb = launch_wgs<T>(V, n3, j + 1, hA + j * K1, w, w, n3, 1, part, s);
         KL(c, launch_wreduce(part, j + 1, nb, hB + j * K1, s));
         nb = launch_wgs<T>(V, n3, j + 1, hB + j * K1, w, w, n3, 2, part, s);
-        KL(c, launch_wreduce(part, 1, nb, nr + j, s));
+        if (j + 1 < k)
+            KL(c, launch_wreduce(part, 1, nb, nr + j, s));
+        else   // the stage's last norm and its least-squares solve
+            KL(c, launch_wreduce_lsq(part, nb, nr + j, hA, hB, nr, beta2, k, y, s));
         c->launches += 2;
         if (j + 1 < k) KL(c, launch_wscale<T>(w, nr + j, V + (size_t)(j + 1) * n3, n3, s));
     }
-    if (!one) KL(c, launch_wlsq(hA, hB, nr, beta2, k, y, s));
     KL(c, launch_wmaxpy<T>(Z, n3, k, y, 1.0, x, xo, n3, s));
 }
 
