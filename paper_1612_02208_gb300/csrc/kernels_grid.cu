@@ -377,6 +377,274 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4)
     }
 }
 
+// FP32 form of the tiled sweep with two vertically adjacent cells per thread (TX x TY / 2 threads):
+// the residual stencils of a pair share their x reads, and each thread keeps its cells' residuals
+// and patch corrections in registers.  Shared memory carries only what a neighbour reads: the u
+// residuals (read by the patch to the left), the lower cell's v residual (read by the pair below's
+// upper patch), the corrections d1 (read by the cell to the right) and the upper cell's d3 (read by
+// the pair above).  The ring of residual cells and the left / bottom ring of patches are formed by
+// the first threads as in k_vanka_tiled; staging, set-up data and the arithmetic are the same.
+constexpr int VK2_THREADS = TX * TY / 2;
+template <typename T, bool ZERO>
+__global__ void __launch_bounds__(VK2_THREADS, 8)
+    k_vanka_pair(GridK<T> g, VankaBulk<T> kb, const __grid_constant__ CUtensorMap mx,
+                 const __grid_constant__ CUtensorMap mb, int tma, int first_wave, const T* __restrict__ x,
+                 const T* __restrict__ b, T* __restrict__ xo) {
+    constexpr int NT = VK2_THREADS;
+    __shared__ __align__(128) T stage[VK_STAGE];
+    __shared__ T bs[7][VK_PY][VK_PX];   // patch factors of the patches of an active tile
+    __shared__ uint64_t bar;
+    T(*sb)[VK_BR][VK_W] = reinterpret_cast<T(*)[VK_BR][VK_W]>(stage);
+    T(*sx)[VK_XR][VK_W] = reinterpret_cast<T(*)[VK_XR][VK_W]>(stage + VK_XOFF);
+    T(*ds)[VK_PY][VK_PX] = reinterpret_cast<T(*)[VK_PY][VK_PX]>(stage + VK_XOFF);   // [0] d1, [1] d3
+    const int N = g.N, n = N * N, m = N - 1;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;   // ty: pair row, cells 2 ty, 2 ty + 1
+    const bool bulk = tma && i0 >= TX && i0 + 2 * TX <= N && j0 >= TY && j0 + 2 * TY <= N;
+    const bool early = (int)(blockIdx.y * gridDim.x + blockIdx.x) < first_wave;
+    bool act = false;
+    auto load_patch_ib = [&]() {
+        for (int q = tid; q < VK_PY * VK_PX; q += NT) {
+            const int pj = q / VK_PX, pi = q - pj * VK_PX;
+            const int cc = ((j0 - 1 + pj) & m) * N + ((i0 - 1 + pi) & m);
+#pragma unroll
+            for (int k = 0; k < 7; ++k) bs[k][pj][pi] = g.pf[(size_t)k * n + cc];
+        }
+    };
+    if (early) {
+        act = g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x];
+        if (act) load_patch_ib();
+    }
+    if (bulk && tid == 0) {
+        tma_prefetch_map(&mb);
+        if (!ZERO) tma_prefetch_map(&mx);
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    if (early) __syncthreads();
+    pdl_entry();
+    if (bulk && tid == 0) {
+        constexpr uint32_t bb = 3 * VK_BR * VK_W * sizeof(T), bx = 3 * VK_XR * VK_W * sizeof(T);
+        mbar_expect_tx(&bar, ZERO ? bb : bb + bx);
+        tma_load_3d(&sb[0][0][0], &mb, &bar, i0 - 4, j0 - 1, 0);
+        if (!ZERO) tma_load_3d(&sx[0][0][0], &mx, &bar, i0 - 4, j0 - 2, 0);
+    }
+    if (!early) {
+        act = g.tile != nullptr && g.tile[blockIdx.y * g.ntx + blockIdx.x];
+        if (act) load_patch_ib();
+    }
+    constexpr int RING = 2 * (TX + 2) + 2 * TY;
+    static_assert(RING <= NT && VK_PX + TY <= NT, "one ring cell and one ring patch per thread");
+    int ri2 = 0, rj2 = 0;
+    if (tid < TX + 2) {
+        ri2 = tid;
+    } else if (tid < 2 * (TX + 2)) {
+        ri2 = tid - (TX + 2);
+        rj2 = TY + 1;
+    } else if (tid < 2 * (TX + 2) + TY) {
+        rj2 = tid - 2 * (TX + 2) + 1;
+    } else {
+        ri2 = TX + 1;
+        rj2 = tid - 2 * (TX + 2) - TY + 1;
+    }
+    T fu[2] = {T(0), T(0)}, fv[2] = {T(0), T(0)}, fu1 = T(0), fv1 = T(0);
+    if (!ZERO && act) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int cc = (j0 + 2 * ty + c) * N + (i0 + tx);
+            fu[c] = g.fib[cc];
+            fv[c] = g.fib[n + cc];
+        }
+        if (tid < RING) {
+            const int c1 = ((j0 - 1 + rj2) & m) * N + ((i0 - 1 + ri2) & m);
+            fu1 = g.fib[c1];
+            fv1 = g.fib[n + c1];
+        }
+    }
+    if (!early) __syncthreads();
+    if (bulk) {
+        const bool ok = mbar_wait_bounded(&bar, 0, VK_WAIT_LIMIT);
+        if (!__syncthreads_and(ok)) {   // copies never completed: report, let them drain, leave
+            if (tid == 0 && g.err) *(volatile int*)g.err = SIB_DEV_ERR_TMA_WAIT;
+            mbar_wait_bounded(&bar, 0, VK_WAIT_LIMIT);
+            return;
+        }
+    } else {   // b at rows j0-1.., columns i0-1..i0+32; x at rows j0-2.., columns i0-2..i0+33
+        constexpr int NB = VK_BR * (TX + 2), NX = VK_XR * (TX + 4);
+        constexpr int PB = (NB + NT - 1) / NT, PXN = (NX + NT - 1) / NT;
+        T vb[PB][3], vx[PXN][3];
+#pragma unroll
+        for (int k = 0; k < PB; ++k) {   // every load issued before the first store
+            const int q = tid + k * NT;
+            if (q < NB) {
+                const int rj = q / (TX + 2), ri = q - rj * (TX + 2);
+                const int gc = ((j0 - 1 + rj) & m) * N + ((i0 - 1 + ri) & m);
+                vb[k][0] = b[gc];
+                vb[k][1] = b[n + gc];
+                vb[k][2] = b[2 * n + gc];
+            }
+        }
+        if (!ZERO) {
+#pragma unroll
+            for (int k = 0; k < PXN; ++k) {
+                const int q = tid + k * NT;
+                if (q < NX) {
+                    const int jj = q / (TX + 4), ii = q - jj * (TX + 4);
+                    const int gc = ((j0 - 2 + jj) & m) * N + ((i0 - 2 + ii) & m);
+                    vx[k][0] = x[gc];
+                    vx[k][1] = x[n + gc];
+                    vx[k][2] = x[2 * n + gc];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PB; ++k) {
+            const int q = tid + k * NT;
+            if (q < NB) {
+                const int rj = q / (TX + 2), ri = q - rj * (TX + 2);
+                sb[0][rj][ri + 3] = vb[k][0];
+                sb[1][rj][ri + 3] = vb[k][1];
+                sb[2][rj][ri + 3] = vb[k][2];
+            }
+        }
+        if (!ZERO) {
+#pragma unroll
+            for (int k = 0; k < PXN; ++k) {
+                const int q = tid + k * NT;
+                if (q < NX) {
+                    const int jj = q / (TX + 4), ii = q - jj * (TX + 4);
+                    sx[0][jj][ii + 2] = vx[k][0];
+                    sx[1][jj][ii + 2] = vx[k][1];
+                    sx[2][jj][ii + 2] = vx[k][2];
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // residuals of the pair, staged coordinates (ri, rj) = (tx + 1, 2 ty + 1 + c), c = 0 lower, 1 upper
+    const int ri = tx + 1, rj0 = 2 * ty + 1, sc = ri + 3;
+    T ru[2], rv[2], rp[2], xu[2] = {T(0), T(0)}, xv[2] = {T(0), T(0)}, xp[2] = {T(0), T(0)};
+    if (ZERO) {   // x = 0: the residual is b, already in place
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            ru[c] = sb[0][rj0 + c][sc];
+            rv[c] = sb[1][rj0 + c][sc];
+            rp[c] = sb[2][rj0 + c][sc];
+        }
+    } else {
+        const int y0 = rj0 + 1;   // staged x row of the lower cell
+        const T uS = sx[0][y0 - 1][sc], u0 = sx[0][y0][sc], u1 = sx[0][y0 + 1][sc], uN = sx[0][y0 + 2][sc];
+        const T uE0 = sx[0][y0][sc + 1], uW0 = sx[0][y0][sc - 1], uE1 = sx[0][y0 + 1][sc + 1], uW1 = sx[0][y0 + 1][sc - 1];
+        const T vS = sx[1][y0 - 1][sc], v0 = sx[1][y0][sc], v1 = sx[1][y0 + 1][sc], vN = sx[1][y0 + 2][sc];
+        const T vE0 = sx[1][y0][sc + 1], vW0 = sx[1][y0][sc - 1], vE1 = sx[1][y0 + 1][sc + 1], vW1 = sx[1][y0 + 1][sc - 1];
+        const T pS = sx[2][y0 - 1][sc], p0 = sx[2][y0][sc], p1 = sx[2][y0 + 1][sc];
+        const T pW0 = sx[2][y0][sc - 1], pW1 = sx[2][y0 + 1][sc - 1];
+        T Au0 = g.a0 * u0 - g.c * ((uE0 + uW0) + (u1 + uS)) + (p0 - pW0) * g.inv_h;
+        T Av0 = g.a0 * v0 - g.c * ((vE0 + vW0) + (v1 + vS)) + (p0 - pS) * g.inv_h;
+        T Au1 = g.a0 * u1 - g.c * ((uE1 + uW1) + (uN + u0)) + (p1 - pW1) * g.inv_h;
+        T Av1 = g.a0 * v1 - g.c * ((vE1 + vW1) + (vN + v0)) + (p1 - p0) * g.inv_h;
+        if (act) {
+            Au0 -= g.dt * fu[0];
+            Av0 -= g.dt * fv[0];
+            Au1 -= g.dt * fu[1];
+            Av1 -= g.dt * fv[1];
+        }
+        ru[0] = sb[0][rj0][sc] - Au0;
+        rv[0] = sb[1][rj0][sc] - Av0;
+        rp[0] = sb[2][rj0][sc] + ((uE0 - u0) + (v1 - v0)) * g.inv_h;
+        ru[1] = sb[0][rj0 + 1][sc] - Au1;
+        rv[1] = sb[1][rj0 + 1][sc] - Av1;
+        rp[1] = sb[2][rj0 + 1][sc] + ((uE1 - u1) + (vN - v1)) * g.inv_h;
+        xu[0] = u0;
+        xu[1] = u1;
+        xv[0] = v0;
+        xv[1] = v1;
+        xp[0] = p0;
+        xp[1] = p1;
+        // handed to the neighbours: both u residuals, the lower v residual
+        sb[0][rj0][sc] = ru[0];
+        sb[0][rj0 + 1][sc] = ru[1];
+        sb[1][rj0][sc] = rv[0];
+        if (tid < RING) {   // one ring cell, all three components in place
+            const int sxc = ri2 + 3, sy = rj2 + 1;
+            const T uc = sx[0][sy][sxc], vc = sx[1][sy][sxc], pc = sx[2][sy][sxc];
+            const T uE = sx[0][sy][sxc + 1], vN1 = sx[1][sy + 1][sxc];
+            T Au = g.a0 * uc - g.c * ((uE + sx[0][sy][sxc - 1]) + (sx[0][sy + 1][sxc] + sx[0][sy - 1][sxc])) +
+                   (pc - sx[2][sy][sxc - 1]) * g.inv_h;
+            T Av = g.a0 * vc - g.c * ((sx[1][sy][sxc + 1] + sx[1][sy][sxc - 1]) + (vN1 + sx[1][sy - 1][sxc])) +
+                   (pc - sx[2][sy - 1][sxc]) * g.inv_h;
+            if (act) {
+                Au -= g.dt * fu1;
+                Av -= g.dt * fv1;
+            }
+            sb[0][rj2][sxc] = sb[0][rj2][sxc] - Au;
+            sb[1][rj2][sxc] = sb[1][rj2][sxc] - Av;
+            sb[2][rj2][sxc] = sb[2][rj2][sxc] + ((uE - uc) + (vN1 - vc)) * g.inv_h;
+        }
+        __syncthreads();   // residuals handed over; the x area is free for the corrections
+    }
+    const T ih = g.inv_h;
+    auto solve = [&](int pi, int pj, T r0, T r1, T r2, T r3, T r4, T& d0, T& d1, T& d2, T& d3, T& dp) {
+        if (!act) {
+            const T tu0 = kb.ai0 * r0 + kb.ai1 * r1, tu1 = kb.ai1 * r0 + kb.ai0 * r1;
+            const T tv0 = kb.ai0 * r2 + kb.ai1 * r3, tv1 = kb.ai1 * r2 + kb.ai0 * r3;
+            dp = (ih * ((tu0 - tu1) + (tv0 - tv1)) - r4) * kb.invS;
+            d0 = tu0 - kb.s0 * dp;
+            d1 = tu1 + kb.s0 * dp;
+            d2 = tv0 - kb.s0 * dp;
+            d3 = tv1 + kb.s0 * dp;
+        } else {
+            T f[7];
+#pragma unroll
+            for (int k = 0; k < 7; ++k) f[k] = bs[k][pj][pi];
+            patch_solve(f, ih, r0, r1, r2, r3, r4, d0, d1, d2, d3, dp);
+        }
+    };
+    // the pair's patches (pi, pj) = (tx + 1, 2 ty + 1 + c): r_u of the right face from the cell to the
+    // right, r_v of the upper cell's top face from the pair above (or the ring)
+    T d0[2], d1[2], d2[2], d3[2], dp[2];
+    const T ruR0 = sb[0][rj0][sc + 1], ruR1 = sb[0][rj0 + 1][sc + 1], rvT = sb[1][rj0 + 2][sc];
+    solve(ri, rj0, ru[0], ruR0, rv[0], rv[1], rp[0], d0[0], d1[0], d2[0], d3[0], dp[0]);
+    solve(ri, rj0 + 1, ru[1], ruR1, rv[1], rvT, rp[1], d0[1], d1[1], d2[1], d3[1], dp[1]);
+    // ring patches: bottom row pj = 0 (their d3 feeds the tile's bottom cells), then the left column
+    // pi = 0 (their d1 feeds the tile's left cells); one call, no divergent copies
+    T e0 = T(0), e1 = T(0), e2 = T(0), e3 = T(0), ep = T(0);
+    const bool ringPatch = tid < VK_PX + TY;
+    const bool rowPatch = tid < VK_PX;
+    const int qi = rowPatch ? tid : 0, qj = rowPatch ? 0 : tid - VK_PX + 1;
+    if (ringPatch)
+        solve(qi, qj, sb[0][qj][qi + 3], sb[0][qj][qi + 4], sb[1][qj][qi + 3], sb[1][qj + 1][qi + 3],
+              sb[2][qj][qi + 3], e0, e1, e2, e3, ep);
+    ds[0][rj0][ri] = d1[0];   // the x area is no longer read
+    ds[0][rj0 + 1][ri] = d1[1];
+    ds[1][rj0 + 1][ri] = d3[1];
+    if (ringPatch) {
+        if (rowPatch)
+            ds[1][qj][qi] = e3;
+        else
+            ds[0][qj][qi] = e1;
+    }
+    __syncthreads();
+    const T hw = T(0.5) * g.omega;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int cc = (j0 + 2 * ty + c) * N + (i0 + tx);
+        const T du = hw * (d0[c] + ds[0][rj0 + c][ri - 1]);
+        const T dv = hw * (d2[c] + (c == 0 ? ds[1][rj0 - 1][ri] : d3[0]));
+        const T dq = g.omega * dp[c];
+        if (ZERO) {
+            xo[cc] = du;
+            xo[n + cc] = dv;
+            xo[2 * n + cc] = dq;
+        } else {
+            xo[cc] = xu[c] + du;
+            xo[n + cc] = xv[c] + dv;
+            xo[2 * n + cc] = xp[c] + dq;
+        }
+    }
+}
+
 // Tensor map of a level vector [u | v | p] viewed as N x N x 3 (column fastest) with a box of
 // VK_W x rows x 3; false if the base is not 16-byte aligned or the driver cannot encode it.
 // Encoded maps are kept per thread, keyed by (base, N, element size, rows).
@@ -424,11 +692,11 @@ static bool field_map(CUtensorMap* out, const void* base, int N, int es, int row
 
 // blocks of a kernel that are resident on the GPU at once (occupancy x SM count); 0 if unknown
 template <typename K>
-int resident_blocks(K kern) {
+int resident_blocks(K kern, int threads = TX * TY) {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, TX * TY, 0) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, 0) != cudaSuccess)
         return 0;
     return sms * per;
 }
@@ -447,6 +715,11 @@ void launch_vanka_any(const GridK<T>& g, const T* x, const T* b, T* xo, cudaStre
     // interior tiles exist from N = 4 TX on; the maps are only read by those tiles
     const int tma = g.N >= 4 * TX && field_map(&mb, b, g.N, sizeof(T), VK_BR) &&
                     (ZERO || field_map(&mx, x, g.N, sizeof(T), VK_XR));
+    if constexpr (sizeof(T) == 4) {   // FP32: two cells per thread
+        static const int first_wave2 = resident_blocks(k_vanka_pair<T, ZERO>, VK2_THREADS);
+        launch_pdl(k_vanka_pair<T, ZERO>, grd, dim3(TX, TY / 2), 0, s, g, kb, mx, mb, tma, first_wave2, x, b, xo);
+        return;
+    }
     static const int first_wave = resident_blocks(k_vanka_tiled<T, ZERO>);
     launch_pdl(k_vanka_tiled<T, ZERO>, grd, blk, 0, s, g, kb, mx, mb, tma, first_wave, x, b, xo);
 }

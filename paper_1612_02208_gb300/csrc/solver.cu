@@ -1851,7 +1851,8 @@ void time_kernel(sib_ctx* c, int kernel, int l, int reps, bool cold, cudaStream_
                 launch_residual<T>(g, (const T*)b.x, (const T*)b.b, (T*)b.r, s);
                 break;
             case SIB_KERNEL_SPREAD:
-                launch_spread<T>(k, F, (T*)b.fib, lv.tiles, lv.nTiles, lv.hnTiles, lv.tx, lv.ty, lv.ntx, lv.spreadWarp, s);
+                launch_spread<T>(k, F, (T*)b.fib, lv.tiles, lv.nTiles, lv.hnRowTiles, lv.tx, lv.ty, lv.ntx, lv.spreadWarp,
+                                 s, lv.rowSlots, lv.nRowTiles);
                 break;
             case SIB_KERNEL_INTERP:
                 launch_interp<T>(k, (const T*)b.x, U, s);
@@ -1880,9 +1881,12 @@ void time_kernel(sib_ctx* c, int kernel, int l, int reps, bool cold, cudaStream_
         case SIB_KERNEL_RESIDUAL:
             by = 9.0 * n * w + 2.0 * active * w;
             break;
-        case SIB_KERNEL_SPREAD:   // every active face written, every marker's weights and force read once
-            by = 2.0 * active * w + (double)c->M * 2.0 * (8.0 * w + 4.0 + w) + 2.0 * (n + 1) * 4.0;
+        case SIB_KERNEL_SPREAD: {   // every face of a stencil-touched tile written and its bin offset read, every
+                                    // marker's weights, sorted id and force read once
+            const double rows = c->haveIB ? (double)lv.hnRowTiles * lv.tx * lv.ty : 0.0;
+            by = 2.0 * rows * w + (double)c->M * 2.0 * (8.0 * w + 4.0 + w) + 2.0 * rows * 4.0;
             break;
+        }
         case SIB_KERNEL_INTERP:   // stencil origin, weights, W^2 velocities (distinct faces at most), U
             by = (double)c->M * 2.0 * (4.0 + 8.0 * w + w) + std::min(2.0 * active, (double)c->M * 2.0 * lv.W * lv.W) * w;
             break;
