@@ -61,7 +61,7 @@ CSRC = os.path.join(ROOT, "paper_1612_02208_gb300", "csrc")
 # the source text of each roofline kernel: file, first and last marker (the kernel and its launcher)
 KERNEL_SOURCES = {
     "k_ib_window_f32": ("kernels_ib.cu", "struct WinVec;", "template void launch_ib_window<float>"),
-    "k_vanka_f32": ("kernels_grid.cu", "k_vanka_tiled(GridK<T> g", "void launch_vanka("),
+    "k_vanka_f32": ("kernels_grid.cu", "k_vanka_pair(GridK<T> g", "void launch_vanka("),
 }
 
 

@@ -561,6 +561,135 @@ void launch_spread(const IBK<T>& k, const T* F, T* f, const int* tiles, const in
 }
 
 // ------------------------------------------------------------------------------------------
+// Spreading as a stored sparse product.  The gather's walk is done once per set-up: for every face of
+// a stencil-touched tile and component, the markers it collects, in the gather's order (b, then a,
+// then the bin's Morton order), with their weight products wx[a] wy[b] in FP64 and in FP32 (each
+// formed as gather_face forms it).  Every (marker, a, b) pair lands on exactly one face, so a
+// component holds M W^2 entries.  Row R = (c maxRow + r) tx ty + q: row tile r of the list, face q of
+// the tile (row by row), component c.  Applying it, f = (1/h^2) S F is one ordered dot product per
+// face, with the gather's rounding.
+__device__ __forceinline__ void spread_face(int tile, int tx, int ty, int ntx, int q, int& i, int& j) {
+    i = (tile % ntx) * tx + q % tx;
+    j = (tile / ntx) * ty + q / tx;
+}
+// counts per face, their exclusive prefix within the tile (loc) and the tile's total (tileCnt)
+__global__ void __launch_bounds__(256) k_spread_count(IBK<double> k, const int* __restrict__ tiles,
+                                                      const int* __restrict__ rowSlots, const int* __restrict__ nRow,
+                                                      int maxRow, int tx, int ty, int ntx, int* __restrict__ loc,
+                                                      int* __restrict__ tileCnt) {
+    pdl_entry();
+    __shared__ int wsum[8];
+    const int per = tx * ty, q = threadIdx.x, c = blockIdx.y, r = blockIdx.x;
+    const int mk = k.N - 1;
+    int cnt = 0;
+    if (r < *nRow && q < per) {
+        int i, j;
+        spread_face(tiles[rowSlots[r]], tx, ty, ntx, q, i, j);
+        const int* bs = c ? k.binStart[1] : k.binStart[0];
+        for (int b = 0; b < k.W; ++b)
+            for (int a = 0; a < k.W; ++a) {
+                const uint32_t bin = morton((i - a) & mk, (j - b) & mk);
+                cnt += bs[bin + 1] - bs[bin];
+            }
+    }
+    // exclusive block scan of the 256 counts
+    const int lane = q & 31, w = q >> 5;
+    int x = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    int before = 0;
+    for (int v = 0; v < w; ++v) before += wsum[v];
+    if (q < per) loc[(size_t)(c * maxRow + r) * per + q] = before + x - cnt;
+    if (q == 255) tileCnt[c * maxRow + r] = before + x;
+}
+template <typename T>
+__device__ __forceinline__ T spread_product(const T* w, int m, int a, int b) {
+    return w[8 * m + a] * w[8 * m + 4 + b];
+}
+// the rows' absolute offsets (off[R] = tileOff[tile] + loc[R], off[rows] = the total) and the entries
+__global__ void __launch_bounds__(256) k_spread_fill(IBK<double> k, const float* __restrict__ w32u,
+                                                     const float* __restrict__ w32v, const int* __restrict__ tiles,
+                                                     const int* __restrict__ rowSlots, const int* __restrict__ nRow,
+                                                     int maxRow, int tx, int ty, int ntx, const int* __restrict__ loc,
+                                                     const int* __restrict__ tileOff, int64_t cap, int* __restrict__ off,
+                                                     int* __restrict__ col, double* __restrict__ v64,
+                                                     float* __restrict__ v32) {
+    pdl_entry();
+    const int per = tx * ty, q = threadIdx.x, c = blockIdx.y, r = blockIdx.x;
+    if (q >= per) return;
+    const size_t R = (size_t)(c * maxRow + r) * per + q;
+    int p = tileOff[c * maxRow + r] + loc[R];
+    off[R] = p;
+    if (R + 1 == (size_t)2 * maxRow * per) off[R + 1] = tileOff[2 * maxRow];
+    if (r >= *nRow) return;
+    int i, j;
+    spread_face(tiles[rowSlots[r]], tx, ty, ntx, q, i, j);
+    const int mk = k.N - 1;
+    const int* bs = c ? k.binStart[1] : k.binStart[0];
+    const int* srt = c ? k.sorted[1] : k.sorted[0];
+    const double* wg = c ? k.wgt[1] : k.wgt[0];
+    const float* w32 = c ? w32v : w32u;
+    for (int b = 0; b < k.W; ++b)
+        for (int a = 0; a < k.W; ++a) {
+            const uint32_t bin = morton((i - a) & mk, (j - b) & mk);
+            for (int s = bs[bin]; s < bs[bin + 1]; ++s, ++p) {
+                if (p >= cap) continue;   // cannot happen: a component holds exactly M W^2 entries
+                const int m = srt[s];
+                col[p] = m;
+                v64[p] = spread_product(wg, m, a, b);
+                v32[p] = spread_product(w32, m, a, b);
+            }
+        }
+}
+void launch_spread_store(const IBK<double>& k, const float* w32u, const float* w32v, const int* tiles,
+                         const int* rowSlots, const int* nRow, int maxRow, int tx, int ty, int ntx, int* loc,
+                         int* tileCnt, int* tileOff, int64_t cap, int* off, int* col, double* v64, float* v32,
+                         cudaStream_t s) {
+    if (maxRow == 0) return;
+    const dim3 grd(maxRow, 2);
+    launch_pdl(k_spread_count, grd, 256, 0, s, k, tiles, rowSlots, nRow, maxRow, tx, ty, ntx, loc, tileCnt);
+    launch_pdl(k_scan_single, 1, 1024, 0, s, (const int*)tileCnt, 2 * maxRow, tileOff);
+    launch_pdl(k_spread_fill, grd, 256, 0, s, k, w32u, w32v, tiles, rowSlots, nRow, maxRow, tx, ty, ntx,
+               (const int*)loc, (const int*)tileOff, cap, off, col, v64, v32);
+}
+// f = (1/h^2) S F from the stored product: one thread per face of a stencil-touched tile and component
+template <typename T>
+__global__ void __launch_bounds__(256) k_spread_stored(const int* __restrict__ off, const int* __restrict__ col,
+                                                       const T* __restrict__ val, const T* __restrict__ F, int M,
+                                                       T inv_h2, const int* __restrict__ tiles,
+                                                       const int* __restrict__ rowSlots, const int* __restrict__ nRow,
+                                                       int maxRow, int N, int tx, int ty, int ntx, T* __restrict__ f) {
+    pdl_entry();
+    const int per = tx * ty, q = threadIdx.x, c = blockIdx.y, r = blockIdx.x;
+    if (r >= *nRow || q >= per) return;
+    const size_t R = (size_t)(c * maxRow + r) * per + q;
+    const T* Fc = F + (size_t)c * M;
+    T acc = T(0);
+    const int e1 = off[R + 1];
+    for (int e = off[R]; e < e1; ++e) acc += val[e] * Fc[col[e]];
+    int i, j;
+    spread_face(tiles[rowSlots[r]], tx, ty, ntx, q, i, j);
+    f[(size_t)c * N * N + (size_t)j * N + i] = inv_h2 * acc;
+}
+template <typename T>
+void launch_spread_stored(const int* off, const int* col, const T* val, const T* F, int M, T inv_h2, const int* tiles,
+                          const int* rowSlots, const int* nRow, int maxRow, int N, int tx, int ty, int ntx, T* f,
+                          cudaStream_t s) {
+    if (maxRow == 0) return;
+    launch_pdl(k_spread_stored<T>, dim3(maxRow, 2), 256, 0, s, off, col, val, F, M, inv_h2, tiles, rowSlots, nRow,
+               maxRow, N, tx, ty, ntx, f);
+}
+template void launch_spread_stored<float>(const int*, const int*, const float*, const float*, int, float, const int*,
+                                          const int*, const int*, int, int, int, int, int, float*, cudaStream_t);
+template void launch_spread_stored<double>(const int*, const int*, const double*, const double*, int, double,
+                                           const int*, const int*, const int*, int, int, int, int, int, double*,
+                                           cudaStream_t);
+
+// ------------------------------------------------------------------------------------------
 // Set-up assembly of IB operator entries from the markers, B = [S K J]^l =
 // -(1/h^2) sum_e kappa_e d_e d_e^T with d_e = J_l[a] - J_l[b] (the level-l stencil rows of the
 // spring's two markers), used where the assembled windows overflow.

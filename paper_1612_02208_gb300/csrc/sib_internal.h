@@ -303,6 +303,16 @@ template <typename T> void launch_spring(const int* start, const int* nbr, const
 template <typename T> void launch_spread(const IBK<T>& k, const T* F, T* f, const int* tiles, const int* nTiles,
                                          int maxTiles, int tx, int ty, int ntx, int warpPerFace, cudaStream_t s,
                                          const int* rowSlots = nullptr, const int* nRow = nullptr);
+// the spreading's walk stored at set-up (rows: faces of the stencil-touched tiles, entries in the
+// gather's order, cap = 2 M W^2), then applied as one ordered dot product per face
+void launch_spread_store(const IBK<double>& k, const float* w32u, const float* w32v, const int* tiles,
+                         const int* rowSlots, const int* nRow, int maxRow, int tx, int ty, int ntx, int* loc,
+                         int* tileCnt, int* tileOff, int64_t cap, int* off, int* col, double* v64, float* v32,
+                         cudaStream_t s);
+template <typename T>
+void launch_spread_stored(const int* off, const int* col, const T* val, const T* F, int M, T inv_h2, const int* tiles,
+                          const int* rowSlots, const int* nRow, int maxRow, int N, int tx, int ty, int ntx, T* f,
+                          cudaStream_t s);
 // the patch entries B(f, f), B(f, f + e) and the coarsest dense IB block from the markers and springs
 // (where the assembled windows are not available), by fixed-order gathers
 void launch_patch_entries(const IBK<double>& k, const int* adjStart, const int* adjNbr, const double* adjKap,

@@ -80,6 +80,18 @@ struct Level {
     int* slotOf = nullptr;               // tile -> slot in the active-tile list, -1 if inactive
     int useWindow = 0;                   // windows valid on this level
     int applyWindow = 0;                 // the solve applies the IB operator through the windows
+    // the spreading's walk stored for the marker path (levels that do not apply the windows): row
+    // offsets over the faces of the stencil-touched tiles, per-tile counts and offsets, and the
+    // entries (marker, weight product in FP64 and FP32)
+    int* spLoc = nullptr;
+    int* spOff = nullptr;
+    int* spTileCnt = nullptr;
+    int* spTileOff = nullptr;
+    int* spCol = nullptr;
+    double* spV64 = nullptr;
+    float* spV32 = nullptr;
+    size_t spRowsCap = 0, spEntCap = 0;
+    bool spReady = false;
     // box RAS smoother: boxes meeting IB windows, their slots, and the owned rows of the subdomain
     // inverses (slot 0 the shared IB-free inverse), FP64 and FP32
     int* rasList = nullptr;
@@ -298,6 +310,20 @@ void dot_into(sib_ctx* c, const double* x, const double* y, int64_t n, double* d
     KL(c, launch_reduce_partials(c->part, 1, NBLK, dst, s));
 }
 
+// f = (1/h^2) S F on the tiles a marker stencil touches: the stored walk where the set-up made it,
+// else the cell-binned gather
+template <typename T>
+void spread_apply(sib_ctx* c, const Level& lv, const IBK<T>& k, const T* F, T* f, cudaStream_t s) {
+    if (lv.spReady) {
+        const T* val = Prec<T>::id == 0 ? (const T*)(const void*)lv.spV64 : (const T*)(const void*)lv.spV32;
+        KL(c, launch_spread_stored<T>(lv.spOff, lv.spCol, val, F, c->M, k.inv_h2, lv.tiles, lv.rowSlots, lv.nRowTiles,
+                                      lv.hnRowTiles, lv.N, lv.tx, lv.ty, lv.ntx, f, s));
+        return;
+    }
+    KL(c, launch_spread<T>(k, F, f, lv.tiles, lv.nTiles, lv.hnRowTiles, lv.tx, lv.ty, lv.ntx, lv.spreadWarp, s,
+                           lv.rowSlots, lv.nRowTiles));
+}
+
 // f = [S K J]^l u (velocity part of x), written into the level's fib (only IB-active tiles)
 template <typename T>
 void ib_apply(sib_ctx* c, int l, const T* u, cudaStream_t s) {
@@ -314,8 +340,7 @@ void ib_apply(sib_ctx* c, int l, const T* u, cudaStream_t s) {
     T* F = (T*)c->F[pi];
     KL(c, launch_interp<T>(k, u, U, s));
     KL(c, launch_spring<T>(c->adjStart, c->adjNbr, kapp<T>(c), c->M, U, F, s));
-    KL(c, launch_spread<T>(k, F, (T*)lv.p[pi].fib, lv.tiles, lv.nTiles, lv.hnRowTiles, lv.tx, lv.ty, lv.ntx,
-                           lv.spreadWarp, s, lv.rowSlots, lv.nRowTiles));
+    spread_apply<T>(c, lv, k, F, (T*)lv.p[pi].fib, s);
 }
 
 template <typename T>
@@ -1356,6 +1381,33 @@ void setup(sib_ctx* c, cudaStream_t s) {
             const double winEnt = (double)lv.hnTiles * lv.tx * lv.ty * 2.0 * WIN_SIZE;
             const double pairs = (double)c->M * 2.0 * lv.W * lv.W;
             lv.applyWindow = c->haveIB && lv.useWindow && (l < c->lmax || winEnt <= 8.0 * pairs);
+            lv.spReady = false;
+            if (c->haveIB && !lv.applyWindow && lv.hnRowTiles > 0) {   // the marker path's stored spreading
+                const size_t rows = 2 * (size_t)lv.hnRowTiles * lv.tx * lv.ty;
+                const size_t ent = 2 * (size_t)c->M * lv.W * lv.W;
+                if (rows > lv.spRowsCap) {
+                    for (void* p : {(void*)lv.spLoc, (void*)lv.spOff, (void*)lv.spTileCnt, (void*)lv.spTileOff})
+                        dfree(c, p);
+                    lv.spLoc = (int*)dalloc(c, sizeof(int) * rows);
+                    lv.spOff = (int*)dalloc(c, sizeof(int) * (rows + 1));
+                    lv.spTileCnt = (int*)dalloc(c, sizeof(int) * 2 * (size_t)lv.hnRowTiles);
+                    lv.spTileOff = (int*)dalloc(c, sizeof(int) * (2 * (size_t)lv.hnRowTiles + 1));
+                    lv.spRowsCap = rows;
+                }
+                if (ent > lv.spEntCap) {
+                    for (void* p : {(void*)lv.spCol, (void*)lv.spV64, (void*)lv.spV32}) dfree(c, p);
+                    lv.spCol = (int*)dalloc(c, sizeof(int) * ent);
+                    lv.spV64 = (double*)dalloc(c, sizeof(double) * ent);
+                    lv.spV32 = (float*)dalloc(c, sizeof(float) * ent);
+                    lv.spEntCap = ent;
+                }
+                c->launches += 3;
+                launch_spread_store(ibk<double>(c, l), (const float*)lv.p[1].w[0], (const float*)lv.p[1].w[1], lv.tiles,
+                                    lv.rowSlots, lv.nRowTiles, lv.hnRowTiles, lv.tx, lv.ty, lv.ntx, lv.spLoc,
+                                    lv.spTileCnt, lv.spTileOff, (int64_t)ent, lv.spOff, lv.spCol, lv.spV64, lv.spV32,
+                                    s);
+                lv.spReady = true;
+            }
         }
         Level& l0 = c->L[0];
         CK(cudaMemsetAsync(c->B0, 0, sizeof(double) * 2 * (size_t)c->n0 / 3 * c->n0 / 3, s));
@@ -1851,8 +1903,7 @@ void time_kernel(sib_ctx* c, int kernel, int l, int reps, bool cold, cudaStream_
                 launch_residual<T>(g, (const T*)b.x, (const T*)b.b, (T*)b.r, s);
                 break;
             case SIB_KERNEL_SPREAD:
-                launch_spread<T>(k, F, (T*)b.fib, lv.tiles, lv.nTiles, lv.hnRowTiles, lv.tx, lv.ty, lv.ntx, lv.spreadWarp,
-                                 s, lv.rowSlots, lv.nRowTiles);
+                spread_apply<T>(c, lv, k, F, (T*)b.fib, s);
                 break;
             case SIB_KERNEL_INTERP:
                 launch_interp<T>(k, (const T*)b.x, U, s);
