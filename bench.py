@@ -76,6 +76,8 @@ def parse_args(argv=None):
     p.add_argument("--no-paper", action="store_true", help="skip the paper-workload and cavity tables")
     p.add_argument("--quick", action="store_true", help="headline only (no other legs)")
     p.add_argument("--large-n", type=int, default=LARGE_N, help="grid of the large-grid V-cycle roofline")
+    p.add_argument("--profile-setup", action="store_true",
+                   help="the headline's set-up twice inside an NVTX range (for an ncu launch list)")
     p.add_argument("--profile-vcycle", choices=["headline", "large", "large64", "large2k", "ras8o2"], default=None,
                    help="two FP32 V-cycles in an NVTX range 'vcycle', with a one-vector FGMRES basis (the small-memory "
                         "case for ncu captures): 'headline' = the headline workload and smoother, 'large' = the "
@@ -1094,6 +1096,33 @@ def run_profile_vcycle(which):
     S.close()
 
 
+def run_profile_setup():
+    """The headline's per-step set-up (set_structure + setup: binning, windows, patch factors, SC
+    eigenvalue estimates, coarsest pseudo-inverse), twice inside an NVTX range "setup" after one
+    outside it, each timed by CUDA events: the case the set-up's launch list uses."""
+    import torch
+    from paper_1612_02208_gb300 import sib
+    dev = torch.device("cuda")
+    H = Headline(sib, torch, dev)
+    stream = torch.cuda.current_stream()
+    H.S.set_structure(H.X, H.E, H.kap)
+    H.S.setup()
+    torch.cuda.synchronize()
+    ms = []
+    torch.cuda.nvtx.range_push("setup")
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        H.S.set_structure(H.X, H.E, H.kap)
+        H.S.setup()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(round(e0.elapsed_time(e1), 3))
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_setup": H.prob.name, "setup_ms": ms, "launches": H.S.launch_count}))
+    H.S.close()
+
+
 def run_profile_solve():
     """One FGMRES solve (Vanka, kappa = 1e2, FP32 V-cycle) of the 128^2 disk without CUDA graphs."""
     import torch
@@ -1115,6 +1144,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.profile_vcycle:
         run_profile_vcycle(args.profile_vcycle)
+    elif args.profile_setup:
+        run_profile_setup()
     elif args.profile_solve:
         run_profile_solve()
     elif args.cpu_breadth:

@@ -129,6 +129,10 @@ struct sib_ctx {
     void* gjWork = nullptr;              // work arrays of the blocked Gauss-Jordan inversion
     cudaStream_t aux = nullptr;          // set-up work that runs beside the main stream
     cudaEvent_t evFork = nullptr, evJoin = nullptr;
+    // the levels' eigenvalue estimates run side by side, one stream (and completion event) per level
+    static constexpr int LVS = 16;
+    cudaStream_t lvStream[LVS] = {};
+    cudaEvent_t lvDone[LVS] = {};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // structure
     int M = 0, E = 0;
@@ -305,9 +309,12 @@ const T* kapp(sib_ctx* c) {
         return c->kap32;
 }
 
-void dot_into(sib_ctx* c, const double* x, const double* y, int64_t n, double* dst, cudaStream_t s) {
-    KL(c, launch_dot_partials(x, y, n, c->part, NBLK, s));
-    KL(c, launch_reduce_partials(c->part, 1, NBLK, dst, s));
+// dst = x . y (FP64, fixed order); part: NBLK partial sums (default: the context's)
+void dot_into(sib_ctx* c, const double* x, const double* y, int64_t n, double* dst, cudaStream_t s,
+              double* part = nullptr) {
+    if (!part) part = c->part;
+    KL(c, launch_dot_partials(x, y, n, part, NBLK, s));
+    KL(c, launch_reduce_partials(part, 1, NBLK, dst, s));
 }
 
 // f = (1/h^2) S F on the tiles a marker stencil touches: the stored walk where the set-up made it,
@@ -1007,15 +1014,16 @@ void alloc_krylov(sib_ctx* c) {
 
 // Power iterations for lambda_max of DA^{-1} A_IB and of DM^{-1} D At^{-1} G on level l (FP64),
 // from the hash start vector; everything stays on the device, ||w||^2 of the last iterate lands in
-// scal[slot] (setup reads all levels back with one synchronisation per operator).
-void power_A_enqueue(sib_ctx* c, int l, int slot, cudaStream_t s) {
+// scal[slot] (setup reads all levels back with one synchronisation per operator).  A level's chain
+// touches only that level's buffers, its slot and its own NBLK partial sums (part).
+void power_A_enqueue(sib_ctx* c, int l, int slot, double* part, cudaStream_t s) {
     Level& lv = c->L[l];
     const int64_t nv = 2LL * lv.N * lv.N;
     double* v = (double*)lv.p[0].tv[6];
     double* w = (double*)lv.p[0].tv[7];
     GridK<double> g = gridk<double>(c, l);
     KL(c, launch_hash_vector(v, nv, s));
-    dot_into(c, v, v, nv, c->scal + slot, s);
+    dot_into(c, v, v, nv, c->scal + slot, s, part);
     KL(c, launch_scale(v, c->scal, slot, nv, s));
     for (int it = 0; it < c->opts.power_iters; ++it) {
         ib_apply<double>(c, l, v, s);
@@ -1026,12 +1034,12 @@ void power_A_enqueue(sib_ctx* c, int l, int slot, cudaStream_t s) {
         } else {
             KL(c, launch_power_A<double>(g, v, w, s));
         }
-        dot_into(c, w, w, nv, c->scal + slot, s);
+        dot_into(c, w, w, nv, c->scal + slot, s, part);
         KL(c, launch_scale(w, c->scal, slot, nv, s));
         std::swap(v, w);
     }
 }
-void power_M_enqueue(sib_ctx* c, int l, int slot, cudaStream_t s) {
+void power_M_enqueue(sib_ctx* c, int l, int slot, double* part, cudaStream_t s) {
     Level& lv = c->L[l];
     const int64_t np = (int64_t)lv.N * lv.N;
     double* v = (double*)lv.p[0].tp[0];
@@ -1043,7 +1051,7 @@ void power_M_enqueue(sib_ctx* c, int l, int slot, cudaStream_t s) {
     GridK<double> g = gridk<double>(c, l);
     const Cheb2<double> ka = cheb2<double>(lv.lamA, c->opts.cheb_lo, c->opts.cheb_hi);
     KL(c, launch_hash_vector(v, np, s));
-    dot_into(c, v, v, np, c->scal + slot, s);
+    dot_into(c, v, v, np, c->scal + slot, s, part);
     KL(c, launch_scale(v, c->scal, slot, np, s));
     for (int it = 0; it < c->opts.power_iters; ++it) {
         if (sc_fused(c)) {
@@ -1057,7 +1065,7 @@ void power_M_enqueue(sib_ctx* c, int l, int slot, cudaStream_t s) {
             KL(c, launch_divergence<double>(g, ya, md, s));
             precond_M<double>(c, l, md, w, 1.0, s);
         }
-        dot_into(c, w, w, np, c->scal + slot, s);
+        dot_into(c, w, w, np, c->scal + slot, s, part);
         KL(c, launch_scale(w, c->scal, slot, np, s));
         std::swap(v, w);
     }
@@ -1467,11 +1475,26 @@ void setup(sib_ctx* c, cudaStream_t s) {
         }
         if (!c->lamOverride && c->lmax > 0) {
             const int L = c->lmax;
-            for (int l = 1; l <= L; ++l) power_A_enqueue(c, l, 300 + l, s);
+            // the levels' chains side by side: a level on its own stream, except where the IB force
+            // goes through the markers (the marker buffers are shared), which stays on s in order
+            auto levels = [&](auto enqueue) {
+                CK(cudaEventRecord(c->evFork, s));
+                for (int l = 1; l <= L; ++l) {
+                    const bool own = (!c->haveIB || c->L[l].applyWindow) && l < sib_ctx::LVS && c->lvStream[l];
+                    cudaStream_t ls = own ? c->lvStream[l] : s;
+                    if (own) CK(cudaStreamWaitEvent(ls, c->evFork, 0));
+                    enqueue(l, c->part + (size_t)l * NBLK, ls);
+                    if (own) CK(cudaEventRecord(c->lvDone[l], ls));
+                }
+                for (int l = 1; l <= L; ++l)
+                    if ((!c->haveIB || c->L[l].applyWindow) && l < sib_ctx::LVS && c->lvStream[l])
+                        CK(cudaStreamWaitEvent(s, c->lvDone[l], 0));
+            };
+            levels([&](int l, double* part, cudaStream_t ls) { power_A_enqueue(c, l, 300 + l, part, ls); });
             CK(cudaMemcpyAsync(c->hbuf + 300, c->scal + 300, sizeof(double) * (L + 1), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             for (int l = 1; l <= L; ++l) c->L[l].lamA = std::sqrt(c->hbuf[300 + l]);
-            for (int l = 1; l <= L; ++l) power_M_enqueue(c, l, 320 + l, s);
+            levels([&](int l, double* part, cudaStream_t ls) { power_M_enqueue(c, l, 320 + l, part, ls); });
             CK(cudaMemcpyAsync(c->hbuf + 320, c->scal + 320, sizeof(double) * (L + 1), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             for (int l = 1; l <= L; ++l) c->L[l].lamM = std::sqrt(c->hbuf[320 + l]);
@@ -2077,6 +2100,10 @@ int sib_create(sib_ctx** out, int N, int n_min) {
         CK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&c->evFork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c->evJoin, cudaEventDisableTiming));
+        for (int l = 1; l <= lmax && l < sib_ctx::LVS; ++l) {
+            CK(cudaStreamCreateWithFlags(&c->lvStream[l], cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&c->lvDone[l], cudaEventDisableTiming));
+        }
         CK(cudaEventCreate(&c->ev0));
         CK(cudaEventCreate(&c->ev1));
         alloc_level_bufs(c);
@@ -2122,6 +2149,10 @@ void sib_destroy(sib_ctx* c) {
     if (c->aux) cudaStreamDestroy(c->aux);
     if (c->evFork) cudaEventDestroy(c->evFork);
     if (c->evJoin) cudaEventDestroy(c->evJoin);
+    for (int l = 0; l < sib_ctx::LVS; ++l) {
+        if (c->lvStream[l]) cudaStreamDestroy(c->lvStream[l]);
+        if (c->lvDone[l]) cudaEventDestroy(c->lvDone[l]);
+    }
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;
