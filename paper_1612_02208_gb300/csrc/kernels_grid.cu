@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(256) k_vanka(GridK<T> g, const T* __restrict__
 
 // Tiled form of the same sweep for levels with N >= 32 (tiles exactly TX x TY): x is staged in
 // shared memory with a two-cell halo by coalesced loads, index arithmetic uses compile-time tile
-// sizes, and cells of tiles without IB entries use the constant patch inverse (no divisions).
+// sizes, and cells of tiles without IB entries use the constant patch inverse (no divisions).  FP64
+// levels take k_vanka_tiled (one cell per thread), FP32 levels k_vanka_pair (two cells per thread).
 template <typename T>
 VankaBulk<T> vanka_bulk(double a0, double c, double inv_h) {
     const double det = a0 * a0 - c * c;
