@@ -78,7 +78,7 @@ def parse_args(argv=None):
     p.add_argument("--large-n", type=int, default=LARGE_N, help="grid of the large-grid V-cycle roofline")
     p.add_argument("--profile-setup", action="store_true",
                    help="the headline's set-up twice inside an NVTX range (for an ncu launch list)")
-    p.add_argument("--profile-vcycle", choices=["headline", "large", "large64", "large2k", "ras8o2"], default=None,
+    p.add_argument("--profile-vcycle", choices=["headline", "large", "large64", "large2k", "ras16", "ras8o2"], default=None,
                    help="two FP32 V-cycles in an NVTX range 'vcycle', with a one-vector FGMRES basis (the small-memory "
                         "case for ncu captures): 'headline' = the headline workload and smoother, 'large' = the "
                         "4096^2 thin ellipse with Vanka, 'large64' = the same body on 2048^2 with the FP64 V-cycle, "
@@ -1057,6 +1057,7 @@ def run_profile_vcycle(which):
     case ncu captures of the V-cycle kernels use.  'headline': the headline workload and smoother;
     'large': the 4096^2 thin ellipse (rho = 1, kappa = 1e4) with Vanka, the roofline leg's V-cycle;
     'large64': that body on 2048^2 with the FP64 V-cycle; 'large2k': that body on 2048^2 in FP32;
+    'ras16': the 128^2 thick annulus (Stokes, gamma = 50) with the paper's 16 x 16 boxes of overlap 4;
     'ras8o2': the 2048^2 grid without a structure
     (rho = 1), RAS with 8 x 8 boxes of overlap 2, their correction on the tensor cores."""
     import torch
@@ -1072,6 +1073,9 @@ def run_profile_vcycle(which):
     elif which == "large2k":   # the roofline leg's body on 2048^2, FP32, for full captures of its kernels
         prob = inputs.thin_ellipse_re(LARGE_N // 2, kappa=1e4, seed=2)
         opts = dict(smoother=sib.SMOOTHER_VANKA)
+    elif which == "ras16":   # the paper's 16 x 16 boxes with overlap 4: the 128^2 thick annulus, Stokes, gamma = 50
+        prob = inputs.paper_problem("annulus", 128, 50.0)
+        opts = dict(smoother=sib.SMOOTHER_RAS, box=HUGE_BOX[0], box_overlap=HUGE_BOX[1], ras_tc=1)
     elif which == "ras8o2":   # no structure: every box takes the tensor-core correction, about 3 GB on the device
         prob = inputs.no_structure(LARGE_N // 2, rho=1.0, seed=2)
         opts = dict(smoother=sib.SMOOTHER_RAS, box=WIDE_BOX[0], box_overlap=WIDE_BOX[1], ras_tc=1)

@@ -806,8 +806,11 @@ static_assert(MAX_N <= (1 << 15), "k_ras_apply_tc packs a box origin's two coord
 template <int NC, int PF>
 __global__ void __launch_bounds__(RT_THREADS + 32, 1)
     k_ras_apply_tc(RasGeo G, const int* __restrict__ slotOfBox, const float* __restrict__ pack, int npad, int nch,
-                   int nsb, int ns, int rowOff, float omega, const float* __restrict__ r, const float* x, float* xo,
-                   int* err) {
+                   int nsb, int ns, int rowOff, long long groupFloats, float omega, const float* __restrict__ r,
+                   const float* x, float* xo, int* err) {
+    // row group blockIdx.y: the next npad owned rows, from its own packed slice of the inverse
+    pack += (size_t)blockIdx.y * (size_t)groupFloats;
+    rowOff += (int)blockIdx.y * npad;
     extern __shared__ __align__(1024) unsigned char rt_smem[];
     __shared__ __align__(8) uint64_t tma_bar[RT_MAXSB];
     __shared__ __align__(8) uint64_t mma_bar[RT_MAXNS];    // the slot's MMAs are complete (one commit)
@@ -1653,7 +1656,8 @@ void launch_ras_tc_pack(int b, int o, const double* inv64, float* pack, cudaStre
 // as many inverse stages as the shared memory holds (all nch chunks where they fit).  False, and nothing
 // launched, where the shared memory cannot hold two inverse stages.
 bool launch_ras_apply_tc(int N, int b, int o, const int* slotOfBox, const float* pack, float omega, const float* r,
-                         const float* x, float* xo, int* err, cudaStream_t s, int rowOff = 0, int npadGroup = 0) {
+                         const float* x, float* xo, int* err, cudaStream_t s, int rowOff = 0, int npadGroup = 0,
+                         int groups = 1, long long groupFloats = 0) {
     const RasGeo G = ras_geo(N, b, o);
     const int npad = npadGroup > 0 ? npadGroup : ras_tc_npad(b), nch = (G.ne + RT_KC - 1) / RT_KC;
     // owned rows per thread, rounded up to whole TMEM loads; narrow boxes keep two chunks of residual
@@ -1694,13 +1698,14 @@ bool launch_ras_apply_tc(int N, int b, int o, const int* slotOfBox, const float*
         allowed[nc == 48] = smem;
     }
     const int ntiles = (G.nbs * G.nbs + RT_NB - 1) / RT_NB;
-    const dim3 grd(std::min(ntiles, sms)), blk(RT_THREADS + 32);   // 16 worker warps and the issuing warp
+    // 16 worker warps and the issuing warp; row groups (16 x 16 boxes) side by side along y
+    const dim3 grd(std::min(ntiles, sms), groups), blk(RT_THREADS + 32);
     if (nc == 16)
-        launch_pdl(k_ras_apply_tc<16, 2>, grd, blk, smem, s, G, slotOfBox, pack, npad, nch, nsb, ns, rowOff, omega, r, x,
-                   xo, err);
+        launch_pdl(k_ras_apply_tc<16, 2>, grd, blk, smem, s, G, slotOfBox, pack, npad, nch, nsb, ns, rowOff,
+                   groupFloats, omega, r, x, xo, err);
     else
-        launch_pdl(k_ras_apply_tc<48, 1>, grd, blk, smem, s, G, slotOfBox, pack, npad, nch, nsb, ns, rowOff, omega, r, x,
-                   xo, err);
+        launch_pdl(k_ras_apply_tc<48, 1>, grd, blk, smem, s, G, slotOfBox, pack, npad, nch, nsb, ns, rowOff,
+                   groupFloats, omega, r, x, xo, err);
     return true;
 }
 
@@ -1752,12 +1757,102 @@ template void launch_ras_huge_apply<float>(int, int, int, const float*, float, c
                                            cudaStream_t);
 template void launch_ras_huge_apply<double>(int, int, int, const double*, double, const double*, const double*,
                                             double*, cudaStream_t);
+// FP32 levels, spread over the GPU: the low-rank term of every IB box in three launches over (box, chunk),
+// so that the FP64 products run on every SM instead of one SM per IB box.  The same sums as
+// k_ras_wb_apply's FP32 branch: y_T = (L_0^{-1})_{T,:} r_k and z = W y_T a warp per row; the owned rows'
+// update a thread per row, reading (L_0^{-1})_{T, own} (L_0 is symmetric), so that a warp's reads of one
+// row of the inverse are consecutive.
+constexpr int WB_ROWS = 32;   // rows of T per block in the first two launches
+template <typename T>
+__global__ void __launch_bounds__(256) k_ras_wb_y(RasGeo G, const int* __restrict__ list, const int* __restrict__ offT,
+                                                  const int* __restrict__ Tl, const double* __restrict__ inv0,
+                                                  const T* __restrict__ r, double* __restrict__ yT) {
+    extern __shared__ double wb_rk[];   // ne: r_k
+    pdl_entry();   // every block waits (a block with no rows too), so completion orders the three launches
+    const int t0 = offT[blockIdx.x], m = offT[blockIdx.x + 1] - t0;
+    const int a0 = blockIdx.y * WB_ROWS;
+    if (a0 >= m) return;
+    const int N = G.N, n = N * N, mk = N - 1, ne = G.ne;
+    const int k = list[blockIdx.x];
+    const int I = k % G.nbs, J = k / G.nbs, i0 = I * G.b - G.o, j0 = J * G.b - G.o;
+    const int* Ts = Tl + t0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+        int comp, ii, jj;
+        ras_dof(G, q, comp, ii, jj);
+        wb_rk[q] = (double)r[(size_t)comp * n + (size_t)((j0 + jj) & mk) * N + ((i0 + ii) & mk)];
+    }
+    __syncthreads();
+    const int a1 = min(m, a0 + WB_ROWS);
+    for (int a = a0 + warp; a < a1; a += nw) {
+        const double* row = inv0 + (size_t)Ts[a] * ne;
+        double acc = 0.0;
+        for (int t = lane; t < ne; t += 32) acc += row[t] * wb_rk[t];
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) yT[t0 + a] = acc;
+    }
+}
+__global__ void __launch_bounds__(256) k_ras_wb_z(const int* __restrict__ offT, const long long* __restrict__ offW,
+                                                  const double* __restrict__ Wd, const double* __restrict__ yT,
+                                                  double* __restrict__ z) {
+    pdl_entry();
+    const int t0 = offT[blockIdx.x], m = offT[blockIdx.x + 1] - t0;
+    const int a0 = blockIdx.y * WB_ROWS;
+    if (a0 >= m) return;
+    const double* Wb = Wd + offW[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int a1 = min(m, a0 + WB_ROWS);
+    for (int a = a0 + warp; a < a1; a += nw) {
+        const double* row = Wb + (size_t)a * m;
+        double acc = 0.0;
+        for (int t = lane; t < m; t += 32) acc += row[t] * yT[t0 + t];
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) z[t0 + a] = acc;
+    }
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_ras_wb_out(RasGeo G, const int* __restrict__ list, const int* __restrict__ offT,
+                                                    const int* __restrict__ Tl, const double* __restrict__ inv0,
+                                                    const double* __restrict__ z, T omega, T* xo) {
+    pdl_entry();
+    const int rr = blockIdx.y * blockDim.x + threadIdx.x;
+    if (rr >= G.nown) return;
+    const int N = G.N, n = N * N, ne = G.ne, bb = G.b * G.b;
+    const int k = list[blockIdx.x];
+    const int I = k % G.nbs, J = k / G.nbs;
+    const int t0 = offT[blockIdx.x], m = offT[blockIdx.x + 1] - t0;
+    const int* Ts = Tl + t0;
+    const int q = ras_owned(G, rr);
+    double acc = 0.0;
+    for (int a = 0; a < m; ++a) acc += inv0[(size_t)Ts[a] * ne + q] * z[t0 + a];
+    const int comp = rr / bb, rem = rr - comp * bb;
+    const size_t d = (size_t)comp * n + (size_t)(J * G.b + rem / G.b) * N + I * G.b + rem % G.b;
+    xo[d] = (T)((double)xo[d] - (double)omega * acc);
+}
+
 template <typename T>
 void launch_ras_wb_apply(int N, int b, int o, const RasIB& ib, double a0, double c, double inv_h, double dt,
                          const int* list, int nIB, const int* offT, const int* Tl, const long long* offW,
-                         const double* W, const double* inv0, int mmax, T omega, const T* r, T* xo, cudaStream_t s) {
+                         const double* W, const double* inv0, int mmax, T omega, const T* r, T* xo, cudaStream_t s,
+                         double* scratch) {
     if (nIB <= 0) return;
     const RasGeo G = ras_geo(N, b, o);
+    if (sizeof(T) == 4 && scratch) {   // FP32: the low-rank term over the whole GPU
+        double* yT = scratch;
+        double* z = scratch + (size_t)mmax * nIB;   // the caller's scratch holds 2 mmax nIB values
+        const int chunks = (mmax + WB_ROWS - 1) / WB_ROWS;
+        const size_t smem = sizeof(double) * (size_t)G.ne;
+        static thread_local size_t allowedY = 48 * 1024;
+        if (smem > allowedY) {
+            cudaFuncSetAttribute(k_ras_wb_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            allowedY = smem;
+        }
+        launch_pdl(k_ras_wb_y<T>, dim3(nIB, chunks), dim3(256), smem, s, G, list, offT, Tl, inv0, r, yT);
+        launch_pdl(k_ras_wb_z, dim3(nIB, chunks), dim3(256), 0, s, offT, offW, W, (const double*)yT, z);
+        launch_pdl(k_ras_wb_out<T>, dim3(nIB, (G.nown + 255) / 256), dim3(256), 0, s, G, list, offT, Tl, inv0,
+                   (const double*)z, omega, xo);
+        return;
+    }
     const size_t smem = sizeof(double) * (4 * (size_t)G.ne + (size_t)mmax);
     static thread_local size_t allowed = 48 * 1024;
     if (smem > allowed) {
@@ -1769,10 +1864,10 @@ void launch_ras_wb_apply(int N, int b, int o, const RasIB& ib, double a0, double
 }
 template void launch_ras_wb_apply<float>(int, int, int, const RasIB&, double, double, double, double, const int*, int,
                                          const int*, const int*, const long long*, const double*, const double*, int,
-                                         float, const float*, float*, cudaStream_t);
+                                         float, const float*, float*, cudaStream_t, double*);
 template void launch_ras_wb_apply<double>(int, int, int, const RasIB&, double, double, double, double, const int*,
                                           int, const int*, const int*, const long long*, const double*,
-                                          const double*, int, double, const double*, double*, cudaStream_t);
+                                          const double*, int, double, const double*, double*, cudaStream_t, double*);
 size_t ras_tc_group_floats(int b, int o) {
     const RasGeo G = ras_geo(16, b, o);
     const int nch = (G.ne + RT_KC - 1) / RT_KC;
@@ -1785,9 +1880,10 @@ void launch_ras_tc_pack_rows(int b, int o, const double* inv0, int g, float* out
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
     k_ras_tc_pack_rows<<<blocks, 256, 0, s>>>(G, inv0, g * RAS_TC_GROUP, RAS_TC_GROUP, nch, out);
 }
-bool launch_ras_apply_tc_group(int N, int b, int o, const float* pack, int g, float omega, const float* r,
-                               const float* x, float* xo, int* err, cudaStream_t s) {
-    return launch_ras_apply_tc(N, b, o, nullptr, pack, omega, r, x, xo, err, s, g * RAS_TC_GROUP, RAS_TC_GROUP);
+bool launch_ras_apply_tc_groups(int N, int b, int o, const float* pack, int groups, float omega, const float* r,
+                                const float* x, float* xo, int* err, cudaStream_t s) {
+    return launch_ras_apply_tc(N, b, o, nullptr, pack, omega, r, x, xo, err, s, 0, RAS_TC_GROUP, groups,
+                               (long long)ras_tc_group_floats(b, o));
 }
 
 template <typename T>

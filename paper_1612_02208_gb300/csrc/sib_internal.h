@@ -165,11 +165,14 @@ void launch_ras_huge_apply(int N, int b, int o, const T* inv, T omega, const T* 
 template <typename T>
 void launch_ras_wb_apply(int N, int b, int o, const RasIB& ib, double a0, double c, double inv_h, double dt,
                          const int* list, int nIB, const int* offT, const int* Tl, const long long* offW,
-                         const double* W, const double* inv0, int mmax, T omega, const T* r, T* xo, cudaStream_t s);
+                         const double* W, const double* inv0, int mmax, T omega, const T* r, T* xo, cudaStream_t s,
+                         double* scratch = nullptr);   // FP32 with scratch (2 mmax nIB values): three launches
 size_t ras_tc_group_floats(int b, int o);
 void launch_ras_tc_pack_rows(int b, int o, const double* inv0, int g, float* out, cudaStream_t s);
-bool launch_ras_apply_tc_group(int N, int b, int o, const float* pack, int g, float omega, const float* r,
-                               const float* x, float* xo, int* err, cudaStream_t s);
+// the 16 x 16 boxes' shared correction on the tensor cores, all `groups` row groups of RAS_TC_GROUP owned
+// rows in one launch (pack: the groups' packed slices, ras_tc_group_floats apart)
+bool launch_ras_apply_tc_groups(int N, int b, int o, const float* pack, int groups, float omega, const float* r,
+                                const float* x, float* xo, int* err, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
 // Levels 1 and 0 of the V-cycle in one thread block (kernels_small.cu).

@@ -112,6 +112,7 @@ struct Level {
     int* wbT = nullptr;                  // the IB-touched local dofs of every IB box, ascending
     long long* wbOffW = nullptr;         // nIB offsets into wbW
     double* wbW = nullptr;               // W = (I + E Q)^-1 E per IB box
+    double* wbScratch = nullptr;         // 2 mmax nIB: y_T and z of the FP32 levels' low-rank term
     int wbMmax = 0;                      // largest |T|
 };
 
@@ -572,13 +573,9 @@ void ras_apply(sib_ctx* c, int l, const T* r, const T* x, T* xo, double omega, c
     if (ras_huge(b)) {   // 16 x 16 boxes: the shared correction of every box, then the IB boxes' update
         bool done = false;
         if (Prec<T>::id == 1 && c->opts.ras_tc) {
-            const size_t gf = ras_tc_group_floats(b, o);
-            done = true;
-            for (int g = 0; g < 3 * b * b / RAS_TC_GROUP && done; ++g) {
-                done = launch_ras_apply_tc_group(lv.N, b, o, lv.rasTC + g * gf, g, (float)omega, (const float*)r,
-                                                 (const float*)x, (float*)xo, c->herr, s);
-                if (done) ++c->launches;
-            }
+            done = launch_ras_apply_tc_groups(lv.N, b, o, lv.rasTC, 3 * b * b / RAS_TC_GROUP, (float)omega,
+                                              (const float*)r, (const float*)x, (float*)xo, c->herr, s);
+            if (done) ++c->launches;
         }
         if (!done) KL(c, launch_ras_huge_apply<T>(lv.N, b, o, (const T*)lv.hugeInv[pi], (T)omega, r, x, xo, s));
         if (lv.rasNIB > 0) {
@@ -586,7 +583,8 @@ void ras_apply(sib_ctx* c, int l, const T* r, const T* x, T* xo, double omega, c
             const double h = lv.h, a0 = c->rho / c->dt + 4.0 * c->mu / (h * h), cc = c->mu / (h * h);
             KL(c, launch_ras_wb_apply<T>(lv.N, b, o, ib, a0, cc, 1.0 / h, c->dt, lv.rasList, lv.rasNIB, lv.wbOffT,
                                          lv.wbT, lv.wbOffW, lv.wbW, (const double*)lv.hugeInv[0], lv.wbMmax,
-                                         (T)omega, r, xo, s));
+                                         (T)omega, r, xo, s, lv.wbScratch));
+            if (Prec<T>::id == 1) c->launches += 2;   // the FP32 form is three launches
         }
         return;
     }
@@ -1131,6 +1129,8 @@ void ras_huge_setup(sib_ctx* c, int l, int nIB, std::vector<void*>& tmp, int* gi
     dfree(c, lv.wbT);
     dfree(c, lv.wbOffW);
     dfree(c, lv.wbW);
+    dfree(c, lv.wbScratch);
+    lv.wbScratch = nullptr;
     lv.wbOffT = nullptr;
     lv.wbT = nullptr;
     lv.wbOffW = nullptr;
@@ -1156,6 +1156,7 @@ void ras_huge_setup(sib_ctx* c, int l, int nIB, std::vector<void*>& tmp, int* gi
     lv.wbOffW = (long long*)dalloc(c, sizeof(long long) * (size_t)nIB);
     lv.wbT = (int*)dalloc(c, sizeof(int) * (size_t)std::max(1, offT[nIB]));
     lv.wbW = (double*)dalloc(c, sizeof(double) * (size_t)std::max(1LL, wTot));
+    lv.wbScratch = (double*)dalloc(c, sizeof(double) * 2 * (size_t)std::max(1, lv.wbMmax) * (size_t)nIB);
     double* wwork = (double*)dalloc(c, sizeof(double) * (size_t)std::max(1LL, 2 * wTot));
     tmp.push_back(wwork);
     CK(cudaMemcpyAsync(lv.wbOffT, offT.data(), sizeof(int) * (size_t)(nIB + 1), cudaMemcpyHostToDevice, s));
