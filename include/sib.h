@@ -94,7 +94,8 @@ typedef struct {
     int    domain;        /* SIB_DOMAIN_PERIODIC (default) or SIB_DOMAIN_CAVITY (see below)          */
     int    ras_tc;        /* RAS, FP32 levels: the correction of the boxes that share one inverse runs
                              on the tensor cores (tcgen05, three TF32 products per pair for FP32
-                             accuracy) (1) or on the FP32 CUDA cores (0) (1)                         */
+                             accuracy) (1) or on the FP32 CUDA cores (0) (1).  With 16 x 16 boxes a
+                             level of fewer than 1,024 boxes takes the CUDA cores either way        */
     int    l2_persist;    /* the graphs' kernels keep the finest level's FP32 IB windows in the L2
                              cache (an access-policy window, with this process's persisting L2 limit
                              set to their size) (1) or treat them as any other data (0) (0: on the

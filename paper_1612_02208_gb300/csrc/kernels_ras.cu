@@ -1371,7 +1371,8 @@ __global__ void __launch_bounds__(RAS_WB_THREADS)
 // Shared correction of every box with 16 x 16 boxes, on the CUDA cores: a block takes RH_BX boxes,
 // gathers their windows into shared memory, and each warp walks owned rows: row own(r) of the shared
 // inverse, read once per block, against the RH_BX windows.  xo(owned) = x(owned) + omega c
-// (x == nullptr: 0).
+// (x == nullptr: 0).  Blocks along y split the owned rows (rows blockIdx.y, blockIdx.y + gridDim.y, ...
+// of the warps' walk), so that a level with few boxes still fills the GPU.
 constexpr int RH_BX = 8, RH_THREADS = 256;
 template <typename T>
 __global__ void __launch_bounds__(RH_THREADS)
@@ -1394,7 +1395,7 @@ __global__ void __launch_bounds__(RH_THREADS)
         win[t] = v;
     }
     __syncthreads();
-    for (int rr = warp; rr < G.nown; rr += nw) {
+    for (int rr = (int)blockIdx.y * nw + warp; rr < G.nown; rr += nw * (int)gridDim.y) {
         const T* row = inv + (size_t)ras_owned(G, rr) * ne;
         T acc[RH_BX];
 #pragma unroll
@@ -1750,28 +1751,37 @@ void launch_ras_huge_apply(int N, int b, int o, const T* inv, T omega, const T* 
         cudaFuncSetAttribute(k_ras_huge_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         allowed = smem;
     }
-    launch_pdl(k_ras_huge_apply<T>, dim3((G.nbs * G.nbs + RH_BX - 1) / RH_BX), dim3(RH_THREADS), smem, s, G, inv, omega,
-               r, x, xo);
+    // row splits: about two blocks per SM in all, at most one warp's row per split and warp
+    const int boxBlocks = (G.nbs * G.nbs + RH_BX - 1) / RH_BX, nw = RH_THREADS / 32;
+    const int splits = std::max(1, std::min((2 * 152 + boxBlocks - 1) / boxBlocks, (G.nown + nw - 1) / nw));
+    launch_pdl(k_ras_huge_apply<T>, dim3(boxBlocks, splits), dim3(RH_THREADS), smem, s, G, inv, omega, r, x, xo);
 }
 template void launch_ras_huge_apply<float>(int, int, int, const float*, float, const float*, const float*, float*,
                                            cudaStream_t);
 template void launch_ras_huge_apply<double>(int, int, int, const double*, double, const double*, const double*,
                                             double*, cudaStream_t);
-// FP32 levels, spread over the GPU: the low-rank term of every IB box in three launches over (box, chunk),
-// so that the FP64 products run on every SM instead of one SM per IB box.  The same sums as
-// k_ras_wb_apply's FP32 branch: y_T = (L_0^{-1})_{T,:} r_k and z = W y_T a warp per row; the owned rows'
-// update a thread per row, reading (L_0^{-1})_{T, own} (L_0 is symmetric), so that a warp's reads of one
-// row of the inverse are consecutive.
-constexpr int WB_ROWS = 32;   // rows of T per block in the first two launches
+// FP32 levels, spread over the GPU: every IB box's local solve in three launches over (box, chunk), so
+// that the FP64 products run on every SM instead of one SM per IB box.
+//   1. y = L_0^{-1} r_k on the rows T and on the owned rows, a warp per row;
+//   2. z = W y_T, a warp per row;
+//   3. xo(owned) = x(owned) + omega (y_own - (L_0^{-1})_{own,T} z), 32 owned rows per block and eight
+//      partial sums per row, reading (L_0^{-1})_{T,own} (L_0 is symmetric) so that a warp's reads of one
+//      row of the inverse are consecutive.
+// The owned values of an IB box are written whole, from FP64 sums.  With a stiff structure the shared
+// term y_own and the low-rank term nearly cancel, and the FP32 shared correction of those rows (already
+// written by the kernel for all boxes) would carry its rounding, scaled by that cancellation, into the
+// result.
+constexpr int WB_ROWS = 32;   // rows per block in the first two launches
 template <typename T>
 __global__ void __launch_bounds__(256) k_ras_wb_y(RasGeo G, const int* __restrict__ list, const int* __restrict__ offT,
                                                   const int* __restrict__ Tl, const double* __restrict__ inv0,
-                                                  const T* __restrict__ r, double* __restrict__ yT) {
+                                                  const T* __restrict__ r, double* __restrict__ yT,
+                                                  double* __restrict__ yOwn) {
     extern __shared__ double wb_rk[];   // ne: r_k
     pdl_entry();   // every block waits (a block with no rows too), so completion orders the three launches
     const int t0 = offT[blockIdx.x], m = offT[blockIdx.x + 1] - t0;
-    const int a0 = blockIdx.y * WB_ROWS;
-    if (a0 >= m) return;
+    const int a0 = blockIdx.y * WB_ROWS;   // rows a < m: T; a >= m: owned row a - m
+    if (a0 >= m + G.nown) return;
     const int N = G.N, n = N * N, mk = N - 1, ne = G.ne;
     const int k = list[blockIdx.x];
     const int I = k % G.nbs, J = k / G.nbs, i0 = I * G.b - G.o, j0 = J * G.b - G.o;
@@ -1783,13 +1793,18 @@ __global__ void __launch_bounds__(256) k_ras_wb_y(RasGeo G, const int* __restric
         wb_rk[q] = (double)r[(size_t)comp * n + (size_t)((j0 + jj) & mk) * N + ((i0 + ii) & mk)];
     }
     __syncthreads();
-    const int a1 = min(m, a0 + WB_ROWS);
+    const int a1 = min(m + G.nown, a0 + WB_ROWS);
     for (int a = a0 + warp; a < a1; a += nw) {
-        const double* row = inv0 + (size_t)Ts[a] * ne;
+        const double* row = inv0 + (size_t)(a < m ? Ts[a] : ras_owned(G, a - m)) * ne;
         double acc = 0.0;
         for (int t = lane; t < ne; t += 32) acc += row[t] * wb_rk[t];
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (lane == 0) yT[t0 + a] = acc;
+        if (lane == 0) {
+            if (a < m)
+                yT[t0 + a] = acc;
+            else
+                yOwn[(size_t)blockIdx.x * G.nown + (a - m)] = acc;
+        }
     }
 }
 __global__ void __launch_bounds__(256) k_ras_wb_z(const int* __restrict__ offT, const long long* __restrict__ offW,
@@ -1813,44 +1828,59 @@ __global__ void __launch_bounds__(256) k_ras_wb_z(const int* __restrict__ offT, 
 template <typename T>
 __global__ void __launch_bounds__(256) k_ras_wb_out(RasGeo G, const int* __restrict__ list, const int* __restrict__ offT,
                                                     const int* __restrict__ Tl, const double* __restrict__ inv0,
-                                                    const double* __restrict__ z, T omega, T* xo) {
+                                                    const double* __restrict__ z, const double* __restrict__ yOwn,
+                                                    T omega, const T* x, T* xo) {
+    // 32 owned rows per block; warp w sums the terms a = w, w + 8, ... of each row (lane = row), and
+    // the eight partial sums are added in warp order
+    __shared__ double part[8][32];
     pdl_entry();
-    const int rr = blockIdx.y * blockDim.x + threadIdx.x;
-    if (rr >= G.nown) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int rr = blockIdx.y * 32 + lane;
+    const bool live = rr < G.nown;
     const int N = G.N, n = N * N, ne = G.ne, bb = G.b * G.b;
-    const int k = list[blockIdx.x];
-    const int I = k % G.nbs, J = k / G.nbs;
     const int t0 = offT[blockIdx.x], m = offT[blockIdx.x + 1] - t0;
     const int* Ts = Tl + t0;
-    const int q = ras_owned(G, rr);
+    const int q = live ? ras_owned(G, rr) : 0;
     double acc = 0.0;
-    for (int a = 0; a < m; ++a) acc += inv0[(size_t)Ts[a] * ne + q] * z[t0 + a];
+    if (live)
+        for (int a = w; a < m; a += 8) acc += inv0[(size_t)Ts[a] * ne + q] * z[t0 + a];
+    part[w][lane] = acc;
+    __syncthreads();
+    if (w != 0 || !live) return;
+    double sum = part[0][lane];
+#pragma unroll
+    for (int v = 1; v < 8; ++v) sum += part[v][lane];
+    const int k = list[blockIdx.x];
+    const int I = k % G.nbs, J = k / G.nbs;
     const int comp = rr / bb, rem = rr - comp * bb;
     const size_t d = (size_t)comp * n + (size_t)(J * G.b + rem / G.b) * N + I * G.b + rem % G.b;
-    xo[d] = (T)((double)xo[d] - (double)omega * acc);
+    const double delta = yOwn[(size_t)blockIdx.x * G.nown + rr] - sum;
+    xo[d] = (T)((x ? (double)x[d] : 0.0) + (double)omega * delta);
 }
 
 template <typename T>
 void launch_ras_wb_apply(int N, int b, int o, const RasIB& ib, double a0, double c, double inv_h, double dt,
                          const int* list, int nIB, const int* offT, const int* Tl, const long long* offW,
                          const double* W, const double* inv0, int mmax, T omega, const T* r, T* xo, cudaStream_t s,
-                         double* scratch) {
+                         double* scratch, const T* x) {
     if (nIB <= 0) return;
     const RasGeo G = ras_geo(N, b, o);
-    if (sizeof(T) == 4 && scratch) {   // FP32: the low-rank term over the whole GPU
+    if (sizeof(T) == 4 && scratch) {   // FP32: the IB boxes' local solves over the whole GPU
+        // the caller's scratch holds (2 mmax + nown) nIB values
         double* yT = scratch;
-        double* z = scratch + (size_t)mmax * nIB;   // the caller's scratch holds 2 mmax nIB values
-        const int chunks = (mmax + WB_ROWS - 1) / WB_ROWS;
+        double* z = scratch + (size_t)mmax * nIB;
+        double* yOwn = z + (size_t)mmax * nIB;
+        const int chunks = (mmax + WB_ROWS - 1) / WB_ROWS, chunksY = (mmax + G.nown + WB_ROWS - 1) / WB_ROWS;
         const size_t smem = sizeof(double) * (size_t)G.ne;
         static thread_local size_t allowedY = 48 * 1024;
         if (smem > allowedY) {
             cudaFuncSetAttribute(k_ras_wb_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             allowedY = smem;
         }
-        launch_pdl(k_ras_wb_y<T>, dim3(nIB, chunks), dim3(256), smem, s, G, list, offT, Tl, inv0, r, yT);
+        launch_pdl(k_ras_wb_y<T>, dim3(nIB, chunksY), dim3(256), smem, s, G, list, offT, Tl, inv0, r, yT, yOwn);
         launch_pdl(k_ras_wb_z, dim3(nIB, chunks), dim3(256), 0, s, offT, offW, W, (const double*)yT, z);
-        launch_pdl(k_ras_wb_out<T>, dim3(nIB, (G.nown + 255) / 256), dim3(256), 0, s, G, list, offT, Tl, inv0,
-                   (const double*)z, omega, xo);
+        launch_pdl(k_ras_wb_out<T>, dim3(nIB, (G.nown + 31) / 32), dim3(256), 0, s, G, list, offT, Tl, inv0,
+                   (const double*)z, (const double*)yOwn, omega, x, xo);
         return;
     }
     const size_t smem = sizeof(double) * (4 * (size_t)G.ne + (size_t)mmax);
@@ -1864,10 +1894,11 @@ void launch_ras_wb_apply(int N, int b, int o, const RasIB& ib, double a0, double
 }
 template void launch_ras_wb_apply<float>(int, int, int, const RasIB&, double, double, double, double, const int*, int,
                                          const int*, const int*, const long long*, const double*, const double*, int,
-                                         float, const float*, float*, cudaStream_t, double*);
+                                         float, const float*, float*, cudaStream_t, double*, const float*);
 template void launch_ras_wb_apply<double>(int, int, int, const RasIB&, double, double, double, double, const int*,
                                           int, const int*, const int*, const long long*, const double*,
-                                          const double*, int, double, const double*, double*, cudaStream_t, double*);
+                                          const double*, int, double, const double*, double*, cudaStream_t, double*,
+                                          const double*);
 size_t ras_tc_group_floats(int b, int o) {
     const RasGeo G = ras_geo(16, b, o);
     const int nch = (G.ne + RT_KC - 1) / RT_KC;

@@ -148,7 +148,11 @@ void launch_ras_tc_pack(int b, int o, const double* inv64, float* pack, cudaStre
 // low-rank (Woodbury) update of it for the IB boxes: T lists (IB-touched dofs, ascending), W = (I + E Q)^-1 E
 // per box (row-major |T| x |T| at offW); the shared correction of every box, then the IB boxes' update
 constexpr int RAS_BOX_HUGE = 16;
-constexpr int RAS_TC_GROUP = 192;   // owned rows per tensor-core launch with 16 x 16 boxes (768 = 4 x 192)
+constexpr int RAS_TC_GROUP = 192;   // owned rows per tensor-core row group with 16 x 16 boxes (768 = 4 x 192)
+// 16 x 16 boxes: levels with fewer boxes than this take the CUDA-core correction, split over rows, even
+// with the tensor-core option on (a few tiles of 128 boxes leave the tensor-core form a few CTAs, each
+// walking the whole K = 1,776 in sequence)
+constexpr int RAS_TC_MIN_BOXES = 1024;
 bool ras_huge(int b);
 int ras_huge_n(int b, int o);
 void launch_ras_huge_assemble(int N, int b, int o, double a0, double c, double inv_h, double* Aug, cudaStream_t s);
@@ -166,7 +170,9 @@ template <typename T>
 void launch_ras_wb_apply(int N, int b, int o, const RasIB& ib, double a0, double c, double inv_h, double dt,
                          const int* list, int nIB, const int* offT, const int* Tl, const long long* offW,
                          const double* W, const double* inv0, int mmax, T omega, const T* r, T* xo, cudaStream_t s,
-                         double* scratch = nullptr);   // FP32 with scratch (2 mmax nIB values): three launches
+                         double* scratch = nullptr, const T* x = nullptr);
+// (FP32 with scratch, (2 mmax + 3 b^2) nIB values: three launches, which write the IB boxes' owned values
+// whole from x, distinct from xo; x == nullptr: zero)
 size_t ras_tc_group_floats(int b, int o);
 void launch_ras_tc_pack_rows(int b, int o, const double* inv0, int g, float* out, cudaStream_t s);
 // the 16 x 16 boxes' shared correction on the tensor cores, all `groups` row groups of RAS_TC_GROUP owned

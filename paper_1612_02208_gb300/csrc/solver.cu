@@ -112,7 +112,7 @@ struct Level {
     int* wbT = nullptr;                  // the IB-touched local dofs of every IB box, ascending
     long long* wbOffW = nullptr;         // nIB offsets into wbW
     double* wbW = nullptr;               // W = (I + E Q)^-1 E per IB box
-    double* wbScratch = nullptr;         // 2 mmax nIB: y_T and z of the FP32 levels' low-rank term
+    double* wbScratch = nullptr;         // (2 mmax + 3 b^2) nIB: y_T, z and y_own of the FP32 levels' IB boxes
     int wbMmax = 0;                      // largest |T|
 };
 
@@ -560,7 +560,8 @@ const float* ras_tc_pack_for(const sib_ctx* c, const Level& lv) {
     return (Prec<T>::id == 1 && c->opts.ras_tc) ? lv.rasTC : nullptr;
 }
 
-// one RAS correction on level l: xo = x + omega Rt^T L_k^{-1} r (x == nullptr: zero initial guess)
+// one RAS correction on level l: xo = x + omega Rt^T L_k^{-1} r (x == nullptr: zero initial guess; x and xo
+// are distinct buffers)
 template <typename T>
 void ras_apply(sib_ctx* c, int l, const T* r, const T* x, T* xo, double omega, cudaStream_t s) {
     Level& lv = c->L[l];
@@ -572,7 +573,7 @@ void ras_apply(sib_ctx* c, int l, const T* r, const T* x, T* xo, double omega, c
     }
     if (ras_huge(b)) {   // 16 x 16 boxes: the shared correction of every box, then the IB boxes' update
         bool done = false;
-        if (Prec<T>::id == 1 && c->opts.ras_tc) {
+        if (Prec<T>::id == 1 && c->opts.ras_tc && (lv.N / b) * (lv.N / b) >= RAS_TC_MIN_BOXES) {
             done = launch_ras_apply_tc_groups(lv.N, b, o, lv.rasTC, 3 * b * b / RAS_TC_GROUP, (float)omega,
                                               (const float*)r, (const float*)x, (float*)xo, c->herr, s);
             if (done) ++c->launches;
@@ -583,7 +584,7 @@ void ras_apply(sib_ctx* c, int l, const T* r, const T* x, T* xo, double omega, c
             const double h = lv.h, a0 = c->rho / c->dt + 4.0 * c->mu / (h * h), cc = c->mu / (h * h);
             KL(c, launch_ras_wb_apply<T>(lv.N, b, o, ib, a0, cc, 1.0 / h, c->dt, lv.rasList, lv.rasNIB, lv.wbOffT,
                                          lv.wbT, lv.wbOffW, lv.wbW, (const double*)lv.hugeInv[0], lv.wbMmax,
-                                         (T)omega, r, xo, s, lv.wbScratch));
+                                         (T)omega, r, xo, s, lv.wbScratch, x));
             if (Prec<T>::id == 1) c->launches += 2;   // the FP32 form is three launches
         }
         return;
@@ -1156,7 +1157,7 @@ void ras_huge_setup(sib_ctx* c, int l, int nIB, std::vector<void*>& tmp, int* gi
     lv.wbOffW = (long long*)dalloc(c, sizeof(long long) * (size_t)nIB);
     lv.wbT = (int*)dalloc(c, sizeof(int) * (size_t)std::max(1, offT[nIB]));
     lv.wbW = (double*)dalloc(c, sizeof(double) * (size_t)std::max(1LL, wTot));
-    lv.wbScratch = (double*)dalloc(c, sizeof(double) * 2 * (size_t)std::max(1, lv.wbMmax) * (size_t)nIB);
+    lv.wbScratch = (double*)dalloc(c, sizeof(double) * (2 * (size_t)std::max(1, lv.wbMmax) + 3 * (size_t)b * b) * nIB);
     double* wwork = (double*)dalloc(c, sizeof(double) * (size_t)std::max(1LL, 2 * wTot));
     tmp.push_back(wwork);
     CK(cudaMemcpyAsync(lv.wbOffT, offT.data(), sizeof(int) * (size_t)(nIB + 1), cudaMemcpyHostToDevice, s));
