@@ -646,20 +646,22 @@ __global__ void __launch_bounds__(VK2_THREADS, 8)
     }
 }
 
-// Tensor map of a level vector [u | v | p] viewed as N x N x 3 (column fastest) with a box of
-// VK_W x rows x 3; false if the base is not 16-byte aligned or the driver cannot encode it.
-// Encoded maps are kept per thread, keyed by (base, N, element size, rows).
-static bool field_map(CUtensorMap* out, const void* base, int N, int es, int rows) {
+// Tensor map of a level vector [u | v | p] (comps = 3) or of the IB force [f_u | f_v] (comps = 2)
+// viewed as N x N x comps (column fastest) with a box of boxW x rows x comps; false if the base is not
+// 16-byte aligned or the driver cannot encode it.  Encoded maps are kept per thread, keyed by (base, N,
+// element size, rows, box width, components).
+static bool field_map(CUtensorMap* out, const void* base, int N, int es, int rows, int boxW = VK_W, int comps = 3) {
     struct Entry {
         const void* p;
-        int N, es, rows;
+        int N, es, rows, boxW, comps;
         CUtensorMap m;
     };
     constexpr int CACHE = 32;
     static thread_local Entry cache[CACHE];
     static thread_local int used = 0, next = 0;
     for (int k = 0; k < used; ++k)
-        if (cache[k].p == base && cache[k].N == N && cache[k].es == es && cache[k].rows == rows) {
+        if (cache[k].p == base && cache[k].N == N && cache[k].es == es && cache[k].rows == rows &&
+            cache[k].boxW == boxW && cache[k].comps == comps) {
             *out = cache[k].m;
             return true;
         }
@@ -673,9 +675,9 @@ static bool field_map(CUtensorMap* out, const void* base, int N, int es, int row
         return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
     }();
     if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, 3};
+    const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)comps};
     const cuuint64_t strides[2] = {(cuuint64_t)N * es, (cuuint64_t)N * N * es};
-    const cuuint32_t box[3] = {(cuuint32_t)VK_W, (cuuint32_t)rows, 3};
+    const cuuint32_t box[3] = {(cuuint32_t)boxW, (cuuint32_t)rows, (cuuint32_t)comps};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUtensorMap m;
     const CUresult r = enc(&m, es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
@@ -684,7 +686,7 @@ static bool field_map(CUtensorMap* out, const void* base, int N, int es, int row
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return false;
     Entry& e = cache[next];
-    e = Entry{base, N, es, rows, m};
+    e = Entry{base, N, es, rows, boxW, comps, m};
     next = (next + 1) % CACHE;
     if (used < CACHE) ++used;
     *out = m;
@@ -761,7 +763,10 @@ constexpr int RR_CX = 32, RR_CY = 8;                 // coarse cells per block
 constexpr int RR_FX = 2 * RR_CX, RR_FY = 2 * RR_CY;  // fine cells per block
 constexpr int RR_W = RR_FX + 8;                      // staged row width (columns fi0-4 .. fi0+67)
 constexpr int RR_XH = RR_FY + 4, RR_BH = RR_FY + 2;  // staged rows of x (fj0-2 ..) and of b, f (fj0-1 ..)
-constexpr int RR_WORDS = (3 * RR_XH + 3 * RR_BH + 2 * RR_BH) * RR_W;
+// staged x (3 x RR_XH rows), b (3 x RR_BH) and, from a 128-byte boundary, the IB force (2 x RR_BH)
+constexpr int RR_FOFF = ((3 * RR_XH + 3 * RR_BH) * RR_W + 31) / 32 * 32;
+constexpr int RR_WORDS = RR_FOFF + 2 * RR_BH * RR_W;
+static_assert((3 * RR_XH * RR_W) % 32 == 0, "the staged b starts on a 128-byte boundary");
 template <typename T>
 struct RRVec;
 template <>
@@ -775,20 +780,23 @@ struct RRVec<double> {
     using pair = double2;
 };
 template <typename T>
-__global__ void __launch_bounds__(RR_CX * RR_CY) k_residual_restrict_tiled(GridK<T> g, const T* __restrict__ x,
+__global__ void __launch_bounds__(RR_CX * RR_CY) k_residual_restrict_tiled(GridK<T> g,
+                                                                           const __grid_constant__ CUtensorMap mx,
+                                                                           const __grid_constant__ CUtensorMap mb,
+                                                                           const __grid_constant__ CUtensorMap mf,
+                                                                           int tma, const T* __restrict__ x,
                                                                            const T* __restrict__ b,
                                                                            T* __restrict__ bc) {
-    using VT = typename RRVec<T>::type;
-    constexpr int VN = 16 / (int)sizeof(T);
-    constexpr int RV = RR_W / VN;                             // vectors per staged row
-    constexpr int NROWS = 3 * RR_XH + 3 * RR_BH + 2 * RR_BH;  // staged rows: x, b, f
+    constexpr int NXB = 3 * RR_XH + 3 * RR_BH;                 // staged rows of x and b
+    constexpr int NROWS = NXB + 2 * RR_BH;                     // and of the IB force
     constexpr int NT = RR_CX * RR_CY;
-    constexpr int PER = (NROWS * RV + NT - 1) / NT;            // vectors per thread
-    extern __shared__ __align__(16) unsigned char rr_smem[];
-    T* st = reinterpret_cast<T*>(rr_smem);   // NROWS x RR_W: x (3 x RR_XH rows), b (3 x RR_BH), f (2 x RR_BH)
-    T* sx = st;
-    T* sb = st + 3 * RR_XH * RR_W;
-    T* sf = sb + 3 * RR_BH * RR_W;
+    extern __shared__ unsigned char rr_smem[];
+    __shared__ __align__(8) uint64_t rr_bar;
+    // the staged tile from a 128-byte boundary (the launch adds 128 bytes): the TMA boxes land there
+    T* st = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(rr_smem) + 127) & ~(uintptr_t)127);
+    T* sx = st;                       // 3 x RR_XH rows
+    T* sb = st + 3 * RR_XH * RR_W;    // 3 x RR_BH rows
+    T* sf = st + RR_FOFF;             // 2 x RR_BH rows
     const int N = g.N, n = N * N, m = N - 1, Nc = N / 2;
     const int tid = threadIdx.y * RR_CX + threadIdx.x;
     const int fi0 = blockIdx.x * RR_FX, fj0 = blockIdx.y * RR_FY;
@@ -799,53 +807,63 @@ __global__ void __launch_bounds__(RR_CX * RR_CY) k_residual_restrict_tiled(GridK
         act = g.tile[tj * g.ntx + ti] || g.tile[tj * g.ntx + ti + 1] || g.tile[(tj + 1) * g.ntx + ti] ||
               g.tile[(tj + 1) * g.ntx + ti + 1];
     }
-    const int rows = act ? NROWS : 3 * RR_XH + 3 * RR_BH;
-    // staged row r: source array, component and grid row
-    auto src_row = [&](int r, const T*& base, int& gj) {
-        if (r < 3 * RR_XH) {
-            const int comp = r / RR_XH;
-            base = x + (size_t)comp * n;
-            gj = fj0 - 2 + (r - comp * RR_XH);
-        } else if (r < 3 * RR_XH + 3 * RR_BH) {
-            const int rr = r - 3 * RR_XH, comp = rr / RR_BH;
-            base = b + (size_t)comp * n;
-            gj = fj0 - 1 + (rr - comp * RR_BH);
-        } else {
-            const int rr = r - 3 * RR_XH - 3 * RR_BH, comp = rr / RR_BH;
-            base = g.fib + (size_t)comp * n;
-            gj = fj0 - 1 + (rr - comp * RR_BH);
-        }
-    };
-    pdl_entry();
+    // tiles whose staged rows and columns lie inside the grid take three TMA box copies (x, b and the
+    // IB force); the others (the periodic wrap) gather element by element
     const bool interior = fi0 >= 4 && fi0 + RR_FX + 4 <= N && fj0 >= 2 && fj0 + RR_FY + 2 <= N;
-    if (interior) {
-        VT v[PER];
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {   // every load issued before the first store
-            const int q = tid + k * NT;
-            if (q < rows * RV) {
-                const int r = q / RV, cv = q - r * RV;
-                const T* base;
-                int gj;
-                src_row(r, base, gj);
-                v[k] = *reinterpret_cast<const VT*>(base + (size_t)gj * N + fi0 - 4 + cv * VN);
-            }
+    const bool bulk = tma && interior;
+    if (bulk) {
+        if (tid == 0) {
+            tma_prefetch_map(&mx);
+            tma_prefetch_map(&mb);
+            if (act) tma_prefetch_map(&mf);
+            mbar_init(&rr_bar, 1);
+            fence_mbar_init();
         }
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int q = tid + k * NT;
-            if (q < rows * RV) reinterpret_cast<VT*>(st)[q] = v[k];
+        __syncthreads();
+    }
+    pdl_entry();
+    if (bulk) {
+        if (tid == 0) {
+            constexpr uint32_t bx = 3 * RR_XH * RR_W * sizeof(T), bb3 = 3 * RR_BH * RR_W * sizeof(T),
+                               bf = 2 * RR_BH * RR_W * sizeof(T);
+            mbar_expect_tx(&rr_bar, bx + bb3 + (act ? bf : 0u));
+            tma_load_3d(sx, &mx, &rr_bar, fi0 - 4, fj0 - 2, 0);
+            tma_load_3d(sb, &mb, &rr_bar, fi0 - 4, fj0 - 1, 0);
+            if (act) tma_load_3d(sf, &mf, &rr_bar, fi0 - 4, fj0 - 1, 0);
+        }
+        const bool ok = mbar_wait_bounded(&rr_bar, 0, VK_WAIT_LIMIT);
+        if (!__syncthreads_and(ok)) {   // copies never completed: report, let them drain, leave
+            if (tid == 0 && g.err) *(volatile int*)g.err = SIB_DEV_ERR_TMA_WAIT;
+            mbar_wait_bounded(&rr_bar, 0, VK_WAIT_LIMIT);
+            return;
         }
     } else {
+        const int rows = act ? NROWS : NXB;
         for (int q = tid; q < rows * RR_W; q += NT) {
             const int r = q / RR_W, cc = q - r * RR_W;
             const T* base;
             int gj;
-            src_row(r, base, gj);
-            st[q] = base[(size_t)(gj & m) * N + ((fi0 - 4 + cc) & m)];
+            T* dst;
+            if (r < 3 * RR_XH) {
+                const int comp = r / RR_XH;
+                base = x + (size_t)comp * n;
+                gj = fj0 - 2 + (r - comp * RR_XH);
+                dst = sx + r * RR_W;
+            } else if (r < NXB) {
+                const int rr = r - 3 * RR_XH, comp = rr / RR_BH;
+                base = b + (size_t)comp * n;
+                gj = fj0 - 1 + (rr - comp * RR_BH);
+                dst = sb + rr * RR_W;
+            } else {
+                const int rr = r - NXB, comp = rr / RR_BH;
+                base = g.fib + (size_t)comp * n;
+                gj = fj0 - 1 + (rr - comp * RR_BH);
+                dst = sf + rr * RR_W;
+            }
+            dst[cc] = base[(size_t)(gj & m) * N + ((fi0 - 4 + cc) & m)];
         }
+        __syncthreads();
     }
-    __syncthreads();
     using P2 = typename RRVec<T>::pair;
     const T* U = sx;
     const T* V = sx + RR_XH * RR_W;
@@ -872,68 +890,68 @@ __global__ void __launch_bounds__(RR_CX * RR_CY) k_residual_restrict_tiled(GridK
     T su, sv, sp;
     T du[2][2];   // U(xi + 1) - U(xi) of the p residuals, rows 2J, 2J + 1, columns 2I, 2I + 1
     {
-        T u[4][6], pp[2][4], bu[2][4], fu[2][4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) pairs(U, r0 + 1 + r, 0, 3, u[r]);
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            pairs(P, r0 + 2 + r, 0, 2, pp[r]);
-            pairs(Bu, r0 + 1 + r, 0, 2, bu[r]);
-            if (act) pairs(Fu, r0 + 1 + r, 0, 2, fu[r]);
-        }
+        // u residuals at fine columns 2I - 1 + a (k = 1 + a), row 2J + r, one row at a time: x rows
+        // 2J + 1 + r .. 2J + 3 + r (staged rows r0 + 1 + r ..), b and f row 2J + 1 + r
         T ru[2][3];
 #pragma unroll
-        for (int r = 0; r < 2; ++r)
+        for (int r = 0; r < 2; ++r) {
+            T u[3][6], pp[4], bu[4], fu[4];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) pairs(U, r0 + 1 + r + q, 0, 3, u[q]);
+            pairs(P, r0 + 2 + r, 0, 2, pp);
+            pairs(Bu, r0 + 1 + r, 0, 2, bu);
+            if (act) pairs(Fu, r0 + 1 + r, 0, 2, fu);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                const int k = 1 + a, ur = 1 + r;
-                T Au = g.a0 * u[ur][k] - g.c * ((u[ur][k + 1] + u[ur][k - 1]) + (u[ur + 1][k] + u[ur - 1][k])) +
-                       (pp[r][k] - pp[r][k - 1]) * g.inv_h;
-                Au -= g.dt * (act ? fu[r][k] : T(0));
-                ru[r][a] = bu[r][k] - Au;
+                const int k = 1 + a;
+                T Au = g.a0 * u[1][k] - g.c * ((u[1][k + 1] + u[1][k - 1]) + (u[2][k] + u[0][k])) +
+                       (pp[k] - pp[k - 1]) * g.inv_h;
+                Au -= g.dt * (act ? fu[k] : T(0));
+                ru[r][a] = bu[k] - Au;
             }
+#pragma unroll
+            for (int a = 0; a < 2; ++a) du[r][a] = u[1][3 + a] - u[1][2 + a];
+        }
         // ru[r][a]: fine column 2I - 1 + a
         su = (ru[0][1] + ru[1][1]) + T(0.5) * ((ru[0][2] + ru[1][2]) + (ru[0][0] + ru[1][0]));
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int a = 0; a < 2; ++a) du[r][a] = u[1 + r][3 + a] - u[1 + r][2 + a];
     }
     {
-        // v residuals at fine columns 2I + a (k = 2 + a), rows 2J - 1 + r: x rows 2J + 1 + r (v rows
-        // 1 + r of v[], loaded from staged rows 2J ..), b and f rows 2J + r
-        T v[5][6], pp[4][2], bv[3][2], fv[3][2], bp[2][2];
-#pragma unroll
-        for (int r = 0; r < 5; ++r) pairs(V, r0 + r, 0, 3, v[r]);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) pairs(P, r0 + r, 2, 1, pp[r]);
+        // v residuals at fine columns 2I + a (k = 2 + a), row 2J - 1 + r, one row at a time: x rows
+        // 2J + r .. 2J + 2 + r (staged rows r0 + r ..), b and f row 2J + r
+        T rv[3][2], dv[2][2];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            pairs(Bv, r0 + r, 2, 1, bv[r]);
-            if (act) pairs(Fv, r0 + r, 2, 1, fv[r]);
-        }
+            T v[3][6], pc[2], pm[2], bv[2], fv[2];
 #pragma unroll
-        for (int r = 0; r < 2; ++r) pairs(Bp, r0 + 1 + r, 2, 1, bp[r]);
-        // v[vr][j]: staged column c0 + j (fine column 2I - 2 + j), staged row 2J + vr
-        T rv[3][2];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
+            for (int q = 0; q < 3; ++q) pairs(V, r0 + r + q, 0, 3, v[q]);
+            pairs(P, r0 + 1 + r, 2, 1, pc);   // P at the v face's row and the row below
+            pairs(P, r0 + r, 2, 1, pm);
+            pairs(Bv, r0 + r, 2, 1, bv);
+            if (act) pairs(Fv, r0 + r, 2, 1, fv);
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
-                const int k = 2 + a, vr = 1 + r;
-                T Av = g.a0 * v[vr][k] - g.c * ((v[vr][k + 1] + v[vr][k - 1]) + (v[vr + 1][k] + v[vr - 1][k])) +
-                       (pp[vr][a] - pp[vr - 1][a]) * g.inv_h;
-                Av -= g.dt * (act ? fv[r][a] : T(0));
-                rv[r][a] = bv[r][a] - Av;
+                const int k = 2 + a;
+                T Av = g.a0 * v[1][k] - g.c * ((v[1][k + 1] + v[1][k - 1]) + (v[2][k] + v[0][k])) +
+                       (pc[a] - pm[a]) * g.inv_h;
+                Av -= g.dt * (act ? fv[a] : T(0));
+                rv[r][a] = bv[a] - Av;
             }
+            // V(xi, xj + 1) - V(xi, xj) of the p residual of row 2J - 2 + r (rows 2J and 2J + 1)
+            if (r >= 1) {
+#pragma unroll
+                for (int a = 0; a < 2; ++a) dv[r - 1][a] = v[2][2 + a] - v[1][2 + a];
+            }
+        }
         // rv[r][a]: fine row 2J - 1 + r, column 2I + a
         sv = (rv[1][0] + rv[1][1]) + T(0.5) * ((rv[2][0] + rv[2][1]) + (rv[0][0] + rv[0][1]));
         T rp[2][2];
 #pragma unroll
-        for (int r = 0; r < 2; ++r)
+        for (int r = 0; r < 2; ++r) {
+            T bp[2];
+            pairs(Bp, r0 + 1 + r, 2, 1, bp);
 #pragma unroll
-            for (int a = 0; a < 2; ++a)
-                rp[r][a] = bp[r][a] + (du[r][a] + (v[3 + r][2 + a] - v[2 + r][2 + a])) * g.inv_h;
+            for (int a = 0; a < 2; ++a) rp[r][a] = bp[a] + (du[r][a] + dv[r][a]) * g.inv_h;
+        }
         sp = (rp[0][0] + rp[0][1]) + (rp[1][0] + rp[1][1]);
     }
     const int I = blockIdx.x * RR_CX + threadIdx.x, J = blockIdx.y * RR_CY + threadIdx.y;
@@ -947,13 +965,24 @@ template <typename T>
 void launch_residual_restrict(const GridK<T>& g, const T* x, const T* b, T* bc, cudaStream_t s) {
     const int Nc = g.N / 2;
     if (Nc >= RR_CX && g.tx == TX && g.ty == TY) {   // fine tiles of 32 x 8: two by two per block
-        const size_t smem = sizeof(T) * (size_t)RR_WORDS;
+        const size_t smem = sizeof(T) * (size_t)RR_WORDS + 128;   // 128: room to align the staged tile
         static thread_local bool enabled = false;
         if (!enabled) {
             cudaFuncSetAttribute(k_residual_restrict_tiled<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             enabled = true;
         }
-        launch_pdl(k_residual_restrict_tiled<T>, dim3(Nc / RR_CX, Nc / RR_CY), dim3(RR_CX, RR_CY), smem, s, g, x, b, bc);
+        CUtensorMap mx, mb, mf;
+        std::memset(&mx, 0, sizeof(mx));
+        std::memset(&mb, 0, sizeof(mb));
+        std::memset(&mf, 0, sizeof(mf));
+        // interior tiles exist from N = 4 RR_FX on (a tile's staged columns reach 4 beyond it on each side);
+        // the maps are only read by those tiles, the IB force's only where a tile is IB-active
+        const int es = (int)sizeof(T);
+        const int tma = g.N >= 4 * RR_FX && field_map(&mx, x, g.N, es, RR_XH, RR_W, 3) &&
+                        field_map(&mb, b, g.N, es, RR_BH, RR_W, 3) &&
+                        (!g.tile || !g.fib || field_map(&mf, g.fib, g.N, es, RR_BH, RR_W, 2));
+        launch_pdl(k_residual_restrict_tiled<T>, dim3(Nc / RR_CX, Nc / RR_CY), dim3(RR_CX, RR_CY), smem, s, g, mx, mb,
+                   mf, tma, x, b, bc);
         return;
     }
     dim3 blk(Nc < 32 ? Nc : 32, Nc < 8 ? Nc : 8);
