@@ -61,7 +61,7 @@ CSRC = os.path.join(ROOT, "paper_1612_02208_gb300", "csrc")
 # the source text of each roofline kernel: file, first and last marker (the kernel and its launcher)
 KERNEL_SOURCES = {
     "k_ib_window_f32": ("kernels_ib.cu", "struct WinVec;", "template void launch_ib_window<float>"),
-    "k_vanka_f32": ("kernels_grid.cu", "k_vanka_pair(GridK<T> g", "void launch_vanka("),
+    "k_vanka_f32": ("kernels_grid.cu", "k_vanka_pair(GridK<T> g", "// Tensor map of a level vector"),
 }
 
 
@@ -588,7 +588,7 @@ def large_vcycle(sib, torch, reps=20, N=None):
     lmax = S.num_levels - 1
     out = {"workload": f"thin_ellipse_re_N{LARGE}_kappa1e4", "N": LARGE, "vcycle_ms": round(t_v, 4),
            "vcycle_mdofs": round(n3 / (t_v * 1e-3) / 1e6, 1), "kernels": {}}
-    for name in ("vanka", "residual", "restrict", "prolong", "interp", "spread"):
+    for name in ("vanka", "residual", "restrict", "residual_restrict", "prolong", "interp", "spread"):
         ms, by = S.time_kernel(name, lmax, True, reps=20)
         out["kernels"][name] = {"ms": round(ms, 5), "bytes": by, "gbs": round(by / (ms * 1e-3) / 1e9, 1)}
     for (bx, ov), key in (((4, 1), "ras"), (WIDE_BOX, "ras8o2")):

@@ -235,6 +235,7 @@ int sib_advance_markers(sib_ctx* ctx, const double* w, double* X_next, void* str
 #define SIB_KERNEL_PROLONG   5   /* prolongation-correction from level-1 to `level`                   */
 #define SIB_KERNEL_RAS       6   /* box RAS correction from a residual (needs the RAS smoother's setup) */
 #define SIB_KERNEL_IB_WINDOW 7   /* the IB force [S K J]^l u through the level's assembled windows      */
+#define SIB_KERNEL_RESIDUAL_RESTRICT 8   /* the fused residual r = b - L x and its restriction to level-1 */
 #define SIB_TIME_COLD     0x100  /* or-ed into `kernel`: no warm-up launch before the timed ones, so that
                                     a caller who flushes L2 first (and times reps = 1) gets a cold launch */
 /* Times `reps` back-to-back launches of one kernel of the V-cycle on `level` (operands: the

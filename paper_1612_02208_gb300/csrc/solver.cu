@@ -1936,6 +1936,9 @@ void time_kernel(sib_ctx* c, int kernel, int l, int reps, bool cold, cudaStream_
             case SIB_KERNEL_RESTRICT:
                 launch_restrict<T>(c->L[l - 1].N, (const T*)b.r, (T*)c->L[l - 1].p[pi].b, s);
                 break;
+            case SIB_KERNEL_RESIDUAL_RESTRICT:
+                launch_residual_restrict<T>(g, (const T*)b.x, (const T*)b.b, (T*)c->L[l - 1].p[pi].b, s);
+                break;
             case SIB_KERNEL_PROLONG:
                 launch_prolong_add<T>(c->L[l - 1].N, (const T*)c->L[l - 1].p[pi].x, (T*)b.x, s);
                 break;
@@ -1968,6 +1971,9 @@ void time_kernel(sib_ctx* c, int kernel, int l, int reps, bool cold, cudaStream_
             break;
         case SIB_KERNEL_RESTRICT:
             by = 3.0 * n * w + 0.75 * n * w;
+            break;
+        case SIB_KERNEL_RESIDUAL_RESTRICT:   // x, b read; the coarse residual written; f_IB in active tiles
+            by = 6.0 * n * w + 0.75 * n * w + 2.0 * active * w;
             break;
         case SIB_KERNEL_PROLONG:
             by = 0.75 * n * w + 6.0 * n * w;
@@ -2604,7 +2610,7 @@ int sib_time_kernel(sib_ctx* c, int kernel, int l, int prec, int reps, void* str
     check_level(c, l, 0);
     if (!valid_prec(prec) || reps < 1 || !ms || !bytes) throw SibError(SIB_ERR_ARG, "bad argument");
     if ((kernel == SIB_KERNEL_RESTRICT || kernel == SIB_KERNEL_PROLONG || kernel == SIB_KERNEL_VANKA ||
-         kernel == SIB_KERNEL_RAS) && l < 1)
+         kernel == SIB_KERNEL_RAS || kernel == SIB_KERNEL_RESIDUAL_RESTRICT) && l < 1)
         throw SibError(SIB_ERR_ARG, "kernel needs level >= 1");
     if (kernel == SIB_KERNEL_RAS && c->opts.smoother != SIB_SMOOTHER_RAS)
         throw SibError(SIB_ERR_STATE, "the RAS kernel needs the RAS smoother set up");

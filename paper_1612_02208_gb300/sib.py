@@ -46,7 +46,8 @@ EXPORTS = [
     "sib_device_bytes", "sib_spread_noalloc", "sib_advance_markers",
 ]
 TIME_COLD = 0x100
-KERNELS = {"vanka": 0, "residual": 1, "spread": 2, "interp": 3, "restrict": 4, "prolong": 5, "ras": 6, "ib_window": 7}
+KERNELS = {"vanka": 0, "residual": 1, "spread": 2, "interp": 3, "restrict": 4, "prolong": 5, "ras": 6, "ib_window": 7,
+           "residual_restrict": 8}
 
 
 class SibOpts(ctypes.Structure):
