@@ -1242,7 +1242,7 @@ constexpr int RAS_WB_THREADS = 256;
 __global__ void __launch_bounds__(RAS_WB_THREADS)
     k_ras_wb_setup(RasGeo G, RasIB ib, double dt, const int* __restrict__ list, const int* __restrict__ offT,
                    const int* __restrict__ Tl, const long long* __restrict__ offW, const double* __restrict__ inv0,
-                   double* __restrict__ work, double* __restrict__ W, int* __restrict__ info) {
+                   double* __restrict__ work, double* __restrict__ W, int* __restrict__ info, int mOneMax) {
     extern __shared__ double smem_wb[];
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int k = list[blockIdx.x];
@@ -1310,6 +1310,7 @@ __global__ void __launch_bounds__(RAS_WB_THREADS)
         __syncwarp();
     }
     __syncthreads();
+    if (m > mOneMax) return;   // a large box: [I + E Q | E] is eliminated by the blocked Gauss-Jordan
     for (int kk = 0; kk < m; ++kk) {
         double best = -1.0;
         int bi = kk;
@@ -1733,14 +1734,44 @@ void launch_ras_wb_fill(int N, int b, int o, const RasIB& ib, const int* list, i
 }
 void launch_ras_wb_setup(int N, int b, int o, const RasIB& ib, double dt, const int* list, int nIB, const int* offT,
                          const int* T, const long long* offW, const double* inv0, double* work, double* W, int* info,
-                         int mmax, cudaStream_t s) {
+                         int mmax, int mOneMax, cudaStream_t s) {
     if (nIB <= 0) return;
     const int nw = RAS_WB_THREADS / 32;
     const size_t smem = sizeof(double) * (3 * (size_t)mmax + 32) +
                         sizeof(int) * (32 + nw * WIN_SIZE + ((nw * WIN_SIZE) & 1)) + sizeof(double) * nw * WIN_SIZE;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_ras_wb_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_ras_wb_setup<<<nIB, RAS_WB_THREADS, smem, s>>>(ras_geo(N, b, o), ib, dt, list, offT, T, offW, inv0, work, W,
-                                                     info);
+                                                     info, mOneMax);
+}
+
+// A large IB box's [I + E Q | E] (m x 2m, row-major) into the blocked Gauss-Jordan's layout, padded to
+// m16 (a multiple of 16) with identity rows: Aug is m16 x 2 m16, [A | B] with A = I + E Q and B = E.
+__global__ void k_ras_wb_pad(const double* __restrict__ Mx, int m, int m16, double* __restrict__ Aug) {
+    const int i = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < 2 * m16; j += gridDim.x * blockDim.x) {
+        double v = 0.0;
+        if (i < m) {
+            if (j < m) v = Mx[(size_t)i * 2 * m + j];
+            else if (j >= m16 && j < m16 + m) v = Mx[(size_t)i * 2 * m + m + (j - m16)];
+        } else if (j == i) {
+            v = 1.0;
+        }
+        Aug[(size_t)i * 2 * m16 + j] = v;
+    }
+}
+// W = A^{-1} B from the eliminated Aug: row a is the right half of pivot row piv[a]
+__global__ void k_ras_wb_take(const double* __restrict__ Aug, const int* __restrict__ piv, int m, int m16,
+                              double* __restrict__ Wb) {
+    const int a = blockIdx.y;
+    const double* row = Aug + (size_t)piv[a] * 2 * m16 + m16;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) Wb[(size_t)a * m + c] = row[c];
+}
+void launch_ras_wb_big(const double* Mx, int m, double* Aug, int* piv, void* work, int* info, double* Wb,
+                       cudaStream_t s) {
+    const int m16 = (m + 15) / 16 * 16;
+    k_ras_wb_pad<<<dim3((2 * m16 + 255) / 256, m16), 256, 0, s>>>(Mx, m, m16, Aug);
+    launch_gauss_jordan(Aug, m16, info, piv, work, s);
+    k_ras_wb_take<<<dim3((m + 255) / 256, m), 256, 0, s>>>(Aug, piv, m, m16, Wb);
 }
 template <typename T>
 void launch_ras_huge_apply(int N, int b, int o, const T* inv, T omega, const T* r, const T* x, T* xo, cudaStream_t s) {

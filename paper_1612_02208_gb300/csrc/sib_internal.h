@@ -163,7 +163,13 @@ void launch_ras_wb_fill(int N, int b, int o, const RasIB& ib, const int* list, i
                         cudaStream_t s);
 void launch_ras_wb_setup(int N, int b, int o, const RasIB& ib, double dt, const int* list, int nIB, const int* offT,
                          const int* T, const long long* offW, const double* inv0, double* work, double* W, int* info,
-                         int mmax, cudaStream_t s);
+                         int mmax, int mOneMax, cudaStream_t s);
+// boxes with |T| > RAS_WB_ONE_MAX: launch_ras_wb_setup only fills their [I + E Q | E] (Mx, m x 2m); this
+// eliminates it by the blocked Gauss-Jordan (Aug: m16 x 2 m16, piv: m16, work: gauss_jordan_work_bytes(m16),
+// m16 = m rounded up to 16) and writes W (m x m)
+constexpr int RAS_WB_ONE_MAX = 256;
+void launch_ras_wb_big(const double* Mx, int m, double* Aug, int* piv, void* work, int* info, double* Wb,
+                       cudaStream_t s);
 template <typename T>
 void launch_ras_huge_apply(int N, int b, int o, const T* inv, T omega, const T* r, const T* x, T* xo, cudaStream_t s);
 template <typename T>

@@ -1164,7 +1164,24 @@ void ras_huge_setup(sib_ctx* c, int l, int nIB, std::vector<void*>& tmp, int* gi
     CK(cudaMemcpyAsync(lv.wbOffW, offW.data(), sizeof(long long) * (size_t)nIB, cudaMemcpyHostToDevice, s));
     KL(c, launch_ras_wb_fill(lv.N, b, o, ib, lv.rasList, nIB, lv.wbOffT, lv.wbT, s));
     KL(c, launch_ras_wb_setup(lv.N, b, o, ib, c->dt, lv.rasList, nIB, lv.wbOffT, lv.wbT, lv.wbOffW,
-                              (const double*)lv.hugeInv[0], wwork, lv.wbW, c->rasInfo, lv.wbMmax, s));
+                              (const double*)lv.hugeInv[0], wwork, lv.wbW, c->rasInfo, lv.wbMmax, RAS_WB_ONE_MAX, s));
+    // boxes with many IB-touched dofs: their [I + E Q | E] by the blocked Gauss-Jordan over the whole GPU,
+    // one box after another (one block per box would leave each |T|^3 elimination to a single SM)
+    int bigMax = 0;
+    for (int k = 0; k < nIB; ++k)
+        if (cnt[k] > RAS_WB_ONE_MAX) bigMax = std::max(bigMax, cnt[k]);
+    if (bigMax > 0) {
+        const int m16 = (bigMax + 15) / 16 * 16;
+        double* augB = (double*)dalloc(c, sizeof(double) * (size_t)m16 * 2 * m16);
+        int* pivB = (int*)dalloc(c, sizeof(int) * (size_t)m16);
+        void* workB = dalloc(c, gauss_jordan_work_bytes(m16));
+        tmp.insert(tmp.end(), {augB, pivB, workB});
+        for (int k = 0; k < nIB; ++k)
+            if (cnt[k] > RAS_WB_ONE_MAX) {
+                launch_ras_wb_big(wwork + 2 * offW[k], cnt[k], augB, pivB, workB, c->rasInfo, lv.wbW + offW[k], s);
+                c->launches += 2 + 3 * ((cnt[k] + 15) / 16);
+            }
+    }
     CK(cudaStreamSynchronize(s));   // the host vectors above are the copies' sources
     c->launches += 3;
 }
