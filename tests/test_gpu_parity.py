@@ -579,3 +579,23 @@ def test_iteration_counts_match_stored_oracle_histories():
         S.set_options(vcycle_fp32=1)
         S.solve(cu(prob.g), allow_unconverged=True)
         assert abs(S.stats.iterations - rec["iterations"]) <= 1, key
+
+
+def test_time_kernel_every_kernel_id():
+    """sib_time_kernel launches each kernel of the V-cycle on a level and reports a positive time and
+    its algorithmic bytes; the fused residual and restriction moves 6.75 words per fine cell plus the IB
+    force of the active tiles (FP32 and FP64)."""
+    prob = I.disk_stokes(128, kappa=1e2)
+    S = sib.solver_for(prob)
+    lmax = S.num_levels - 1
+    n = 128 * 128
+    for name in ("vanka", "residual", "restrict", "residual_restrict", "prolong", "interp", "spread", "ib_window"):
+        for fp32 in (True, False):
+            ms, by = S.time_kernel(name, lmax, fp32, reps=2)
+            assert ms > 0 and by > 0, (name, fp32, ms, by)
+            if name == "residual_restrict":
+                w = 4 if fp32 else 8
+                assert 6.75 * n * w <= by <= (6.75 + 2.0) * n * w, (fp32, by)
+    with pytest.raises(sib.SibError):
+        S.time_kernel("residual_restrict", 0, True)   # the coarsest level has nothing to restrict to
+    S.close()
