@@ -1012,9 +1012,11 @@ void alloc_krylov(sib_ctx* c) {
 }
 
 // Power iterations for lambda_max of DA^{-1} A_IB and of DM^{-1} D At^{-1} G on level l (FP64),
-// from the hash start vector; everything stays on the device, ||w||^2 of the last iterate lands in
-// scal[slot] (setup reads all levels back with one synchronisation per operator).  A level's chain
-// touches only that level's buffers, its slot and its own NBLK partial sums (part).
+// from the normalised hash start vector, without renormalising between steps (the growth over the
+// steps stays far inside FP64's range): ||A v||^2 of the last step lands in scal[slot] and ||v||^2 in
+// scal[slot + 40], so that lambda = (||A v|| / ||v||), the normalised iteration's estimate (setup reads
+// all levels back with one synchronisation per operator).  A level's chain touches only that level's
+// buffers, its slots and its own NBLK partial sums (part).
 void power_A_enqueue(sib_ctx* c, int l, int slot, double* part, cudaStream_t s) {
     Level& lv = c->L[l];
     const int64_t nv = 2LL * lv.N * lv.N;
@@ -1033,10 +1035,10 @@ void power_A_enqueue(sib_ctx* c, int l, int slot, double* part, cudaStream_t s) 
         } else {
             KL(c, launch_power_A<double>(g, v, w, s));
         }
-        dot_into(c, w, w, nv, c->scal + slot, s, part);
-        KL(c, launch_scale(w, c->scal, slot, nv, s));
-        std::swap(v, w);
+        if (it + 1 < c->opts.power_iters) std::swap(v, w);
     }
+    dot_into(c, w, w, nv, c->scal + slot, s, part);
+    dot_into(c, v, v, nv, c->scal + slot + 40, s, part);
 }
 void power_M_enqueue(sib_ctx* c, int l, int slot, double* part, cudaStream_t s) {
     Level& lv = c->L[l];
@@ -1064,10 +1066,10 @@ void power_M_enqueue(sib_ctx* c, int l, int slot, double* part, cudaStream_t s) 
             KL(c, launch_divergence<double>(g, ya, md, s));
             precond_M<double>(c, l, md, w, 1.0, s);
         }
-        dot_into(c, w, w, np, c->scal + slot, s, part);
-        KL(c, launch_scale(w, c->scal, slot, np, s));
-        std::swap(v, w);
+        if (it + 1 < c->opts.power_iters) std::swap(v, w);
     }
+    dot_into(c, w, w, np, c->scal + slot, s, part);
+    dot_into(c, v, v, np, c->scal + slot + 40, s, part);
 }
 
 // Box RAS set-up on levels 1..lmax (Sec. 3.3, Alg. 2 with boxes): classify the boxes by whether
@@ -1510,13 +1512,13 @@ void setup(sib_ctx* c, cudaStream_t s) {
                         CK(cudaStreamWaitEvent(s, c->lvDone[l], 0));
             };
             levels([&](int l, double* part, cudaStream_t ls) { power_A_enqueue(c, l, 300 + l, part, ls); });
-            CK(cudaMemcpyAsync(c->hbuf + 300, c->scal + 300, sizeof(double) * (L + 1), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(c->hbuf + 300, c->scal + 300, sizeof(double) * 60, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            for (int l = 1; l <= L; ++l) c->L[l].lamA = std::sqrt(c->hbuf[300 + l]);
+            for (int l = 1; l <= L; ++l) c->L[l].lamA = std::sqrt(c->hbuf[300 + l] / c->hbuf[340 + l]);
             levels([&](int l, double* part, cudaStream_t ls) { power_M_enqueue(c, l, 320 + l, part, ls); });
-            CK(cudaMemcpyAsync(c->hbuf + 320, c->scal + 320, sizeof(double) * (L + 1), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(c->hbuf + 320, c->scal + 320, sizeof(double) * 60, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            for (int l = 1; l <= L; ++l) c->L[l].lamM = std::sqrt(c->hbuf[320 + l]);
+            for (int l = 1; l <= L; ++l) c->L[l].lamM = std::sqrt(c->hbuf[320 + l] / c->hbuf[360 + l]);
         }
     }
     CK(cudaStreamWaitEvent(s, c->evJoin, 0));
